@@ -1,0 +1,824 @@
+/*
+ * dsmc_oracle.c -- plain FP64 CPU oracle of dSMC (de-Sequentialized Monte Carlo,
+ * Corenflos, Chopin and Sarkka, arXiv 2202.02264).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call this
+ * file: only the tests, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
+ * legs use it.  It shares no code, header or constant table with the CUDA library.
+ *
+ * What it follows, step by step and in the paper's order:
+ *   - Algorithm 2 (smoother initialisation): independent proposals q_t, leaf weights
+ *     h_0 P_0 / q_0 at t = 0 and nu_t / q_t for t >= 1, normalisation, L_t = mean weight.
+ *   - Appendix A, Algorithm 6 (ParallelReshapeCombination): left-aligned blocks of size
+ *     2^l; at level l, block pair (2m, 2m+1) is combined when the right block exists,
+ *     otherwise the left block is passed through unchanged.
+ *   - Algorithm 1 (Combine) with the product-form weights of Eq. (normalized-weights)
+ *     and the stitching weight omega_c = p_c h_c / nu_c of Proposition 2; the
+ *     trajectories are copied explicitly, as the two ParFor loops of Algorithm 1 do.
+ *   - The normalising-constant increment of Eq. (Lab), weighted form.
+ *   - Algorithm 5 (ConditionalCombine) and the star-trajectory draw of Section 3.1.
+ *   - Algorithm 8 (rejection-sampling lazy resampling), with (I, J, u) redrawn at every
+ *     attempt (standard rejection sampling) and an attempt cap.
+ *
+ * Readings of the paper this file takes (they are listed with reasons in the design
+ * notes): time runs t = 0..K-1; pair index m/i is the left block (time c-1) and n/j the
+ * right block (time c); multinomial resampling by inverse CDF on the row-major flattened
+ * N x N matrix with one uniform per output slot; conditional slot 0 is the reference
+ * trajectory; the next reference comes from one extra pair draw at the root.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel random numbers:
+ * as easy as 1, 2, 3", SC'11), key = 64-bit seed, counter = (slot, id, purpose | base<<4,
+ * j).  The conversions to uniforms are:
+ *   u24(w)     = ((w >> 8) + 0.5) * 2^-24        (exactly representable in FP32 and FP64)
+ *   u53(w0,w1) = (((w0 << 21) | (w1 >> 11)) + 0.5) * 2^-53
+ * Normals are Box-Muller pairs from (u24(w0), u24(w1)) and (u24(w2), u24(w3)).
+ *
+ * Build: gcc -O2 -std=c11 -fPIC -shared -ffp-contract=off -fopenmp (no -ffast-math).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PURPOSE_INIT 1u
+#define ORC_PURPOSE_DENSE 2u
+#define ORC_PURPOSE_RS 3u
+
+#define ORC_OK 0
+#define ORC_ERR_INVALID 1
+#define ORC_ERR_OOM 3
+#define ORC_ERR_DEGENERATE 7
+#define ORC_ERR_RS_LIMIT 8
+
+/* ------------------------------------------------------------------------------------ */
+/* Philox4x32-10                                                                          */
+/* ------------------------------------------------------------------------------------ */
+
+/* One Philox4x32 round: two 32x32->64 multiplications by the round constants, the high
+ * halves xor-ed with the other two words and the round key, the words permuted. */
+static void philox_round(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+  uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+  uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+  uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+  uint32_t n0 = hi1 ^ c[1] ^ k0;
+  uint32_t n2 = hi0 ^ c[3] ^ k1;
+  c[0] = n0;
+  c[1] = lo1;
+  c[2] = n2;
+  c[3] = lo0;
+}
+
+/* Ten rounds; the key is bumped by the Weyl constants before every round but the first. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    philox_round(c, k0, k1);
+  }
+  out[0] = c[0];
+  out[1] = c[1];
+  out[2] = c[2];
+  out[3] = c[3];
+}
+
+/* Many counters at once (for the CPU/GPU stream comparison). ctrs: [n][4], out: [n][4]. */
+void orc_philox_many(int64_t n, const uint32_t* ctrs, const uint32_t key[2], uint32_t* out) {
+  for (int64_t i = 0; i < n; ++i) orc_philox4x32_10(ctrs + 4 * i, key, out + 4 * i);
+}
+
+static void draw(uint32_t seed_lo, uint32_t seed_hi, uint32_t slot, uint32_t id,
+                 uint32_t purpose, uint32_t base, uint32_t j, uint32_t w[4]) {
+  uint32_t ctr[4] = {slot, id, purpose | (base << 4), j};
+  uint32_t key[2] = {seed_lo, seed_hi};
+  orc_philox4x32_10(ctr, key, w);
+}
+
+static double u24(uint32_t w) { return ((double)(w >> 8) + 0.5) * 0x1p-24; }
+static double u53(uint32_t w0, uint32_t w1) {
+  uint64_t m = ((uint64_t)w0 << 21) | (uint64_t)(w1 >> 11);
+  return ((double)m + 0.5) * 0x1p-53;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Model: state-space model of Eq. (ssm) / Feynman-Kac form of Eq. (fk)                   */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct {
+  int kind; /* 0: linear-Gaussian x_t = A x_{t-1} + N(0,Q), y_t = x_t + N(0,R), x_0 ~ N(m0,P0)
+               1: stochastic volatility x_t = mu + phi (x_{t-1} - mu) + sigma e,
+                  y_t = exp(x_t / 2) v, x_0 ~ N(mu, sigma^2 / (1 - phi^2)), d = 1 */
+  int d;
+  const double *A, *Q, *R, *m0, *P0; /* row-major d x d / d */
+  double mu, phi, sigma;
+  int prop_kind;     /* 0: q_t = N(y_t, s^2 I);  1: q_t = N(mean_t, diag(std_t^2)) */
+  double prop_scale; /* s */
+  const double *prop_mean, *prop_std; /* [K][d] when prop_kind == 1 */
+  int nu;            /* 0: nu_t = q_t;  1: nu_t proportional to h_t(y_t | .) */
+} orc_model;
+
+typedef struct {
+  int K, N;
+  uint32_t seed_lo, seed_hi, counter_base;
+  int resampler; /* 0: multinomial inverse CDF on the full N x N matrix; 1: rejection */
+  uint32_t rs_max_attempts;
+  int conditional;
+} orc_config;
+
+static const double LOG_2PI = 1.8378770664093454835606594728112;
+
+/* Cholesky factor L (lower) of a d x d SPD matrix; returns 0 on success. */
+static int cholesky(int d, const double* S, double* L) {
+  memset(L, 0, sizeof(double) * d * d);
+  for (int i = 0; i < d; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = S[i * d + j];
+      for (int k = 0; k < j; ++k) s -= L[i * d + k] * L[j * d + k];
+      if (i == j) {
+        if (!(s > 0.0)) return -1;
+        L[i * d + i] = sqrt(s);
+      } else {
+        L[i * d + j] = s / L[j * d + j];
+      }
+    }
+  }
+  return 0;
+}
+
+/* log N(x; m, L L^T) by forward substitution. */
+static double gauss_logpdf_chol(int d, const double* x, const double* m, const double* L) {
+  double z[64];
+  double quad = 0.0, logdet = 0.0;
+  for (int i = 0; i < d; ++i) {
+    double s = x[i] - m[i];
+    for (int k = 0; k < i; ++k) s -= L[i * d + k] * z[k];
+    z[i] = s / L[i * d + i];
+    quad += z[i] * z[i];
+    logdet += log(L[i * d + i]);
+  }
+  return -0.5 * quad - logdet - 0.5 * d * LOG_2PI;
+}
+
+static double normal_logpdf(double x, double m, double s) {
+  double z = (x - m) / s;
+  return -0.5 * z * z - log(s) - 0.5 * LOG_2PI;
+}
+
+typedef struct {
+  const orc_model* m;
+  int K;
+  const double* y; /* [K][d] */
+  double LQ[32 * 32], LR[32 * 32], LP0[32 * 32];
+} model_ctx;
+
+static int ctx_init(model_ctx* c, const orc_model* m, int K, const double* y) {
+  c->m = m;
+  c->K = K;
+  c->y = y;
+  if (m->d < 1 || m->d > 32) return ORC_ERR_INVALID;
+  if (m->kind == 0) {
+    if (cholesky(m->d, m->Q, c->LQ) || cholesky(m->d, m->R, c->LR) || cholesky(m->d, m->P0, c->LP0))
+      return ORC_ERR_INVALID;
+  } else if (m->kind == 1) {
+    if (m->d != 1 || !(m->sigma > 0.0) || !(fabs(m->phi) < 1.0)) return ORC_ERR_INVALID;
+  } else {
+    return ORC_ERR_INVALID;
+  }
+  return ORC_OK;
+}
+
+/* log p_t(x' | x): transition density P_t of Eq. (ssm). */
+static double log_f(const model_ctx* c, const double* x, const double* xn) {
+  const orc_model* m = c->m;
+  if (m->kind == 0) {
+    double mean[32];
+    for (int i = 0; i < m->d; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < m->d; ++k) s += m->A[i * m->d + k] * x[k];
+      mean[i] = s;
+    }
+    return gauss_logpdf_chol(m->d, xn, mean, c->LQ);
+  }
+  return normal_logpdf(xn[0], m->mu + m->phi * (x[0] - m->mu), m->sigma);
+}
+
+/* sup over (x, x') of log p_t(x' | x): the Gaussian density at its mode. */
+static double log_f_max(const model_ctx* c) {
+  const orc_model* m = c->m;
+  if (m->kind == 0) {
+    double logdet = 0.0;
+    for (int i = 0; i < m->d; ++i) logdet += log(c->LQ[i * m->d + i]);
+    return -logdet - 0.5 * m->d * LOG_2PI;
+  }
+  return -log(m->sigma) - 0.5 * LOG_2PI;
+}
+
+/* log h_t(y_t | x): observation density. */
+static double log_h(const model_ctx* c, int t, const double* x) {
+  const orc_model* m = c->m;
+  const double* yt = c->y + (size_t)t * m->d;
+  if (m->kind == 0) return gauss_logpdf_chol(m->d, yt, x, c->LR);
+  /* y | x ~ N(0, exp(x)) */
+  return -0.5 * LOG_2PI - 0.5 * x[0] - 0.5 * yt[0] * yt[0] * exp(-x[0]);
+}
+
+/* log P_0(x): prior of x_0. */
+static double log_p0(const model_ctx* c, const double* x) {
+  const orc_model* m = c->m;
+  if (m->kind == 0) return gauss_logpdf_chol(m->d, x, m->m0, c->LP0);
+  double s0 = m->sigma / sqrt(1.0 - m->phi * m->phi);
+  return normal_logpdf(x[0], m->mu, s0);
+}
+
+static void prop_params(const model_ctx* c, int t, int i, double* mean, double* sd) {
+  const orc_model* m = c->m;
+  if (m->prop_kind == 0) {
+    *mean = c->y[(size_t)t * m->d + i];
+    *sd = m->prop_scale;
+  } else {
+    *mean = m->prop_mean[(size_t)t * m->d + i];
+    *sd = m->prop_std[(size_t)t * m->d + i];
+  }
+}
+
+/* log q_t(x): independent diagonal-Gaussian proposal. */
+static double log_q(const model_ctx* c, int t, const double* x) {
+  double s = 0.0;
+  for (int i = 0; i < c->m->d; ++i) {
+    double mu, sd;
+    prop_params(c, t, i, &mu, &sd);
+    s += normal_logpdf(x[i], mu, sd);
+  }
+  return s;
+}
+
+/* log nu_t(x) for t >= 1 (Definition 1): either q_t itself, or h_t(y_t | .) normalised
+ * over x.  For the linear-Gaussian model with identity observation matrix the latter is
+ * N(x; y_t, R); for the stochastic-volatility model the integral of h_t over x is 1/|y_t|. */
+static double log_nu(const model_ctx* c, int t, const double* x) {
+  const orc_model* m = c->m;
+  if (m->nu == 0) return log_q(c, t, x);
+  if (m->kind == 0) return log_h(c, t, x);
+  return log_h(c, t, x) + log(fabs(c->y[t]));
+}
+
+/* log omega_c(x_{c-1}, x_c) = log p_c(x_c | x_{c-1}) + log h_c(x_c) - log nu_c(x_c)
+ * (Proposition 2, Eq. weights-formula). */
+static double log_omega(const model_ctx* c, int tc, const double* xprev, const double* xcur) {
+  return log_f(c, xprev, xcur) + log_h(c, tc, xcur) - log_nu(c, tc, xcur);
+}
+
+/* Box-Muller normals for particle (t, n): dims 4j..4j+3 come from the counter j. */
+static void draw_particle(const orc_config* cf, int d, int t, int n, double* z) {
+  for (int j = 0; 4 * j < d; ++j) {
+    uint32_t w[4];
+    draw(cf->seed_lo, cf->seed_hi, (uint32_t)n, (uint32_t)t, ORC_PURPOSE_INIT, cf->counter_base,
+         (uint32_t)j, w);
+    for (int p = 0; p < 2; ++p) {
+      double u1 = u24(w[2 * p]), u2 = u24(w[2 * p + 1]);
+      double r = sqrt(-2.0 * log(u1));
+      double th = 6.283185307179586476925286766559 * u2;
+      int k0 = 4 * j + 2 * p;
+      if (k0 < d) z[k0] = r * cos(th);
+      if (k0 + 1 < d) z[k0 + 1] = r * sin(th);
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Algorithm 2: smoother initialisation                                                  */
+/* ------------------------------------------------------------------------------------ */
+
+/* X: [K][N][d]; logw: [K][N] normalised log-weights; logL: [K] log L_t.
+ * x_ref (conditional mode, Section 3.2): slot 0 at every t is x_ref[t], weighted like the
+ * others.  Returns ORC_OK or an error code. */
+int orc_init(const orc_model* m, const orc_config* cf, const double* y, const double* x_ref,
+             double* X, double* logw, double* logL) {
+  model_ctx c;
+  int st = ctx_init(&c, m, cf->K, y);
+  if (st) return st;
+  const int K = cf->K, N = cf->N, d = m->d;
+#pragma omp parallel for schedule(static)
+  for (int t = 0; t < K; ++t) {
+    double* lw = logw + (size_t)t * N;
+    for (int n = 0; n < N; ++n) {
+      double* x = X + ((size_t)t * N + n) * d;
+      if (cf->conditional && n == 0) {
+        for (int i = 0; i < d; ++i) x[i] = x_ref[(size_t)t * d + i];
+      } else {
+        double z[32];
+        draw_particle(cf, d, t, n, z);
+        for (int i = 0; i < d; ++i) {
+          double mu, sd;
+          prop_params(&c, t, i, &mu, &sd);
+          x[i] = mu + sd * z[i];
+        }
+      }
+      if (t == 0)
+        lw[n] = log_h(&c, 0, x) + log_p0(&c, x) - log_q(&c, 0, x);
+      else
+        lw[n] = log_nu(&c, t, x) - log_q(&c, t, x);
+    }
+    double mx = -INFINITY;
+    for (int n = 0; n < N; ++n) mx = lw[n] > mx ? lw[n] : mx;
+    double s = 0.0;
+    for (int n = 0; n < N; ++n) s += exp(lw[n] - mx);
+    double lse = mx + log(s);
+    for (int n = 0; n < N; ++n) lw[n] -= lse;
+    logL[t] = lse - log((double)N);
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Algorithm 6 schedule                                                                   */
+/* ------------------------------------------------------------------------------------ */
+
+int orc_num_levels(int K) {
+  int L = 0;
+  while ((1 << L) < K) ++L;
+  return L;
+}
+
+/* Number of combinations at level l: block pairs (2m, 2m+1) of size 2^l whose right block
+ * starts before K. */
+int orc_merges_at_level(int K, int l) {
+  int64_t size = (int64_t)1 << l;
+  if (size >= K) return 0;
+  return (int)((K - size + 2 * size - 1) / (2 * size));
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Algorithm 1 / 5 / 8                                                                    */
+/* ------------------------------------------------------------------------------------ */
+
+/* Draw one pair from the N x N weights by inverse CDF on the row-major flattened matrix:
+ * the first flat index whose inclusive cumulative sum exceeds u * S. */
+static int64_t inverse_cdf(const double* C, const double* E, int64_t n, double u) {
+  double target = u * C[n - 1];
+  int64_t lo = 0, hi = n; /* first index with C > target */
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (C[mid] > target) hi = mid; else lo = mid + 1;
+  }
+  if (lo >= n) { /* rounding pushed the target past the total: last positive entry */
+    lo = n - 1;
+    while (lo > 0 && !(E[lo] > 0.0)) --lo;
+  }
+  return lo;
+}
+
+/* Multinomial pair draws for slots [n0, n1): one u53 uniform per slot from the counter
+ * (n, gid, DENSE | base<<4, 0), inverse CDF over the row-major flattened matrix.
+ * E: [N*N] nonnegative weights, C: their inclusive cumulative sums. */
+static void dense_draws(int N, const double* E, const double* C, uint32_t seed_lo,
+                        uint32_t seed_hi, uint32_t base, uint32_t gid, int n0, int n1,
+                        int32_t* li, int32_t* ri) {
+  int64_t NN = (int64_t)N * N;
+  for (int n = n0; n < n1; ++n) {
+    uint32_t w[4];
+    draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_DENSE, base, 0u, w);
+    int64_t f = inverse_cdf(C, E, NN, u53(w[0], w[1]));
+    li[n - n0] = (int32_t)(f / N);
+    ri[n - n0] = (int32_t)(f % N);
+  }
+}
+
+/* Rejection draws (Algorithm 8) for slots [n0, n1) given the log-weights logW[i][j] and a
+ * bound logbar >= max logW: per attempt (I, J, u) = (w0 N >> 32, w1 N >> 32, u24(w2)) from
+ * the counter (n, gid, RS | base<<4, attempt); accept when u < exp(logW_IJ - logbar).
+ * logW is evaluated through the callback so that the N x N matrix need not exist. */
+typedef double (*pair_logw_fn)(const void* ctx, int i, int j);
+static int rs_draws(int N, pair_logw_fn fn, const void* ctx, double logbar, uint32_t seed_lo,
+                    uint32_t seed_hi, uint32_t base, uint32_t gid, int n0, int n1,
+                    uint32_t max_attempts, int32_t* li, int32_t* ri, uint64_t* attempts) {
+  int status = ORC_OK;
+  for (int n = n0; n < n1; ++n) {
+    uint32_t att;
+    int I = 0, J = 0, ok = 0;
+    for (att = 0; att < max_attempts; ++att) {
+      uint32_t w[4];
+      draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_RS, base, att, w);
+      I = (int)(((uint64_t)w[0] * (uint64_t)N) >> 32);
+      J = (int)(((uint64_t)w[1] * (uint64_t)N) >> 32);
+      double u = u24(w[2]);
+      if (u < exp(fn(ctx, I, J) - logbar)) { ok = 1; ++att; break; }
+    }
+    if (!ok) status = ORC_ERR_RS_LIMIT;
+    if (attempts) *attempts += att;
+    li[n - n0] = I;
+    ri[n - n0] = J;
+  }
+  return status;
+}
+
+typedef struct {
+  const model_ctx* mc;
+  const double *Zl, *Zr, *wl, *bcol;
+  int d;
+} rs_ctx;
+
+static double rs_model_logw(const void* p, int i, int j) {
+  const rs_ctx* r = (const rs_ctx*)p;
+  return log_f(r->mc, r->Zl + (size_t)i * r->d, r->Zr + (size_t)j * r->d) + r->wl[i] + r->bcol[j];
+}
+
+typedef struct {
+  const double* W;
+  int N;
+} mat_ctx;
+
+static double mat_logw(const void* p, int i, int j) {
+  const mat_ctx* m = (const mat_ctx*)p;
+  return m->W[(size_t)i * m->N + j];
+}
+
+/* Exported for the sampler tests: dense multinomial draws from a given FP64 log-weight
+ * matrix (the same code path Combine uses). */
+int orc_dense_pairs(int N, const double* logW, uint32_t seed_lo, uint32_t seed_hi, uint32_t base,
+                    uint32_t gid, int n0, int n1, int32_t* li, int32_t* ri) {
+  int64_t NN = (int64_t)N * N;
+  double* E = (double*)malloc(sizeof(double) * NN);
+  double* C = (double*)malloc(sizeof(double) * NN);
+  if (!E || !C) { free(E); free(C); return ORC_ERR_OOM; }
+  double M = -INFINITY;
+  for (int64_t f = 0; f < NN; ++f) M = logW[f] > M ? logW[f] : M;
+  double S = 0.0;
+  for (int64_t f = 0; f < NN; ++f) { E[f] = exp(logW[f] - M); S += E[f]; C[f] = S; }
+  dense_draws(N, E, C, seed_lo, seed_hi, base, gid, n0, n1, li, ri);
+  free(E);
+  free(C);
+  return ORC_OK;
+}
+
+/* Exported for the sampler tests: rejection draws from a given FP64 log-weight matrix. */
+int orc_rs_pairs(int N, const double* logW, double logbar, uint32_t seed_lo, uint32_t seed_hi,
+                 uint32_t base, uint32_t gid, int n0, int n1, uint32_t max_attempts, int32_t* li,
+                 int32_t* ri, uint64_t* attempts) {
+  mat_ctx m = {logW, N};
+  return rs_draws(N, mat_logw, &m, logbar, seed_lo, seed_hi, base, gid, n0, n1, max_attempts, li,
+                  ri, attempts);
+}
+
+typedef struct {
+  double* Z;       /* [K][N][d]: value at time t of trajectory n of the block holding t */
+  double* logw;    /* [K][N]: block weights, stored at the block's start time */
+  double* logL;    /* [K]: block log normalising constant, at the block's start time */
+} blocks;
+
+/* Combine left block [a, c-1] with right block [c, b] (Algorithm 1, or Algorithm 5 when
+ * conditional).  pairs: [2][N] output (l_n, r_n).  star: if non-NULL ([K][d]), one extra
+ * draw (I*, J*) from the same W, at slot N, gives the next reference trajectory
+ * [left trajectory I*, right trajectory J*] (Section 3.1), read before the copy. */
+static int combine(const model_ctx* mc, const orc_config* cf, blocks* B, int a, int c, int b,
+                   int gid, int32_t* pairs, double* star, uint64_t* attempts) {
+  const int N = cf->N, d = mc->m->d;
+  const double* wl = B->logw + (size_t)a * N;
+  const double* wr = B->logw + (size_t)c * N;
+  int status = ORC_OK;
+  int n0 = cf->conditional ? 1 : 0;
+  int nslots = N + (star ? 1 : 0);
+  int32_t* li = (int32_t*)malloc(sizeof(int32_t) * nslots);
+  int32_t* ri = (int32_t*)malloc(sizeof(int32_t) * nslots);
+  double inc;
+  if (!li || !ri) { free(li); free(ri); return ORC_ERR_OOM; }
+
+  if (cf->resampler == 0) {
+    int64_t NN = (int64_t)N * N;
+    double* W = (double*)malloc(sizeof(double) * NN);
+    double* C = (double*)malloc(sizeof(double) * NN);
+    if (!W || !C) { free(W); free(C); free(li); free(ri); return ORC_ERR_OOM; }
+    double M = -INFINITY;
+    for (int i = 0; i < N; ++i) {
+      const double* xl = B->Z + ((size_t)(c - 1) * N + i) * d;
+      for (int j = 0; j < N; ++j) {
+        const double* xr = B->Z + ((size_t)c * N + j) * d;
+        double v = log_omega(mc, c, xl, xr) + wl[i] + wr[j];
+        W[(int64_t)i * N + j] = v;
+        if (v > M) M = v;
+      }
+    }
+    if (!(M > -INFINITY) || isnan(M)) {
+      free(W); free(C); free(li); free(ri);
+      return ORC_ERR_DEGENERATE;
+    }
+    double S = 0.0;
+    for (int64_t f = 0; f < NN; ++f) {
+      W[f] = exp(W[f] - M);
+      S += W[f];
+      C[f] = S;
+    }
+    inc = M + log(S);
+    dense_draws(N, W, C, cf->seed_lo, cf->seed_hi, cf->counter_base, (uint32_t)gid, n0, nslots,
+                li + n0, ri + n0);
+    free(W);
+    free(C);
+  } else {
+    /* Algorithm 8 with the finite-set bound log wbar = log f_max + max_i a_i + max_j b'_j,
+     * b'_j = logw_R[j] + log h_c - log nu_c (the N x N weights are never formed). */
+    double amax = -INFINITY, bmax = -INFINITY;
+    double* bcol = (double*)malloc(sizeof(double) * N);
+    if (!bcol) { free(li); free(ri); return ORC_ERR_OOM; }
+    for (int i = 0; i < N; ++i) amax = wl[i] > amax ? wl[i] : amax;
+    for (int j = 0; j < N; ++j) {
+      const double* xr = B->Z + ((size_t)c * N + j) * d;
+      bcol[j] = wr[j] + log_h(mc, c, xr) - log_nu(mc, c, xr);
+      bmax = bcol[j] > bmax ? bcol[j] : bmax;
+    }
+    double logbar = log_f_max(mc) + amax + bmax;
+    rs_ctx rc = {mc, B->Z + (size_t)(c - 1) * N * d, B->Z + (size_t)c * N * d, wl, bcol, d};
+    status = rs_draws(N, rs_model_logw, &rc, logbar, cf->seed_lo, cf->seed_hi, cf->counter_base,
+                      (uint32_t)gid, n0, nslots, cf->rs_max_attempts, li + n0, ri + n0, attempts);
+    free(bcol);
+    /* the increment still needs the full weighted sum (Eq. Lab) */
+    double M = -INFINITY;
+    double* row = (double*)malloc(sizeof(double) * N);
+    if (!row) { free(li); free(ri); return ORC_ERR_OOM; }
+    double S = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double* xl = B->Z + ((size_t)(c - 1) * N + i) * d;
+      for (int j = 0; j < N; ++j) {
+        const double* xr = B->Z + ((size_t)c * N + j) * d;
+        row[j] = log_omega(mc, c, xl, xr) + wl[i] + wr[j];
+      }
+      for (int j = 0; j < N; ++j) {
+        if (row[j] > M) { S *= exp(M - row[j]); M = row[j]; }
+        S += exp(row[j] - M);
+      }
+    }
+    free(row);
+    inc = M + log(S);
+  }
+  if (cf->conditional) {
+    li[0] = 0;
+    ri[0] = 0;
+  }
+  for (int n = 0; n < N; ++n) {
+    pairs[n] = li[n];
+    pairs[N + n] = ri[n];
+  }
+  if (star) {
+    for (int t = a; t <= b; ++t) {
+      int src = t < c ? li[N] : ri[N];
+      for (int k = 0; k < d; ++k) star[(size_t)t * d + k] = B->Z[((size_t)t * N + src) * d + k];
+    }
+  }
+
+  /* the two copy loops of Algorithm 1 */
+  double* tmp = (double*)malloc(sizeof(double) * (size_t)N * d);
+  if (!tmp) { free(li); free(ri); return ORC_ERR_OOM; }
+  for (int t = a; t <= b; ++t) {
+    const int32_t* src = t < c ? li : ri;
+    double* Zt = B->Z + (size_t)t * N * d;
+    for (int n = 0; n < N; ++n)
+      for (int k = 0; k < d; ++k) tmp[(size_t)n * d + k] = Zt[(size_t)src[n] * d + k];
+    memcpy(Zt, tmp, sizeof(double) * (size_t)N * d);
+  }
+  free(tmp);
+  double* lwa = B->logw + (size_t)a * N;
+  for (int n = 0; n < N; ++n) lwa[n] = -log((double)N);
+  B->logL[a] = B->logL[a] + B->logL[c] + inc;
+  free(li);
+  free(ri);
+  return status;
+}
+
+/* Full dSMC smoother (Algorithm 2 followed by Algorithm 6 with Combine / ConditionalCombine).
+ *   y        [K][d]
+ *   x_ref    [K][d] or NULL (required when cf->conditional)
+ *   X_leaf   [K][N][d] or NULL: the Algorithm 2 particles
+ *   pairs    [K-1][2][N] or NULL: (l_n, r_n) of every combination, level-major order
+ *   traj     [K][N][d] or NULL: the N output trajectories
+ *   mean     [K][d]: smoothing means (weighted by the root weights)
+ *   m2       [K][d] or NULL: smoothing second moments
+ *   logL     scalar: log of the normalising-constant estimate
+ *   x_star   [K][d] or NULL: conditional mode, the next reference trajectory
+ *   rs_attempts: total rejection-sampling attempts (may be NULL) */
+int orc_smooth(const orc_model* m, const orc_config* cf, const double* y, const double* x_ref,
+               double* X_leaf, int32_t* pairs, double* traj, double* mean, double* m2,
+               double* logL, double* x_star, uint64_t* rs_attempts) {
+  model_ctx mc;
+  int st = ctx_init(&mc, m, cf->K, y);
+  if (st) return st;
+  const int K = cf->K, N = cf->N, d = m->d;
+  if (K < 1 || N < 1 || (cf->conditional && (!x_ref || N < 2))) return ORC_ERR_INVALID;
+  blocks B;
+  B.Z = (double*)malloc(sizeof(double) * (size_t)K * N * d);
+  B.logw = (double*)malloc(sizeof(double) * (size_t)K * N);
+  B.logL = (double*)malloc(sizeof(double) * (size_t)K);
+  if (!B.Z || !B.logw || !B.logL) { free(B.Z); free(B.logw); free(B.logL); return ORC_ERR_OOM; }
+  st = orc_init(m, cf, y, x_ref, B.Z, B.logw, B.logL);
+  if (st) goto done;
+  if (X_leaf) memcpy(X_leaf, B.Z, sizeof(double) * (size_t)K * N * d);
+
+  int L = orc_num_levels(K);
+  int gid = 0;
+  uint64_t attempts = 0;
+  int status = ORC_OK;
+  int32_t* pbuf = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)N * (K > 1 ? K - 1 : 1));
+  if (!pbuf) { st = ORC_ERR_OOM; goto done; }
+  for (int l = 0; l < L; ++l) {
+    int size = 1 << l;
+    int M = orc_merges_at_level(K, l);
+    int root = (l == L - 1);
+    int lvl_status = ORC_OK;
+    uint64_t lvl_att = 0;
+#pragma omp parallel for schedule(dynamic) reduction(+ : lvl_att) reduction(max : lvl_status)
+    for (int mm = 0; mm < M; ++mm) {
+      int a = 2 * mm * size, c = a + size;
+      int b = (a + 2 * size < K ? a + 2 * size : K) - 1;
+      uint64_t att = 0;
+      int s = combine(&mc, cf, &B, a, c, b, gid + mm, pbuf + (size_t)(gid + mm) * 2 * N,
+                      (root && cf->conditional) ? x_star : NULL, &att);
+      lvl_att += att;
+      if (s > lvl_status) lvl_status = s;
+    }
+    attempts += lvl_att;
+    if (lvl_status == ORC_ERR_DEGENERATE || lvl_status == ORC_ERR_OOM) { st = lvl_status; free(pbuf); goto done; }
+    if (lvl_status) status = lvl_status;
+    gid += M;
+  }
+  if (pairs && K > 1) memcpy(pairs, pbuf, sizeof(int32_t) * 2 * (size_t)N * (K - 1));
+  free(pbuf);
+  if (rs_attempts) *rs_attempts = attempts;
+
+  /* Output: the root block.  For K >= 2 it is uniformly weighted (every Combine returns
+   * 1/N weights); for K == 1 it is the Algorithm 2 leaf with its own weights. */
+  for (int t = 0; t < K; ++t) {
+    for (int k = 0; k < d; ++k) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int n = 0; n < N; ++n) {
+        double w = exp(B.logw[n]); /* root weights live at start time 0 */
+        double x = B.Z[((size_t)t * N + n) * d + k];
+        s1 += w * x;
+        s2 += w * x * x;
+      }
+      mean[(size_t)t * d + k] = s1;
+      if (m2) m2[(size_t)t * d + k] = s2;
+    }
+  }
+  if (traj) memcpy(traj, B.Z, sizeof(double) * (size_t)K * N * d);
+  *logL = B.logL[0];
+
+  if (cf->conditional && x_star && K == 1) {
+    /* no combination: draw the next reference from the weighted leaf at t = 0 */
+    double* E = (double*)malloc(sizeof(double) * N);
+    double* C = (double*)malloc(sizeof(double) * N);
+    if (!E || !C) { free(E); free(C); st = ORC_ERR_OOM; goto done; }
+    double S = 0.0;
+    for (int n = 0; n < N; ++n) { E[n] = exp(B.logw[n]); S += E[n]; C[n] = S; }
+    uint32_t w[4];
+    draw(cf->seed_lo, cf->seed_hi, (uint32_t)N, 0u, ORC_PURPOSE_DENSE, cf->counter_base, 0u, w);
+    int64_t f = inverse_cdf(C, E, N, u53(w[0], w[1]));
+    for (int k = 0; k < d; ++k) x_star[k] = B.Z[(size_t)f * d + k];
+    free(E);
+    free(C);
+  }
+  st = status;
+done:
+  free(B.Z);
+  free(B.logw);
+  free(B.logL);
+  return st;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* log omega matrix for given particles (parity of the merge log-weights)                */
+/* ------------------------------------------------------------------------------------ */
+
+/* out[i][j] = log omega_c(xl_i, xr_j) + wl[i] + wr[j]  (FP64; Eq. normalized-weights). */
+int orc_logw_matrix(const orc_model* m, int K, const double* y, int c, int N, const double* xl,
+                    const double* xr, const double* wl, const double* wr, double* out) {
+  model_ctx mc;
+  int st = ctx_init(&mc, m, K, y);
+  if (st) return st;
+  const int d = m->d;
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j)
+      out[(size_t)i * N + j] =
+          log_omega(&mc, c, xl + (size_t)i * d, xr + (size_t)j * d) + wl[i] + wr[j];
+  return ORC_OK;
+}
+
+/* log f_max, log h, log nu for tests of the model densities. */
+int orc_model_logdens(const orc_model* m, int K, const double* y, int t, const double* xprev,
+                      const double* x, double out[5]) {
+  model_ctx mc;
+  int st = ctx_init(&mc, m, K, y);
+  if (st) return st;
+  out[0] = log_f(&mc, xprev, x);
+  out[1] = log_h(&mc, t, x);
+  out[2] = log_nu(&mc, t, x);
+  out[3] = log_q(&mc, t, x);
+  out[4] = log_f_max(&mc);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Pair samplers in the device's precision (the bit-exact index contract)                */
+/* ------------------------------------------------------------------------------------ */
+
+/* Three-stage inverse CDF: row, then 32..512-wide column tile, then column.
+ * Inputs are the device's own FP32 weights, all relative to one shift per row:
+ *   r[i]        row weight (relative to the largest row), in (0, 1]
+ *   t[i][k]     tile weight of row i, tile k (columns kB .. kB+B-1)
+ *   e[i][j]     element weight (same per-row shift as t)
+ * Decisions:
+ *   row:    Rq_i = trunc(r_i * 2^40) (uint64, exact prefix sums); target
+ *           T = floor(U * S / 2^64), U = (w0 << 32) | w1; row = #{i : cumRq_i <= T}
+ *   tile:   FP32 sequential sum over k; tau = u24(w2) * total (FP32); first k whose
+ *           running sum exceeds tau, else the last k with positive weight
+ *   column: the same on e within the tile, with u24(w3)
+ * Slots n in [n0, n1) use the counter (n, gid, DENSE | base<<4, 0).  A zero-weight entry is
+ * never chosen. */
+static uint64_t mulhi64(uint64_t a, uint64_t b) {
+  unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+  return (uint64_t)(p >> 64);
+}
+
+static uint64_t row_quant(float r) {
+  if (!(r > 0.0f)) return 0;
+  if (r > 1.0f) r = 1.0f;
+  return (uint64_t)(r * 0x1p40f);
+}
+
+static int seq_pick(const float* v, int n, float u) {
+  float tot = 0.0f;
+  for (int k = 0; k < n; ++k) tot = tot + v[k];
+  float tau = u * tot;
+  float cum = 0.0f;
+  for (int k = 0; k < n; ++k) {
+    cum = cum + v[k];
+    if (cum > tau) return k;
+  }
+  for (int k = n - 1; k > 0; --k)
+    if (v[k] > 0.0f) return k;
+  return 0;
+}
+
+int orc_kp_dense_pairs(int N, int B, const float* r, const float* t, const float* e,
+                       uint32_t seed_lo, uint32_t seed_hi, uint32_t base, uint32_t gid, int n0,
+                       int n1, int32_t* li, int32_t* ri) {
+  int nT = (N + B - 1) / B;
+  uint64_t* cum = (uint64_t*)malloc(sizeof(uint64_t) * N);
+  if (!cum) return ORC_ERR_OOM;
+  uint64_t S = 0;
+  for (int i = 0; i < N; ++i) {
+    S += row_quant(r[i]);
+    cum[i] = S;
+  }
+  if (S == 0) { free(cum); return ORC_ERR_DEGENERATE; }
+  for (int n = n0; n < n1; ++n) {
+    uint32_t w[4];
+    draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_DENSE, base, 0u, w);
+    uint64_t U = ((uint64_t)w[0] << 32) | (uint64_t)w[1];
+    uint64_t T = mulhi64(U, S);
+    int lo = 0, hi = N;
+    while (lo < hi) {
+      int mid = (lo + hi) / 2;
+      if (cum[mid] > T) hi = mid; else lo = mid + 1;
+    }
+    int i = lo;
+    float u2 = (float)(((double)(w[2] >> 8) + 0.5) * 0x1p-24);
+    float u3 = (float)(((double)(w[3] >> 8) + 0.5) * 0x1p-24);
+    int k = seq_pick(t + (size_t)i * nT, nT, u2);
+    int j0 = k * B;
+    int width = (j0 + B <= N) ? B : N - j0;
+    int j = j0 + seq_pick(e + (size_t)i * N + j0, width, u3);
+    li[n - n0] = i;
+    ri[n - n0] = j;
+  }
+  free(cum);
+  return ORC_OK;
+}
+
+/* Algorithm 8 in the device's precision: ratio[I][J] = exp(logW_IJ - log wbar) as the
+ * device computed it (FP32); per attempt (I, J, u) = (w0 N >> 32, w1 N >> 32, u24(w2)),
+ * counter (n, gid, RS | base<<4, attempt); accept when u < ratio. */
+int orc_kp_rs_pairs(int N, const float* ratio, uint32_t seed_lo, uint32_t seed_hi, uint32_t base,
+                    uint32_t gid, int n0, int n1, uint32_t max_attempts, int32_t* li, int32_t* ri,
+                    uint32_t* attempts) {
+  int status = ORC_OK;
+  for (int n = n0; n < n1; ++n) {
+    uint32_t a;
+    int I = 0, J = 0, ok = 0;
+    for (a = 0; a < max_attempts; ++a) {
+      uint32_t w[4];
+      draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_RS, base, a, w);
+      I = (int)(((uint64_t)w[0] * (uint64_t)N) >> 32);
+      J = (int)(((uint64_t)w[1] * (uint64_t)N) >> 32);
+      float u = (float)(((double)(w[2] >> 8) + 0.5) * 0x1p-24);
+      if (u < ratio[(size_t)I * N + J]) { ok = 1; ++a; break; }
+    }
+    if (!ok) status = ORC_ERR_RS_LIMIT;
+    li[n - n0] = I;
+    ri[n - n0] = J;
+    attempts[n - n0] = a;
+  }
+  return status;
+}
