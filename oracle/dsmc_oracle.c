@@ -29,9 +29,9 @@
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel random numbers:
  * as easy as 1, 2, 3", SC'11), key = 64-bit seed, counter = (slot, id, purpose | base<<4,
  * j).  The conversions to uniforms are:
- *   u24(w)     = ((w >> 8) + 0.5) * 2^-24        (exactly representable in FP32 and FP64)
+ *   u23(w)     = ((w >> 9) + 0.5) * 2^-23        (exact in FP32 and FP64, inside (0, 1))
  *   u53(w0,w1) = (((w0 << 21) | (w1 >> 11)) + 0.5) * 2^-53
- * Normals are Box-Muller pairs from (u24(w0), u24(w1)) and (u24(w2), u24(w3)).
+ * Normals are Box-Muller pairs from (u23(w0), u23(w1)) and (u23(w2), u23(w3)).
  *
  * Build: gcc -O2 -std=c11 -fPIC -shared -ffp-contract=off -fopenmp (no -ffast-math).
  */
@@ -98,7 +98,7 @@ static void draw(uint32_t seed_lo, uint32_t seed_hi, uint32_t slot, uint32_t id,
   orc_philox4x32_10(ctr, key, w);
 }
 
-static double u24(uint32_t w) { return ((double)(w >> 8) + 0.5) * 0x1p-24; }
+static double u23(uint32_t w) { return ((double)(w >> 9) + 0.5) * 0x1p-23; }
 static double u53(uint32_t w0, uint32_t w1) {
   uint64_t m = ((uint64_t)w0 << 21) | (uint64_t)(w1 >> 11);
   return ((double)m + 0.5) * 0x1p-53;
@@ -279,7 +279,7 @@ static void draw_particle(const orc_config* cf, int d, int t, int n, double* z) 
     draw(cf->seed_lo, cf->seed_hi, (uint32_t)n, (uint32_t)t, ORC_PURPOSE_INIT, cf->counter_base,
          (uint32_t)j, w);
     for (int p = 0; p < 2; ++p) {
-      double u1 = u24(w[2 * p]), u2 = u24(w[2 * p + 1]);
+      double u1 = u23(w[2 * p]), u2 = u23(w[2 * p + 1]);
       double r = sqrt(-2.0 * log(u1));
       double th = 6.283185307179586476925286766559 * u2;
       int k0 = 4 * j + 2 * p;
@@ -389,7 +389,7 @@ static void dense_draws(int N, const double* E, const double* C, uint32_t seed_l
 }
 
 /* Rejection draws (Algorithm 8) for slots [n0, n1) given the log-weights logW[i][j] and a
- * bound logbar >= max logW: per attempt (I, J, u) = (w0 N >> 32, w1 N >> 32, u24(w2)) from
+ * bound logbar >= max logW: per attempt (I, J, u) = (w0 N >> 32, w1 N >> 32, u23(w2)) from
  * the counter (n, gid, RS | base<<4, attempt); accept when u < exp(logW_IJ - logbar).
  * logW is evaluated through the callback so that the N x N matrix need not exist. */
 typedef double (*pair_logw_fn)(const void* ctx, int i, int j);
@@ -405,7 +405,7 @@ static int rs_draws(int N, pair_logw_fn fn, const void* ctx, double logbar, uint
       draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_RS, base, att, w);
       I = (int)(((uint64_t)w[0] * (uint64_t)N) >> 32);
       J = (int)(((uint64_t)w[1] * (uint64_t)N) >> 32);
-      double u = u24(w[2]);
+      double u = u23(w[2]);
       if (u < exp(fn(ctx, I, J) - logbar)) { ok = 1; ++att; break; }
     }
     if (!ok) status = ORC_ERR_RS_LIMIT;
@@ -731,9 +731,9 @@ int orc_model_logdens(const orc_model* m, int K, const double* y, int t, const d
  * Decisions:
  *   row:    Rq_i = trunc(r_i * 2^40) (uint64, exact prefix sums); target
  *           T = floor(U * S / 2^64), U = (w0 << 32) | w1; row = #{i : cumRq_i <= T}
- *   tile:   FP32 sequential sum over k; tau = u24(w2) * total (FP32); first k whose
+ *   tile:   FP32 sequential sum over k; tau = u23(w2) * total (FP32); first k whose
  *           running sum exceeds tau, else the last k with positive weight
- *   column: the same on e within the tile, with u24(w3)
+ *   column: the same on e within the tile, with u23(w3)
  * Slots n in [n0, n1) use the counter (n, gid, DENSE | base<<4, 0).  A zero-weight entry is
  * never chosen. */
 static uint64_t mulhi64(uint64_t a, uint64_t b) {
@@ -784,8 +784,8 @@ int orc_kp_dense_pairs(int N, int B, const float* r, const float* t, const float
       if (cum[mid] > T) hi = mid; else lo = mid + 1;
     }
     int i = lo;
-    float u2 = (float)(((double)(w[2] >> 8) + 0.5) * 0x1p-24);
-    float u3 = (float)(((double)(w[3] >> 8) + 0.5) * 0x1p-24);
+    float u2 = (float)u23(w[2]);
+    float u3 = (float)u23(w[3]);
     int k = seq_pick(t + (size_t)i * nT, nT, u2);
     int j0 = k * B;
     int width = (j0 + B <= N) ? B : N - j0;
@@ -798,8 +798,8 @@ int orc_kp_dense_pairs(int N, int B, const float* r, const float* t, const float
 }
 
 /* Algorithm 8 in the device's precision: ratio[I][J] = exp(logW_IJ - log wbar) as the
- * device computed it (FP32); per attempt (I, J, u) = (w0 N >> 32, w1 N >> 32, u24(w2)),
- * counter (n, gid, RS | base<<4, attempt); accept when u < ratio. */
+ * device computed it (FP32); per attempt (I, J, u) = (w0 N >> 32, w1 N >> 32, u23(w2)),
+ * counter (n, gid, RS | base<<4, attempt); accept when u < ratio, u = u23(w2). */
 int orc_kp_rs_pairs(int N, const float* ratio, uint32_t seed_lo, uint32_t seed_hi, uint32_t base,
                     uint32_t gid, int n0, int n1, uint32_t max_attempts, int32_t* li, int32_t* ri,
                     uint32_t* attempts) {
@@ -812,7 +812,7 @@ int orc_kp_rs_pairs(int N, const float* ratio, uint32_t seed_lo, uint32_t seed_h
       draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_RS, base, a, w);
       I = (int)(((uint64_t)w[0] * (uint64_t)N) >> 32);
       J = (int)(((uint64_t)w[1] * (uint64_t)N) >> 32);
-      float u = (float)(((double)(w[2] >> 8) + 0.5) * 0x1p-24);
+      float u = (float)u23(w[2]);
       if (u < ratio[(size_t)I * N + J]) { ok = 1; ++a; break; }
     }
     if (!ok) status = ORC_ERR_RS_LIMIT;
