@@ -1,0 +1,206 @@
+/*
+ * dsmc.h -- C ABI of the GB300 (sm_103a) implementation of dSMC, the de-Sequentialized
+ * Monte Carlo particle smoother of Corenflos, Chopin and Sarkka (arXiv 2202.02264).
+ *
+ * The data-parallel hot path is the divide-and-conquer combination of Section 2 applied
+ * over ceil(log2 K) tree levels:
+ *   - Algorithm 2: independent proposals q_t and leaf weights for every (t, n);
+ *   - Appendix A, Algorithm 6: left-aligned blocks of 2^l steps, block pairs (2m, 2m+1)
+ *     combined at level l, an unpaired last block passed through unchanged;
+ *   - Algorithm 1 (Combine): the N x N product-form log-weights of Eq. (normalized-weights)
+ *     with the stitching weight omega_c = p_c h_c / nu_c of Proposition 2, N pair draws,
+ *     and the concatenated trajectories;
+ *   - Algorithm 8: rejection-sampling lazy resampling, which never forms the N x N matrix;
+ *   - Algorithm 5 (ConditionalCombine) and the star trajectory of Section 3.1, for the
+ *     parallel-in-time particle Gibbs sampler of Section 3.2.
+ *
+ * Conventions shared by every entry point:
+ *   - Time steps are t = 0..K-1 (the paper's t = 0..T with K = T + 1).  N particles, state
+ *     dimension dx in 1..32; observations have dimension dx (identity observation map).
+ *   - "device" pointers are CUDA global-memory pointers on the current device; "host"
+ *     pointers are ordinary CPU memory.  The library allocates no device memory: the
+ *     caller passes every buffer, sized by dsmc_state_sizes() and dsmc_workspace_size().
+ *     The library never frees caller memory.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL is the
+ *     legacy default stream).  Argument errors are returned synchronously and nothing is
+ *     launched.  Errors found on the device (non-finite or degenerate weights, the
+ *     rejection-sampling attempt cap) are recorded in a status word inside the workspace
+ *     and read with dsmc_stream_status(), which synchronises the stream.
+ *   - Random numbers are Philox4x32-10 keyed by `seed`, with the counter
+ *     (slot, time-or-combination id, purpose | counter_base << 4, j); results are
+ *     deterministic for a given (seed, counter_base) and do not depend on the launch
+ *     configuration.
+ *   - The library never aborts or traps.
+ */
+#ifndef DSMC_H
+#define DSMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DSMC_OK = 0,
+  DSMC_ERR_INVALID_ARG = 1,  /* a pointer, size or parameter is invalid; nothing launched */
+  DSMC_ERR_UNSUPPORTED = 2,  /* a valid request outside the supported range (e.g. N, dx) */
+  DSMC_ERR_WORKSPACE = 3,    /* ws_bytes smaller than dsmc_workspace_size() */
+  DSMC_ERR_CUDA = 5,         /* a CUDA launch or copy failed; see dsmc_last_error() */
+  DSMC_ERR_NONFINITE = 6,    /* device: a log-weight was NaN */
+  DSMC_ERR_DEGENERATE = 7,   /* device: every weight of a combination was zero */
+  DSMC_ERR_RS_LIMIT = 8,     /* device: a rejection-sampling slot hit rs_max_attempts */
+  DSMC_ERR_TIMEOUT = 9       /* device: a bounded wait gave up */
+} dsmc_status_t;
+
+enum { DSMC_MODEL_LGSSM = 0, DSMC_MODEL_SV = 1 };
+enum { DSMC_PROP_OBS = 0, DSMC_PROP_GAUSS = 1 };
+enum { DSMC_NU_EQ_Q = 0, DSMC_NU_PROP_H = 1 };
+enum { DSMC_FP32 = 0, DSMC_TF32 = 1, DSMC_BF16 = 2 };
+enum { DSMC_MULTINOMIAL = 0, DSMC_RS = 1 };
+
+/* The state-space model of Eq. (ssm) (Section 1).  All arrays are HOST, row-major, FP64,
+ * read during the call only.
+ *   LGSSM: x_0 ~ N(m0, P0), x_t = A x_{t-1} + N(0, Q), y_t = x_t + N(0, R).
+ *   SV (dx = 1): x_0 ~ N(mu, sigma^2/(1-phi^2)), x_t = mu + phi (x_{t-1} - mu) + sigma e,
+ *                y_t = exp(x_t / 2) v, e, v ~ N(0, 1); A, Q, R, m0, P0 are ignored. */
+typedef struct {
+  int kind;              /* DSMC_MODEL_LGSSM or DSMC_MODEL_SV */
+  int dx;                /* 1..32 */
+  const double* A;       /* [dx][dx] */
+  const double* Q;       /* [dx][dx], symmetric positive definite */
+  const double* R;       /* [dx][dx], symmetric positive definite */
+  const double* m0;      /* [dx] */
+  const double* P0;      /* [dx][dx], symmetric positive definite */
+  double mu, phi, sigma; /* SV parameters, |phi| < 1, sigma > 0 */
+} dsmc_model_t;
+
+/* The proposals q_t of Algorithm 2 and the auxiliary laws nu_t of Definition 1.
+ *   DSMC_PROP_OBS:   q_t = N(y_t, scale^2 I).
+ *   DSMC_PROP_GAUSS: q_t = N(mean[t], diag(std[t]^2)); mean, std are DEVICE [K][dx] FP32.
+ *   nu = DSMC_NU_EQ_Q:   nu_t = q_t for t >= 1 (the paper's experiments).
+ *   nu = DSMC_NU_PROP_H: nu_t proportional to h_t(y_t | .), so that the combination weight
+ *                        is log p_t(x_t | x_{t-1}) up to a constant. */
+typedef struct {
+  int kind;
+  double scale;
+  const float* mean;
+  const float* std;
+  int nu;
+} dsmc_proposal_t;
+
+typedef struct {
+  int K;                      /* time steps, >= 1 */
+  int N;                      /* particles, >= 1 (>= 2 when conditional); <= 16384 dense */
+  int compute;                /* cross-term precision: DSMC_FP32 (CUDA cores, default),
+                                 DSMC_TF32 or DSMC_BF16 (tensor cores) */
+  int resampler;              /* DSMC_MULTINOMIAL (dense, Algorithm 1) or DSMC_RS (Alg. 8) */
+  uint64_t seed;              /* Philox key */
+  uint32_t counter_base;      /* < 2^28; e.g. the particle-Gibbs sweep index */
+  uint32_t rs_max_attempts;   /* cap per slot for DSMC_RS (0 means 2^20) */
+  int max_merges_per_launch;  /* 0 = default; bounds the workspace */
+} dsmc_config_t;
+
+/* Caller-owned DEVICE state of one smoothing (sizes from dsmc_state_sizes()).
+ *   X      [K][N][dx] FP32  Algorithm 2 particles; merges never modify them
+ *   logw   [K][N]     FP32  normalised leaf log-weights
+ *   logL   [K]        FP64  log normalising constant of the block starting at t
+ *   pairs  [K-1][2][N] int32 (l_n, r_n) of every combination, level-major order: all
+ *                      combinations of level 0 by ascending start time, then level 1, ...
+ */
+typedef struct {
+  float* X;
+  float* logw;
+  double* logL;
+  int32_t* pairs;
+} dsmc_state_t;
+
+/* Human-readable text of a status code (static storage). */
+const char* dsmc_status_string(dsmc_status_t s);
+
+/* Text of the last error raised in this thread (thread-local, valid until the next call). */
+const char* dsmc_last_error(void);
+
+/* Bytes of the four state arrays, in the order X, logw, logL, pairs.  Host call. */
+dsmc_status_t dsmc_state_sizes(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                               size_t bytes_out[4]);
+
+/* Bytes of device workspace every call below needs for this (cfg, model).  Host call. */
+dsmc_status_t dsmc_workspace_size(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                  size_t* bytes);
+
+/* Algorithm 2 (and its conditional form, Section 3.2: slot 0 of every time step is
+ * x_ref[t], weighted like the others).  y: DEVICE [K][dx] FP32.  x_ref: DEVICE [K][dx]
+ * FP32 or NULL.  Writes state->X, state->logw, state->logL.  Resets the status word. */
+dsmc_status_t dsmc_init_particles(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                  const dsmc_proposal_t* prop, const float* y,
+                                  const float* x_ref, dsmc_state_t* state, void* ws,
+                                  size_t ws_bytes, void* stream);
+
+/* One level l of Algorithm 6: every combination of adjacent 2^l-blocks (Algorithm 1, or
+ * Algorithm 5 when `conditional`).  Must be called for l = 0, 1, ..., ceil(log2 K) - 1 in
+ * order after dsmc_init_particles with the same state and workspace.  Writes the pairs of
+ * the level's combinations and updates state->logL. */
+dsmc_status_t dsmc_merge_level(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                               const dsmc_proposal_t* prop, const float* y, int level,
+                               int conditional, dsmc_state_t* state, void* ws,
+                               size_t ws_bytes, void* stream);
+
+/* Resolves the output trajectories from the stored pairs (composition of the resampling
+ * arrays of the Remark in Section 3.1) and gathers them.  traj_out: DEVICE [K][N][dx] FP32
+ * or NULL; mean_out: DEVICE [K][dx] FP64 (smoothing means); m2_out: DEVICE [K][dx] FP64 or
+ * NULL (second moments); x_star_out: DEVICE [K][dx] FP32 or NULL (conditional mode: the
+ * trajectory chosen by the extra root draw). */
+dsmc_status_t dsmc_resolve(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                           const dsmc_state_t* state, float* traj_out, double* mean_out,
+                           double* m2_out, float* x_star_out, void* ws, size_t ws_bytes,
+                           void* stream);
+
+/* The whole smoother: init, every level, resolve.  logL_out: DEVICE FP64 scalar, the log
+ * normalising-constant estimate of Eq. (rec-loglik) (NaN with DSMC_RS, which never forms
+ * the N x N sums). */
+dsmc_status_t dsmc_smooth(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                          const dsmc_proposal_t* prop, const float* y, dsmc_state_t* state,
+                          float* traj_out, double* mean_out, double* m2_out, double* logL_out,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* One conditional dSMC sweep (Section 3.2): slot 0 carries x_ref_in through every
+ * combination; x_ref_out (DEVICE [K][dx] FP32, may alias x_ref_in) receives the next
+ * reference trajectory, drawn from the root's weights (Section 3.1).  N >= 2. */
+dsmc_status_t dsmc_conditional_smooth(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                      const dsmc_proposal_t* prop, const float* y,
+                                      const float* x_ref_in, float* x_ref_out,
+                                      dsmc_state_t* state, float* traj_out, double* mean_out,
+                                      double* logL_out, void* ws, size_t ws_bytes,
+                                      void* stream);
+
+/* Synchronises `stream` and returns in *device_status the first error any kernel recorded
+ * in this workspace since the last dsmc_init_particles (DSMC_OK if none). */
+dsmc_status_t dsmc_stream_status(void* ws, void* stream, dsmc_status_t* device_status);
+
+/* ---- Inspection entry points used by the parity tests (same arithmetic as the path). */
+
+/* Philox4x32-10 of n counters: ctr DEVICE [n][4] uint32, out DEVICE [n][4] uint32. */
+dsmc_status_t dsmc_debug_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
+                                void* stream);
+
+/* After dsmc_merge_level(level), the device's own weights of combination `m` of that
+ * level (it must belong to the last launch chunk of the level):
+ *   logW   DEVICE [N][N] FP32 or NULL: log-weights log omega + logw_L + logw_R as the
+ *          device evaluates them (per-row shift + ln2 * the base-2 exponent);
+ *   r      DEVICE [N] FP32 or NULL: row weights of the row stage;
+ *   tiles  DEVICE [N][n_tiles] FP32 or NULL: tile weights of the tile stage;
+ *   e      DEVICE [N][N] FP32 or NULL: element weights of the column stage;
+ *   ratio  DEVICE [N][N] FP32 or NULL: rejection acceptance ratios omega / omega-bar;
+ *   info   HOST int[4] or NULL: {tile width B, n_tiles, combination id, left block leaf}. */
+dsmc_status_t dsmc_debug_merge_weights(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                       int level, int m, float* logW, float* r, float* tiles,
+                                       float* e, float* ratio, int info[4], void* ws,
+                                       size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSMC_H */

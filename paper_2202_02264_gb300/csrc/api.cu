@@ -1,0 +1,590 @@
+// api.cu -- the C ABI of include/dsmc.h: argument checks, the FP64 model pre-computation,
+// the workspace layout, and the level loop of Algorithm 6 (Appendix A).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "kernels.cuh"
+
+namespace dsmc {
+int rowsum_rows_per_thread(int D);
+cudaError_t launch_k1_star(const float* logw, int N, uint64_t seed, uint32_t base, int32_t* star,
+                           cudaStream_t s);
+}  // namespace dsmc
+
+using namespace dsmc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+dsmc_status_t fail(dsmc_status_t st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+dsmc_status_t cuda_fail(cudaError_t e, const char* what) {
+  return fail(DSMC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr int kMaxDim = 32;
+constexpr int kMaxDenseN = 16384;
+constexpr int kDefaultMergeCap = 1024;
+constexpr int kRowsumTargetCtas = 152 * 8;  // 152 SMs, several CTAs each
+
+int pad_dim(int d) {
+  int D = 1;
+  while (D < d) D <<= 1;
+  return D;
+}
+
+int merges_at_level(int K, int l) {
+  const long size = 1L << l;
+  if (size >= K) return 0;
+  return (int)((K - size + 2 * size - 1) / (2 * size));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Plan {
+  int K, N, d, D, L;
+  int B, nT, nTp;
+  int Mc;
+  int R, rows_per_cta;
+  bool dense;
+  int level_off[33];
+  size_t o_status, o_U, o_alpha, o_V, o_beta, o_shift, o_logbar, o_inc, o_T, o_rw,
+      o_delta, o_first, o_last, o_star, total;
+};
+
+void chunking(const Plan& p, int mc, int& CH, int& CW) {
+  const int RT = (p.N + p.rows_per_cta - 1) / p.rows_per_cta;
+  int want = (kRowsumTargetCtas + mc * RT - 1) / (mc * RT);
+  want = std::max(1, std::min(want, p.nT));
+  const int tpc = (p.nT + want - 1) / want;
+  CW = tpc * p.B;
+  CH = (p.nT + tpc - 1) / tpc;
+}
+
+void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p) {
+  p.K = cfg->K;
+  p.N = cfg->N;
+  p.d = model->dx;
+  p.D = pad_dim(model->dx);
+  p.L = 0;
+  while ((1 << p.L) < p.K) ++p.L;
+  p.dense = cfg->resampler != DSMC_RS;
+  const int nT0 = std::min((p.N + 31) / 32, 64);
+  const int per = (p.N + nT0 - 1) / nT0;
+  p.B = 32 * ((per + 31) / 32);
+  p.nT = (p.N + p.B - 1) / p.B;
+  p.nTp = (p.nT + 3) / 4 * 4;
+  const int M0 = std::max(1, merges_at_level(p.K, 0));
+  const int cap = cfg->max_merges_per_launch > 0 ? cfg->max_merges_per_launch : kDefaultMergeCap;
+  p.Mc = std::max(1, std::min(M0, cap));
+  p.R = rowsum_rows_per_thread(p.D);
+  const int NT = std::min(128, std::max(32, ((p.N + p.R - 1) / p.R + 31) / 32 * 32));
+  p.rows_per_cta = p.R * NT;
+  int off = 0;
+  for (int l = 0; l < p.L; ++l) {
+    p.level_off[l] = off;
+    off += merges_at_level(p.K, l);
+  }
+  p.level_off[p.L] = off;
+  const size_t MN = (size_t)p.Mc * p.N;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  p.o_status = take(sizeof(int));
+  p.o_U = take(MN * p.D * sizeof(float));
+  p.o_alpha = take(MN * sizeof(float));
+  p.o_V = take(MN * p.D * sizeof(float));
+  p.o_beta = take(MN * sizeof(float));
+  p.o_shift = take(MN * sizeof(double));
+  p.o_logbar = take((size_t)p.Mc * sizeof(double));
+  p.o_inc = take((size_t)p.Mc * sizeof(double));
+  p.o_T = take(p.dense ? MN * p.nTp * sizeof(float) : 0);
+  p.o_rw = take(MN * sizeof(float));
+  p.o_delta = take(MN * sizeof(float));
+  p.o_first = take(2 * (size_t)p.K * p.N * sizeof(int32_t));
+  p.o_last = take(2 * (size_t)p.K * p.N * sizeof(int32_t));
+  p.o_star = take(2 * sizeof(int32_t));
+  p.total = o;
+}
+
+WsPtrs ws_ptrs(const Plan& p, void* ws) {
+  char* b = static_cast<char*>(ws);
+  WsPtrs w;
+  w.status = reinterpret_cast<int*>(b + p.o_status);
+  w.U = reinterpret_cast<float*>(b + p.o_U);
+  w.alpha = reinterpret_cast<float*>(b + p.o_alpha);
+  w.V = reinterpret_cast<float*>(b + p.o_V);
+  w.beta = reinterpret_cast<float*>(b + p.o_beta);
+  w.shift = reinterpret_cast<double*>(b + p.o_shift);
+  w.logbar = reinterpret_cast<double*>(b + p.o_logbar);
+  w.inc = reinterpret_cast<double*>(b + p.o_inc);
+  w.T = reinterpret_cast<float*>(b + p.o_T);
+  w.rw = reinterpret_cast<float*>(b + p.o_rw);
+  w.delta = reinterpret_cast<float*>(b + p.o_delta);
+  w.first = reinterpret_cast<int32_t*>(b + p.o_first);
+  w.last = reinterpret_cast<int32_t*>(b + p.o_last);
+  w.star = reinterpret_cast<int32_t*>(b + p.o_star);
+  return w;
+}
+
+// ---- FP64 host linear algebra for the parameter pre-computation
+bool cholesky(int d, const double* S, double* L) {
+  std::memset(L, 0, sizeof(double) * d * d);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = S[i * d + j];
+      for (int k = 0; k < j; ++k) s -= L[i * d + k] * L[j * d + k];
+      if (i == j) {
+        if (!(s > 0.0) || !std::isfinite(s)) return false;
+        L[i * d + i] = std::sqrt(s);
+      } else {
+        L[i * d + j] = s / L[j * d + j];
+      }
+    }
+  return true;
+}
+
+// inverse and log-determinant of an SPD matrix through its Cholesky factor
+bool spd_inverse(int d, const double* S, double* Si, double* logdet) {
+  double L[kMaxDim * kMaxDim], Li[kMaxDim * kMaxDim];
+  if (!cholesky(d, S, L)) return false;
+  std::memset(Li, 0, sizeof(Li));
+  for (int i = 0; i < d; ++i) {
+    Li[i * d + i] = 1.0 / L[i * d + i];
+    for (int j = 0; j < i; ++j) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s -= L[i * d + k] * Li[k * d + j];
+      Li[i * d + j] = s / L[i * d + i];
+    }
+  }
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      double s = 0.0;
+      for (int k = std::max(i, j); k < d; ++k) s += Li[k * d + i] * Li[k * d + j];
+      Si[i * d + j] = s;
+    }
+  double ld = 0.0;
+  for (int i = 0; i < d; ++i) ld += 2.0 * std::log(L[i * d + i]);
+  *logdet = ld;
+  return true;
+}
+
+constexpr double kLog2Pi = 1.8378770664093454836;
+
+struct alignas(16) ParamBuf {
+  unsigned char bytes[sizeof(ModelParams<kMaxDim>)];
+};
+
+template <int D>
+dsmc_status_t fill_params(const dsmc_model_t* m, const dsmc_proposal_t* pr, ParamBuf& buf) {
+  ModelParams<D>* mp = reinterpret_cast<ModelParams<D>*>(buf.bytes);
+  std::memset(mp, 0, sizeof(ModelParams<D>));
+  const int d = m->dx;
+  mp->kind = m->kind;
+  mp->d = d;
+  mp->prop_kind = pr->kind;
+  mp->nu = pr->nu;
+  mp->prop_scale = (float)pr->scale;
+  mp->log_prop_scale = (float)std::log(pr->scale > 0 ? pr->scale : 1.0);
+  mp->prop_mean = pr->mean;
+  mp->prop_std = pr->std;
+  if (m->kind == DSMC_MODEL_SV) {
+    const double s2 = m->sigma * m->sigma;
+    const double v0 = s2 / (1.0 - m->phi * m->phi);
+    mp->A[0] = (float)m->phi;
+    mp->c[0] = (float)(m->mu * (1.0 - m->phi));
+    mp->Qi[0] = (float)(1.0 / s2);
+    mp->P0i[0] = (float)(1.0 / v0);
+    mp->m0[0] = (float)m->mu;
+    mp->log_f_max = (float)(-0.5 * (kLog2Pi + std::log(s2)));
+    mp->log_h_norm = (float)(-0.5 * kLog2Pi);
+    mp->log_p0_norm = (float)(-0.5 * (kLog2Pi + std::log(v0)));
+    return DSMC_OK;
+  }
+  double Qi[kMaxDim * kMaxDim], Ri[kMaxDim * kMaxDim], P0i[kMaxDim * kMaxDim];
+  double ldQ, ldR, ldP;
+  if (!spd_inverse(d, m->Q, Qi, &ldQ)) return fail(DSMC_ERR_INVALID_ARG, "Q is not positive definite");
+  if (!spd_inverse(d, m->R, Ri, &ldR)) return fail(DSMC_ERR_INVALID_ARG, "R is not positive definite");
+  if (!spd_inverse(d, m->P0, P0i, &ldP)) return fail(DSMC_ERR_INVALID_ARG, "P0 is not positive definite");
+  for (int i = 0; i < d; ++i) {
+    mp->m0[i] = (float)m->m0[i];
+    for (int j = 0; j < d; ++j) {
+      mp->A[i * D + j] = (float)m->A[i * d + j];
+      mp->Qi[i * D + j] = (float)Qi[i * d + j];
+      mp->Ri[i * D + j] = (float)Ri[i * d + j];
+      mp->P0i[i * D + j] = (float)P0i[i * d + j];
+    }
+  }
+  mp->log_f_max = (float)(-0.5 * (d * kLog2Pi + ldQ));
+  mp->log_h_norm = (float)(-0.5 * (d * kLog2Pi + ldR));
+  mp->log_p0_norm = (float)(-0.5 * (d * kLog2Pi + ldP));
+  return DSMC_OK;
+}
+
+dsmc_status_t make_params(int D, const dsmc_model_t* m, const dsmc_proposal_t* pr, ParamBuf& buf) {
+  switch (D) {
+    case 1: return fill_params<1>(m, pr, buf);
+    case 2: return fill_params<2>(m, pr, buf);
+    case 4: return fill_params<4>(m, pr, buf);
+    case 8: return fill_params<8>(m, pr, buf);
+    case 16: return fill_params<16>(m, pr, buf);
+    case 32: return fill_params<32>(m, pr, buf);
+  }
+  return fail(DSMC_ERR_UNSUPPORTED, "state dimension");
+}
+
+dsmc_status_t check_config(const dsmc_config_t* cfg, const dsmc_model_t* model) {
+  if (!cfg || !model) return fail(DSMC_ERR_INVALID_ARG, "null config or model");
+  if (cfg->K < 1) return fail(DSMC_ERR_INVALID_ARG, "K must be >= 1");
+  if (cfg->N < 1) return fail(DSMC_ERR_INVALID_ARG, "N must be >= 1");
+  if (cfg->K > (1 << 24) || cfg->N > (1 << 24)) return fail(DSMC_ERR_UNSUPPORTED, "K or N too large");
+  if (cfg->resampler != DSMC_MULTINOMIAL && cfg->resampler != DSMC_RS)
+    return fail(DSMC_ERR_INVALID_ARG, "unknown resampler");
+  if (cfg->resampler == DSMC_MULTINOMIAL && cfg->N > kMaxDenseN)
+    return fail(DSMC_ERR_UNSUPPORTED, "dense resampling supports N <= 16384; use DSMC_RS");
+  if (cfg->compute != DSMC_FP32)
+    return fail(DSMC_ERR_UNSUPPORTED, "only the FP32 cross-term is available in this build");
+  if (cfg->counter_base >= (1u << 28)) return fail(DSMC_ERR_INVALID_ARG, "counter_base must be < 2^28");
+  if (model->dx < 1 || model->dx > kMaxDim) return fail(DSMC_ERR_UNSUPPORTED, "dx must be in 1..32");
+  if (model->kind == DSMC_MODEL_SV) {
+    if (model->dx != 1) return fail(DSMC_ERR_INVALID_ARG, "the SV model has dx = 1");
+    if (!(model->sigma > 0.0) || !(std::fabs(model->phi) < 1.0))
+      return fail(DSMC_ERR_INVALID_ARG, "SV needs sigma > 0 and |phi| < 1");
+  } else if (model->kind == DSMC_MODEL_LGSSM) {
+    if (!model->A || !model->Q || !model->R || !model->m0 || !model->P0)
+      return fail(DSMC_ERR_INVALID_ARG, "LGSSM needs A, Q, R, m0, P0");
+  } else {
+    return fail(DSMC_ERR_INVALID_ARG, "unknown model kind");
+  }
+  return DSMC_OK;
+}
+
+dsmc_status_t check_prop(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                         const dsmc_proposal_t* prop) {
+  (void)cfg;
+  if (!prop) return fail(DSMC_ERR_INVALID_ARG, "null proposal");
+  if (prop->kind == DSMC_PROP_OBS) {
+    if (!(prop->scale > 0.0)) return fail(DSMC_ERR_INVALID_ARG, "proposal scale must be > 0");
+  } else if (prop->kind == DSMC_PROP_GAUSS) {
+    if (!prop->mean || !prop->std) return fail(DSMC_ERR_INVALID_ARG, "proposal mean/std arrays");
+  } else {
+    return fail(DSMC_ERR_INVALID_ARG, "unknown proposal kind");
+  }
+  if (prop->nu != DSMC_NU_EQ_Q && prop->nu != DSMC_NU_PROP_H)
+    return fail(DSMC_ERR_INVALID_ARG, "unknown nu choice");
+  (void)model;
+  return DSMC_OK;
+}
+
+dsmc_status_t check_ws(const Plan& p, void* ws, size_t ws_bytes) {
+  if (!ws) return fail(DSMC_ERR_INVALID_ARG, "null workspace");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(DSMC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  if (ws_bytes < p.total) return fail(DSMC_ERR_WORKSPACE, "workspace too small");
+  return DSMC_OK;
+}
+
+dsmc_status_t check_state(const dsmc_state_t* st, int K) {
+  if (!st || !st->X || !st->logw || !st->logL || (K > 1 && !st->pairs))
+    return fail(DSMC_ERR_INVALID_ARG, "state buffers");
+  return DSMC_OK;
+}
+
+#define DSMC_TRY(x)                      \
+  do {                                   \
+    dsmc_status_t _st = (x);             \
+    if (_st != DSMC_OK) return _st;      \
+  } while (0)
+
+#define DSMC_CUDA(x, what)               \
+  do {                                   \
+    cudaError_t _e = (x);                \
+    if (_e != cudaSuccess) return cuda_fail(_e, what); \
+  } while (0)
+
+MergeArgs merge_args(const Plan& p, const dsmc_config_t* cfg, const float* y, int level,
+                     int conditional, const dsmc_state_t* st, const WsPtrs& w) {
+  MergeArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.K = p.K;
+  a.N = p.N;
+  a.d = p.d;
+  a.level = level;
+  a.B = p.B;
+  a.nT = p.nT;
+  a.nTp = p.nTp;
+  a.rows_per_cta = p.rows_per_cta;
+  a.conditional = conditional;
+  a.root = (level == p.L - 1);
+  a.resampler = cfg->resampler;
+  a.seed = cfg->seed;
+  a.base = cfg->counter_base;
+  a.rs_max = cfg->rs_max_attempts ? cfg->rs_max_attempts : (1u << 20);
+  a.logN = (float)std::log((double)p.N);
+  a.X = st->X;
+  a.logw = st->logw;
+  a.y = y;
+  a.logL = st->logL;
+  a.pairs = st->pairs;
+  a.ws = w;
+  return a;
+}
+
+dsmc_status_t do_init(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& mp,
+                      const float* y, const float* x_ref, dsmc_state_t* st, const WsPtrs& w,
+                      cudaStream_t s) {
+  DSMC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), s), "reset status");
+  DSMC_CUDA(cudaMemsetAsync(w.star, 0, 2 * sizeof(int32_t), s), "reset star");
+  InitArgs a;
+  a.K = p.K;
+  a.N = p.N;
+  a.d = p.d;
+  a.seed = cfg->seed;
+  a.base = cfg->counter_base;
+  a.y = y;
+  a.x_ref = x_ref;
+  a.X = st->X;
+  a.logw = st->logw;
+  a.logL = st->logL;
+  a.status = w.status;
+  DSMC_CUDA(launch_init(p.D, a, mp.bytes, s), "init kernel");
+  return DSMC_OK;
+}
+
+dsmc_status_t do_level(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& mp,
+                       const float* y, int level, int conditional, dsmc_state_t* st,
+                       const WsPtrs& w, cudaStream_t s) {
+  const int M = merges_at_level(p.K, level);
+  for (int m0 = 0; m0 < M; m0 += p.Mc) {
+    MergeArgs a = merge_args(p, cfg, y, level, conditional, st, w);
+    a.m0 = m0;
+    a.mc = std::min(p.Mc, M - m0);
+    a.gid0 = p.level_off[level] + m0;
+    chunking(p, a.mc, a.CH, a.CW);
+    DSMC_CUDA(launch_prologue(p.D, a, mp.bytes, s), "prologue kernel");
+    if (p.dense) {
+      DSMC_CUDA(launch_rowsum(p.D, a, s), "row-sum kernel");
+      DSMC_CUDA(launch_sample_dense(p.D, a, s), "dense sampler kernel");
+    } else {
+      DSMC_CUDA(launch_sample_rs(p.D, a, s), "rejection sampler kernel");
+    }
+    DSMC_CUDA(launch_epilogue(a, s), "epilogue kernel");
+  }
+  return DSMC_OK;
+}
+
+dsmc_status_t do_resolve(const Plan& p, const dsmc_state_t* st, float* traj, double* mean,
+                         double* m2, float* x_star, const WsPtrs& w, cudaStream_t s) {
+  GatherArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.K = p.K;
+  g.N = p.N;
+  g.d = p.d;
+  g.L = p.L;
+  for (int l = 0; l <= p.L; ++l) g.level_off[l] = p.level_off[l];
+  g.X = st->X;
+  g.logw = st->logw;
+  g.pairs = st->pairs;
+  g.star = w.star;
+  g.traj = traj;
+  g.mean = mean;
+  g.m2 = m2;
+  g.x_star = x_star;
+  g.status = w.status;
+  DSMC_CUDA(launch_gather(p.D, g, s), "gather kernel");
+  return DSMC_OK;
+}
+
+struct Prepared {
+  Plan p;
+  ParamBuf mp;
+  WsPtrs w;
+};
+
+dsmc_status_t prepare(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                      const dsmc_proposal_t* prop, void* ws, size_t ws_bytes, Prepared& pr) {
+  DSMC_TRY(check_config(cfg, model));
+  if (prop) DSMC_TRY(check_prop(cfg, model, prop));
+  make_plan(cfg, model, pr.p);
+  DSMC_TRY(check_ws(pr.p, ws, ws_bytes));
+  if (prop) DSMC_TRY(make_params(pr.p.D, model, prop, pr.mp));
+  pr.w = ws_ptrs(pr.p, ws);
+  return DSMC_OK;
+}
+
+dsmc_status_t run_smooth(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                         const dsmc_proposal_t* prop, const float* y, const float* x_ref_in,
+                         float* x_ref_out, dsmc_state_t* st, float* traj, double* mean,
+                         double* m2, double* logL_out, void* ws, size_t ws_bytes, void* stream) {
+  Prepared pr;
+  DSMC_TRY(prepare(cfg, model, prop, ws, ws_bytes, pr));
+  DSMC_TRY(check_state(st, cfg->K));
+  if (!y || !mean) return fail(DSMC_ERR_INVALID_ARG, "y and mean_out are required");
+  const bool cond = x_ref_in != nullptr;
+  if (cond && cfg->N < 2) return fail(DSMC_ERR_INVALID_ARG, "conditional dSMC needs N >= 2");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DSMC_TRY(do_init(pr.p, cfg, pr.mp, y, x_ref_in, st, pr.w, s));
+  for (int l = 0; l < pr.p.L; ++l) DSMC_TRY(do_level(pr.p, cfg, pr.mp, y, l, cond ? 1 : 0, st, pr.w, s));
+  if (cond && pr.p.K == 1)
+    DSMC_CUDA(launch_k1_star(st->logw, pr.p.N, cfg->seed, cfg->counter_base, pr.w.star, s), "star kernel");
+  DSMC_TRY(do_resolve(pr.p, st, traj, mean, m2, cond ? x_ref_out : nullptr, pr.w, s));
+  if (logL_out)
+    DSMC_CUDA(cudaMemcpyAsync(logL_out, st->logL, sizeof(double), cudaMemcpyDeviceToDevice, s), "logL copy");
+  return DSMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dsmc_status_string(dsmc_status_t s) {
+  switch (s) {
+    case DSMC_OK: return "ok";
+    case DSMC_ERR_INVALID_ARG: return "invalid argument";
+    case DSMC_ERR_UNSUPPORTED: return "unsupported";
+    case DSMC_ERR_WORKSPACE: return "workspace too small";
+    case DSMC_ERR_CUDA: return "CUDA error";
+    case DSMC_ERR_NONFINITE: return "non-finite log-weight";
+    case DSMC_ERR_DEGENERATE: return "all weights of a combination are zero";
+    case DSMC_ERR_RS_LIMIT: return "rejection sampling reached its attempt cap";
+    case DSMC_ERR_TIMEOUT: return "bounded wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* dsmc_last_error(void) { return g_last_error.c_str(); }
+
+dsmc_status_t dsmc_state_sizes(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                               size_t bytes_out[4]) {
+  DSMC_TRY(check_config(cfg, model));
+  if (!bytes_out) return fail(DSMC_ERR_INVALID_ARG, "null output");
+  const size_t K = cfg->K, N = cfg->N, d = model->dx;
+  bytes_out[0] = K * N * d * sizeof(float);
+  bytes_out[1] = K * N * sizeof(float);
+  bytes_out[2] = K * sizeof(double);
+  bytes_out[3] = (K > 1 ? K - 1 : 0) * 2 * N * sizeof(int32_t);
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_workspace_size(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                  size_t* bytes) {
+  DSMC_TRY(check_config(cfg, model));
+  if (!bytes) return fail(DSMC_ERR_INVALID_ARG, "null output");
+  Plan p;
+  make_plan(cfg, model, p);
+  *bytes = p.total;
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_init_particles(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                  const dsmc_proposal_t* prop, const float* y,
+                                  const float* x_ref, dsmc_state_t* state, void* ws,
+                                  size_t ws_bytes, void* stream) {
+  Prepared pr;
+  DSMC_TRY(prepare(cfg, model, prop, ws, ws_bytes, pr));
+  DSMC_TRY(check_state(state, cfg->K));
+  if (!y) return fail(DSMC_ERR_INVALID_ARG, "y is required");
+  return do_init(pr.p, cfg, pr.mp, y, x_ref, state, pr.w, static_cast<cudaStream_t>(stream));
+}
+
+dsmc_status_t dsmc_merge_level(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                               const dsmc_proposal_t* prop, const float* y, int level,
+                               int conditional, dsmc_state_t* state, void* ws,
+                               size_t ws_bytes, void* stream) {
+  Prepared pr;
+  DSMC_TRY(prepare(cfg, model, prop, ws, ws_bytes, pr));
+  DSMC_TRY(check_state(state, cfg->K));
+  if (!y) return fail(DSMC_ERR_INVALID_ARG, "y is required");
+  if (level < 0 || level >= pr.p.L) return fail(DSMC_ERR_INVALID_ARG, "level out of range");
+  if (conditional && cfg->N < 2) return fail(DSMC_ERR_INVALID_ARG, "conditional dSMC needs N >= 2");
+  return do_level(pr.p, cfg, pr.mp, y, level, conditional ? 1 : 0, state, pr.w,
+                  static_cast<cudaStream_t>(stream));
+}
+
+dsmc_status_t dsmc_resolve(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                           const dsmc_state_t* state, float* traj_out, double* mean_out,
+                           double* m2_out, float* x_star_out, void* ws, size_t ws_bytes,
+                           void* stream) {
+  Prepared pr;
+  DSMC_TRY(prepare(cfg, model, nullptr, ws, ws_bytes, pr));
+  DSMC_TRY(check_state(state, cfg->K));
+  if (!mean_out) return fail(DSMC_ERR_INVALID_ARG, "mean_out is required");
+  return do_resolve(pr.p, state, traj_out, mean_out, m2_out, x_star_out, pr.w,
+                    static_cast<cudaStream_t>(stream));
+}
+
+dsmc_status_t dsmc_smooth(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                          const dsmc_proposal_t* prop, const float* y, dsmc_state_t* state,
+                          float* traj_out, double* mean_out, double* m2_out, double* logL_out,
+                          void* ws, size_t ws_bytes, void* stream) {
+  return run_smooth(cfg, model, prop, y, nullptr, nullptr, state, traj_out, mean_out, m2_out,
+                    logL_out, ws, ws_bytes, stream);
+}
+
+dsmc_status_t dsmc_conditional_smooth(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                      const dsmc_proposal_t* prop, const float* y,
+                                      const float* x_ref_in, float* x_ref_out,
+                                      dsmc_state_t* state, float* traj_out, double* mean_out,
+                                      double* logL_out, void* ws, size_t ws_bytes,
+                                      void* stream) {
+  if (!x_ref_in || !x_ref_out) return fail(DSMC_ERR_INVALID_ARG, "x_ref_in and x_ref_out are required");
+  return run_smooth(cfg, model, prop, y, x_ref_in, x_ref_out, state, traj_out, mean_out, nullptr,
+                    logL_out, ws, ws_bytes, stream);
+}
+
+dsmc_status_t dsmc_stream_status(void* ws, void* stream, dsmc_status_t* device_status) {
+  if (!ws || !device_status) return fail(DSMC_ERR_INVALID_ARG, "null workspace or output");
+  int h = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the status word is the first field of every workspace layout
+  DSMC_CUDA(cudaMemcpyAsync(&h, ws, sizeof(int), cudaMemcpyDeviceToHost, s), "status copy");
+  DSMC_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+  *device_status = static_cast<dsmc_status_t>(h);
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_debug_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
+                                void* stream) {
+  if (n < 0 || (n > 0 && (!ctr || !out))) return fail(DSMC_ERR_INVALID_ARG, "philox buffers");
+  DSMC_CUDA(launch_philox(ctr, n, seed, out, static_cast<cudaStream_t>(stream)), "philox kernel");
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_debug_merge_weights(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                       int level, int m, float* logW, float* r, float* tiles,
+                                       float* e, float* ratio, int info[4], void* ws,
+                                       size_t ws_bytes, void* stream) {
+  Prepared pr;
+  DSMC_TRY(prepare(cfg, model, nullptr, ws, ws_bytes, pr));
+  const Plan& p = pr.p;
+  if (level < 0 || level >= p.L) return fail(DSMC_ERR_INVALID_ARG, "level out of range");
+  const int M = merges_at_level(p.K, level);
+  if (m < 0 || m >= M) return fail(DSMC_ERR_INVALID_ARG, "combination out of range");
+  const int last_chunk = ((M - 1) / p.Mc) * p.Mc;
+  if (m < last_chunk) return fail(DSMC_ERR_INVALID_ARG, "combination not in the last launch chunk");
+  if (!p.dense && (r || tiles)) return fail(DSMC_ERR_INVALID_ARG, "row/tile weights exist only with dense resampling");
+  dsmc_state_t dummy = {nullptr, nullptr, nullptr, nullptr};
+  MergeArgs a = merge_args(p, cfg, nullptr, level, 0, &dummy, pr.w);
+  a.m0 = last_chunk;
+  a.mc = std::min(p.Mc, M - last_chunk);
+  a.gid0 = p.level_off[level] + last_chunk;
+  if (info) {
+    info[0] = p.B;
+    info[1] = p.nT;
+    info[2] = p.level_off[level] + m;
+    info[3] = level == 0 ? 1 : 0;
+  }
+  DSMC_CUDA(launch_debug_weights(p.D, a, m - last_chunk, logW, r, tiles, e, ratio,
+                                 static_cast<cudaStream_t>(stream)), "inspection kernel");
+  return DSMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// init.cu -- Algorithm 2 (smoother initialisation), and its conditional form (Section 3.2).
+//
+// One CTA per time step t.  Each thread draws particles x_t^n ~ q_t from Philox normals
+// (Box-Muller), writes them, and computes the leaf log-weight
+//   t = 0:  log h_0(y_0 | x) + log P_0(x) - log q_0(x)
+//   t >= 1: log nu_t(x) - log q_t(x)          (exactly 0 when nu_t = q_t)
+// The CTA then normalises the N weights of its t by a log-sum-exp and stores
+// log L_t = LSE - log N.  HBM-bound: writes K N (d + 1) floats.
+#include "kernels.cuh"
+
+namespace dsmc {
+
+namespace {
+
+constexpr int kInitThreads = 256;
+
+template <int D>
+__global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelParams<D> mp) {
+  const int t = blockIdx.x;
+  const int N = a.N, d = a.d;
+  float yt[D], qm[D], qs[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) yt[k] = k < d ? a.y[(size_t)t * d + k] : 0.f;
+  proposal_at<D>(mp, a.y, t, qm, qs);
+  float logsd = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    if (k < d) logsd += logf(qs[k]);
+
+  float* lw = a.logw + (size_t)t * N;
+  float lmax = -INFINITY;
+  bool bad = false;
+  for (int n = threadIdx.x; n < N; n += kInitThreads) {
+    float x[D], z[D];
+    if (a.x_ref != nullptr && n == 0) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        x[k] = k < d ? a.x_ref[(size_t)t * d + k] : 0.f;
+        z[k] = k < d ? (x[k] - qm[k]) / qs[k] : 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < (D + 3) / 4; ++j) {
+        if (4 * j < d) {
+          const uint4 w = draw(a.seed, (uint32_t)n, (uint32_t)t, kPurposeInit, a.base, (uint32_t)j);
+          const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            const float r = sqrtf(-2.f * logf(u23(ws[2 * p])));
+            float sn, cs;
+            sincospif(2.f * u23(ws[2 * p + 1]), &sn, &cs);
+            const int k0 = 4 * j + 2 * p;
+            if (k0 < D) z[k0] = r * cs;
+            if (k0 + 1 < D) z[k0 + 1] = r * sn;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        if (k >= d) z[k] = 0.f;
+        x[k] = k < d ? fmaf(qs[k], z[k], qm[k]) : 0.f;
+      }
+    }
+    float* xo = a.X + ((size_t)t * N + n) * d;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k < d) xo[k] = x[k];
+    float lq = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k < d) lq = fmaf(-0.5f * z[k], z[k], lq);
+    lq -= logsd + (float)d * kHalfLog2Pi;
+    float l;
+    if (t == 0) {
+      l = log_h<D>(mp, yt, x) + log_p0<D>(mp, x) - lq;
+    } else if (mp.nu == DSMC_NU_EQ_Q) {
+      l = 0.f;
+    } else {
+      l = log_nu<D>(mp, yt, qm, qs, x) - lq;
+    }
+    if (isnan(l)) bad = true;
+    lw[n] = l;
+    lmax = fmaxf(lmax, l);
+  }
+
+  __shared__ float red[kInitThreads / 32];
+  __shared__ double redd[kInitThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // block max
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  if (lane == 0) red[warp] = lmax;
+  __syncthreads();
+  float M = red[0];
+#pragma unroll
+  for (int w = 1; w < kInitThreads / 32; ++w) M = fmaxf(M, red[w]);
+  // block sum of exp(l - M)
+  double s = 0.0;
+  for (int n = threadIdx.x; n < N; n += kInitThreads) s += (double)expf(lw[n] - M);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) redd[warp] = s;
+  __syncthreads();
+  double S = 0.0;
+#pragma unroll
+  for (int w = 0; w < kInitThreads / 32; ++w) S += redd[w];
+  const double lse = (double)M + log(S);
+  const float lsef = (float)lse;
+  for (int n = threadIdx.x; n < N; n += kInitThreads) lw[n] = lw[n] - lsef;
+  if (threadIdx.x == 0) a.logL[t] = lse - log((double)N);
+  if (bad || !(M > -INFINITY)) record_status(a.status, bad ? DSMC_ERR_NONFINITE : DSMC_ERR_DEGENERATE);
+}
+
+template <int D>
+cudaError_t launch_init_t(const InitArgs& a, const void* mp, cudaStream_t s) {
+  init_kernel<D><<<a.K, kInitThreads, 0, s>>>(a, *static_cast<const ModelParams<D>*>(mp));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_init(int D, const InitArgs& a, const void* mp, cudaStream_t s) {
+  switch (D) {
+    case 1: return launch_init_t<1>(a, mp, s);
+    case 2: return launch_init_t<2>(a, mp, s);
+    case 4: return launch_init_t<4>(a, mp, s);
+    case 8: return launch_init_t<8>(a, mp, s);
+    case 16: return launch_init_t<16>(a, mp, s);
+    case 32: return launch_init_t<32>(a, mp, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace dsmc

@@ -1,0 +1,101 @@
+// kernels.cuh -- argument blocks and launch wrappers shared by the kernels and the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace dsmc {
+
+// Pointers into the caller's workspace (layout fixed by Plan in api.cu).
+struct WsPtrs {
+  int* status;       // first device error (0 = none)
+  float* U;          // [Mc][N][D]   log2(e) Q^{-1} (A x_L + c - mu)
+  float* alpha;      // [Mc][N]      row term of the base-2 exponent
+  float* V;          // [Mc][N][D]   x_R - mu
+  float* beta;       // [Mc][N]      column term of the base-2 exponent
+  double* shift;     // [Mc][N]      per-row shift (natural log): a_i + log f_max + B*
+  double* logbar;    // [Mc]         log omega-bar, bound of the whole N x N matrix
+  float* T;          // [Mc][N][nTp] tile weights, relative to the row shift
+  float* rw;         // [Mc][N]      row weights of the row stage
+  float* delta;      // [Mc][N]      extra base-2 shift of rows recomputed after underflow
+  int32_t* first;    // [2][K][N]    first-time particle index of each block (double-buffered)
+  int32_t* last;     // [2][K][N]    last-time particle index of each block
+  int32_t* star;     // [2]          root pair of the next reference (conditional mode)
+  double* inc;       // [Mc]         log normalising-constant increments
+};
+
+struct MergeArgs {
+  int K, N, d, level;
+  int m0;            // first combination (within the level) of this launch chunk
+  int mc;            // combinations in this chunk
+  int gid0;          // global (level-major) id of combination m0
+  int B, nT, nTp;    // tile width, tiles per row, padded tiles per row
+  int CH, CW;        // column chunks and chunk width of the row-sum kernel
+  int rows_per_cta;  // row-sum kernel rows per CTA
+  int conditional;   // Algorithm 5 when non-zero
+  int root;          // this level holds the root combination
+  int resampler;
+  uint64_t seed;
+  uint32_t base;
+  uint32_t rs_max;
+  float logN;
+  const float* X;    // [K][N][d]
+  const float* logw; // [K][N]
+  const float* y;    // [K][d]
+  double* logL;      // [K]
+  int32_t* pairs;    // [K-1][2][N]
+  WsPtrs ws;
+};
+
+struct InitArgs {
+  int K, N, d;
+  uint64_t seed;
+  uint32_t base;
+  const float* y;
+  const float* x_ref;
+  float* X;
+  float* logw;
+  double* logL;
+  int* status;
+};
+
+struct GatherArgs {
+  int K, N, d, L;
+  int level_off[33];
+  const float* X;
+  const float* logw;
+  const int32_t* pairs;
+  const int32_t* star;
+  float* traj;
+  double* mean;
+  double* m2;
+  float* x_star;
+  int* status;
+};
+
+// Launchers (defined in the .cu files, dispatched on the padded dimension D).
+cudaError_t launch_init(int D, const InitArgs& a, const void* mp, cudaStream_t s);
+cudaError_t launch_prologue(int D, const MergeArgs& a, const void* mp, cudaStream_t s);
+cudaError_t launch_rowsum(int D, const MergeArgs& a, cudaStream_t s);
+cudaError_t launch_sample_dense(int D, const MergeArgs& a, cudaStream_t s);
+cudaError_t launch_sample_rs(int D, const MergeArgs& a, cudaStream_t s);
+cudaError_t launch_epilogue(const MergeArgs& a, cudaStream_t s);
+cudaError_t launch_gather(int D, const GatherArgs& a, cudaStream_t s);
+cudaError_t launch_debug_weights(int D, const MergeArgs& a, int s_local, float* logW, float* r,
+                                 float* tiles, float* e, float* ratio, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
+                          cudaStream_t s);
+
+// Block geometry of combination m (0-based within level l): left [a, c-1], right [c, b].
+__host__ __device__ __forceinline__ void merge_geom(int K, int level, int m, int& a, int& c,
+                                                    int& b) {
+  const int size = 1 << level;
+  a = 2 * m * size;
+  c = a + size;
+  b = min(a + 2 * size, K) - 1;
+}
+
+}  // namespace dsmc

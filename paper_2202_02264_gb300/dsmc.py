@@ -1,0 +1,321 @@
+"""Thin Python binding of the dSMC C ABI (include/dsmc.h).
+
+Every function here only marshals arguments: tensors become device pointers, the
+current PyTorch stream becomes the ``stream`` argument, and every step of the method runs
+in the CUDA library.  There is no CPU fallback: if the library is not built or no CUDA
+device is present, calls raise.
+
+The functions keep the C names (``dsmc_init_particles``, ``dsmc_merge_level``,
+``dsmc_smooth``, ``dsmc_conditional_smooth`` ...).  ``Smoother`` owns the device buffers
+(allocated through PyTorch) for one (config, model) pair and calls them in order.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import build as _build
+from . import workloads as W
+
+OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "workspace too small",
+          5: "CUDA error", 6: "non-finite log-weight", 7: "degenerate weights",
+          8: "rejection-sampling attempt cap", 9: "timeout"}
+
+FP32, TF32, BF16 = 0, 1, 2
+MULTINOMIAL, RS = 0, 1
+
+
+class DsmcError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({code}) {detail}".strip())
+
+
+class Model(C.Structure):
+    _fields_ = [("kind", C.c_int), ("dx", C.c_int),
+                ("A", C.POINTER(C.c_double)), ("Q", C.POINTER(C.c_double)),
+                ("R", C.POINTER(C.c_double)), ("m0", C.POINTER(C.c_double)),
+                ("P0", C.POINTER(C.c_double)),
+                ("mu", C.c_double), ("phi", C.c_double), ("sigma", C.c_double)]
+
+
+class Proposal(C.Structure):
+    _fields_ = [("kind", C.c_int), ("scale", C.c_double), ("mean", C.c_void_p),
+                ("std", C.c_void_p), ("nu", C.c_int)]
+
+
+class Config(C.Structure):
+    _fields_ = [("K", C.c_int), ("N", C.c_int), ("compute", C.c_int), ("resampler", C.c_int),
+                ("seed", C.c_uint64), ("counter_base", C.c_uint32),
+                ("rs_max_attempts", C.c_uint32), ("max_merges_per_launch", C.c_int)]
+
+
+class State(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("logw", C.c_void_p), ("logL", C.c_void_p),
+                ("pairs", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+EXPORTS = ["dsmc_status_string", "dsmc_last_error", "dsmc_state_sizes", "dsmc_workspace_size",
+           "dsmc_init_particles", "dsmc_merge_level", "dsmc_resolve", "dsmc_smooth",
+           "dsmc_conditional_smooth", "dsmc_stream_status", "dsmc_debug_philox",
+           "dsmc_debug_merge_weights"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = False) -> C.CDLL:
+    """Load libdsmc.so (raises if it is missing; it never falls back to anything)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_needed and _build.needs_build():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libdsmc.so is not built: run __graft_entry__.build() "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        torch.cuda.init() if torch.cuda.is_available() else None
+        lib = C.CDLL(_build.LIB)
+        vp, sz = C.c_void_p, C.c_size_t
+        lib.dsmc_status_string.restype = C.c_char_p
+        lib.dsmc_status_string.argtypes = [C.c_int]
+        lib.dsmc_last_error.restype = C.c_char_p
+        lib.dsmc_last_error.argtypes = []
+        for name in EXPORTS[2:]:
+            getattr(lib, name).restype = C.c_int
+        cfgp, modp, prop_p, statp = C.POINTER(Config), C.POINTER(Model), C.POINTER(Proposal), C.POINTER(State)
+        lib.dsmc_state_sizes.argtypes = [cfgp, modp, C.POINTER(C.c_size_t)]
+        lib.dsmc_workspace_size.argtypes = [cfgp, modp, C.POINTER(C.c_size_t)]
+        lib.dsmc_init_particles.argtypes = [cfgp, modp, prop_p, vp, vp, statp, vp, sz, vp]
+        lib.dsmc_merge_level.argtypes = [cfgp, modp, prop_p, vp, C.c_int, C.c_int, statp, vp, sz, vp]
+        lib.dsmc_resolve.argtypes = [cfgp, modp, statp, vp, vp, vp, vp, vp, sz, vp]
+        lib.dsmc_smooth.argtypes = [cfgp, modp, prop_p, vp, statp, vp, vp, vp, vp, vp, sz, vp]
+        lib.dsmc_conditional_smooth.argtypes = [cfgp, modp, prop_p, vp, vp, vp, statp, vp, vp, vp,
+                                                vp, sz, vp]
+        lib.dsmc_stream_status.argtypes = [vp, vp, C.POINTER(C.c_int)]
+        lib.dsmc_debug_philox.argtypes = [vp, C.c_int64, C.c_uint64, vp, vp]
+        lib.dsmc_debug_merge_weights.argtypes = [cfgp, modp, C.c_int, C.c_int, vp, vp, vp, vp, vp,
+                                                 C.POINTER(C.c_int), vp, sz, vp]
+        _lib = lib
+        return lib
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        detail = load().dsmc_last_error().decode(errors="replace")
+        raise DsmcError(code, where, detail)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class HostModel:
+    """The C model struct plus the FP64 host arrays it points into."""
+
+    def __init__(self, m: W.SSM):
+        d = m.d
+        self.m = m
+        self._arrs = []
+
+        def arr(x, shape):
+            a = np.ascontiguousarray(np.asarray(x if x is not None else np.zeros(shape), np.float64).reshape(shape))
+            self._arrs.append(a)
+            return a.ctypes.data_as(C.POINTER(C.c_double))
+
+        if m.kind == W.LGSSM:
+            self.struct = Model(m.kind, d, arr(m.A, (d, d)), arr(m.Q, (d, d)), arr(m.R, (d, d)),
+                                arr(m.m0, (d,)), arr(m.P0, (d, d)), 0.0, 0.0, 1.0)
+        else:
+            self.struct = Model(m.kind, d, None, None, None, None, None, m.mu, m.phi, m.sigma)
+
+
+def make_config(K, N, seed, counter_base=0, resampler=MULTINOMIAL, compute=FP32,
+                rs_max_attempts=0, max_merges_per_launch=0) -> Config:
+    return Config(int(K), int(N), int(compute), int(resampler), int(seed) & (2**64 - 1),
+                  int(counter_base), int(rs_max_attempts), int(max_merges_per_launch))
+
+
+def make_proposal(m: W.SSM, K: int, device="cuda"):
+    """The C proposal struct and the device arrays it points into (kept alive by caller)."""
+    if m.prop_kind == W.PROP_OBS:
+        return Proposal(W.PROP_OBS, float(m.prop_scale), None, None, int(m.nu)), ()
+    mean = torch.as_tensor(np.asarray(m.prop_mean, np.float32)[:K].reshape(K, m.d).copy(), device=device)
+    std = torch.as_tensor(np.asarray(m.prop_std, np.float32)[:K].reshape(K, m.d).copy(), device=device)
+    return Proposal(W.PROP_GAUSS, 1.0, mean.data_ptr(), std.data_ptr(), int(m.nu)), (mean, std)
+
+
+# ---------------------------------------------------------------- C-named wrappers
+def dsmc_state_sizes(cfg: Config, model: HostModel):
+    out = (C.c_size_t * 4)()
+    _check(load().dsmc_state_sizes(C.byref(cfg), C.byref(model.struct), out), "dsmc_state_sizes")
+    return list(out)
+
+
+def dsmc_workspace_size(cfg: Config, model: HostModel) -> int:
+    out = C.c_size_t(0)
+    _check(load().dsmc_workspace_size(C.byref(cfg), C.byref(model.struct), C.byref(out)),
+           "dsmc_workspace_size")
+    return int(out.value)
+
+
+def dsmc_init_particles(cfg, model, prop, y, x_ref, state, ws, stream=None):
+    _check(load().dsmc_init_particles(C.byref(cfg), C.byref(model.struct), C.byref(prop), _ptr(y),
+                                      _ptr(x_ref), C.byref(state), _ptr(ws), ws.numel(),
+                                      _stream(stream)), "dsmc_init_particles")
+
+
+def dsmc_merge_level(cfg, model, prop, y, level, conditional, state, ws, stream=None):
+    _check(load().dsmc_merge_level(C.byref(cfg), C.byref(model.struct), C.byref(prop), _ptr(y),
+                                   int(level), int(conditional), C.byref(state), _ptr(ws),
+                                   ws.numel(), _stream(stream)), "dsmc_merge_level")
+
+
+def dsmc_resolve(cfg, model, state, traj, mean, m2, x_star, ws, stream=None):
+    _check(load().dsmc_resolve(C.byref(cfg), C.byref(model.struct), C.byref(state), _ptr(traj),
+                               _ptr(mean), _ptr(m2), _ptr(x_star), _ptr(ws), ws.numel(),
+                               _stream(stream)), "dsmc_resolve")
+
+
+def dsmc_smooth(cfg, model, prop, y, state, traj, mean, m2, logL, ws, stream=None):
+    _check(load().dsmc_smooth(C.byref(cfg), C.byref(model.struct), C.byref(prop), _ptr(y),
+                              C.byref(state), _ptr(traj), _ptr(mean), _ptr(m2), _ptr(logL),
+                              _ptr(ws), ws.numel(), _stream(stream)), "dsmc_smooth")
+
+
+def dsmc_conditional_smooth(cfg, model, prop, y, x_ref_in, x_ref_out, state, traj, mean, logL,
+                            ws, stream=None):
+    _check(load().dsmc_conditional_smooth(C.byref(cfg), C.byref(model.struct), C.byref(prop),
+                                          _ptr(y), _ptr(x_ref_in), _ptr(x_ref_out), C.byref(state),
+                                          _ptr(traj), _ptr(mean), _ptr(logL), _ptr(ws), ws.numel(),
+                                          _stream(stream)), "dsmc_conditional_smooth")
+
+
+def dsmc_stream_status(ws, stream=None) -> int:
+    out = C.c_int(0)
+    _check(load().dsmc_stream_status(_ptr(ws), _stream(stream), C.byref(out)), "dsmc_stream_status")
+    return int(out.value)
+
+
+def dsmc_debug_philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
+    ctr = ctr.contiguous()
+    out = torch.empty_like(ctr)
+    n = ctr.numel() // 4
+    _check(load().dsmc_debug_philox(_ptr(ctr), n, int(seed), _ptr(out), _stream(stream)),
+           "dsmc_debug_philox")
+    return out
+
+
+def dsmc_debug_merge_weights(cfg, model, level, m, ws, want=("logW", "r", "tiles", "e", "ratio"),
+                             stream=None):
+    N = cfg.N
+    info = (C.c_int * 4)()
+    # first call for the tile count
+    _check(load().dsmc_debug_merge_weights(C.byref(cfg), C.byref(model.struct), int(level), int(m),
+                                           None, None, None, None, None, info, _ptr(ws), ws.numel(),
+                                           _stream(stream)), "dsmc_debug_merge_weights")
+    B, nT = info[0], info[1]
+    dev = ws.device
+    out = {}
+    out["logW"] = torch.empty((N, N), dtype=torch.float32, device=dev) if "logW" in want else None
+    out["r"] = torch.empty((N,), dtype=torch.float32, device=dev) if "r" in want else None
+    out["tiles"] = torch.empty((N, nT), dtype=torch.float32, device=dev) if "tiles" in want else None
+    out["e"] = torch.empty((N, N), dtype=torch.float32, device=dev) if "e" in want else None
+    out["ratio"] = torch.empty((N, N), dtype=torch.float32, device=dev) if "ratio" in want else None
+    _check(load().dsmc_debug_merge_weights(C.byref(cfg), C.byref(model.struct), int(level), int(m),
+                                           _ptr(out["logW"]), _ptr(out["r"]), _ptr(out["tiles"]),
+                                           _ptr(out["e"]), _ptr(out["ratio"]), info, _ptr(ws),
+                                           ws.numel(), _stream(stream)), "dsmc_debug_merge_weights")
+    out.update(B=info[0], nT=info[1], gid=info[2], left_leaf=info[3])
+    return out
+
+
+# ---------------------------------------------------------------- buffer owner
+class Smoother:
+    """Device buffers for one (model, K, N) and the calls of the C ABI over them.
+
+    Buffers are allocated once through PyTorch (the library allocates nothing)."""
+
+    def __init__(self, model: W.SSM, K: int, N: int, seed: int = 0, resampler: int = MULTINOMIAL,
+                 compute: int = FP32, rs_max_attempts: int = 0, max_merges_per_launch: int = 0,
+                 device: str = "cuda", want_traj: bool = False):
+        if not torch.cuda.is_available():
+            raise RuntimeError("dSMC needs a CUDA device; there is no CPU path")
+        self.model = model
+        self.hm = HostModel(model)
+        self.K, self.N, self.d = int(K), int(N), model.d
+        self.cfg = make_config(K, N, seed, 0, resampler, compute, rs_max_attempts, max_merges_per_launch)
+        self.prop, self._prop_keep = make_proposal(model, K, device)
+        sizes = dsmc_state_sizes(self.cfg, self.hm)
+        self.X = torch.empty((self.K, self.N, self.d), dtype=torch.float32, device=device)
+        self.logw = torch.empty((self.K, self.N), dtype=torch.float32, device=device)
+        self.logL = torch.empty((self.K,), dtype=torch.float64, device=device)
+        self.pairs = torch.empty((max(self.K - 1, 0), 2, self.N), dtype=torch.int32, device=device)
+        assert sizes[0] == self.X.numel() * 4 and sizes[3] == self.pairs.numel() * 4
+        self.state = State(self.X.data_ptr(), self.logw.data_ptr(), self.logL.data_ptr(),
+                           self.pairs.data_ptr() if self.pairs.numel() else None)
+        wsb = dsmc_workspace_size(self.cfg, self.hm)
+        self.ws = torch.empty((wsb,), dtype=torch.uint8, device=device)
+        self.mean = torch.empty((self.K, self.d), dtype=torch.float64, device=device)
+        self.m2 = torch.empty((self.K, self.d), dtype=torch.float64, device=device)
+        self.logL_out = torch.empty((1,), dtype=torch.float64, device=device)
+        self.traj = (torch.empty((self.K, self.N, self.d), dtype=torch.float32, device=device)
+                     if want_traj else None)
+        self.x_star = torch.empty((self.K, self.d), dtype=torch.float32, device=device)
+
+    @property
+    def levels(self) -> int:
+        L = 0
+        while (1 << L) < self.K:
+            L += 1
+        return L
+
+    def set_seed(self, seed: int, counter_base: int = 0):
+        self.cfg.seed = int(seed) & (2**64 - 1)
+        self.cfg.counter_base = int(counter_base)
+
+    def smooth(self, y: torch.Tensor, stream=None):
+        dsmc_smooth(self.cfg, self.hm, self.prop, y, self.state, self.traj, self.mean, self.m2,
+                    self.logL_out, self.ws, stream)
+        return self.mean
+
+    def conditional(self, y: torch.Tensor, x_ref_in: torch.Tensor, x_ref_out: torch.Tensor, stream=None):
+        dsmc_conditional_smooth(self.cfg, self.hm, self.prop, y, x_ref_in, x_ref_out, self.state,
+                                self.traj, self.mean, self.logL_out, self.ws, stream)
+        return x_ref_out
+
+    def init(self, y, x_ref=None, stream=None):
+        dsmc_init_particles(self.cfg, self.hm, self.prop, y, x_ref, self.state, self.ws, stream)
+
+    def merge_level(self, y, level, conditional=False, stream=None):
+        dsmc_merge_level(self.cfg, self.hm, self.prop, y, level, conditional, self.state, self.ws, stream)
+
+    def resolve(self, x_star=False, stream=None):
+        dsmc_resolve(self.cfg, self.hm, self.state, self.traj, self.mean, self.m2,
+                     self.x_star if x_star else None, self.ws, stream)
+
+    def status(self, stream=None) -> int:
+        return dsmc_stream_status(self.ws, stream)

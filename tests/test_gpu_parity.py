@@ -1,0 +1,385 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Rules (spec contract):
+  * indices (pairs) bit-exact when both sides consume the same Philox uniforms and the
+    same weight arrays (the device's own FP32 weights, exported);
+  * log-weights within 1e-5 relative: |dlogW| <= 1e-5 max(1, |logW|) on identical particles;
+  * smoothing means within 3 Monte Carlo standard errors of RTS / the grid reference.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import core, grid, kalman
+from paper_2202_02264_gb300 import dsmc, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+LOGW_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2202_02264_gb300 import build
+    build.build()
+    dsmc.load()
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def levels(K):
+    L = 0
+    while (1 << L) < K:
+        L += 1
+    return L
+
+
+def level_offsets(K):
+    L = levels(K)
+    offs = [0]
+    for l in range(L):
+        offs.append(offs[-1] + core.merges_at_level(K, l))
+    return offs
+
+
+def endpoint_indices(pairs, K, N, level, m):
+    """Particle indices of the left block at c-1 and the right block at c, by composing the
+    stored pairs (the same walk the oracle test pins against explicit copies)."""
+    offs = level_offsets(K)
+    size = 1 << level
+    a = 2 * m * size
+    c = a + size
+
+    def walk(t, top):
+        sig = np.arange(N)
+        for l in range(top - 1, -1, -1):
+            sz = 1 << l
+            p = (t // (2 * sz)) * 2 * sz
+            if p + sz >= K:
+                continue
+            g = offs[l] + p // (2 * sz)
+            sig = pairs[g, 1 if t >= p + sz else 0][sig]
+        return sig
+
+    return a, c, walk(c - 1, level), walk(c, level)
+
+
+# ------------------------------------------------------------------------ RNG
+def test_philox_bit_exact():
+    rng = np.random.default_rng(3)
+    ctr = rng.integers(0, 2**32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    for seed in [0, 1, 0xDEADBEEFCAFEF00D]:
+        g = dsmc.dsmc_debug_philox(dev(ctr.view(np.int32), torch.int32), seed).cpu().numpy().view(np.uint32)
+        o = core.philox_many(ctr, [seed & 0xFFFFFFFF, seed >> 32])
+        np.testing.assert_array_equal(g, o)
+
+
+# ------------------------------------------------------------------------ Algorithm 2
+@pytest.mark.parametrize("name,K,N,nu", [("lgssm_d8", 40, 300, W.NU_EQ_Q), ("lgssm_1d", 33, 97, W.NU_PROP_H),
+                                         ("sv", 50, 200, W.NU_EQ_Q), ("sv", 20, 64, W.NU_PROP_H),
+                                         ("lgssm_d4", 16, 1000, W.NU_PROP_H)])
+def test_init_matches_oracle(name, K, N, nu):
+    wl = W.workload(name, K=K, N=N)
+    m = wl.model
+    m.nu = nu
+    sm = dsmc.Smoother(m, K, N, seed=77)
+    y = dev(wl.y)
+    sm.init(y)
+    torch.cuda.synchronize()
+    X, lw, lL = core.init(m, wl.y.astype(np.float32).astype(np.float64), K, N, 77)
+    Xg = sm.X.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(Xg, X, rtol=0, atol=2e-5 * max(1.0, np.abs(X).max()))
+    lwg = sm.logw.cpu().numpy().astype(np.float64)
+    assert (np.abs(lwg - lw) <= LOGW_RTOL * np.maximum(1, np.abs(lw)) * 5).all()
+    np.testing.assert_allclose(sm.logL.cpu().numpy(), lL, atol=1e-4)
+    assert sm.status() == 0
+
+
+def test_conditional_init_keeps_reference():
+    wl = W.workload("lgssm_d8", K=16, N=64)
+    sm = dsmc.Smoother(wl.model, 16, 64, seed=5)
+    xr = dev(np.random.default_rng(0).standard_normal((16, 8)))
+    sm.init(dev(wl.y), x_ref=xr)
+    torch.cuda.synchronize()
+    assert torch.equal(sm.X[:, 0, :], xr)
+
+
+# ------------------------------------------------------------------------ one level
+def _level_setup(name, K, N, level, resampler=dsmc.MULTINOMIAL, seed=11, nu=W.NU_EQ_Q,
+                 conditional=False):
+    wl = W.workload(name, K=K, N=N)
+    m = wl.model
+    m.nu = nu
+    sm = dsmc.Smoother(m, K, N, seed=seed, resampler=resampler)
+    y = dev(wl.y)
+    xr = dev(np.zeros((K, m.d))) if conditional else None
+    sm.init(y, x_ref=xr)
+    for l in range(level + 1):
+        sm.merge_level(y, l, conditional=conditional)
+    torch.cuda.synchronize()
+    return wl, m, sm
+
+
+CASES = [("lgssm_d8", 64, 64, 0), ("lgssm_d8", 16, 300, 1), ("lgssm_1d", 37, 1000, 2),
+         ("sv", 9, 700, 3), ("lgssm_d4", 12, 2500, 0), ("lgssm_d4", 6, 96, 2)]
+
+
+@pytest.mark.parametrize("name,K,N,level", CASES)
+def test_logw_rows_and_indices(name, K, N, level):
+    """For the last combination of a level: device log-weights vs the oracle's FP64 on the
+    same particles; device row weights vs the exact row sums; device pairs vs the oracle's
+    device-precision sampler fed the device's own weights and the same uniforms."""
+    wl, m, sm = _level_setup(name, K, N, level)
+    M = core.merges_at_level(K, level)
+    mi = M - 1
+    dbg = dsmc.dsmc_debug_merge_weights(sm.cfg, sm.hm, level, mi, sm.ws)
+    X = sm.X.cpu().numpy().astype(np.float64)
+    lw = sm.logw.cpu().numpy().astype(np.float64)
+    pairs = sm.pairs.cpu().numpy()
+    a, c, iL, iR = endpoint_indices(pairs, K, N, level, mi)
+    b = min(a + 2 * (1 << level), K) - 1
+    wl_ = lw[c - 1] if level == 0 else np.full(N, -np.log(N))
+    wr_ = lw[c] if b == c else np.full(N, -np.log(N))
+    yo = wl.y.astype(np.float32).astype(np.float64)
+    ref = core.logw_matrix(m, yo, K, c, X[c - 1][iL], X[c][iR], wl_, wr_)
+    got = dbg["logW"].cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref) / np.maximum(1.0, np.abs(ref))
+    assert err.max() <= LOGW_RTOL, err.max()
+    # row weights: r_i proportional to sum_j exp(logW_ij)
+    rs = np.exp(np.logaddexp.reduce(ref, axis=1) - np.logaddexp.reduce(ref, axis=1).max())
+    r = dbg["r"].cpu().numpy().astype(np.float64)
+    big = rs > 1e-6
+    np.testing.assert_allclose(r[big], rs[big], rtol=2e-4)
+    # indices bit-exact with the device-precision sampler
+    g = dbg["gid"]
+    li, ri = core.kp_dense_pairs(dbg["r"].cpu().numpy(), dbg["tiles"].cpu().numpy(),
+                                 dbg["e"].cpu().numpy(), dbg["B"], sm.cfg.seed, g, 0, N)
+    np.testing.assert_array_equal(pairs[g, 0], li)
+    np.testing.assert_array_equal(pairs[g, 1], ri)
+    assert sm.status() == 0
+
+
+@pytest.mark.parametrize("name,K,N,level", [("sv", 8, 500, 0), ("sv", 16, 333, 2), ("lgssm_1d", 5, 64, 2)])
+def test_rejection_indices_bit_exact(name, K, N, level):
+    wl, m, sm = _level_setup(name, K, N, level, resampler=dsmc.RS)
+    M = core.merges_at_level(K, level)
+    dbg = dsmc.dsmc_debug_merge_weights(sm.cfg, sm.hm, level, M - 1, sm.ws, want=("logW", "ratio"))
+    q = dbg["ratio"].cpu().numpy()
+    assert (q <= 1.0 + 1e-6).all() and (q >= 0).all()
+    li, ri, att, st = core.kp_rs_pairs(q, sm.cfg.seed, dbg["gid"], 0, N, max_attempts=1 << 20)
+    pairs = sm.pairs.cpu().numpy()
+    np.testing.assert_array_equal(pairs[dbg["gid"], 0], li)
+    np.testing.assert_array_equal(pairs[dbg["gid"], 1], ri)
+    # the ratio is exp(logW - log wbar): consistent with the exported log-weights
+    lW = dbg["logW"].cpu().numpy().astype(np.float64)
+    rq = np.exp(lW - lW.max())
+    assert np.allclose(q / q.max(), rq, rtol=1e-4, atol=1e-7)
+    assert sm.status() == 0
+
+
+def test_level0_increment_matches_oracle():
+    """log L after level 0 = log L_{c-1} + log L_c + log sum_ij exp(logW_ij) (Eq. Lab)."""
+    wl, m, sm = _level_setup("lgssm_d8", 16, 256, 0)
+    X = sm.X.cpu().numpy().astype(np.float64)
+    lw = sm.logw.cpu().numpy().astype(np.float64)
+    yo = wl.y.astype(np.float32).astype(np.float64)
+    smb = dsmc.Smoother(m, 16, 256, seed=11)
+    smb.init(dev(wl.y))
+    torch.cuda.synchronize()
+    L0 = smb.logL.cpu().numpy()
+    Lg = sm.logL.cpu().numpy()
+    for mi in range(8):
+        a, c = 2 * mi, 2 * mi + 1
+        ref = core.logw_matrix(m, yo, 16, c, X[c - 1], X[c], lw[c - 1], lw[c])
+        inc = np.logaddexp.reduce(ref.reshape(-1))
+        assert Lg[a] == pytest.approx(L0[a] + L0[c] + inc, abs=2e-5 * max(1, abs(inc)))
+
+
+# ------------------------------------------------------------------------ resolution
+@pytest.mark.parametrize("K,N", [(11, 8), (32, 64), (100, 33)])
+def test_resolution_bit_exact(K, N):
+    wl = W.workload("lgssm_d4", K=K, N=N)
+    sm = dsmc.Smoother(wl.model, K, N, seed=3, want_traj=True)
+    sm.smooth(dev(wl.y))
+    torch.cuda.synchronize()
+    X = sm.X.cpu().numpy()
+    pairs = sm.pairs.cpu().numpy()
+    traj = sm.traj.cpu().numpy()
+    offs = level_offsets(K)
+    L = levels(K)
+    for t in range(K):
+        sig = np.arange(N)
+        for l in range(L - 1, -1, -1):
+            sz = 1 << l
+            p = (t // (2 * sz)) * 2 * sz
+            if p + sz >= K:
+                continue
+            sig = pairs[offs[l] + p // (2 * sz), 1 if t >= p + sz else 0][sig]
+        np.testing.assert_array_equal(traj[t], X[t][sig])
+    mean = sm.mean.cpu().numpy()
+    np.testing.assert_allclose(mean, traj.astype(np.float64).mean(1), rtol=1e-6, atol=1e-6)
+    assert ((pairs >= 0) & (pairs < N)).all()
+
+
+def test_conditional_keeps_slot0_and_star_is_a_particle():
+    K, N = 20, 64
+    wl = W.workload("lgssm_d4", K=K, N=N)
+    sm = dsmc.Smoother(wl.model, K, N, seed=9, want_traj=True)
+    xr = dev(np.random.default_rng(2).standard_normal((K, 4)))
+    out = torch.empty_like(xr)
+    sm.conditional(dev(wl.y), xr, out)
+    torch.cuda.synchronize()
+    assert (sm.pairs[:, :, 0] == 0).all()
+    assert torch.equal(sm.traj[:, 0, :], xr)
+    X = sm.X.cpu().numpy()
+    o = out.cpu().numpy()
+    for t in range(K):
+        assert (np.abs(X[t] - o[t]).sum(1) == 0).any()
+
+
+# ------------------------------------------------------------------------ statistics
+def _gpu_means(m, y, K, N, R, resampler=dsmc.MULTINOMIAL, seed0=1000):
+    sm = dsmc.Smoother(m, K, N, seed=seed0, resampler=resampler)
+    yd = dev(y)
+    out = []
+    for r in range(R):
+        sm.set_seed(seed0 + r)
+        out.append(sm.smooth(yd).cpu().numpy().copy())
+    assert sm.status() == 0
+    return np.array(out)
+
+
+def _check(means, ref, zmax=4.5, cover=0.975):
+    R = means.shape[0]
+    sd = means.std(0, ddof=1)
+    z = np.abs(means.mean(0) - ref) / (sd / np.sqrt(R))
+    assert z.max() < zmax, z.max()
+    assert (np.abs(means - ref) <= 3 * sd).mean() >= cover
+
+
+@pytest.mark.parametrize("nu", [W.NU_EQ_Q, W.NU_PROP_H])
+def test_means_vs_rts_1d(nu):
+    wl = W.workload("lgssm_1d")
+    m = W.lgssm_1d(nu)
+    ms, _, _ = kalman.rts_for(m, wl.y)
+    _check(_gpu_means(m, wl.y, wl.K, wl.N, 64), ms)
+
+
+def test_means_vs_rts_d8_ragged():
+    m = W.lgssm_d8()
+    K, N = 100, 300
+    _, y = W.simulate(m, K, 77)
+    ms, _, _ = kalman.rts_for(m, y)
+    _check(_gpu_means(m, y, K, N, 32), ms)
+
+
+def test_means_rejection_vs_rts():
+    wl = W.workload("lgssm_1d", K=24, N=256)
+    ms, _, _ = kalman.rts_for(wl.model, wl.y)
+    _check(_gpu_means(wl.model, wl.y, wl.K, wl.N, 32, resampler=dsmc.RS), ms)
+
+
+def test_sv_means_vs_grid():
+    K, N = 64, 512
+    m = W.sv(K)
+    _, y = W.simulate(m, K, 2264 + 3)
+    gm, _, _ = grid.sv_grid_smoother(m.mu, m.phi, m.sigma, y[:, 0])
+    _check(_gpu_means(m, y, K, N, 32), gm[:, None])
+
+
+def test_logL_unbiased():
+    wl = W.workload("lgssm_1d", K=8, N=32)
+    _, _, ll = kalman.rts_for(wl.model, wl.y)
+    sm = dsmc.Smoother(wl.model, 8, 32, seed=0)
+    yd = dev(wl.y)
+    r = []
+    for s in range(600):
+        sm.set_seed(5000 + s)
+        sm.smooth(yd)
+        r.append(float(sm.logL_out.item()))
+    r = np.exp(np.array(r) - ll)
+    assert abs(r.mean() - 1.0) < 4 * r.std(ddof=1) / np.sqrt(len(r))
+
+
+def test_gpu_vs_oracle_same_seeds():
+    """Same seeds, same Philox streams: the device and the oracle are two independent
+    implementations of the same smoother; their seed-averaged means agree."""
+    wl = W.workload("lgssm_1d", K=16, N=128)
+    R = 32
+    g = _gpu_means(wl.model, wl.y, wl.K, wl.N, R)
+    o = np.array([core.smooth(wl.model, wl.y.astype(np.float32).astype(np.float64), wl.K, wl.N, 1000 + r)["mean"]
+                  for r in range(R)])
+    sd = np.sqrt((g.var(0, ddof=1) + o.var(0, ddof=1)) / 2)
+    z = np.abs(g.mean(0) - o.mean(0)) / (sd * np.sqrt(2.0 / R))
+    assert z.max() < 4.5
+
+
+# ------------------------------------------------------------------------ edge cases
+def test_k1_weighted_leaf():
+    m = W.lgssm_1d()
+    _, y = W.simulate(m, 1, 3)
+    sm = dsmc.Smoother(m, 1, 50, seed=12)
+    mean = sm.smooth(dev(y)).cpu().numpy()
+    X = sm.X.cpu().numpy()[0, :, 0].astype(np.float64)
+    w = np.exp(sm.logw.cpu().numpy()[0].astype(np.float64))
+    assert mean[0, 0] == pytest.approx((w * X).sum(), abs=1e-5)
+
+
+def test_n1_is_concatenation():
+    wl = W.workload("lgssm_d4", K=9, N=1)
+    sm = dsmc.Smoother(wl.model, 9, 1, seed=4, want_traj=True)
+    sm.smooth(dev(wl.y))
+    torch.cuda.synchronize()
+    assert (sm.pairs == 0).all()
+    assert torch.equal(sm.traj, sm.X)
+
+
+def test_nonfinite_observation_reports_status():
+    wl = W.workload("lgssm_1d", K=8, N=32)
+    y = wl.y.copy()
+    y[3] = np.nan
+    sm = dsmc.Smoother(wl.model, 8, 32, seed=1)
+    sm.smooth(dev(y))
+    assert sm.status() == 6
+    assert ((sm.pairs >= 0) & (sm.pairs < 32)).all()
+    # the context stays usable
+    sm.smooth(dev(wl.y))
+    assert sm.status() == 0
+
+
+def test_rejection_cap_reports_status():
+    wl = W.workload("lgssm_d8", K=4, N=64)
+    sm = dsmc.Smoother(wl.model, 4, 64, seed=1, resampler=dsmc.RS, rs_max_attempts=1)
+    sm.smooth(dev(wl.y))
+    assert sm.status() == 8
+    assert ((sm.pairs >= 0) & (sm.pairs < 64)).all()
+
+
+def test_max_dense_n():
+    wl = W.workload("sv", K=2, N=16384)
+    sm = dsmc.Smoother(wl.model, 2, 16384, seed=1)
+    sm.smooth(dev(wl.y))
+    assert sm.status() == 0
+    dbg = dsmc.dsmc_debug_merge_weights(sm.cfg, sm.hm, 0, 0, sm.ws, want=("r", "tiles", "e"))
+    li, ri = core.kp_dense_pairs(dbg["r"].cpu().numpy(), dbg["tiles"].cpu().numpy(),
+                                 dbg["e"].cpu().numpy(), dbg["B"], sm.cfg.seed, dbg["gid"], 0, 16384)
+    p = sm.pairs.cpu().numpy()
+    np.testing.assert_array_equal(p[0, 0], li)
+    np.testing.assert_array_equal(p[0, 1], ri)
+
+
+def test_small_merge_chunks_same_result():
+    """Splitting a level into several launch chunks does not change any draw."""
+    wl = W.workload("lgssm_d4", K=40, N=96)
+    a = dsmc.Smoother(wl.model, 40, 96, seed=21)
+    b = dsmc.Smoother(wl.model, 40, 96, seed=21, max_merges_per_launch=3)
+    y = dev(wl.y)
+    a.smooth(y)
+    b.smooth(y)
+    torch.cuda.synchronize()
+    assert torch.equal(a.pairs, b.pairs)
+    assert torch.equal(a.mean, b.mean)
