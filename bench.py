@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Throughput of the dSMC smoother (N*T/s) on GB300, with roofline, end-to-end and CPU
+oracle baselines.
+
+A step is one full smoothing of one synthetic sequence: Algorithm 2 init, every level of
+Algorithm 6 (prologue, fused exp / tile-sum, three-stage pair sampler, map epilogue) and
+the trajectory resolve with fused means.  Default workload: the 8-dimensional
+linear-Gaussian model, K = 1024 steps, N = 1024 particles, FP32.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload NAME]
+
+Under torchrun each rank smooths its own independent sequence (replicas, weak scaling);
+no collective touches the data path, one barrier brackets the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dSMC N·T/s per GB300 (batched mixed vs plain) at fixed error; p50/p99 latency"
+UNIT = "N·T/s"
+MUFU_EX2_PER_CLK_SM = 32       # measured on GB300 (ex2 probe), twice B200's 16
+FMA_PER_CLK_SM = 128
+SMS = 152
+
+WORKLOADS = {
+    "lgssm_d8": dict(K=1024, N=1024, resampler="dense"),
+    "lgssm_1d": dict(K=32, N=64, resampler="dense"),
+    "sv": dict(K=4096, N=4096, resampler="dense"),
+    "sv_rs": dict(K=4096, N=16384, resampler="rs"),
+    "lgssm_d4": dict(K=512, N=512, resampler="dense"),
+}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    lrank = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, lrank
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(wl, target_s=12.0, seed=1000):
+    """The FP64 CPU oracle on a bounded sample of the workload: the first K' steps of the
+    same sequence at the same N (whole smoothings), K' grown until ~target_s of work."""
+    from oracle import core
+    m, y, N = wl.model, wl.y.astype(np.float32).astype(np.float64), wl.N
+    Kp = 8
+    done_units, done_s, runs = 0, 0.0, []
+    while True:
+        Kp = min(Kp, wl.K)
+        t0 = time.perf_counter()
+        core.smooth(m, y[:Kp], Kp, N, seed)
+        dt = time.perf_counter() - t0
+        runs.append((Kp, dt))
+        done_units += Kp * N
+        done_s += dt
+        if done_s >= target_s or Kp == wl.K:
+            break
+        Kp = Kp * 2 if dt < target_s / 8 else Kp
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    Klast, tlast = runs[-1]
+    return {"value": Klast * N / tlast, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"whole smoothings of the first {Klast} of {wl.K} steps, N={N}, "
+                      f"d={m.d}, FP64; {len(runs)} runs, {done_s:.1f} s total"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2202_02264_gb300 import workloads as W
+    spec = WORKLOADS[args.workload]
+    wl = W.workload(args.workload.replace("_rs", ""), K=spec["K"], N=spec["N"])
+    from oracle import core
+    y = wl.y.astype(np.float32).astype(np.float64)
+    # calibrate K' so that each step is a bounded slice of the workload (~2-4 s)
+    Kp = 8
+    while True:
+        t0 = time.perf_counter()
+        core.smooth(wl.model, y[:Kp], Kp, wl.N, 999)
+        dt = time.perf_counter() - t0
+        if dt > 1.0 or Kp >= wl.K:
+            break
+        Kp = min(Kp * 2, wl.K)
+    for w in range(args.warmup):
+        core.smooth(wl.model, y[:Kp], Kp, wl.N, 900 + w)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        core.smooth(wl.model, y[:Kp], Kp, wl.N, 1000 + s)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps * Kp * wl.N / tot
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "K": wl.K, "N": wl.N, "dx": wl.model.d,
+                       "sample_K": Kp},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: a whole smoothing of the first {Kp} of {wl.K} "
+                                       f"steps, N={wl.N}, FP64"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2202_02264_gb300 import dsmc, workloads as W
+
+    world, rank, lrank = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(lrank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spec = WORKLOADS[args.workload]
+    base_name = args.workload.replace("_rs", "")
+    wl = W.workload(base_name, K=spec["K"], N=spec["N"])
+    K, N = wl.K, wl.N
+    resampler = dsmc.RS if spec["resampler"] == "rs" else dsmc.MULTINOMIAL
+    sm = dsmc.Smoother(wl.model, K, N, seed=1000 + 7919 * rank, resampler=resampler)
+    y = torch.as_tensor(wl.y, dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        sm.set_seed(1000 + 7919 * rank, counter_base=i)
+        sm.smooth(y)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    st = sm.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after warm-up")
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    dsmc.dsmc_profile_enable(True)
+    for i in range(args.steps):
+        flush.zero_()                      # L2 flushed between timed steps, outside the events
+        ev[i][0].record(stream)
+        step(args.warmup + i)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    rs_ms, rs_n, rs_pairs, launches = dsmc.dsmc_profile_read()
+    dsmc.dsmc_profile_enable(False)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(per_step) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+    st = sm.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after timed steps")
+    value = world * args.steps * N * K / t_total
+
+    # end to end through the C ABI with host buffers: H2D of y, smoothing, D2H of results
+    y_host = torch.as_tensor(wl.y, dtype=torch.float32).pin_memory()
+    mean_host = torch.empty((K, wl.model.d), dtype=torch.float64).pin_memory()
+    logL_host = torch.empty((1,), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(e2e_steps)]
+    for i in range(e2e_steps):
+        flush.zero_()
+        eev[i][0].record(stream)
+        y.copy_(y_host, non_blocking=True)
+        sm.set_seed(1000 + 7919 * rank, counter_base=10_000 + i)
+        sm.smooth(y)
+        mean_host.copy_(sm.mean, non_blocking=True)
+        logL_host.copy_(sm.logL_out, non_blocking=True)
+        eev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_t = sum(a.elapsed_time(b) for a, b in eev) / 1e3 / e2e_steps
+    e2e = {"value": world * N * K / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": y_host.numel() * 4,
+           "d2h_bytes_per_step": mean_host.numel() * 8 + 8}
+
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    ex2_peak = MUFU_EX2_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9       # G exp / s
+    achieved = rs_pairs / (rs_ms / 1e3) / 1e9 if rs_ms > 0 else None   # G exp / s
+    d = wl.model.d
+    roofline = {"bound": "alu", "kernel": "rowsum_kernel (fused exp / tile sums)",
+                "achieved": achieved, "peak": ex2_peak, "unit": "Gexp/s",
+                "frac": achieved / ex2_peak if achieved else None,
+                "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
+                               f"({src} max clock)",
+                "fma_bound_frac": (achieved / (FMA_PER_CLK_SM / (d + 2) * SMS * sm_max * 1e-3)
+                                   if achieved else None),
+                "avg_launch_ms": rs_ms / max(rs_n, 1), "launches": rs_n,
+                "traffic": None}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "K": K, "N": N, "dx": d,
+                       "resampler": spec["resampler"], "compute": "fp32 cuda-core",
+                       "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches,
+            "step_ms": {"median": float(np.median(per_step)), "p99": float(np.percentile(per_step, 99))}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(wl)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lgssm_d8", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        from oracle import core  # built here so cpu_baseline does not compile mid-run
+        core.build()
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

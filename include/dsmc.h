@@ -179,6 +179,21 @@ dsmc_status_t dsmc_conditional_smooth(const dsmc_config_t* cfg, const dsmc_model
  * in this workspace since the last dsmc_init_particles (DSMC_OK if none). */
 dsmc_status_t dsmc_stream_status(void* ws, void* stream, dsmc_status_t* device_status);
 
+/* ---- Measurement: CUDA-event timing of the fused exp / tile-sum kernel (the N x N part of
+ * Algorithm 1), recorded on the stream that kernel runs on. */
+
+/* enable = 1 starts timing the calls made from this host thread (counters reset);
+ * enable = 0 stops.  Host call; no device work. */
+dsmc_status_t dsmc_profile_enable(int enable);
+
+/* Synchronises the events recorded since dsmc_profile_enable(1) and returns, all HOST:
+ *   rowsum_ms        summed device time of the exp / tile-sum launches (ms)
+ *   rowsum_launches  their number
+ *   rowsum_pairs     pair exponentials they evaluated (sum over launches of merges * N^2)
+ *   all_launches     kernel launches of every kind made by the library. */
+dsmc_status_t dsmc_profile_read(double* rowsum_ms, int64_t* rowsum_launches, double* rowsum_pairs,
+                                int64_t* all_launches);
+
 /* ---- Inspection entry points used by the parity tests (same arithmetic as the path). */
 
 /* Philox4x32-10 of n counters: ctr DEVICE [n][4] uint32, out DEVICE [n][4] uint32. */
@@ -190,14 +205,15 @@ dsmc_status_t dsmc_debug_philox(const uint32_t* ctr, int64_t n, uint64_t seed, u
  *   logW   DEVICE [N][N] FP32 or NULL: log-weights log omega + logw_L + logw_R as the
  *          device evaluates them (per-row shift + ln2 * the base-2 exponent);
  *   r      DEVICE [N] FP32 or NULL: row weights of the row stage;
+ *   rowsum DEVICE [N] FP32 or NULL: row totals (the sums of each row's tile weights);
  *   tiles  DEVICE [N][n_tiles] FP32 or NULL: tile weights of the tile stage;
  *   e      DEVICE [N][N] FP32 or NULL: element weights of the column stage;
  *   ratio  DEVICE [N][N] FP32 or NULL: rejection acceptance ratios omega / omega-bar;
  *   info   HOST int[4] or NULL: {tile width B, n_tiles, combination id, left block leaf}. */
 dsmc_status_t dsmc_debug_merge_weights(const dsmc_config_t* cfg, const dsmc_model_t* model,
-                                       int level, int m, float* logW, float* r, float* tiles,
-                                       float* e, float* ratio, int info[4], void* ws,
-                                       size_t ws_bytes, void* stream);
+                                       int level, int m, float* logW, float* r, float* rowsum,
+                                       float* tiles, float* e, float* ratio, int info[4],
+                                       void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

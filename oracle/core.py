@@ -60,8 +60,8 @@ def _lib_handle():
             lib.orc_init.argtypes = [C.POINTER(Model), C.POINTER(Config), dp, dp, dp, dp, dp]
             lib.orc_smooth.argtypes = [C.POINTER(Model), C.POINTER(Config), dp, dp, dp, ip, dp, dp,
                                        dp, dp, dp, u64p]
-            lib.orc_logw_matrix.argtypes = [C.POINTER(Model), C.c_int, dp, C.c_int, C.c_int, dp, dp,
-                                            dp, dp, dp]
+            lib.orc_logw_matrix.argtypes = [C.POINTER(Model), C.c_int, dp, C.c_int, C.c_int, C.c_int,
+                                            dp, dp, dp, dp, dp]
             lib.orc_model_logdens.argtypes = [C.POINTER(Model), C.c_int, dp, C.c_int, dp, dp, dp]
             lib.orc_num_levels.argtypes = [C.c_int]
             lib.orc_merges_at_level.argtypes = [C.c_int, C.c_int]
@@ -69,8 +69,9 @@ def _lib_handle():
                                             C.c_uint32, C.c_int, C.c_int, ip, ip]
             lib.orc_rs_pairs.argtypes = [C.c_int, dp, C.c_double, C.c_uint32, C.c_uint32, C.c_uint32,
                                          C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip, u64p]
-            lib.orc_kp_dense_pairs.argtypes = [C.c_int, C.c_int, fp, fp, fp, C.c_uint32, C.c_uint32,
-                                               C.c_uint32, C.c_uint32, C.c_int, C.c_int, ip, ip]
+            lib.orc_kp_dense_pairs.argtypes = [C.c_int, C.c_int, fp, fp, fp, C.c_uint32,
+                                               C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, C.c_int,
+                                               ip, ip]
             lib.orc_kp_rs_pairs.argtypes = [C.c_int, fp, C.c_uint32, C.c_uint32, C.c_uint32,
                                             C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip, up]
             _lib = lib
@@ -204,10 +205,10 @@ def logw_matrix(model, y, K, c, xl, xr, wl, wr):
     xr = np.ascontiguousarray(xr, np.float64)
     wl = np.ascontiguousarray(wl, np.float64)
     wr = np.ascontiguousarray(wr, np.float64)
-    N = wl.shape[0]
-    out = np.zeros((N, N))
-    _check(lib.orc_logw_matrix(C.byref(keep.struct), K, _p(keep.y), c, N, _p(xl), _p(xr), _p(wl),
-                               _p(wr), _p(out)), "logw_matrix")
+    Nl, Nr = wl.shape[0], wr.shape[0]
+    out = np.zeros((Nl, Nr))
+    _check(lib.orc_logw_matrix(C.byref(keep.struct), K, _p(keep.y), c, Nl, Nr, _p(xl), _p(xr),
+                               _p(wl), _p(wr), _p(out)), "logw_matrix")
     return out
 
 
@@ -250,8 +251,9 @@ def rs_pairs(logW, logbar, seed, gid, n0, n1, max_attempts=1 << 20, counter_base
 
 
 def kp_dense_pairs(r, t, e, B, seed, gid, n0, n1, counter_base=0):
-    """Device-precision three-stage sampler (row / tile / column) on the device's own FP32
-    weights: r [N], t [N][nT], e [N][N]."""
+    """Device-precision three-stage sampler (row / tile / column, exact fixed point) on the
+    device's own FP32 weights: r [N] row weights, t [N][nT] tile weights, e [N][N] element
+    weights."""
     lib = _lib_handle()
     r = np.ascontiguousarray(r, np.float32)
     t = np.ascontiguousarray(t, np.float32)

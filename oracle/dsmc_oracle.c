@@ -690,17 +690,19 @@ done:
 /* log omega matrix for given particles (parity of the merge log-weights)                */
 /* ------------------------------------------------------------------------------------ */
 
-/* out[i][j] = log omega_c(xl_i, xr_j) + wl[i] + wr[j]  (FP64; Eq. normalized-weights). */
-int orc_logw_matrix(const orc_model* m, int K, const double* y, int c, int N, const double* xl,
-                    const double* xr, const double* wl, const double* wr, double* out) {
+/* out[i][j] = log omega_c(xl_i, xr_j) + wl[i] + wr[j]  (FP64; Eq. normalized-weights),
+ * for Nl left states and Nr right states. */
+int orc_logw_matrix(const orc_model* m, int K, const double* y, int c, int Nl, int Nr,
+                    const double* xl, const double* xr, const double* wl, const double* wr,
+                    double* out) {
   model_ctx mc;
   int st = ctx_init(&mc, m, K, y);
   if (st) return st;
   const int d = m->d;
 #pragma omp parallel for schedule(static)
-  for (int i = 0; i < N; ++i)
-    for (int j = 0; j < N; ++j)
-      out[(size_t)i * N + j] =
+  for (int i = 0; i < Nl; ++i)
+    for (int j = 0; j < Nr; ++j)
+      out[(size_t)i * Nr + j] =
           log_omega(&mc, c, xl + (size_t)i * d, xr + (size_t)j * d) + wl[i] + wr[j];
   return ORC_OK;
 }
@@ -725,17 +727,22 @@ int orc_model_logdens(const orc_model* m, int K, const double* y, int t, const d
 
 /* Three-stage inverse CDF: row, then 32..512-wide column tile, then column.
  * Inputs are the device's own FP32 weights, all relative to one shift per row:
- *   r[i]        row weight (relative to the largest row), in (0, 1]
+ *   r[i]        row weight (relative to the largest row), in [0, 1]
  *   t[i][k]     tile weight of row i, tile k (columns kB .. kB+B-1)
  *   e[i][j]     element weight (same per-row shift as t)
- * Decisions:
- *   row:    Rq_i = trunc(r_i * 2^40) (uint64, exact prefix sums); target
- *           T = floor(U * S / 2^64), U = (w0 << 32) | w1; row = #{i : cumRq_i <= T}
- *   tile:   FP32 sequential sum over k; tau = u23(w2) * total (FP32); first k whose
- *           running sum exceeds tau, else the last k with positive weight
- *   column: the same on e within the tile, with u23(w3)
- * Slots n in [n0, n1) use the counter (n, gid, DENSE | base<<4, 0).  A zero-weight entry is
- * never chosen. */
+ * Every decision is an exact integer computation on fixed-point images of these weights,
+ * so it does not depend on any summation order:
+ *   row:    Rq_i = trunc(r_i 2^40); T = floor(U S / 2^64), U = (w0 << 32) | w1, S = sum Rq;
+ *           row = #{i : Rq_0 + ... + Rq_i <= T}
+ *   tile:   q_k = q40(t_ik; max_k t_ik), T = floor(w2 Q / 2^32), Q = sum q;
+ *           tile = #{k : prefix <= T}
+ *   column: q_j = q40(e_ij; t_ik) over the tile's columns, the same with w3
+ * where q40(x; ref) = floor(x 2^(40 - E)) with 2^(E-2) <= ref < 2^(E-1) (one binade of
+ * headroom), computed on the bit patterns as (significand << 16) >> (E_ref - E_x) with the
+ * shift clamped to [0, 63] (the clamp at 0 saturates weights above twice their reference,
+ * which the device never produces); zero, negative, subnormal and non-finite x give 0.  A zero
+ * weight is never chosen; a tile whose column weights are all zero yields its first column.
+ * Slots n in [n0, n1) use the counter (n, gid, DENSE | base<<4, 0). */
 static uint64_t mulhi64(uint64_t a, uint64_t b) {
   unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
   return (uint64_t)(p >> 64);
@@ -747,53 +754,81 @@ static uint64_t row_quant(float r) {
   return (uint64_t)(r * 0x1p40f);
 }
 
-static int seq_pick(const float* v, int n, float u) {
-  float tot = 0.0f;
-  for (int k = 0; k < n; ++k) tot = tot + v[k];
-  float tau = u * tot;
-  float cum = 0.0f;
+static uint32_t float_bits(float x) {
+  uint32_t b;
+  memcpy(&b, &x, sizeof b);
+  return b;
+}
+
+/* biased exponent of the reference plus one binade of headroom */
+static int ref_exponent(float ref) {
+  uint32_t b = float_bits(ref);
+  int be = (int)((b >> 23) & 0xFFu);
+  return be + 1;
+}
+
+static uint64_t q40(float x, int ref_be) {
+  uint32_t b = float_bits(x);
+  if (b >> 31) return 0;
+  int be = (int)((b >> 23) & 0xFFu);
+  if (be == 0 || be == 0xFF) return 0;
+  uint64_t m = (uint64_t)((b & 0x7FFFFFu) | 0x800000u);
+  int r = ref_be - be;               /* >= 1 for every weight below its reference */
+  if (r < 0) r = 0;                  /* saturate (never reached by the device's weights) */
+  if (r > 63) r = 63;
+  return (m << 16) >> r;
+}
+
+/* index of the first prefix sum of q[0..n) exceeding floor(w Q / 2^32); 0 if all are zero */
+static int fixed_pick(const uint64_t* q, int n, uint32_t w) {
+  uint64_t Q = 0;
+  for (int k = 0; k < n; ++k) Q += q[k];
+  if (Q == 0) return 0;
+  uint64_t T = mulhi64((uint64_t)w << 32, Q);
+  uint64_t c = 0;
+  int idx = 0;
   for (int k = 0; k < n; ++k) {
-    cum = cum + v[k];
-    if (cum > tau) return k;
+    c += q[k];
+    if (c <= T) idx = k + 1;
   }
-  for (int k = n - 1; k > 0; --k)
-    if (v[k] > 0.0f) return k;
-  return 0;
+  return idx < n ? idx : n - 1;
 }
 
 int orc_kp_dense_pairs(int N, int B, const float* r, const float* t, const float* e,
-                       uint32_t seed_lo, uint32_t seed_hi, uint32_t base, uint32_t gid, int n0,
-                       int n1, int32_t* li, int32_t* ri) {
+                       uint32_t seed_lo, uint32_t seed_hi, uint32_t base,
+                       uint32_t gid, int n0, int n1, int32_t* li, int32_t* ri) {
   int nT = (N + B - 1) / B;
   uint64_t* cum = (uint64_t*)malloc(sizeof(uint64_t) * N);
-  if (!cum) return ORC_ERR_OOM;
+  uint64_t* q = (uint64_t*)malloc(sizeof(uint64_t) * (nT > B ? nT : B));
+  if (!cum || !q) { free(cum); free(q); return ORC_ERR_OOM; }
   uint64_t S = 0;
   for (int i = 0; i < N; ++i) {
     S += row_quant(r[i]);
     cum[i] = S;
   }
-  if (S == 0) { free(cum); return ORC_ERR_DEGENERATE; }
+  if (S == 0) { free(cum); free(q); return ORC_ERR_DEGENERATE; }
   for (int n = n0; n < n1; ++n) {
     uint32_t w[4];
     draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_DENSE, base, 0u, w);
     uint64_t U = ((uint64_t)w[0] << 32) | (uint64_t)w[1];
     uint64_t T = mulhi64(U, S);
-    int lo = 0, hi = N;
-    while (lo < hi) {
-      int mid = (lo + hi) / 2;
-      if (cum[mid] > T) hi = mid; else lo = mid + 1;
-    }
-    int i = lo;
-    float u2 = (float)u23(w[2]);
-    float u3 = (float)u23(w[3]);
-    int k = seq_pick(t + (size_t)i * nT, nT, u2);
+    int i = 0;
+    while (i < N - 1 && cum[i] <= T) ++i;
+    const float* ti = t + (size_t)i * nT;
+    float tmax = 0.0f;
+    for (int k = 0; k < nT; ++k) tmax = ti[k] > tmax ? ti[k] : tmax;
+    int rbe = ref_exponent(tmax);
+    for (int k = 0; k < nT; ++k) q[k] = q40(ti[k], rbe);
+    int k = fixed_pick(q, nT, w[2]);
     int j0 = k * B;
     int width = (j0 + B <= N) ? B : N - j0;
-    int j = j0 + seq_pick(e + (size_t)i * N + j0, width, u3);
+    int tbe = ref_exponent(ti[k]);
+    for (int j = 0; j < width; ++j) q[j] = q40(e[(size_t)i * N + j0 + j], tbe);
     li[n - n0] = i;
-    ri[n - n0] = j;
+    ri[n - n0] = j0 + fixed_pick(q, width, w[3]);
   }
   free(cum);
+  free(q);
   return ORC_OK;
 }
 

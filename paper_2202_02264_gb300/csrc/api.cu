@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "kernels.cuh"
 
@@ -18,6 +19,40 @@ using namespace dsmc;
 namespace {
 
 thread_local std::string g_last_error;
+
+// Per-thread measurement state: events around every exp / tile-sum launch, launch counts.
+struct Profile {
+  bool on = false;
+  std::vector<cudaEvent_t> start, stop;
+  size_t used = 0;
+  int64_t launches = 0;
+  double pairs = 0.0;
+};
+thread_local Profile g_prof;
+
+cudaError_t prof_begin(cudaStream_t s) {
+  if (!g_prof.on) return cudaSuccess;
+  if (g_prof.used == g_prof.start.size()) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return e;
+    g_prof.start.push_back(a);
+    g_prof.stop.push_back(b);
+  }
+  return cudaEventRecord(g_prof.start[g_prof.used], s);
+}
+
+cudaError_t prof_end(cudaStream_t s, double pairs) {
+  if (!g_prof.on) return cudaSuccess;
+  g_prof.pairs += pairs;
+  return cudaEventRecord(g_prof.stop[g_prof.used++], s);
+}
+
+void prof_count(int n) {
+  if (g_prof.on) g_prof.launches += n;
+}
 
 dsmc_status_t fail(dsmc_status_t st, const std::string& msg) {
   g_last_error = msg;
@@ -54,7 +89,7 @@ struct Plan {
   int R, rows_per_cta;
   bool dense;
   int level_off[33];
-  size_t o_status, o_U, o_alpha, o_V, o_beta, o_shift, o_logbar, o_inc, o_T, o_rw,
+  size_t o_status, o_U, o_alpha, o_V, o_beta, o_shift, o_logbar, o_inc, o_T, o_rw, o_rowsum, o_cum,
       o_delta, o_first, o_last, o_star, total;
 };
 
@@ -109,6 +144,8 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p) {
   p.o_inc = take((size_t)p.Mc * sizeof(double));
   p.o_T = take(p.dense ? MN * p.nTp * sizeof(float) : 0);
   p.o_rw = take(MN * sizeof(float));
+  p.o_rowsum = take(p.dense ? MN * sizeof(float) : 0);
+  p.o_cum = take(p.dense ? MN * sizeof(unsigned long long) : 0);
   p.o_delta = take(MN * sizeof(float));
   p.o_first = take(2 * (size_t)p.K * p.N * sizeof(int32_t));
   p.o_last = take(2 * (size_t)p.K * p.N * sizeof(int32_t));
@@ -129,6 +166,8 @@ WsPtrs ws_ptrs(const Plan& p, void* ws) {
   w.inc = reinterpret_cast<double*>(b + p.o_inc);
   w.T = reinterpret_cast<float*>(b + p.o_T);
   w.rw = reinterpret_cast<float*>(b + p.o_rw);
+  w.rowsum = reinterpret_cast<float*>(b + p.o_rowsum);
+  w.cum = reinterpret_cast<unsigned long long*>(b + p.o_cum);
   w.delta = reinterpret_cast<float*>(b + p.o_delta);
   w.first = reinterpret_cast<int32_t*>(b + p.o_first);
   w.last = reinterpret_cast<int32_t*>(b + p.o_last);
@@ -356,6 +395,7 @@ dsmc_status_t do_init(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& m
   a.logL = st->logL;
   a.status = w.status;
   DSMC_CUDA(launch_init(p.D, a, mp.bytes, s), "init kernel");
+  prof_count(1);
   return DSMC_OK;
 }
 
@@ -371,12 +411,16 @@ dsmc_status_t do_level(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& 
     chunking(p, a.mc, a.CH, a.CW);
     DSMC_CUDA(launch_prologue(p.D, a, mp.bytes, s), "prologue kernel");
     if (p.dense) {
-      DSMC_CUDA(launch_rowsum(p.D, a, s), "row-sum kernel");
+      DSMC_CUDA(prof_begin(s), "profile event");
+      DSMC_CUDA(launch_rowsum(p.D, a, s), "tile-sum kernel");
+      DSMC_CUDA(prof_end(s, (double)a.mc * p.N * p.N), "profile event");
       DSMC_CUDA(launch_sample_dense(p.D, a, s), "dense sampler kernel");
+      prof_count(3);
     } else {
       DSMC_CUDA(launch_sample_rs(p.D, a, s), "rejection sampler kernel");
+      DSMC_CUDA(launch_epilogue(a, s), "epilogue kernel");
+      prof_count(3);
     }
-    DSMC_CUDA(launch_epilogue(a, s), "epilogue kernel");
   }
   return DSMC_OK;
 }
@@ -400,6 +444,7 @@ dsmc_status_t do_resolve(const Plan& p, const dsmc_state_t* st, float* traj, dou
   g.x_star = x_star;
   g.status = w.status;
   DSMC_CUDA(launch_gather(p.D, g, s), "gather kernel");
+  prof_count(1);
   return DSMC_OK;
 }
 
@@ -434,7 +479,10 @@ dsmc_status_t run_smooth(const dsmc_config_t* cfg, const dsmc_model_t* model,
   DSMC_TRY(do_init(pr.p, cfg, pr.mp, y, x_ref_in, st, pr.w, s));
   for (int l = 0; l < pr.p.L; ++l) DSMC_TRY(do_level(pr.p, cfg, pr.mp, y, l, cond ? 1 : 0, st, pr.w, s));
   if (cond && pr.p.K == 1)
+  {
     DSMC_CUDA(launch_k1_star(st->logw, pr.p.N, cfg->seed, cfg->counter_base, pr.w.star, s), "star kernel");
+    prof_count(1);
+  }
   DSMC_TRY(do_resolve(pr.p, st, traj, mean, m2, cond ? x_ref_out : nullptr, pr.w, s));
   if (logL_out)
     DSMC_CUDA(cudaMemcpyAsync(logL_out, st->logL, sizeof(double), cudaMemcpyDeviceToDevice, s), "logL copy");
@@ -551,6 +599,30 @@ dsmc_status_t dsmc_stream_status(void* ws, void* stream, dsmc_status_t* device_s
   return DSMC_OK;
 }
 
+dsmc_status_t dsmc_profile_enable(int enable) {
+  g_prof.on = enable != 0;
+  g_prof.used = 0;
+  g_prof.launches = 0;
+  g_prof.pairs = 0.0;
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_profile_read(double* rowsum_ms, int64_t* rowsum_launches, double* rowsum_pairs,
+                                int64_t* all_launches) {
+  double ms = 0.0;
+  for (size_t i = 0; i < g_prof.used; ++i) {
+    DSMC_CUDA(cudaEventSynchronize(g_prof.stop[i]), "profile synchronize");
+    float t = 0.f;
+    DSMC_CUDA(cudaEventElapsedTime(&t, g_prof.start[i], g_prof.stop[i]), "profile elapsed");
+    ms += t;
+  }
+  if (rowsum_ms) *rowsum_ms = ms;
+  if (rowsum_launches) *rowsum_launches = (int64_t)g_prof.used;
+  if (rowsum_pairs) *rowsum_pairs = g_prof.pairs;
+  if (all_launches) *all_launches = g_prof.launches;
+  return DSMC_OK;
+}
+
 dsmc_status_t dsmc_debug_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
                                 void* stream) {
   if (n < 0 || (n > 0 && (!ctr || !out))) return fail(DSMC_ERR_INVALID_ARG, "philox buffers");
@@ -559,9 +631,9 @@ dsmc_status_t dsmc_debug_philox(const uint32_t* ctr, int64_t n, uint64_t seed, u
 }
 
 dsmc_status_t dsmc_debug_merge_weights(const dsmc_config_t* cfg, const dsmc_model_t* model,
-                                       int level, int m, float* logW, float* r, float* tiles,
-                                       float* e, float* ratio, int info[4], void* ws,
-                                       size_t ws_bytes, void* stream) {
+                                       int level, int m, float* logW, float* r, float* rowsum,
+                                       float* tiles, float* e, float* ratio, int info[4],
+                                       void* ws, size_t ws_bytes, void* stream) {
   Prepared pr;
   DSMC_TRY(prepare(cfg, model, nullptr, ws, ws_bytes, pr));
   const Plan& p = pr.p;
@@ -570,7 +642,8 @@ dsmc_status_t dsmc_debug_merge_weights(const dsmc_config_t* cfg, const dsmc_mode
   if (m < 0 || m >= M) return fail(DSMC_ERR_INVALID_ARG, "combination out of range");
   const int last_chunk = ((M - 1) / p.Mc) * p.Mc;
   if (m < last_chunk) return fail(DSMC_ERR_INVALID_ARG, "combination not in the last launch chunk");
-  if (!p.dense && (r || tiles)) return fail(DSMC_ERR_INVALID_ARG, "row/tile weights exist only with dense resampling");
+  if (!p.dense && (r || rowsum || tiles))
+    return fail(DSMC_ERR_INVALID_ARG, "row/tile weights exist only with dense resampling");
   dsmc_state_t dummy = {nullptr, nullptr, nullptr, nullptr};
   MergeArgs a = merge_args(p, cfg, nullptr, level, 0, &dummy, pr.w);
   a.m0 = last_chunk;
@@ -582,7 +655,7 @@ dsmc_status_t dsmc_debug_merge_weights(const dsmc_config_t* cfg, const dsmc_mode
     info[2] = p.level_off[level] + m;
     info[3] = level == 0 ? 1 : 0;
   }
-  DSMC_CUDA(launch_debug_weights(p.D, a, m - last_chunk, logW, r, tiles, e, ratio,
+  DSMC_CUDA(launch_debug_weights(p.D, a, m - last_chunk, logW, r, rowsum, tiles, e, ratio,
                                  static_cast<cudaStream_t>(stream)), "inspection kernel");
   return DSMC_OK;
 }

@@ -44,25 +44,37 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(GatherArgs a) {
 #pragma unroll
   for (int k = 0; k < D; ++k) s1[k] = s2[k] = 0.f;
   bool corrupt = false;
-  for (int n = threadIdx.x; n < N; n += kGatherThreads) {
-    int sidx = n;
-    for (int q = 0; q < np; ++q)
-      sidx = checked_index(a.pairs[((size_t)path_g[q] * 2 + path_side[q]) * N + sidx], N, corrupt);
-    const float* xp = Xt + (size_t)sidx * d;
-    const float w = weighted ? expf(a.logw[n]) : 1.f;
-    float x[D];
+  // four independent walks per thread keep several dependent loads in flight
+  constexpr int W = 4;
+  for (int n0 = threadIdx.x; n0 < N; n0 += W * kGatherThreads) {
+    int sidx[W];
 #pragma unroll
-    for (int k = 0; k < D; ++k) x[k] = k < d ? xp[k] : 0.f;
-    if (a.traj) {
-      float* o = a.traj + ((size_t)t * N + n) * d;
+    for (int q = 0; q < W; ++q) sidx[q] = min(n0 + q * kGatherThreads, N - 1);
+    for (int p = 0; p < np; ++p) {
+      const int32_t* pp = a.pairs + ((size_t)path_g[p] * 2 + path_side[p]) * N;
 #pragma unroll
-      for (int k = 0; k < D; ++k)
-        if (k < d) o[k] = x[k];
+      for (int q = 0; q < W; ++q) sidx[q] = checked_index(pp[sidx[q]], N, corrupt);
     }
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      s1[k] = fmaf(w, x[k], s1[k]);
-      s2[k] = fmaf(w * x[k], x[k], s2[k]);
+    for (int q = 0; q < W; ++q) {
+      const int n = n0 + q * kGatherThreads;
+      if (n >= N) continue;
+      const float* xp = Xt + (size_t)sidx[q] * d;
+      const float w = weighted ? expf(a.logw[n]) : 1.f;
+      float x[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) x[k] = k < d ? xp[k] : 0.f;
+      if (a.traj) {
+        float* o = a.traj + ((size_t)t * N + n) * d;
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          if (k < d) o[k] = x[k];
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        s1[k] = fmaf(w, x[k], s1[k]);
+        s2[k] = fmaf(w * x[k], x[k], s2[k]);
+      }
     }
   }
   if (corrupt) record_status(a.status, DSMC_ERR_INVALID_ARG);

@@ -20,6 +20,8 @@ struct WsPtrs {
   double* logbar;    // [Mc]         log omega-bar, bound of the whole N x N matrix
   float* T;          // [Mc][N][nTp] tile weights, relative to the row shift
   float* rw;         // [Mc][N]      row weights of the row stage
+  float* rowsum;     // [Mc][N]      row totals (sums of the tile weights)
+  unsigned long long* cum;  // [Mc][N] exact 2^40 fixed-point prefix sums of the row weights
   float* delta;      // [Mc][N]      extra base-2 shift of rows recomputed after underflow
   int32_t* first;    // [2][K][N]    first-time particle index of each block (double-buffered)
   int32_t* last;     // [2][K][N]    last-time particle index of each block
@@ -85,7 +87,8 @@ cudaError_t launch_sample_rs(int D, const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_epilogue(const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_gather(int D, const GatherArgs& a, cudaStream_t s);
 cudaError_t launch_debug_weights(int D, const MergeArgs& a, int s_local, float* logW, float* r,
-                                 float* tiles, float* e, float* ratio, cudaStream_t s);
+                                 float* rowsum, float* tiles, float* e, float* ratio,
+                                 cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
                           cudaStream_t s);
 

@@ -17,6 +17,7 @@
 // 2^x on MUFU and keeps per-row and per-tile (32..512 columns) sums.  The sampler draws
 // each pair in three inverse-CDF stages (row, tile, column), recomputing only the
 // chosen tile's columns.
+#include <algorithm>
 #include <cfloat>
 
 #include "kernels.cuh"
@@ -25,8 +26,6 @@ namespace dsmc {
 
 namespace {
 
-constexpr int kProThreads = 256;
-constexpr int kSampThreads = 512;
 constexpr int kEpiThreads = 256;
 constexpr int kRsThreads = 128;
 
@@ -60,7 +59,13 @@ __device__ __forceinline__ T warp_max(T v) {
 // One CTA per combination.
 // ---------------------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(kProThreads) prologue_kernel(MergeArgs a, ModelParams<D> mp) {
+__host__ __device__ constexpr int prologue_threads() {
+  return D <= 8 ? 512 : 256;
+}
+
+template <int D>
+__global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeArgs a, ModelParams<D> mp) {
+  constexpr int kProThreads = prologue_threads<D>();
   constexpr int NW = kProThreads / 32;
   const int s = blockIdx.x;
   const int m = a.m0 + s;
@@ -286,23 +291,6 @@ __global__ void __launch_bounds__(128) rowsum_kernel(MergeArgs a, int SC) {
   }
 }
 
-// Sequential inverse-CDF pick over n FP32 weights: the first k whose running sum exceeds
-// u * total, else the last positive weight (a zero weight is never chosen).
-__device__ __forceinline__ int seq_pick_global(const float* w, int n, float u) {
-  float tot = 0.f;
-  for (int k = 0; k < n; ++k) tot = __fadd_rn(tot, w[k]);
-  const float tau = __fmul_rn(u, tot);
-  float cum = 0.f;
-  int last_pos = 0;
-  for (int k = 0; k < n; ++k) {
-    const float x = w[k];
-    cum = __fadd_rn(cum, x);
-    if (cum > tau) return k;
-    if (x > 0.f) last_pos = k;
-  }
-  return last_pos;
-}
-
 // Block-wide inclusive scan of N uint64 values in shared memory (in place).
 __device__ void block_scan_u64(unsigned long long* v, int N, unsigned long long* warp_tot) {
   const int NT = blockDim.x;
@@ -336,9 +324,9 @@ __device__ void block_scan_u64(unsigned long long* v, int N, unsigned long long*
   __syncthreads();
 }
 
-// Exact-max recomputation of one row (rare: used when the bound-shifted row sum fell
+// Exact-max recomputation of one row (rare: used when the bound-shifted row total fell
 // below 2^-64).  One warp; writes the row's tile sums relative to the new shift, returns
-// the row sum and the extra base-2 shift.
+// the row total (lane-local sums, then a butterfly) and the extra base-2 shift.
 template <int D>
 __device__ void recompute_row(const MergeArgs& a, int s, int i, float* out_sum, float* out_delta) {
   const int N = a.N, B = a.B;
@@ -369,63 +357,101 @@ __device__ void recompute_row(const MergeArgs& a, int s, int i, float* out_sum, 
   *out_delta = mx;
 }
 
+// The fixed-point image floor(x 2^(40 - E)) of a weight x below twice its reference
+// (2^(E-2) <= ref < 2^(E-1), ref_be = the reference's biased exponent + 1):
+// (significand << 16) >> (ref_be - be), the shift clamped to [0, 63].  Exact, order-free and
+// branch-free; zero, negative, subnormal and non-finite x give 0.
+__device__ __forceinline__ unsigned long long q40(float x, int ref_be) {
+  const uint32_t b = __float_as_uint(x);
+  const int be = (int)((b >> 23) & 0xFFu);
+  const bool zero = (b >> 31) || be == 0 || be == 0xFF;
+  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u) << 16;
+  const int r = min(max(ref_be - be, 0), 63);
+  return zero ? 0ull : (m >> r);
+}
+
+__device__ __forceinline__ int ref_exponent(float ref) {
+  return (int)((__float_as_uint(ref) >> 23) & 0xFFu) + 1;
+}
+
+// Sum of a row's tile weights in ascending tile order (vector loads).
+__device__ __forceinline__ float row_total(const float* row, int nT, int nTp) {
+  const float4* t4 = reinterpret_cast<const float4*>(row);
+  float t = 0.f;
+  for (int k4 = 0; k4 < nTp / 4; ++k4) {
+    const float4 v = t4[k4];
+    const int k = 4 * k4;
+    if (k < nT) t = __fadd_rn(t, v.x);
+    if (k + 1 < nT) t = __fadd_rn(t, v.y);
+    if (k + 2 < nT) t = __fadd_rn(t, v.z);
+    if (k + 3 < nT) t = __fadd_rn(t, v.w);
+  }
+  return t;
+}
+
 // ---------------------------------------------------------------------------------------
-// Dense sampler: N pair draws of one combination (one CTA per combination).
-//   row:    fixed-point 2^40 row weights, exact uint64 prefix sums, T = U64 * S >> 64;
-//   tile:   sequential FP32 inverse CDF over the row's tile weights;
-//   column: the chosen tile's columns recomputed (pair_exponent + ex2), sequential FP32.
-// Also the log normalising-constant increment (Eq. Lab) in FP64.
+// Row CDF of one combination (one CTA):
+//   row totals s_i = sum of the row's tile weights in ascending tile order (thread per row,
+//   independent vector loads; no result depends on how the tile-sum kernel chunked the
+//   columns); a row whose total fell below 2^-64 of its bound is recomputed with its exact
+//   maximum as shift (rare; tiles rewritten, extra base-2 shift kept in delta);
+//   row weights r_i = 2^(l_i - max l) in FP32 with l_i = shift_i log2(e) + delta_i + log2 s_i;
+//   their exact 2^40 fixed-point prefix sums (the row stage of the sampler);
+//   the FP64 log normalising-constant increment of Eq. (Lab) and log L_{a:b}.
 // ---------------------------------------------------------------------------------------
+constexpr int kCdfThreads = 512;
+
 template <int D>
-__global__ void __launch_bounds__(kSampThreads) sample_dense_kernel(MergeArgs a) {
-  constexpr int NW = kSampThreads / 32;
+__global__ void __launch_bounds__(kCdfThreads) rowcdf_kernel(MergeArgs a) {
+  constexpr int NW = kCdfThreads / 32;
   const int s = blockIdx.x;
-  const int gid = a.gid0 + s;
-  const int N = a.N, B = a.B, nT = a.nT;
+  const int N = a.N, nT = a.nT, nTp = a.nTp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  extern __shared__ unsigned long long smu[];
-  unsigned long long* cum = smu;                        // [N]
-  float* l2 = reinterpret_cast<float*>(smu + N);        // [N]
+  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned long long* cum = reinterpret_cast<unsigned long long*>(smraw);      // [N]
+  float* l2 = reinterpret_cast<float*>(smraw + (size_t)N * 8);                 // [N]
+  int* under = reinterpret_cast<int*>(cum);  // rows that underflowed (before cum is built)
   __shared__ unsigned long long warp_tot[NW];
   __shared__ double redd[NW];
-  __shared__ int n_under;
-  __shared__ double M_s, inc_s;
-  __shared__ unsigned long long S_s;
-
-  if (threadIdx.x == 0) n_under = 0;
+  __shared__ double M_s;
+  __shared__ int n_under, nonfinite_s;
+  if (threadIdx.x == 0) {
+    n_under = 0;
+    nonfinite_s = 0;
+  }
   __syncthreads();
-  int* under = reinterpret_cast<int*>(cum);  // list of underflowed rows (cum unused yet)
+  const float* Tt = a.ws.T + (size_t)s * N * nTp;
   const double* shift = a.ws.shift + (size_t)s * N;
   float* delta = a.ws.delta + (size_t)s * N;
-  const float* Tt0 = a.ws.T + (size_t)s * N * a.nTp;
-  bool nonfinite = false;
-  for (int i = threadIdx.x; i < N; i += kSampThreads) {
-    float si = 0.f;
-    for (int k = 0; k < nT; ++k) si = __fadd_rn(si, Tt0[(size_t)i * a.nTp + k]);
-    if (isnan(si)) {
-      nonfinite = true;
-      si = 0.f;
+  float* rowsum = a.ws.rowsum + (size_t)s * N;
+  for (int i = threadIdx.x; i < N; i += kCdfThreads) {
+    float t = row_total(Tt + (size_t)i * nTp, nT, nTp);
+    if (isnan(t)) {
+      nonfinite_s = 1;
+      t = 0.f;
     }
+    l2[i] = t;
     delta[i] = 0.f;
-    l2[i] = si;
-    if (si < 0x1p-64f) under[atomicAdd(&n_under, 1)] = i;
+    if (t < 0x1p-64f) under[atomicAdd(&n_under, 1)] = i;
   }
   __syncthreads();
   for (int q = warp; q < n_under; q += NW) {
     const int i = under[q];
     float si, dl;
     recompute_row<D>(a, s, i, &si, &dl);
+    __syncwarp();
     if (lane == 0) {
-      l2[i] = si;
+      si = row_total(Tt + (size_t)i * nTp, nT, nTp);
+      l2[i] = isnan(si) ? 0.f : si;
       delta[i] = dl;
     }
   }
   __syncthreads();
-  // base-2 log of every row's total relative to one global shift
   double mloc = -INFINITY;
-  for (int i = threadIdx.x; i < N; i += kSampThreads) {
-    const float si = l2[i];
-    const float v = si > 0.f ? (float)(shift[i] * kLog2ed + (double)delta[i] + (double)log2f(si)) : -INFINITY;
+  for (int i = threadIdx.x; i < N; i += kCdfThreads) {
+    const float t = l2[i];
+    rowsum[i] = t;
+    const float v = t > 0.f ? (float)(shift[i] * kLog2ed + (double)delta[i] + (double)log2f(t)) : -INFINITY;
     l2[i] = v;
     mloc = fmax(mloc, (double)v);
   }
@@ -442,7 +468,7 @@ __global__ void __launch_bounds__(kSampThreads) sample_dense_kernel(MergeArgs a)
   const bool degenerate = !(M > -INFINITY) || isnan(M);
   float* rw = a.ws.rw + (size_t)s * N;
   double sr = 0.0;
-  for (int i = threadIdx.x; i < N; i += kSampThreads) {
+  for (int i = threadIdx.x; i < N; i += kCdfThreads) {
     float r = degenerate ? 0.f : ex2(__fsub_rn(l2[i], (float)M));
     if (!(r > 0.f)) r = 0.f;
     if (r > 1.f) r = 1.f;
@@ -454,79 +480,216 @@ __global__ void __launch_bounds__(kSampThreads) sample_dense_kernel(MergeArgs a)
   sr = warp_sum(sr);
   if (lane == 0) redd[warp] = sr;
   block_scan_u64(cum, N, warp_tot);
+  unsigned long long* gcum = a.ws.cum + (size_t)s * N;
+  for (int i = threadIdx.x; i < N; i += kCdfThreads) gcum[i] = cum[i];
   if (threadIdx.x == 0) {
+    int at, c, b;
+    merge_geom(a.K, a.level, a.m0 + s, at, c, b);
     double t = 0.0;
     for (int w = 0; w < NW; ++w) t += redd[w];
-    inc_s = degenerate ? (double)NAN : M * kLn2d + log(t);
-    S_s = cum[N - 1];
-    a.ws.inc[s] = inc_s;
+    const double inc = degenerate ? (double)NAN : M * kLn2d + log(t);
+    a.ws.inc[s] = inc;
+    a.logL[at] = a.logL[at] + a.logL[c] + inc;
+    if (degenerate || cum[N - 1] == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
+    if (nonfinite_s) record_status(a.ws.status, DSMC_ERR_NONFINITE);
   }
-  __syncthreads();
-  const unsigned long long S = S_s;
-  if (threadIdx.x == 0 && (degenerate || S == 0ull))
-    record_status(a.ws.status, DSMC_ERR_DEGENERATE);
-  if (nonfinite) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+}
 
-  const float* U = a.ws.U + (size_t)s * N * D;
-  const float* alpha = a.ws.alpha + (size_t)s * N;
-  const float* V = a.ws.V + (size_t)s * N * D;
-  const float* beta = a.ws.beta + (size_t)s * N;
-  const float* Tt = a.ws.T + (size_t)s * N * a.nTp;
+// Fixed-point pick over n <= 32 weights held in registers: q_k = q40(x_k; ref), Q = sum q,
+// T = w Q >> 32 (w a 32-bit uniform word), the first k whose prefix sum exceeds T.  The
+// images are recomputed in the second pass (cheap) rather than kept (64 registers).
+__device__ __forceinline__ int pick_regs(const float* x, int n, uint32_t w, int ref_be) {
+  unsigned long long Q = 0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) Q += (k < n) ? q40(x[k], ref_be) : 0ull;
+  if (Q == 0ull) return 0;
+  const unsigned long long T = __umul64hi((unsigned long long)w << 32, Q);
+  unsigned long long c = 0;
+  int idx = 0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    c += (k < n) ? q40(x[k], ref_be) : 0ull;
+    idx += (c <= T) ? 1 : 0;
+  }
+  return min(idx, n - 1);
+}
+
+// D floats of a row of U or V into registers (vector loads when D is a multiple of 4; the
+// rows are then 16-byte aligned).
+template <int D>
+__device__ __forceinline__ void load_row(const float* p, float* r) {
+  if ((D % 4) == 0) {
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < D / 4; ++k) {
+      const float4 v = p4[k];
+      r[4 * k] = v.x;
+      r[4 * k + 1] = v.y;
+      r[4 * k + 2] = v.z;
+      r[4 * k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) r[k] = p[k];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Pair draws (one thread per slot, many small CTAs per combination):
+//   row:    T = U64 * S >> 64 against the exact prefix sums (binary search, L1-cached);
+//   tile:   fixed-point tile weights of the row (reference: its largest tile), T = w2 Q >> 32;
+//   column: the chosen tile's columns recomputed (pair_exponent + ex2), fixed point
+//           (reference: the tile weight t_ik), w3;
+// then the pair and the new block's first / last index maps (the composition of the
+// Remark in Section 3.1) into the other map buffer.  REG = 1 keeps the row's tiles and the
+// tile's exponentials in registers (nT <= 32 and B = 32, i.e. N <= 1024).
+// ---------------------------------------------------------------------------------------
+constexpr int kSlotThreads = 128;
+
+template <int D, int REG>
+__global__ void __launch_bounds__(kSlotThreads) slots_kernel(MergeArgs a, int cum_in_smem) {
+  const int s = blockIdx.x;
+  const int gid = a.gid0 + s;
+  const int N = a.N, B = a.B, nT = a.nT, nTp = a.nTp;
+  // the row prefix sums: copied to shared memory in one round trip when they fit
+  extern __shared__ unsigned long long scum[];
+  const unsigned long long* gcum = a.ws.cum + (size_t)s * N;
+  if (cum_in_smem) {
+    for (int q = threadIdx.x; q < N; q += kSlotThreads) scum[q] = gcum[q];
+    __syncthreads();
+    gcum = scum;
+  }
+  const float* Tt = a.ws.T + (size_t)s * N * nTp;
+  int at, c, b;
+  merge_geom(a.K, a.level, a.m0 + s, at, c, b);
   int32_t* pl = a.pairs + (size_t)gid * 2 * N;
   int32_t* pr = pl + N;
   const int n_lo = a.conditional ? 1 : 0;
   const int n_hi = N + ((a.conditional && a.root) ? 1 : 0);
-  if (a.conditional && threadIdx.x == 0) {
+  const bool left_leaf = (a.level == 0);
+  const int sR = b - c + 1;
+  const bool right_leaf = (sR == 1);
+  const int bufL = a.level & 1, bufR = ceil_log2(sR) & 1, bufO = (a.level + 1) & 1;
+  int32_t* first_out = a.ws.first + ((size_t)bufO * a.K + at) * N;
+  int32_t* last_out = a.ws.last + ((size_t)bufO * a.K + at) * N;
+  const int32_t* first_L = a.ws.first + ((size_t)bufL * a.K + at) * N;
+  const int32_t* last_R = a.ws.last + ((size_t)bufR * a.K + c) * N;
+  if (a.conditional && blockIdx.y == 0 && threadIdx.x == 0) {
     pl[0] = 0;
     pr[0] = 0;
+    first_out[0] = left_leaf ? 0 : first_L[0];
+    last_out[0] = right_leaf ? 0 : last_R[0];
   }
-  for (int n = n_lo + threadIdx.x; n < n_hi; n += kSampThreads) {
-    int i = 0, j = 0;
-    if (!(degenerate || S == 0ull)) {
-      const uint4 w = draw(a.seed, (uint32_t)n, (uint32_t)gid, kPurposeDense, a.base, 0u);
-      const unsigned long long Uw = ((unsigned long long)w.x << 32) | (unsigned long long)w.y;
-      const unsigned long long Tg = __umul64hi(Uw, S);
-      int lo = 0, hi = N;  // first i with cum[i] > Tg
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (cum[mid] > Tg) hi = mid; else lo = mid + 1;
-      }
-      i = min(lo, N - 1);
-      const int kt = seq_pick_global(Tt + (size_t)i * a.nTp, nT, u23(w.z));
-      // column stage: recompute the tile's exponents
-      float u[D];
+  const int n = n_lo + blockIdx.y * kSlotThreads + threadIdx.x;
+  if (n >= n_hi) return;
+  const unsigned long long S = gcum[N - 1];
+  int i, j;
+  if (S == 0ull) {
+    i = n % N;
+    j = n % N;
+  } else {
+    const uint4 w = draw(a.seed, (uint32_t)n, (uint32_t)gid, kPurposeDense, a.base, 0u);
+    const unsigned long long Uw = ((unsigned long long)w.x << 32) | (unsigned long long)w.y;
+    const unsigned long long Tg = __umul64hi(Uw, S);
+    int lo = 0, hi = N - 1;  // first i with cum[i] > Tg (cum[N-1] = S > Tg)
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (gcum[mid] > Tg) hi = mid; else lo = mid + 1;
+    }
+    i = lo;
+    const float* Ti = Tt + (size_t)i * nTp;
+    const float4* Ti4 = reinterpret_cast<const float4*>(Ti);
+    float u[D];
+    load_row<D>(a.ws.U + ((size_t)s * N + i) * D, u);
+    const float al = __fsub_rn(a.ws.alpha[(size_t)s * N + i], a.ws.delta[(size_t)s * N + i]);
+    const float* V = a.ws.V + (size_t)s * N * D;
+    const float* beta = a.ws.beta + (size_t)s * N;
+    int kt;
+    if (REG) {
+      float t[32];
 #pragma unroll
-      for (int k = 0; k < D; ++k) u[k] = U[(size_t)i * D + k];
-      const float al = __fsub_rn(alpha[i], delta[i]);
-      const int jb = kt * B, je = min(jb + B, N);
-      float tot = 0.f;
-      for (int jj = jb; jj < je; ++jj)
-        tot = __fadd_rn(tot, ex2(pair_exponent<D>(u, al, V + (size_t)jj * D, beta[jj])));
-      const float tau = __fmul_rn(u23(w.w), tot);
-      float cumc = 0.f;
-      j = -1;
-      int last_pos = jb;
-      for (int jj = jb; jj < je; ++jj) {
-        const float e = ex2(pair_exponent<D>(u, al, V + (size_t)jj * D, beta[jj]));
-        cumc = __fadd_rn(cumc, e);
-        if (e > 0.f) last_pos = jj;
-        if (cumc > tau) {
-          j = jj;
-          break;
-        }
+      for (int k4 = 0; k4 < 8; ++k4) {
+        const float4 v = (4 * k4 < nTp) ? Ti4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        t[4 * k4] = v.x;
+        t[4 * k4 + 1] = v.y;
+        t[4 * k4 + 2] = v.z;
+        t[4 * k4 + 3] = v.w;
       }
-      if (j < 0) j = last_pos;
+      float tmax = 0.f;
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (k < nT) tmax = fmaxf(tmax, t[k]);
+      kt = pick_regs(t, nT, w.z, ref_exponent(tmax));
     } else {
-      i = n % N;
-      j = n % N;
+      float tmax = 0.f;
+      for (int k = 0; k < nT; ++k) tmax = fmaxf(tmax, Ti[k]);
+      const int rbe = ref_exponent(tmax);
+      unsigned long long Q = 0;
+      for (int k = 0; k < nT; ++k) Q += q40(Ti[k], rbe);
+      kt = 0;
+      if (Q != 0ull) {
+        const unsigned long long Tq = __umul64hi((unsigned long long)w.z << 32, Q);
+        unsigned long long cc = 0;
+        for (int k = 0; k < nT; ++k) {
+          cc += q40(Ti[k], rbe);
+          kt += (cc <= Tq) ? 1 : 0;
+        }
+        kt = min(kt, nT - 1);
+      }
     }
-    if (n < N) {
-      pl[n] = i;
-      pr[n] = j;
+    const int tbe = ref_exponent(Ti[kt]);
+    const int jb = kt * B, je = min(jb + B, N);
+    if (REG) {
+      // the tile's 32 columns: beta as 8 vector loads, each v_j as D/4 vector loads
+      float bt[32], e[32];
+      // vector loads only when the tile is full and its beta run is 16-byte aligned (the
+      // per-combination stride N need not be a multiple of 4)
+      if (je - jb == 32 && ((reinterpret_cast<uintptr_t>(beta + jb) & 15u) == 0)) {
+        const float4* b4 = reinterpret_cast<const float4*>(beta + jb);
+#pragma unroll
+        for (int q4 = 0; q4 < 8; ++q4) {
+          const float4 v = b4[q4];
+          bt[4 * q4] = v.x;
+          bt[4 * q4 + 1] = v.y;
+          bt[4 * q4 + 2] = v.z;
+          bt[4 * q4 + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) bt[q] = beta[min(jb + q, N - 1)];
+      }
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        float v[D];
+        load_row<D>(V + (size_t)min(jb + q, N - 1) * D, v);
+        e[q] = (jb + q < je) ? ex2(pair_exponent<D>(u, al, v, bt[q])) : 0.f;
+      }
+      j = jb + pick_regs(e, je - jb, w.w, tbe);
     } else {
-      a.ws.star[0] = i;
-      a.ws.star[1] = j;
+      unsigned long long Qc = 0;
+      for (int jj = jb; jj < je; ++jj)
+        Qc += q40(ex2(pair_exponent<D>(u, al, V + (size_t)jj * D, beta[jj])), tbe);
+      j = jb;
+      if (Qc != 0ull) {
+        const unsigned long long Tc = __umul64hi((unsigned long long)w.w << 32, Qc);
+        unsigned long long cc = 0;
+        int cnt = 0;
+        for (int jj = jb; jj < je; ++jj) {
+          cc += q40(ex2(pair_exponent<D>(u, al, V + (size_t)jj * D, beta[jj])), tbe);
+          cnt += (cc <= Tc) ? 1 : 0;
+        }
+        j = jb + min(cnt, je - jb - 1);
+      }
     }
+  }
+  if (n < N) {
+    pl[n] = i;
+    pr[n] = j;
+    first_out[n] = left_leaf ? i : first_L[i];
+    last_out[n] = right_leaf ? j : last_R[j];
+  } else {
+    a.ws.star[0] = i;
+    a.ws.star[1] = j;
   }
 }
 
@@ -626,8 +789,8 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(MergeArgs a) {
 // Inspection: the device's own weights of one combination, for the parity tests.
 // ---------------------------------------------------------------------------------------
 template <int D>
-__global__ void debug_weights_kernel(MergeArgs a, int s, float* logW, float* r, float* tiles,
-                                     float* e, float* ratio) {
+__global__ void debug_weights_kernel(MergeArgs a, int s, float* logW, float* r, float* rowsum,
+                                     float* tiles, float* e, float* ratio) {
   const int i = blockIdx.x;
   const int N = a.N;
   const float* U = a.ws.U + (size_t)s * N * D;
@@ -648,6 +811,7 @@ __global__ void debug_weights_kernel(MergeArgs a, int s, float* logW, float* r, 
     if (ratio) ratio[(size_t)i * N + j] = rs_ratio<D>(a, s, i, j, logbar);
   }
   if (threadIdx.x == 0 && r) r[i] = a.ws.rw[(size_t)s * N + i];
+  if (threadIdx.x == 0 && rowsum) rowsum[i] = a.ws.rowsum[(size_t)s * N + i];
   if (tiles)
     for (int k = threadIdx.x; k < a.nT; k += blockDim.x)
       tiles[(size_t)i * a.nT + k] = a.ws.T[((size_t)s * N + i) * a.nTp + k];
@@ -656,12 +820,12 @@ __global__ void debug_weights_kernel(MergeArgs a, int s, float* logW, float* r, 
 // ------------------------------------------------------------------- launch wrappers
 template <int D>
 cudaError_t prologue_t(const MergeArgs& a, const void* mp, cudaStream_t st) {
-  prologue_kernel<D><<<a.mc, kProThreads, 0, st>>>(a, *static_cast<const ModelParams<D>*>(mp));
+  prologue_kernel<D><<<a.mc, prologue_threads<D>(), 0, st>>>(a, *static_cast<const ModelParams<D>*>(mp));
   return cudaGetLastError();
 }
 
 template <int D>
-constexpr int rows_per_thread() {
+__host__ __device__ constexpr int rows_per_thread() {
   return D <= 8 ? 4 : (D <= 16 ? 2 : 1);
 }
 
@@ -679,12 +843,22 @@ cudaError_t rowsum_t(const MergeArgs& a, cudaStream_t st) {
 template <int D>
 cudaError_t sample_dense_t(const MergeArgs& a, cudaStream_t st) {
   const size_t smem = (size_t)a.N * (sizeof(unsigned long long) + sizeof(float));
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(sample_dense_kernel<D>,
+  if (smem > 40 * 1024) {  // static shared memory counts against the 48 KB default
+    cudaError_t e = cudaFuncSetAttribute(rowcdf_kernel<D>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  sample_dense_kernel<D><<<a.mc, kSampThreads, smem, st>>>(a);
+  rowcdf_kernel<D><<<a.mc, kCdfThreads, smem, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int slots = a.N + ((a.conditional && a.root) ? 1 : 0) - (a.conditional ? 1 : 0);
+  dim3 grid(a.mc, (slots + kSlotThreads - 1) / kSlotThreads);
+  const int cum_in_smem = a.N <= 4096 ? 1 : 0;   // <= 32 KB: several CTAs per SM
+  const size_t smem_slot = cum_in_smem ? (size_t)a.N * sizeof(unsigned long long) : 0;
+  if (a.nT <= 32 && a.B == 32)
+    slots_kernel<D, 1><<<grid, kSlotThreads, smem_slot, st>>>(a, cum_in_smem);
+  else
+    slots_kernel<D, 0><<<grid, kSlotThreads, smem_slot, st>>>(a, cum_in_smem);
   return cudaGetLastError();
 }
 
@@ -697,9 +871,9 @@ cudaError_t sample_rs_t(const MergeArgs& a, cudaStream_t st) {
 }
 
 template <int D>
-cudaError_t debug_t(const MergeArgs& a, int s, float* logW, float* r, float* tiles, float* e,
-                    float* ratio, cudaStream_t st) {
-  debug_weights_kernel<D><<<a.N, 128, 0, st>>>(a, s, logW, r, tiles, e, ratio);
+cudaError_t debug_t(const MergeArgs& a, int s, float* logW, float* r, float* rowsum, float* tiles,
+                    float* e, float* ratio, cudaStream_t st) {
+  debug_weights_kernel<D><<<a.N, 128, 0, st>>>(a, s, logW, r, rowsum, tiles, e, ratio);
   return cudaGetLastError();
 }
 
@@ -739,8 +913,9 @@ cudaError_t launch_epilogue(const MergeArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_debug_weights(int D, const MergeArgs& a, int s_local, float* logW, float* r,
-                                 float* tiles, float* e, float* ratio, cudaStream_t s) {
-  DSMC_DISPATCH(D, debug_t<DD>(a, s_local, logW, r, tiles, e, ratio, s))
+                                 float* rowsum, float* tiles, float* e, float* ratio,
+                                 cudaStream_t s) {
+  DSMC_DISPATCH(D, debug_t<DD>(a, s_local, logW, r, rowsum, tiles, e, ratio, s))
 }
 
 int rowsum_rows_per_thread(int D) {

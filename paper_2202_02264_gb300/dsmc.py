@@ -67,8 +67,8 @@ _lock = threading.Lock()
 
 EXPORTS = ["dsmc_status_string", "dsmc_last_error", "dsmc_state_sizes", "dsmc_workspace_size",
            "dsmc_init_particles", "dsmc_merge_level", "dsmc_resolve", "dsmc_smooth",
-           "dsmc_conditional_smooth", "dsmc_stream_status", "dsmc_debug_philox",
-           "dsmc_debug_merge_weights"]
+           "dsmc_conditional_smooth", "dsmc_stream_status", "dsmc_profile_enable",
+           "dsmc_profile_read", "dsmc_debug_philox", "dsmc_debug_merge_weights"]
 
 
 def library_path() -> str:
@@ -105,9 +105,12 @@ def load(build_if_needed: bool = False) -> C.CDLL:
         lib.dsmc_conditional_smooth.argtypes = [cfgp, modp, prop_p, vp, vp, vp, statp, vp, vp, vp,
                                                 vp, sz, vp]
         lib.dsmc_stream_status.argtypes = [vp, vp, C.POINTER(C.c_int)]
+        lib.dsmc_profile_enable.argtypes = [C.c_int]
+        lib.dsmc_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         lib.dsmc_debug_philox.argtypes = [vp, C.c_int64, C.c_uint64, vp, vp]
         lib.dsmc_debug_merge_weights.argtypes = [cfgp, modp, C.c_int, C.c_int, vp, vp, vp, vp, vp,
-                                                 C.POINTER(C.c_int), vp, sz, vp]
+                                                 vp, C.POINTER(C.c_int), vp, sz, vp]
         _lib = lib
         return lib
 
@@ -220,6 +223,18 @@ def dsmc_stream_status(ws, stream=None) -> int:
     return int(out.value)
 
 
+def dsmc_profile_enable(enable: bool):
+    _check(load().dsmc_profile_enable(1 if enable else 0), "dsmc_profile_enable")
+
+
+def dsmc_profile_read():
+    """(rowsum_ms, rowsum_launches, rowsum_pairs, all_launches) since profiling was enabled."""
+    ms, n, pairs, alln = C.c_double(0), C.c_int64(0), C.c_double(0), C.c_int64(0)
+    _check(load().dsmc_profile_read(C.byref(ms), C.byref(n), C.byref(pairs), C.byref(alln)),
+           "dsmc_profile_read")
+    return ms.value, n.value, pairs.value, alln.value
+
+
 def dsmc_debug_philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
     ctr = ctr.contiguous()
     out = torch.empty_like(ctr)
@@ -229,24 +244,27 @@ def dsmc_debug_philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor
     return out
 
 
-def dsmc_debug_merge_weights(cfg, model, level, m, ws, want=("logW", "r", "tiles", "e", "ratio"),
-                             stream=None):
+def dsmc_debug_merge_weights(cfg, model, level, m, ws,
+                             want=("logW", "r", "rowsum", "tiles", "e", "ratio"), stream=None):
     N = cfg.N
     info = (C.c_int * 4)()
     # first call for the tile count
     _check(load().dsmc_debug_merge_weights(C.byref(cfg), C.byref(model.struct), int(level), int(m),
-                                           None, None, None, None, None, info, _ptr(ws), ws.numel(),
+                                           None, None, None, None, None, None, info, _ptr(ws),
+                                           ws.numel(),
                                            _stream(stream)), "dsmc_debug_merge_weights")
     B, nT = info[0], info[1]
     dev = ws.device
     out = {}
     out["logW"] = torch.empty((N, N), dtype=torch.float32, device=dev) if "logW" in want else None
     out["r"] = torch.empty((N,), dtype=torch.float32, device=dev) if "r" in want else None
+    out["rowsum"] = torch.empty((N,), dtype=torch.float32, device=dev) if "rowsum" in want else None
     out["tiles"] = torch.empty((N, nT), dtype=torch.float32, device=dev) if "tiles" in want else None
     out["e"] = torch.empty((N, N), dtype=torch.float32, device=dev) if "e" in want else None
     out["ratio"] = torch.empty((N, N), dtype=torch.float32, device=dev) if "ratio" in want else None
     _check(load().dsmc_debug_merge_weights(C.byref(cfg), C.byref(model.struct), int(level), int(m),
-                                           _ptr(out["logW"]), _ptr(out["r"]), _ptr(out["tiles"]),
+                                           _ptr(out["logW"]), _ptr(out["r"]), _ptr(out["rowsum"]),
+                                           _ptr(out["tiles"]),
                                            _ptr(out["e"]), _ptr(out["ratio"]), info, _ptr(ws),
                                            ws.numel(), _stream(stream)), "dsmc_debug_merge_weights")
     out.update(B=info[0], nT=info[1], gid=info[2], left_leaf=info[3])

@@ -115,21 +115,33 @@ def test_rejection_sampler_cap():
     assert ((0 <= li) & (li < 4)).all() and ((0 <= ri) & (ri < 4)).all()
 
 
+def _q40(x, ref):
+    """floor(x 2^(40 - E)) with 2^(E-2) <= ref < 2^(E-1): the fixed-point image the sampler
+    uses for weights below twice their reference, from numpy's frexp (independent of the
+    oracle's bit manipulation)."""
+    _, e_ref = np.frexp(np.float64(ref))      # ref = m 2^e_ref, m in [0.5, 1)
+    E = int(e_ref) + 1
+    x = np.asarray(x, np.float64)
+    out = np.floor(np.ldexp(x, 40 - E))
+    out[(x <= 0) | (np.abs(x) < np.finfo(np.float32).tiny)] = 0
+    return out
+
+
 def _kp_law(r, t, e, B):
-    """Exact law of the three-stage sampler: row by the truncated 2^40 fixed-point weights,
-    tile and column by their FP32 weights."""
+    """Exact law of the three-stage sampler: rows by the truncated 2^40 fixed-point weights,
+    tiles and columns by their fixed-point images."""
     N = r.shape[0]
     nT = t.shape[1]
     Rq = np.floor(np.clip(r.astype(np.float64), 0, 1) * 2.0**40)
     P = np.zeros((N, N))
     for i in range(N):
-        pt = t[i].astype(np.float64) / t[i].astype(np.float64).sum()
+        qt = _q40(t[i], t[i].max())
         for k in range(nT):
             j0, j1 = k * B, min((k + 1) * B, N)
-            pe = e[i, j0:j1].astype(np.float64)
-            if pe.sum() == 0:
+            qe = _q40(e[i, j0:j1], t[i, k])
+            if qe.sum() == 0 or qt.sum() == 0:
                 continue
-            P[i, j0:j1] = Rq[i] / Rq.sum() * pt[k] * pe / pe.sum()
+            P[i, j0:j1] = Rq[i] / Rq.sum() * qt[k] / qt.sum() * qe / qe.sum()
     return P
 
 
@@ -142,6 +154,7 @@ def test_kp_dense_sampler_chi_square():
     r[r.argmax()] = 1.0
     e = rng.uniform(0, 1, (N, N)).astype(np.float32)
     e[:, 4] = 0.0          # a zero column is never chosen
+    e[5] *= np.float32(1e-30)   # a row far below 1: the fixed point scales per row
     t = np.stack([[e[i, k * B:(k + 1) * B].sum() for k in range(nT)] for i in range(N)]).astype(np.float32)
     li, ri = core.kp_dense_pairs(r, t, e, B, seed=3, gid=11, n0=0, n1=300_000)
     P = _kp_law(r, t, e, B)
@@ -162,13 +175,19 @@ def test_kp_dense_sampler_zero_tail_and_single_row():
     assert (li == 3).all() and (ri == 4).all()
 
 
-def test_kp_rs_sampler_chi_square():
-    rng = np.random.default_rng(8)
-    N = 4
-    q = rng.uniform(0.05, 1, (N, N)).astype(np.float32)
-    q[1, 3] = 0.0
-    li, ri, att, st = core.kp_rs_pairs(q, seed=5, gid=2, n0=0, n1=200_000)
-    assert st == 0
-    P = q.astype(np.float64) / q.sum()
-    assert _chi2(li, ri, P) > 1e-3
-    assert att.mean() == pytest.approx(N * N / q.sum(), rel=0.03)
+def test_kp_fixed_point_image():
+    """The bit-pattern quantisation equals floor(x 2^(40-E)) computed through frexp/ldexp."""
+    rng = np.random.default_rng(9)
+    N = B = 64                                 # one tile per row
+    for scale in [1.0, 1e-20, 1e20]:
+        e = (rng.uniform(0, 1, (N, N)) * scale).astype(np.float32)
+        t = e.sum(1, keepdims=True).astype(np.float32)
+        for i in [0, 17, 63]:
+            q_ref = _q40(e[i], t[i, 0])
+            rr = np.zeros(N, np.float32)
+            rr[i] = 1.0                        # all row weight on row i
+            li, ri = core.kp_dense_pairs(rr, t, e, B, seed=5, gid=i, n0=0, n1=20000)
+            assert (li == i).all()
+            p = q_ref / q_ref.sum()
+            counts = np.bincount(ri, minlength=B)
+            assert stats.chisquare(counts, p * counts.sum()).pvalue > 1e-3
