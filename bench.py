@@ -189,7 +189,8 @@ def run_ours(args):
     wl = W.workload(base_name, K=spec["K"], N=spec["N"])
     K, N = wl.K, wl.N
     resampler = dsmc.RS if spec["resampler"] == "rs" else dsmc.MULTINOMIAL
-    sm = dsmc.Smoother(wl.model, K, N, seed=1000 + 7919 * rank, resampler=resampler)
+    compute = {"fp32": dsmc.FP32, "tf32": dsmc.TF32, "bf16": dsmc.BF16}[args.compute]
+    sm = dsmc.Smoother(wl.model, K, N, seed=1000 + 7919 * rank, resampler=resampler, compute=compute)
     y = torch.as_tensor(wl.y, dtype=torch.float32, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
     stream = torch.cuda.current_stream()
@@ -262,7 +263,9 @@ def run_ours(args):
     ex2_peak = MUFU_EX2_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9       # G exp / s
     achieved = rs_pairs / (rs_ms / 1e3) / 1e9 if rs_ms > 0 else None   # G exp / s
     d = wl.model.d
-    roofline = {"bound": "alu", "kernel": "rowsum_kernel (fused exp / tile sums)",
+    roofline = {"bound": "alu",
+                "kernel": ("rowsum_kernel (fused exp / tile sums)" if args.compute == "fp32"
+                           else "rowsum_tc_kernel (tcgen05 cross term, fused exp / tile sums)"),
                 "achieved": achieved, "peak": ex2_peak, "unit": "Gexp/s",
                 "frac": achieved / ex2_peak if achieved else None,
                 "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
@@ -276,7 +279,10 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "K": K, "N": N, "dx": d,
-                       "resampler": spec["resampler"], "compute": "fp32 cuda-core",
+                       "resampler": spec["resampler"],
+                       "compute": {"fp32": "fp32 cuda-core cross term",
+                                   "tf32": "tf32 tcgen05 cross term, fp32 accumulate / exp",
+                                   "bf16": "bf16 tcgen05 cross term, fp32 accumulate / exp"}[args.compute],
                        "l2": "flushed between timed steps (512 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "clocks": clk,
@@ -297,6 +303,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lgssm_d8", choices=sorted(WORKLOADS))
+    ap.add_argument("--compute", default="fp32", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

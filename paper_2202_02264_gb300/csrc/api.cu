@@ -84,16 +84,28 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Plan {
   int K, N, d, D, L;
+  int compute, Nr;
   int B, nT, nTp;
   int Mc;
   int R, rows_per_cta;
   bool dense;
   int level_off[33];
   size_t o_status, o_U, o_alpha, o_V, o_beta, o_shift, o_logbar, o_inc, o_T, o_rw, o_rowsum, o_cum,
-      o_delta, o_first, o_last, o_star, total;
+      o_delta, o_first, o_last, o_star, o_Ub, o_Vb, o_betap, total;
 };
 
 void chunking(const Plan& p, int mc, int& CH, int& CW) {
+  if (p.compute != DSMC_FP32) {
+    // tensor-core path: 128-row CTAs, two per SM, chunks of whole 128-column blocks
+    const int RT = (p.N + 127) / 128;
+    const int nblk = (p.N + 127) / 128;
+    int want = (152 * 2 * 2 + mc * RT - 1) / (mc * RT);
+    want = std::max(1, std::min(want, nblk));
+    const int bpc = (nblk + want - 1) / want;
+    CW = bpc * 128;
+    CH = (nblk + bpc - 1) / bpc;
+    return;
+  }
   const int RT = (p.N + p.rows_per_cta - 1) / p.rows_per_cta;
   int want = (kRowsumTargetCtas + mc * RT - 1) / (mc * RT);
   want = std::max(1, std::min(want, p.nT));
@@ -110,6 +122,8 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p) {
   p.L = 0;
   while ((1 << p.L) < p.K) ++p.L;
   p.dense = cfg->resampler != DSMC_RS;
+  p.compute = cfg->compute;
+  p.Nr = (p.N + 127) / 128 * 128;
   const int nT0 = std::min((p.N + 31) / 32, 64);
   const int per = (p.N + nT0 - 1) / nT0;
   p.B = 32 * ((per + 31) / 32);
@@ -150,6 +164,10 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p) {
   p.o_first = take(2 * (size_t)p.K * p.N * sizeof(int32_t));
   p.o_last = take(2 * (size_t)p.K * p.N * sizeof(int32_t));
   p.o_star = take(2 * sizeof(int32_t));
+  const bool tc = p.compute != DSMC_FP32;
+  p.o_Ub = take(tc ? (size_t)p.Mc * p.Nr * 32 : 0);
+  p.o_Vb = take(tc ? (size_t)p.Mc * p.Nr * 32 : 0);
+  p.o_betap = take(tc ? (size_t)p.Mc * p.Nr * sizeof(float) : 0);
   p.total = o;
 }
 
@@ -172,6 +190,9 @@ WsPtrs ws_ptrs(const Plan& p, void* ws) {
   w.first = reinterpret_cast<int32_t*>(b + p.o_first);
   w.last = reinterpret_cast<int32_t*>(b + p.o_last);
   w.star = reinterpret_cast<int32_t*>(b + p.o_star);
+  w.Ub = reinterpret_cast<unsigned char*>(b + p.o_Ub);
+  w.Vb = reinterpret_cast<unsigned char*>(b + p.o_Vb);
+  w.betap = reinterpret_cast<float*>(b + p.o_betap);
   return w;
 }
 
@@ -290,8 +311,14 @@ dsmc_status_t check_config(const dsmc_config_t* cfg, const dsmc_model_t* model) 
     return fail(DSMC_ERR_INVALID_ARG, "unknown resampler");
   if (cfg->resampler == DSMC_MULTINOMIAL && cfg->N > kMaxDenseN)
     return fail(DSMC_ERR_UNSUPPORTED, "dense resampling supports N <= 16384; use DSMC_RS");
-  if (cfg->compute != DSMC_FP32)
-    return fail(DSMC_ERR_UNSUPPORTED, "only the FP32 cross-term is available in this build");
+  if (cfg->compute != DSMC_FP32 && cfg->compute != DSMC_TF32 && cfg->compute != DSMC_BF16)
+    return fail(DSMC_ERR_INVALID_ARG, "unknown compute precision");
+  if (cfg->compute == DSMC_TF32 && model->dx > 8)
+    return fail(DSMC_ERR_UNSUPPORTED, "the TF32 tensor-core cross term supports dx <= 8");
+  if (cfg->compute == DSMC_BF16 && model->dx > 16)
+    return fail(DSMC_ERR_UNSUPPORTED, "the BF16 tensor-core cross term supports dx <= 16");
+  if (cfg->compute != DSMC_FP32 && cfg->resampler == DSMC_MULTINOMIAL && cfg->N > 4096)
+    return fail(DSMC_ERR_UNSUPPORTED, "the tensor-core cross term supports N <= 4096");
   if (cfg->counter_base >= (1u << 28)) return fail(DSMC_ERR_INVALID_ARG, "counter_base must be < 2^28");
   if (model->dx < 1 || model->dx > kMaxDim) return fail(DSMC_ERR_UNSUPPORTED, "dx must be in 1..32");
   if (model->kind == DSMC_MODEL_SV) {
@@ -364,6 +391,8 @@ MergeArgs merge_args(const Plan& p, const dsmc_config_t* cfg, const float* y, in
   a.conditional = conditional;
   a.root = (level == p.L - 1);
   a.resampler = cfg->resampler;
+  a.compute = cfg->compute;
+  a.Nr = p.Nr;
   a.seed = cfg->seed;
   a.base = cfg->counter_base;
   a.rs_max = cfg->rs_max_attempts ? cfg->rs_max_attempts : (1u << 20);
@@ -412,7 +441,10 @@ dsmc_status_t do_level(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& 
     DSMC_CUDA(launch_prologue(p.D, a, mp.bytes, s), "prologue kernel");
     if (p.dense) {
       DSMC_CUDA(prof_begin(s), "profile event");
-      DSMC_CUDA(launch_rowsum(p.D, a, s), "tile-sum kernel");
+      if (p.compute == DSMC_FP32)
+        DSMC_CUDA(launch_rowsum(p.D, a, s), "tile-sum kernel");
+      else
+        DSMC_CUDA(launch_rowsum_tc(a, s), "tensor-core tile-sum kernel");
       DSMC_CUDA(prof_end(s, (double)a.mc * p.N * p.N), "profile event");
       DSMC_CUDA(launch_sample_dense(p.D, a, s), "dense sampler kernel");
       prof_count(3);

@@ -27,6 +27,13 @@ struct WsPtrs {
   int32_t* last;     // [2][K][N]    last-time particle index of each block
   int32_t* star;     // [2]          root pair of the next reference (conditional mode)
   double* inc;       // [Mc]         log normalising-constant increments
+  // tensor-core operands (compute = DSMC_TF32 / DSMC_BF16): U and V rounded to the MMA
+  // type, K padded to 32 bytes per row, in the canonical no-swizzle K-major layout of
+  // 8-row x 16-byte core matrices (row group g at g*256 B, 16-byte K chunk c at c*128 B),
+  // rows padded to a multiple of 128; beta copied with the same padded stride.
+  unsigned char* Ub; // [Mc][Nr][32 B]
+  unsigned char* Vb; // [Mc][Nr][32 B]
+  float* betap;      // [Mc][Nr]
 };
 
 struct MergeArgs {
@@ -40,6 +47,8 @@ struct MergeArgs {
   int conditional;   // Algorithm 5 when non-zero
   int root;          // this level holds the root combination
   int resampler;
+  int compute;       // DSMC_FP32, DSMC_TF32 or DSMC_BF16
+  int Nr;            // N rounded up to 128 (tensor-core operand rows)
   uint64_t seed;
   uint32_t base;
   uint32_t rs_max;
@@ -82,6 +91,7 @@ struct GatherArgs {
 cudaError_t launch_init(int D, const InitArgs& a, const void* mp, cudaStream_t s);
 cudaError_t launch_prologue(int D, const MergeArgs& a, const void* mp, cudaStream_t s);
 cudaError_t launch_rowsum(int D, const MergeArgs& a, cudaStream_t s);
+cudaError_t launch_rowsum_tc(const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_sample_dense(int D, const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_sample_rs(int D, const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_epilogue(const MergeArgs& a, cudaStream_t s);

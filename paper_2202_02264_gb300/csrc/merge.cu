@@ -20,6 +20,8 @@
 #include <algorithm>
 #include <cfloat>
 
+#include <cuda_bf16.h>
+
 #include "kernels.cuh"
 
 namespace dsmc {
@@ -52,6 +54,29 @@ __device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
+}
+
+// One row of a tensor-core operand: element k of row r at (r/8)*256 + (k/epc)*128 +
+// (r%8)*16 + (k%epc)*eb bytes (8-row x 16-byte core matrices, K = 32 bytes: 16 BF16 or 8
+// TF32 values; entries beyond D are zero).  TF32 is rounded to nearest.
+template <int D>
+__device__ __forceinline__ void store_mma_row(unsigned char* base, int r, const float* x, int compute) {
+  unsigned char* row = base + (size_t)(r / 8) * 256 + (size_t)(r % 8) * 16;
+  if (compute == DSMC_BF16) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float v = k < D ? x[k] : 0.f;
+      *reinterpret_cast<__nv_bfloat16*>(row + (k / 8) * 128 + (k % 8) * 2) = __float2bfloat16_rn(v);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float v = k < D ? x[k] : 0.f;
+      uint32_t t;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
+      *reinterpret_cast<uint32_t*>(row + (k / 4) * 128 + (k % 4) * 4) = t;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -153,6 +178,18 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
 #pragma unroll
     for (int k = 0; k < D; ++k) V[(size_t)j * D + k] = v[k];
     beta[j] = kLog2e * (beta[j] - bstar - 0.5f * quad_form<D>(mp.Qi, v));
+    if (a.compute != DSMC_FP32) {
+      store_mma_row<D>(a.ws.Vb + (size_t)s * a.Nr * 32, j, v, a.compute);
+      a.ws.betap[(size_t)s * a.Nr + j] = beta[j];
+    }
+  }
+  if (a.compute != DSMC_FP32) {  // zero the padding rows of the tensor-core operands
+    const float zero[D] = {};
+    for (int j = N + threadIdx.x; j < a.Nr; j += kProThreads) {
+      store_mma_row<D>(a.ws.Vb + (size_t)s * a.Nr * 32, j, zero, a.compute);
+      store_mma_row<D>(a.ws.Ub + (size_t)s * a.Nr * 32, j, zero, a.compute);
+      a.ws.betap[(size_t)s * a.Nr + j] = 0.f;
+    }
   }
   // pass 2b: rows  w_i = A xL_i + c - mu,  u_i = log2(e) Q^-1 w_i,
   //                alpha_i = -log2(e) 1/2 w_i' Q^-1 w_i  (B* is folded into beta)
@@ -183,6 +220,12 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
     bad |= isnan(ai);
 #pragma unroll
     for (int k = 0; k < D; ++k) U[(size_t)i * D + k] = kLog2e * u[k];
+    if (a.compute != DSMC_FP32) {
+      float ul[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) ul[k] = kLog2e * u[k];
+      store_mma_row<D>(a.ws.Ub + (size_t)s * a.Nr * 32, i, ul, a.compute);
+    }
     alpha[i] = -0.5f * kLog2e * q;
     shift[i] = (double)ai + (double)mp.log_f_max + (double)bstar;
     amax = fmaxf(amax, ai);

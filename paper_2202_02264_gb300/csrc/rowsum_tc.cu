@@ -1,0 +1,396 @@
+// rowsum_tc.cu -- the N x N exponent / tile-sum pass of Algorithm 1 with the Gaussian
+// cross term u_i . v_j on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// One CTA computes 128 rows (one TMEM lane each) of one combination against a chunk of
+// columns, in blocks of 128 columns:
+//   - a control warp stages the row tile once and each 128-column block of v_j with TMA
+//     bulk copies (cp.async.bulk, operands pre-laid out by the prologue in the canonical
+//     no-swizzle K-major layout), and issues one tcgen05.mma (M = 128, N = 128, K = 32 bytes:
+//     16 BF16 or 8 TF32 values) per block into one of two 128-column TMEM accumulators;
+//   - eight epilogue warps (two per TMEM lane quarter, splitting the block's columns) read the
+//     accumulator with tcgen05.ld, add alpha_i and beta_j in FP32, take 2^x on MUFU and keep
+//     the per-tile sums, while the tensor core already computes the next block.
+// Every wait is bounded; on a timeout the CTA records DSMC_ERR_TIMEOUT, waits (bounded) for
+// its own outstanding MMA, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+
+namespace dsmc {
+
+namespace {
+
+constexpr int kTcRows = 128;                   // MMA M: one TMEM lane per row
+constexpr int kTcCols = 128;                   // MMA N: columns per block
+constexpr int kEpiWarps = 8;
+constexpr int kTcThreads = (kEpiWarps + 1) * 32;
+constexpr int kTileBytes = 128 * 32;           // 128 rows (or columns) x 32 bytes of K
+constexpr uint32_t kTmemCols = 2 * kTcCols;    // two accumulators
+constexpr uint32_t kWaitLimit = 1u << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kWaitLimit && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// No-swizzle K-major operand: 16-byte K chunks 128 bytes apart (leading), 8-row groups 256
+// bytes apart (stride), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)(256u >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16 with BF16 operands, or kind::tf32; FP32 accumulator; both K-major; M x N.
+template <int KIND>
+__device__ __forceinline__ uint32_t instr_desc() {
+  const uint32_t fmt = KIND == DSMC_BF16 ? 1u : 2u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTcCols >> 3) << 17) |
+         ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t da, uint64_t db) {
+  const uint32_t idesc = instr_desc<KIND>();
+  const uint32_t accum = 0;
+  if (KIND == DSMC_BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(accum));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(accum));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+// Issue a 32x32b.x32 TMEM load (one row per lane, 32 consecutive columns); the registers
+// are valid after tmem_wait().
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,"
+      "%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Sum over 32 columns of 2^(acc + beta_j + alpha) with packed FP32 adds (pairs of columns);
+// columns at or beyond `valid` contribute nothing.  The order of the additions is fixed.
+template <bool MASK>
+__device__ __forceinline__ float exp_sum32(const uint32_t* acc, const float* beta, float al, int valid) {
+  const float4* b4 = reinterpret_cast<const float4*>(beta);
+  const float2 al2 = make_float2(al, al);
+  float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q4 = 0; q4 < 8; ++q4) {
+    const float4 bv = b4[q4];
+    float2 x0 = __fadd2_rn(make_float2(__uint_as_float(acc[4 * q4]), __uint_as_float(acc[4 * q4 + 1])),
+                           make_float2(bv.x, bv.y));
+    float2 x1 = __fadd2_rn(make_float2(__uint_as_float(acc[4 * q4 + 2]), __uint_as_float(acc[4 * q4 + 3])),
+                           make_float2(bv.z, bv.w));
+    x0 = __fadd2_rn(x0, al2);
+    x1 = __fadd2_rn(x1, al2);
+    float2 e0 = make_float2(ex2(x0.x), ex2(x0.y));
+    float2 e1 = make_float2(ex2(x1.x), ex2(x1.y));
+    if (MASK) {
+      const int q = 4 * q4;
+      e0.x = q < valid ? e0.x : 0.f;
+      e0.y = q + 1 < valid ? e0.y : 0.f;
+      e1.x = q + 2 < valid ? e1.x : 0.f;
+      e1.y = q + 3 < valid ? e1.y : 0.f;
+    }
+    s2 = __fadd2_rn(s2, e0);
+    s2 = __fadd2_rn(s2, e1);
+  }
+  return __fadd_rn(s2.x, s2.y);
+}
+
+// Work item = (combination s, 128-row tile rt, column chunk ch); the grid is persistent
+// (two CTAs per SM) and each CTA walks items blockIdx.x, blockIdx.x + gridDim.x, ...
+struct Item {
+  int s, rt, j0, j1, nblk;
+};
+
+__device__ __forceinline__ Item item_of(const MergeArgs& a, int it) {
+  const int RT = (a.N + kTcRows - 1) / kTcRows;
+  Item r;
+  r.s = it / (RT * a.CH);
+  const int rem = it % (RT * a.CH);
+  r.rt = rem / a.CH;
+  r.j0 = (rem % a.CH) * a.CW;
+  r.j1 = min(r.j0 + a.CW, a.N);
+  r.nblk = (r.j1 - r.j0 + kTcCols - 1) / kTcCols;
+  return r;
+}
+
+constexpr int kVSlots = 16;   // column blocks (v_j tile + beta_j run) staged ahead
+constexpr int kRefillLag = 4; // a slot is refilled once the epilogue finished its block
+constexpr int kBetaBytes = kTcCols * 4;
+
+template <int KIND>
+__global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, int n_items) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  unsigned char* sA = dsm;                                        // [2][4 KB] row tiles
+  unsigned char* sV = dsm + 2 * kTileBytes;                       // [kVSlots][4 KB] v_j tiles
+  float* sB = reinterpret_cast<float*>(sV + kVSlots * kTileBytes); // [kVSlots][128] beta_j
+  __shared__ __align__(8) uint64_t bar_a[2], bar_v[kVSlots], bar_done[kVSlots], bar_mma[2], bar_epi[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_s;
+
+  const int N = a.N, B = a.B;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    abort_s = 0;
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(smem_u32(&bar_a[q]), 1);
+      mbar_init(smem_u32(&bar_mma[q]), 1);
+      mbar_init(smem_u32(&bar_epi[q]), kEpiWarps);
+    }
+    for (int q = 0; q < kVSlots; ++q) {
+      mbar_init(smem_u32(&bar_v[q]), 1);
+      mbar_init(smem_u32(&bar_done[q]), kEpiWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == kEpiWarps) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tb = tmem_base;
+
+  if (warp == kEpiWarps) {
+    // ------------------------------------------------------------ control: TMA + MMA
+    if (lane == 0) {
+      bool ok = true;
+      int issued = 0;
+      // load cursor over the CTA's block sequence
+      int l_it = blockIdx.x, l_b = 0, lq = 0, l_k = 0;
+      Item li = item_of(a, l_it);
+      auto load_next = [&]() {  // v_j tile and beta_j run of the next block, one barrier
+        if (l_it >= n_items) return;
+        const size_t col = (size_t)li.s * a.Nr + li.j0 + (size_t)l_b * kTcCols;
+        const int slot = lq % kVSlots;
+        const uint32_t bar = smem_u32(&bar_v[slot]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)(kTileBytes + kBetaBytes))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sV + (size_t)slot * kTileBytes)),
+            "l"(a.ws.Vb + col * 32), "r"((uint32_t)kTileBytes), "r"(bar)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sB + (size_t)slot * kTcCols)),
+            "l"(a.ws.betap + col), "r"((uint32_t)kBetaBytes), "r"(bar)
+            : "memory");
+        ++lq;
+        if (++l_b == li.nblk) {
+          l_b = 0;
+          l_it += gridDim.x;
+          ++l_k;
+          if (l_it < n_items) li = item_of(a, l_it);
+        }
+      };
+      auto load_a = [&](int it, int slot) {
+        if (it >= n_items) return;
+        const Item t = item_of(a, it);
+        const unsigned char* src = a.ws.Ub + (size_t)t.s * a.Nr * 32 + (size_t)t.rt * kTileBytes;
+        tma_load(smem_u32(sA + (size_t)slot * kTileBytes), src, kTileBytes, smem_u32(&bar_a[slot]));
+      };
+      load_a(blockIdx.x, 0);
+      load_a(blockIdx.x + gridDim.x, 1);
+      for (int q = 0; q < kVSlots; ++q) load_next();
+      // blocks whose epilogue completion still has to release their slot / A tile
+      int r = 0, r_b = 0, r_k = 0;
+      Item ri = item_of(a, blockIdx.x);
+      auto retire = [&](int upto) {  // refill slots of blocks r < upto (epilogue done)
+        while (ok && r < upto) {
+          ok = mbar_wait(smem_u32(&bar_done[r % kVSlots]), (uint32_t)(r / kVSlots) & 1);
+          if (!ok) break;
+          load_next();
+          if (r_b == ri.nblk - 1) load_a(blockIdx.x + (r_k + 2) * gridDim.x, r_k & 1);
+          ++r;
+          if (++r_b == ri.nblk) {
+            r_b = 0;
+            ++r_k;
+            const int nit = blockIdx.x + r_k * gridDim.x;
+            if (nit < n_items) ri = item_of(a, nit);
+          }
+        }
+      };
+      int q = 0;       // global block index of this CTA
+      int k = 0;       // item index of this CTA
+      int q_prev = 0;  // first block of the previous item
+      for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++k) {
+        const Item cur = item_of(a, it);
+        // item k's row tile is loaded when item k-2 retires: retire every block before the
+        // previous item first (short items would otherwise outrun the refill lag)
+        if (k >= 2) retire(q_prev);
+        q_prev = q;
+        if (ok) ok = mbar_wait(smem_u32(&bar_a[k & 1]), (uint32_t)(k >> 1) & 1);
+        const uint64_t da = smem_desc(smem_u32(sA + (size_t)(k & 1) * kTileBytes));
+        for (int b = 0; b < cur.nblk && ok; ++b, ++q) {
+          const int buf = q & 1;
+          const int slot = q % kVSlots;
+          retire(q - kRefillLag);
+          if (ok && q >= 2) ok = mbar_wait(smem_u32(&bar_epi[buf]), (uint32_t)((q >> 1) - 1) & 1);
+          if (ok) ok = mbar_wait(smem_u32(&bar_v[slot]), (uint32_t)(q / kVSlots) & 1);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          mma<KIND>(tb + (uint32_t)buf * kTcCols, da, smem_desc(smem_u32(sV + (size_t)slot * kTileBytes)));
+          mma_commit(smem_u32(&bar_mma[buf]));
+          ++issued;
+        }
+      }
+      // the last committed MMA must be complete before TMEM is released
+      if (issued > 0) {
+        const int qq = issued - 1;
+        mbar_wait(smem_u32(&bar_mma[qq & 1]), (uint32_t)(qq >> 1) & 1);
+      }
+      if (!ok) {
+        atomicExch(&abort_s, 1);
+        record_status(a.ws.status, DSMC_ERR_TIMEOUT);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue warps
+    const int g = warp & 3, h = warp >> 2;
+    int q = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+      const Item cur = item_of(a, it);
+      const int s = cur.s;
+      const int row = cur.rt * kTcRows + 32 * g + lane;
+      const float al = row < N ? a.ws.alpha[(size_t)s * N + row] : 0.f;
+      float* Trow = a.ws.T + ((size_t)s * N + (row < N ? row : 0)) * a.nTp;
+      bool stop = false;
+      for (int b = 0; b < cur.nblk; ++b, ++q) {
+        const int buf = q & 1;
+        const int slot = q % kVSlots;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_mma[buf]), (uint32_t)(q >> 1) & 1)) &&
+                        !*reinterpret_cast<volatile int*>(&abort_s);
+        if (!ok) {  // warp-uniform
+          if (lane == 0) {
+            atomicExch(&abort_s, 1);
+            record_status(a.ws.status, DSMC_ERR_TIMEOUT);
+          }
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int col0 = cur.j0 + b * kTcCols + 64 * h;
+        uint32_t acc0[32], acc1[32];
+        const uint32_t taddr = tb + ((uint32_t)(32 * g) << 16) + (uint32_t)buf * kTcCols + 64 * h;
+        tmem_ld32(taddr, acc0);
+        tmem_ld32(taddr + 32, acc1);
+        tmem_wait();
+        // the accumulator is in registers: release the TMEM buffer to the MMA issuer now
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_epi[buf]));
+        const float* beta = sB + (size_t)slot * kTcCols + 64 * h;
+        float t0, t1;
+        if (col0 + 64 <= cur.j1) {
+          t0 = exp_sum32<false>(acc0, beta, al, 32);
+          t1 = exp_sum32<false>(acc1, beta + 32, al, 32);
+        } else {
+          t0 = exp_sum32<true>(acc0, beta, al, cur.j1 - col0);
+          t1 = exp_sum32<true>(acc1, beta + 32, al, cur.j1 - col0 - 32);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_done[slot]));  // slot (v_j, beta_j) free
+        if (row < N) {
+          if (B == 32) {
+            if (col0 < cur.j1) Trow[col0 / 32] = t0;
+            if (col0 + 32 < cur.j1) Trow[col0 / 32 + 1] = t1;
+          } else if (col0 < cur.j1) {
+            Trow[col0 / 64] = __fadd_rn(t0, t1);
+          }
+        }
+      }
+      if (stop) break;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == kEpiWarps) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tb), "r"(kTmemCols));
+  }
+}
+
+// Dynamic shared memory: 2 row tiles + kVSlots column blocks with their beta runs
+// (~80 KB), padded so that at most two CTAs (2 x 256 TMEM columns) share an SM.
+constexpr size_t kDynSmem = 100 * 1024;
+static_assert((2 + kVSlots) * kTileBytes + kVSlots * kBetaBytes <= kDynSmem, "staging buffers");
+
+template <int KIND>
+cudaError_t launch_t(const MergeArgs& a, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(rowsum_tc_kernel<KIND>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
+  if (e != cudaSuccess) return e;
+  const int RT = (a.N + kTcRows - 1) / kTcRows;
+  const int n_items = a.mc * RT * a.CH;
+  const int grid = n_items < 2 * 152 ? n_items : 2 * 152;
+  rowsum_tc_kernel<KIND><<<grid, kTcThreads, kDynSmem, st>>>(a, n_items);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_rowsum_tc(const MergeArgs& a, cudaStream_t s) {
+  if (a.compute == DSMC_BF16) return launch_t<DSMC_BF16>(a, s);
+  if (a.compute == DSMC_TF32) return launch_t<DSMC_TF32>(a, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace dsmc

@@ -433,3 +433,70 @@ def test_bench_configuration_full_size():
         np.testing.assert_array_equal(pairs[dbg["gid"], 0], li)
         np.testing.assert_array_equal(pairs[dbg["gid"], 1], ri)
     assert sm.status() == 0
+
+
+# ------------------------------------------------------------------------ tensor cores
+TC_TOL = {dsmc.TF32: 0.06, dsmc.BF16: 0.25}   # max |log2 tile ratio| vs the FP32 path
+
+
+@pytest.mark.parametrize("compute", [dsmc.TF32, dsmc.BF16])
+@pytest.mark.parametrize("name,K,N,level", [("lgssm_d8", 16, 1000, 0), ("lgssm_d8", 9, 300, 3),
+                                            ("lgssm_d4", 8, 2500, 1), ("sv", 6, 64, 2)])
+def test_tensor_core_tiles_and_indices(compute, name, K, N, level):
+    """The tcgen05 cross term: tile weights within the precision's error of the FP32 path on
+    identical particles, and indices bit-exact against the oracle's device-precision
+    sampler fed the device's own (tensor-core) weights."""
+    wl = W.workload(name, K=K, N=N)
+    y = dev(wl.y)
+    out = {}
+    for cm in (dsmc.FP32, compute):
+        sm = dsmc.Smoother(wl.model, K, N, seed=5, compute=cm)
+        sm.init(y)
+        for l in range(level + 1):
+            sm.merge_level(y, l)
+        torch.cuda.synchronize()
+        M = core.merges_at_level(K, level)
+        out[cm] = (sm, dsmc.dsmc_debug_merge_weights(sm.cfg, sm.hm, level, M - 1, sm.ws))
+    if level == 0:
+        t32 = out[dsmc.FP32][1]["tiles"].cpu().numpy().astype(np.float64)
+        ttc = out[compute][1]["tiles"].cpu().numpy().astype(np.float64)
+        big = t32 > 1e-6 * t32.max()
+        err = np.abs(np.log2(ttc[big]) - np.log2(t32[big]))
+        assert err.max() < TC_TOL[compute], err.max()
+    sm, dbg = out[compute]
+    pairs = sm.pairs.cpu().numpy()
+    li, ri = core.kp_dense_pairs(dbg["r"].cpu().numpy(), dbg["tiles"].cpu().numpy(),
+                                 dbg["e"].cpu().numpy(), dbg["B"], sm.cfg.seed, dbg["gid"], 0, N)
+    np.testing.assert_array_equal(pairs[dbg["gid"], 0], li)
+    np.testing.assert_array_equal(pairs[dbg["gid"], 1], ri)
+    assert sm.status() == 0
+
+
+@pytest.mark.parametrize("compute", [dsmc.TF32, dsmc.BF16])
+def test_tensor_core_means_vs_rts(compute):
+    m = W.lgssm_d8()
+    K, N = 100, 500
+    _, y = W.simulate(m, K, 77)
+    ms, _, _ = kalman.rts_for(m, y)
+    sm = dsmc.Smoother(m, K, N, seed=1000, compute=compute)
+    yd = dev(y)
+    g = []
+    for r in range(32):
+        sm.set_seed(1000 + r)
+        g.append(sm.smooth(yd).cpu().numpy().copy())
+    assert sm.status() == 0
+    _check(np.array(g), ms)
+
+
+@pytest.mark.parametrize("compute", [dsmc.TF32, dsmc.BF16])
+def test_tensor_core_bench_configuration(compute):
+    wl = W.workload("lgssm_d8")
+    ms, _, _ = kalman.rts_for(wl.model, wl.y)
+    sm = dsmc.Smoother(wl.model, wl.K, wl.N, seed=1000, compute=compute)
+    yd = dev(wl.y)
+    g = []
+    for r in range(24):
+        sm.set_seed(1000 + r)
+        g.append(sm.smooth(yd).cpu().numpy().copy())
+    assert sm.status() == 0
+    _check(np.array(g), ms)
