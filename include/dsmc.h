@@ -175,6 +175,33 @@ dsmc_status_t dsmc_conditional_smooth(const dsmc_config_t* cfg, const dsmc_model
                                       double* logL_out, void* ws, size_t ws_bytes,
                                       void* stream);
 
+/* Size of the library's static device scratch used by dsmc_smooth_noalloc (32 MiB). */
+#define DSMC_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/* dsmc_smooth without a caller-supplied workspace, for callers that cannot allocate device
+ * memory: code that runs inside another allocator's pool or a memory budget it does not
+ * own, plugins and runtimes that forbid cudaMalloc after start-up, and hosts whose own
+ * allocator must stay the only one.  (The paper has no counterpart: this is an interface
+ * convenience of this library.)
+ *   - The workspace is a fixed DSMC_NOALLOC_SCRATCH_BYTES array inside the library, held on
+ *     every device that loads the library until the process exits.  A problem whose
+ *     workspace (dsmc_workspace_size) is larger returns DSMC_ERR_WORKSPACE and launches
+ *     nothing.  The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ *     routine.
+ *   - The first call on a device looks up the array's device address (once per device,
+ *     with that device current); make that first call before any stream capture.
+ *   - Every call shares the one array and leaves its contents behind; the smoother clears
+ *     what must start at zero (its status word) at the start of each call.  Calls whose
+ *     work overlaps on the GPU (other streams, other host threads) race on the array:
+ *     serialise them.
+ *   - The state, y and outputs are the caller's, as for dsmc_smooth.  device_status: HOST
+ *     pointer or NULL; if given, the call synchronises `stream` and stores the first device
+ *     error of this smoothing (the workspace is not reachable otherwise). */
+dsmc_status_t dsmc_smooth_noalloc(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                  const dsmc_proposal_t* prop, const float* y, dsmc_state_t* state,
+                                  float* traj_out, double* mean_out, double* m2_out,
+                                  double* logL_out, dsmc_status_t* device_status, void* stream);
+
 /* Synchronises `stream` and returns in *device_status the first error any kernel recorded
  * in this workspace since the last dsmc_init_particles (DSMC_OK if none). */
 dsmc_status_t dsmc_stream_status(void* ws, void* stream, dsmc_status_t* device_status);

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -521,6 +522,30 @@ dsmc_status_t run_smooth(const dsmc_config_t* cfg, const dsmc_model_t* model,
   return DSMC_OK;
 }
 
+// ---- Scratch for callers that cannot allocate device memory (dsmc_smooth_noalloc).
+// A fixed-size device array owned by the library: every device that loads this library
+// holds it until the process exits.  Its device address is looked up once per device.
+constexpr size_t kNoAllocScratchBytes = DSMC_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+dsmc_status_t noalloc_scratch(void** ptr) {
+  int dev = 0;
+  DSMC_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(DSMC_ERR_UNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    // the host-side name of the array is not a device address: ask the runtime for it
+    void* p = nullptr;
+    DSMC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = p;
+  }
+  *ptr = g_noalloc_ptr[dev];
+  return DSMC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -618,6 +643,32 @@ dsmc_status_t dsmc_conditional_smooth(const dsmc_config_t* cfg, const dsmc_model
   if (!x_ref_in || !x_ref_out) return fail(DSMC_ERR_INVALID_ARG, "x_ref_in and x_ref_out are required");
   return run_smooth(cfg, model, prop, y, x_ref_in, x_ref_out, state, traj_out, mean_out, nullptr,
                     logL_out, ws, ws_bytes, stream);
+}
+
+dsmc_status_t dsmc_smooth_noalloc(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                  const dsmc_proposal_t* prop, const float* y, dsmc_state_t* state,
+                                  float* traj_out, double* mean_out, double* m2_out,
+                                  double* logL_out, dsmc_status_t* device_status, void* stream) {
+  DSMC_TRY(check_config(cfg, model));
+  Plan p;
+  make_plan(cfg, model, p);
+  if (p.total > kNoAllocScratchBytes)
+    return fail(DSMC_ERR_WORKSPACE,
+                "this problem needs " + std::to_string(p.total) + " bytes of workspace, more than the " +
+                    std::to_string(kNoAllocScratchBytes) +
+                    "-byte static scratch of dsmc_smooth_noalloc; use dsmc_smooth with a caller buffer");
+  void* ws = nullptr;
+  DSMC_TRY(noalloc_scratch(&ws));
+  DSMC_TRY(run_smooth(cfg, model, prop, y, nullptr, nullptr, state, traj_out, mean_out, m2_out,
+                      logL_out, ws, kNoAllocScratchBytes, stream));
+  if (device_status) {
+    int h = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DSMC_CUDA(cudaMemcpyAsync(&h, ws, sizeof(int), cudaMemcpyDeviceToHost, s), "status copy");
+    DSMC_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+    *device_status = static_cast<dsmc_status_t>(h);
+  }
+  return DSMC_OK;
 }
 
 dsmc_status_t dsmc_stream_status(void* ws, void* stream, dsmc_status_t* device_status) {

@@ -67,7 +67,8 @@ _lock = threading.Lock()
 
 EXPORTS = ["dsmc_status_string", "dsmc_last_error", "dsmc_state_sizes", "dsmc_workspace_size",
            "dsmc_init_particles", "dsmc_merge_level", "dsmc_resolve", "dsmc_smooth",
-           "dsmc_conditional_smooth", "dsmc_stream_status", "dsmc_profile_enable",
+           "dsmc_conditional_smooth", "dsmc_smooth_noalloc", "dsmc_stream_status",
+           "dsmc_profile_enable",
            "dsmc_profile_read", "dsmc_debug_philox", "dsmc_debug_merge_weights"]
 
 
@@ -104,6 +105,8 @@ def load(build_if_needed: bool = False) -> C.CDLL:
         lib.dsmc_smooth.argtypes = [cfgp, modp, prop_p, vp, statp, vp, vp, vp, vp, vp, sz, vp]
         lib.dsmc_conditional_smooth.argtypes = [cfgp, modp, prop_p, vp, vp, vp, statp, vp, vp, vp,
                                                 vp, sz, vp]
+        lib.dsmc_smooth_noalloc.argtypes = [cfgp, modp, prop_p, vp, statp, vp, vp, vp, vp,
+                                             C.POINTER(C.c_int), vp]
         lib.dsmc_stream_status.argtypes = [vp, vp, C.POINTER(C.c_int)]
         lib.dsmc_profile_enable.argtypes = [C.c_int]
         lib.dsmc_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64),
@@ -215,6 +218,16 @@ def dsmc_conditional_smooth(cfg, model, prop, y, x_ref_in, x_ref_out, state, tra
                                           _ptr(y), _ptr(x_ref_in), _ptr(x_ref_out), C.byref(state),
                                           _ptr(traj), _ptr(mean), _ptr(logL), _ptr(ws), ws.numel(),
                                           _stream(stream)), "dsmc_conditional_smooth")
+
+
+def dsmc_smooth_noalloc(cfg, model, prop, y, state, traj, mean, m2, logL, stream=None) -> int:
+    """dsmc_smooth on the library's static scratch (no workspace argument, no allocation);
+    returns the device status of the smoothing (the call synchronises the stream)."""
+    st = C.c_int(0)
+    _check(load().dsmc_smooth_noalloc(C.byref(cfg), C.byref(model.struct), C.byref(prop), _ptr(y),
+                                      C.byref(state), _ptr(traj), _ptr(mean), _ptr(m2), _ptr(logL),
+                                      C.byref(st), _stream(stream)), "dsmc_smooth_noalloc")
+    return int(st.value)
 
 
 def dsmc_stream_status(ws, stream=None) -> int:
