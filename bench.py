@@ -5,7 +5,8 @@ oracle baselines.
 A step is one full smoothing of one synthetic sequence: Algorithm 2 init, every level of
 Algorithm 6 (prologue, fused exp / tile-sum, three-stage pair sampler, map epilogue) and
 the trajectory resolve with fused means.  Default workload: the 8-dimensional
-linear-Gaussian model, K = 1024 steps, N = 1024 particles, FP32.
+linear-Gaussian model, K = 1024 steps, N = 1024 particles, cross term on the tensor cores
+in TF32 (``--compute fp32`` for the CUDA-core form).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload NAME]
 
@@ -32,6 +33,14 @@ UNIT = "N·T/s"
 MUFU_EX2_PER_CLK_SM = 32       # measured on GB300 (ex2 probe), twice B200's 16
 FMA_PER_CLK_SM = 128
 SMS = 152
+
+# DRAM bytes (read + write) per launch of the cross-term / tile-sum kernel, mean over the
+# ten levels of one lgssm_d8 K = N = 1024 smoothing, from one ncu capture of the kernel
+# revision named; None once that kernel has changed since the counters were taken.
+TRAFFIC_PER_LAUNCH = {
+    ("lgssm_d8", "fp32"): {"bytes": 19.91e6, "kernel": "rowsum_kernel<8,4>"},
+    ("lgssm_d8", "tf32"): {"bytes": 8.96e6, "kernel": "rowsum_tc_kernel<TF32>, beta staged in smem"},
+}
 
 WORKLOADS = {
     "lgssm_d8": dict(K=1024, N=1024, resampler="dense"),
@@ -273,10 +282,12 @@ def run_ours(args):
                 "fma_bound_frac": (achieved / (FMA_PER_CLK_SM / (d + 2) * SMS * sm_max * 1e-3)
                                    if achieved else None),
                 "avg_launch_ms": rs_ms / max(rs_n, 1), "launches": rs_n,
-                "traffic": None}
+                "traffic": (TRAFFIC_PER_LAUNCH.get((args.workload, args.compute)) or {}).get("bytes"),
+                "traffic_unit": "B per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "tf32": "tf32+f32", "bf16": "bf16+f32"}[args.compute],
             "data": "synthetic",
             "config": {"workload": args.workload, "K": K, "N": N, "dx": d,
                        "resampler": spec["resampler"],
@@ -299,11 +310,11 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lgssm_d8", choices=sorted(WORKLOADS))
-    ap.add_argument("--compute", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--compute", default="tf32", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
