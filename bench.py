@@ -39,7 +39,7 @@ SMS = 152
 # revision named; None once that kernel has changed since the counters were taken.
 TRAFFIC_PER_LAUNCH = {
     ("lgssm_d8", "fp32"): {"bytes": 19.91e6, "kernel": "rowsum_kernel<8,4>"},
-    ("lgssm_d8", "tf32"): {"bytes": 8.96e6, "kernel": "rowsum_tc_kernel<TF32>, beta staged in smem"},
+    ("lgssm_d8", "tf32"): {"bytes": None, "kernel": "rowsum_tc_kernel<TF32, 2 K planes>, exponent in the MMA"},
 }
 
 WORKLOADS = {

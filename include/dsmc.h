@@ -94,12 +94,18 @@ typedef struct {
   int K;                      /* time steps, >= 1 */
   int N;                      /* particles, >= 1 (>= 2 when conditional); <= 16384 dense */
   int compute;                /* cross-term precision: DSMC_FP32 (CUDA cores, default),
-                                 DSMC_TF32 or DSMC_BF16 (tensor cores) */
+                                 DSMC_TF32 (dx <= 8) or DSMC_BF16 (dx <= 16) on the tensor
+                                 cores: the whole base-2 exponent alpha_i + beta_j + u_i.v_j
+                                 is one MMA, alpha and beta entering as two-term splits in
+                                 the MMA type; FP32 accumulate, exp and sums; dense N <= 4096 */
   int resampler;              /* DSMC_MULTINOMIAL (dense, Algorithm 1) or DSMC_RS (Alg. 8) */
   uint64_t seed;              /* Philox key */
   uint32_t counter_base;      /* < 2^28; e.g. the particle-Gibbs sweep index */
   uint32_t rs_max_attempts;   /* cap per slot for DSMC_RS (0 means 2^20) */
   int max_merges_per_launch;  /* 0 = default; bounds the workspace */
+  int fused_max_merges;       /* dense sampler: levels with at most this many combinations run
+                                 as one fused launch (a thread-block cluster per combination,
+                                 FP32 cross term); 0 = default (64), < 0 = never */
 } dsmc_config_t;
 
 /* Caller-owned DEVICE state of one smoothing (sizes from dsmc_state_sizes()).

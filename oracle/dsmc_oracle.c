@@ -734,13 +734,14 @@ int orc_model_logdens(const orc_model* m, int K, const double* y, int t, const d
  * so it does not depend on any summation order:
  *   row:    Rq_i = trunc(r_i 2^40); T = floor(U S / 2^64), U = (w0 << 32) | w1, S = sum Rq;
  *           row = #{i : Rq_0 + ... + Rq_i <= T}
- *   tile:   q_k = q40(t_ik; max_k t_ik), T = floor(w2 Q / 2^32), Q = sum q;
+ *   tile:   q_k = q24(t_ik; max_k t_ik), T = floor(w2 Q / 2^32), Q = sum q;
  *           tile = #{k : prefix <= T}
- *   column: q_j = q40(e_ij; t_ik) over the tile's columns, the same with w3
- * where q40(x; ref) = floor(x 2^(40 - E)) with 2^(E-2) <= ref < 2^(E-1) (one binade of
- * headroom), computed on the bit patterns as (significand << 16) >> (E_ref - E_x) with the
- * shift clamped to [0, 63] (the clamp at 0 saturates weights above twice their reference,
- * which the device never produces); zero, negative, subnormal and non-finite x give 0.  A zero
+ *   column: q_j = q24(e_ij; t_ik) over the tile's columns, the same with w3
+ * where q24(x; ref) = floor(x 2^(24 - E)) with 2^(E-2) <= ref < 2^(E-1) (one binade of
+ * headroom), computed on the bit patterns as significand >> (E_ref - E_x) with the shift
+ * clamped to [0, 31] (the clamp at 0 saturates weights above twice their reference, which
+ * the device never produces); zero, negative, subnormal and non-finite x give 0.  A weight
+ * equal to its reference keeps 23 significant bits, as many as its FP32 value.  A zero
  * weight is never chosen; a tile whose column weights are all zero yields its first column.
  * Slots n in [n0, n1) use the counter (n, gid, DENSE | base<<4, 0). */
 static uint64_t mulhi64(uint64_t a, uint64_t b) {
@@ -767,7 +768,7 @@ static int ref_exponent(float ref) {
   return be + 1;
 }
 
-static uint64_t q40(float x, int ref_be) {
+static uint64_t q24(float x, int ref_be) {
   uint32_t b = float_bits(x);
   if (b >> 31) return 0;
   int be = (int)((b >> 23) & 0xFFu);
@@ -775,8 +776,8 @@ static uint64_t q40(float x, int ref_be) {
   uint64_t m = (uint64_t)((b & 0x7FFFFFu) | 0x800000u);
   int r = ref_be - be;               /* >= 1 for every weight below its reference */
   if (r < 0) r = 0;                  /* saturate (never reached by the device's weights) */
-  if (r > 63) r = 63;
-  return (m << 16) >> r;
+  if (r > 31) r = 31;
+  return m >> r;
 }
 
 /* index of the first prefix sum of q[0..n) exceeding floor(w Q / 2^32); 0 if all are zero */
@@ -818,12 +819,12 @@ int orc_kp_dense_pairs(int N, int B, const float* r, const float* t, const float
     float tmax = 0.0f;
     for (int k = 0; k < nT; ++k) tmax = ti[k] > tmax ? ti[k] : tmax;
     int rbe = ref_exponent(tmax);
-    for (int k = 0; k < nT; ++k) q[k] = q40(ti[k], rbe);
+    for (int k = 0; k < nT; ++k) q[k] = q24(ti[k], rbe);
     int k = fixed_pick(q, nT, w[2]);
     int j0 = k * B;
     int width = (j0 + B <= N) ? B : N - j0;
     int tbe = ref_exponent(ti[k]);
-    for (int j = 0; j < width; ++j) q[j] = q40(e[(size_t)i * N + j0 + j], tbe);
+    for (int j = 0; j < width; ++j) q[j] = q24(e[(size_t)i * N + j0 + j], tbe);
     li[n - n0] = i;
     ri[n - n0] = j0 + fixed_pick(q, width, w[3]);
   }

@@ -11,6 +11,9 @@
 
 namespace dsmc {
 int rowsum_rows_per_thread(int D);
+cudaError_t launch_level_fused(int D, const MergeArgs& a, const void* mp, int C, cudaStream_t s);
+cudaError_t level_fused_max_clusters(int D, const MergeArgs& a, int C, int* n);
+size_t fused_level_smem(int D, int N, int C);
 cudaError_t launch_k1_star(const float* logw, int N, uint64_t seed, uint32_t base, int32_t* star,
                            cudaStream_t s);
 }  // namespace dsmc
@@ -85,14 +88,14 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Plan {
   int K, N, d, D, L;
-  int compute, Nr;
+  int compute, Nr, planes;
   int B, nT, nTp;
   int Mc;
   int R, rows_per_cta;
   bool dense;
   int level_off[33];
   size_t o_status, o_U, o_alpha, o_V, o_beta, o_shift, o_logbar, o_inc, o_T, o_rw, o_rowsum, o_cum,
-      o_delta, o_first, o_last, o_star, o_Ub, o_Vb, o_betap, total;
+      o_delta, o_first, o_last, o_star, o_Ub, o_Vb, total;
 };
 
 void chunking(const Plan& p, int mc, int& CH, int& CW) {
@@ -125,6 +128,10 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p) {
   p.dense = cfg->resampler != DSMC_RS;
   p.compute = cfg->compute;
   p.Nr = (p.N + 127) / 128 * 128;
+  {
+    const int kp = p.compute == DSMC_BF16 ? 16 : 8;
+    p.planes = (p.D + 4 + kp - 1) / kp;
+  }
   const int nT0 = std::min((p.N + 31) / 32, 64);
   const int per = (p.N + nT0 - 1) / nT0;
   p.B = 32 * ((per + 31) / 32);
@@ -166,9 +173,8 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p) {
   p.o_last = take(2 * (size_t)p.K * p.N * sizeof(int32_t));
   p.o_star = take(2 * sizeof(int32_t));
   const bool tc = p.compute != DSMC_FP32;
-  p.o_Ub = take(tc ? (size_t)p.Mc * p.Nr * 32 : 0);
-  p.o_Vb = take(tc ? (size_t)p.Mc * p.Nr * 32 : 0);
-  p.o_betap = take(tc ? (size_t)p.Mc * p.Nr * sizeof(float) : 0);
+  p.o_Ub = take(tc ? (size_t)p.Mc * p.planes * p.Nr * 32 : 0);
+  p.o_Vb = take(tc ? (size_t)p.Mc * p.planes * p.Nr * 32 : 0);
   p.total = o;
 }
 
@@ -193,7 +199,6 @@ WsPtrs ws_ptrs(const Plan& p, void* ws) {
   w.star = reinterpret_cast<int32_t*>(b + p.o_star);
   w.Ub = reinterpret_cast<unsigned char*>(b + p.o_Ub);
   w.Vb = reinterpret_cast<unsigned char*>(b + p.o_Vb);
-  w.betap = reinterpret_cast<float*>(b + p.o_betap);
   return w;
 }
 
@@ -394,6 +399,7 @@ MergeArgs merge_args(const Plan& p, const dsmc_config_t* cfg, const float* y, in
   a.resampler = cfg->resampler;
   a.compute = cfg->compute;
   a.Nr = p.Nr;
+  a.mma_planes = p.planes;
   a.seed = cfg->seed;
   a.base = cfg->counter_base;
   a.rs_max = cfg->rs_max_attempts ? cfg->rs_max_attempts : (1u << 20);
@@ -429,16 +435,65 @@ dsmc_status_t do_init(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& m
   return DSMC_OK;
 }
 
+// The fused single-launch level (dense sampler only): cluster size C for a level of M
+// combinations, or 0 for the split path.  C doubles while the level still fills at most
+// one wave of the SMs and every CTA keeps at least 32 rows; the shared-memory footprint
+// (all N column terms per CTA) must fit one SM.
+constexpr int kDefaultFusedMaxMerges = 64;
+constexpr size_t kFusedSmemLimit = 220 * 1024;
+
+int fused_policy(const Plan& p, const dsmc_config_t* cfg, int M) {
+  if (!p.dense) return 0;
+  const int cap = cfg->fused_max_merges == 0 ? kDefaultFusedMaxMerges : cfg->fused_max_merges;
+  if (cap < 0 || M > cap) return 0;
+  int C = 1;
+  while (C < 16 && (size_t)M * C * 2 <= 152 && p.N / (2 * C) >= 32) C *= 2;
+  if (fused_level_smem(p.D, p.N, C) > kFusedSmemLimit) return 0;
+  return C;
+}
+
+// Largest cluster size <= C that the device can schedule for this shape (queried once).
+int fused_schedulable(const Plan& p, const MergeArgs& a, int C) {
+  static std::mutex mu;
+  static std::vector<std::pair<long long, int>> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const long long key = ((((long long)dev * 64 + p.D) * 32768 + p.N) * 64 + a.B) * 32 + C;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    for (auto& kv : cache)
+      if (kv.first == key) return kv.second;
+  }
+  int ok = 0;
+  for (int c = C; c >= 1 && !ok; c /= 2) {
+    int n = 0;
+    if (level_fused_max_clusters(p.D, a, c, &n) == cudaSuccess && n > 0) ok = c;
+  }
+  cudaGetLastError();
+  std::lock_guard<std::mutex> g(mu);
+  cache.emplace_back(key, ok);
+  return ok;
+}
+
 dsmc_status_t do_level(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& mp,
                        const float* y, int level, int conditional, dsmc_state_t* st,
                        const WsPtrs& w, cudaStream_t s) {
   const int M = merges_at_level(p.K, level);
+  const int Cf = fused_policy(p, cfg, M);
   for (int m0 = 0; m0 < M; m0 += p.Mc) {
     MergeArgs a = merge_args(p, cfg, y, level, conditional, st, w);
     a.m0 = m0;
     a.mc = std::min(p.Mc, M - m0);
     a.gid0 = p.level_off[level] + m0;
     chunking(p, a.mc, a.CH, a.CW);
+    if (Cf > 0) {
+      const int C = fused_schedulable(p, a, Cf);
+      if (C > 0) {
+        DSMC_CUDA(launch_level_fused(p.D, a, mp.bytes, C, s), "fused level kernel");
+        prof_count(1);
+        continue;
+      }
+    }
     DSMC_CUDA(launch_prologue(p.D, a, mp.bytes, s), "prologue kernel");
     if (p.dense) {
       DSMC_CUDA(prof_begin(s), "profile event");

@@ -109,26 +109,27 @@ __device__ __forceinline__ float log_h(const ModelParams<D>& mp, const float* yt
   return mp.log_h_norm - 0.5f * quad_form<D>(mp.Ri, r);
 }
 
-// log q_t(x) for the diagonal Gaussian proposal with mean qm and standard deviation qs.
+// log q_t(x) for the diagonal Gaussian proposal with mean qm and standard deviation s_k,
+// given the per-t constants qinv_k = 1 / s_k and qnorm = -sum_k log s_k - d/2 log(2 pi).
 template <int D>
-__device__ __forceinline__ float log_q(int d, const float* qm, const float* qs, const float* x) {
+__device__ __forceinline__ float log_q(int d, const float* qm, const float* qinv, float qnorm, const float* x) {
   float s = 0.f;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     if (k < d) {
-      const float z = (x[k] - qm[k]) / qs[k];
-      s += -0.5f * z * z - logf(qs[k]) - kHalfLog2Pi;
+      const float z = (x[k] - qm[k]) * qinv[k];
+      s = fmaf(z, z, s);
     }
   }
-  return s;
+  return fmaf(-0.5f, s, qnorm);
 }
 
 // log nu_t(x) (Definition 1): q_t itself, or h_t(y_t | .) normalised over x
 // (N(x; y_t, R) for the linear-Gaussian model; h_t * |y_t| for SV).
 template <int D>
 __device__ __forceinline__ float log_nu(const ModelParams<D>& mp, const float* yt, const float* qm,
-                                        const float* qs, const float* x) {
-  if (mp.nu == DSMC_NU_EQ_Q) return log_q<D>(mp.d, qm, qs, x);
+                                        const float* qinv, float qnorm, const float* x) {
+  if (mp.nu == DSMC_NU_EQ_Q) return log_q<D>(mp.d, qm, qinv, qnorm, x);
   const float lh = log_h<D>(mp, yt, x);
   return mp.kind == DSMC_MODEL_SV ? lh + logf(fabsf(yt[0])) : lh;
 }
@@ -161,6 +162,18 @@ __device__ __forceinline__ void proposal_at(const ModelParams<D>& mp, const floa
       qs[k] = 1.f;
     }
   }
+}
+
+// The per-t constants of log_q from the proposal standard deviations.
+template <int D>
+__device__ __forceinline__ float proposal_consts(int d, const float* qs, float* qinv) {
+  float lsum = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    qinv[k] = 1.f / qs[k];
+    if (k < d) lsum += logf(qs[k]);
+  }
+  return -lsum - (float)d * kHalfLog2Pi;
 }
 
 __device__ __forceinline__ void record_status(int* status, int code) {

@@ -22,6 +22,8 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
 #pragma unroll
   for (int k = 0; k < D; ++k) yt[k] = k < d ? a.y[(size_t)t * d + k] : 0.f;
   proposal_at<D>(mp, a.y, t, qm, qs);
+  float qinv[D];
+  const float qnorm = proposal_consts<D>(d, qs, qinv);
   float logsd = 0.f;
 #pragma unroll
   for (int k = 0; k < D; ++k)
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
     } else if (mp.nu == DSMC_NU_EQ_Q) {
       l = 0.f;
     } else {
-      l = log_nu<D>(mp, yt, qm, qs, x) - lq;
+      l = log_nu<D>(mp, yt, qm, qinv, qnorm, x) - lq;
     }
     if (isnan(l)) bad = true;
     lw[n] = l;

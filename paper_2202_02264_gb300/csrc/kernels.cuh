@@ -27,13 +27,12 @@ struct WsPtrs {
   int32_t* last;     // [2][K][N]    last-time particle index of each block
   int32_t* star;     // [2]          root pair of the next reference (conditional mode)
   double* inc;       // [Mc]         log normalising-constant increments
-  // tensor-core operands (compute = DSMC_TF32 / DSMC_BF16): U and V rounded to the MMA
-  // type, K padded to 32 bytes per row, in the canonical no-swizzle K-major layout of
-  // 8-row x 16-byte core matrices (row group g at g*256 B, 16-byte K chunk c at c*128 B),
-  // rows padded to a multiple of 128; beta copied with the same padded stride.
-  unsigned char* Ub; // [Mc][Nr][32 B]
-  unsigned char* Vb; // [Mc][Nr][32 B]
-  float* betap;      // [Mc][Nr]
+  // tensor-core operands (compute = DSMC_TF32 / DSMC_BF16): [u, alpha_hi, alpha_lo, 1, 1]
+  // and [v, 1, 1, beta_hi, beta_lo] rounded to the MMA type, in 32-byte K planes, each
+  // plane in the canonical no-swizzle K-major layout (8-row x 16-byte core matrices, row
+  // group g at g*256 B, chunk c at c*128 B), rows padded to a multiple of 128.
+  unsigned char* Ub; // [Mc][planes][Nr][32 B]
+  unsigned char* Vb; // [Mc][planes][Nr][32 B]
 };
 
 struct MergeArgs {
@@ -49,6 +48,7 @@ struct MergeArgs {
   int resampler;
   int compute;       // DSMC_FP32, DSMC_TF32 or DSMC_BF16
   int Nr;            // N rounded up to 128 (tensor-core operand rows)
+  int mma_planes;    // 32-byte K planes of the tensor-core operands
   uint64_t seed;
   uint32_t base;
   uint32_t rs_max;

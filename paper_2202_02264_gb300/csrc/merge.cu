@@ -23,59 +23,78 @@
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
+#include "merge_parts.cuh"
 
 namespace dsmc {
 
 namespace {
 
+using namespace parts;
+
 constexpr int kEpiThreads = 256;
 constexpr int kRsThreads = 128;
 
-// The base-2 exponent of pair (i, j): (alpha_i + beta_j) then u_i . v_j by FMAs in
-// ascending k.  Every kernel that evaluates a pair uses this one function, so the
-// row-sum pass and the sampler's recomputation agree bit for bit.
-template <int D>
-__device__ __forceinline__ float pair_exponent(const float* u, float al, const float* v, float be) {
-  float acc = __fadd_rn(al, be);
-#pragma unroll
-  for (int k = 0; k < D; ++k) acc = __fmaf_rn(u[k], v[k], acc);
-  return acc;
+// Tensor-core operand rows.  The K dimension holds the D state coordinates followed by
+// four extra columns that carry the per-row and per-column exponent terms exactly as
+// two-term (hi + lo) splits in the MMA type:
+//   row i    (U): [u_i, alpha_hi, alpha_lo, 1, 1]
+//   column j (V): [v_j, 1, 1, beta_hi, beta_lo]
+// so that the MMA accumulates alpha_i + beta_j + u_i . v_j.  K is cut into 32-byte planes
+// (16 BF16 or 8 TF32 values); plane p of a combination is a [Nr][32 B] array in the
+// canonical no-swizzle K-major layout (8-row x 16-byte core matrices: row group g at
+// g*256 B, 16-byte chunk c at c*128 B).  Entries beyond D + 4 are zero.
+__host__ __device__ __forceinline__ int mma_planes(int D, int compute) {
+  const int kp = compute == DSMC_BF16 ? 16 : 8;
+  return (D + 4 + kp - 1) / kp;
 }
 
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_max(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// One row of a tensor-core operand: element k of row r at (r/8)*256 + (k/epc)*128 +
-// (r%8)*16 + (k%epc)*eb bytes (8-row x 16-byte core matrices, K = 32 bytes: 16 BF16 or 8
-// TF32 values; entries beyond D are zero).  TF32 is rounded to nearest.
-template <int D>
-__device__ __forceinline__ void store_mma_row(unsigned char* base, int r, const float* x, int compute) {
+template <int D, int KIND>
+__device__ __forceinline__ void store_mma_row_t(unsigned char* base, int Nr, int r, const float* x,
+                                                const float* ext) {
+  constexpr int kp = KIND == DSMC_BF16 ? 16 : 8;      // values per 32-byte plane
+  constexpr int kc = KIND == DSMC_BF16 ? 8 : 4;       // values per 16-byte chunk
+  constexpr int np = (D + 4 + kp - 1) / kp;
   unsigned char* row = base + (size_t)(r / 8) * 256 + (size_t)(r % 8) * 16;
+#pragma unroll
+  for (int ch = 0; ch < 2 * np; ++ch) {  // one 16-byte store per chunk
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (KIND == DSMC_BF16) {
+        const int k0 = ch * kc + 2 * q;
+        const float v0 = k0 < D ? x[k0] : (k0 < D + 4 ? ext[k0 - D] : 0.f);
+        const float v1 = k0 + 1 < D ? x[k0 + 1] : (k0 + 1 < D + 4 ? ext[k0 + 1 - D] : 0.f);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+        w[q] = *reinterpret_cast<const uint32_t*>(&h);
+      } else {
+        const int k = ch * kc + q;
+        const float v = k < D ? x[k] : (k < D + 4 ? ext[k - D] : 0.f);
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[q]) : "f"(v));
+      }
+    }
+    *reinterpret_cast<uint4*>(row + (size_t)(ch / 2) * Nr * 32 + (ch % 2) * 128) =
+        make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void store_mma_row(unsigned char* base, int Nr, int r, const float* x,
+                                              const float* ext, int compute) {
+  if (compute == DSMC_BF16) store_mma_row_t<D, DSMC_BF16>(base, Nr, r, x, ext);
+  else store_mma_row_t<D, DSMC_TF32>(base, Nr, r, x, ext);
+}
+
+// hi + lo split of x in the MMA type (the two values the tensor core reads).
+__device__ __forceinline__ void split_mma(float x, int compute, float* hi, float* lo) {
   if (compute == DSMC_BF16) {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const float v = k < D ? x[k] : 0.f;
-      *reinterpret_cast<__nv_bfloat16*>(row + (k / 8) * 128 + (k % 8) * 2) = __float2bfloat16_rn(v);
-    }
+    *hi = __bfloat162float(__float2bfloat16_rn(x));
+    *lo = __bfloat162float(__float2bfloat16_rn(x - *hi));
   } else {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float v = k < D ? x[k] : 0.f;
-      uint32_t t;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
-      *reinterpret_cast<uint32_t*>(row + (k / 4) * 128 + (k % 4) * 4) = t;
-    }
+    uint32_t t;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
+    *hi = __uint_as_float(t);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x - *hi));
+    *lo = __uint_as_float(t);
   }
 }
 
@@ -108,6 +127,8 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
 #pragma unroll
   for (int k = 0; k < D; ++k) yc[k] = k < d ? a.y[(size_t)c * d + k] : 0.f;
   proposal_at<D>(mp, a.y, c, qm, qs);
+  float qinv[D];
+  const float qnorm = proposal_consts<D>(d, qs, qinv);
 
   float* V = a.ws.V + (size_t)s * N * D;
   float* beta = a.ws.beta + (size_t)s * N;
@@ -129,14 +150,8 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
   float bmax = -INFINITY;
   bool bad = false, corrupt = false;
   for (int j = threadIdx.x; j < N; j += kProThreads) {
-    const int idx = right_leaf ? j : checked_index(firstR[j], N, corrupt);
-    const float* xp = a.X + ((size_t)c * N + idx) * d;
     float x[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) x[k] = k < d ? xp[k] : 0.f;
-    const float bj = right_leaf ? a.logw[(size_t)c * N + j] : -a.logN;
-    const float g = log_h<D>(mp, yc, x) - log_nu<D>(mp, yc, qm, qs, x);
-    const float bp = bj + g;
+    const float bp = column_bprime<D>(mp, a, c, yc, qm, qinv, qnorm, firstR, right_leaf, j, x, corrupt);
     bad |= isnan(bp);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -174,59 +189,43 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
   for (int j = threadIdx.x; j < N; j += kProThreads) {
     float v[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) v[k] = V[(size_t)j * D + k] - mu[k];
+    for (int k = 0; k < D; ++k) v[k] = V[(size_t)j * D + k];
+    beta[j] = column_beta<D>(mp, v, mu, beta[j], bstar);
 #pragma unroll
     for (int k = 0; k < D; ++k) V[(size_t)j * D + k] = v[k];
-    beta[j] = kLog2e * (beta[j] - bstar - 0.5f * quad_form<D>(mp.Qi, v));
     if (a.compute != DSMC_FP32) {
-      store_mma_row<D>(a.ws.Vb + (size_t)s * a.Nr * 32, j, v, a.compute);
-      a.ws.betap[(size_t)s * a.Nr + j] = beta[j];
+      float ext[4];
+      ext[0] = 1.f;
+      ext[1] = 1.f;
+      split_mma(beta[j], a.compute, &ext[2], &ext[3]);
+      store_mma_row<D>(a.ws.Vb + (size_t)s * a.Nr * a.mma_planes * 32, a.Nr, j, v, ext, a.compute);
     }
   }
   if (a.compute != DSMC_FP32) {  // zero the padding rows of the tensor-core operands
     const float zero[D] = {};
+    const float zext[4] = {0.f, 0.f, 0.f, 0.f};
     for (int j = N + threadIdx.x; j < a.Nr; j += kProThreads) {
-      store_mma_row<D>(a.ws.Vb + (size_t)s * a.Nr * 32, j, zero, a.compute);
-      store_mma_row<D>(a.ws.Ub + (size_t)s * a.Nr * 32, j, zero, a.compute);
-      a.ws.betap[(size_t)s * a.Nr + j] = 0.f;
+      store_mma_row<D>(a.ws.Vb + (size_t)s * a.Nr * a.mma_planes * 32, a.Nr, j, zero, zext, a.compute);
+      store_mma_row<D>(a.ws.Ub + (size_t)s * a.Nr * a.mma_planes * 32, a.Nr, j, zero, zext, a.compute);
     }
   }
   // pass 2b: rows  w_i = A xL_i + c - mu,  u_i = log2(e) Q^-1 w_i,
   //                alpha_i = -log2(e) 1/2 w_i' Q^-1 w_i  (B* is folded into beta)
   float amax = -INFINITY;
   for (int i = threadIdx.x; i < N; i += kProThreads) {
-    const int idx = left_leaf ? i : checked_index(lastL[i], N, corrupt);
-    const float* xp = a.X + ((size_t)(c - 1) * N + idx) * d;
-    float x[D], w[D], u[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) x[k] = k < d ? xp[k] : 0.f;
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-      float acc = mp.c[r];
-#pragma unroll
-      for (int k = 0; k < D; ++k) acc = fmaf(mp.A[r * D + k], x[k], acc);
-      w[r] = acc - mu[r];
-    }
-    float q = 0.f;
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-      float acc = 0.f;
-#pragma unroll
-      for (int k = 0; k < D; ++k) acc = fmaf(mp.Qi[r * D + k], w[k], acc);
-      u[r] = acc;
-      q = fmaf(w[r], acc, q);
-    }
-    const float ai = left_leaf ? a.logw[(size_t)(c - 1) * N + i] : -a.logN;
+    float ul[D], ai;
+    const float al = row_terms<D>(mp, a, c, lastL, left_leaf, i, mu, ul, ai, corrupt);
     bad |= isnan(ai);
 #pragma unroll
-    for (int k = 0; k < D; ++k) U[(size_t)i * D + k] = kLog2e * u[k];
+    for (int k = 0; k < D; ++k) U[(size_t)i * D + k] = ul[k];
     if (a.compute != DSMC_FP32) {
-      float ul[D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) ul[k] = kLog2e * u[k];
-      store_mma_row<D>(a.ws.Ub + (size_t)s * a.Nr * 32, i, ul, a.compute);
+      float ext[4];
+      split_mma(al, a.compute, &ext[0], &ext[1]);
+      ext[2] = 1.f;
+      ext[3] = 1.f;
+      store_mma_row<D>(a.ws.Ub + (size_t)s * a.Nr * a.mma_planes * 32, a.Nr, i, ul, ext, a.compute);
     }
-    alpha[i] = -0.5f * kLog2e * q;
+    alpha[i] = al;
     shift[i] = (double)ai + (double)mp.log_f_max + (double)bstar;
     amax = fmaxf(amax, ai);
   }
@@ -334,104 +333,6 @@ __global__ void __launch_bounds__(128) rowsum_kernel(MergeArgs a, int SC) {
   }
 }
 
-// Block-wide inclusive scan of N uint64 values in shared memory (in place).
-__device__ void block_scan_u64(unsigned long long* v, int N, unsigned long long* warp_tot) {
-  const int NT = blockDim.x;
-  const int per = (N + NT - 1) / NT;
-  const int lo = min(threadIdx.x * per, N), hi = min(lo + per, N);
-  unsigned long long run = 0;
-  for (int i = lo; i < hi; ++i) run += v[i];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long incl = run;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) warp_tot[warp] = incl;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long acc = 0;
-    for (int w = 0; w < NT / 32; ++w) {
-      const unsigned long long t = warp_tot[w];
-      warp_tot[w] = acc;
-      acc += t;
-    }
-  }
-  __syncthreads();
-  unsigned long long pre = warp_tot[warp] + incl - run;
-  for (int i = lo; i < hi; ++i) {
-    pre += v[i];
-    v[i] = pre;
-  }
-  __syncthreads();
-}
-
-// Exact-max recomputation of one row (rare: used when the bound-shifted row total fell
-// below 2^-64).  One warp; writes the row's tile sums relative to the new shift, returns
-// the row total (lane-local sums, then a butterfly) and the extra base-2 shift.
-template <int D>
-__device__ void recompute_row(const MergeArgs& a, int s, int i, float* out_sum, float* out_delta) {
-  const int N = a.N, B = a.B;
-  const int lane = threadIdx.x & 31;
-  const float* U = a.ws.U + (size_t)s * N * D;
-  const float* V = a.ws.V + (size_t)s * N * D;
-  const float* beta = a.ws.beta + (size_t)s * N;
-  float u[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) u[k] = U[(size_t)i * D + k];
-  const float al = a.ws.alpha[(size_t)s * N + i];
-  float mx = -INFINITY;
-  for (int j = lane; j < N; j += 32) mx = fmaxf(mx, pair_exponent<D>(u, al, V + (size_t)j * D, beta[j]));
-  mx = warp_max(mx);
-  if (!(mx > -INFINITY)) mx = 0.f;  // all -inf: the row keeps weight zero
-  float* T = a.ws.T + ((size_t)s * N + i) * a.nTp;
-  float tot = 0.f;
-  for (int kt = lane; kt < a.nT; kt += 32) {
-    const int jb = kt * B, je = min(jb + B, N);
-    float ts = 0.f;
-    for (int j = jb; j < je; ++j)
-      ts = __fadd_rn(ts, ex2(pair_exponent<D>(u, al, V + (size_t)j * D, beta[j]) - mx));
-    T[kt] = ts;
-    tot += ts;
-  }
-  tot = warp_sum(tot);
-  *out_sum = tot;
-  *out_delta = mx;
-}
-
-// The fixed-point image floor(x 2^(40 - E)) of a weight x below twice its reference
-// (2^(E-2) <= ref < 2^(E-1), ref_be = the reference's biased exponent + 1):
-// (significand << 16) >> (ref_be - be), the shift clamped to [0, 63].  Exact, order-free and
-// branch-free; zero, negative, subnormal and non-finite x give 0.
-__device__ __forceinline__ unsigned long long q40(float x, int ref_be) {
-  const uint32_t b = __float_as_uint(x);
-  const int be = (int)((b >> 23) & 0xFFu);
-  const bool zero = (b >> 31) || be == 0 || be == 0xFF;
-  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u) << 16;
-  const int r = min(max(ref_be - be, 0), 63);
-  return zero ? 0ull : (m >> r);
-}
-
-__device__ __forceinline__ int ref_exponent(float ref) {
-  return (int)((__float_as_uint(ref) >> 23) & 0xFFu) + 1;
-}
-
-// Sum of a row's tile weights in ascending tile order (vector loads).
-__device__ __forceinline__ float row_total(const float* row, int nT, int nTp) {
-  const float4* t4 = reinterpret_cast<const float4*>(row);
-  float t = 0.f;
-  for (int k4 = 0; k4 < nTp / 4; ++k4) {
-    const float4 v = t4[k4];
-    const int k = 4 * k4;
-    if (k < nT) t = __fadd_rn(t, v.x);
-    if (k + 1 < nT) t = __fadd_rn(t, v.y);
-    if (k + 2 < nT) t = __fadd_rn(t, v.z);
-    if (k + 3 < nT) t = __fadd_rn(t, v.w);
-  }
-  return t;
-}
-
 // ---------------------------------------------------------------------------------------
 // Row CDF of one combination (one CTA):
 //   row totals s_i = sum of the row's tile weights in ascending tile order (thread per row,
@@ -455,8 +356,8 @@ __global__ void __launch_bounds__(kCdfThreads) rowcdf_kernel(MergeArgs a) {
   float* l2 = reinterpret_cast<float*>(smraw + (size_t)N * 8);                 // [N]
   int* under = reinterpret_cast<int*>(cum);  // rows that underflowed (before cum is built)
   __shared__ unsigned long long warp_tot[NW];
-  __shared__ double redd[NW];
-  __shared__ double M_s;
+  __shared__ float redf[NW];
+  __shared__ float M_s;
   __shared__ int n_under, nonfinite_s;
   if (threadIdx.x == 0) {
     n_under = 0;
@@ -481,7 +382,11 @@ __global__ void __launch_bounds__(kCdfThreads) rowcdf_kernel(MergeArgs a) {
   for (int q = warp; q < n_under; q += NW) {
     const int i = under[q];
     float si, dl;
-    recompute_row<D>(a, s, i, &si, &dl);
+    {
+      const float* U = a.ws.U + (size_t)s * N * D;
+      recompute_row<D, false>(U + (size_t)i * D, a.ws.alpha[(size_t)s * N + i], a.ws.V + (size_t)s * N * D,
+                       a.ws.beta + (size_t)s * N, N, a.B, nT, a.ws.T + ((size_t)s * N + i) * nTp, &si, &dl);
+    }
     __syncwarp();
     if (lane == 0) {
       si = row_total(Tt + (size_t)i * nTp, nT, nTp);
@@ -490,47 +395,41 @@ __global__ void __launch_bounds__(kCdfThreads) rowcdf_kernel(MergeArgs a) {
     }
   }
   __syncthreads();
-  double mloc = -INFINITY;
+  float mloc = -INFINITY;
   for (int i = threadIdx.x; i < N; i += kCdfThreads) {
     const float t = l2[i];
     rowsum[i] = t;
-    const float v = t > 0.f ? (float)(shift[i] * kLog2ed + (double)delta[i] + (double)log2f(t)) : -INFINITY;
+    const float v = row_log2_weight(shift[i], delta[i], t);
     l2[i] = v;
-    mloc = fmax(mloc, (double)v);
+    mloc = fmaxf(mloc, v);
   }
   mloc = warp_max(mloc);
-  if (lane == 0) redd[warp] = mloc;
+  if (lane == 0) redf[warp] = mloc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = redd[0];
-    for (int w = 1; w < NW; ++w) t = fmax(t, redd[w]);
+    float t = redf[0];
+    for (int w = 1; w < NW; ++w) t = fmaxf(t, redf[w]);
     M_s = t;
   }
   __syncthreads();
-  const double M = M_s;
+  const float M = M_s;
   const bool degenerate = !(M > -INFINITY) || isnan(M);
   float* rw = a.ws.rw + (size_t)s * N;
-  double sr = 0.0;
   for (int i = threadIdx.x; i < N; i += kCdfThreads) {
-    float r = degenerate ? 0.f : ex2(__fsub_rn(l2[i], (float)M));
-    if (!(r > 0.f)) r = 0.f;
-    if (r > 1.f) r = 1.f;
+    const float r = row_weight(l2[i], M, degenerate);
     rw[i] = r;
-    sr += (double)r;
     cum[i] = (unsigned long long)__float2ull_rz(r * 0x1p40f);
   }
   __syncthreads();
-  sr = warp_sum(sr);
-  if (lane == 0) redd[warp] = sr;
   block_scan_u64(cum, N, warp_tot);
   unsigned long long* gcum = a.ws.cum + (size_t)s * N;
   for (int i = threadIdx.x; i < N; i += kCdfThreads) gcum[i] = cum[i];
   if (threadIdx.x == 0) {
     int at, c, b;
     merge_geom(a.K, a.level, a.m0 + s, at, c, b);
-    double t = 0.0;
-    for (int w = 0; w < NW; ++w) t += redd[w];
-    const double inc = degenerate ? (double)NAN : M * kLn2d + log(t);
+    // Eq. (Lab): log of sum_ij exp(logW_ij) = M ln 2 + ln(sum_i r_i), the row-weight total
+    // taken from its exact fixed-point image
+    const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(cum[N - 1]);
     a.ws.inc[s] = inc;
     a.logL[at] = a.logL[at] + a.logL[c] + inc;
     if (degenerate || cum[N - 1] == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
@@ -538,201 +437,246 @@ __global__ void __launch_bounds__(kCdfThreads) rowcdf_kernel(MergeArgs a) {
   }
 }
 
-// Fixed-point pick over n <= 32 weights held in registers: q_k = q40(x_k; ref), Q = sum q,
-// T = w Q >> 32 (w a 32-bit uniform word), the first k whose prefix sum exceeds T.  The
-// images are recomputed in the second pass (cheap) rather than kept (64 registers).
-__device__ __forceinline__ int pick_regs(const float* x, int n, uint32_t w, int ref_be) {
-  unsigned long long Q = 0;
-#pragma unroll
-  for (int k = 0; k < 32; ++k) Q += (k < n) ? q40(x[k], ref_be) : 0ull;
-  if (Q == 0ull) return 0;
-  const unsigned long long T = __umul64hi((unsigned long long)w << 32, Q);
-  unsigned long long c = 0;
-  int idx = 0;
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    c += (k < n) ? q40(x[k], ref_be) : 0ull;
-    idx += (c <= T) ? 1 : 0;
-  }
-  return min(idx, n - 1);
-}
-
-// D floats of a row of U or V into registers (vector loads when D is a multiple of 4; the
-// rows are then 16-byte aligned).
-template <int D>
-__device__ __forceinline__ void load_row(const float* p, float* r) {
-  if ((D % 4) == 0) {
-    const float4* p4 = reinterpret_cast<const float4*>(p);
-#pragma unroll
-    for (int k = 0; k < D / 4; ++k) {
-      const float4 v = p4[k];
-      r[4 * k] = v.x;
-      r[4 * k + 1] = v.y;
-      r[4 * k + 2] = v.z;
-      r[4 * k + 3] = v.w;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < D; ++k) r[k] = p[k];
-  }
-}
-
 // ---------------------------------------------------------------------------------------
-// Pair draws (one thread per slot, many small CTAs per combination):
-//   row:    T = U64 * S >> 64 against the exact prefix sums (binary search, L1-cached);
-//   tile:   fixed-point tile weights of the row (reference: its largest tile), T = w2 Q >> 32;
-//   column: the chosen tile's columns recomputed (pair_exponent + ex2), fixed point
-//           (reference: the tile weight t_ik), w3;
-// then the pair and the new block's first / last index maps (the composition of the
-// Remark in Section 3.1) into the other map buffer.  REG = 1 keeps the row's tiles and the
-// tile's exponentials in registers (nT <= 32 and B = 32, i.e. N <= 1024).
+// Pair draws (one thread per slot, many small CTAs per combination; used when a
+// combination's operands do not fit one CTA's shared memory): draw_pair, then the pair and
+// the new block's first / last index maps (the composition of the Remark in Section 3.1)
+// into the other map buffer.
 // ---------------------------------------------------------------------------------------
 constexpr int kSlotThreads = 128;
 
-template <int D, int REG>
-__global__ void __launch_bounds__(kSlotThreads) slots_kernel(MergeArgs a, int cum_in_smem) {
-  const int s = blockIdx.x;
-  const int gid = a.gid0 + s;
-  const int N = a.N, B = a.B, nT = a.nT, nTp = a.nTp;
-  // the row prefix sums: copied to shared memory in one round trip when they fit
-  extern __shared__ unsigned long long scum[];
-  const unsigned long long* gcum = a.ws.cum + (size_t)s * N;
-  if (cum_in_smem) {
-    for (int q = threadIdx.x; q < N; q += kSlotThreads) scum[q] = gcum[q];
-    __syncthreads();
-    gcum = scum;
+struct SlotOut {
+  int32_t *pl, *pr, *first_out, *last_out;
+  const int32_t *first_L, *last_R;
+  bool left_leaf, right_leaf;
+  int N;
+  int32_t* star;
+  __device__ __forceinline__ void put(int n, int i, int j) const {
+    if (n < N) {
+      pl[n] = i;
+      pr[n] = j;
+      first_out[n] = left_leaf ? i : first_L[i];
+      last_out[n] = right_leaf ? j : last_R[j];
+    } else {
+      star[0] = i;
+      star[1] = j;
+    }
   }
-  const float* Tt = a.ws.T + (size_t)s * N * nTp;
+};
+
+// The output maps of combination s (and slot 0 of a conditional combination).
+__device__ __forceinline__ SlotOut slot_out(const MergeArgs& a, int s, int gid, bool write_slot0) {
   int at, c, b;
   merge_geom(a.K, a.level, a.m0 + s, at, c, b);
-  int32_t* pl = a.pairs + (size_t)gid * 2 * N;
-  int32_t* pr = pl + N;
+  const int N = a.N;
+  const int sR = b - c + 1;
+  const int bufL = a.level & 1, bufR = ceil_log2(sR) & 1, bufO = (a.level + 1) & 1;
+  SlotOut o;
+  o.pl = a.pairs + (size_t)gid * 2 * N;
+  o.pr = o.pl + N;
+  o.first_out = a.ws.first + ((size_t)bufO * a.K + at) * N;
+  o.last_out = a.ws.last + ((size_t)bufO * a.K + at) * N;
+  o.first_L = a.ws.first + ((size_t)bufL * a.K + at) * N;
+  o.last_R = a.ws.last + ((size_t)bufR * a.K + c) * N;
+  o.left_leaf = (a.level == 0);
+  o.right_leaf = (sR == 1);
+  o.N = N;
+  o.star = a.ws.star;
+  if (a.conditional && write_slot0) {
+    o.pl[0] = 0;
+    o.pr[0] = 0;
+    o.first_out[0] = o.left_leaf ? 0 : o.first_L[0];
+    o.last_out[0] = o.right_leaf ? 0 : o.last_R[0];
+  }
+  return o;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kSlotThreads) slots_kernel(MergeArgs a) {
+  const int s = blockIdx.x;
+  const int gid = a.gid0 + s;
+  const int N = a.N;
+  const SlotOut o = slot_out(a, s, gid, blockIdx.y == 0 && threadIdx.x == 0);
   const int n_lo = a.conditional ? 1 : 0;
   const int n_hi = N + ((a.conditional && a.root) ? 1 : 0);
-  const bool left_leaf = (a.level == 0);
-  const int sR = b - c + 1;
-  const bool right_leaf = (sR == 1);
-  const int bufL = a.level & 1, bufR = ceil_log2(sR) & 1, bufO = (a.level + 1) & 1;
-  int32_t* first_out = a.ws.first + ((size_t)bufO * a.K + at) * N;
-  int32_t* last_out = a.ws.last + ((size_t)bufO * a.K + at) * N;
-  const int32_t* first_L = a.ws.first + ((size_t)bufL * a.K + at) * N;
-  const int32_t* last_R = a.ws.last + ((size_t)bufR * a.K + c) * N;
-  if (a.conditional && blockIdx.y == 0 && threadIdx.x == 0) {
-    pl[0] = 0;
-    pr[0] = 0;
-    first_out[0] = left_leaf ? 0 : first_L[0];
-    last_out[0] = right_leaf ? 0 : last_R[0];
-  }
   const int n = n_lo + blockIdx.y * kSlotThreads + threadIdx.x;
   if (n >= n_hi) return;
-  const unsigned long long S = gcum[N - 1];
+  DrawIn in;
+  in.cum = a.ws.cum + (size_t)s * N;
+  in.T = a.ws.T + (size_t)s * N * a.nTp;
+  in.U = a.ws.U + (size_t)s * N * D;
+  in.alpha = a.ws.alpha + (size_t)s * N;
+  in.delta = a.ws.delta + (size_t)s * N;
+  in.V = a.ws.V + (size_t)s * N * D;
+  in.beta = a.ws.beta + (size_t)s * N;
+  in.N = N;
+  in.B = a.B;
+  in.nT = a.nT;
+  in.nTp = a.nTp;
   int i, j;
-  if (S == 0ull) {
-    i = n % N;
-    j = n % N;
+  draw_pair<D, false>(in, a.seed, a.base, gid, n, i, j);
+  o.put(n, i, j);
+}
+
+// ---------------------------------------------------------------------------------------
+// Row CDF and pair draws of one combination in one CTA (when its operands fit shared
+// memory): the column terms v_j, beta_j and the row terms u_i are staged in shared memory,
+// the row totals, the row CDF and the increment are computed as in rowcdf_kernel, then
+// every slot is drawn (one thread per slot) against the shared-memory copies.
+// ---------------------------------------------------------------------------------------
+constexpr int kCdfSlotThreads = 512;
+
+// Shared memory: padded v [vpad_floats], u [N][D], padded beta, l [N], prefix sums [N].
+struct CdfSlotsSmem {
+  size_t v, u, b, l, c, total;
+};
+
+template <int D>
+__host__ __device__ __forceinline__ CdfSlotsSmem cdf_slots_smem(int N) {
+  const auto r16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  CdfSlotsSmem f;
+  size_t o = 0;
+  f.v = o; o = r16(o + (size_t)vpad_floats<D>(N) * 4);
+  f.u = o; o = r16(o + (size_t)N * D * 4);
+  f.b = o; o = r16(o + (size_t)bpad_floats(N) * 4);
+  f.l = o; o = r16(o + (size_t)N * 4);
+  f.c = o; o = r16(o + (size_t)N * 8);
+  f.total = o;
+  return f;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kCdfSlotThreads) cdf_slots_kernel(MergeArgs a) {
+  constexpr int NT = kCdfSlotThreads;
+  constexpr int NW = NT / 32;
+  const int s = blockIdx.x;
+  const int gid = a.gid0 + s;
+  const int N = a.N, nT = a.nT, nTp = a.nTp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const CdfSlotsSmem L = cdf_slots_smem<D>(N);
+  float* sV = reinterpret_cast<float*>(smraw + L.v);
+  float* sU = reinterpret_cast<float*>(smraw + L.u);
+  float* sB = reinterpret_cast<float*>(smraw + L.b);
+  float* sL = reinterpret_cast<float*>(smraw + L.l);
+  unsigned long long* sC = reinterpret_cast<unsigned long long*>(smraw + L.c);
+  int* under = reinterpret_cast<int*>(sC);
+  __shared__ unsigned long long warp_tot[NW];
+  __shared__ float redf[NW];
+  __shared__ float M_s;
+  __shared__ int n_under, nonfinite_s;
+  if (threadIdx.x == 0) {
+    n_under = 0;
+    nonfinite_s = 0;
+  }
+  const float* U = a.ws.U + (size_t)s * N * D;
+  const float* V = a.ws.V + (size_t)s * N * D;
+  const float* beta = a.ws.beta + (size_t)s * N;
+  const float* alpha = a.ws.alpha + (size_t)s * N;
+  float* Tt = a.ws.T + (size_t)s * N * nTp;
+  const double* shift = a.ws.shift + (size_t)s * N;
+  float* delta = a.ws.delta + (size_t)s * N;
+  float* rowsum = a.ws.rowsum + (size_t)s * N;
+  // stage the operands (vector copies when D % 4 == 0: rows and pads are 16-byte aligned)
+  if ((D % 4) == 0) {
+    const float4* V4 = reinterpret_cast<const float4*>(V);
+    const float4* U4 = reinterpret_cast<const float4*>(U);
+    for (int q = threadIdx.x; q < N * D / 4; q += NT) {
+      const int j = q / (D / 4), k4 = q - j * (D / 4);
+      reinterpret_cast<float4*>(sV + vidx<D, true>(j))[k4] = V4[q];
+      reinterpret_cast<float4*>(sU)[q] = U4[q];
+    }
   } else {
-    const uint4 w = draw(a.seed, (uint32_t)n, (uint32_t)gid, kPurposeDense, a.base, 0u);
-    const unsigned long long Uw = ((unsigned long long)w.x << 32) | (unsigned long long)w.y;
-    const unsigned long long Tg = __umul64hi(Uw, S);
-    int lo = 0, hi = N - 1;  // first i with cum[i] > Tg (cum[N-1] = S > Tg)
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (gcum[mid] > Tg) hi = mid; else lo = mid + 1;
-    }
-    i = lo;
-    const float* Ti = Tt + (size_t)i * nTp;
-    const float4* Ti4 = reinterpret_cast<const float4*>(Ti);
-    float u[D];
-    load_row<D>(a.ws.U + ((size_t)s * N + i) * D, u);
-    const float al = __fsub_rn(a.ws.alpha[(size_t)s * N + i], a.ws.delta[(size_t)s * N + i]);
-    const float* V = a.ws.V + (size_t)s * N * D;
-    const float* beta = a.ws.beta + (size_t)s * N;
-    int kt;
-    if (REG) {
-      float t[32];
-#pragma unroll
-      for (int k4 = 0; k4 < 8; ++k4) {
-        const float4 v = (4 * k4 < nTp) ? Ti4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
-        t[4 * k4] = v.x;
-        t[4 * k4 + 1] = v.y;
-        t[4 * k4 + 2] = v.z;
-        t[4 * k4 + 3] = v.w;
-      }
-      float tmax = 0.f;
-#pragma unroll
-      for (int k = 0; k < 32; ++k)
-        if (k < nT) tmax = fmaxf(tmax, t[k]);
-      kt = pick_regs(t, nT, w.z, ref_exponent(tmax));
-    } else {
-      float tmax = 0.f;
-      for (int k = 0; k < nT; ++k) tmax = fmaxf(tmax, Ti[k]);
-      const int rbe = ref_exponent(tmax);
-      unsigned long long Q = 0;
-      for (int k = 0; k < nT; ++k) Q += q40(Ti[k], rbe);
-      kt = 0;
-      if (Q != 0ull) {
-        const unsigned long long Tq = __umul64hi((unsigned long long)w.z << 32, Q);
-        unsigned long long cc = 0;
-        for (int k = 0; k < nT; ++k) {
-          cc += q40(Ti[k], rbe);
-          kt += (cc <= Tq) ? 1 : 0;
-        }
-        kt = min(kt, nT - 1);
-      }
-    }
-    const int tbe = ref_exponent(Ti[kt]);
-    const int jb = kt * B, je = min(jb + B, N);
-    if (REG) {
-      // the tile's 32 columns: beta as 8 vector loads, each v_j as D/4 vector loads
-      float bt[32], e[32];
-      // vector loads only when the tile is full and its beta run is 16-byte aligned (the
-      // per-combination stride N need not be a multiple of 4)
-      if (je - jb == 32 && ((reinterpret_cast<uintptr_t>(beta + jb) & 15u) == 0)) {
-        const float4* b4 = reinterpret_cast<const float4*>(beta + jb);
-#pragma unroll
-        for (int q4 = 0; q4 < 8; ++q4) {
-          const float4 v = b4[q4];
-          bt[4 * q4] = v.x;
-          bt[4 * q4 + 1] = v.y;
-          bt[4 * q4 + 2] = v.z;
-          bt[4 * q4 + 3] = v.w;
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 32; ++q) bt[q] = beta[min(jb + q, N - 1)];
-      }
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        float v[D];
-        load_row<D>(V + (size_t)min(jb + q, N - 1) * D, v);
-        e[q] = (jb + q < je) ? ex2(pair_exponent<D>(u, al, v, bt[q])) : 0.f;
-      }
-      j = jb + pick_regs(e, je - jb, w.w, tbe);
-    } else {
-      unsigned long long Qc = 0;
-      for (int jj = jb; jj < je; ++jj)
-        Qc += q40(ex2(pair_exponent<D>(u, al, V + (size_t)jj * D, beta[jj])), tbe);
-      j = jb;
-      if (Qc != 0ull) {
-        const unsigned long long Tc = __umul64hi((unsigned long long)w.w << 32, Qc);
-        unsigned long long cc = 0;
-        int cnt = 0;
-        for (int jj = jb; jj < je; ++jj) {
-          cc += q40(ex2(pair_exponent<D>(u, al, V + (size_t)jj * D, beta[jj])), tbe);
-          cnt += (cc <= Tc) ? 1 : 0;
-        }
-        j = jb + min(cnt, je - jb - 1);
-      }
+    for (int q = threadIdx.x; q < N * D; q += NT) {
+      const int j = q / D, k = q - j * D;
+      sV[vidx<D, true>(j) + k] = V[q];
+      sU[q] = U[q];
     }
   }
-  if (n < N) {
-    pl[n] = i;
-    pr[n] = j;
-    first_out[n] = left_leaf ? i : first_L[i];
-    last_out[n] = right_leaf ? j : last_R[j];
-  } else {
-    a.ws.star[0] = i;
-    a.ws.star[1] = j;
+  for (int q = threadIdx.x; q < N; q += NT) sB[bidx<true>(q)] = beta[q];
+  // row totals
+  for (int i = threadIdx.x; i < N; i += NT) {
+    float t = row_total(Tt + (size_t)i * nTp, nT, nTp);
+    if (isnan(t)) {
+      nonfinite_s = 1;
+      t = 0.f;
+    }
+    sL[i] = t;
+    delta[i] = 0.f;
+    if (t < 0x1p-64f) under[atomicAdd(&n_under, 1)] = i;
+  }
+  __syncthreads();
+  for (int q = warp; q < n_under; q += NW) {
+    const int i = under[q];
+    float si, dl;
+    recompute_row<D, true>(sU + (size_t)i * D, alpha[i], sV, sB, N, a.B, nT, Tt + (size_t)i * nTp, &si, &dl);
+    __syncwarp();
+    if (lane == 0) {
+      si = row_total(Tt + (size_t)i * nTp, nT, nTp);
+      sL[i] = isnan(si) ? 0.f : si;
+      delta[i] = dl;
+    }
+  }
+  __syncthreads();
+  // row CDF
+  float mloc = -INFINITY;
+  for (int i = threadIdx.x; i < N; i += NT) {
+    const float t = sL[i];
+    rowsum[i] = t;
+    const float v = row_log2_weight(shift[i], delta[i], t);
+    sL[i] = v;
+    mloc = fmaxf(mloc, v);
+  }
+  mloc = warp_max(mloc);
+  if (lane == 0) redf[warp] = mloc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = redf[0];
+    for (int w = 1; w < NW; ++w) t = fmaxf(t, redf[w]);
+    M_s = t;
+  }
+  __syncthreads();
+  const float M = M_s;
+  const bool degenerate = !(M > -INFINITY) || isnan(M);
+  float* rw = a.ws.rw + (size_t)s * N;
+  for (int i = threadIdx.x; i < N; i += NT) {
+    const float r = row_weight(sL[i], M, degenerate);
+    rw[i] = r;
+    sC[i] = (unsigned long long)__float2ull_rz(r * 0x1p40f);
+  }
+  __syncthreads();
+  block_scan_u64(sC, N, warp_tot);
+  unsigned long long* gcum = a.ws.cum + (size_t)s * N;
+  for (int i = threadIdx.x; i < N; i += NT) gcum[i] = sC[i];
+  int at, c, b;
+  merge_geom(a.K, a.level, a.m0 + s, at, c, b);
+  if (threadIdx.x == 0) {
+    const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(sC[N - 1]);
+    a.ws.inc[s] = inc;
+    a.logL[at] = a.logL[at] + a.logL[c] + inc;
+    if (degenerate || sC[N - 1] == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
+    if (nonfinite_s) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+  }
+  // pair draws
+  const SlotOut o = slot_out(a, s, gid, threadIdx.x == 0);
+  DrawIn in;
+  in.cum = sC;
+  in.T = Tt;
+  in.U = sU;
+  in.alpha = alpha;
+  in.delta = delta;
+  in.V = sV;
+  in.beta = sB;
+  in.N = N;
+  in.B = a.B;
+  in.nT = nT;
+  in.nTp = nTp;
+  const int n_lo = a.conditional ? 1 : 0;
+  const int n_hi = N + ((a.conditional && a.root) ? 1 : 0);
+  for (int n = n_lo + threadIdx.x; n < n_hi; n += NT) {
+    int i, j;
+    draw_pair<D, true>(in, a.seed, a.base, gid, n, i, j);
+    o.put(n, i, j);
   }
 }
 
@@ -885,6 +829,14 @@ cudaError_t rowsum_t(const MergeArgs& a, cudaStream_t st) {
 
 template <int D>
 cudaError_t sample_dense_t(const MergeArgs& a, cudaStream_t st) {
+  const size_t smem_cs = cdf_slots_smem<D>(a.N).total;
+  if (smem_cs <= 200 * 1024) {  // one CTA per combination: row CDF and draws
+    cudaError_t e = cudaFuncSetAttribute(cdf_slots_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_cs);
+    if (e != cudaSuccess) return e;
+    cdf_slots_kernel<D><<<a.mc, kCdfSlotThreads, smem_cs, st>>>(a);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)a.N * (sizeof(unsigned long long) + sizeof(float));
   if (smem > 40 * 1024) {  // static shared memory counts against the 48 KB default
     cudaError_t e = cudaFuncSetAttribute(rowcdf_kernel<D>,
@@ -896,12 +848,7 @@ cudaError_t sample_dense_t(const MergeArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int slots = a.N + ((a.conditional && a.root) ? 1 : 0) - (a.conditional ? 1 : 0);
   dim3 grid(a.mc, (slots + kSlotThreads - 1) / kSlotThreads);
-  const int cum_in_smem = a.N <= 4096 ? 1 : 0;   // <= 32 KB: several CTAs per SM
-  const size_t smem_slot = cum_in_smem ? (size_t)a.N * sizeof(unsigned long long) : 0;
-  if (a.nT <= 32 && a.B == 32)
-    slots_kernel<D, 1><<<grid, kSlotThreads, smem_slot, st>>>(a, cum_in_smem);
-  else
-    slots_kernel<D, 0><<<grid, kSlotThreads, smem_slot, st>>>(a, cum_in_smem);
+  slots_kernel<D><<<grid, kSlotThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

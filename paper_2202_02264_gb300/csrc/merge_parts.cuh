@@ -1,0 +1,408 @@
+// merge_parts.cuh -- the per-pair, per-column, per-row and per-slot arithmetic of one
+// combination of Algorithm 1 / Algorithm 5, shared by the split per-level kernels
+// (merge.cu) and the fused single-launch level kernel (level_fused.cu), so that both paths
+// produce the same bits from the same inputs.
+//
+// Notation (Section 3.1): left block [a, c-1], right block [c, b]; xL_i = left state at c-1,
+// xR_j = right state at c; a_i = logw_L[i]; b'_j = logw_R[j] + log h_c(y_c|xR_j) - log nu_c(xR_j).
+// For the Gaussian transition N(A x + c, Q) with centre mu (mean of the xR_j):
+//   w_i = A xL_i + c - mu,  v_j = xR_j - mu,  u_i = log2(e) Q^-1 w_i,
+//   alpha_i = -log2(e) 1/2 w_i' Q^-1 w_i,  beta_j = log2(e) (b'_j - B* - 1/2 v_j' Q^-1 v_j),
+// and the base-2 exponent of pair (i, j) relative to the row bound
+// shift_i = a_i + log f_max + B* is alpha_i + beta_j + u_i . v_j <= 0.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace dsmc {
+namespace parts {
+
+// The base-2 exponent of pair (i, j): (alpha_i + beta_j) then u_i . v_j by FMAs in
+// ascending k.  Every kernel that evaluates a pair on the CUDA cores uses this function.
+template <int D>
+__device__ __forceinline__ float pair_exponent(const float* u, float al, const float* v, float be) {
+  float acc = __fadd_rn(al, be);
+#pragma unroll
+  for (int k = 0; k < D; ++k) acc = __fmaf_rn(u[k], v[k], acc);
+  return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Column-term layouts.  In global memory v_j is row j of [N][D] and beta_j element j.
+// Shared-memory copies (PAD = true) insert a gap after every 32 columns (one tile at
+// B = 32): kVPad<D> floats for v, one float for beta.  Threads that read column q of
+// different tiles then hit different banks instead of all hitting the same one.
+template <int D>
+constexpr int kVPad = D >= 4 ? 4 : D;
+
+template <int D, bool PAD>
+__host__ __device__ __forceinline__ int vidx(int j) {
+  return PAD ? j * D + (j >> 5) * kVPad<D> : j * D;
+}
+
+template <bool PAD>
+__host__ __device__ __forceinline__ int bidx(int j) {
+  return PAD ? j + (j >> 5) : j;
+}
+
+// Floats of a padded shared-memory copy of N columns.
+template <int D>
+__host__ __device__ __forceinline__ int vpad_floats(int N) {
+  return N * D + ((N + 31) >> 5) * kVPad<D>;
+}
+__host__ __device__ __forceinline__ int bpad_floats(int N) { return N + ((N + 31) >> 5); }
+
+// ---------------------------------------------------------------- column and row terms
+// Column j, first pass: the right block's state xR_j (through the first-index map unless
+// the right block is a leaf) and b'_j.  Returns b'_j; x receives the padded state.
+template <int D>
+__device__ __forceinline__ float column_bprime(const ModelParams<D>& mp, const MergeArgs& a, int c,
+                                               const float* yc, const float* qm, const float* qinv,
+                                               float qnorm, const int32_t* firstR, bool right_leaf,
+                                               int j, float* x, bool& corrupt) {
+  const int N = a.N, d = a.d;
+  const int idx = right_leaf ? j : checked_index(firstR[j], N, corrupt);
+  const float* xp = a.X + ((size_t)c * N + idx) * d;
+#pragma unroll
+  for (int k = 0; k < D; ++k) x[k] = k < d ? xp[k] : 0.f;
+  const float bj = right_leaf ? a.logw[(size_t)c * N + j] : -a.logN;
+  const float g = log_h<D>(mp, yc, x) - log_nu<D>(mp, yc, qm, qinv, qnorm, x);
+  return bj + g;
+}
+
+// Column j, second pass: v_j = xR_j - mu (in place) and beta_j.
+template <int D>
+__device__ __forceinline__ float column_beta(const ModelParams<D>& mp, float* v, const float* mu,
+                                             float bprime, float bstar) {
+#pragma unroll
+  for (int k = 0; k < D; ++k) v[k] = v[k] - mu[k];
+  return kLog2e * (bprime - bstar - 0.5f * quad_form<D>(mp.Qi, v));
+}
+
+// Row i: the left block's state xL_i (through the last-index map unless the left block is
+// a leaf), u_i (already scaled by log2(e)), alpha_i, a_i.  Returns alpha_i.
+template <int D>
+__device__ __forceinline__ float row_terms(const ModelParams<D>& mp, const MergeArgs& a, int c,
+                                           const int32_t* lastL, bool left_leaf, int i,
+                                           const float* mu, float* ul, float& ai, bool& corrupt) {
+  const int N = a.N, d = a.d;
+  const int idx = left_leaf ? i : checked_index(lastL[i], N, corrupt);
+  const float* xp = a.X + ((size_t)(c - 1) * N + idx) * d;
+  float x[D], w[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) x[k] = k < d ? xp[k] : 0.f;
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    float acc = mp.c[r];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc = fmaf(mp.A[r * D + k], x[k], acc);
+    w[r] = acc - mu[r];
+  }
+  float q = 0.f;
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc = fmaf(mp.Qi[r * D + k], w[k], acc);
+    ul[r] = kLog2e * acc;
+    q = fmaf(w[r], acc, q);
+  }
+  ai = left_leaf ? a.logw[(size_t)(c - 1) * N + i] : -a.logN;
+  return -0.5f * kLog2e * q;
+}
+
+// ---------------------------------------------------------------- row totals and CDF
+// Sum of a row's tile weights in ascending tile order (vector loads; the row is 16-byte
+// aligned, nTp a multiple of 4).
+__device__ __forceinline__ float row_total(const float* row, int nT, int nTp) {
+  const float4* t4 = reinterpret_cast<const float4*>(row);
+  float t = 0.f;
+  for (int k4 = 0; k4 < nTp / 4; ++k4) {
+    const float4 v = t4[k4];
+    const int k = 4 * k4;
+    if (k < nT) t = __fadd_rn(t, v.x);
+    if (k + 1 < nT) t = __fadd_rn(t, v.y);
+    if (k + 2 < nT) t = __fadd_rn(t, v.z);
+    if (k + 3 < nT) t = __fadd_rn(t, v.w);
+  }
+  return t;
+}
+
+// The row's base-2 log weight l_i = shift_i log2(e) + delta_i + log2 s_i (-inf when s_i = 0).
+__device__ __forceinline__ float row_log2_weight(double shift, float delta, float total) {
+  return total > 0.f ? (float)(shift * kLog2ed + (double)delta + (double)log2f(total)) : -INFINITY;
+}
+
+// The row weight r_i = 2^(l_i - M) in FP32, clamped to [0, 1].
+__device__ __forceinline__ float row_weight(float l, float M, bool degenerate) {
+  float r = degenerate ? 0.f : ex2(__fsub_rn(l, M));
+  if (!(r > 0.f)) r = 0.f;
+  if (r > 1.f) r = 1.f;
+  return r;
+}
+
+// Natural log of the row-weight total from its exact fixed-point image S = sum_i
+// floor(r_i 2^40) (r_i <= 1, so the truncation is below N 2^-40 of a total >= 1):
+// ln(S 2^-40) with S = m 2^e, m in [1, 2) taken from the top 24 bits, log2 m in FP32.
+__device__ __forceinline__ double log_fixed_total(unsigned long long S) {
+  if (S == 0ull) return (double)NAN;
+  const int e = 63 - __clzll(S);
+  const unsigned long long top = e >= 23 ? (S >> (e - 23)) : (S << (23 - e));
+  const float m = (float)(uint32_t)top * 0x1p-23f;
+  return ((double)(e - 40) + (double)log2f(m)) * kLn2d;
+}
+
+// Block-wide inclusive scan of N uint64 values in shared memory (in place); warp_tot holds
+// blockDim.x / 32 entries.  Integer: the result does not depend on the thread count.
+__device__ __forceinline__ void block_scan_u64(unsigned long long* v, int N, unsigned long long* warp_tot) {
+  const int NT = blockDim.x;
+  const int per = (N + NT - 1) / NT;
+  const int lo = min(threadIdx.x * per, N), hi = min(lo + per, N);
+  unsigned long long run = 0;
+  for (int i = lo; i < hi; ++i) run += v[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long acc = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+      const unsigned long long t = warp_tot[w];
+      warp_tot[w] = acc;
+      acc += t;
+    }
+  }
+  __syncthreads();
+  unsigned long long pre = warp_tot[warp] + incl - run;
+  for (int i = lo; i < hi; ++i) {
+    pre += v[i];
+    v[i] = pre;
+  }
+  __syncthreads();
+}
+
+// Exact-max recomputation of one row (rare: used when the bound-shifted row total fell
+// below 2^-64).  One warp; rewrites the row's tile sums relative to the new shift, returns
+// the row total (lane-local sums, then a butterfly) and the extra base-2 shift.
+template <int D, bool PAD>
+__device__ void recompute_row(const float* u, float al, const float* V, const float* beta, int N,
+                              int B, int nT, float* Trow, float* out_sum, float* out_delta) {
+  const int lane = threadIdx.x & 31;
+  float mx = -INFINITY;
+  for (int j = lane; j < N; j += 32)
+    mx = fmaxf(mx, pair_exponent<D>(u, al, V + vidx<D, PAD>(j), beta[bidx<PAD>(j)]));
+  mx = warp_max(mx);
+  if (!(mx > -INFINITY)) mx = 0.f;  // all -inf: the row keeps weight zero
+  float tot = 0.f;
+  for (int kt = lane; kt < nT; kt += 32) {
+    const int jb = kt * B, je = min(jb + B, N);
+    float ts = 0.f;
+    for (int j = jb; j < je; ++j)
+      ts = __fadd_rn(ts, ex2(pair_exponent<D>(u, al, V + vidx<D, PAD>(j), beta[bidx<PAD>(j)]) - mx));
+    Trow[kt] = ts;
+    tot += ts;
+  }
+  tot = warp_sum(tot);
+  *out_sum = tot;
+  *out_delta = mx;
+}
+
+// ---------------------------------------------------------------- fixed-point draws
+// The fixed-point image floor(x 2^(24 - E)) of a weight x below twice its reference
+// (2^(E-2) <= ref < 2^(E-1), ref_be = the reference's biased exponent + 1): the 24-bit
+// significand shifted right by ref_be - be, the shift clamped to [0, 31].  Exact, order-free
+// and branch-free; zero, negative, subnormal and non-finite x give 0.  A weight equal to its
+// reference keeps 23 significant bits, as many as the FP32 weight carries.
+__device__ __forceinline__ uint32_t q24(float x, int ref_be) {
+  const uint32_t b = __float_as_uint(x);
+  const int be = (int)((b >> 23) & 0xFFu);
+  const bool zero = (b >> 31) || be == 0 || be == 0xFF;
+  const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
+  const int r = min(max(ref_be - be, 0), 31);
+  return zero ? 0u : (m >> r);
+}
+
+__device__ __forceinline__ int ref_exponent(float ref) {
+  return (int)((__float_as_uint(ref) >> 23) & 0xFFu) + 1;
+}
+
+// D floats of a row of U or V into registers (vector loads when D is a multiple of 4; the
+// rows are then 16-byte aligned).
+template <int D>
+__device__ __forceinline__ void load_row(const float* p, float* r) {
+  if ((D % 4) == 0) {
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < D / 4; ++k) {
+      const float4 v = p4[k];
+      r[4 * k] = v.x;
+      r[4 * k + 1] = v.y;
+      r[4 * k + 2] = v.z;
+      r[4 * k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) r[k] = p[k];
+  }
+}
+
+// The inputs of one combination's pair draws.  Each pair is drawn in three fixed-point
+// inverse-CDF stages:
+//   row:    T = U64 * S >> 64 against the exact prefix sums of trunc(r_i 2^40);
+//   tile:   24-bit fixed-point images of the row's tile weights (reference: its largest
+//           tile), T = floor(w2 Q / 2^32);
+//   column: the chosen tile's columns recomputed (pair_exponent + ex2), images relative to
+//           the tile weight t_ik, w3.
+struct DrawIn {
+  const unsigned long long* cum;  // [N] exact prefix sums of the row weights
+  const float* T;                 // [N][nTp] tile weights
+  const float* U;                 // [N][D]
+  const float* alpha;             // [N]
+  const float* delta;             // [N]
+  const float* V;                 // [N][D]
+  const float* beta;              // [N]
+  int N, B, nT, nTp;
+};
+
+// Fixed-point pick over n <= 32 weights held in registers: q_k = q24(x_k; ref), Q = sum q
+// (< 2^29 for tile weights below their maximum, < 2^29 for columns below twice their tile
+// weight), T = floor(w Q / 2^32) (w a 32-bit uniform word), the number of prefix sums <= T,
+// clamped to n - 1; 0 when Q = 0.
+__device__ __forceinline__ int pick32(const float* x, int n, uint32_t w, int ref_be) {
+  uint32_t q[32];
+  uint32_t Q = 0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    q[k] = (k < n) ? q24(x[k], ref_be) : 0u;
+    Q += q[k];
+  }
+  if (Q == 0u) return 0;
+  const uint32_t T = __umulhi(w, Q);
+  uint32_t c = 0;
+  int idx = 0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    c += q[k];
+    idx += (c <= T) ? 1 : 0;
+  }
+  return min(idx, n - 1);
+}
+
+// The same pick over n weights in memory (any n; 64-bit sums).
+__device__ __forceinline__ int pick_mem(const float* x, int n, uint32_t w, int ref_be) {
+  unsigned long long Q = 0;
+  for (int k = 0; k < n; ++k) Q += q24(x[k], ref_be);
+  if (Q == 0ull) return 0;
+  const unsigned long long T = __umul64hi((unsigned long long)w << 32, Q);
+  unsigned long long c = 0;
+  int idx = 0;
+  for (int k = 0; k < n; ++k) {
+    c += q24(x[k], ref_be);
+    idx += (c <= T) ? 1 : 0;
+  }
+  return min(idx, n - 1);
+}
+
+// Slot n's pair (i, j) of combination gid, one thread:
+//   row:    binary search of T = U64 * S >> 64 in the exact prefix sums;
+//   tile:   pick over the row's tile weights (reference: the largest), word w2;
+//   column: the chosen tile's columns recomputed (pair_exponent + ex2), pick with the
+//           tile weight t_ik as reference, word w3.
+// The tiles are held in registers when nT <= 32, the columns when the tile has <= 32.
+template <int D, bool PAD>
+__device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint32_t base, int gid, int n,
+                                          int& i, int& j) {
+  const int N = in.N, B = in.B, nT = in.nT, nTp = in.nTp;
+  const unsigned long long S = in.cum[N - 1];
+  if (S == 0ull) {
+    i = n % N;
+    j = n % N;
+    return;
+  }
+  const uint4 w = draw(seed, (uint32_t)n, (uint32_t)gid, kPurposeDense, base, 0u);
+  const unsigned long long Uw = ((unsigned long long)w.x << 32) | (unsigned long long)w.y;
+  const unsigned long long Tg = __umul64hi(Uw, S);
+  int lo = 0, hi = N - 1;  // first i with cum[i] > Tg (cum[N-1] = S > Tg)
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (in.cum[mid] > Tg) hi = mid; else lo = mid + 1;
+  }
+  i = lo;
+  const float* Ti = in.T + (size_t)i * nTp;
+  int kt;
+  if (nT <= 32) {
+    float t[32];
+    const float4* Ti4 = reinterpret_cast<const float4*>(Ti);
+#pragma unroll
+    for (int k4 = 0; k4 < 8; ++k4) {
+      const float4 v = (4 * k4 < nT) ? Ti4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      t[4 * k4] = v.x;
+      t[4 * k4 + 1] = v.y;
+      t[4 * k4 + 2] = v.z;
+      t[4 * k4 + 3] = v.w;
+    }
+    float tmax = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      if (k < nT) tmax = fmaxf(tmax, t[k]);
+    kt = pick32(t, nT, w.z, ref_exponent(tmax));
+  } else {
+    float tmax = 0.f;
+    for (int k = 0; k < nT; ++k) tmax = fmaxf(tmax, Ti[k]);
+    kt = pick_mem(Ti, nT, w.z, ref_exponent(tmax));
+  }
+  const int tbe = ref_exponent(Ti[kt]);
+  const int jb = kt * B, ncol = min(jb + B, N) - jb;
+  float u[D];
+  load_row<D>(in.U + (size_t)i * D, u);
+  const float al = __fsub_rn(in.alpha[i], in.delta[i]);
+  const float* V = in.V;
+  const float* beta = in.beta;
+  if (ncol <= 32) {
+    float e[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int jj = jb + min(q, ncol - 1);
+      float v[D];
+      load_row<D>(V + vidx<D, PAD>(jj), v);
+      e[q] = (q < ncol) ? ex2(pair_exponent<D>(u, al, v, beta[bidx<PAD>(jj)])) : 0.f;
+    }
+    j = jb + pick32(e, ncol, w.w, tbe);
+  } else {
+    unsigned long long Qc = 0;
+    for (int jj = jb; jj < jb + ncol; ++jj)
+      Qc += q24(ex2(pair_exponent<D>(u, al, V + vidx<D, PAD>(jj), beta[bidx<PAD>(jj)])), tbe);
+    j = jb;
+    if (Qc != 0ull) {
+      const unsigned long long Tc = __umul64hi((unsigned long long)w.w << 32, Qc);
+      unsigned long long cc = 0;
+      int cnt = 0;
+      for (int jj = jb; jj < jb + ncol; ++jj) {
+        cc += q24(ex2(pair_exponent<D>(u, al, V + vidx<D, PAD>(jj), beta[bidx<PAD>(jj)])), tbe);
+        cnt += (cc <= Tc) ? 1 : 0;
+      }
+      j = jb + min(cnt, ncol - 1);
+    }
+  }
+}
+
+}  // namespace parts
+}  // namespace dsmc

@@ -2,14 +2,18 @@
 // cross term u_i . v_j on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
 // One CTA computes 128 rows (one TMEM lane each) of one combination against a chunk of
-// columns, in blocks of 128 columns:
-//   - a control warp stages the row tile once and each 128-column block of v_j with TMA
-//     bulk copies (cp.async.bulk, operands pre-laid out by the prologue in the canonical
-//     no-swizzle K-major layout), and issues one tcgen05.mma (M = 128, N = 128, K = 32 bytes:
-//     16 BF16 or 8 TF32 values) per block into one of two 128-column TMEM accumulators;
+// columns, in blocks of 128 columns.  The operands carry the whole base-2 exponent: row i is
+// [u_i, alpha_hi, alpha_lo, 1, 1] and column j is [v_j, 1, 1, beta_hi, beta_lo] (two-term
+// splits of alpha_i and beta_j in the MMA type), so the accumulator holds
+// e_ij = alpha_i + beta_j + u_i . v_j and the epilogue is only 2^e and the tile sums:
+//   - a control warp stages the row tile once and each 128-column block of the columns with
+//     TMA bulk copies (cp.async.bulk, operands pre-laid out by the prologue in the canonical
+//     no-swizzle K-major layout, one 32-byte K plane = 16 BF16 or 8 TF32 values per copy), and
+//     issues P tcgen05.mma (M = 128, N = 128, one per K plane) per block into one of two
+//     128-column TMEM accumulators;
 //   - eight epilogue warps (two per TMEM lane quarter, splitting the block's columns) read the
-//     accumulator with tcgen05.ld, add alpha_i and beta_j in FP32, take 2^x on MUFU and keep
-//     the per-tile sums, while the tensor core already computes the next block.
+//     accumulator with tcgen05.ld, take 2^x on MUFU and keep the per-tile sums, while the
+//     tensor core already computes the next block.
 // Every wait is bounded; on a timeout the CTA records DSMC_ERR_TIMEOUT, waits (bounded) for
 // its own outstanding MMA, frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -77,9 +81,8 @@ __device__ __forceinline__ uint32_t instr_desc() {
 }
 
 template <int KIND>
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t da, uint64_t db) {
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t accum) {
   const uint32_t idesc = instr_desc<KIND>();
-  const uint32_t accum = 0;
   if (KIND == DSMC_BF16) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -117,33 +120,19 @@ __device__ __forceinline__ void tmem_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Sum over 32 columns of 2^(acc + beta_j + alpha) with packed FP32 adds (pairs of columns);
-// columns at or beyond `valid` contribute nothing.  The order of the additions is fixed.
+// Sum over 32 columns of 2^acc with packed FP32 adds (pairs of columns); columns at or
+// beyond `valid` contribute nothing.  The order of the additions is fixed.
 template <bool MASK>
-__device__ __forceinline__ float exp_sum32(const uint32_t* acc, const float* beta, float al, int valid) {
-  const float4* b4 = reinterpret_cast<const float4*>(beta);
-  const float2 al2 = make_float2(al, al);
+__device__ __forceinline__ float exp_sum32(const uint32_t* acc, int valid) {
   float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int q4 = 0; q4 < 8; ++q4) {
-    const float4 bv = b4[q4];
-    float2 x0 = __fadd2_rn(make_float2(__uint_as_float(acc[4 * q4]), __uint_as_float(acc[4 * q4 + 1])),
-                           make_float2(bv.x, bv.y));
-    float2 x1 = __fadd2_rn(make_float2(__uint_as_float(acc[4 * q4 + 2]), __uint_as_float(acc[4 * q4 + 3])),
-                           make_float2(bv.z, bv.w));
-    x0 = __fadd2_rn(x0, al2);
-    x1 = __fadd2_rn(x1, al2);
-    float2 e0 = make_float2(ex2(x0.x), ex2(x0.y));
-    float2 e1 = make_float2(ex2(x1.x), ex2(x1.y));
+  for (int q2 = 0; q2 < 16; ++q2) {
+    float2 e = make_float2(ex2(__uint_as_float(acc[2 * q2])), ex2(__uint_as_float(acc[2 * q2 + 1])));
     if (MASK) {
-      const int q = 4 * q4;
-      e0.x = q < valid ? e0.x : 0.f;
-      e0.y = q + 1 < valid ? e0.y : 0.f;
-      e1.x = q + 2 < valid ? e1.x : 0.f;
-      e1.y = q + 3 < valid ? e1.y : 0.f;
+      e.x = 2 * q2 < valid ? e.x : 0.f;
+      e.y = 2 * q2 + 1 < valid ? e.y : 0.f;
     }
-    s2 = __fadd2_rn(s2, e0);
-    s2 = __fadd2_rn(s2, e1);
+    s2 = __fadd2_rn(s2, e);
   }
   return __fadd_rn(s2.x, s2.y);
 }
@@ -166,16 +155,21 @@ __device__ __forceinline__ Item item_of(const MergeArgs& a, int it) {
   return r;
 }
 
-constexpr int kVSlots = 16;   // column blocks (v_j tile + beta_j run) staged ahead
-constexpr int kRefillLag = 4; // a slot is refilled once the epilogue finished its block
-constexpr int kBetaBytes = kTcCols * 4;
+// Column blocks staged ahead (P = 1: 16 x 4 KB, P = 2: 10 x 8 KB) and the refill lag: a
+// slot is refilled once the epilogue finished its block.
+template <int P>
+__host__ __device__ constexpr int v_slots() {
+  return P == 1 ? 16 : 10;
+}
+constexpr int kRefillLag = 4;
 
-template <int KIND>
+template <int KIND, int P>
 __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, int n_items) {
+  constexpr int kVSlots = v_slots<P>();
+  constexpr int kSlotBytes = P * kTileBytes;
   extern __shared__ __align__(128) unsigned char dsm[];
-  unsigned char* sA = dsm;                                        // [2][4 KB] row tiles
-  unsigned char* sV = dsm + 2 * kTileBytes;                       // [kVSlots][4 KB] v_j tiles
-  float* sB = reinterpret_cast<float*>(sV + kVSlots * kTileBytes); // [kVSlots][128] beta_j
+  unsigned char* sA = dsm;                                        // [2][P][4 KB] row tiles
+  unsigned char* sV = dsm + 2 * kSlotBytes;                       // [kVSlots][P][4 KB] column blocks
   __shared__ __align__(8) uint64_t bar_a[2], bar_v[kVSlots], bar_done[kVSlots], bar_mma[2], bar_epi[2];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_s;
@@ -215,24 +209,23 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
       // load cursor over the CTA's block sequence
       int l_it = blockIdx.x, l_b = 0, lq = 0, l_k = 0;
       Item li = item_of(a, l_it);
-      auto load_next = [&]() {  // v_j tile and beta_j run of the next block, one barrier
+      const size_t plane = (size_t)a.Nr * 32;  // bytes of one K plane of one combination
+      auto load_next = [&]() {  // the P planes of the next column block, one barrier
         if (l_it >= n_items) return;
-        const size_t col = (size_t)li.s * a.Nr + li.j0 + (size_t)l_b * kTcCols;
+        const unsigned char* src =
+            a.ws.Vb + (size_t)li.s * P * plane + ((size_t)li.j0 + (size_t)l_b * kTcCols) * 32;
         const int slot = lq % kVSlots;
         const uint32_t bar = smem_u32(&bar_v[slot]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"((uint32_t)(kTileBytes + kBetaBytes))
+                     "r"((uint32_t)kSlotBytes)
                      : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(sV + (size_t)slot * kTileBytes)),
-            "l"(a.ws.Vb + col * 32), "r"((uint32_t)kTileBytes), "r"(bar)
-            : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(sB + (size_t)slot * kTcCols)),
-            "l"(a.ws.betap + col), "r"((uint32_t)kBetaBytes), "r"(bar)
-            : "memory");
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_u32(sV + (size_t)slot * kSlotBytes + (size_t)p * kTileBytes)),
+              "l"(src + (size_t)p * plane), "r"((uint32_t)kTileBytes), "r"(bar)
+              : "memory");
         ++lq;
         if (++l_b == li.nblk) {
           l_b = 0;
@@ -244,8 +237,18 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
       auto load_a = [&](int it, int slot) {
         if (it >= n_items) return;
         const Item t = item_of(a, it);
-        const unsigned char* src = a.ws.Ub + (size_t)t.s * a.Nr * 32 + (size_t)t.rt * kTileBytes;
-        tma_load(smem_u32(sA + (size_t)slot * kTileBytes), src, kTileBytes, smem_u32(&bar_a[slot]));
+        const unsigned char* src = a.ws.Ub + (size_t)t.s * P * plane + (size_t)t.rt * kTileBytes;
+        const uint32_t bar = smem_u32(&bar_a[slot]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)kSlotBytes)
+                     : "memory");
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_u32(sA + (size_t)slot * kSlotBytes + (size_t)p * kTileBytes)),
+              "l"(src + (size_t)p * plane), "r"((uint32_t)kTileBytes), "r"(bar)
+              : "memory");
       };
       load_a(blockIdx.x, 0);
       load_a(blockIdx.x + gridDim.x, 1);
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
         if (k >= 2) retire(q_prev);
         q_prev = q;
         if (ok) ok = mbar_wait(smem_u32(&bar_a[k & 1]), (uint32_t)(k >> 1) & 1);
-        const uint64_t da = smem_desc(smem_u32(sA + (size_t)(k & 1) * kTileBytes));
+        const uint32_t sa = smem_u32(sA + (size_t)(k & 1) * kSlotBytes);
         for (int b = 0; b < cur.nblk && ok; ++b, ++q) {
           const int buf = q & 1;
           const int slot = q % kVSlots;
@@ -287,7 +290,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
           if (ok) ok = mbar_wait(smem_u32(&bar_v[slot]), (uint32_t)(q / kVSlots) & 1);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          mma<KIND>(tb + (uint32_t)buf * kTcCols, da, smem_desc(smem_u32(sV + (size_t)slot * kTileBytes)));
+          const uint32_t sv = smem_u32(sV + (size_t)slot * kSlotBytes);
+#pragma unroll
+          for (int p = 0; p < P; ++p)
+            mma<KIND>(tb + (uint32_t)buf * kTcCols, smem_desc(sa + p * kTileBytes), smem_desc(sv + p * kTileBytes),
+                      p > 0 ? 1u : 0u);
           mma_commit(smem_u32(&bar_mma[buf]));
           ++issued;
         }
@@ -310,7 +317,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
       const Item cur = item_of(a, it);
       const int s = cur.s;
       const int row = cur.rt * kTcRows + 32 * g + lane;
-      const float al = row < N ? a.ws.alpha[(size_t)s * N + row] : 0.f;
       float* Trow = a.ws.T + ((size_t)s * N + (row < N ? row : 0)) * a.nTp;
       bool stop = false;
       for (int b = 0; b < cur.nblk; ++b, ++q) {
@@ -337,17 +343,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bar_epi[buf]));
-        const float* beta = sB + (size_t)slot * kTcCols + 64 * h;
+        // the MMA that read the slot has completed (its commit arrived): the slot is free
+        if (lane == 0) mbar_arrive(smem_u32(&bar_done[slot]));
         float t0, t1;
         if (col0 + 64 <= cur.j1) {
-          t0 = exp_sum32<false>(acc0, beta, al, 32);
-          t1 = exp_sum32<false>(acc1, beta + 32, al, 32);
+          t0 = exp_sum32<false>(acc0, 32);
+          t1 = exp_sum32<false>(acc1, 32);
         } else {
-          t0 = exp_sum32<true>(acc0, beta, al, cur.j1 - col0);
-          t1 = exp_sum32<true>(acc1, beta + 32, al, cur.j1 - col0 - 32);
+          t0 = exp_sum32<true>(acc0, cur.j1 - col0);
+          t1 = exp_sum32<true>(acc1, cur.j1 - col0 - 32);
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bar_done[slot]));  // slot (v_j, beta_j) free
         if (row < N) {
           if (B == 32) {
             if (col0 < cur.j1) Trow[col0 / 32] = t0;
@@ -368,28 +373,31 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
   }
 }
 
-// Dynamic shared memory: 2 row tiles + kVSlots column blocks with their beta runs
-// (~80 KB), padded so that at most two CTAs (2 x 256 TMEM columns) share an SM.
+// Dynamic shared memory: 2 row tiles + the column-block ring (72 KB at P = 1, 96 KB at
+// P = 2), padded so that at most two CTAs (2 x 256 TMEM columns) share an SM.
 constexpr size_t kDynSmem = 100 * 1024;
-static_assert((2 + kVSlots) * kTileBytes + kVSlots * kBetaBytes <= kDynSmem, "staging buffers");
+static_assert((2 + v_slots<1>()) * kTileBytes <= kDynSmem, "staging buffers, one K plane");
+static_assert((2 + v_slots<2>()) * 2 * kTileBytes <= kDynSmem, "staging buffers, two K planes");
 
-template <int KIND>
+template <int KIND, int P>
 cudaError_t launch_t(const MergeArgs& a, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(rowsum_tc_kernel<KIND>,
+  cudaError_t e = cudaFuncSetAttribute(rowsum_tc_kernel<KIND, P>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
   if (e != cudaSuccess) return e;
   const int RT = (a.N + kTcRows - 1) / kTcRows;
   const int n_items = a.mc * RT * a.CH;
   const int grid = n_items < 2 * 152 ? n_items : 2 * 152;
-  rowsum_tc_kernel<KIND><<<grid, kTcThreads, kDynSmem, st>>>(a, n_items);
+  rowsum_tc_kernel<KIND, P><<<grid, kTcThreads, kDynSmem, st>>>(a, n_items);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_rowsum_tc(const MergeArgs& a, cudaStream_t s) {
-  if (a.compute == DSMC_BF16) return launch_t<DSMC_BF16>(a, s);
-  if (a.compute == DSMC_TF32) return launch_t<DSMC_TF32>(a, s);
+  if (a.compute == DSMC_BF16 && a.mma_planes == 1) return launch_t<DSMC_BF16, 1>(a, s);
+  if (a.compute == DSMC_BF16 && a.mma_planes == 2) return launch_t<DSMC_BF16, 2>(a, s);
+  if (a.compute == DSMC_TF32 && a.mma_planes == 1) return launch_t<DSMC_TF32, 1>(a, s);
+  if (a.compute == DSMC_TF32 && a.mma_planes == 2) return launch_t<DSMC_TF32, 2>(a, s);
   return cudaErrorInvalidValue;
 }
 

@@ -115,14 +115,14 @@ def test_rejection_sampler_cap():
     assert ((0 <= li) & (li < 4)).all() and ((0 <= ri) & (ri < 4)).all()
 
 
-def _q40(x, ref):
-    """floor(x 2^(40 - E)) with 2^(E-2) <= ref < 2^(E-1): the fixed-point image the sampler
+def _q24(x, ref):
+    """floor(x 2^(24 - E)) with 2^(E-2) <= ref < 2^(E-1): the fixed-point image the sampler
     uses for weights below twice their reference, from numpy's frexp (independent of the
     oracle's bit manipulation)."""
     _, e_ref = np.frexp(np.float64(ref))      # ref = m 2^e_ref, m in [0.5, 1)
     E = int(e_ref) + 1
     x = np.asarray(x, np.float64)
-    out = np.floor(np.ldexp(x, 40 - E))
+    out = np.floor(np.ldexp(x, 24 - E))
     out[(x <= 0) | (np.abs(x) < np.finfo(np.float32).tiny)] = 0
     return out
 
@@ -135,10 +135,10 @@ def _kp_law(r, t, e, B):
     Rq = np.floor(np.clip(r.astype(np.float64), 0, 1) * 2.0**40)
     P = np.zeros((N, N))
     for i in range(N):
-        qt = _q40(t[i], t[i].max())
+        qt = _q24(t[i], t[i].max())
         for k in range(nT):
             j0, j1 = k * B, min((k + 1) * B, N)
-            qe = _q40(e[i, j0:j1], t[i, k])
+            qe = _q24(e[i, j0:j1], t[i, k])
             if qe.sum() == 0 or qt.sum() == 0:
                 continue
             P[i, j0:j1] = Rq[i] / Rq.sum() * qt[k] / qt.sum() * qe / qe.sum()
@@ -176,14 +176,14 @@ def test_kp_dense_sampler_zero_tail_and_single_row():
 
 
 def test_kp_fixed_point_image():
-    """The bit-pattern quantisation equals floor(x 2^(40-E)) computed through frexp/ldexp."""
+    """The bit-pattern quantisation equals floor(x 2^(24-E)) computed through frexp/ldexp."""
     rng = np.random.default_rng(9)
     N = B = 64                                 # one tile per row
     for scale in [1.0, 1e-20, 1e20]:
         e = (rng.uniform(0, 1, (N, N)) * scale).astype(np.float32)
         t = e.sum(1, keepdims=True).astype(np.float32)
         for i in [0, 17, 63]:
-            q_ref = _q40(e[i], t[i, 0])
+            q_ref = _q24(e[i], t[i, 0])
             rr = np.zeros(N, np.float32)
             rr[i] = 1.0                        # all row weight on row i
             li, ri = core.kp_dense_pairs(rr, t, e, B, seed=5, gid=i, n0=0, n1=20000)
