@@ -105,7 +105,7 @@ typedef struct {
   int max_merges_per_launch;  /* 0 = default; bounds the workspace */
   int fused_max_merges;       /* dense sampler: levels with at most this many combinations run
                                  as one fused launch (a thread-block cluster per combination,
-                                 FP32 cross term); 0 = default (64), < 0 = never */
+                                 FP32 cross term); 0 = default (32), < 0 = never */
 } dsmc_config_t;
 
 /* Caller-owned DEVICE state of one smoothing (sizes from dsmc_state_sizes()).

@@ -737,12 +737,11 @@ int orc_model_logdens(const orc_model* m, int K, const double* y, int t, const d
  *   tile:   q_k = q24(t_ik; max_k t_ik), T = floor(w2 Q / 2^32), Q = sum q;
  *           tile = #{k : prefix <= T}
  *   column: q_j = q24(e_ij; t_ik) over the tile's columns, the same with w3
- * where q24(x; ref) = floor(x 2^(24 - E)) with 2^(E-2) <= ref < 2^(E-1) (one binade of
- * headroom), computed on the bit patterns as significand >> (E_ref - E_x) with the shift
- * clamped to [0, 31] (the clamp at 0 saturates weights above twice their reference, which
- * the device never produces); zero, negative, subnormal and non-finite x give 0.  A weight
- * equal to its reference keeps 23 significant bits, as many as its FP32 value.  A zero
- * weight is never chosen; a tile whose column weights are all zero yields its first column.
+ * where q24(x; ref) = floor(x 2^k) with k = min(24 - E, 127), 2^(E-2) <= ref < 2^(E-1) (one
+ * binade of headroom), saturated at 2^32 - 1, computed on the bit patterns as the
+ * significand shifted by the exponent difference; negative and NaN x give 0.  A weight equal to its
+ * reference keeps 23 significant bits, as many as its FP32 value.  A zero weight is never
+ * chosen; a tile whose column weights are all zero yields its first column.
  * Slots n in [n0, n1) use the counter (n, gid, DENSE | base<<4, 0). */
 static uint64_t mulhi64(uint64_t a, uint64_t b) {
   unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
@@ -770,14 +769,20 @@ static int ref_exponent(float ref) {
 
 static uint64_t q24(float x, int ref_be) {
   uint32_t b = float_bits(x);
-  if (b >> 31) return 0;
+  if (b >> 31) return 0;                      /* negative (and -0) */
   int be = (int)((b >> 23) & 0xFFu);
-  if (be == 0 || be == 0xFF) return 0;
-  uint64_t m = (uint64_t)((b & 0x7FFFFFu) | 0x800000u);
-  int r = ref_be - be;               /* >= 1 for every weight below its reference */
-  if (r < 0) r = 0;                  /* saturate (never reached by the device's weights) */
-  if (r > 31) r = 31;
-  return m >> r;
+  if (be == 0xFF) return (b & 0x7FFFFFu) ? 0 : 0xFFFFFFFFu;   /* NaN, +inf */
+  /* x = M 2^ex exactly: normal M = 1.f * 2^23, ex = be - 150; subnormal M = f, ex = -149 */
+  uint64_t M = be ? (uint64_t)((b & 0x7FFFFFu) | 0x800000u) : (uint64_t)(b & 0x7FFFFFu);
+  int ex = be ? be - 150 : -149;
+  int k = 150 - ref_be;                       /* the scale 2^(24 - E) */
+  if (k > 127) k = 127;
+  int sh = ex + k;                            /* image = floor(M 2^sh) */
+  if (sh <= -64) return 0;
+  if (sh <= 0) return M >> (-sh);
+  if (sh >= 9) return 0xFFFFFFFFu;            /* M < 2^24: at least 2^33 */
+  uint64_t v = M << sh;
+  return v > 0xFFFFFFFFu ? 0xFFFFFFFFu : v;
 }
 
 /* index of the first prefix sum of q[0..n) exceeding floor(w Q / 2^32); 0 if all are zero */

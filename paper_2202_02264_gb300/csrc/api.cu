@@ -439,7 +439,7 @@ dsmc_status_t do_init(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& m
 // combinations, or 0 for the split path.  C doubles while the level still fills at most
 // one wave of the SMs and every CTA keeps at least 32 rows; the shared-memory footprint
 // (all N column terms per CTA) must fit one SM.
-constexpr int kDefaultFusedMaxMerges = 64;
+constexpr int kDefaultFusedMaxMerges = 32;
 constexpr size_t kFusedSmemLimit = 220 * 1024;
 
 int fused_policy(const Plan& p, const dsmc_config_t* cfg, int M) {

@@ -546,7 +546,7 @@ __host__ __device__ __forceinline__ CdfSlotsSmem cdf_slots_smem(int N) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(kCdfSlotThreads) cdf_slots_kernel(MergeArgs a) {
+__global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 2 : 1) cdf_slots_kernel(MergeArgs a) {
   constexpr int NT = kCdfSlotThreads;
   constexpr int NW = NT / 32;
   const int s = blockIdx.x;

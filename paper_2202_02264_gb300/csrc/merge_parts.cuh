@@ -226,18 +226,18 @@ __device__ void recompute_row(const float* u, float al, const float* V, const fl
 }
 
 // ---------------------------------------------------------------- fixed-point draws
-// The fixed-point image floor(x 2^(24 - E)) of a weight x below twice its reference
-// (2^(E-2) <= ref < 2^(E-1), ref_be = the reference's biased exponent + 1): the 24-bit
-// significand shifted right by ref_be - be, the shift clamped to [0, 31].  Exact, order-free
-// and branch-free; zero, negative, subnormal and non-finite x give 0.  A weight equal to its
-// reference keeps 23 significant bits, as many as the FP32 weight carries.
+// The fixed-point image q24(x; ref) = floor(x 2^(24 - E)) of a weight x >= 0, where
+// 2^(E-2) <= ref < 2^(E-1) (ref_be = the reference's biased exponent + 1, E = ref_be - 126),
+// saturated at 2^32 - 1; negative and NaN x give 0.  Computed as one exact power-of-two
+// scaling and a truncating conversion (the scale exponent is clamped to 127, which no
+// chosen tile reaches: a chosen tile weighs at least 2^-24 of its row's largest tile and
+// that one at least 2^-70 of the row bound).  A weight equal to its reference keeps 23
+// significant bits, as many as the FP32 weight carries; below twice the reference the
+// image is < 2^24.
 __device__ __forceinline__ uint32_t q24(float x, int ref_be) {
-  const uint32_t b = __float_as_uint(x);
-  const int be = (int)((b >> 23) & 0xFFu);
-  const bool zero = (b >> 31) || be == 0 || be == 0xFF;
-  const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
-  const int r = min(max(ref_be - be, 0), 31);
-  return zero ? 0u : (m >> r);
+  const int k = min(150 - ref_be, 127);
+  const float scale = __uint_as_float((uint32_t)(k + 127) << 23);
+  return __float2uint_rz(x * scale);
 }
 
 __device__ __forceinline__ int ref_exponent(float ref) {

@@ -122,7 +122,7 @@ def _q24(x, ref):
     _, e_ref = np.frexp(np.float64(ref))      # ref = m 2^e_ref, m in [0.5, 1)
     E = int(e_ref) + 1
     x = np.asarray(x, np.float64)
-    out = np.floor(np.ldexp(x, 24 - E))
+    out = np.minimum(np.floor(np.ldexp(x, min(24 - E, 127))), 2.0**32 - 1)
     out[(x <= 0) | (np.abs(x) < np.finfo(np.float32).tiny)] = 0
     return out
 
@@ -160,6 +160,16 @@ def test_kp_dense_sampler_chi_square():
     P = _kp_law(r, t, e, B)
     assert (li != 2).all() and (ri != 4).all()
     assert _chi2(li, ri, P) > 1e-3
+    # the fixed-point law is the plain product law of the weights to 2^-23: the same draws
+    # pass against r_i / sum r * t_ik / sum_k t_ik * e_ij / sum_(j in tile k) e_ij directly
+    rd, td, ed = r.astype(np.float64), t.astype(np.float64), e.astype(np.float64)
+    Pw = np.zeros((N, N))
+    for i in range(N):
+        for k in range(nT):
+            j0, j1 = k * B, min((k + 1) * B, N)
+            if ed[i, j0:j1].sum() > 0:
+                Pw[i, j0:j1] = rd[i] / rd.sum() * td[i, k] / td[i].sum() * ed[i, j0:j1] / ed[i, j0:j1].sum()
+    assert _chi2(li, ri, Pw) > 1e-3
 
 
 def test_kp_dense_sampler_zero_tail_and_single_row():
