@@ -212,6 +212,52 @@ dsmc_status_t dsmc_smooth_noalloc(const dsmc_config_t* cfg, const dsmc_model_t* 
  * in this workspace since the last dsmc_init_particles (DSMC_OK if none). */
 dsmc_status_t dsmc_stream_status(void* ws, void* stream, dsmc_status_t* device_status);
 
+/* ---- Batched smoothing: many independent sequences of one model, particle count and
+ * precision (one dsmc_config_t; its K and seed are ignored) in one call.  Every sequence has
+ * its own length, observations, seed, state and outputs; the combinations of level l of
+ * all sequences (Algorithm 6) are launched together, so a level's kernels see the whole
+ * batch's work.  Each sequence's result is the one dsmc_smooth (or, with x_ref_in,
+ * dsmc_conditional_smooth) gives for it alone with the same seed and counter_base: the
+ * draws depend only on (seed, counter_base, combination id within the sequence, slot).
+ * The workspace (dsmc_batch_workspace_size) holds the merge workspace, the per-sequence
+ * index maps and the batch's descriptor tables. */
+typedef struct {
+  int K;                   /* steps of this sequence, >= 1 */
+  const float* y;          /* DEVICE [K][dx] FP32 */
+  const float* prop_mean;  /* DEVICE [K][dx] when the proposal kind is DSMC_PROP_GAUSS, else NULL */
+  const float* prop_std;   /* DEVICE [K][dx] */
+  dsmc_state_t state;      /* DEVICE buffers sized by dsmc_state_sizes for this K */
+  double* mean_out;        /* DEVICE [K][dx] FP64 smoothing means */
+  double* m2_out;          /* DEVICE [K][dx] FP64 second moments, or NULL */
+  double* logL_out;        /* DEVICE FP64 scalar, or NULL */
+  const float* x_ref_in;   /* DEVICE [K][dx]: a conditional (particle-Gibbs) sweep, or NULL */
+  float* x_ref_out;        /* DEVICE [K][dx]: the next reference (conditional only; may alias) */
+  uint64_t seed;
+  uint32_t counter_base;   /* < 2^28 */
+} dsmc_seq_t;
+
+/* Workspace bytes of a batch with sequence lengths K[0..n_seq) (HOST array).  Host call. */
+dsmc_status_t dsmc_batch_workspace_size(const dsmc_config_t* cfg, const dsmc_model_t* model, int n_seq,
+                                        const int* K, size_t* bytes);
+
+/* Writes the batch's descriptor tables (sequence pointers, seeds, the level-major list of
+ * combinations) into the workspace: host-to-device copies on `stream`, then synchronises
+ * it.  seqs: HOST array of n_seq. */
+dsmc_status_t dsmc_batch_prepare(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                 const dsmc_proposal_t* prop, int n_seq, const dsmc_seq_t* seqs, void* ws,
+                                 size_t ws_bytes, void* stream);
+
+/* Launches the whole batched smoothing (init, every level, resolve) on `stream` after
+ * dsmc_batch_prepare with the same arguments; asynchronous, no host-device copies or
+ * synchronisation, so it can be captured in a CUDA graph and replayed. */
+dsmc_status_t dsmc_batch_run(const dsmc_config_t* cfg, const dsmc_model_t* model, const dsmc_proposal_t* prop,
+                             int n_seq, const dsmc_seq_t* seqs, void* ws, size_t ws_bytes, void* stream);
+
+/* dsmc_batch_prepare followed by dsmc_batch_run. */
+dsmc_status_t dsmc_smooth_batch(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                const dsmc_proposal_t* prop, int n_seq, const dsmc_seq_t* seqs, void* ws,
+                                size_t ws_bytes, void* stream);
+
 /* ---- Measurement: CUDA-event timing of the fused exp / tile-sum kernel (the N x N part of
  * Algorithm 1), recorded on the stream that kernel runs on. */
 

@@ -118,7 +118,10 @@ void chunking(const Plan& p, int mc, int& CH, int& CW) {
   CH = (p.nT + tpc - 1) / tpc;
 }
 
-void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p) {
+// Workspace plan of one smoothing; a batched call passes the level-0 combination count of
+// the whole batch (M0) and keeps the per-sequence index maps outside (no_maps).
+void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p, int M0_batch = -1,
+               bool no_maps = false) {
   p.K = cfg->K;
   p.N = cfg->N;
   p.d = model->dx;
@@ -137,7 +140,7 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p) {
   p.B = 32 * ((per + 31) / 32);
   p.nT = (p.N + p.B - 1) / p.B;
   p.nTp = (p.nT + 3) / 4 * 4;
-  const int M0 = std::max(1, merges_at_level(p.K, 0));
+  const int M0 = std::max(1, M0_batch >= 0 ? M0_batch : merges_at_level(p.K, 0));
   const int cap = cfg->max_merges_per_launch > 0 ? cfg->max_merges_per_launch : kDefaultMergeCap;
   p.Mc = std::max(1, std::min(M0, cap));
   p.R = rowsum_rows_per_thread(p.D);
@@ -169,8 +172,8 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p) {
   p.o_rowsum = take(p.dense ? MN * sizeof(float) : 0);
   p.o_cum = take(p.dense ? MN * sizeof(unsigned long long) : 0);
   p.o_delta = take(MN * sizeof(float));
-  p.o_first = take(2 * (size_t)p.K * p.N * sizeof(int32_t));
-  p.o_last = take(2 * (size_t)p.K * p.N * sizeof(int32_t));
+  p.o_first = take(no_maps ? 0 : 2 * (size_t)p.K * p.N * sizeof(int32_t));
+  p.o_last = take(no_maps ? 0 : 2 * (size_t)p.K * p.N * sizeof(int32_t));
   p.o_star = take(2 * sizeof(int32_t));
   const bool tc = p.compute != DSMC_FP32;
   p.o_Ub = take(tc ? (size_t)p.Mc * p.planes * p.Nr * 32 : 0);
@@ -248,6 +251,8 @@ constexpr double kLog2Pi = 1.8378770664093454836;
 
 struct alignas(16) ParamBuf {
   unsigned char bytes[sizeof(ModelParams<kMaxDim>)];
+  const float* prop_mean;  // the proposal arrays of a single-sequence call (or null)
+  const float* prop_std;
 };
 
 template <int D>
@@ -297,6 +302,8 @@ dsmc_status_t fill_params(const dsmc_model_t* m, const dsmc_proposal_t* pr, Para
 }
 
 dsmc_status_t make_params(int D, const dsmc_model_t* m, const dsmc_proposal_t* pr, ParamBuf& buf) {
+  buf.prop_mean = pr->mean;
+  buf.prop_std = pr->std;
   switch (D) {
     case 1: return fill_params<1>(m, pr, buf);
     case 2: return fill_params<2>(m, pr, buf);
@@ -404,6 +411,10 @@ MergeArgs merge_args(const Plan& p, const dsmc_config_t* cfg, const float* y, in
   a.base = cfg->counter_base;
   a.rs_max = cfg->rs_max_attempts ? cfg->rs_max_attempts : (1u << 20);
   a.logN = (float)std::log((double)p.N);
+  a.prop_mean = nullptr;
+  a.prop_std = nullptr;
+  a.seqs = nullptr;
+  a.items = nullptr;
   a.X = st->X;
   a.logw = st->logw;
   a.y = y;
@@ -475,16 +486,21 @@ int fused_schedulable(const Plan& p, const MergeArgs& a, int C) {
   return ok;
 }
 
-dsmc_status_t do_level(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& mp,
-                       const float* y, int level, int conditional, dsmc_state_t* st,
-                       const WsPtrs& w, cudaStream_t s) {
-  const int M = merges_at_level(p.K, level);
+// The launches of one level: M combinations, either of the single sequence in `st` (items
+// null) or the batched list items[0..M) over the sequences `seqs`, in chunks of Mc.
+dsmc_status_t launch_level(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& mp, const float* y,
+                           int level, int conditional, dsmc_state_t* st, const WsPtrs& w, cudaStream_t s,
+                           int M, const CombItem* items, const SeqDesc* seqs) {
   const int Cf = fused_policy(p, cfg, M);
   for (int m0 = 0; m0 < M; m0 += p.Mc) {
     MergeArgs a = merge_args(p, cfg, y, level, conditional, st, w);
+    a.prop_mean = mp.prop_mean;
+    a.prop_std = mp.prop_std;
+    a.items = items;
+    a.seqs = seqs;
     a.m0 = m0;
     a.mc = std::min(p.Mc, M - m0);
-    a.gid0 = p.level_off[level] + m0;
+    a.gid0 = items ? 0 : p.level_off[level] + m0;
     chunking(p, a.mc, a.CH, a.CW);
     if (Cf > 0) {
       const int C = fused_schedulable(p, a, Cf);
@@ -511,6 +527,13 @@ dsmc_status_t do_level(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& 
     }
   }
   return DSMC_OK;
+}
+
+dsmc_status_t do_level(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& mp,
+                       const float* y, int level, int conditional, dsmc_state_t* st,
+                       const WsPtrs& w, cudaStream_t s) {
+  return launch_level(p, cfg, mp, y, level, conditional, st, w, s, merges_at_level(p.K, level), nullptr,
+                      nullptr);
 }
 
 dsmc_status_t do_resolve(const Plan& p, const dsmc_state_t* st, float* traj, double* mean,
@@ -548,6 +571,8 @@ dsmc_status_t prepare(const dsmc_config_t* cfg, const dsmc_model_t* model,
   if (prop) DSMC_TRY(check_prop(cfg, model, prop));
   make_plan(cfg, model, pr.p);
   DSMC_TRY(check_ws(pr.p, ws, ws_bytes));
+  pr.mp.prop_mean = nullptr;
+  pr.mp.prop_std = nullptr;
   if (prop) DSMC_TRY(make_params(pr.p.D, model, prop, pr.mp));
   pr.w = ws_ptrs(pr.p, ws);
   return DSMC_OK;
@@ -598,6 +623,251 @@ dsmc_status_t noalloc_scratch(void** ptr) {
     g_noalloc_ptr[dev] = p;
   }
   *ptr = g_noalloc_ptr[dev];
+  return DSMC_OK;
+}
+
+// ---- Batched smoothing: many sequences of one (model, N, precision), their combinations
+// of each level launched together (one item list per level, chunks of Mc).
+template <int D>
+void set_prop_t(ParamBuf& b, const float* mean, const float* sd) {
+  ModelParams<D>* mp = reinterpret_cast<ModelParams<D>*>(b.bytes);
+  mp->prop_mean = mean;
+  mp->prop_std = sd;
+  b.prop_mean = mean;
+  b.prop_std = sd;
+}
+
+void set_prop(int D, ParamBuf& b, const float* mean, const float* sd) {
+  switch (D) {
+    case 1: set_prop_t<1>(b, mean, sd); break;
+    case 2: set_prop_t<2>(b, mean, sd); break;
+    case 4: set_prop_t<4>(b, mean, sd); break;
+    case 8: set_prop_t<8>(b, mean, sd); break;
+    case 16: set_prop_t<16>(b, mean, sd); break;
+    default: set_prop_t<32>(b, mean, sd); break;
+  }
+}
+
+int levels_of(int K) {
+  int L = 0;
+  while ((1 << L) < K) ++L;
+  return L;
+}
+
+struct BatchLayout {
+  Plan p;                        // merge workspace for Mc combinations (K = the longest sequence)
+  int n_seq = 0, Lmax = 0;
+  std::vector<int> level_start;  // [Lmax + 1] offsets of each level's items
+  std::vector<size_t> map_off;   // per sequence: byte offset of its first / last maps
+  size_t n_items = 0;
+  size_t o_desc = 0, o_items = 0, o_maps = 0, o_star = 0, total = 0;
+};
+
+dsmc_status_t batch_layout(const dsmc_config_t* cfg, const dsmc_model_t* model, int n_seq, const int* K,
+                           BatchLayout& bl) {
+  if (n_seq < 1 || !K) return fail(DSMC_ERR_INVALID_ARG, "a batch needs n_seq >= 1 sequence lengths");
+  int Kmax = 0;
+  long long m0 = 0, items = 0;
+  for (int i = 0; i < n_seq; ++i) {
+    if (K[i] < 1) return fail(DSMC_ERR_INVALID_ARG, "every sequence needs K >= 1");
+    Kmax = std::max(Kmax, K[i]);
+    m0 += merges_at_level(K[i], 0);
+    items += K[i] - 1;
+  }
+  if (items > (1LL << 30)) return fail(DSMC_ERR_INVALID_ARG, "too many combinations in one batch");
+  dsmc_config_t c = *cfg;
+  c.K = Kmax;
+  DSMC_TRY(check_config(&c, model));
+  make_plan(&c, model, bl.p, (int)std::min<long long>(m0, 1 << 30), true);
+  bl.n_seq = n_seq;
+  bl.Lmax = levels_of(Kmax);
+  bl.level_start.assign(bl.Lmax + 1, 0);
+  for (int l = 0; l < bl.Lmax; ++l) {
+    long long cnt = 0;
+    for (int i = 0; i < n_seq; ++i) cnt += merges_at_level(K[i], l);
+    bl.level_start[l + 1] = bl.level_start[l] + (int)cnt;
+  }
+  bl.n_items = (size_t)items;
+  size_t o = bl.p.total;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  bl.o_desc = take((size_t)n_seq * sizeof(SeqDesc));
+  bl.o_items = take(bl.n_items * sizeof(CombItem));
+  bl.o_star = take((size_t)n_seq * 2 * sizeof(int32_t));
+  bl.map_off.resize(n_seq);
+  bl.o_maps = o;
+  for (int i = 0; i < n_seq; ++i) bl.map_off[i] = take(2 * 2 * (size_t)K[i] * cfg->N * sizeof(int32_t));
+  bl.total = o;
+  return DSMC_OK;
+}
+
+// Host copies of the descriptors and the level-major item list of a batch.
+dsmc_status_t batch_tables(const dsmc_config_t* cfg, const BatchLayout& bl, const dsmc_seq_t* seqs,
+                           char* ws, std::vector<SeqDesc>& desc, std::vector<CombItem>& items) {
+  const int N = cfg->N;
+  desc.resize(bl.n_seq);
+  for (int i = 0; i < bl.n_seq; ++i) {
+    const dsmc_seq_t& q = seqs[i];
+    SeqDesc& d = desc[i];
+    d.K = q.K;
+    d.L = levels_of(q.K);
+    d.X = q.state.X;
+    d.logw = q.state.logw;
+    d.y = q.y;
+    d.logL = q.state.logL;
+    d.pairs = q.state.pairs;
+    d.first = reinterpret_cast<int32_t*>(ws + bl.map_off[i]);
+    d.last = d.first + 2 * (size_t)q.K * N;
+    d.star = reinterpret_cast<int32_t*>(ws + bl.o_star) + 2 * (size_t)i;
+    d.prop_mean = q.prop_mean;
+    d.prop_std = q.prop_std;
+    d.seed = q.seed;
+    d.base = q.counter_base;
+    d.conditional = q.x_ref_in != nullptr ? 1 : 0;
+  }
+  items.resize(bl.n_items);
+  std::vector<int> off(bl.n_seq, 0);  // per sequence: combinations of the levels so far
+  for (int l = 0; l < bl.Lmax; ++l) {
+    size_t at = bl.level_start[l];
+    for (int i = 0; i < bl.n_seq; ++i) {
+      const int M = merges_at_level(seqs[i].K, l);
+      for (int m = 0; m < M; ++m) items[at++] = CombItem{i, m, off[i] + m};
+      off[i] += M;
+    }
+  }
+  return DSMC_OK;
+}
+
+dsmc_status_t check_batch(const dsmc_config_t* cfg, const dsmc_model_t* model, const dsmc_proposal_t* prop,
+                          int n_seq, const dsmc_seq_t* seqs) {
+  if (!prop) return fail(DSMC_ERR_INVALID_ARG, "null proposal");
+  if (n_seq < 1 || !seqs) return fail(DSMC_ERR_INVALID_ARG, "a batch needs n_seq >= 1 sequences");
+  for (int i = 0; i < n_seq; ++i) {
+    const dsmc_seq_t& q = seqs[i];
+    if (q.K < 1 || !q.y || !q.mean_out) return fail(DSMC_ERR_INVALID_ARG, "sequence: K, y and mean_out");
+    DSMC_TRY(check_state(&q.state, q.K));
+    if (prop->kind == DSMC_PROP_GAUSS && (!q.prop_mean || !q.prop_std))
+      return fail(DSMC_ERR_INVALID_ARG, "sequence: proposal mean/std arrays");
+    if (q.x_ref_in && cfg->N < 2) return fail(DSMC_ERR_INVALID_ARG, "conditional dSMC needs N >= 2");
+    if (q.counter_base >= (1u << 28)) return fail(DSMC_ERR_INVALID_ARG, "counter_base must be < 2^28");
+  }
+  dsmc_config_t c = *cfg;
+  c.K = seqs[0].K;
+  DSMC_TRY(check_config(&c, model));
+  dsmc_proposal_t pp = *prop;
+  pp.mean = seqs[0].prop_mean;
+  pp.std = seqs[0].prop_std;
+  DSMC_TRY(check_prop(&c, model, &pp));
+  return DSMC_OK;
+}
+
+std::vector<int> batch_lengths(int n_seq, const dsmc_seq_t* seqs) {
+  std::vector<int> K(n_seq);
+  for (int i = 0; i < n_seq; ++i) K[i] = seqs[i].K;
+  return K;
+}
+
+// Everything of a batched call that the launches need.
+struct BatchRun {
+  BatchLayout bl;
+  ParamBuf mp;
+  WsPtrs w;
+};
+
+dsmc_status_t batch_setup(const dsmc_config_t* cfg, const dsmc_model_t* model, const dsmc_proposal_t* prop,
+                          int n_seq, const dsmc_seq_t* seqs, void* ws, size_t ws_bytes, BatchRun& br) {
+  DSMC_TRY(check_batch(cfg, model, prop, n_seq, seqs));
+  const std::vector<int> K = batch_lengths(n_seq, seqs);
+  DSMC_TRY(batch_layout(cfg, model, n_seq, K.data(), br.bl));
+  if (!ws) return fail(DSMC_ERR_INVALID_ARG, "null workspace");
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return fail(DSMC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  if (ws_bytes < br.bl.total) return fail(DSMC_ERR_WORKSPACE, "workspace too small for the batch");
+  br.mp.prop_mean = nullptr;
+  br.mp.prop_std = nullptr;
+  dsmc_proposal_t pp = *prop;
+  pp.mean = nullptr;
+  pp.std = nullptr;
+  DSMC_TRY(make_params(br.bl.p.D, model, &pp, br.mp));
+  br.w = ws_ptrs(br.bl.p, ws);
+  return DSMC_OK;
+}
+
+dsmc_status_t batch_upload(const dsmc_config_t* cfg, const BatchRun& br, const dsmc_seq_t* seqs, void* ws,
+                           cudaStream_t s) {
+  std::vector<SeqDesc> desc;
+  std::vector<CombItem> items;
+  char* b = static_cast<char*>(ws);
+  DSMC_TRY(batch_tables(cfg, br.bl, seqs, b, desc, items));
+  DSMC_CUDA(cudaMemcpyAsync(b + br.bl.o_desc, desc.data(), desc.size() * sizeof(SeqDesc),
+                            cudaMemcpyHostToDevice, s), "descriptor upload");
+  if (!items.empty())
+    DSMC_CUDA(cudaMemcpyAsync(b + br.bl.o_items, items.data(), items.size() * sizeof(CombItem),
+                              cudaMemcpyHostToDevice, s), "item upload");
+  // pageable sources: the copies are staged before the calls return; wait for them so the
+  // host tables may go out of scope whatever the runtime does
+  DSMC_CUDA(cudaStreamSynchronize(s), "upload synchronize");
+  return DSMC_OK;
+}
+
+dsmc_status_t batch_launch(const dsmc_config_t* cfg, const dsmc_model_t* model, const BatchRun& br,
+                           const dsmc_seq_t* seqs, void* ws, cudaStream_t s) {
+  const BatchLayout& bl = br.bl;
+  const Plan& p = bl.p;
+  char* b = static_cast<char*>(ws);
+  DSMC_CUDA(cudaMemsetAsync(br.w.status, 0, sizeof(int), s), "reset status");
+  DSMC_CUDA(cudaMemsetAsync(b + bl.o_star, 0, (size_t)bl.n_seq * 2 * sizeof(int32_t), s), "reset stars");
+  // Algorithm 2 per sequence
+  for (int i = 0; i < bl.n_seq; ++i) {
+    const dsmc_seq_t& q = seqs[i];
+    ParamBuf mp = br.mp;
+    set_prop(p.D, mp, q.prop_mean, q.prop_std);
+    InitArgs ia;
+    ia.K = q.K;
+    ia.N = p.N;
+    ia.d = p.d;
+    ia.seed = q.seed;
+    ia.base = q.counter_base;
+    ia.y = q.y;
+    ia.x_ref = q.x_ref_in;
+    ia.X = q.state.X;
+    ia.logw = q.state.logw;
+    ia.logL = q.state.logL;
+    ia.status = br.w.status;
+    DSMC_CUDA(launch_init(p.D, ia, mp.bytes, s), "init kernel");
+    prof_count(1);
+  }
+  // the levels of Algorithm 6, every sequence's combinations of a level together
+  const SeqDesc* descs = reinterpret_cast<const SeqDesc*>(b + bl.o_desc);
+  const CombItem* items = reinterpret_cast<const CombItem*>(b + bl.o_items);
+  dsmc_state_t none = {nullptr, nullptr, nullptr, nullptr};
+  for (int l = 0; l < bl.Lmax; ++l) {
+    const int M = bl.level_start[l + 1] - bl.level_start[l];
+    if (M > 0)
+      DSMC_TRY(launch_level(p, cfg, br.mp, nullptr, l, 0, &none, br.w, s, M, items + bl.level_start[l], descs));
+  }
+  // resolution per sequence
+  for (int i = 0; i < bl.n_seq; ++i) {
+    const dsmc_seq_t& q = seqs[i];
+    dsmc_config_t c = *cfg;
+    c.K = q.K;
+    Plan pi;
+    make_plan(&c, model, pi, 1, true);
+    WsPtrs wi = br.w;
+    wi.star = reinterpret_cast<int32_t*>(b + bl.o_star) + 2 * (size_t)i;
+    const bool cond = q.x_ref_in != nullptr;
+    if (cond && q.K == 1) {
+      DSMC_CUDA(launch_k1_star(q.state.logw, p.N, q.seed, q.counter_base, wi.star, s), "star kernel");
+      prof_count(1);
+    }
+    dsmc_state_t st = q.state;
+    DSMC_TRY(do_resolve(pi, &st, nullptr, q.mean_out, q.m2_out, cond ? q.x_ref_out : nullptr, wi, s));
+    if (q.logL_out)
+      DSMC_CUDA(cudaMemcpyAsync(q.logL_out, q.state.logL, sizeof(double), cudaMemcpyDeviceToDevice, s),
+                "logL copy");
+  }
   return DSMC_OK;
 }
 
@@ -796,6 +1066,43 @@ dsmc_status_t dsmc_debug_merge_weights(const dsmc_config_t* cfg, const dsmc_mode
   DSMC_CUDA(launch_debug_weights(p.D, a, m - last_chunk, logW, r, rowsum, tiles, e, ratio,
                                  static_cast<cudaStream_t>(stream)), "inspection kernel");
   return DSMC_OK;
+}
+
+dsmc_status_t dsmc_batch_workspace_size(const dsmc_config_t* cfg, const dsmc_model_t* model, int n_seq,
+                                        const int* K, size_t* bytes) {
+  if (!cfg || !model || !bytes) return fail(DSMC_ERR_INVALID_ARG, "null argument");
+  BatchLayout bl;
+  DSMC_TRY(batch_layout(cfg, model, n_seq, K, bl));
+  *bytes = bl.total;
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_batch_prepare(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                 const dsmc_proposal_t* prop, int n_seq, const dsmc_seq_t* seqs, void* ws,
+                                 size_t ws_bytes, void* stream) {
+  if (!cfg || !model) return fail(DSMC_ERR_INVALID_ARG, "null argument");
+  BatchRun br;
+  DSMC_TRY(batch_setup(cfg, model, prop, n_seq, seqs, ws, ws_bytes, br));
+  return batch_upload(cfg, br, seqs, ws, static_cast<cudaStream_t>(stream));
+}
+
+dsmc_status_t dsmc_batch_run(const dsmc_config_t* cfg, const dsmc_model_t* model, const dsmc_proposal_t* prop,
+                             int n_seq, const dsmc_seq_t* seqs, void* ws, size_t ws_bytes, void* stream) {
+  if (!cfg || !model) return fail(DSMC_ERR_INVALID_ARG, "null argument");
+  BatchRun br;
+  DSMC_TRY(batch_setup(cfg, model, prop, n_seq, seqs, ws, ws_bytes, br));
+  return batch_launch(cfg, model, br, seqs, ws, static_cast<cudaStream_t>(stream));
+}
+
+dsmc_status_t dsmc_smooth_batch(const dsmc_config_t* cfg, const dsmc_model_t* model,
+                                const dsmc_proposal_t* prop, int n_seq, const dsmc_seq_t* seqs, void* ws,
+                                size_t ws_bytes, void* stream) {
+  if (!cfg || !model) return fail(DSMC_ERR_INVALID_ARG, "null argument");
+  BatchRun br;
+  DSMC_TRY(batch_setup(cfg, model, prop, n_seq, seqs, ws, ws_bytes, br));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DSMC_TRY(batch_upload(cfg, br, seqs, ws, s));
+  return batch_launch(cfg, model, br, seqs, ws, s);
 }
 
 }  // extern "C"

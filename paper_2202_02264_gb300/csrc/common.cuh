@@ -145,8 +145,8 @@ __device__ __forceinline__ float log_p0(const ModelParams<D>& mp, const float* x
 
 // Proposal mean / std of time t into registers (zero / one beyond d).
 template <int D>
-__device__ __forceinline__ void proposal_at(const ModelParams<D>& mp, const float* y, int t,
-                                            float* qm, float* qs) {
+__device__ __forceinline__ void proposal_at(const ModelParams<D>& mp, const float* y, const float* prop_mean,
+                                            const float* prop_std, int t, float* qm, float* qs) {
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     if (k < mp.d) {
@@ -154,8 +154,8 @@ __device__ __forceinline__ void proposal_at(const ModelParams<D>& mp, const floa
         qm[k] = y[(size_t)t * mp.d + k];
         qs[k] = mp.prop_scale;
       } else {
-        qm[k] = mp.prop_mean[(size_t)t * mp.d + k];
-        qs[k] = mp.prop_std[(size_t)t * mp.d + k];
+        qm[k] = prop_mean[(size_t)t * mp.d + k];
+        qs[k] = prop_std[(size_t)t * mp.d + k];
       }
     } else {
       qm[k] = 0.f;

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
   float yt[D], qm[D], qs[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) yt[k] = k < d ? a.y[(size_t)t * d + k] : 0.f;
-  proposal_at<D>(mp, a.y, t, qm, qs);
+  proposal_at<D>(mp, a.y, mp.prop_mean, mp.prop_std, t, qm, qs);
   float qinv[D];
   const float qnorm = proposal_consts<D>(d, qs, qinv);
   float logsd = 0.f;

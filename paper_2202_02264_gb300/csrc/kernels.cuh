@@ -35,6 +35,30 @@ struct WsPtrs {
   unsigned char* Vb; // [Mc][planes][Nr][32 B]
 };
 
+// One sequence of a batched launch (device memory; built by the host per batch).
+struct SeqDesc {
+  int K, L;                  // steps, levels
+  const float* X;            // [K][N][d]
+  const float* logw;         // [K][N]
+  const float* y;            // [K][d]
+  double* logL;              // [K]
+  int32_t* pairs;            // [K-1][2][N]
+  int32_t* first;            // [2][K][N] map buffers of this sequence
+  int32_t* last;             // [2][K][N]
+  int32_t* star;             // [2]
+  const float* prop_mean;    // [K][d] (DSMC_PROP_GAUSS) or null
+  const float* prop_std;     // [K][d]
+  uint64_t seed;
+  uint32_t base;
+  int conditional;
+};
+
+// One combination of a batched level: sequence, combination index within the level, and
+// its row in the sequence's pairs array.
+struct CombItem {
+  int seq, m, gid;
+};
+
 struct MergeArgs {
   int K, N, d, level;
   int m0;            // first combination (within the level) of this launch chunk
@@ -58,8 +82,85 @@ struct MergeArgs {
   const float* y;    // [K][d]
   double* logL;      // [K]
   int32_t* pairs;    // [K-1][2][N]
+  const float* prop_mean;  // [K][d] (DSMC_PROP_GAUSS) or null
+  const float* prop_std;
+  const SeqDesc* seqs;     // batched launches: the sequences (device), else null
+  const CombItem* items;   // batched launches: combination m0 + s is items[m0 + s]
   WsPtrs ws;
 };
+
+// Block geometry of combination m (0-based within level l): left [a, c-1], right [c, b].
+__host__ __device__ __forceinline__ void merge_geom(int K, int level, int m, int& a, int& c,
+                                                    int& b) {
+  const int size = 1 << level;
+  a = 2 * m * size;
+  c = a + size;
+  b = min(a + 2 * size, K) - 1;
+}
+
+// Everything combination s of a launch needs from its sequence.
+struct Comb {
+  int K, m, gid, at, c, b;
+  bool root;
+  int conditional;
+  const float* X;
+  const float* logw;
+  const float* y;
+  double* logL;
+  int32_t* pairs;
+  int32_t* first;
+  int32_t* last;
+  int32_t* star;
+  const float* prop_mean;
+  const float* prop_std;
+  uint64_t seed;
+  uint32_t base;
+};
+
+__device__ __forceinline__ Comb comb_of(const MergeArgs& a, int s) {
+  Comb cb;
+  if (a.items == nullptr) {
+    cb.K = a.K;
+    cb.m = a.m0 + s;
+    cb.gid = a.gid0 + s;
+    cb.root = a.root != 0;
+    cb.conditional = a.conditional;
+    cb.X = a.X;
+    cb.logw = a.logw;
+    cb.y = a.y;
+    cb.logL = a.logL;
+    cb.pairs = a.pairs;
+    cb.first = a.ws.first;
+    cb.last = a.ws.last;
+    cb.star = a.ws.star;
+    cb.prop_mean = a.prop_mean;
+    cb.prop_std = a.prop_std;
+    cb.seed = a.seed;
+    cb.base = a.base;
+  } else {
+    const CombItem it = a.items[a.m0 + s];
+    const SeqDesc& q = a.seqs[it.seq];
+    cb.K = q.K;
+    cb.m = it.m;
+    cb.gid = it.gid;
+    cb.root = (a.level == q.L - 1);
+    cb.conditional = q.conditional;
+    cb.X = q.X;
+    cb.logw = q.logw;
+    cb.y = q.y;
+    cb.logL = q.logL;
+    cb.pairs = q.pairs;
+    cb.first = q.first;
+    cb.last = q.last;
+    cb.star = q.star;
+    cb.prop_mean = q.prop_mean;
+    cb.prop_std = q.prop_std;
+    cb.seed = q.seed;
+    cb.base = q.base;
+  }
+  merge_geom(cb.K, a.level, cb.m, cb.at, cb.c, cb.b);
+  return cb;
+}
 
 struct InitArgs {
   int K, N, d;
@@ -101,14 +202,5 @@ cudaError_t launch_debug_weights(int D, const MergeArgs& a, int s_local, float* 
                                  cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
                           cudaStream_t s);
-
-// Block geometry of combination m (0-based within level l): left [a, c-1], right [c, b].
-__host__ __device__ __forceinline__ void merge_geom(int K, int level, int m, int& a, int& c,
-                                                    int& b) {
-  const int size = 1 << level;
-  a = 2 * m * size;
-  c = a + size;
-  b = min(a + 2 * size, K) - 1;
-}
 
 }  // namespace dsmc

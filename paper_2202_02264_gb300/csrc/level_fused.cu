@@ -63,10 +63,9 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   cg::cluster_group cluster = cg::this_cluster();
   const int r = (int)cluster.block_rank();
   const int s = blockIdx.x / C;           // combination within this launch
-  const int m = a.m0 + s;
-  const int gid = a.gid0 + s;
-  int at, c, b;
-  merge_geom(a.K, a.level, m, at, c, b);
+  const Comb cb = comb_of(a, s);
+  const int gid = cb.gid, K = cb.K;
+  const int at = cb.at, c = cb.c, b = cb.b;
   const int N = a.N, d = a.d, B = a.B, nT = a.nT, nTp = a.nTp;
   const bool left_leaf = (a.level == 0);
   const int sR = b - c + 1;
@@ -107,14 +106,14 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   double* shift = a.ws.shift + (size_t)s * N;
   float* Tt = a.ws.T + (size_t)s * N * nTp;
   float* delta = a.ws.delta + (size_t)s * N;
-  const int32_t* firstR = a.ws.first + ((size_t)bufR * a.K + c) * N;
-  const int32_t* lastL = a.ws.last + ((size_t)bufL * a.K + at) * N;
+  const int32_t* firstR = cb.first + ((size_t)bufR * K + c) * N;
+  const int32_t* lastL = cb.last + ((size_t)bufL * K + at) * N;
 
   // ---------------------------------------------------------------- columns (all N)
   float yc[D], qm[D], qs[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) yc[k] = k < d ? a.y[(size_t)c * d + k] : 0.f;
-  proposal_at<D>(mp, a.y, c, qm, qs);
+  for (int k = 0; k < D; ++k) yc[k] = k < d ? cb.y[(size_t)c * d + k] : 0.f;
+  proposal_at<D>(mp, cb.y, cb.prop_mean, cb.prop_std, c, qm, qs);
   float qinv[D];
   const float qnorm = proposal_consts<D>(d, qs, qinv);
   float sx[D];
@@ -124,7 +123,7 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   bool bad = false, corrupt = false;
   for (int j = threadIdx.x; j < N; j += NT) {
     float x[D];
-    const float bp = column_bprime<D>(mp, a, c, yc, qm, qinv, qnorm, firstR, right_leaf, j, x, corrupt);
+    const float bp = column_bprime<D>(mp, a, cb, yc, qm, qinv, qnorm, firstR, right_leaf, j, x, corrupt);
     bad |= isnan(bp);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -175,7 +174,7 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   // ---------------------------------------------------------------- own rows
   for (int i = lo + threadIdx.x; i < hi; i += NT) {
     float ul[D], ai;
-    const float al = row_terms<D>(mp, a, c, lastL, left_leaf, i, mu, ul, ai, corrupt);
+    const float al = row_terms<D>(mp, a, cb, lastL, left_leaf, i, mu, ul, ai, corrupt);
     bad |= isnan(ai);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -195,7 +194,7 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   if (r == 0) {  // the matrix bound log omega-bar (read by the inspection entry point)
     float amax = -INFINITY;
     for (int i = threadIdx.x; i < N; i += NT)
-      amax = fmaxf(amax, left_leaf ? a.logw[(size_t)(c - 1) * N + i] : -a.logN);
+      amax = fmaxf(amax, left_leaf ? cb.logw[(size_t)(c - 1) * N + i] : -a.logN);
     amax = warp_max(amax);
     __syncthreads();
     if (lane == 0) red_s[warp] = amax;
@@ -325,21 +324,21 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   if (r == 0 && threadIdx.x == 0) {
     const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(sC[N - 1]);
     a.ws.inc[s] = inc;
-    a.logL[at] = a.logL[at] + a.logL[c] + inc;
+    cb.logL[at] = cb.logL[at] + cb.logL[c] + inc;
     if (degenerate || sC[N - 1] == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
   }
   if (threadIdx.x == 0 && nonfinite_s) record_status(a.ws.status, DSMC_ERR_NONFINITE);
 
   // ---------------------------------------------------------------- this CTA's slots
-  int32_t* pl = a.pairs + (size_t)gid * 2 * N;
+  int32_t* pl = cb.pairs + (size_t)gid * 2 * N;
   int32_t* pr = pl + N;
-  const int n_lo = a.conditional ? 1 : 0;
-  const int n_hi = N + ((a.conditional && a.root) ? 1 : 0);
-  int32_t* first_out = a.ws.first + ((size_t)bufO * a.K + at) * N;
-  int32_t* last_out = a.ws.last + ((size_t)bufO * a.K + at) * N;
-  const int32_t* first_L = a.ws.first + ((size_t)bufL * a.K + at) * N;
-  const int32_t* last_R = a.ws.last + ((size_t)bufR * a.K + c) * N;
-  if (a.conditional && r == 0 && threadIdx.x == 0) {
+  const int n_lo = cb.conditional ? 1 : 0;
+  const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
+  int32_t* first_out = cb.first + ((size_t)bufO * K + at) * N;
+  int32_t* last_out = cb.last + ((size_t)bufO * K + at) * N;
+  const int32_t* first_L = cb.first + ((size_t)bufL * K + at) * N;
+  const int32_t* last_R = cb.last + ((size_t)bufR * K + c) * N;
+  if (cb.conditional && r == 0 && threadIdx.x == 0) {
     pl[0] = 0;
     pr[0] = 0;
     first_out[0] = left_leaf ? 0 : first_L[0];
@@ -361,15 +360,15 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   const int n0 = min(n_hi, n_lo + r * per), n1 = min(n_hi, n0 + per);
   for (int n = n0 + threadIdx.x; n < n1; n += NT) {
     int i, j;
-    draw_pair<D, true>(in, a.seed, a.base, gid, n, i, j);
+    draw_pair<D, true>(in, cb.seed, cb.base, gid, n, i, j);
     if (n < N) {
       pl[n] = i;
       pr[n] = j;
       first_out[n] = left_leaf ? i : first_L[i];
       last_out[n] = right_leaf ? j : last_R[j];
     } else {
-      a.ws.star[0] = i;
-      a.ws.star[1] = j;
+      cb.star[0] = i;
+      cb.star[1] = j;
     }
   }
   // peers may still be reading this CTA's l_i

@@ -112,9 +112,8 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
   constexpr int kProThreads = prologue_threads<D>();
   constexpr int NW = kProThreads / 32;
   const int s = blockIdx.x;
-  const int m = a.m0 + s;
-  int at, c, b;
-  merge_geom(a.K, a.level, m, at, c, b);
+  const Comb cb = comb_of(a, s);
+  const int at = cb.at, c = cb.c, b = cb.b;
   const int N = a.N, d = a.d;
   const bool left_leaf = (a.level == 0);
   const int sR = b - c + 1;
@@ -125,8 +124,8 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
 
   float yc[D], qm[D], qs[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) yc[k] = k < d ? a.y[(size_t)c * d + k] : 0.f;
-  proposal_at<D>(mp, a.y, c, qm, qs);
+  for (int k = 0; k < D; ++k) yc[k] = k < d ? cb.y[(size_t)c * d + k] : 0.f;
+  proposal_at<D>(mp, cb.y, cb.prop_mean, cb.prop_std, c, qm, qs);
   float qinv[D];
   const float qnorm = proposal_consts<D>(d, qs, qinv);
 
@@ -135,8 +134,8 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
   float* U = a.ws.U + (size_t)s * N * D;
   float* alpha = a.ws.alpha + (size_t)s * N;
   double* shift = a.ws.shift + (size_t)s * N;
-  const int32_t* firstR = a.ws.first + ((size_t)bufR * a.K + c) * N;
-  const int32_t* lastL = a.ws.last + ((size_t)bufL * a.K + at) * N;
+  const int32_t* firstR = cb.first + ((size_t)bufR * cb.K + c) * N;
+  const int32_t* lastL = cb.last + ((size_t)bufL * cb.K + at) * N;
 
   __shared__ float red_v[NW][D];
   __shared__ float red_s[NW];
@@ -151,7 +150,7 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
   bool bad = false, corrupt = false;
   for (int j = threadIdx.x; j < N; j += kProThreads) {
     float x[D];
-    const float bp = column_bprime<D>(mp, a, c, yc, qm, qinv, qnorm, firstR, right_leaf, j, x, corrupt);
+    const float bp = column_bprime<D>(mp, a, cb, yc, qm, qinv, qnorm, firstR, right_leaf, j, x, corrupt);
     bad |= isnan(bp);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -214,7 +213,7 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
   float amax = -INFINITY;
   for (int i = threadIdx.x; i < N; i += kProThreads) {
     float ul[D], ai;
-    const float al = row_terms<D>(mp, a, c, lastL, left_leaf, i, mu, ul, ai, corrupt);
+    const float al = row_terms<D>(mp, a, cb, lastL, left_leaf, i, mu, ul, ai, corrupt);
     bad |= isnan(ai);
 #pragma unroll
     for (int k = 0; k < D; ++k) U[(size_t)i * D + k] = ul[k];
@@ -425,13 +424,12 @@ __global__ void __launch_bounds__(kCdfThreads) rowcdf_kernel(MergeArgs a) {
   unsigned long long* gcum = a.ws.cum + (size_t)s * N;
   for (int i = threadIdx.x; i < N; i += kCdfThreads) gcum[i] = cum[i];
   if (threadIdx.x == 0) {
-    int at, c, b;
-    merge_geom(a.K, a.level, a.m0 + s, at, c, b);
+    const Comb cb = comb_of(a, s);
     // Eq. (Lab): log of sum_ij exp(logW_ij) = M ln 2 + ln(sum_i r_i), the row-weight total
     // taken from its exact fixed-point image
     const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(cum[N - 1]);
     a.ws.inc[s] = inc;
-    a.logL[at] = a.logL[at] + a.logL[c] + inc;
+    cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
     if (degenerate || cum[N - 1] == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
     if (nonfinite_s) record_status(a.ws.status, DSMC_ERR_NONFINITE);
   }
@@ -464,25 +462,24 @@ struct SlotOut {
   }
 };
 
-// The output maps of combination s (and slot 0 of a conditional combination).
-__device__ __forceinline__ SlotOut slot_out(const MergeArgs& a, int s, int gid, bool write_slot0) {
-  int at, c, b;
-  merge_geom(a.K, a.level, a.m0 + s, at, c, b);
+// The output maps of combination cb (and slot 0 of a conditional combination).
+__device__ __forceinline__ SlotOut slot_out(const MergeArgs& a, const Comb& cb, bool write_slot0) {
+  const int at = cb.at, c = cb.c, b = cb.b, K = cb.K;
   const int N = a.N;
   const int sR = b - c + 1;
   const int bufL = a.level & 1, bufR = ceil_log2(sR) & 1, bufO = (a.level + 1) & 1;
   SlotOut o;
-  o.pl = a.pairs + (size_t)gid * 2 * N;
+  o.pl = cb.pairs + (size_t)cb.gid * 2 * N;
   o.pr = o.pl + N;
-  o.first_out = a.ws.first + ((size_t)bufO * a.K + at) * N;
-  o.last_out = a.ws.last + ((size_t)bufO * a.K + at) * N;
-  o.first_L = a.ws.first + ((size_t)bufL * a.K + at) * N;
-  o.last_R = a.ws.last + ((size_t)bufR * a.K + c) * N;
+  o.first_out = cb.first + ((size_t)bufO * K + at) * N;
+  o.last_out = cb.last + ((size_t)bufO * K + at) * N;
+  o.first_L = cb.first + ((size_t)bufL * K + at) * N;
+  o.last_R = cb.last + ((size_t)bufR * K + c) * N;
   o.left_leaf = (a.level == 0);
   o.right_leaf = (sR == 1);
   o.N = N;
-  o.star = a.ws.star;
-  if (a.conditional && write_slot0) {
+  o.star = cb.star;
+  if (cb.conditional && write_slot0) {
     o.pl[0] = 0;
     o.pr[0] = 0;
     o.first_out[0] = o.left_leaf ? 0 : o.first_L[0];
@@ -494,11 +491,12 @@ __device__ __forceinline__ SlotOut slot_out(const MergeArgs& a, int s, int gid, 
 template <int D>
 __global__ void __launch_bounds__(kSlotThreads) slots_kernel(MergeArgs a) {
   const int s = blockIdx.x;
-  const int gid = a.gid0 + s;
+  const Comb cb = comb_of(a, s);
+  const int gid = cb.gid;
   const int N = a.N;
-  const SlotOut o = slot_out(a, s, gid, blockIdx.y == 0 && threadIdx.x == 0);
-  const int n_lo = a.conditional ? 1 : 0;
-  const int n_hi = N + ((a.conditional && a.root) ? 1 : 0);
+  const SlotOut o = slot_out(a, cb, blockIdx.y == 0 && threadIdx.x == 0);
+  const int n_lo = cb.conditional ? 1 : 0;
+  const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
   const int n = n_lo + blockIdx.y * kSlotThreads + threadIdx.x;
   if (n >= n_hi) return;
   DrawIn in;
@@ -514,7 +512,7 @@ __global__ void __launch_bounds__(kSlotThreads) slots_kernel(MergeArgs a) {
   in.nT = a.nT;
   in.nTp = a.nTp;
   int i, j;
-  draw_pair<D, false>(in, a.seed, a.base, gid, n, i, j);
+  draw_pair<D, false>(in, cb.seed, cb.base, gid, n, i, j);
   o.put(n, i, j);
 }
 
@@ -550,7 +548,8 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 2 : 1) cdf_slots_ker
   constexpr int NT = kCdfSlotThreads;
   constexpr int NW = NT / 32;
   const int s = blockIdx.x;
-  const int gid = a.gid0 + s;
+  const Comb cb = comb_of(a, s);
+  const int gid = cb.gid;
   const int N = a.N, nT = a.nT, nTp = a.nTp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -648,17 +647,15 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 2 : 1) cdf_slots_ker
   block_scan_u64(sC, N, warp_tot);
   unsigned long long* gcum = a.ws.cum + (size_t)s * N;
   for (int i = threadIdx.x; i < N; i += NT) gcum[i] = sC[i];
-  int at, c, b;
-  merge_geom(a.K, a.level, a.m0 + s, at, c, b);
   if (threadIdx.x == 0) {
     const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(sC[N - 1]);
     a.ws.inc[s] = inc;
-    a.logL[at] = a.logL[at] + a.logL[c] + inc;
+    cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
     if (degenerate || sC[N - 1] == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
     if (nonfinite_s) record_status(a.ws.status, DSMC_ERR_NONFINITE);
   }
   // pair draws
-  const SlotOut o = slot_out(a, s, gid, threadIdx.x == 0);
+  const SlotOut o = slot_out(a, cb, threadIdx.x == 0);
   DrawIn in;
   in.cum = sC;
   in.T = Tt;
@@ -671,11 +668,11 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 2 : 1) cdf_slots_ker
   in.B = a.B;
   in.nT = nT;
   in.nTp = nTp;
-  const int n_lo = a.conditional ? 1 : 0;
-  const int n_hi = N + ((a.conditional && a.root) ? 1 : 0);
+  const int n_lo = cb.conditional ? 1 : 0;
+  const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
   for (int n = n_lo + threadIdx.x; n < n_hi; n += NT) {
     int i, j;
-    draw_pair<D, true>(in, a.seed, a.base, gid, n, i, j);
+    draw_pair<D, true>(in, cb.seed, cb.base, gid, n, i, j);
     o.put(n, i, j);
   }
 }
@@ -704,17 +701,18 @@ __device__ __forceinline__ float rs_ratio(const MergeArgs& a, int s, int I, int 
 template <int D>
 __global__ void __launch_bounds__(kRsThreads) sample_rs_kernel(MergeArgs a) {
   const int s = blockIdx.y;
-  const int gid = a.gid0 + s;
+  const Comb cb = comb_of(a, s);
+  const int gid = cb.gid;
   const int N = a.N;
-  const int n_lo = a.conditional ? 1 : 0;
-  const int n_hi = N + ((a.conditional && a.root) ? 1 : 0);
+  const int n_lo = cb.conditional ? 1 : 0;
+  const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
   const int n = n_lo + blockIdx.x * kRsThreads + threadIdx.x;
   const double logbar = a.ws.logbar[s];
-  int32_t* pl = a.pairs + (size_t)gid * 2 * N;
+  int32_t* pl = cb.pairs + (size_t)gid * 2 * N;
   int32_t* pr = pl + N;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.ws.inc[s] = (double)NAN;  // the lazy sampler never forms the N x N sum
-    if (a.conditional) {
+    if (cb.conditional) {
       pl[0] = 0;
       pr[0] = 0;
     }
@@ -723,7 +721,7 @@ __global__ void __launch_bounds__(kRsThreads) sample_rs_kernel(MergeArgs a) {
   int I = 0, J = 0;
   bool ok = false;
   for (uint32_t att = 0; att < a.rs_max; ++att) {
-    const uint4 w = draw(a.seed, (uint32_t)n, (uint32_t)gid, kPurposeRS, a.base, att);
+    const uint4 w = draw(cb.seed, (uint32_t)n, (uint32_t)gid, kPurposeRS, cb.base, att);
     I = (int)__umulhi(w.x, (uint32_t)N);
     J = (int)__umulhi(w.y, (uint32_t)N);
     if (u23(w.z) < rs_ratio<D>(a, s, I, J, logbar)) {
@@ -736,8 +734,8 @@ __global__ void __launch_bounds__(kRsThreads) sample_rs_kernel(MergeArgs a) {
     pl[n] = I;
     pr[n] = J;
   } else {
-    a.ws.star[0] = I;
-    a.ws.star[1] = J;
+    cb.star[0] = I;
+    cb.star[1] = J;
   }
 }
 
@@ -748,28 +746,24 @@ __global__ void __launch_bounds__(kRsThreads) sample_rs_kernel(MergeArgs a) {
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(MergeArgs a) {
   const int s = blockIdx.x;
-  const int m = a.m0 + s;
-  const int gid = a.gid0 + s;
-  int at, c, b;
-  merge_geom(a.K, a.level, m, at, c, b);
+  const Comb cb = comb_of(a, s);
+  const int at = cb.at, c = cb.c, b = cb.b, K = cb.K;
   const int N = a.N;
   const bool left_leaf = (a.level == 0);
   const int sR = b - c + 1;
   const bool right_leaf = (sR == 1);
   const int bufL = a.level & 1, bufR = ceil_log2(sR) & 1, bufO = (a.level + 1) & 1;
   const int n = blockIdx.y * kEpiThreads + threadIdx.x;
-  const int32_t* pl = a.pairs + (size_t)gid * 2 * N;
+  const int32_t* pl = cb.pairs + (size_t)cb.gid * 2 * N;
   const int32_t* pr = pl + N;
   if (n < N) {
     bool corrupt = false;
     const int l = checked_index(pl[n], N, corrupt), r = checked_index(pr[n], N, corrupt);
-    a.ws.first[((size_t)bufO * a.K + at) * N + n] =
-        left_leaf ? l : a.ws.first[((size_t)bufL * a.K + at) * N + l];
-    a.ws.last[((size_t)bufO * a.K + at) * N + n] =
-        right_leaf ? r : a.ws.last[((size_t)bufR * a.K + c) * N + r];
+    cb.first[((size_t)bufO * K + at) * N + n] = left_leaf ? l : cb.first[((size_t)bufL * K + at) * N + l];
+    cb.last[((size_t)bufO * K + at) * N + n] = right_leaf ? r : cb.last[((size_t)bufR * K + c) * N + r];
     if (corrupt) record_status(a.ws.status, DSMC_ERR_INVALID_ARG);
   }
-  if (blockIdx.y == 0 && threadIdx.x == 0) a.logL[at] = a.logL[at] + a.logL[c] + a.ws.inc[s];
+  if (blockIdx.y == 0 && threadIdx.x == 0) cb.logL[at] = cb.logL[at] + cb.logL[c] + a.ws.inc[s];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -805,6 +799,14 @@ __global__ void debug_weights_kernel(MergeArgs a, int s, float* logW, float* r, 
 }
 
 // ------------------------------------------------------------------- launch wrappers
+// Slots per combination to cover: N, one fewer when conditional (slot 0 is fixed), one more
+// at a conditional root (the next reference).  Batched launches cover N + 1 (every
+// combination decides its own range).
+int launch_slots(const MergeArgs& a) {
+  if (a.items != nullptr) return a.N + 1;
+  return a.N + ((a.conditional && a.root) ? 1 : 0) - (a.conditional ? 1 : 0);
+}
+
 template <int D>
 cudaError_t prologue_t(const MergeArgs& a, const void* mp, cudaStream_t st) {
   prologue_kernel<D><<<a.mc, prologue_threads<D>(), 0, st>>>(a, *static_cast<const ModelParams<D>*>(mp));
@@ -846,16 +848,14 @@ cudaError_t sample_dense_t(const MergeArgs& a, cudaStream_t st) {
   rowcdf_kernel<D><<<a.mc, kCdfThreads, smem, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int slots = a.N + ((a.conditional && a.root) ? 1 : 0) - (a.conditional ? 1 : 0);
-  dim3 grid(a.mc, (slots + kSlotThreads - 1) / kSlotThreads);
+  dim3 grid(a.mc, (launch_slots(a) + kSlotThreads - 1) / kSlotThreads);
   slots_kernel<D><<<grid, kSlotThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t sample_rs_t(const MergeArgs& a, cudaStream_t st) {
-  const int slots = a.N + ((a.conditional && a.root) ? 1 : 0) - (a.conditional ? 1 : 0);
-  dim3 grid((slots + kRsThreads - 1) / kRsThreads, a.mc);
+  dim3 grid((launch_slots(a) + kRsThreads - 1) / kRsThreads, a.mc);
   sample_rs_kernel<D><<<grid, kRsThreads, 0, st>>>(a);
   return cudaGetLastError();
 }

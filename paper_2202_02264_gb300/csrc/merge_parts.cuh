@@ -69,16 +69,16 @@ __host__ __device__ __forceinline__ int bpad_floats(int N) { return N + ((N + 31
 // Column j, first pass: the right block's state xR_j (through the first-index map unless
 // the right block is a leaf) and b'_j.  Returns b'_j; x receives the padded state.
 template <int D>
-__device__ __forceinline__ float column_bprime(const ModelParams<D>& mp, const MergeArgs& a, int c,
+__device__ __forceinline__ float column_bprime(const ModelParams<D>& mp, const MergeArgs& a, const Comb& cb,
                                                const float* yc, const float* qm, const float* qinv,
                                                float qnorm, const int32_t* firstR, bool right_leaf,
                                                int j, float* x, bool& corrupt) {
-  const int N = a.N, d = a.d;
+  const int N = a.N, d = a.d, c = cb.c;
   const int idx = right_leaf ? j : checked_index(firstR[j], N, corrupt);
-  const float* xp = a.X + ((size_t)c * N + idx) * d;
+  const float* xp = cb.X + ((size_t)c * N + idx) * d;
 #pragma unroll
   for (int k = 0; k < D; ++k) x[k] = k < d ? xp[k] : 0.f;
-  const float bj = right_leaf ? a.logw[(size_t)c * N + j] : -a.logN;
+  const float bj = right_leaf ? cb.logw[(size_t)c * N + j] : -a.logN;
   const float g = log_h<D>(mp, yc, x) - log_nu<D>(mp, yc, qm, qinv, qnorm, x);
   return bj + g;
 }
@@ -95,12 +95,12 @@ __device__ __forceinline__ float column_beta(const ModelParams<D>& mp, float* v,
 // Row i: the left block's state xL_i (through the last-index map unless the left block is
 // a leaf), u_i (already scaled by log2(e)), alpha_i, a_i.  Returns alpha_i.
 template <int D>
-__device__ __forceinline__ float row_terms(const ModelParams<D>& mp, const MergeArgs& a, int c,
+__device__ __forceinline__ float row_terms(const ModelParams<D>& mp, const MergeArgs& a, const Comb& cb,
                                            const int32_t* lastL, bool left_leaf, int i,
                                            const float* mu, float* ul, float& ai, bool& corrupt) {
-  const int N = a.N, d = a.d;
+  const int N = a.N, d = a.d, c = cb.c;
   const int idx = left_leaf ? i : checked_index(lastL[i], N, corrupt);
-  const float* xp = a.X + ((size_t)(c - 1) * N + idx) * d;
+  const float* xp = cb.X + ((size_t)(c - 1) * N + idx) * d;
   float x[D], w[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) x[k] = k < d ? xp[k] : 0.f;
@@ -120,7 +120,7 @@ __device__ __forceinline__ float row_terms(const ModelParams<D>& mp, const Merge
     ul[r] = kLog2e * acc;
     q = fmaf(w[r], acc, q);
   }
-  ai = left_leaf ? a.logw[(size_t)(c - 1) * N + i] : -a.logN;
+  ai = left_leaf ? cb.logw[(size_t)(c - 1) * N + i] : -a.logN;
   return -0.5f * kLog2e * q;
 }
 

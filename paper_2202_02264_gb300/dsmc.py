@@ -63,6 +63,14 @@ class State(C.Structure):
                 ("pairs", C.c_void_p)]
 
 
+class Seq(C.Structure):
+    """dsmc_seq_t: one sequence of a batched call."""
+    _fields_ = [("K", C.c_int), ("y", C.c_void_p), ("prop_mean", C.c_void_p), ("prop_std", C.c_void_p),
+                ("state", State), ("mean_out", C.c_void_p), ("m2_out", C.c_void_p),
+                ("logL_out", C.c_void_p), ("x_ref_in", C.c_void_p), ("x_ref_out", C.c_void_p),
+                ("seed", C.c_uint64), ("counter_base", C.c_uint32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -70,7 +78,8 @@ EXPORTS = ["dsmc_status_string", "dsmc_last_error", "dsmc_state_sizes", "dsmc_wo
            "dsmc_init_particles", "dsmc_merge_level", "dsmc_resolve", "dsmc_smooth",
            "dsmc_conditional_smooth", "dsmc_smooth_noalloc", "dsmc_stream_status",
            "dsmc_profile_enable",
-           "dsmc_profile_read", "dsmc_debug_philox", "dsmc_debug_merge_weights"]
+           "dsmc_profile_read", "dsmc_debug_philox", "dsmc_debug_merge_weights",
+           "dsmc_batch_workspace_size", "dsmc_batch_prepare", "dsmc_batch_run", "dsmc_smooth_batch"]
 
 
 def library_path() -> str:
@@ -115,6 +124,10 @@ def load(build_if_needed: bool = False) -> C.CDLL:
         lib.dsmc_debug_philox.argtypes = [vp, C.c_int64, C.c_uint64, vp, vp]
         lib.dsmc_debug_merge_weights.argtypes = [cfgp, modp, C.c_int, C.c_int, vp, vp, vp, vp, vp,
                                                  vp, C.POINTER(C.c_int), vp, sz, vp]
+        seqp = C.POINTER(Seq)
+        lib.dsmc_batch_workspace_size.argtypes = [cfgp, modp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
+        for name in ("dsmc_batch_prepare", "dsmc_batch_run", "dsmc_smooth_batch"):
+            getattr(lib, name).argtypes = [cfgp, modp, prop_p, C.c_int, seqp, vp, sz, vp]
         _lib = lib
         return lib
 
@@ -286,6 +299,32 @@ def dsmc_debug_merge_weights(cfg, model, level, m, ws,
     return out
 
 
+def dsmc_batch_workspace_size(cfg: Config, model: HostModel, Ks) -> int:
+    K = (C.c_int * len(Ks))(*[int(k) for k in Ks])
+    out = C.c_size_t(0)
+    _check(load().dsmc_batch_workspace_size(C.byref(cfg), C.byref(model.struct), len(Ks), K, C.byref(out)),
+           "dsmc_batch_workspace_size")
+    return int(out.value)
+
+
+def _batch_call(name, cfg, model, prop, seqs, ws, stream):
+    arr = (Seq * len(seqs))(*seqs)
+    _check(getattr(load(), name)(C.byref(cfg), C.byref(model.struct), C.byref(prop), len(seqs), arr, _ptr(ws),
+                                 ws.numel(), _stream(stream)), name)
+
+
+def dsmc_batch_prepare(cfg, model, prop, seqs, ws, stream=None):
+    _batch_call("dsmc_batch_prepare", cfg, model, prop, seqs, ws, stream)
+
+
+def dsmc_batch_run(cfg, model, prop, seqs, ws, stream=None):
+    _batch_call("dsmc_batch_run", cfg, model, prop, seqs, ws, stream)
+
+
+def dsmc_smooth_batch(cfg, model, prop, seqs, ws, stream=None):
+    _batch_call("dsmc_smooth_batch", cfg, model, prop, seqs, ws, stream)
+
+
 # ---------------------------------------------------------------- buffer owner
 class Smoother:
     """Device buffers for one (model, K, N) and the calls of the C ABI over them.
@@ -350,6 +389,93 @@ class Smoother:
     def resolve(self, x_star=False, stream=None):
         dsmc_resolve(self.cfg, self.hm, self.state, self.traj, self.mean, self.m2,
                      self.x_star if x_star else None, self.ws, stream)
+
+    def status(self, stream=None) -> int:
+        return dsmc_stream_status(self.ws, stream)
+
+
+class BatchSmoother:
+    """Device buffers for a batch of sequences of one model and N (lengths Ks, observations
+    ys), and the batched calls over them.  Each sequence gets its own seed (seeds[i]) and
+    counter base; ``run`` launches without host synchronisation (CUDA-graph capturable)
+    after ``prepare``."""
+
+    def __init__(self, model: W.SSM, Ks, N: int, seeds=None, resampler: int = MULTINOMIAL,
+                 compute: int = FP32, max_merges_per_launch: int = 0, fused_max_merges: int = 0,
+                 device: str = "cuda", want_m2: bool = False):
+        if not torch.cuda.is_available():
+            raise RuntimeError("dSMC needs a CUDA device; there is no CPU path")
+        self.model = model
+        self.hm = HostModel(model)
+        self.Ks = [int(k) for k in Ks]
+        self.N, self.d = int(N), model.d
+        n = len(self.Ks)
+        self.seeds = list(seeds) if seeds is not None else [1000 + i for i in range(n)]
+        self.counter_base = [0] * n
+        self.cfg = make_config(max(self.Ks), N, 0, 0, resampler, compute, 0, max_merges_per_launch,
+                               fused_max_merges)
+        if model.prop_kind == W.PROP_GAUSS:
+            self.prop = Proposal(W.PROP_GAUSS, 1.0, None, None, int(model.nu))
+        else:
+            self.prop = Proposal(W.PROP_OBS, float(model.prop_scale), None, None, int(model.nu))
+        f32, f64, i32 = torch.float32, torch.float64, torch.int32
+        dev = device
+        self.X = [torch.empty((k, N, self.d), dtype=f32, device=dev) for k in self.Ks]
+        self.logw = [torch.empty((k, N), dtype=f32, device=dev) for k in self.Ks]
+        self.logL = [torch.empty((k,), dtype=f64, device=dev) for k in self.Ks]
+        self.pairs = [torch.empty((max(k - 1, 0), 2, N), dtype=i32, device=dev) for k in self.Ks]
+        self.mean = [torch.empty((k, self.d), dtype=f64, device=dev) for k in self.Ks]
+        self.m2 = [torch.empty((k, self.d), dtype=f64, device=dev) for k in self.Ks] if want_m2 else None
+        self.logL_out = torch.empty((n,), dtype=f64, device=dev)
+        self.y = [None] * n
+        self.pm = [None] * n
+        self.ps = [None] * n
+        self.x_in = [None] * n
+        self.x_out = [None] * n
+        self.ws = torch.empty((dsmc_batch_workspace_size(self.cfg, self.hm, self.Ks),), dtype=torch.uint8,
+                              device=dev)
+
+    def set_inputs(self, ys, x_ref_in=None, x_ref_out=None):
+        """Observations (device [K_i][d] FP32 tensors) and, for a particle-Gibbs sweep, the
+        references in and out per sequence (None entries: plain smoothing)."""
+        n = len(self.Ks)
+        for i in range(n):
+            self.y[i] = ys[i]
+            if self.model.prop_kind == W.PROP_GAUSS:
+                K = self.Ks[i]
+                self.pm[i] = torch.as_tensor(np.asarray(self.model.prop_mean, np.float32)[:K], device=ys[i].device).contiguous() \
+                    if self.model.prop_mean.shape[0] >= K else torch.full((K, self.d), float(self.model.prop_mean[0, 0]),
+                                                                          dtype=torch.float32, device=ys[i].device)
+                self.ps[i] = torch.as_tensor(np.asarray(self.model.prop_std, np.float32)[:K], device=ys[i].device).contiguous() \
+                    if self.model.prop_std.shape[0] >= K else torch.full((K, self.d), float(self.model.prop_std[0, 0]),
+                                                                         dtype=torch.float32, device=ys[i].device)
+            self.x_in[i] = x_ref_in[i] if x_ref_in is not None else None
+            self.x_out[i] = x_ref_out[i] if x_ref_out is not None else None
+
+    def seqs(self):
+        out = []
+        for i, K in enumerate(self.Ks):
+            st = State(self.X[i].data_ptr(), self.logw[i].data_ptr(), self.logL[i].data_ptr(),
+                       self.pairs[i].data_ptr() if self.pairs[i].numel() else None)
+            out.append(Seq(K, self.y[i].data_ptr(),
+                           self.pm[i].data_ptr() if self.pm[i] is not None else None,
+                           self.ps[i].data_ptr() if self.ps[i] is not None else None, st,
+                           self.mean[i].data_ptr(), self.m2[i].data_ptr() if self.m2 is not None else None,
+                           self.logL_out.data_ptr() + 8 * i,
+                           self.x_in[i].data_ptr() if self.x_in[i] is not None else None,
+                           self.x_out[i].data_ptr() if self.x_out[i] is not None else None,
+                           int(self.seeds[i]) & (2**64 - 1), int(self.counter_base[i])))
+        return out
+
+    def prepare(self, stream=None):
+        dsmc_batch_prepare(self.cfg, self.hm, self.prop, self.seqs(), self.ws, stream)
+
+    def run(self, stream=None):
+        dsmc_batch_run(self.cfg, self.hm, self.prop, self.seqs(), self.ws, stream)
+
+    def smooth(self, stream=None):
+        dsmc_smooth_batch(self.cfg, self.hm, self.prop, self.seqs(), self.ws, stream)
+        return self.mean
 
     def status(self, stream=None) -> int:
         return dsmc_stream_status(self.ws, stream)
