@@ -2,16 +2,22 @@
 """Throughput of the dSMC smoother (N*T/s) on GB300, with roofline, end-to-end and CPU
 oracle baselines.
 
-A step is one full smoothing of one synthetic sequence: Algorithm 2 init, every level of
-Algorithm 6 (prologue, fused exp / tile-sum, three-stage pair sampler, map epilogue) and
-the trajectory resolve with fused means.  Default workload: the 8-dimensional
-linear-Gaussian model, K = 1024 steps, N = 1024 particles, cross term on the tensor cores
-in TF32 (``--compute fp32`` for the CUDA-core form).
+Default workload (``batched_lgssm_d4``): 256 independent sequences of the 4-dimensional
+linear-Gaussian model with lengths uniform in [64, 4096], N = 512 particles, smoothed in one
+batched call per step (one launch per level of Algorithm 6 for the whole batch; cross term
+on the tensor cores in BF16 with FP32 accumulation).  The same line reports the plain form
+(FP32, each sequence smoothed alone, one after another) and the smoothing-mean error of both
+against Kalman/RTS.  ``--workload lgssm_d8`` times one sequence of the 8-dimensional model,
+K = N = 1024 (cross term in TF32; ``--compute fp32`` for the CUDA-core form).
+
+A step is one full smoothing (of the batch, or of the sequence): Algorithm 2 init, every
+level (column/row terms, fused exp / tile sums, row CDF and three-stage pair draws) and the
+trajectory resolve with fused means.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload NAME]
 
-Under torchrun each rank smooths its own independent sequence (replicas, weak scaling);
-no collective touches the data path, one barrier brackets the timed region.
+Under torchrun each rank smooths its own independent batch (replicas, weak scaling); no
+collective touches the data path, one barrier brackets the timed region.
 """
 from __future__ import annotations
 
@@ -43,6 +49,7 @@ TRAFFIC_PER_LAUNCH = {
 }
 
 WORKLOADS = {
+    "batched_lgssm_d4": dict(kind="batch", n_seq=256, N=512, resampler="dense"),
     "lgssm_d8": dict(K=1024, N=1024, resampler="dense"),
     "lgssm_1d": dict(K=32, N=64, resampler="dense"),
     "sv": dict(K=4096, N=4096, resampler="dense"),
@@ -145,7 +152,11 @@ def run_reference(args):
         return
     from paper_2202_02264_gb300 import workloads as W
     spec = WORKLOADS[args.workload]
-    wl = W.workload(args.workload.replace("_rs", ""), K=spec["K"], N=spec["N"])
+    if spec.get("kind") == "batch":   # the oracle on the batch's first sequence
+        bw = W.batch_workload(spec["n_seq"], spec["N"])
+        wl = W.Workload(args.workload, bw.model, int(bw.Ks[0]), bw.N, bw.ys[0], None)
+    else:
+        wl = W.workload(args.workload.replace("_rs", ""), K=spec["K"], N=spec["N"])
     from oracle import core
     y = wl.y.astype(np.float32).astype(np.float64)
     # calibrate K' so that each step is a bounded slice of the workload (~2-4 s)
@@ -307,24 +318,203 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def _rmse_vs_rts(model, ys, means):
+    from oracle import kalman
+    out = []
+    for y, m in zip(ys, means):
+        ms, _, _ = kalman.rts_for(model, y)
+        out.append(float(np.sqrt(np.mean((np.asarray(m) - ms) ** 2))))
+    return np.array(out)
+
+
+def run_batched(args):
+    """The batched workload: 256 sequences of the d = 4 linear-Gaussian model with uneven
+    lengths in one batched call per step (one launch per level for the whole batch), against
+    the plain form (FP32, each sequence smoothed alone, one after another)."""
+    import torch
+
+    from paper_2202_02264_gb300 import dsmc, workloads as W
+
+    world, rank, lrank = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(lrank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spec = WORKLOADS[args.workload]
+    bw = W.batch_workload(spec["n_seq"], spec["N"])
+    model, N, Ks, d = bw.model, bw.N, [int(k) for k in bw.Ks], bw.model.d
+    units = N * sum(Ks)
+    compute = {"fp32": dsmc.FP32, "tf32": dsmc.TF32, "bf16": dsmc.BF16}[args.compute]
+    seeds = [1000 + 7919 * rank + i for i in range(len(Ks))]
+    b = dsmc.BatchSmoother(model, Ks, N, seeds=seeds, compute=compute, max_merges_per_launch=8192)
+    ys = [torch.as_tensor(y, dtype=torch.float32, device=dev) for y in bw.ys]
+    b.set_inputs(ys)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def prep(i):
+        b.counter_base = [i] * len(Ks)
+        b.prepare()
+
+    for i in range(args.warmup):
+        prep(i)
+        b.run()
+    torch.cuda.synchronize()
+    if b.status() != 0:
+        raise RuntimeError(f"device status {b.status()} after warm-up")
+    clocks = ClockSampler(torch.cuda.current_device())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    dsmc.dsmc_profile_enable(True)
+    for i in range(args.steps):
+        prep(args.warmup + i)                 # descriptor upload (host tables), outside the events
+        flush.zero_()                         # L2 flushed between timed steps, outside the events
+        ev[i][0].record(stream)
+        b.run()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    rs_ms, rs_n, rs_pairs, launches = dsmc.dsmc_profile_read()
+    dsmc.dsmc_profile_enable(False)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    per_step = [a.elapsed_time(c) for a, c in ev]
+    t_total = sum(per_step) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+    if b.status() != 0:
+        raise RuntimeError(f"device status {b.status()} after timed steps")
+    value = world * args.steps * units / t_total
+    mixed_means = [m.cpu().numpy().copy() for m in b.mean[:32]]
+
+    # end to end through the public API: pinned host observations in, means and logL out
+    y_host = [torch.as_tensor(y, dtype=torch.float32).pin_memory() for y in bw.ys]
+    m_host = [torch.empty((K, d), dtype=torch.float64).pin_memory() for K in Ks]
+    l_host = torch.empty((len(Ks),), dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    t_e2e = 0.0
+    for i in range(e2e_steps):
+        prep(10_000 + i)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for yd, yh in zip(ys, y_host):
+            yd.copy_(yh, non_blocking=True)
+        b.run()
+        for mh, md in zip(m_host, b.mean):
+            mh.copy_(md, non_blocking=True)
+        l_host.copy_(b.logL_out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e += e0.elapsed_time(e1) / 1e3
+    e2e = {"value": world * units * e2e_steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": sum(y.numel() * 4 for y in y_host),
+           "d2h_bytes_per_step": sum(m.numel() * 8 for m in m_host) + l_host.numel() * 8}
+
+    # the plain form: FP32, each sequence smoothed alone, one call after another
+    Kmax = max(Ks)
+    single = dsmc.Smoother(model, Kmax, N, seed=seeds[0], compute=dsmc.FP32)
+    plain_means = []
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for i, K in enumerate(Ks):
+        cfg = dsmc.make_config(K, N, seeds[i], 0, dsmc.MULTINOMIAL, dsmc.FP32)
+        dsmc.dsmc_smooth(cfg, single.hm, single.prop, ys[i], single.state, None, single.mean, None,
+                         single.logL_out, single.ws)
+        if i < 32:
+            plain_means.append(single.mean[:K].clone())
+    p1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = p0.elapsed_time(p1) / 1e3
+    plain_value = units / t_plain
+    plain_means = [m.cpu().numpy() for m in plain_means]
+    r_mixed = _rmse_vs_rts(model, bw.ys[:32], mixed_means)
+    r_plain = _rmse_vs_rts(model, bw.ys[:32], plain_means)
+    diff = r_mixed - r_plain
+    accuracy = {"sequences": 32, "metric": "RMSE of smoothing means vs Kalman/RTS, mean over sequences",
+                "mixed": float(r_mixed.mean()), "mixed_se": float(r_mixed.std(ddof=1) / np.sqrt(32)),
+                "plain_fp32": float(r_plain.mean()), "plain_fp32_se": float(r_plain.std(ddof=1) / np.sqrt(32)),
+                "difference": float(diff.mean()), "difference_se": float(diff.std(ddof=1) / np.sqrt(32))}
+    accuracy["equal_within_2se"] = bool(abs(accuracy["difference"]) <= 2 * accuracy["difference_se"])
+
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    ex2_peak = MUFU_EX2_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9
+    achieved = rs_pairs / (rs_ms / 1e3) / 1e9 if rs_ms > 0 else None
+    kname = {"fp32": "rowsum_kernel (fused exp / tile sums)",
+             "tf32": "rowsum_tc_kernel (tcgen05 cross term, fused exp / tile sums)",
+             "bf16": "rowsum_tc_kernel (tcgen05 cross term, fused exp / tile sums)"}[args.compute]
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": ex2_peak, "unit": "Gexp/s",
+                "frac": achieved / ex2_peak if achieved else None,
+                "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
+                               f"({src} max clock)",
+                "avg_launch_ms": rs_ms / max(rs_n, 1), "launches": rs_n,
+                "traffic": (TRAFFIC_PER_LAUNCH.get((args.workload, args.compute)) or {}).get("bytes"),
+                "traffic_unit": "B per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "tf32": "tf32+f32", "bf16": "bf16+f32"}[args.compute],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_seq": len(Ks), "sum_K": sum(Ks), "K_range": [min(Ks), max(Ks)],
+                       "N": N, "dx": d, "resampler": "dense",
+                       "compute": f"{args.compute} cross term (fp32 accumulate / exp), batched: one launch "
+                                  "per level for all sequences",
+                       "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "plain_fp32_per_request": {"value": plain_value, "unit": UNIT,
+                                       "ms_per_batch": 1e3 * t_plain,
+                                       "form": "FP32, each sequence smoothed alone (dsmc_smooth), in order"},
+            "mixed_over_plain": value / world / plain_value,
+            "accuracy": accuracy,
+            "roofline": roofline, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+            "step_ms": {"median": float(np.median(per_step)), "p99": float(np.percentile(per_step, 99))}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        wl = W.Workload("batched_lgssm_d4_seq0", model, Ks[0], N, bw.ys[0], None)
+        line["cpu_baseline"] = oracle_sample(wl)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 10 batched smoothings, or 400 single smoothings)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lgssm_d8", choices=sorted(WORKLOADS))
-    ap.add_argument("--compute", default="tf32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--workload", default="batched_lgssm_d4", choices=sorted(WORKLOADS))
+    ap.add_argument("--compute", default=None, choices=["fp32", "tf32", "bf16"],
+                    help="cross-term precision (default: bf16 for the batched workload, tf32 otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    kind = WORKLOADS[args.workload].get("kind", "single")
+    if args.steps is None:
+        args.steps = 10 if kind == "batch" else 400
+    if args.compute is None:
+        args.compute = "bf16" if kind == "batch" else "tf32"
     if args.impl == "reference":
         run_reference(args)
     else:
         from oracle import core  # built here so cpu_baseline does not compile mid-run
         core.build()
-        run_ours(args)
+        if kind == "batch":
+            run_batched(args)
+        else:
+            run_ours(args)
 
 
 if __name__ == "__main__":

@@ -173,3 +173,22 @@ def workload(name: str, K: Optional[int] = None, N: Optional[int] = None) -> Wor
 def batched_lengths(n_seq: int = 256, lo: int = 64, hi: int = 4096, seed: int = 2264 + 4) -> np.ndarray:
     """Sequence lengths K_i drawn uniformly in [lo, hi] (includes non-powers of two)."""
     return np.random.default_rng(seed).integers(lo, hi + 1, size=n_seq)
+
+
+@dataclass
+class BatchWorkload:
+    name: str
+    model: SSM
+    N: int
+    Ks: np.ndarray
+    ys: list = field(repr=False)
+
+
+def batch_workload(n_seq: int = 256, N: int = 512, lo: int = 64, hi: int = 4096) -> BatchWorkload:
+    """The batched workload: n_seq independent sequences of the d = 4 linear-Gaussian model
+    (A = 0.8 I, Q = I, R = 0.5 I), lengths uniform in [lo, hi] (seed 2268), sequence i's
+    observations simulated with seed 40000 + i."""
+    m = lgssm_d4()
+    Ks = batched_lengths(n_seq, lo, hi)
+    ys = [simulate(m, int(K), 40000 + i)[1] for i, K in enumerate(Ks)]
+    return BatchWorkload("batched_lgssm_d4", m, int(N), Ks, ys)
