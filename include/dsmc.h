@@ -234,7 +234,13 @@ typedef struct {
   float* x_ref_out;        /* DEVICE [K][dx]: the next reference (conditional only; may alias) */
   uint64_t seed;
   uint32_t counter_base;   /* < 2^28 */
+  void* maps;              /* DEVICE scratch of dsmc_seq_maps_bytes(K, N) bytes for the sequence's
+                              index maps and root draw, or NULL (batched call: kept in its workspace;
+                              required by dsmc_serve_tick, where it lives across ticks) */
 } dsmc_seq_t;
+
+/* Bytes of a sequence's own index-map scratch (dsmc_seq_t.maps).  Host call. */
+size_t dsmc_seq_maps_bytes(int K, int N);
 
 /* Workspace bytes of a batch with sequence lengths K[0..n_seq) (HOST array).  Host call. */
 dsmc_status_t dsmc_batch_workspace_size(const dsmc_config_t* cfg, const dsmc_model_t* model, int n_seq,
@@ -257,6 +263,24 @@ dsmc_status_t dsmc_batch_run(const dsmc_config_t* cfg, const dsmc_model_t* model
 dsmc_status_t dsmc_smooth_batch(const dsmc_config_t* cfg, const dsmc_model_t* model,
                                 const dsmc_proposal_t* prop, int n_seq, const dsmc_seq_t* seqs, void* ws,
                                 size_t ws_bytes, void* stream);
+
+/* ---- Continuous batching (serving).  A request is a sequence that advances one stage per
+ * tick: stage -1 = Algorithm 2, stages 0 .. L-1 = level l of Algorithm 6 (L = ceil(log2 K)),
+ * stage L = resolve (outputs written).  dsmc_serve_tick runs, for every sequence of the call,
+ * its stage[i] (HOST array), the combinations of all sequences launched together (levels may
+ * differ between sequences); sequences may join and leave between ticks.  Every sequence
+ * needs its own maps scratch.  A sequence's results equal those of dsmc_smooth (or
+ * dsmc_conditional_smooth) for it alone: the draws depend only on its own seed, counter base
+ * and combination ids, and whether a level runs fused depends only on that sequence.  The
+ * tick uploads its tables (host-to-device copies on `stream`, then synchronises it) and
+ * returns with the launches queued.  The status word (dsmc_stream_status on ws) is reset at
+ * the start of each tick. */
+dsmc_status_t dsmc_serve_workspace_size(const dsmc_config_t* cfg, const dsmc_model_t* model, int max_seq,
+                                        int max_combinations, size_t* bytes);
+
+dsmc_status_t dsmc_serve_tick(const dsmc_config_t* cfg, const dsmc_model_t* model, const dsmc_proposal_t* prop,
+                              int n_seq, const dsmc_seq_t* seqs, const int* stage, void* ws, size_t ws_bytes,
+                              void* stream);
 
 /* ---- Measurement: CUDA-event timing of the fused exp / tile-sum kernel (the N x N part of
  * Algorithm 1), recorded on the stream that kernel runs on. */

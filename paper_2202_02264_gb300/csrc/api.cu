@@ -453,14 +453,18 @@ dsmc_status_t do_init(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& m
 constexpr int kDefaultFusedMaxMerges = 32;
 constexpr size_t kFusedSmemLimit = 220 * 1024;
 
+// Smallest cluster size whose per-CTA shared memory fits (0: the fused level never fits).
+int fused_min_cluster(const Plan& p) {
+  for (int C = 1; C <= 16; C *= 2)
+    if (fused_level_smem(p.D, p.N, C) <= kFusedSmemLimit) return C;
+  return 0;
+}
+
 int fused_policy(const Plan& p, const dsmc_config_t* cfg, int M) {
   if (!p.dense) return 0;
   const int cap = cfg->fused_max_merges == 0 ? kDefaultFusedMaxMerges : cfg->fused_max_merges;
   if (cap < 0 || M > cap) return 0;
-  int C = 1;
-  while (C < 16 && (size_t)M * C * 2 <= 152 && p.N / (2 * C) >= 32) C *= 2;
-  if (fused_level_smem(p.D, p.N, C) > kFusedSmemLimit) return 0;
-  return C;
+  return fused_min_cluster(p);
 }
 
 // Largest cluster size <= C that the device can schedule for this shape (queried once).
@@ -486,12 +490,26 @@ int fused_schedulable(const Plan& p, const MergeArgs& a, int C) {
   return ok;
 }
 
-// The launches of one level: M combinations, either of the single sequence in `st` (items
-// null) or the batched list items[0..M) over the sequences `seqs`, in chunks of Mc.
-dsmc_status_t launch_level(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& mp, const float* y,
+// Whether a sequence's level with M combinations runs as the fused single-launch level.
+// The rule depends only on the sequence's own level (never on what else is launched with
+// it), so a sequence's result is the same alone, in a batch or in a serving mix.
+bool fused_eligible(const Plan& p, const dsmc_config_t* cfg, int M) { return fused_policy(p, cfg, M) > 0; }
+
+// Cluster size for a fused launch of M combinations: C doubles while the launch still
+// fills at most one wave of the SMs and every CTA keeps at least 32 rows.
+int fused_cluster(const Plan& p, int M) {
+  int C = 1;
+  while (C < 16 && (size_t)M * C * 2 <= 152 && p.N / (2 * C) >= 32) C *= 2;
+  return std::max(C, fused_min_cluster(p));
+}
+
+// The launches of M combinations: of the single sequence in `st` at `level` (items null),
+// or the list items[0..M) over the sequences `seqs` (levels per item), in chunks of Mc,
+// either as fused levels or through the split kernels.
+dsmc_status_t launch_combs(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& mp, const float* y,
                            int level, int conditional, dsmc_state_t* st, const WsPtrs& w, cudaStream_t s,
-                           int M, const CombItem* items, const SeqDesc* seqs) {
-  const int Cf = fused_policy(p, cfg, M);
+                           int M, const CombItem* items, const SeqDesc* seqs, bool fused) {
+  const int Cf = fused ? fused_cluster(p, M) : 0;
   for (int m0 = 0; m0 < M; m0 += p.Mc) {
     MergeArgs a = merge_args(p, cfg, y, level, conditional, st, w);
     a.prop_mean = mp.prop_mean;
@@ -532,8 +550,9 @@ dsmc_status_t launch_level(const Plan& p, const dsmc_config_t* cfg, const ParamB
 dsmc_status_t do_level(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& mp,
                        const float* y, int level, int conditional, dsmc_state_t* st,
                        const WsPtrs& w, cudaStream_t s) {
-  return launch_level(p, cfg, mp, y, level, conditional, st, w, s, merges_at_level(p.K, level), nullptr,
-                      nullptr);
+  const int M = merges_at_level(p.K, level);
+  return launch_combs(p, cfg, mp, y, level, conditional, st, w, s, M, nullptr, nullptr,
+                      fused_eligible(p, cfg, M));
 }
 
 dsmc_status_t do_resolve(const Plan& p, const dsmc_state_t* st, float* traj, double* mean,
@@ -658,6 +677,7 @@ struct BatchLayout {
   Plan p;                        // merge workspace for Mc combinations (K = the longest sequence)
   int n_seq = 0, Lmax = 0;
   std::vector<int> level_start;  // [Lmax + 1] offsets of each level's items
+  std::vector<int> level_fused;  // [Lmax] end of the level's fused items (they come first)
   std::vector<size_t> map_off;   // per sequence: byte offset of its first / last maps
   size_t n_items = 0;
   size_t o_desc = 0, o_items = 0, o_maps = 0, o_star = 0, total = 0;
@@ -682,10 +702,16 @@ dsmc_status_t batch_layout(const dsmc_config_t* cfg, const dsmc_model_t* model, 
   bl.n_seq = n_seq;
   bl.Lmax = levels_of(Kmax);
   bl.level_start.assign(bl.Lmax + 1, 0);
+  bl.level_fused.assign(bl.Lmax, 0);
   for (int l = 0; l < bl.Lmax; ++l) {
-    long long cnt = 0;
-    for (int i = 0; i < n_seq; ++i) cnt += merges_at_level(K[i], l);
+    long long cnt = 0, cf = 0;
+    for (int i = 0; i < n_seq; ++i) {
+      const int M = merges_at_level(K[i], l);
+      cnt += M;
+      if (M > 0 && fused_eligible(bl.p, cfg, M)) cf += M;
+    }
     bl.level_start[l + 1] = bl.level_start[l] + (int)cnt;
+    bl.level_fused[l] = bl.level_start[l] + (int)cf;
   }
   bl.n_items = (size_t)items;
   size_t o = bl.p.total;
@@ -719,9 +745,15 @@ dsmc_status_t batch_tables(const dsmc_config_t* cfg, const BatchLayout& bl, cons
     d.y = q.y;
     d.logL = q.state.logL;
     d.pairs = q.state.pairs;
-    d.first = reinterpret_cast<int32_t*>(ws + bl.map_off[i]);
-    d.last = d.first + 2 * (size_t)q.K * N;
-    d.star = reinterpret_cast<int32_t*>(ws + bl.o_star) + 2 * (size_t)i;
+    if (q.maps) {
+      d.first = static_cast<int32_t*>(q.maps);
+      d.last = d.first + 2 * (size_t)q.K * N;
+      d.star = d.last + 2 * (size_t)q.K * N;
+    } else {
+      d.first = reinterpret_cast<int32_t*>(ws + bl.map_off[i]);
+      d.last = d.first + 2 * (size_t)q.K * N;
+      d.star = reinterpret_cast<int32_t*>(ws + bl.o_star) + 2 * (size_t)i;
+    }
     d.prop_mean = q.prop_mean;
     d.prop_std = q.prop_std;
     d.seed = q.seed;
@@ -731,10 +763,11 @@ dsmc_status_t batch_tables(const dsmc_config_t* cfg, const BatchLayout& bl, cons
   items.resize(bl.n_items);
   std::vector<int> off(bl.n_seq, 0);  // per sequence: combinations of the levels so far
   for (int l = 0; l < bl.Lmax; ++l) {
-    size_t at = bl.level_start[l];
+    size_t at_f = bl.level_start[l], at_s = bl.level_fused[l];
     for (int i = 0; i < bl.n_seq; ++i) {
       const int M = merges_at_level(seqs[i].K, l);
-      for (int m = 0; m < M; ++m) items[at++] = CombItem{i, m, off[i] + m};
+      const bool fz = M > 0 && fused_eligible(bl.p, cfg, M);
+      for (int m = 0; m < M; ++m) items[fz ? at_f++ : at_s++] = CombItem{i, m, off[i] + m, l};
       off[i] += M;
     }
   }
@@ -768,6 +801,12 @@ std::vector<int> batch_lengths(int n_seq, const dsmc_seq_t* seqs) {
   std::vector<int> K(n_seq);
   for (int i = 0; i < n_seq; ++i) K[i] = seqs[i].K;
   return K;
+}
+
+// The root-draw pair of sequence i: in its own maps scratch, or slot i of `stars`.
+int32_t* seq_star(const dsmc_seq_t& q, int N, char* stars, int i) {
+  if (q.maps) return static_cast<int32_t*>(q.maps) + 4 * (size_t)q.K * N;
+  return reinterpret_cast<int32_t*>(stars) + 2 * (size_t)i;
 }
 
 // Everything of a batched call that the launches need.
@@ -819,6 +858,9 @@ dsmc_status_t batch_launch(const dsmc_config_t* cfg, const dsmc_model_t* model, 
   char* b = static_cast<char*>(ws);
   DSMC_CUDA(cudaMemsetAsync(br.w.status, 0, sizeof(int), s), "reset status");
   DSMC_CUDA(cudaMemsetAsync(b + bl.o_star, 0, (size_t)bl.n_seq * 2 * sizeof(int32_t), s), "reset stars");
+  for (int i = 0; i < bl.n_seq; ++i)
+    if (seqs[i].maps)
+      DSMC_CUDA(cudaMemsetAsync(seq_star(seqs[i], p.N, nullptr, i), 0, 2 * sizeof(int32_t), s), "reset star");
   // Algorithm 2 per sequence
   for (int i = 0; i < bl.n_seq; ++i) {
     const dsmc_seq_t& q = seqs[i];
@@ -844,9 +886,14 @@ dsmc_status_t batch_launch(const dsmc_config_t* cfg, const dsmc_model_t* model, 
   const CombItem* items = reinterpret_cast<const CombItem*>(b + bl.o_items);
   dsmc_state_t none = {nullptr, nullptr, nullptr, nullptr};
   for (int l = 0; l < bl.Lmax; ++l) {
-    const int M = bl.level_start[l + 1] - bl.level_start[l];
-    if (M > 0)
-      DSMC_TRY(launch_level(p, cfg, br.mp, nullptr, l, 0, &none, br.w, s, M, items + bl.level_start[l], descs));
+    const int Mf = bl.level_fused[l] - bl.level_start[l];
+    const int Ms = bl.level_start[l + 1] - bl.level_fused[l];
+    if (Mf > 0)
+      DSMC_TRY(launch_combs(p, cfg, br.mp, nullptr, l, 0, &none, br.w, s, Mf, items + bl.level_start[l], descs,
+                            true));
+    if (Ms > 0)
+      DSMC_TRY(launch_combs(p, cfg, br.mp, nullptr, l, 0, &none, br.w, s, Ms, items + bl.level_fused[l], descs,
+                            false));
   }
   // resolution per sequence
   for (int i = 0; i < bl.n_seq; ++i) {
@@ -856,10 +903,148 @@ dsmc_status_t batch_launch(const dsmc_config_t* cfg, const dsmc_model_t* model, 
     Plan pi;
     make_plan(&c, model, pi, 1, true);
     WsPtrs wi = br.w;
-    wi.star = reinterpret_cast<int32_t*>(b + bl.o_star) + 2 * (size_t)i;
+    wi.star = seq_star(q, p.N, b + bl.o_star, i);
     const bool cond = q.x_ref_in != nullptr;
     if (cond && q.K == 1) {
       DSMC_CUDA(launch_k1_star(q.state.logw, p.N, q.seed, q.counter_base, wi.star, s), "star kernel");
+      prof_count(1);
+    }
+    dsmc_state_t st = q.state;
+    DSMC_TRY(do_resolve(pi, &st, nullptr, q.mean_out, q.m2_out, cond ? q.x_ref_out : nullptr, wi, s));
+    if (q.logL_out)
+      DSMC_CUDA(cudaMemcpyAsync(q.logL_out, q.state.logL, sizeof(double), cudaMemcpyDeviceToDevice, s),
+                "logL copy");
+  }
+  return DSMC_OK;
+}
+
+// ---- Continuous batching: one tick = one stage of every sequence of the call.
+// Workspace: the merge workspace for Mc combinations (Mc = the launch cap), then the tick's
+// descriptor table and its combination list.
+dsmc_status_t serve_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p) {
+  dsmc_config_t c = *cfg;
+  c.K = 2;
+  DSMC_TRY(check_config(&c, model));
+  const int cap = cfg->max_merges_per_launch > 0 ? cfg->max_merges_per_launch : kDefaultMergeCap;
+  make_plan(&c, model, p, cap, true);
+  return DSMC_OK;
+}
+
+int level_offset(int K, int level) {
+  int off = 0;
+  for (int l = 0; l < level; ++l) off += merges_at_level(K, l);
+  return off;
+}
+
+dsmc_status_t serve_tick(const dsmc_config_t* cfg, const dsmc_model_t* model, const dsmc_proposal_t* prop,
+                         int n_seq, const dsmc_seq_t* seqs, const int* stage, void* ws, size_t ws_bytes,
+                         cudaStream_t s) {
+  DSMC_TRY(check_batch(cfg, model, prop, n_seq, seqs));
+  if (!stage) return fail(DSMC_ERR_INVALID_ARG, "null stage array");
+  for (int i = 0; i < n_seq; ++i) {
+    if (!seqs[i].maps) return fail(DSMC_ERR_INVALID_ARG, "serving needs every sequence's maps scratch");
+    if (stage[i] < -1 || stage[i] > levels_of(seqs[i].K)) return fail(DSMC_ERR_INVALID_ARG, "stage out of range");
+  }
+  Plan p;
+  DSMC_TRY(serve_plan(cfg, model, p));
+  if (!ws) return fail(DSMC_ERR_INVALID_ARG, "null workspace");
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return fail(DSMC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  ParamBuf mp;
+  mp.prop_mean = nullptr;
+  mp.prop_std = nullptr;
+  dsmc_proposal_t pp = *prop;
+  pp.mean = nullptr;
+  pp.std = nullptr;
+  DSMC_TRY(make_params(p.D, model, &pp, mp));
+  const WsPtrs w = ws_ptrs(p, ws);
+  char* b = static_cast<char*>(ws);
+  const int N = p.N;
+  // tables: descriptors, then the combinations (fused-eligible first)
+  std::vector<SeqDesc> desc(n_seq);
+  std::vector<CombItem> fz, sp;
+  for (int i = 0; i < n_seq; ++i) {
+    const dsmc_seq_t& q = seqs[i];
+    SeqDesc& d = desc[i];
+    d.K = q.K;
+    d.L = levels_of(q.K);
+    d.X = q.state.X;
+    d.logw = q.state.logw;
+    d.y = q.y;
+    d.logL = q.state.logL;
+    d.pairs = q.state.pairs;
+    d.first = static_cast<int32_t*>(q.maps);
+    d.last = d.first + 2 * (size_t)q.K * N;
+    d.star = d.last + 2 * (size_t)q.K * N;
+    d.prop_mean = q.prop_mean;
+    d.prop_std = q.prop_std;
+    d.seed = q.seed;
+    d.base = q.counter_base;
+    d.conditional = q.x_ref_in != nullptr ? 1 : 0;
+    const int l = stage[i];
+    if (l >= 0 && l < d.L) {
+      const int M = merges_at_level(q.K, l);
+      const int off = level_offset(q.K, l);
+      std::vector<CombItem>& dst = fused_eligible(p, cfg, M) ? fz : sp;
+      for (int m = 0; m < M; ++m) dst.push_back(CombItem{i, m, off + m, l});
+    }
+  }
+  const size_t o_desc = align256(p.total);
+  const size_t o_items = align256(o_desc + (size_t)n_seq * sizeof(SeqDesc));
+  const size_t need = o_items + (fz.size() + sp.size()) * sizeof(CombItem);
+  if (ws_bytes < need) return fail(DSMC_ERR_WORKSPACE, "workspace too small for this tick");
+  std::vector<CombItem> items(fz);
+  items.insert(items.end(), sp.begin(), sp.end());
+  DSMC_CUDA(cudaMemcpyAsync(b + o_desc, desc.data(), desc.size() * sizeof(SeqDesc), cudaMemcpyHostToDevice, s),
+            "descriptor upload");
+  if (!items.empty())
+    DSMC_CUDA(cudaMemcpyAsync(b + o_items, items.data(), items.size() * sizeof(CombItem), cudaMemcpyHostToDevice,
+                              s), "item upload");
+  DSMC_CUDA(cudaStreamSynchronize(s), "upload synchronize");
+  DSMC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), s), "reset status");
+  // stage -1: Algorithm 2
+  for (int i = 0; i < n_seq; ++i) {
+    if (stage[i] != -1) continue;
+    const dsmc_seq_t& q = seqs[i];
+    DSMC_CUDA(cudaMemsetAsync(desc[i].star, 0, 2 * sizeof(int32_t), s), "reset star");
+    ParamBuf mpi = mp;
+    set_prop(p.D, mpi, q.prop_mean, q.prop_std);
+    InitArgs ia;
+    ia.K = q.K;
+    ia.N = N;
+    ia.d = p.d;
+    ia.seed = q.seed;
+    ia.base = q.counter_base;
+    ia.y = q.y;
+    ia.x_ref = q.x_ref_in;
+    ia.X = q.state.X;
+    ia.logw = q.state.logw;
+    ia.logL = q.state.logL;
+    ia.status = w.status;
+    DSMC_CUDA(launch_init(p.D, ia, mpi.bytes, s), "init kernel");
+    prof_count(1);
+  }
+  // merge stages: every sequence's level, together
+  const SeqDesc* descs = reinterpret_cast<const SeqDesc*>(b + o_desc);
+  const CombItem* dev_items = reinterpret_cast<const CombItem*>(b + o_items);
+  dsmc_state_t none = {nullptr, nullptr, nullptr, nullptr};
+  if (!fz.empty())
+    DSMC_TRY(launch_combs(p, cfg, mp, nullptr, 0, 0, &none, w, s, (int)fz.size(), dev_items, descs, true));
+  if (!sp.empty())
+    DSMC_TRY(launch_combs(p, cfg, mp, nullptr, 0, 0, &none, w, s, (int)sp.size(), dev_items + fz.size(), descs,
+                          false));
+  // stage L: resolve
+  for (int i = 0; i < n_seq; ++i) {
+    const dsmc_seq_t& q = seqs[i];
+    if (stage[i] != desc[i].L) continue;
+    dsmc_config_t c = *cfg;
+    c.K = q.K;
+    Plan pi;
+    make_plan(&c, model, pi, 1, true);
+    WsPtrs wi = w;
+    wi.star = desc[i].star;
+    const bool cond = q.x_ref_in != nullptr;
+    if (cond && q.K == 1) {
+      DSMC_CUDA(launch_k1_star(q.state.logw, N, q.seed, q.counter_base, wi.star, s), "star kernel");
       prof_count(1);
     }
     dsmc_state_t st = q.state;
@@ -1103,6 +1288,30 @@ dsmc_status_t dsmc_smooth_batch(const dsmc_config_t* cfg, const dsmc_model_t* mo
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DSMC_TRY(batch_upload(cfg, br, seqs, ws, s));
   return batch_launch(cfg, model, br, seqs, ws, s);
+}
+
+size_t dsmc_seq_maps_bytes(int K, int N) {
+  if (K < 1 || N < 1) return 0;
+  return (size_t)4 * K * N * sizeof(int32_t) + 2 * sizeof(int32_t);
+}
+
+dsmc_status_t dsmc_serve_workspace_size(const dsmc_config_t* cfg, const dsmc_model_t* model, int max_seq,
+                                        int max_combinations, size_t* bytes) {
+  if (!cfg || !model || !bytes) return fail(DSMC_ERR_INVALID_ARG, "null argument");
+  if (max_seq < 1 || max_combinations < 0) return fail(DSMC_ERR_INVALID_ARG, "max_seq >= 1, max_combinations >= 0");
+  Plan p;
+  DSMC_TRY(serve_plan(cfg, model, p));
+  const size_t o_desc = align256(p.total);
+  const size_t o_items = align256(o_desc + (size_t)max_seq * sizeof(SeqDesc));
+  *bytes = align256(o_items + (size_t)max_combinations * sizeof(CombItem));
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_serve_tick(const dsmc_config_t* cfg, const dsmc_model_t* model, const dsmc_proposal_t* prop,
+                              int n_seq, const dsmc_seq_t* seqs, const int* stage, void* ws, size_t ws_bytes,
+                              void* stream) {
+  if (!cfg || !model) return fail(DSMC_ERR_INVALID_ARG, "null argument");
+  return serve_tick(cfg, model, prop, n_seq, seqs, stage, ws, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

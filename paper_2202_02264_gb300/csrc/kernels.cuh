@@ -53,10 +53,10 @@ struct SeqDesc {
   int conditional;
 };
 
-// One combination of a batched level: sequence, combination index within the level, and
-// its row in the sequence's pairs array.
+// One combination of a batched launch: sequence, combination index within its level, its
+// row in the sequence's pairs array, and the level (one launch may mix levels).
 struct CombItem {
-  int seq, m, gid;
+  int seq, m, gid, level;
 };
 
 struct MergeArgs {
@@ -100,7 +100,7 @@ __host__ __device__ __forceinline__ void merge_geom(int K, int level, int m, int
 
 // Everything combination s of a launch needs from its sequence.
 struct Comb {
-  int K, m, gid, at, c, b;
+  int K, level, m, gid, at, c, b;
   bool root;
   int conditional;
   const float* X;
@@ -121,6 +121,7 @@ __device__ __forceinline__ Comb comb_of(const MergeArgs& a, int s) {
   Comb cb;
   if (a.items == nullptr) {
     cb.K = a.K;
+    cb.level = a.level;
     cb.m = a.m0 + s;
     cb.gid = a.gid0 + s;
     cb.root = a.root != 0;
@@ -141,9 +142,10 @@ __device__ __forceinline__ Comb comb_of(const MergeArgs& a, int s) {
     const CombItem it = a.items[a.m0 + s];
     const SeqDesc& q = a.seqs[it.seq];
     cb.K = q.K;
+    cb.level = it.level;
     cb.m = it.m;
     cb.gid = it.gid;
-    cb.root = (a.level == q.L - 1);
+    cb.root = (it.level == q.L - 1);
     cb.conditional = q.conditional;
     cb.X = q.X;
     cb.logw = q.logw;
@@ -158,7 +160,7 @@ __device__ __forceinline__ Comb comb_of(const MergeArgs& a, int s) {
     cb.seed = q.seed;
     cb.base = q.base;
   }
-  merge_geom(cb.K, a.level, cb.m, cb.at, cb.c, cb.b);
+  merge_geom(cb.K, cb.level, cb.m, cb.at, cb.c, cb.b);
   return cb;
 }
 

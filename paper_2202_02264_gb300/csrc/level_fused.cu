@@ -67,10 +67,10 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   const int gid = cb.gid, K = cb.K;
   const int at = cb.at, c = cb.c, b = cb.b;
   const int N = a.N, d = a.d, B = a.B, nT = a.nT, nTp = a.nTp;
-  const bool left_leaf = (a.level == 0);
+  const bool left_leaf = (cb.level == 0);
   const int sR = b - c + 1;
   const bool right_leaf = (sR == 1);
-  const int bufL = a.level & 1, bufR = ceil_log2(sR) & 1, bufO = (a.level + 1) & 1;
+  const int bufL = cb.level & 1, bufR = ceil_log2(sR) & 1, bufO = (cb.level + 1) & 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rows_per = (N + C - 1) / C;
   const int lo = min(r * rows_per, N), hi = min(lo + rows_per, N);

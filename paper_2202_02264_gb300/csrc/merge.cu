@@ -115,10 +115,10 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
   const Comb cb = comb_of(a, s);
   const int at = cb.at, c = cb.c, b = cb.b;
   const int N = a.N, d = a.d;
-  const bool left_leaf = (a.level == 0);
+  const bool left_leaf = (cb.level == 0);
   const int sR = b - c + 1;
   const bool right_leaf = (sR == 1);
-  const int bufL = a.level & 1;
+  const int bufL = cb.level & 1;
   const int bufR = ceil_log2(sR) & 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -467,7 +467,7 @@ __device__ __forceinline__ SlotOut slot_out(const MergeArgs& a, const Comb& cb, 
   const int at = cb.at, c = cb.c, b = cb.b, K = cb.K;
   const int N = a.N;
   const int sR = b - c + 1;
-  const int bufL = a.level & 1, bufR = ceil_log2(sR) & 1, bufO = (a.level + 1) & 1;
+  const int bufL = cb.level & 1, bufR = ceil_log2(sR) & 1, bufO = (cb.level + 1) & 1;
   SlotOut o;
   o.pl = cb.pairs + (size_t)cb.gid * 2 * N;
   o.pr = o.pl + N;
@@ -475,7 +475,7 @@ __device__ __forceinline__ SlotOut slot_out(const MergeArgs& a, const Comb& cb, 
   o.last_out = cb.last + ((size_t)bufO * K + at) * N;
   o.first_L = cb.first + ((size_t)bufL * K + at) * N;
   o.last_R = cb.last + ((size_t)bufR * K + c) * N;
-  o.left_leaf = (a.level == 0);
+  o.left_leaf = (cb.level == 0);
   o.right_leaf = (sR == 1);
   o.N = N;
   o.star = cb.star;
@@ -749,10 +749,10 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(MergeArgs a) {
   const Comb cb = comb_of(a, s);
   const int at = cb.at, c = cb.c, b = cb.b, K = cb.K;
   const int N = a.N;
-  const bool left_leaf = (a.level == 0);
+  const bool left_leaf = (cb.level == 0);
   const int sR = b - c + 1;
   const bool right_leaf = (sR == 1);
-  const int bufL = a.level & 1, bufR = ceil_log2(sR) & 1, bufO = (a.level + 1) & 1;
+  const int bufL = cb.level & 1, bufR = ceil_log2(sR) & 1, bufO = (cb.level + 1) & 1;
   const int n = blockIdx.y * kEpiThreads + threadIdx.x;
   const int32_t* pl = cb.pairs + (size_t)cb.gid * 2 * N;
   const int32_t* pr = pl + N;

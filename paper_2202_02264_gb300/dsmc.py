@@ -68,7 +68,7 @@ class Seq(C.Structure):
     _fields_ = [("K", C.c_int), ("y", C.c_void_p), ("prop_mean", C.c_void_p), ("prop_std", C.c_void_p),
                 ("state", State), ("mean_out", C.c_void_p), ("m2_out", C.c_void_p),
                 ("logL_out", C.c_void_p), ("x_ref_in", C.c_void_p), ("x_ref_out", C.c_void_p),
-                ("seed", C.c_uint64), ("counter_base", C.c_uint32)]
+                ("seed", C.c_uint64), ("counter_base", C.c_uint32), ("maps", C.c_void_p)]
 
 
 _lib = None
@@ -79,7 +79,8 @@ EXPORTS = ["dsmc_status_string", "dsmc_last_error", "dsmc_state_sizes", "dsmc_wo
            "dsmc_conditional_smooth", "dsmc_smooth_noalloc", "dsmc_stream_status",
            "dsmc_profile_enable",
            "dsmc_profile_read", "dsmc_debug_philox", "dsmc_debug_merge_weights",
-           "dsmc_batch_workspace_size", "dsmc_batch_prepare", "dsmc_batch_run", "dsmc_smooth_batch"]
+           "dsmc_batch_workspace_size", "dsmc_batch_prepare", "dsmc_batch_run", "dsmc_smooth_batch",
+           "dsmc_seq_maps_bytes", "dsmc_serve_workspace_size", "dsmc_serve_tick"]
 
 
 def library_path() -> str:
@@ -124,6 +125,10 @@ def load(build_if_needed: bool = False) -> C.CDLL:
         lib.dsmc_debug_philox.argtypes = [vp, C.c_int64, C.c_uint64, vp, vp]
         lib.dsmc_debug_merge_weights.argtypes = [cfgp, modp, C.c_int, C.c_int, vp, vp, vp, vp, vp,
                                                  vp, C.POINTER(C.c_int), vp, sz, vp]
+        lib.dsmc_seq_maps_bytes.restype = C.c_size_t
+        lib.dsmc_seq_maps_bytes.argtypes = [C.c_int, C.c_int]
+        lib.dsmc_serve_workspace_size.argtypes = [cfgp, modp, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
+        lib.dsmc_serve_tick.argtypes = [cfgp, modp, prop_p, C.c_int, C.POINTER(Seq), C.POINTER(C.c_int), vp, sz, vp]
         seqp = C.POINTER(Seq)
         lib.dsmc_batch_workspace_size.argtypes = [cfgp, modp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         for name in ("dsmc_batch_prepare", "dsmc_batch_run", "dsmc_smooth_batch"):
@@ -184,9 +189,18 @@ def make_proposal(m: W.SSM, K: int, device="cuda"):
     """The C proposal struct and the device arrays it points into (kept alive by caller)."""
     if m.prop_kind == W.PROP_OBS:
         return Proposal(W.PROP_OBS, float(m.prop_scale), None, None, int(m.nu)), ()
-    mean = torch.as_tensor(np.asarray(m.prop_mean, np.float32)[:K].reshape(K, m.d).copy(), device=device)
-    std = torch.as_tensor(np.asarray(m.prop_std, np.float32)[:K].reshape(K, m.d).copy(), device=device)
+    mean = torch.as_tensor(proposal_rows(m.prop_mean, K, m.d), device=device)
+    std = torch.as_tensor(proposal_rows(m.prop_std, K, m.d), device=device)
     return Proposal(W.PROP_GAUSS, 1.0, mean.data_ptr(), std.data_ptr(), int(m.nu)), (mean, std)
+
+
+def proposal_rows(a, K: int, d: int) -> np.ndarray:
+    """K rows of a per-t proposal array as FP32 [K][d]; a single row is a stationary proposal
+    and is repeated."""
+    a = np.asarray(a, np.float32).reshape(-1, d)
+    if a.shape[0] == 1:
+        return np.repeat(a, K, axis=0)
+    return np.ascontiguousarray(a[:K])
 
 
 # ---------------------------------------------------------------- C-named wrappers
@@ -325,6 +339,24 @@ def dsmc_smooth_batch(cfg, model, prop, seqs, ws, stream=None):
     _batch_call("dsmc_smooth_batch", cfg, model, prop, seqs, ws, stream)
 
 
+def dsmc_seq_maps_bytes(K: int, N: int) -> int:
+    return int(load().dsmc_seq_maps_bytes(int(K), int(N)))
+
+
+def dsmc_serve_workspace_size(cfg: Config, model: HostModel, max_seq: int, max_combinations: int) -> int:
+    out = C.c_size_t(0)
+    _check(load().dsmc_serve_workspace_size(C.byref(cfg), C.byref(model.struct), int(max_seq),
+                                            int(max_combinations), C.byref(out)), "dsmc_serve_workspace_size")
+    return int(out.value)
+
+
+def dsmc_serve_tick(cfg, model, prop, seqs, stages, ws, stream=None):
+    arr = (Seq * len(seqs))(*seqs)
+    st = (C.c_int * len(stages))(*[int(s) for s in stages])
+    _check(load().dsmc_serve_tick(C.byref(cfg), C.byref(model.struct), C.byref(prop), len(seqs), arr, st,
+                                  _ptr(ws), ws.numel(), _stream(stream)), "dsmc_serve_tick")
+
+
 # ---------------------------------------------------------------- buffer owner
 class Smoother:
     """Device buffers for one (model, K, N) and the calls of the C ABI over them.
@@ -443,12 +475,8 @@ class BatchSmoother:
             self.y[i] = ys[i]
             if self.model.prop_kind == W.PROP_GAUSS:
                 K = self.Ks[i]
-                self.pm[i] = torch.as_tensor(np.asarray(self.model.prop_mean, np.float32)[:K], device=ys[i].device).contiguous() \
-                    if self.model.prop_mean.shape[0] >= K else torch.full((K, self.d), float(self.model.prop_mean[0, 0]),
-                                                                          dtype=torch.float32, device=ys[i].device)
-                self.ps[i] = torch.as_tensor(np.asarray(self.model.prop_std, np.float32)[:K], device=ys[i].device).contiguous() \
-                    if self.model.prop_std.shape[0] >= K else torch.full((K, self.d), float(self.model.prop_std[0, 0]),
-                                                                         dtype=torch.float32, device=ys[i].device)
+                self.pm[i] = torch.as_tensor(proposal_rows(self.model.prop_mean, K, self.d), device=ys[i].device)
+                self.ps[i] = torch.as_tensor(proposal_rows(self.model.prop_std, K, self.d), device=ys[i].device)
             self.x_in[i] = x_ref_in[i] if x_ref_in is not None else None
             self.x_out[i] = x_ref_out[i] if x_ref_out is not None else None
 
@@ -464,7 +492,7 @@ class BatchSmoother:
                            self.logL_out.data_ptr() + 8 * i,
                            self.x_in[i].data_ptr() if self.x_in[i] is not None else None,
                            self.x_out[i].data_ptr() if self.x_out[i] is not None else None,
-                           int(self.seeds[i]) & (2**64 - 1), int(self.counter_base[i])))
+                           int(self.seeds[i]) & (2**64 - 1), int(self.counter_base[i]), None))
         return out
 
     def prepare(self, stream=None):
