@@ -50,6 +50,7 @@ TRAFFIC_PER_LAUNCH = {
 
 WORKLOADS = {
     "batched_lgssm_d4": dict(kind="batch", n_seq=256, N=512, resampler="dense"),
+    "serving": dict(kind="serving", n_req=300, rate=2000.0, resampler="dense"),
     "lgssm_d8": dict(K=1024, N=1024, resampler="dense"),
     "lgssm_1d": dict(K=32, N=64, resampler="dense"),
     "sv": dict(K=4096, N=4096, resampler="dense"),
@@ -155,6 +156,10 @@ def run_reference(args):
     if spec.get("kind") == "batch":   # the oracle on the batch's first sequence
         bw = W.batch_workload(spec["n_seq"], spec["N"])
         wl = W.Workload(args.workload, bw.model, int(bw.Ks[0]), bw.N, bw.ys[0], None)
+    elif spec.get("kind") == "serving":   # the oracle on the stream's first request
+        from paper_2202_02264_gb300 import serving as S
+        r0 = S.request_stream(1, spec["rate"])[0]
+        wl = W.Workload(args.workload, r0.model, r0.K, r0.N, r0.y, None)
     else:
         wl = W.workload(args.workload.replace("_rs", ""), K=spec["K"], N=spec["N"])
     from oracle import core
@@ -487,6 +492,88 @@ def run_batched(args):
         torch.distributed.destroy_process_group()
 
 
+def run_serving(args):
+    """The serving workload: a Poisson stream of smoothing requests (70 % linear-Gaussian
+    with d in {2, 8, 32}, 30 % stochastic volatility; K log-uniform in [64, 8192]; N in
+    {256, 1024, 4096}) served by continuous batching under a 150 GB budget.  One pass at the
+    stated arrival rate (2000 / s: above capacity, so latency includes queueing; its
+    throughput is the saturation throughput), then the same requests at 70 % of the
+    measured capacity."""
+    import torch
+
+    from paper_2202_02264_gb300 import dsmc, serving as S
+
+    world, rank, lrank = _dist()
+    torch.cuda.set_device(lrank if world > 1 else 0)
+    spec = WORKLOADS[args.workload]
+    n = spec["n_req"]
+    reqs = S.request_stream(n, spec["rate"])
+    units = sum(r.N * r.K for r in reqs)
+    # warm-up: a short stream through the same lanes
+    warm = S.request_stream(24, spec["rate"], seed=7, K_range=(64, 256))
+    for i in range(args.warmup):
+        S.Server().run(warm, realtime=False)
+    torch.cuda.synchronize()
+
+    def serve(stream):
+        srv = S.Server(hbm_budget_bytes=150 * 10**9)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = srv.run(stream, realtime=True)
+        t1 = time.perf_counter()
+        lat = np.array([r.latency for r in res]) * 1e3
+        return srv, res, t1 - t0, lat
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    dsmc.dsmc_profile_enable(True)
+    srv, res, makespan, lat = serve(reqs)
+    rs_ms, rs_n, rs_pairs, launches = dsmc.dsmc_profile_read()
+    dsmc.dsmc_profile_enable(False)
+    clk = clocks.stop()
+    value = units / makespan
+    capacity = len(res) / makespan
+    rate70 = 0.7 * capacity
+    scale = spec["rate"] / rate70
+    reqs70 = [S.Request(r.rid, r.lane, r.model, r.N, r.y, r.seed, r.arrival * scale) for r in reqs]
+    _, res70, makespan70, lat70 = serve(reqs70)
+
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    ex2_peak = MUFU_EX2_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9
+    achieved = rs_pairs / (rs_ms / 1e3) / 1e9 if rs_ms > 0 else None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+            "ms_per_step": 1e3 * makespan, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f32", "data": "synthetic",
+            "config": {"workload": args.workload, "requests": n, "arrival_rate_per_s": spec["rate"],
+                       "mix": "70% linear-Gaussian d in {2, 8, 32}, 30% stochastic volatility",
+                       "K": "log-uniform [64, 8192]", "N": [256, 1024, 4096], "sum_N_K": units,
+                       "hbm_budget_bytes": 150 * 10**9,
+                       "serving": "continuous batching, one lane per (model, N, precision), level by level"},
+            "latency_ms": {
+                "stated_rate": {"rate_per_s": spec["rate"], "p50": float(np.percentile(lat, 50)),
+                                "p99": float(np.percentile(lat, 99)), "makespan_s": makespan,
+                                "note": "offered load above capacity: latency includes queueing"},
+                "at_70pct_capacity": {"rate_per_s": rate70, "p50": float(np.percentile(lat70, 50)),
+                                      "p99": float(np.percentile(lat70, 99)), "makespan_s": makespan70,
+                                      "throughput": units / makespan70}},
+            "capacity_req_per_s": capacity,
+            "peak_active_requests": srv.sched.peak_active, "peak_request_bytes": srv.sched.peak_used,
+            "roofline": {"bound": "alu", "kernel": "rowsum_tc_kernel / rowsum_kernel (fused exp / tile sums)",
+                         "achieved": achieved, "peak": ex2_peak, "unit": "Gexp/s",
+                         "frac": achieved / ex2_peak if achieved else None,
+                         "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
+                                        f"({src} max clock)",
+                         "launches": rs_n, "traffic": None},
+            "e2e": {"value": value, "unit": UNIT,
+                    "h2d_bytes_per_step": sum(r.y.size * 4 for r in reqs),
+                    "d2h_bytes_per_step": sum(r.K * r.model.d * 8 + 8 for r in reqs),
+                    "note": "host observations in, host means and logL out, per request"},
+            "clocks": clk, "gpu_launches": launches}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -503,7 +590,7 @@ def main():
         args.warmup = 3
     kind = WORKLOADS[args.workload].get("kind", "single")
     if args.steps is None:
-        args.steps = 10 if kind == "batch" else 400
+        args.steps = {"batch": 10, "serving": 1}.get(kind, 400)
     if args.compute is None:
         args.compute = "bf16" if kind == "batch" else "tf32"
     if args.impl == "reference":
@@ -513,6 +600,8 @@ def main():
         core.build()
         if kind == "batch":
             run_batched(args)
+        elif kind == "serving":
+            run_serving(args)
         else:
             run_ours(args)
 

@@ -94,7 +94,7 @@ typedef struct {
   int K;                      /* time steps, >= 1 */
   int N;                      /* particles, >= 1 (>= 2 when conditional); <= 16384 dense */
   int compute;                /* cross-term precision: DSMC_FP32 (CUDA cores, default),
-                                 DSMC_TF32 (dx <= 8) or DSMC_BF16 (dx <= 16) on the tensor
+                                 DSMC_TF32 (dx <= 16) or DSMC_BF16 (any dx) on the tensor
                                  cores: the whole base-2 exponent alpha_i + beta_j + u_i.v_j
                                  is one MMA, alpha and beta entering as two-term splits in
                                  the MMA type; FP32 accumulate, exp and sums; dense N <= 4096 */

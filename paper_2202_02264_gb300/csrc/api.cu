@@ -326,10 +326,8 @@ dsmc_status_t check_config(const dsmc_config_t* cfg, const dsmc_model_t* model) 
     return fail(DSMC_ERR_UNSUPPORTED, "dense resampling supports N <= 16384; use DSMC_RS");
   if (cfg->compute != DSMC_FP32 && cfg->compute != DSMC_TF32 && cfg->compute != DSMC_BF16)
     return fail(DSMC_ERR_INVALID_ARG, "unknown compute precision");
-  if (cfg->compute == DSMC_TF32 && model->dx > 8)
-    return fail(DSMC_ERR_UNSUPPORTED, "the TF32 tensor-core cross term supports dx <= 8");
-  if (cfg->compute == DSMC_BF16 && model->dx > 16)
-    return fail(DSMC_ERR_UNSUPPORTED, "the BF16 tensor-core cross term supports dx <= 16");
+  if (cfg->compute == DSMC_TF32 && model->dx > 16)
+    return fail(DSMC_ERR_UNSUPPORTED, "the TF32 tensor-core cross term supports dx <= 16");
   if (cfg->compute != DSMC_FP32 && cfg->resampler == DSMC_MULTINOMIAL && cfg->N > 4096)
     return fail(DSMC_ERR_UNSUPPORTED, "the tensor-core cross term supports N <= 4096");
   if (cfg->counter_base >= (1u << 28)) return fail(DSMC_ERR_INVALID_ARG, "counter_base must be < 2^28");

@@ -171,10 +171,13 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
     }
   }
 
+  __syncthreads();  // the column terms are in shared memory: the rows read a sample of them
   // ---------------------------------------------------------------- own rows
   for (int i = lo + threadIdx.x; i < hi; i += NT) {
     float ul[D], ai;
-    const float al = row_terms<D>(mp, a, cb, lastL, left_leaf, i, mu, ul, ai, corrupt);
+    const float al0 = row_terms<D>(mp, a, cb, lastL, left_leaf, i, mu, ul, ai, corrupt);
+    const float dl = row_shift<D, true>(ul, al0, sV, sB, N);
+    const float al = __fsub_rn(al0, dl);
     bad |= isnan(ai);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
     }
     alpha[i] = al;
     sAl[i - lo] = al;
-    const double sh = (double)ai + (double)mp.log_f_max + (double)bstar;
+    const double sh = (double)ai + (double)mp.log_f_max + (double)bstar + (double)dl * kLn2d;
     shift[i] = sh;
     sSh[i - lo] = sh;
   }

@@ -208,12 +208,16 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
       store_mma_row<D>(a.ws.Ub + (size_t)s * a.Nr * a.mma_planes * 32, a.Nr, j, zero, zext, a.compute);
     }
   }
+  __syncthreads();  // the column terms are written: the rows read a sample of them
   // pass 2b: rows  w_i = A xL_i + c - mu,  u_i = log2(e) Q^-1 w_i,
-  //                alpha_i = -log2(e) 1/2 w_i' Q^-1 w_i  (B* is folded into beta)
+  //                alpha_i = -log2(e) 1/2 w_i' Q^-1 w_i - delta_i  (B* is folded into beta,
+  //                delta_i, the row's sampled shift, into shift_i)
   float amax = -INFINITY;
   for (int i = threadIdx.x; i < N; i += kProThreads) {
     float ul[D], ai;
-    const float al = row_terms<D>(mp, a, cb, lastL, left_leaf, i, mu, ul, ai, corrupt);
+    const float al0 = row_terms<D>(mp, a, cb, lastL, left_leaf, i, mu, ul, ai, corrupt);
+    const float dl = row_shift<D, false>(ul, al0, V, beta, N);
+    const float al = __fsub_rn(al0, dl);
     bad |= isnan(ai);
 #pragma unroll
     for (int k = 0; k < D; ++k) U[(size_t)i * D + k] = ul[k];
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
       store_mma_row<D>(a.ws.Ub + (size_t)s * a.Nr * a.mma_planes * 32, a.Nr, i, ul, ext, a.compute);
     }
     alpha[i] = al;
-    shift[i] = (double)ai + (double)mp.log_f_max + (double)bstar;
+    shift[i] = (double)ai + (double)mp.log_f_max + (double)bstar + (double)dl * kLn2d;
     amax = fmaxf(amax, ai);
   }
   amax = warp_max(amax);
@@ -568,6 +572,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 2 : 1) cdf_slots_ker
     n_under = 0;
     nonfinite_s = 0;
   }
+  __syncthreads();  // the counters are zero before any thread adds to them
   const float* U = a.ws.U + (size_t)s * N * D;
   const float* V = a.ws.V + (size_t)s * N * D;
   const float* beta = a.ws.beta + (size_t)s * N;

@@ -155,11 +155,11 @@ __device__ __forceinline__ Item item_of(const MergeArgs& a, int it) {
   return r;
 }
 
-// Column blocks staged ahead (P = 1: 16 x 4 KB, P = 2: 10 x 8 KB) and the refill lag: a
+// Column blocks staged ahead (P = 1: 16 x 4 KB, P = 2: 10 x 8 KB, P = 3: 6 x 12 KB) and the refill lag: a
 // slot is refilled once the epilogue finished its block.
 template <int P>
 __host__ __device__ constexpr int v_slots() {
-  return P == 1 ? 16 : 10;
+  return P == 1 ? 16 : (P == 2 ? 10 : 6);
 }
 constexpr int kRefillLag = 4;
 
@@ -374,10 +374,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
 }
 
 // Dynamic shared memory: 2 row tiles + the column-block ring (72 KB at P = 1, 96 KB at
-// P = 2), padded so that at most two CTAs (2 x 256 TMEM columns) share an SM.
+// P = 2 and at P = 3), padded so that at most two CTAs (2 x 256 TMEM columns) share an SM.
 constexpr size_t kDynSmem = 100 * 1024;
 static_assert((2 + v_slots<1>()) * kTileBytes <= kDynSmem, "staging buffers, one K plane");
 static_assert((2 + v_slots<2>()) * 2 * kTileBytes <= kDynSmem, "staging buffers, two K planes");
+static_assert((2 + v_slots<3>()) * 3 * kTileBytes <= kDynSmem, "staging buffers, three K planes");
 
 template <int KIND, int P>
 cudaError_t launch_t(const MergeArgs& a, cudaStream_t st) {
@@ -396,6 +397,8 @@ cudaError_t launch_t(const MergeArgs& a, cudaStream_t st) {
 cudaError_t launch_rowsum_tc(const MergeArgs& a, cudaStream_t s) {
   if (a.compute == DSMC_BF16 && a.mma_planes == 1) return launch_t<DSMC_BF16, 1>(a, s);
   if (a.compute == DSMC_BF16 && a.mma_planes == 2) return launch_t<DSMC_BF16, 2>(a, s);
+  if (a.compute == DSMC_BF16 && a.mma_planes == 3) return launch_t<DSMC_BF16, 3>(a, s);
+  if (a.compute == DSMC_TF32 && a.mma_planes == 3) return launch_t<DSMC_TF32, 3>(a, s);
   if (a.compute == DSMC_TF32 && a.mma_planes == 1) return launch_t<DSMC_TF32, 1>(a, s);
   if (a.compute == DSMC_TF32 && a.mma_planes == 2) return launch_t<DSMC_TF32, 2>(a, s);
   return cudaErrorInvalidValue;

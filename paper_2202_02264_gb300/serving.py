@@ -285,7 +285,7 @@ class Server:
         self.dsmc = dsmc
         self.device = device
         self.max_comb = int(max_comb_per_tick)
-        self.precision = precision or (lambda m, N: dsmc.BF16 if m.d <= 16 else dsmc.FP32)
+        self.precision = precision or (lambda m, N: dsmc.BF16)
         self.lanes: dict[str, _Lane] = {}
 
         def bytes_of(r: Request) -> int:

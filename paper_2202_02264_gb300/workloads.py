@@ -164,6 +164,11 @@ def workload(name: str, K: Optional[int] = None, N: Optional[int] = None) -> Wor
         K = 512 if K is None else K
         N = 512 if N is None else N
         m, seed = lgssm_d4(), 2264 + 4
+    elif name in ("lgssm_d2", "lgssm_d16", "lgssm_d32"):
+        dd = int(name[len("lgssm_d"):])
+        K = 256 if K is None else K
+        N = 256 if N is None else N
+        m, seed = lgssm_dn(dd), 2264 + 5 + dd
     else:
         raise KeyError(name)
     x, y = simulate(m, K, seed)

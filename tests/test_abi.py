@@ -56,15 +56,17 @@ def test_sizes_and_argument_checks(lib):
     # RS lifts the dense N limit
     c = dsmc.make_config(8, 20000, 1, resampler=dsmc.RS)
     assert dsmc.dsmc_workspace_size(c, hm) > 0
-    # tensor-core precisions: BF16 up to dx = 16, TF32 up to dx = 8, N <= 4096 when dense
+    # tensor-core precisions: BF16 for every dx, TF32 up to dx = 16, N <= 4096 when dense
     assert dsmc.dsmc_workspace_size(dsmc.make_config(8, 64, 1, compute=dsmc.BF16), hm) > 0
     assert dsmc.dsmc_workspace_size(dsmc.make_config(8, 64, 1, compute=dsmc.TF32), hm) > 0
     with pytest.raises(dsmc.DsmcError) as e:
         dsmc.dsmc_workspace_size(dsmc.make_config(8, 8192, 1, compute=dsmc.BF16), hm)
     assert e.value.code == 2
-    hm16 = dsmc.HostModel(W.lgssm_dn(16))
+    hm16, hm32 = dsmc.HostModel(W.lgssm_dn(16)), dsmc.HostModel(W.lgssm_dn(32))
+    assert dsmc.dsmc_workspace_size(dsmc.make_config(8, 64, 1, compute=dsmc.TF32), hm16) > 0
+    assert dsmc.dsmc_workspace_size(dsmc.make_config(8, 64, 1, compute=dsmc.BF16), hm32) > 0
     with pytest.raises(dsmc.DsmcError) as e:
-        dsmc.dsmc_workspace_size(dsmc.make_config(8, 64, 1, compute=dsmc.TF32), hm16)
+        dsmc.dsmc_workspace_size(dsmc.make_config(8, 64, 1, compute=dsmc.TF32), hm32)
     assert e.value.code == 2
 
 
