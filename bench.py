@@ -51,6 +51,7 @@ TRAFFIC_PER_LAUNCH = {
 WORKLOADS = {
     "batched_lgssm_d4": dict(kind="batch", n_seq=256, N=512, resampler="dense"),
     "serving": dict(kind="serving", n_req=300, rate=2000.0, resampler="dense"),
+    "pg_sv": dict(kind="pg", K=4096, N=4096, sweeps=200, resampler="dense"),
     "lgssm_d8": dict(K=1024, N=1024, resampler="dense"),
     "lgssm_1d": dict(K=32, N=64, resampler="dense"),
     "sv": dict(K=4096, N=4096, resampler="dense"),
@@ -574,6 +575,83 @@ def run_serving(args):
         print(json.dumps(line))
 
 
+def run_pg(args):
+    """Particle Gibbs at fixed parameters on the stochastic-volatility model (K = N = 4096):
+    each step is one conditional dSMC sweep (Section 3.2), the reference of the next sweep
+    being the trajectory drawn at the root; reports sweeps / s, N*T/s and the per-t update
+    rate (the fraction of sweeps in which x*_t changed)."""
+    import torch
+
+    from paper_2202_02264_gb300 import dsmc, workloads as W
+
+    world, rank, lrank = _dist()
+    torch.cuda.set_device(lrank if world > 1 else 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spec = WORKLOADS[args.workload]
+    wl = W.workload("sv", K=spec["K"], N=spec["N"])
+    K, N = wl.K, wl.N
+    sweeps = spec["sweeps"] if args.steps is None else args.steps
+    compute = {"fp32": dsmc.FP32, "tf32": dsmc.TF32, "bf16": dsmc.BF16}[args.compute]
+    sm = dsmc.Smoother(wl.model, K, N, seed=2000 + rank, compute=compute)
+    y = torch.as_tensor(wl.y, dtype=torch.float32, device=dev)
+    xa = torch.full((K, 1), float(wl.model.mu), dtype=torch.float32, device=dev)
+    xb = torch.empty_like(xa)
+    changed = torch.zeros((K,), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def sweep(s, count):
+        nonlocal xa, xb
+        sm.set_seed(2000 + rank, counter_base=s)
+        sm.conditional(y, xa, xb)
+        if count:
+            changed.add_((xb != xa).any(1).to(torch.int32))
+        xa, xb = xb, xa
+
+    for s in range(args.warmup):
+        sweep(s, False)
+    torch.cuda.synchronize()
+    if sm.status() != 0:
+        raise RuntimeError(f"device status {sm.status()} after warm-up")
+    clocks = ClockSampler(torch.cuda.current_device())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    dsmc.dsmc_profile_enable(True)
+    e0.record(stream)
+    for s in range(sweeps):
+        sweep(args.warmup + s, True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rs_ms, rs_n, rs_pairs, launches = dsmc.dsmc_profile_read()
+    dsmc.dsmc_profile_enable(False)
+    clk = clocks.stop()
+    if sm.status() != 0:
+        raise RuntimeError(f"device status {sm.status()} after the sweeps")
+    t = e0.elapsed_time(e1) / 1e3
+    rate = changed.cpu().numpy() / sweeps
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    ex2_peak = MUFU_EX2_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9
+    achieved = rs_pairs / (rs_ms / 1e3) / 1e9 if rs_ms > 0 else None
+    line = {"metric": METRIC, "value": sweeps * N * K / t, "unit": UNIT, "n_gpus": 1, "steps": sweeps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / sweeps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32+f32", "bf16": "bf16+f32"}[args.compute],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "K": K, "N": N, "dx": 1, "model": "stochastic volatility",
+                       "sweeps": sweeps, "resampler": "dense",
+                       "form": "conditional dSMC sweeps at fixed parameters (particle Gibbs)"},
+            "sweeps_per_s": sweeps / t,
+            "update_rate": {"mean": float(rate.mean()), "min": float(rate.min()),
+                            "p10": float(np.percentile(rate, 10)), "p50": float(np.percentile(rate, 50)),
+                            "first_t": float(rate[0]), "last_t": float(rate[-1])},
+            "roofline": {"bound": "alu", "kernel": "rowsum kernels (fused exp / tile sums)", "achieved": achieved,
+                         "peak": ex2_peak, "unit": "Gexp/s", "frac": achieved / ex2_peak if achieved else None,
+                         "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
+                                        f"({src} max clock)", "launches": rs_n, "traffic": None},
+            "clocks": clk, "gpu_launches": launches}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -589,10 +667,10 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     kind = WORKLOADS[args.workload].get("kind", "single")
-    if args.steps is None:
+    if args.steps is None and kind != "pg":
         args.steps = {"batch": 10, "serving": 1}.get(kind, 400)
     if args.compute is None:
-        args.compute = "bf16" if kind == "batch" else "tf32"
+        args.compute = {"batch": "bf16", "pg": "fp32"}.get(kind, "tf32")
     if args.impl == "reference":
         run_reference(args)
     else:
@@ -602,6 +680,8 @@ def main():
             run_batched(args)
         elif kind == "serving":
             run_serving(args)
+        elif kind == "pg":
+            run_pg(args)
         else:
             run_ours(args)
 

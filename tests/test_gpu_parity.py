@@ -559,3 +559,34 @@ def test_tensor_core_bench_configuration(compute):
         g.append(sm.smooth(yd).cpu().numpy().copy())
     assert sm.status() == 0
     _check(np.array(g), ms)
+
+
+def test_particle_gibbs_chain_on_rts():
+    """Conditional dSMC sweeps at fixed parameters (Section 3.2): the chain of references
+    x* <- c-dSMC(x*) leaves the smoother invariant, so its time averages agree with the
+    Kalman/RTS means within batch-means Monte Carlo error; every sweep keeps slot 0."""
+    m = W.lgssm_1d()
+    K, N, S, burn = 32, 64, 800, 100
+    _, y = W.simulate(m, K, 19)
+    ms, _, _ = kalman.rts_for(m, y)
+    sm = dsmc.Smoother(m, K, N, seed=77)
+    yd = dev(y)
+    xa = torch.zeros((K, 1), dtype=torch.float32, device="cuda")
+    xb = torch.empty_like(xa)
+    chain = []
+    for s in range(S):
+        sm.set_seed(77, counter_base=s)
+        sm.conditional(yd, xa, xb)
+        if s == 0:
+            torch.cuda.synchronize()
+            assert (sm.pairs[:, :, 0] == 0).all()
+        xa, xb = xb, xa
+        if s >= burn:
+            chain.append(xa[:, 0].clone())
+    assert sm.status() == 0
+    chain = torch.stack(chain).cpu().numpy()
+    nb = 25
+    bm = chain[: (len(chain) // nb) * nb].reshape(nb, -1, K).mean(1)
+    se = bm.std(0, ddof=1) / np.sqrt(nb)
+    z = np.abs(bm.mean(0) - ms[:, 0]) / se
+    assert z.max() < 4.5, z.max()
