@@ -355,7 +355,11 @@ def run_batched(args):
     units = N * sum(Ks)
     compute = {"fp32": dsmc.FP32, "tf32": dsmc.TF32, "bf16": dsmc.BF16}[args.compute]
     seeds = [1000 + 7919 * rank + i for i in range(len(Ks))]
-    b = dsmc.BatchSmoother(model, Ks, N, seeds=seeds, compute=compute, max_merges_per_launch=8192)
+    from paper_2202_02264_gb300 import autotune
+    tuned = autotune.tune_batch(model, Ks, N, bw.ys, compute, use_cache=False)   # untimed
+    b = dsmc.BatchSmoother(model, Ks, N, seeds=seeds, compute=compute,
+                           fused_max_merges=tuned["fused_max_merges"],
+                           max_merges_per_launch=tuned["max_merges_per_launch"])
     ys = [torch.as_tensor(y, dtype=torch.float32, device=dev) for y in bw.ys]
     b.set_inputs(ys)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -476,7 +480,10 @@ def run_batched(args):
                        "compute": f"{args.compute} cross term (fp32 accumulate / exp), batched: one launch "
                                   "per level for all sequences",
                        "l2": "flushed between timed steps (512 MiB write)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "autotuned": {"fused_max_merges": tuned["fused_max_merges"],
+                                     "max_merges_per_launch": tuned["max_merges_per_launch"],
+                                     "candidates_ms": tuned["timings"]}},
             "plain_fp32_per_request": {"value": plain_value, "unit": UNIT,
                                        "ms_per_batch": 1e3 * t_plain,
                                        "form": "FP32, each sequence smoothed alone (dsmc_smooth), in order"},
