@@ -350,13 +350,16 @@ def run_batched(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     spec = WORKLOADS[args.workload]
-    bw = W.batch_workload(spec["n_seq"], spec["N"])
+    bw = W.batch_workload(args.n_seq or spec["n_seq"], spec["N"])
     model, N, Ks, d = bw.model, bw.N, [int(k) for k in bw.Ks], bw.model.d
     units = N * sum(Ks)
     compute = {"fp32": dsmc.FP32, "tf32": dsmc.TF32, "bf16": dsmc.BF16}[args.compute]
     seeds = [1000 + 7919 * rank + i for i in range(len(Ks))]
     from paper_2202_02264_gb300 import autotune
-    tuned = autotune.tune_batch(model, Ks, N, bw.ys, compute, use_cache=False)   # untimed
+    if args.no_autotune:
+        tuned = {"fused_max_merges": 0, "max_merges_per_launch": 0, "timings": {}}
+    else:
+        tuned = autotune.tune_batch(model, Ks, N, bw.ys, compute, use_cache=False)   # untimed
     b = dsmc.BatchSmoother(model, Ks, N, seeds=seeds, compute=compute,
                            fused_max_merges=tuned["fused_max_merges"],
                            max_merges_per_launch=tuned["max_merges_per_launch"])
@@ -670,6 +673,8 @@ def main():
     ap.add_argument("--compute", default=None, choices=["fp32", "tf32", "bf16"],
                     help="cross-term precision (default: bf16 for the batched workload, tf32 otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="batched workload: default launch schedule")
+    ap.add_argument("--n-seq", type=int, default=None, help="batched workload: fewer sequences (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

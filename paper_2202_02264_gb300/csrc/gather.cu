@@ -78,11 +78,13 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(GatherArgs a) {
     }
   }
   if (corrupt) record_status(a.status, DSMC_ERR_INVALID_ARG);
-  __shared__ double red1[NW][D], red2[NW][D];
+  // moments: FP32 within each warp (butterfly), FP64 across the warps by d threads only
+  // (FP64 is slow on this part)
+  __shared__ float red1[NW][D], red2[NW][D];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    double v1 = s1[k], v2 = s2[k];
+    float v1 = s1[k], v2 = s2[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       v1 += __shfl_xor_sync(0xffffffffu, v1, o);
@@ -97,8 +99,8 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(GatherArgs a) {
   if (threadIdx.x < d) {
     double v1 = 0.0, v2 = 0.0;
     for (int w = 0; w < NW; ++w) {
-      v1 += red1[w][threadIdx.x];
-      v2 += red2[w][threadIdx.x];
+      v1 += (double)red1[w][threadIdx.x];
+      v2 += (double)red2[w][threadIdx.x];
     }
     const double scale = weighted ? 1.0 : 1.0 / (double)N;
     a.mean[(size_t)t * d + threadIdx.x] = v1 * scale;

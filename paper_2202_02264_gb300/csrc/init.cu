@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
   }
 
   __shared__ float red[kInitThreads / 32];
-  __shared__ double redd[kInitThreads / 32];
+  __shared__ float reds[kInitThreads / 32];
+  __shared__ float lse_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // block max
 #pragma unroll
@@ -96,20 +97,25 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
   float M = red[0];
 #pragma unroll
   for (int w = 1; w < kInitThreads / 32; ++w) M = fmaxf(M, red[w]);
-  // block sum of exp(l - M)
-  double s = 0.0;
-  for (int n = threadIdx.x; n < N; n += kInitThreads) s += (double)expf(lw[n] - M);
+  // block sum of exp(l - M): FP32 within each warp (a few terms per thread, then a
+  // butterfly), FP64 across the warps and for the log, by one thread (FP64 is slow here)
+  float s = 0.f;
+  for (int n = threadIdx.x; n < N; n += kInitThreads) s += expf(lw[n] - M);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) redd[warp] = s;
+  if (lane == 0) reds[warp] = s;
   __syncthreads();
-  double S = 0.0;
+  if (threadIdx.x == 0) {
+    double S = 0.0;
 #pragma unroll
-  for (int w = 0; w < kInitThreads / 32; ++w) S += redd[w];
-  const double lse = (double)M + log(S);
-  const float lsef = (float)lse;
+    for (int w = 0; w < kInitThreads / 32; ++w) S += (double)reds[w];
+    const double lse = (double)M + log(S);
+    lse_s = (float)lse;
+    a.logL[t] = lse - log((double)N);
+  }
+  __syncthreads();
+  const float lsef = lse_s;
   for (int n = threadIdx.x; n < N; n += kInitThreads) lw[n] = lw[n] - lsef;
-  if (threadIdx.x == 0) a.logL[t] = lse - log((double)N);
   if (bad || !(M > -INFINITY)) record_status(a.status, bad ? DSMC_ERR_NONFINITE : DSMC_ERR_DEGENERATE);
 }
 
