@@ -428,8 +428,10 @@ dsmc_status_t do_init(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& m
   DSMC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), s), "reset status");
   DSMC_CUDA(cudaMemsetAsync(w.star, 0, 2 * sizeof(int32_t), s), "reset star");
   InitArgs a;
+  std::memset(&a, 0, sizeof(a));
   a.K = p.K;
   a.N = p.N;
+  a.logN = (float)std::log((double)p.N);
   a.d = p.d;
   a.seed = cfg->seed;
   a.base = cfg->counter_base;
@@ -553,8 +555,9 @@ dsmc_status_t do_level(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& 
                       fused_eligible(p, cfg, M));
 }
 
-dsmc_status_t do_resolve(const Plan& p, const dsmc_state_t* st, float* traj, double* mean,
-                         double* m2, float* x_star, const WsPtrs& w, cudaStream_t s) {
+// The gather of one sequence from its composed maps S (w.first, [K][N+1]).
+dsmc_status_t do_gather(const Plan& p, const dsmc_state_t* st, float* traj, double* mean, double* m2,
+                        float* x_star, const WsPtrs& w, cudaStream_t s) {
   GatherArgs g;
   std::memset(&g, 0, sizeof(g));
   g.K = p.K;
@@ -562,6 +565,7 @@ dsmc_status_t do_resolve(const Plan& p, const dsmc_state_t* st, float* traj, dou
   g.d = p.d;
   g.L = p.L;
   for (int l = 0; l <= p.L; ++l) g.level_off[l] = p.level_off[l];
+  g.S = w.first;
   g.X = st->X;
   g.logw = st->logw;
   g.pairs = st->pairs;
@@ -574,6 +578,25 @@ dsmc_status_t do_resolve(const Plan& p, const dsmc_state_t* st, float* traj, dou
   DSMC_CUDA(launch_gather(p.D, g, s), "gather kernel");
   prof_count(1);
   return DSMC_OK;
+}
+
+// Resolution of one sequence: the top-down composition of its pairs (one launch per level,
+// root first), then the gather.  w.first must hold [K][N+1] int32 (the map buffers do).
+dsmc_status_t do_resolve(const Plan& p, const dsmc_state_t* st, float* traj, double* mean,
+                         double* m2, float* x_star, const WsPtrs& w, cudaStream_t s) {
+  dsmc_config_t c;
+  std::memset(&c, 0, sizeof(c));
+  c.K = p.K;
+  c.N = p.N;
+  for (int l = p.L - 1; l >= 0; --l) {
+    MergeArgs a = merge_args(p, &c, nullptr, l, 0, const_cast<dsmc_state_t*>(st), w);
+    a.m0 = 0;
+    a.mc = merges_at_level(p.K, l);
+    a.gid0 = p.level_off[l];
+    DSMC_CUDA(launch_resolve_level(a, s), "resolve kernel");
+    prof_count(1);
+  }
+  return do_gather(p, st, traj, mean, m2, x_star, w, s);
 }
 
 struct Prepared {
@@ -678,7 +701,8 @@ struct BatchLayout {
   std::vector<int> level_fused;  // [Lmax] end of the level's fused items (they come first)
   std::vector<size_t> map_off;   // per sequence: byte offset of its first / last maps
   size_t n_items = 0;
-  size_t o_desc = 0, o_items = 0, o_maps = 0, o_star = 0, total = 0;
+  size_t o_desc = 0, o_kstart = 0, o_items = 0, o_maps = 0, o_star = 0, total = 0;
+  long long sumK = 0;
 };
 
 dsmc_status_t batch_layout(const dsmc_config_t* cfg, const dsmc_model_t* model, int n_seq, const int* K,
@@ -712,6 +736,9 @@ dsmc_status_t batch_layout(const dsmc_config_t* cfg, const dsmc_model_t* model, 
     bl.level_fused[l] = bl.level_start[l] + (int)cf;
   }
   bl.n_items = (size_t)items;
+  bl.sumK = 0;
+  for (int i = 0; i < n_seq; ++i) bl.sumK += K[i];
+  if (bl.sumK > (1LL << 31) - 1) return fail(DSMC_ERR_INVALID_ARG, "too many time steps in one batch");
   size_t o = bl.p.total;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -719,6 +746,7 @@ dsmc_status_t batch_layout(const dsmc_config_t* cfg, const dsmc_model_t* model, 
     return at;
   };
   bl.o_desc = take((size_t)n_seq * sizeof(SeqDesc));
+  bl.o_kstart = take((size_t)(n_seq + 1) * sizeof(int));
   bl.o_items = take(bl.n_items * sizeof(CombItem));
   bl.o_star = take((size_t)n_seq * 2 * sizeof(int32_t));
   bl.map_off.resize(n_seq);
@@ -730,7 +758,8 @@ dsmc_status_t batch_layout(const dsmc_config_t* cfg, const dsmc_model_t* model, 
 
 // Host copies of the descriptors and the level-major item list of a batch.
 dsmc_status_t batch_tables(const dsmc_config_t* cfg, const BatchLayout& bl, const dsmc_seq_t* seqs,
-                           char* ws, std::vector<SeqDesc>& desc, std::vector<CombItem>& items) {
+                           char* ws, std::vector<SeqDesc>& desc, std::vector<CombItem>& items,
+                           std::vector<int>& kstart) {
   const int N = cfg->N;
   desc.resize(bl.n_seq);
   for (int i = 0; i < bl.n_seq; ++i) {
@@ -757,7 +786,14 @@ dsmc_status_t batch_tables(const dsmc_config_t* cfg, const BatchLayout& bl, cons
     d.seed = q.seed;
     d.base = q.counter_base;
     d.conditional = q.x_ref_in != nullptr ? 1 : 0;
+    d.x_ref = q.x_ref_in;
+    d.mean = q.mean_out;
+    d.m2 = q.m2_out;
+    d.x_star = q.x_ref_out;
+    d.logL_out = q.logL_out;
   }
+  kstart.assign(bl.n_seq + 1, 0);
+  for (int i = 0; i < bl.n_seq; ++i) kstart[i + 1] = kstart[i] + seqs[i].K;
   items.resize(bl.n_items);
   std::vector<int> off(bl.n_seq, 0);  // per sequence: combinations of the levels so far
   for (int l = 0; l < bl.Lmax; ++l) {
@@ -836,10 +872,13 @@ dsmc_status_t batch_upload(const dsmc_config_t* cfg, const BatchRun& br, const d
                            cudaStream_t s) {
   std::vector<SeqDesc> desc;
   std::vector<CombItem> items;
+  std::vector<int> kstart;
   char* b = static_cast<char*>(ws);
-  DSMC_TRY(batch_tables(cfg, br.bl, seqs, b, desc, items));
+  DSMC_TRY(batch_tables(cfg, br.bl, seqs, b, desc, items, kstart));
   DSMC_CUDA(cudaMemcpyAsync(b + br.bl.o_desc, desc.data(), desc.size() * sizeof(SeqDesc),
                             cudaMemcpyHostToDevice, s), "descriptor upload");
+  DSMC_CUDA(cudaMemcpyAsync(b + br.bl.o_kstart, kstart.data(), kstart.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, s), "time-step table upload");
   if (!items.empty())
     DSMC_CUDA(cudaMemcpyAsync(b + br.bl.o_items, items.data(), items.size() * sizeof(CombItem),
                               cudaMemcpyHostToDevice, s), "item upload");
@@ -859,28 +898,24 @@ dsmc_status_t batch_launch(const dsmc_config_t* cfg, const dsmc_model_t* model, 
   for (int i = 0; i < bl.n_seq; ++i)
     if (seqs[i].maps)
       DSMC_CUDA(cudaMemsetAsync(seq_star(seqs[i], p.N, nullptr, i), 0, 2 * sizeof(int32_t), s), "reset star");
-  // Algorithm 2 per sequence
-  for (int i = 0; i < bl.n_seq; ++i) {
-    const dsmc_seq_t& q = seqs[i];
-    ParamBuf mp = br.mp;
-    set_prop(p.D, mp, q.prop_mean, q.prop_std);
+  // Algorithm 2: one launch over every time step of every sequence
+  const SeqDesc* descs = reinterpret_cast<const SeqDesc*>(b + bl.o_desc);
+  const int* kstart = reinterpret_cast<const int*>(b + bl.o_kstart);
+  {
     InitArgs ia;
-    ia.K = q.K;
+    std::memset(&ia, 0, sizeof(ia));
+    ia.K = (int)bl.sumK;
     ia.N = p.N;
     ia.d = p.d;
-    ia.seed = q.seed;
-    ia.base = q.counter_base;
-    ia.y = q.y;
-    ia.x_ref = q.x_ref_in;
-    ia.X = q.state.X;
-    ia.logw = q.state.logw;
-    ia.logL = q.state.logL;
+    ia.logN = (float)std::log((double)p.N);
+    ia.seqs = descs;
+    ia.kstart = kstart;
+    ia.n_seq = bl.n_seq;
     ia.status = br.w.status;
-    DSMC_CUDA(launch_init(p.D, ia, mp.bytes, s), "init kernel");
+    DSMC_CUDA(launch_init(p.D, ia, br.mp.bytes, s), "init kernel");
     prof_count(1);
   }
   // the levels of Algorithm 6, every sequence's combinations of a level together
-  const SeqDesc* descs = reinterpret_cast<const SeqDesc*>(b + bl.o_desc);
   const CombItem* items = reinterpret_cast<const CombItem*>(b + bl.o_items);
   dsmc_state_t none = {nullptr, nullptr, nullptr, nullptr};
   for (int l = 0; l < bl.Lmax; ++l) {
@@ -893,26 +928,44 @@ dsmc_status_t batch_launch(const dsmc_config_t* cfg, const dsmc_model_t* model, 
       DSMC_TRY(launch_combs(p, cfg, br.mp, nullptr, l, 0, &none, br.w, s, Ms, items + bl.level_fused[l], descs,
                             false));
   }
-  // resolution per sequence
+  // resolution: the top-down composition, every sequence's combinations of a level together
+  // (root levels first)
+  for (int l = bl.Lmax - 1; l >= 0; --l) {
+    const int M = bl.level_start[l + 1] - bl.level_start[l];
+    if (M == 0) continue;
+    MergeArgs a = merge_args(p, cfg, nullptr, l, 0, &none, br.w);
+    a.items = items + bl.level_start[l];
+    a.seqs = descs;
+    a.m0 = 0;
+    a.mc = M;
+    DSMC_CUDA(launch_resolve_level(a, s), "resolve kernel");
+    prof_count(1);
+  }
+  // the root draw of conditional sequences of length 1 (from the weighted leaf)
   for (int i = 0; i < bl.n_seq; ++i) {
     const dsmc_seq_t& q = seqs[i];
-    dsmc_config_t c = *cfg;
-    c.K = q.K;
-    Plan pi;
-    make_plan(&c, model, pi, 1, true);
-    WsPtrs wi = br.w;
-    wi.star = seq_star(q, p.N, b + bl.o_star, i);
-    const bool cond = q.x_ref_in != nullptr;
-    if (cond && q.K == 1) {
-      DSMC_CUDA(launch_k1_star(q.state.logw, p.N, q.seed, q.counter_base, wi.star, s), "star kernel");
+    if (q.x_ref_in != nullptr && q.K == 1) {
+      DSMC_CUDA(launch_k1_star(q.state.logw, p.N, q.seed, q.counter_base, seq_star(q, p.N, b + bl.o_star, i), s),
+                "star kernel");
       prof_count(1);
     }
-    dsmc_state_t st = q.state;
-    DSMC_TRY(do_resolve(pi, &st, nullptr, q.mean_out, q.m2_out, cond ? q.x_ref_out : nullptr, wi, s));
-    if (q.logL_out)
-      DSMC_CUDA(cudaMemcpyAsync(q.logL_out, q.state.logL, sizeof(double), cudaMemcpyDeviceToDevice, s),
-                "logL copy");
   }
+  // the gather: one launch over every time step of every sequence (means, second moments,
+  // next references, log L of the root)
+  {
+    GatherArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.K = (int)bl.sumK;
+    g.N = p.N;
+    g.d = p.d;
+    g.seqs = descs;
+    g.kstart = kstart;
+    g.n_seq = bl.n_seq;
+    g.status = br.w.status;
+    DSMC_CUDA(launch_gather(p.D, g, s), "gather kernel");
+    prof_count(1);
+  }
+  (void)model;
   return DSMC_OK;
 }
 
@@ -978,6 +1031,11 @@ dsmc_status_t serve_tick(const dsmc_config_t* cfg, const dsmc_model_t* model, co
     d.seed = q.seed;
     d.base = q.counter_base;
     d.conditional = q.x_ref_in != nullptr ? 1 : 0;
+    d.x_ref = q.x_ref_in;
+    d.mean = q.mean_out;
+    d.m2 = q.m2_out;
+    d.x_star = q.x_ref_out;
+    d.logL_out = q.logL_out;
     const int l = stage[i];
     if (l >= 0 && l < d.L) {
       const int M = merges_at_level(q.K, l);
@@ -1007,8 +1065,10 @@ dsmc_status_t serve_tick(const dsmc_config_t* cfg, const dsmc_model_t* model, co
     ParamBuf mpi = mp;
     set_prop(p.D, mpi, q.prop_mean, q.prop_std);
     InitArgs ia;
+    std::memset(&ia, 0, sizeof(ia));
     ia.K = q.K;
     ia.N = N;
+    ia.logN = (float)std::log((double)N);
     ia.d = p.d;
     ia.seed = q.seed;
     ia.base = q.counter_base;
@@ -1040,6 +1100,7 @@ dsmc_status_t serve_tick(const dsmc_config_t* cfg, const dsmc_model_t* model, co
     make_plan(&c, model, pi, 1, true);
     WsPtrs wi = w;
     wi.star = desc[i].star;
+    wi.first = desc[i].first;
     const bool cond = q.x_ref_in != nullptr;
     if (cond && q.K == 1) {
       DSMC_CUDA(launch_k1_star(q.state.logw, N, q.seed, q.counter_base, wi.star, s), "star kernel");

@@ -16,12 +16,32 @@ constexpr int kInitThreads = 256;
 
 template <int D>
 __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelParams<D> mp) {
-  const int t = blockIdx.x;
+  int t = blockIdx.x;
   const int N = a.N, d = a.d;
+  // this block's sequence: the call's own, or one of a batch
+  uint64_t seed = a.seed;
+  uint32_t base = a.base;
+  const float *y = a.y, *x_ref = a.x_ref, *pmean = mp.prop_mean, *pstd = mp.prop_std;
+  float *X = a.X, *logw = a.logw;
+  double* logL = a.logL;
+  if (a.seqs != nullptr) {
+    int seq;
+    batch_time(a.kstart, a.n_seq, blockIdx.x, seq, t);
+    const SeqDesc& q = a.seqs[seq];
+    seed = q.seed;
+    base = q.base;
+    y = q.y;
+    x_ref = q.x_ref;
+    pmean = q.prop_mean;
+    pstd = q.prop_std;
+    X = q.X;
+    logw = q.logw;
+    logL = q.logL;
+  }
   float yt[D], qm[D], qs[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) yt[k] = k < d ? a.y[(size_t)t * d + k] : 0.f;
-  proposal_at<D>(mp, a.y, mp.prop_mean, mp.prop_std, t, qm, qs);
+  for (int k = 0; k < D; ++k) yt[k] = k < d ? y[(size_t)t * d + k] : 0.f;
+  proposal_at<D>(mp, y, pmean, pstd, t, qm, qs);
   float qinv[D];
   const float qnorm = proposal_consts<D>(d, qs, qinv);
   float logsd = 0.f;
@@ -29,22 +49,23 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
   for (int k = 0; k < D; ++k)
     if (k < d) logsd += logf(qs[k]);
 
-  float* lw = a.logw + (size_t)t * N;
+  float* lw = logw + (size_t)t * N;
   float lmax = -INFINITY;
   bool bad = false;
+  const bool uniform = (t > 0 && mp.nu == DSMC_NU_EQ_Q);
   for (int n = threadIdx.x; n < N; n += kInitThreads) {
     float x[D], z[D];
-    if (a.x_ref != nullptr && n == 0) {
+    if (x_ref != nullptr && n == 0) {
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        x[k] = k < d ? a.x_ref[(size_t)t * d + k] : 0.f;
+        x[k] = k < d ? x_ref[(size_t)t * d + k] : 0.f;
         z[k] = k < d ? (x[k] - qm[k]) / qs[k] : 0.f;
       }
     } else {
 #pragma unroll
       for (int j = 0; j < (D + 3) / 4; ++j) {
         if (4 * j < d) {
-          const uint4 w = draw(a.seed, (uint32_t)n, (uint32_t)t, kPurposeInit, a.base, (uint32_t)j);
+          const uint4 w = draw(seed, (uint32_t)n, (uint32_t)t, kPurposeInit, base, (uint32_t)j);
           const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
           for (int p = 0; p < 2; ++p) {
@@ -63,7 +84,7 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
         x[k] = k < d ? fmaf(qs[k], z[k], qm[k]) : 0.f;
       }
     }
-    float* xo = a.X + ((size_t)t * N + n) * d;
+    float* xo = X + ((size_t)t * N + n) * d;
 #pragma unroll
     for (int k = 0; k < D; ++k)
       if (k < d) xo[k] = x[k];
@@ -81,8 +102,14 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
       l = log_nu<D>(mp, yt, qm, qinv, qnorm, x) - lq;
     }
     if (isnan(l)) bad = true;
-    lw[n] = l;
+    lw[n] = uniform ? -a.logN : l;
     lmax = fmaxf(lmax, l);
+  }
+  // nu_t = q_t at t >= 1: every log-weight is exactly 0, so the normalised weights are
+  // exactly -log N and log L_t = 0 (what the general path below computes, without it)
+  if (uniform) {
+    if (threadIdx.x == 0) logL[t] = 0.0;
+    return;
   }
 
   __shared__ float red[kInitThreads / 32];
@@ -111,7 +138,7 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
     for (int w = 0; w < kInitThreads / 32; ++w) S += (double)reds[w];
     const double lse = (double)M + log(S);
     lse_s = (float)lse;
-    a.logL[t] = lse - log((double)N);
+    logL[t] = lse - log((double)N);
   }
   __syncthreads();
   const float lsef = lse_s;

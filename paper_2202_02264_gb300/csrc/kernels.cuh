@@ -38,8 +38,8 @@ struct WsPtrs {
 // One sequence of a batched launch (device memory; built by the host per batch).
 struct SeqDesc {
   int K, L;                  // steps, levels
-  const float* X;            // [K][N][d]
-  const float* logw;         // [K][N]
+  float* X;                  // [K][N][d]
+  float* logw;               // [K][N]
   const float* y;            // [K][d]
   double* logL;              // [K]
   int32_t* pairs;            // [K-1][2][N]
@@ -51,7 +51,29 @@ struct SeqDesc {
   uint64_t seed;
   uint32_t base;
   int conditional;
+  const float* x_ref;        // [K][d] reference of a conditional sweep, or null
+  double* mean;              // [K][d] outputs of the resolve
+  double* m2;                // [K][d] or null
+  float* x_star;             // [K][d] next reference (conditional), or null
+  double* logL_out;          // one double, or null
 };
+
+// Block b of a launch over every time step of a batch: sequence s with
+// kstart[s] <= b < kstart[s + 1], time t = b - kstart[s] (thread 0 searches, all read).
+__device__ __forceinline__ void batch_time(const int* kstart, int n_seq, int b, int& seq, int& t) {
+  __shared__ int s_seq;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n_seq - 1;  // last s with kstart[s] <= b
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (kstart[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    s_seq = lo;
+  }
+  __syncthreads();
+  seq = s_seq;
+  t = b - kstart[seq];
+}
 
 // One combination of a batched launch: sequence, combination index within its level, its
 // row in the sequence's pairs array, and the level (one launch may mix levels).
@@ -166,6 +188,10 @@ __device__ __forceinline__ Comb comb_of(const MergeArgs& a, int s) {
 
 struct InitArgs {
   int K, N, d;
+  float logN;        // (float) log N, from FP64
+  const SeqDesc* seqs;   // batched launch over every (sequence, t): the sequences, else null
+  const int* kstart;     // [n_seq + 1] first block of each sequence
+  int n_seq;
   uint64_t seed;
   uint32_t base;
   const float* y;
@@ -178,6 +204,10 @@ struct InitArgs {
 
 struct GatherArgs {
   int K, N, d, L;
+  const SeqDesc* seqs;   // batched launch over every (sequence, t), else null
+  const int* kstart;     // [n_seq + 1]
+  int n_seq;
+  const int32_t* S;  // [K][N+1] leaf index of every output trajectory (and the root draw) per t
   int level_off[33];
   const float* X;
   const float* logw;
@@ -199,6 +229,7 @@ cudaError_t launch_sample_dense(int D, const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_sample_rs(int D, const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_epilogue(const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_gather(int D, const GatherArgs& a, cudaStream_t s);
+cudaError_t launch_resolve_level(const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_debug_weights(int D, const MergeArgs& a, int s_local, float* logW, float* r,
                                  float* rowsum, float* tiles, float* e, float* ratio,
                                  cudaStream_t s);

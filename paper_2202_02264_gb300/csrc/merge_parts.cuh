@@ -124,8 +124,8 @@ __device__ __forceinline__ float row_terms(const ModelParams<D>& mp, const Merge
   return -0.5f * kLog2e * q;
 }
 
-// Row i's base-2 shift delta_i: the largest exponent over a fixed sample of 32 columns
-// (j = k N / 32), floored at -96.  The row's pairs are evaluated relative to
+// Row i's base-2 shift delta_i: the largest exponent over a fixed sample of 8 columns
+// (j = k N / 8), floored at -96.  The row's pairs are evaluated relative to
 // shift_i + delta_i ln 2 (alpha_i - delta_i in base 2): the sampled best column then weighs
 // about 1, so the row total cannot underflow, while every pair stays below 2^96 (the
 // exponents relative to the bound are <= 0), so no tile sum overflows.  In high dimension
@@ -133,9 +133,9 @@ __device__ __forceinline__ float row_terms(const ModelParams<D>& mp, const Merge
 // below FP32's range.
 template <int D, bool PAD>
 __device__ __forceinline__ float row_shift(const float* u, float al, const float* V, const float* beta, int N) {
-  constexpr int S = 32;
+  constexpr int S = 8;
   float mx = -INFINITY;
-#pragma unroll 4
+#pragma unroll
   for (int k = 0; k < S; ++k) {
     const int j = N >= S ? (int)(((long long)k * N) / S) : (k < N ? k : N - 1);
     mx = fmaxf(mx, pair_exponent<D>(u, al, V + vidx<D, PAD>(j), beta[bidx<PAD>(j)]));
