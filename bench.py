@@ -283,6 +283,14 @@ def run_ours(args):
     e2e = {"value": world * N * K / e2e_t, "unit": UNIT,
            "h2d_bytes_per_step": y_host.numel() * 4,
            "d2h_bytes_per_step": mean_host.numel() * 8 + 8}
+    # per-kernel-kind breakdown of a few more steps (CUDA events around every launch; untimed)
+    dsmc.dsmc_profile_breakdown_enable(True)
+    for i in range(4):
+        step(20_000 + i)
+    torch.cuda.synchronize()
+    breakdown = {k: {"ms": v["ms"] / 4, "launches": v["launches"] // 4}
+                 for k, v in dsmc.dsmc_profile_breakdown_read().items()}
+    dsmc.dsmc_profile_breakdown_enable(False)
 
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -315,6 +323,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches,
+            "breakdown_ms_per_step": breakdown,
             "step_ms": {"median": float(np.median(per_step)), "p99": float(np.percentile(per_step, 99))}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(wl)
@@ -432,6 +441,14 @@ def run_batched(args):
            "h2d_bytes_per_step": sum(y.numel() * 4 for y in y_host),
            "d2h_bytes_per_step": sum(m.numel() * 8 for m in m_host) + l_host.numel() * 8}
 
+    # per-kernel-kind breakdown of one more step (CUDA events around every launch; untimed)
+    prep(20_000)
+    dsmc.dsmc_profile_breakdown_enable(True)
+    b.run()
+    torch.cuda.synchronize()
+    breakdown = dsmc.dsmc_profile_breakdown_read()
+    dsmc.dsmc_profile_breakdown_enable(False)
+
     # the plain form: FP32, each sequence smoothed alone, one call after another
     Kmax = max(Ks)
     single = dsmc.Smoother(model, Kmax, N, seed=seeds[0], compute=dsmc.FP32)
@@ -491,6 +508,7 @@ def run_batched(args):
                                        "ms_per_batch": 1e3 * t_plain,
                                        "form": "FP32, each sequence smoothed alone (dsmc_smooth), in order"},
             "mixed_over_plain": value / world / plain_value,
+            "breakdown_ms_per_step": breakdown,
             "accuracy": accuracy,
             "roofline": roofline, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
             "step_ms": {"median": float(np.median(per_step)), "p99": float(np.percentile(per_step, 99))}}

@@ -297,6 +297,22 @@ dsmc_status_t dsmc_profile_enable(int enable);
 dsmc_status_t dsmc_profile_read(double* rowsum_ms, int64_t* rowsum_launches, double* rowsum_pairs,
                                 int64_t* all_launches);
 
+/* Per-kernel-kind breakdown: when enabled, CUDA events on the launching stream around every
+ * launch (of this host thread) of each kind; read returns the summed milliseconds and launch
+ * counts per kind, index DSMC_KIND_*, and synchronises those events.  Enabling resets. */
+enum {
+  DSMC_KIND_INIT = 0,       /* Algorithm 2 */
+  DSMC_KIND_PROLOGUE = 1,   /* column / row terms of the split path */
+  DSMC_KIND_TILE_SUMS = 2,  /* the N x N exponentials and tile sums (CUDA or tensor cores) */
+  DSMC_KIND_DRAWS = 3,      /* row CDF, pair draws and index maps (dense or rejection) */
+  DSMC_KIND_FUSED = 4,      /* fused single-launch levels */
+  DSMC_KIND_RESOLVE = 5,    /* top-down composition of the pairs */
+  DSMC_KIND_GATHER = 6,     /* gather of the trajectories and moments */
+  DSMC_KINDS = 8
+};
+dsmc_status_t dsmc_profile_breakdown_enable(int enable);
+dsmc_status_t dsmc_profile_breakdown_read(double* ms /* [DSMC_KINDS] */, int64_t* launches /* [DSMC_KINDS] */);
+
 /* ---- Inspection entry points used by the parity tests (same arithmetic as the path). */
 
 /* Philox4x32-10 of n counters: ctr DEVICE [n][4] uint32, out DEVICE [n][4] uint32. */

@@ -58,6 +58,36 @@ void prof_count(int n) {
   if (g_prof.on) g_prof.launches += n;
 }
 
+// Per-kernel-kind breakdown: events around every launch of a kind (dsmc_profile_breakdown_*).
+struct Breakdown {
+  bool on = false;
+  std::vector<cudaEvent_t> a, b;
+  std::vector<int> kind;
+  size_t used = 0;
+};
+thread_local Breakdown g_bd;
+
+cudaError_t bd_begin(cudaStream_t s, int kind) {
+  if (!g_bd.on) return cudaSuccess;
+  if (g_bd.used == g_bd.a.size()) {
+    cudaEvent_t x, y;
+    cudaError_t e = cudaEventCreate(&x);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&y);
+    if (e != cudaSuccess) return e;
+    g_bd.a.push_back(x);
+    g_bd.b.push_back(y);
+    g_bd.kind.push_back(0);
+  }
+  g_bd.kind[g_bd.used] = kind;
+  return cudaEventRecord(g_bd.a[g_bd.used], s);
+}
+
+cudaError_t bd_end(cudaStream_t s) {
+  if (!g_bd.on) return cudaSuccess;
+  return cudaEventRecord(g_bd.b[g_bd.used++], s);
+}
+
 dsmc_status_t fail(dsmc_status_t st, const std::string& msg) {
   g_last_error = msg;
   return st;
@@ -441,7 +471,9 @@ dsmc_status_t do_init(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& m
   a.logw = st->logw;
   a.logL = st->logL;
   a.status = w.status;
+  DSMC_CUDA(bd_begin(s, DSMC_KIND_INIT), "profile event");
   DSMC_CUDA(launch_init(p.D, a, mp.bytes, s), "init kernel");
+  DSMC_CUDA(bd_end(s), "profile event");
   prof_count(1);
   return DSMC_OK;
 }
@@ -523,24 +555,34 @@ dsmc_status_t launch_combs(const Plan& p, const dsmc_config_t* cfg, const ParamB
     if (Cf > 0) {
       const int C = fused_schedulable(p, a, Cf);
       if (C > 0) {
+        DSMC_CUDA(bd_begin(s, DSMC_KIND_FUSED), "profile event");
         DSMC_CUDA(launch_level_fused(p.D, a, mp.bytes, C, s), "fused level kernel");
+        DSMC_CUDA(bd_end(s), "profile event");
         prof_count(1);
         continue;
       }
     }
+    DSMC_CUDA(bd_begin(s, DSMC_KIND_PROLOGUE), "profile event");
     DSMC_CUDA(launch_prologue(p.D, a, mp.bytes, s), "prologue kernel");
+    DSMC_CUDA(bd_end(s), "profile event");
     if (p.dense) {
       DSMC_CUDA(prof_begin(s), "profile event");
+      DSMC_CUDA(bd_begin(s, DSMC_KIND_TILE_SUMS), "profile event");
       if (p.compute == DSMC_FP32)
         DSMC_CUDA(launch_rowsum(p.D, a, s), "tile-sum kernel");
       else
         DSMC_CUDA(launch_rowsum_tc(a, s), "tensor-core tile-sum kernel");
+      DSMC_CUDA(bd_end(s), "profile event");
       DSMC_CUDA(prof_end(s, (double)a.mc * p.N * p.N), "profile event");
+      DSMC_CUDA(bd_begin(s, DSMC_KIND_DRAWS), "profile event");
       DSMC_CUDA(launch_sample_dense(p.D, a, s), "dense sampler kernel");
+      DSMC_CUDA(bd_end(s), "profile event");
       prof_count(3);
     } else {
+      DSMC_CUDA(bd_begin(s, DSMC_KIND_DRAWS), "profile event");
       DSMC_CUDA(launch_sample_rs(p.D, a, s), "rejection sampler kernel");
       DSMC_CUDA(launch_epilogue(a, s), "epilogue kernel");
+      DSMC_CUDA(bd_end(s), "profile event");
       prof_count(3);
     }
   }
@@ -575,7 +617,9 @@ dsmc_status_t do_gather(const Plan& p, const dsmc_state_t* st, float* traj, doub
   g.m2 = m2;
   g.x_star = x_star;
   g.status = w.status;
+  DSMC_CUDA(bd_begin(s, DSMC_KIND_GATHER), "profile event");
   DSMC_CUDA(launch_gather(p.D, g, s), "gather kernel");
+  DSMC_CUDA(bd_end(s), "profile event");
   prof_count(1);
   return DSMC_OK;
 }
@@ -593,7 +637,9 @@ dsmc_status_t do_resolve(const Plan& p, const dsmc_state_t* st, float* traj, dou
     a.m0 = 0;
     a.mc = merges_at_level(p.K, l);
     a.gid0 = p.level_off[l];
+    DSMC_CUDA(bd_begin(s, DSMC_KIND_RESOLVE), "profile event");
     DSMC_CUDA(launch_resolve_level(a, s), "resolve kernel");
+    DSMC_CUDA(bd_end(s), "profile event");
     prof_count(1);
   }
   return do_gather(p, st, traj, mean, m2, x_star, w, s);
@@ -912,7 +958,9 @@ dsmc_status_t batch_launch(const dsmc_config_t* cfg, const dsmc_model_t* model, 
     ia.kstart = kstart;
     ia.n_seq = bl.n_seq;
     ia.status = br.w.status;
+    DSMC_CUDA(bd_begin(s, DSMC_KIND_INIT), "profile event");
     DSMC_CUDA(launch_init(p.D, ia, br.mp.bytes, s), "init kernel");
+    DSMC_CUDA(bd_end(s), "profile event");
     prof_count(1);
   }
   // the levels of Algorithm 6, every sequence's combinations of a level together
@@ -938,7 +986,9 @@ dsmc_status_t batch_launch(const dsmc_config_t* cfg, const dsmc_model_t* model, 
     a.seqs = descs;
     a.m0 = 0;
     a.mc = M;
+    DSMC_CUDA(bd_begin(s, DSMC_KIND_RESOLVE), "profile event");
     DSMC_CUDA(launch_resolve_level(a, s), "resolve kernel");
+    DSMC_CUDA(bd_end(s), "profile event");
     prof_count(1);
   }
   // the root draw of conditional sequences of length 1 (from the weighted leaf)
@@ -962,7 +1012,9 @@ dsmc_status_t batch_launch(const dsmc_config_t* cfg, const dsmc_model_t* model, 
     g.kstart = kstart;
     g.n_seq = bl.n_seq;
     g.status = br.w.status;
-    DSMC_CUDA(launch_gather(p.D, g, s), "gather kernel");
+    DSMC_CUDA(bd_begin(s, DSMC_KIND_GATHER), "profile event");
+  DSMC_CUDA(launch_gather(p.D, g, s), "gather kernel");
+  DSMC_CUDA(bd_end(s), "profile event");
     prof_count(1);
   }
   (void)model;
@@ -1078,7 +1130,9 @@ dsmc_status_t serve_tick(const dsmc_config_t* cfg, const dsmc_model_t* model, co
     ia.logw = q.state.logw;
     ia.logL = q.state.logL;
     ia.status = w.status;
+    DSMC_CUDA(bd_begin(s, DSMC_KIND_INIT), "profile event");
     DSMC_CUDA(launch_init(p.D, ia, mpi.bytes, s), "init kernel");
+    DSMC_CUDA(bd_end(s), "profile event");
     prof_count(1);
   }
   // merge stages: every sequence's level, together
@@ -1272,6 +1326,29 @@ dsmc_status_t dsmc_profile_read(double* rowsum_ms, int64_t* rowsum_launches, dou
   if (rowsum_launches) *rowsum_launches = (int64_t)g_prof.used;
   if (rowsum_pairs) *rowsum_pairs = g_prof.pairs;
   if (all_launches) *all_launches = g_prof.launches;
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_profile_breakdown_enable(int enable) {
+  g_bd.on = enable != 0;
+  g_bd.used = 0;
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_profile_breakdown_read(double* ms, int64_t* launches) {
+  if (!ms || !launches) return fail(DSMC_ERR_INVALID_ARG, "null output");
+  for (int k = 0; k < DSMC_KINDS; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (size_t i = 0; i < g_bd.used; ++i) {
+    DSMC_CUDA(cudaEventSynchronize(g_bd.b[i]), "profile synchronize");
+    float t = 0.f;
+    DSMC_CUDA(cudaEventElapsedTime(&t, g_bd.a[i], g_bd.b[i]), "profile elapsed");
+    const int k = g_bd.kind[i];
+    ms[k] += t;
+    launches[k] += 1;
+  }
   return DSMC_OK;
 }
 

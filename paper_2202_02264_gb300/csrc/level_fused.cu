@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   double* sSh = reinterpret_cast<double*>(smraw + L.sh);
   int* under = reinterpret_cast<int*>(sC);  // own rows that underflowed (before the CDF)
 
-  __shared__ float red_v[NW][D];
+  __shared__ float gsum[kMaxColumnGroups * D];
   __shared__ float red_s[NW];
   __shared__ float mu_s[D];
   __shared__ float bstar_s;
@@ -106,8 +106,12 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   double* shift = a.ws.shift + (size_t)s * N;
   float* Tt = a.ws.T + (size_t)s * N * nTp;
   float* delta = a.ws.delta + (size_t)s * N;
-  const int32_t* firstR = cb.first + ((size_t)bufR * K + c) * N;
-  const int32_t* lastL = cb.last + ((size_t)bufL * K + at) * N;
+  const int32_t* firstR = right_leaf ? nullptr : cb.first + ((size_t)bufR * K + c) * N;
+  const int32_t* lastL = left_leaf ? nullptr : cb.last + ((size_t)bufL * K + at) * N;
+  const float* Xc = cb.X + (size_t)c * N * d;
+  const float* Xl = cb.X + (size_t)(c - 1) * N * d;
+  const float* lwc = right_leaf ? cb.logw + (size_t)c * N : nullptr;
+  const float* lwl = left_leaf ? cb.logw + (size_t)(c - 1) * N : nullptr;
 
   // ---------------------------------------------------------------- columns (all N)
   float yc[D], qm[D], qs[D];
@@ -116,46 +120,15 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   proposal_at<D>(mp, cb.y, cb.prop_mean, cb.prop_std, c, qm, qs);
   float qinv[D];
   const float qnorm = proposal_consts<D>(d, qs, qinv);
-  float sx[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) sx[k] = 0.f;
-  float bmax = -INFINITY;
   bool bad = false, corrupt = false;
-  for (int j = threadIdx.x; j < N; j += NT) {
-    float x[D];
-    const float bp = column_bprime<D>(mp, a, cb, yc, qm, qinv, qnorm, firstR, right_leaf, j, x, corrupt);
-    bad |= isnan(bp);
+  float mu[D], bstar;
+  column_pass<D>(N, gsum, red_s, mu_s, &bstar_s, mu, bstar, bad, [&](int j, float* x) {
+    const float bp = column_bprime<D>(mp, N, d, a.logN, yc, qm, qinv, qnorm, Xc, firstR, lwc, j, x, corrupt);
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      sV[vidx<D, true>(j) + k] = x[k];
-      sx[k] += x[k];
-    }
+    for (int k = 0; k < D; ++k) sV[vidx<D, true>(j) + k] = x[k];
     sB[bidx<true>(j)] = bp;
-    bmax = fmaxf(bmax, bp);
-  }
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const float v = warp_sum(sx[k]);
-    if (lane == 0) red_v[warp][k] = v;
-  }
-  bmax = warp_max(bmax);
-  if (lane == 0) red_s[warp] = bmax;
-  __syncthreads();
-  if (threadIdx.x < D) {
-    float t = 0.f;
-    for (int w = 0; w < NW; ++w) t += red_v[w][threadIdx.x];
-    mu_s[threadIdx.x] = t / (float)N;
-  }
-  if (threadIdx.x == 0) {
-    float t = red_s[0];
-    for (int w = 1; w < NW; ++w) t = fmaxf(t, red_s[w]);
-    bstar_s = t;
-  }
-  __syncthreads();
-  float mu[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) mu[k] = mu_s[k];
-  const float bstar = bstar_s;
+    return bp;
+  });
   for (int j = threadIdx.x; j < N; j += NT) {
     float v[D];
 #pragma unroll
@@ -175,7 +148,7 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   // ---------------------------------------------------------------- own rows
   for (int i = lo + threadIdx.x; i < hi; i += NT) {
     float ul[D], ai;
-    const float al0 = row_terms<D>(mp, a, cb, lastL, left_leaf, i, mu, ul, ai, corrupt);
+    const float al0 = row_terms<D>(mp, N, d, a.logN, Xl, lastL, lwl, i, mu, ul, ai, corrupt);
     const float dl = row_shift<D, true>(ul, al0, sV, sB, N);
     const float al = __fsub_rn(al0, dl);
     bad |= isnan(ai);

@@ -104,11 +104,32 @@ __device__ __forceinline__ void split_mma(float x, int compute, float* hi, float
 // ---------------------------------------------------------------------------------------
 template <int D>
 __host__ __device__ constexpr int prologue_threads() {
-  return D <= 8 ? 512 : 256;
+  return D <= 8 ? 256 : 128;   // several combinations per SM: the pass is latency-bound
+}
+
+// Shared-memory staging of the prologue (floats, each array rounded up to 4): the two
+// particle slices X_c and X_{c-1} [N][d], one index map or leaf log-weight row per side
+// [N], and the column terms v [N][D] and beta [N].  Staged when it fits kProStageMax bytes;
+// otherwise every read goes to global memory.
+constexpr size_t kProStageMax = 112 * 1024;
+__host__ __device__ constexpr int round4(int n) { return (n + 3) & ~3; }
+template <int D>
+__host__ __device__ constexpr size_t prologue_stage_bytes(int N, int d) {
+  return sizeof(float) * (2 * (size_t)round4(N * d) + 3 * (size_t)round4(N) + (size_t)round4(N * D));
+}
+template <int D>
+__host__ __device__ constexpr bool prologue_staged(int N, int d) {
+  return prologue_stage_bytes<D>(N, d) <= kProStageMax;
 }
 
 template <int D>
-__global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeArgs a, ModelParams<D> mp) {
+__host__ __device__ constexpr int prologue_min_blocks() {
+  return D <= 4 ? 4 : 0;   // 0: no minimum (larger D would spill)
+}
+
+template <int D>
+__global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>())
+    prologue_kernel(MergeArgs a, ModelParams<D> mp) {
   constexpr int kProThreads = prologue_threads<D>();
   constexpr int NW = kProThreads / 32;
   const int s = blockIdx.x;
@@ -122,6 +143,45 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
   const int bufR = ceil_log2(sR) & 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
+  float* V = a.ws.V + (size_t)s * N * D;
+  float* beta = a.ws.beta + (size_t)s * N;
+  float* U = a.ws.U + (size_t)s * N * D;
+  float* alpha = a.ws.alpha + (size_t)s * N;
+  double* shift = a.ws.shift + (size_t)s * N;
+  const int32_t* firstR = right_leaf ? nullptr : cb.first + ((size_t)bufR * cb.K + c) * N;
+  const int32_t* lastL = left_leaf ? nullptr : cb.last + ((size_t)bufL * cb.K + at) * N;
+  const float* Xc = cb.X + (size_t)c * N * d;
+  const float* Xl = cb.X + (size_t)(c - 1) * N * d;
+  const float* lwc = right_leaf ? cb.logw + (size_t)c * N : nullptr;
+  const float* lwl = left_leaf ? cb.logw + (size_t)(c - 1) * N : nullptr;
+  // the column terms as pass 2 and the row shift read them back
+  float* Vs = V;
+  float* Bs = beta;
+  const bool staged = prologue_staged<D>(N, d);
+  if (staged) {  // every input of the combination in one round of coalesced loads
+    extern __shared__ float4 pro_smem4[];
+    float* sXc = reinterpret_cast<float*>(pro_smem4);
+    float* sXl = sXc + round4(N * d);
+    float* sR0 = sXl + round4(N * d);
+    float* sL0 = sR0 + round4(N);
+    Bs = sL0 + round4(N);
+    Vs = Bs + round4(N);
+    stage_words(sXc, Xc, N * d);
+    stage_words(sXl, Xl, N * d);
+    if (right_leaf)
+      stage_words(sR0, lwc, N);
+    else
+      stage_words(reinterpret_cast<int32_t*>(sR0), firstR, N);
+    if (left_leaf)
+      stage_words(sL0, lwl, N);
+    else
+      stage_words(reinterpret_cast<int32_t*>(sL0), lastL, N);
+    Xc = sXc;
+    Xl = sXl;
+    if (right_leaf) lwc = sR0; else firstR = reinterpret_cast<const int32_t*>(sR0);
+    if (left_leaf) lwl = sL0; else lastL = reinterpret_cast<const int32_t*>(sL0);
+  }
+
   float yc[D], qm[D], qs[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) yc[k] = k < d ? cb.y[(size_t)c * d + k] : 0.f;
@@ -129,74 +189,42 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
   float qinv[D];
   const float qnorm = proposal_consts<D>(d, qs, qinv);
 
-  float* V = a.ws.V + (size_t)s * N * D;
-  float* beta = a.ws.beta + (size_t)s * N;
-  float* U = a.ws.U + (size_t)s * N * D;
-  float* alpha = a.ws.alpha + (size_t)s * N;
-  double* shift = a.ws.shift + (size_t)s * N;
-  const int32_t* firstR = cb.first + ((size_t)bufR * cb.K + c) * N;
-  const int32_t* lastL = cb.last + ((size_t)bufL * cb.K + at) * N;
-
-  __shared__ float red_v[NW][D];
+  __shared__ float gsum[kMaxColumnGroups * D];
   __shared__ float red_s[NW];
   __shared__ float mu_s[D];
   __shared__ float bstar_s;
+  if (staged) __syncthreads();
 
-  // pass 1: right block at time c
-  float sx[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) sx[k] = 0.f;
-  float bmax = -INFINITY;
+  // pass 1: right block at time c (column states, b'_j; the mean mu and B*)
   bool bad = false, corrupt = false;
-  for (int j = threadIdx.x; j < N; j += kProThreads) {
-    float x[D];
-    const float bp = column_bprime<D>(mp, a, cb, yc, qm, qinv, qnorm, firstR, right_leaf, j, x, corrupt);
-    bad |= isnan(bp);
+  float mu[D], bstar;
+  column_pass<D>(N, gsum, red_s, mu_s, &bstar_s, mu, bstar, bad, [&](int j, float* x) {
+    const float bp = column_bprime<D>(mp, N, d, a.logN, yc, qm, qinv, qnorm, Xc, firstR, lwc, j, x, corrupt);
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      V[(size_t)j * D + k] = x[k];
-      sx[k] += x[k];
-    }
-    beta[j] = bp;
-    bmax = fmaxf(bmax, bp);
-  }
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const float v = warp_sum(sx[k]);
-    if (lane == 0) red_v[warp][k] = v;
-  }
-  bmax = warp_max(bmax);
-  if (lane == 0) red_s[warp] = bmax;
-  __syncthreads();
-  if (threadIdx.x < D) {
-    float t = 0.f;
-    for (int w = 0; w < NW; ++w) t += red_v[w][threadIdx.x];
-    mu_s[threadIdx.x] = t / (float)N;
-  }
-  if (threadIdx.x == 0) {
-    float t = red_s[0];
-    for (int w = 1; w < NW; ++w) t = fmaxf(t, red_s[w]);
-    bstar_s = t;
-  }
-  __syncthreads();
-  float mu[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) mu[k] = mu_s[k];
-  const float bstar = bstar_s;
+    for (int k = 0; k < D; ++k) Vs[(size_t)j * D + k] = x[k];
+    Bs[j] = bp;
+    return bp;
+  });
 
   // pass 2a: columns  v_j = xR_j - mu,  beta_j = log2(e) (b'_j - B* - 1/2 v' Q^-1 v)
   for (int j = threadIdx.x; j < N; j += kProThreads) {
     float v[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) v[k] = V[(size_t)j * D + k];
-    beta[j] = column_beta<D>(mp, v, mu, beta[j], bstar);
+    for (int k = 0; k < D; ++k) v[k] = Vs[(size_t)j * D + k];
+    const float bj = column_beta<D>(mp, v, mu, Bs[j], bstar);
+    beta[j] = bj;
 #pragma unroll
     for (int k = 0; k < D; ++k) V[(size_t)j * D + k] = v[k];
+    if (staged) {
+      Bs[j] = bj;
+#pragma unroll
+      for (int k = 0; k < D; ++k) Vs[(size_t)j * D + k] = v[k];
+    }
     if (a.compute != DSMC_FP32) {
       float ext[4];
       ext[0] = 1.f;
       ext[1] = 1.f;
-      split_mma(beta[j], a.compute, &ext[2], &ext[3]);
+      split_mma(bj, a.compute, &ext[2], &ext[3]);
       store_mma_row<D>(a.ws.Vb + (size_t)s * a.Nr * a.mma_planes * 32, a.Nr, j, v, ext, a.compute);
     }
   }
@@ -215,8 +243,8 @@ __global__ void __launch_bounds__(prologue_threads<D>()) prologue_kernel(MergeAr
   float amax = -INFINITY;
   for (int i = threadIdx.x; i < N; i += kProThreads) {
     float ul[D], ai;
-    const float al0 = row_terms<D>(mp, a, cb, lastL, left_leaf, i, mu, ul, ai, corrupt);
-    const float dl = row_shift<D, false>(ul, al0, V, beta, N);
+    const float al0 = row_terms<D>(mp, N, d, a.logN, Xl, lastL, lwl, i, mu, ul, ai, corrupt);
+    const float dl = row_shift<D, false>(ul, al0, Vs, Bs, N);
     const float al = __fsub_rn(al0, dl);
     bad |= isnan(ai);
 #pragma unroll
@@ -582,7 +610,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 2 : 1) cdf_slots_ker
   float* delta = a.ws.delta + (size_t)s * N;
   float* rowsum = a.ws.rowsum + (size_t)s * N;
   // stage the operands (vector copies when D % 4 == 0: rows and pads are 16-byte aligned)
-  if ((D % 4) == 0) {
+  if constexpr ((D % 4) == 0) {
     const float4* V4 = reinterpret_cast<const float4*>(V);
     const float4* U4 = reinterpret_cast<const float4*>(U);
     for (int q = threadIdx.x; q < N * D / 4; q += NT) {
@@ -814,7 +842,11 @@ int launch_slots(const MergeArgs& a) {
 
 template <int D>
 cudaError_t prologue_t(const MergeArgs& a, const void* mp, cudaStream_t st) {
-  prologue_kernel<D><<<a.mc, prologue_threads<D>(), 0, st>>>(a, *static_cast<const ModelParams<D>*>(mp));
+  const size_t smem = prologue_staged<D>(a.N, a.d) ? prologue_stage_bytes<D>(a.N, a.d) : 0;
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      prologue_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProStageMax);
+  if (attr != cudaSuccess) return attr;
+  prologue_kernel<D><<<a.mc, prologue_threads<D>(), smem, st>>>(a, *static_cast<const ModelParams<D>*>(mp));
   return cudaGetLastError();
 }
 

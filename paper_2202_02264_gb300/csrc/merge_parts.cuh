@@ -66,21 +66,77 @@ __host__ __device__ __forceinline__ int vpad_floats(int N) {
 __host__ __device__ __forceinline__ int bpad_floats(int N) { return N + ((N + 31) >> 5); }
 
 // ---------------------------------------------------------------- column and row terms
-// Column j, first pass: the right block's state xR_j (through the first-index map unless
-// the right block is a leaf) and b'_j.  Returns b'_j; x receives the padded state.
+// Column j, first pass: the right block's state xR_j (particle map[j] of the time-c slice
+// Xs [N][d], or particle j when the right block is a leaf, map = nullptr) and
+// b'_j = b_j + log h - log nu, where b_j is the leaf's log-weight lw[j] (lw = nullptr:
+// a merged block, b_j = -log N).  Returns b'_j; x receives the padded state.
 template <int D>
-__device__ __forceinline__ float column_bprime(const ModelParams<D>& mp, const MergeArgs& a, const Comb& cb,
+__device__ __forceinline__ float column_bprime(const ModelParams<D>& mp, int N, int d, float logN,
                                                const float* yc, const float* qm, const float* qinv,
-                                               float qnorm, const int32_t* firstR, bool right_leaf,
-                                               int j, float* x, bool& corrupt) {
-  const int N = a.N, d = a.d, c = cb.c;
-  const int idx = right_leaf ? j : checked_index(firstR[j], N, corrupt);
-  const float* xp = cb.X + ((size_t)c * N + idx) * d;
+                                               float qnorm, const float* Xs, const int32_t* map,
+                                               const float* lw, int j, float* x, bool& corrupt) {
+  const int idx = map != nullptr ? checked_index(map[j], N, corrupt) : j;
+  const float* xp = Xs + (size_t)idx * d;
 #pragma unroll
   for (int k = 0; k < D; ++k) x[k] = k < d ? xp[k] : 0.f;
-  const float bj = right_leaf ? cb.logw[(size_t)c * N + j] : -a.logN;
+  const float bj = lw != nullptr ? lw[j] : -logN;
   const float g = log_h<D>(mp, yc, x) - log_nu<D>(mp, yc, qm, qinv, qnorm, x);
   return bj + g;
+}
+
+// The column pass with the column mean mu reduced in a fixed order that does not depend on
+// the block size.  Columns fall into G <= 32 groups of 32 Q consecutive columns, where
+// Q = ceil(N / 1024); warp w of NW takes the groups g = w, w + NW, ...; in a group, lane l
+// adds its columns 32 (Q g + c) + l in order of c, then the lanes are summed by a butterfly
+// into gsum[g][k]; the group sums are added in group order.  `col(j, x)` evaluates column
+// j (j < N) into x[D] and returns b'_j.  Returns mu (every thread) and B* = max_j b'_j.
+constexpr int kMaxColumnGroups = 32;
+
+template <int D, typename ColFn>
+__device__ __forceinline__ void column_pass(int N, float* gsum, float* red_s, float* mu_s, float* bstar_s,
+                                            float* mu, float& bstar, bool& bad, ColFn col) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  const int Q = (N + 1023) / 1024, Wd = 32 * Q;
+  const int G = (N + Wd - 1) / Wd;
+  float bmax = -INFINITY;
+  for (int g = warp; g < G; g += NW) {
+    float acc[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] = 0.f;
+    for (int c = 0; c < Q; ++c) {
+      const int j = Wd * g + 32 * c + lane;
+      if (j < N) {
+        float x[D];
+        const float bp = col(j, x);
+        bad |= isnan(bp);
+        bmax = fmaxf(bmax, bp);
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[k] += x[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float t = warp_sum(acc[k]);
+      if (lane == 0) gsum[g * D + k] = t;
+    }
+  }
+  bmax = warp_max(bmax);
+  if (lane == 0) red_s[warp] = bmax;
+  __syncthreads();
+  if (threadIdx.x < D) {
+    float t = 0.f;
+    for (int g = 0; g < G; ++g) t += gsum[g * D + threadIdx.x];
+    mu_s[threadIdx.x] = t / (float)N;
+  }
+  if (threadIdx.x == 0) {
+    float t = red_s[0];
+    for (int w = 1; w < NW; ++w) t = fmaxf(t, red_s[w]);
+    *bstar_s = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < D; ++k) mu[k] = mu_s[k];
+  bstar = *bstar_s;
 }
 
 // Column j, second pass: v_j = xR_j - mu (in place) and beta_j.
@@ -92,15 +148,15 @@ __device__ __forceinline__ float column_beta(const ModelParams<D>& mp, float* v,
   return kLog2e * (bprime - bstar - 0.5f * quad_form<D>(mp.Qi, v));
 }
 
-// Row i: the left block's state xL_i (through the last-index map unless the left block is
-// a leaf), u_i (already scaled by log2(e)), alpha_i, a_i.  Returns alpha_i.
+// Row i: the left block's state xL_i (particle map[i] of the time-(c - 1) slice Xs, or
+// particle i when the left block is a leaf, map = nullptr), u_i (already scaled by
+// log2(e)), alpha_i, and a_i (the leaf's log-weight lw[i], or -log N).  Returns alpha_i.
 template <int D>
-__device__ __forceinline__ float row_terms(const ModelParams<D>& mp, const MergeArgs& a, const Comb& cb,
-                                           const int32_t* lastL, bool left_leaf, int i,
+__device__ __forceinline__ float row_terms(const ModelParams<D>& mp, int N, int d, float logN,
+                                           const float* Xs, const int32_t* map, const float* lw, int i,
                                            const float* mu, float* ul, float& ai, bool& corrupt) {
-  const int N = a.N, d = a.d, c = cb.c;
-  const int idx = left_leaf ? i : checked_index(lastL[i], N, corrupt);
-  const float* xp = cb.X + ((size_t)(c - 1) * N + idx) * d;
+  const int idx = map != nullptr ? checked_index(map[i], N, corrupt) : i;
+  const float* xp = Xs + (size_t)idx * d;
   float x[D], w[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) x[k] = k < d ? xp[k] : 0.f;
@@ -120,8 +176,24 @@ __device__ __forceinline__ float row_terms(const ModelParams<D>& mp, const Merge
     ul[r] = kLog2e * acc;
     q = fmaf(w[r], acc, q);
   }
-  ai = left_leaf ? cb.logw[(size_t)(c - 1) * N + i] : -a.logN;
+  ai = lw != nullptr ? lw[i] : -logN;
   return -0.5f * kLog2e * q;
+}
+
+// A block's copy of n 32-bit words from global to shared memory (16-byte vector loads when
+// both ends are 16-byte aligned).  The caller synchronises.
+template <typename T>
+__device__ __forceinline__ void stage_words(T* dst, const T* src, int n) {
+  static_assert(sizeof(T) == 4, "32-bit words");
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+    const int n4 = n >> 2;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    for (int t = threadIdx.x; t < n4; t += blockDim.x) d4[t] = __ldg(s4 + t);
+    for (int t = 4 * n4 + threadIdx.x; t < n; t += blockDim.x) dst[t] = __ldg(src + t);
+  } else {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = __ldg(src + t);
+  }
 }
 
 // Row i's base-2 shift delta_i: the largest exponent over a fixed sample of 8 columns

@@ -80,7 +80,8 @@ EXPORTS = ["dsmc_status_string", "dsmc_last_error", "dsmc_state_sizes", "dsmc_wo
            "dsmc_profile_enable",
            "dsmc_profile_read", "dsmc_debug_philox", "dsmc_debug_merge_weights",
            "dsmc_batch_workspace_size", "dsmc_batch_prepare", "dsmc_batch_run", "dsmc_smooth_batch",
-           "dsmc_seq_maps_bytes", "dsmc_serve_workspace_size", "dsmc_serve_tick"]
+           "dsmc_seq_maps_bytes", "dsmc_serve_workspace_size", "dsmc_serve_tick",
+           "dsmc_profile_breakdown_enable", "dsmc_profile_breakdown_read"]
 
 
 def library_path() -> str:
@@ -129,6 +130,8 @@ def load(build_if_needed: bool = False) -> C.CDLL:
         lib.dsmc_seq_maps_bytes.argtypes = [C.c_int, C.c_int]
         lib.dsmc_serve_workspace_size.argtypes = [cfgp, modp, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
         lib.dsmc_serve_tick.argtypes = [cfgp, modp, prop_p, C.c_int, C.POINTER(Seq), C.POINTER(C.c_int), vp, sz, vp]
+        lib.dsmc_profile_breakdown_enable.argtypes = [C.c_int]
+        lib.dsmc_profile_breakdown_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         seqp = C.POINTER(Seq)
         lib.dsmc_batch_workspace_size.argtypes = [cfgp, modp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         for name in ("dsmc_batch_prepare", "dsmc_batch_run", "dsmc_smooth_batch"):
@@ -337,6 +340,20 @@ def dsmc_batch_run(cfg, model, prop, seqs, ws, stream=None):
 
 def dsmc_smooth_batch(cfg, model, prop, seqs, ws, stream=None):
     _batch_call("dsmc_smooth_batch", cfg, model, prop, seqs, ws, stream)
+
+
+KINDS = ["init", "prologue", "tile_sums", "draws", "fused_levels", "resolve", "gather", "other"]
+
+
+def dsmc_profile_breakdown_enable(enable: bool):
+    _check(load().dsmc_profile_breakdown_enable(1 if enable else 0), "dsmc_profile_breakdown_enable")
+
+
+def dsmc_profile_breakdown_read() -> dict:
+    ms = (C.c_double * 8)()
+    n = (C.c_int64 * 8)()
+    _check(load().dsmc_profile_breakdown_read(ms, n), "dsmc_profile_breakdown_read")
+    return {KINDS[k]: {"ms": ms[k], "launches": int(n[k])} for k in range(8) if n[k] > 0}
 
 
 def dsmc_seq_maps_bytes(K: int, N: int) -> int:
