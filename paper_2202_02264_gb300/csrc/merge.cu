@@ -557,12 +557,21 @@ __global__ void __launch_bounds__(kSlotThreads) slots_kernel(MergeArgs a) {
 constexpr int kCdfSlotThreads = 512;
 
 // Shared memory: padded v [vpad_floats], u [N][D], padded beta, l [N], prefix sums [N].
+// Shared-memory layout of the row CDF + draws kernel.  The tile sums T are staged too (row
+// stride nTs = nTp, plus 4 when nTp / 4 is even, so that the rows of 8 consecutive threads
+// fall in distinct 16-byte bank groups) when the whole fits kCdfStageMax (two CTAs per SM).
+constexpr size_t kCdfStageMax = 100 * 1024;
 struct CdfSlotsSmem {
-  size_t v, u, b, l, c, total;
+  size_t v, u, b, l, c, t, total;
+  int nTs;  // staged row stride of T, 0 when T stays in global memory
 };
 
+__host__ __device__ __forceinline__ int staged_tile_stride(int nTp) {
+  return ((nTp / 4) % 2 == 0) ? nTp + 4 : nTp;
+}
+
 template <int D>
-__host__ __device__ __forceinline__ CdfSlotsSmem cdf_slots_smem(int N) {
+__host__ __device__ __forceinline__ CdfSlotsSmem cdf_slots_smem(int N, int nTp) {
   const auto r16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
   CdfSlotsSmem f;
   size_t o = 0;
@@ -571,6 +580,15 @@ __host__ __device__ __forceinline__ CdfSlotsSmem cdf_slots_smem(int N) {
   f.b = o; o = r16(o + (size_t)bpad_floats(N) * 4);
   f.l = o; o = r16(o + (size_t)N * 4);
   f.c = o; o = r16(o + (size_t)N * 8);
+  f.t = o;
+  const int nTs = staged_tile_stride(nTp);
+  const size_t with_t = r16(o + (size_t)N * nTs * 4);
+  if (with_t <= kCdfStageMax) {
+    f.nTs = nTs;
+    o = with_t;
+  } else {
+    f.nTs = 0;
+  }
   f.total = o;
   return f;
 }
@@ -585,8 +603,9 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 2 : 1) cdf_slots_ker
   const int N = a.N, nT = a.nT, nTp = a.nTp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const CdfSlotsSmem L = cdf_slots_smem<D>(N);
+  const CdfSlotsSmem L = cdf_slots_smem<D>(N, nTp);
   float* sV = reinterpret_cast<float*>(smraw + L.v);
+  float* sT = L.nTs ? reinterpret_cast<float*>(smraw + L.t) : nullptr;
   float* sU = reinterpret_cast<float*>(smraw + L.u);
   float* sB = reinterpret_cast<float*>(smraw + L.b);
   float* sL = reinterpret_cast<float*>(smraw + L.l);
@@ -626,9 +645,14 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 2 : 1) cdf_slots_ker
     }
   }
   for (int q = threadIdx.x; q < N; q += NT) sB[bidx<true>(q)] = beta[q];
-  // row totals
+  // row totals (and the staged copy of the tile sums)
   for (int i = threadIdx.x; i < N; i += NT) {
-    float t = row_total(Tt + (size_t)i * nTp, nT, nTp);
+    if (sT) {
+      const float4* src = reinterpret_cast<const float4*>(Tt + (size_t)i * nTp);
+      float4* dst = reinterpret_cast<float4*>(sT + (size_t)i * L.nTs);
+      for (int k4 = 0; k4 < nTp / 4; ++k4) dst[k4] = src[k4];
+    }
+    float t = sT ? row_total(sT + (size_t)i * L.nTs, nT, nTp) : row_total(Tt + (size_t)i * nTp, nT, nTp);
     if (isnan(t)) {
       nonfinite_s = 1;
       t = 0.f;
@@ -643,6 +667,10 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 2 : 1) cdf_slots_ker
     float si, dl;
     recompute_row<D, true>(sU + (size_t)i * D, alpha[i], sV, sB, N, a.B, nT, Tt + (size_t)i * nTp, &si, &dl);
     __syncwarp();
+    if (sT) {  // the rewritten row into the staged copy
+      for (int k = lane; k < nT; k += 32) sT[(size_t)i * L.nTs + k] = Tt[(size_t)i * nTp + k];
+      __syncwarp();
+    }
     if (lane == 0) {
       si = row_total(Tt + (size_t)i * nTp, nT, nTp);
       sL[i] = isnan(si) ? 0.f : si;
@@ -691,7 +719,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 2 : 1) cdf_slots_ker
   const SlotOut o = slot_out(a, cb, threadIdx.x == 0);
   DrawIn in;
   in.cum = sC;
-  in.T = Tt;
+  in.T = sT ? sT : Tt;
   in.U = sU;
   in.alpha = alpha;
   in.delta = delta;
@@ -700,7 +728,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 2 : 1) cdf_slots_ker
   in.N = N;
   in.B = a.B;
   in.nT = nT;
-  in.nTp = nTp;
+  in.nTp = sT ? L.nTs : nTp;
   const int n_lo = cb.conditional ? 1 : 0;
   const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
   for (int n = n_lo + threadIdx.x; n < n_hi; n += NT) {
@@ -868,7 +896,7 @@ cudaError_t rowsum_t(const MergeArgs& a, cudaStream_t st) {
 
 template <int D>
 cudaError_t sample_dense_t(const MergeArgs& a, cudaStream_t st) {
-  const size_t smem_cs = cdf_slots_smem<D>(a.N).total;
+  const size_t smem_cs = cdf_slots_smem<D>(a.N, a.nTp).total;
   if (smem_cs <= 200 * 1024) {  // one CTA per combination: row CDF and draws
     cudaError_t e = cudaFuncSetAttribute(cdf_slots_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_cs);

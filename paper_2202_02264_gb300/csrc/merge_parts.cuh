@@ -373,15 +373,17 @@ struct DrawIn {
   int N, B, nT, nTp;
 };
 
-// Fixed-point pick over n <= 32 weights held in registers: q_k = q24(x_k; ref), Q = sum q
-// (< 2^29 for tile weights below their maximum, < 2^29 for columns below twice their tile
-// weight), T = floor(w Q / 2^32) (w a 32-bit uniform word), the number of prefix sums <= T,
-// clamped to n - 1; 0 when Q = 0.
-__device__ __forceinline__ int pick32(const float* x, int n, uint32_t w, int ref_be) {
-  uint32_t q[32];
+// Fixed-point pick over n <= W <= 32 weights held in registers: q_k = q24(x_k; ref),
+// Q = sum q (< 2^29 for tile weights below their maximum, < 2^29 for columns below twice
+// their tile weight), T = floor(w Q / 2^32) (w a 32-bit uniform word), the number of prefix
+// sums <= T, clamped to n - 1; 0 when Q = 0.  Entries past n add nothing to Q and never
+// count (their prefix sum is Q > T), so every W >= n gives the same index.
+template <int W>
+__device__ __forceinline__ int pick_w(const float* x, int n, uint32_t w, int ref_be) {
+  uint32_t q[W];
   uint32_t Q = 0;
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
+  for (int k = 0; k < W; ++k) {
     q[k] = (k < n) ? q24(x[k], ref_be) : 0u;
     Q += q[k];
   }
@@ -390,11 +392,35 @@ __device__ __forceinline__ int pick32(const float* x, int n, uint32_t w, int ref
   uint32_t c = 0;
   int idx = 0;
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
+  for (int k = 0; k < W; ++k) {
     c += q[k];
     idx += (c <= T) ? 1 : 0;
   }
   return min(idx, n - 1);
+}
+__device__ __forceinline__ int pick32(const float* x, int n, uint32_t w, int ref_be) {
+  return pick_w<32>(x, n, w, ref_be);
+}
+
+// The tile stage over nT <= W tiles of a row held in registers: the largest tile is the
+// reference.
+template <int W>
+__device__ __forceinline__ int pick_tile(const float* Ti, int nT, uint32_t w) {
+  float t[W];
+  const float4* Ti4 = reinterpret_cast<const float4*>(Ti);
+#pragma unroll
+  for (int k4 = 0; k4 < W / 4; ++k4) {
+    const float4 v = (4 * k4 < nT) ? Ti4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    t[4 * k4] = v.x;
+    t[4 * k4 + 1] = v.y;
+    t[4 * k4 + 2] = v.z;
+    t[4 * k4 + 3] = v.w;
+  }
+  float tmax = 0.f;
+#pragma unroll
+  for (int k = 0; k < W; ++k)
+    if (k < nT) tmax = fmaxf(tmax, t[k]);
+  return pick_w<W>(t, nT, w, ref_exponent(tmax));
 }
 
 // The same pick over n weights in memory (any n; 64-bit sums).
@@ -439,22 +465,10 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
   i = lo;
   const float* Ti = in.T + (size_t)i * nTp;
   int kt;
-  if (nT <= 32) {
-    float t[32];
-    const float4* Ti4 = reinterpret_cast<const float4*>(Ti);
-#pragma unroll
-    for (int k4 = 0; k4 < 8; ++k4) {
-      const float4 v = (4 * k4 < nT) ? Ti4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
-      t[4 * k4] = v.x;
-      t[4 * k4 + 1] = v.y;
-      t[4 * k4 + 2] = v.z;
-      t[4 * k4 + 3] = v.w;
-    }
-    float tmax = 0.f;
-#pragma unroll
-    for (int k = 0; k < 32; ++k)
-      if (k < nT) tmax = fmaxf(tmax, t[k]);
-    kt = pick32(t, nT, w.z, ref_exponent(tmax));
+  if (nT <= 16) {
+    kt = pick_tile<16>(Ti, nT, w.z);
+  } else if (nT <= 32) {
+    kt = pick_tile<32>(Ti, nT, w.z);
   } else {
     float tmax = 0.f;
     for (int k = 0; k < nT; ++k) tmax = fmaxf(tmax, Ti[k]);
@@ -467,7 +481,18 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
   const float al = __fsub_rn(in.alpha[i], in.delta[i]);
   const float* V = in.V;
   const float* beta = in.beta;
-  if (ncol <= 32) {
+  if (ncol == 32) {  // a full tile: the columns sit at fixed offsets from the tile's first
+    const float* Vt = V + vidx<D, PAD>(jb);
+    const float* bt = beta + bidx<PAD>(jb);
+    float e[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      float v[D];
+      load_row<D>(Vt + q * D, v);
+      e[q] = ex2(pair_exponent<D>(u, al, v, bt[q]));
+    }
+    j = jb + pick32(e, 32, w.w, tbe);
+  } else if (ncol <= 32) {
     float e[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
