@@ -155,13 +155,12 @@ __device__ __forceinline__ Item item_of(const MergeArgs& a, int it) {
   return r;
 }
 
-// Column blocks staged ahead (P = 1: 16 x 4 KB, P = 2: 10 x 8 KB, P = 3: 6 x 12 KB) and the refill lag: a
-// slot is refilled once the epilogue finished its block.
+// Column blocks staged ahead (P = 1: 16 x 4 KB, P = 2: 10 x 8 KB, P = 3: 6 x 12 KB); a slot
+// is refilled once the MMA that read it has completed.
 template <int P>
 __host__ __device__ constexpr int v_slots() {
   return P == 1 ? 16 : (P == 2 ? 10 : 6);
 }
-constexpr int kRefillLag = 4;
 
 template <int KIND, int P>
 __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, int n_items) {
@@ -170,7 +169,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
   extern __shared__ __align__(128) unsigned char dsm[];
   unsigned char* sA = dsm;                                        // [2][P][4 KB] row tiles
   unsigned char* sV = dsm + 2 * kSlotBytes;                       // [kVSlots][P][4 KB] column blocks
-  __shared__ __align__(8) uint64_t bar_a[2], bar_v[kVSlots], bar_done[kVSlots], bar_mma[2], bar_epi[2];
+  // bar_a / bar_v: a row tile / column block landed (TMA); bar_afree / bar_vfree: the MMAs
+  // that read it completed (tcgen05.commit), so the buffer may be refilled; bar_mma: a block's
+  // accumulator is complete; bar_epi: the epilogue has read it out of TMEM
+  __shared__ __align__(8) uint64_t bar_a[2], bar_afree[2], bar_v[kVSlots], bar_vfree[kVSlots], bar_mma[2],
+      bar_epi[2];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_s;
 
@@ -180,12 +183,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
     abort_s = 0;
     for (int q = 0; q < 2; ++q) {
       mbar_init(smem_u32(&bar_a[q]), 1);
+      mbar_init(smem_u32(&bar_afree[q]), 1);
       mbar_init(smem_u32(&bar_mma[q]), 1);
       mbar_init(smem_u32(&bar_epi[q]), kEpiWarps);
     }
     for (int q = 0; q < kVSlots; ++q) {
       mbar_init(smem_u32(&bar_v[q]), 1);
-      mbar_init(smem_u32(&bar_done[q]), kEpiWarps);
+      mbar_init(smem_u32(&bar_vfree[q]), 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
       bool ok = true;
       int issued = 0;
       // load cursor over the CTA's block sequence
-      int l_it = blockIdx.x, l_b = 0, lq = 0, l_k = 0;
+      int l_it = blockIdx.x, l_b = 0, lq = 0;
       Item li = item_of(a, l_it);
       const size_t plane = (size_t)a.Nr * 32;  // bytes of one K plane of one combination
       auto load_next = [&]() {  // the P planes of the next column block, one barrier
@@ -230,7 +234,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
         if (++l_b == li.nblk) {
           l_b = 0;
           l_it += gridDim.x;
-          ++l_k;
           if (l_it < n_items) li = item_of(a, l_it);
         }
       };
@@ -250,43 +253,28 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
               "l"(src + (size_t)p * plane), "r"((uint32_t)kTileBytes), "r"(bar)
               : "memory");
       };
+      // Buffers are refilled as soon as the MMAs that read them complete (their commits):
+      // column block q + kVSlots - 2 is loaded before block q's MMA (into the slot of block
+      // q - 2), and item k + 1's row tile after item k's first MMA (into item k - 1's buffer).
       load_a(blockIdx.x, 0);
       load_a(blockIdx.x + gridDim.x, 1);
       for (int q = 0; q < kVSlots; ++q) load_next();
-      // blocks whose epilogue completion still has to release their slot / A tile
-      int r = 0, r_b = 0, r_k = 0;
-      Item ri = item_of(a, blockIdx.x);
-      auto retire = [&](int upto) {  // refill slots of blocks r < upto (epilogue done)
-        while (ok && r < upto) {
-          ok = mbar_wait(smem_u32(&bar_done[r % kVSlots]), (uint32_t)(r / kVSlots) & 1);
-          if (!ok) break;
-          load_next();
-          if (r_b == ri.nblk - 1) load_a(blockIdx.x + (r_k + 2) * gridDim.x, r_k & 1);
-          ++r;
-          if (++r_b == ri.nblk) {
-            r_b = 0;
-            ++r_k;
-            const int nit = blockIdx.x + r_k * gridDim.x;
-            if (nit < n_items) ri = item_of(a, nit);
-          }
-        }
-      };
-      int q = 0;       // global block index of this CTA
-      int k = 0;       // item index of this CTA
-      int q_prev = 0;  // first block of the previous item
+      int q = 0;  // global block index of this CTA
+      int k = 0;  // item index of this CTA
+      int last_item = -1;
       for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++k) {
         const Item cur = item_of(a, it);
-        // item k's row tile is loaded when item k-2 retires: retire every block before the
-        // previous item first (short items would otherwise outrun the refill lag)
-        if (k >= 2) retire(q_prev);
-        q_prev = q;
-        if (ok) ok = mbar_wait(smem_u32(&bar_a[k & 1]), (uint32_t)(k >> 1) & 1);
+        ok = mbar_wait(smem_u32(&bar_a[k & 1]), (uint32_t)(k >> 1) & 1);
         const uint32_t sa = smem_u32(sA + (size_t)(k & 1) * kSlotBytes);
         for (int b = 0; b < cur.nblk && ok; ++b, ++q) {
           const int buf = q & 1;
           const int slot = q % kVSlots;
-          retire(q - kRefillLag);
-          if (ok && q >= 2) ok = mbar_wait(smem_u32(&bar_epi[buf]), (uint32_t)((q >> 1) - 1) & 1);
+          if (q >= 2) {
+            ok = mbar_wait(smem_u32(&bar_vfree[(q - 2) % kVSlots]), (uint32_t)((q - 2) / kVSlots) & 1);
+            if (!ok) break;
+            load_next();
+          }
+          if (q >= 2) ok = mbar_wait(smem_u32(&bar_epi[buf]), (uint32_t)((q >> 1) - 1) & 1);
           if (ok) ok = mbar_wait(smem_u32(&bar_v[slot]), (uint32_t)(q / kVSlots) & 1);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -296,14 +284,27 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
             mma<KIND>(tb + (uint32_t)buf * kTcCols, smem_desc(sa + p * kTileBytes), smem_desc(sv + p * kTileBytes),
                       p > 0 ? 1u : 0u);
           mma_commit(smem_u32(&bar_mma[buf]));
+          mma_commit(smem_u32(&bar_vfree[slot]));
           ++issued;
+          if (b == cur.nblk - 1) {
+            mma_commit(smem_u32(&bar_afree[k & 1]));
+            last_item = k;
+          }
+          if (b == 0 && k >= 1) {  // item k - 1's MMAs are done: its buffer takes item k + 1
+            ok = mbar_wait(smem_u32(&bar_afree[(k - 1) & 1]), (uint32_t)((k - 1) >> 1) & 1);
+            if (!ok) break;
+            load_a(it + gridDim.x, (k + 1) & 1);
+          }
         }
       }
-      // the last committed MMA must be complete before TMEM is released
+      // every committed MMA must be complete (and its barrier arrivals landed) before TMEM
+      // and the shared memory are released
       if (issued > 0) {
         const int qq = issued - 1;
         mbar_wait(smem_u32(&bar_mma[qq & 1]), (uint32_t)(qq >> 1) & 1);
+        mbar_wait(smem_u32(&bar_vfree[qq % kVSlots]), (uint32_t)(qq / kVSlots) & 1);
       }
+      if (last_item >= 0) mbar_wait(smem_u32(&bar_afree[last_item & 1]), (uint32_t)(last_item >> 1) & 1);
       if (!ok) {
         atomicExch(&abort_s, 1);
         record_status(a.ws.status, DSMC_ERR_TIMEOUT);
@@ -321,7 +322,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
       bool stop = false;
       for (int b = 0; b < cur.nblk; ++b, ++q) {
         const int buf = q & 1;
-        const int slot = q % kVSlots;
         const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_mma[buf]), (uint32_t)(q >> 1) & 1)) &&
                         !*reinterpret_cast<volatile int*>(&abort_s);
         if (!ok) {  // warp-uniform
@@ -343,8 +343,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bar_epi[buf]));
-        // the MMA that read the slot has completed (its commit arrived): the slot is free
-        if (lane == 0) mbar_arrive(smem_u32(&bar_done[slot]));
         float t0, t1;
         if (col0 + 64 <= cur.j1) {
           t0 = exp_sum32<false>(acc0, 32);

@@ -257,11 +257,13 @@ def _gpu_means(m, y, K, N, R, resampler=dsmc.MULTINOMIAL, seed0=1000):
     return np.array(out)
 
 
-def _check(means, ref, zmax=6.5, cover=0.985):
+def _check(means, ref, family_alpha=1e-3, cover=0.985):
     """Seed-averaged means against a reference: z = (mean_R - ref) / (sd / sqrt(R)) is
     t-distributed with R - 1 degrees of freedom when dSMC is unbiased at this N.  The number
-    of |z| > 3 must stay within a binomial bound of its expectation, no |z| may reach zmax,
-    and single runs must fall within 3 sd of the reference at the normal rate."""
+    of |z| > 3 must stay within a binomial bound of its expectation; no |z| may reach the
+    larger of 6.5 and the t quantile at which any of the n coordinates exceeds it with
+    probability family_alpha (7.5 for R = 24 and n = 8192: with few seeds the t tails are
+    heavy); single runs must fall within 3 sd of the reference at the normal rate."""
     from scipy import stats as _st
     R = means.shape[0]
     sd = means.std(0, ddof=1)
@@ -270,7 +272,8 @@ def _check(means, ref, zmax=6.5, cover=0.985):
     p3 = 2 * _st.t.sf(3.0, R - 1)
     allowed = n * p3 + 4 * np.sqrt(n * p3) + 1
     assert (z > 3).sum() <= allowed, ((z > 3).sum(), allowed)
-    assert z.max() < zmax, z.max()
+    zmax = max(6.5, _st.t.isf(family_alpha / (2 * n), R - 1))
+    assert z.max() < zmax, (z.max(), zmax)
     assert (np.abs(means - ref) <= 3 * sd).mean() >= cover
 
 
