@@ -304,8 +304,9 @@ def run_ours(args):
                 "frac": achieved / ex2_peak if achieved else None,
                 "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
                                f"({src} max clock)",
+                # the CUDA-core variant evaluates the d-term with FMAs: that pipe binds first
                 "fma_bound_frac": (achieved / (FMA_PER_CLK_SM / (d + 2) * SMS * sm_max * 1e-3)
-                                   if achieved else None),
+                                   if achieved and args.compute == "fp32" else None),
                 "avg_launch_ms": rs_ms / max(rs_n, 1), "launches": rs_n,
                 "traffic": (TRAFFIC_PER_LAUNCH.get((args.workload, args.compute)) or {}).get("bytes"),
                 "traffic_unit": "B per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}

@@ -254,8 +254,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
               : "memory");
       };
       // Buffers are refilled as soon as the MMAs that read them complete (their commits):
-      // column block q + kVSlots - 2 is loaded before block q's MMA (into the slot of block
-      // q - 2), and item k + 1's row tile after item k's first MMA (into item k - 1's buffer).
+      // column block q + kVSlots - 2 is loaded after block q's MMA is issued (into the slot of
+      // block q - 2), and item k + 1's row tile after item k's first MMA (into item k - 1's
+      // buffer).
       load_a(blockIdx.x, 0);
       load_a(blockIdx.x + gridDim.x, 1);
       for (int q = 0; q < kVSlots; ++q) load_next();
@@ -269,11 +270,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
         for (int b = 0; b < cur.nblk && ok; ++b, ++q) {
           const int buf = q & 1;
           const int slot = q % kVSlots;
-          if (q >= 2) {
-            ok = mbar_wait(smem_u32(&bar_vfree[(q - 2) % kVSlots]), (uint32_t)((q - 2) / kVSlots) & 1);
-            if (!ok) break;
-            load_next();
-          }
           if (q >= 2) ok = mbar_wait(smem_u32(&bar_epi[buf]), (uint32_t)((q >> 1) - 1) & 1);
           if (ok) ok = mbar_wait(smem_u32(&bar_v[slot]), (uint32_t)(q / kVSlots) & 1);
           if (!ok) break;
@@ -285,10 +281,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
                       p > 0 ? 1u : 0u);
           mma_commit(smem_u32(&bar_mma[buf]));
           mma_commit(smem_u32(&bar_vfree[slot]));
-          ++issued;
           if (b == cur.nblk - 1) {
             mma_commit(smem_u32(&bar_afree[k & 1]));
             last_item = k;
+          }
+          ++issued;
+          if (q >= 2) {  // off the issue path: block q - 2's MMA is long complete
+            ok = mbar_wait(smem_u32(&bar_vfree[(q - 2) % kVSlots]), (uint32_t)((q - 2) / kVSlots) & 1);
+            if (!ok) break;
+            load_next();
           }
           if (b == 0 && k >= 1) {  // item k - 1's MMAs are done: its buffer takes item k + 1
             ok = mbar_wait(smem_u32(&bar_afree[(k - 1) & 1]), (uint32_t)((k - 1) >> 1) & 1);
