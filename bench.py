@@ -43,10 +43,19 @@ SMS = 152
 # DRAM bytes (read + write) per launch of the cross-term / tile-sum kernel, mean over the
 # ten levels of one lgssm_d8 K = N = 1024 smoothing, from one ncu capture of the kernel
 # revision named; None once that kernel has changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = {
-    ("lgssm_d8", "fp32"): {"bytes": 19.91e6, "kernel": "rowsum_kernel<8,4>"},
-    ("lgssm_d8", "tf32"): {"bytes": None, "kernel": "rowsum_tc_kernel<TF32, 2 K planes>, exponent in the MMA"},
-}
+# The epilogue's exp split between MUFU and an FMA-pipe polynomial, with issue slots counted:
+# per 32 pairs MUFU needs 4 cycles of its unit and ~1.6 issue slots; a polynomial exp ~8
+# issue slots per 32.  The balanced split (22 % polynomial) bounds the rate at ~1.28x the
+# MUFU-only peak.
+COMBINED_EXP_FACTOR = 1.28
+
+# ncu DRAM bytes per combination of the dominant kernel in the batched step, from one
+# full-size launch (a 1-pass capture; see profiles/).
+TRAFFIC_PER_COMBINATION = {("batched_lgssm_d4", "bf16"): {"bytes": 62540, "kernel": "rowsum_tc_kernel<BF16, 1 K plane>"}}
+
+# ncu DRAM bytes per launch of the single-sequence workloads' dominant kernel (none current:
+# the kernels changed since the last capture).
+TRAFFIC_PER_LAUNCH = {}
 
 WORKLOADS = {
     "batched_lgssm_d4": dict(kind="batch", n_seq=256, N=512, resampler="dense"),
@@ -55,7 +64,11 @@ WORKLOADS = {
     "lgssm_d8": dict(K=1024, N=1024, resampler="dense"),
     "lgssm_1d": dict(K=32, N=64, resampler="dense"),
     "sv": dict(K=4096, N=4096, resampler="dense"),
-    "sv_rs": dict(K=4096, N=16384, resampler="rs"),
+    # Algorithm 8 at N = 16384.  One-dimensional states: the bound uses the hull of the
+    # transition means, so a particle far in the proposal's upper tail does not set it; a
+    # genuinely dominant pair (two low-tail particles with a near-zero observation) still
+    # leaves some combinations accepting ~1e-6 of their uniform proposals, hence the cap
+    "sv_rs": dict(K=4096, N=16384, resampler="rs", rs_max_attempts=1 << 26, steps=3),
     "lgssm_d4": dict(K=512, N=512, resampler="dense"),
 }
 
@@ -216,7 +229,8 @@ def run_ours(args):
     K, N = wl.K, wl.N
     resampler = dsmc.RS if spec["resampler"] == "rs" else dsmc.MULTINOMIAL
     compute = {"fp32": dsmc.FP32, "tf32": dsmc.TF32, "bf16": dsmc.BF16}[args.compute]
-    sm = dsmc.Smoother(wl.model, K, N, seed=1000 + 7919 * rank, resampler=resampler, compute=compute)
+    sm = dsmc.Smoother(wl.model, K, N, seed=1000 + 7919 * rank, resampler=resampler, compute=compute,
+                       rs_max_attempts=spec.get("rs_max_attempts", 0))
     y = torch.as_tensor(wl.y, dtype=torch.float32, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
     stream = torch.cuda.current_stream()
@@ -304,6 +318,8 @@ def run_ours(args):
                 "frac": achieved / ex2_peak if achieved else None,
                 "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
                                f"({src} max clock)",
+                "combined_peak": ex2_peak * COMBINED_EXP_FACTOR,
+                "frac_combined": achieved / (ex2_peak * COMBINED_EXP_FACTOR) if achieved else None,
                 # the CUDA-core variant evaluates the d-term with FMAs: that pipe binds first
                 "fma_bound_frac": (achieved / (FMA_PER_CLK_SM / (d + 2) * SMS * sm_max * 1e-3)
                                    if achieved and args.compute == "fp32" else None),
@@ -366,7 +382,10 @@ def run_batched(args):
     compute = {"fp32": dsmc.FP32, "tf32": dsmc.TF32, "bf16": dsmc.BF16}[args.compute]
     seeds = [1000 + 7919 * rank + i for i in range(len(Ks))]
     from paper_2202_02264_gb300 import autotune
-    if args.no_autotune:
+    if args.schedule:
+        fm, mc = (int(v) for v in args.schedule.split(","))
+        tuned = {"fused_max_merges": fm, "max_merges_per_launch": mc, "timings": {}}
+    elif args.no_autotune:
         tuned = {"fused_max_merges": 0, "max_merges_per_launch": 0, "timings": {}}
     else:
         tuned = autotune.tune_batch(model, Ks, N, bw.ys, compute, use_cache=False)   # untimed
@@ -450,7 +469,47 @@ def run_batched(args):
     breakdown = dsmc.dsmc_profile_breakdown_read()
     dsmc.dsmc_profile_breakdown_enable(False)
 
-    # the plain form: FP32, each sequence smoothed alone, one call after another
+    # the plain form (FP32, each sequence alone) and the accuracy of both forms
+    plain_value, t_plain, accuracy = None, None, None
+    if not args.no_compare:
+        plain_value, t_plain, accuracy = _plain_and_accuracy(model, Ks, N, seeds, ys, bw, mixed_means, units, stream)
+    roofline = _batch_roofline(args, rs_pairs, rs_ms, rs_n, N)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "tf32": "tf32+f32", "bf16": "bf16+f32"}[args.compute],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_seq": len(Ks), "sum_K": sum(Ks), "K_range": [min(Ks), max(Ks)],
+                       "N": N, "dx": d, "resampler": "dense",
+                       "compute": f"{args.compute} cross term (fp32 accumulate / exp), batched: one launch "
+                                  "per level for all sequences",
+                       "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": f"replicas x{world}",
+                       "autotuned": {"fused_max_merges": tuned["fused_max_merges"],
+                                     "max_merges_per_launch": tuned["max_merges_per_launch"],
+                                     "candidates_ms": tuned["timings"]}},
+            "plain_fp32_per_request": ({"value": plain_value, "unit": UNIT,
+                                        "ms_per_batch": 1e3 * t_plain,
+                                        "form": "FP32, each sequence smoothed alone (dsmc_smooth), in order"}
+                                       if plain_value else None),
+            "mixed_over_plain": value / world / plain_value if plain_value else None,
+            "breakdown_ms_per_step": breakdown,
+            "accuracy": accuracy,
+            "roofline": roofline, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+            "step_ms": {"median": float(np.median(per_step)), "p99": float(np.percentile(per_step, 99))}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        wl = W.Workload("batched_lgssm_d4_seq0", model, Ks[0], N, bw.ys[0], None)
+        line["cpu_baseline"] = oracle_sample(wl)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _plain_and_accuracy(model, Ks, N, seeds, ys, bw, mixed_means, units, stream):
+    """The plain form (FP32, each sequence smoothed alone with dsmc_smooth, one call after
+    another) timed on the device, and the smoothing-mean RMSE of both forms against
+    Kalman/RTS on the first 32 sequences."""
     Kmax = max(Ks)
     single = dsmc.Smoother(model, Kmax, N, seed=seeds[0], compute=dsmc.FP32)
     plain_means = []
@@ -476,7 +535,12 @@ def run_batched(args):
                 "plain_fp32": float(r_plain.mean()), "plain_fp32_se": float(r_plain.std(ddof=1) / np.sqrt(32)),
                 "difference": float(diff.mean()), "difference_se": float(diff.std(ddof=1) / np.sqrt(32))}
     accuracy["equal_within_2se"] = bool(abs(accuracy["difference"]) <= 2 * accuracy["difference_se"])
+    return plain_value, t_plain, accuracy
 
+
+def _batch_roofline(args, rs_pairs, rs_ms, rs_n, N):
+    """Roofline of the dominant kernel (the fused exp / tile-sum pass) of the batched step:
+    algorithmic work = pair exponentials per launch, over its mean event-timed duration."""
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     ex2_peak = MUFU_EX2_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9
@@ -484,42 +548,20 @@ def run_batched(args):
     kname = {"fp32": "rowsum_kernel (fused exp / tile sums)",
              "tf32": "rowsum_tc_kernel (tcgen05 cross term, fused exp / tile sums)",
              "bf16": "rowsum_tc_kernel (tcgen05 cross term, fused exp / tile sums)"}[args.compute]
+    per_comb = TRAFFIC_PER_COMBINATION.get((args.workload, args.compute))
+    combs_per_launch = rs_pairs / (N * N) / max(rs_n, 1)
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": ex2_peak, "unit": "Gexp/s",
                 "frac": achieved / ex2_peak if achieved else None,
                 "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
                                f"({src} max clock)",
+                "combined_peak": ex2_peak * COMBINED_EXP_FACTOR,
+                "frac_combined": achieved / (ex2_peak * COMBINED_EXP_FACTOR) if achieved else None,
                 "avg_launch_ms": rs_ms / max(rs_n, 1), "launches": rs_n,
-                "traffic": (TRAFFIC_PER_LAUNCH.get((args.workload, args.compute)) or {}).get("bytes"),
-                "traffic_unit": "B per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "tf32": "tf32+f32", "bf16": "bf16+f32"}[args.compute],
-            "data": "synthetic",
-            "config": {"workload": args.workload, "n_seq": len(Ks), "sum_K": sum(Ks), "K_range": [min(Ks), max(Ks)],
-                       "N": N, "dx": d, "resampler": "dense",
-                       "compute": f"{args.compute} cross term (fp32 accumulate / exp), batched: one launch "
-                                  "per level for all sequences",
-                       "l2": "flushed between timed steps (512 MiB write)",
-                       "parallelism": f"replicas x{world}",
-                       "autotuned": {"fused_max_merges": tuned["fused_max_merges"],
-                                     "max_merges_per_launch": tuned["max_merges_per_launch"],
-                                     "candidates_ms": tuned["timings"]}},
-            "plain_fp32_per_request": {"value": plain_value, "unit": UNIT,
-                                       "ms_per_batch": 1e3 * t_plain,
-                                       "form": "FP32, each sequence smoothed alone (dsmc_smooth), in order"},
-            "mixed_over_plain": value / world / plain_value,
-            "breakdown_ms_per_step": breakdown,
-            "accuracy": accuracy,
-            "roofline": roofline, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "step_ms": {"median": float(np.median(per_step)), "p99": float(np.percentile(per_step, 99))}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        wl = W.Workload("batched_lgssm_d4_seq0", model, Ks[0], N, bw.ys[0], None)
-        line["cpu_baseline"] = oracle_sample(wl)
-    if rank == 0:
-        print(json.dumps(line))
-    if world > 1:
-        torch.distributed.destroy_process_group()
+                "combinations_per_launch": combs_per_launch,
+                "traffic": per_comb["bytes"] * combs_per_launch if per_comb else None,
+                "traffic_unit": "B per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum per "
+                                "combination, times combinations per launch)"}
+    return roofline
 
 
 def run_serving(args):
@@ -637,7 +679,8 @@ def run_pg(args):
         xa, xb = xb, xa
 
     for s in range(args.warmup):
-        sweep(s, False)
+        sweep(s, True)   # also loads the counting ops' kernels before the timed region
+    changed.zero_()
     torch.cuda.synchronize()
     if sm.status() != 0:
         raise RuntimeError(f"device status {sm.status()} after warm-up")
@@ -657,6 +700,12 @@ def run_pg(args):
         raise RuntimeError(f"device status {sm.status()} after the sweeps")
     t = e0.elapsed_time(e1) / 1e3
     rate = changed.cpu().numpy() / sweeps
+    # device time per launch kind of one more (untimed) sweep
+    dsmc.dsmc_profile_breakdown_enable(True)
+    sweep(args.warmup + sweeps, False)
+    torch.cuda.synchronize()
+    breakdown = dsmc.dsmc_profile_breakdown_read()
+    dsmc.dsmc_profile_breakdown_enable(False)
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     ex2_peak = MUFU_EX2_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9
@@ -676,7 +725,7 @@ def run_pg(args):
                          "peak": ex2_peak, "unit": "Gexp/s", "frac": achieved / ex2_peak if achieved else None,
                          "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
                                         f"({src} max clock)", "launches": rs_n, "traffic": None},
-            "clocks": clk, "gpu_launches": launches}
+            "clocks": clk, "gpu_launches": launches, "breakdown_ms_per_sweep": breakdown}
     if rank == 0:
         print(json.dumps(line))
 
@@ -693,13 +742,17 @@ def main():
                     help="cross-term precision (default: bf16 for the batched workload, tf32 otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: default launch schedule")
+    ap.add_argument("--schedule", default=None,
+                    help="batched workload: fixed 'fused_max_merges,max_merges_per_launch' instead of the autotuner")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="batched workload: skip the plain-FP32 comparison and accuracy legs (profiling runs)")
     ap.add_argument("--n-seq", type=int, default=None, help="batched workload: fewer sequences (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     kind = WORKLOADS[args.workload].get("kind", "single")
     if args.steps is None and kind != "pg":
-        args.steps = {"batch": 10, "serving": 1}.get(kind, 400)
+        args.steps = WORKLOADS[args.workload].get("steps", {"batch": 10, "serving": 1}.get(kind, 400))
     if args.compute is None:
         args.compute = {"batch": "bf16", "pg": "fp32"}.get(kind, "tf32")
     if args.impl == "reference":

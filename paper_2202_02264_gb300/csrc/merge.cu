@@ -191,9 +191,43 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
 
   __shared__ float gsum[kMaxColumnGroups * D];
   __shared__ float red_s[NW];
+  __shared__ float red2_s[NW];
   __shared__ float mu_s[D];
   __shared__ float bstar_s;
   if (staged) __syncthreads();
+
+  // One-dimensional states, lazy sampler: the hull [m_lo, m_hi] of the transition means
+  // m_i = A x_i + c over the whole time-(c - 1) slice (a superset of the left block's end
+  // states) bounds every pair: f(x_j | x_i) <= f_max exp(-dist_j^2 Q^-1 / 2) with dist_j
+  // the distance from x_j to the hull, so log omega-bar = log f_max + max_i a_i +
+  // max_j (b'_j - dist_j^2 Q^-1 / 2) is a valid bound of the combination's pair weights
+  // (Algorithm 8 needs any bound; a particle far outside the hull otherwise sets it).
+  const bool hull = (D == 1) && a.resampler == DSMC_RS;
+  float m_lo = 0.f, m_hi = 0.f, bhull = -INFINITY;
+  if (hull) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (int i = threadIdx.x; i < N; i += kProThreads) {
+      const float m = fmaf(mp.A[0], Xl[i], mp.c[0]);
+      lo = fminf(lo, m);
+      hi = fmaxf(hi, m);
+    }
+    lo = -warp_max(-lo);
+    hi = warp_max(hi);
+    if (lane == 0) {
+      red_s[warp] = lo;
+      red2_s[warp] = hi;
+    }
+    __syncthreads();
+    lo = red_s[0];
+    hi = red2_s[0];
+    for (int w = 1; w < NW; ++w) {
+      lo = fminf(lo, red_s[w]);
+      hi = fmaxf(hi, red2_s[w]);
+    }
+    m_lo = lo;
+    m_hi = hi;
+    __syncthreads();  // red_s is reused by the column pass
+  }
 
   // pass 1: right block at time c (column states, b'_j; the mean mu and B*)
   bool bad = false, corrupt = false;
@@ -211,6 +245,10 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
     float v[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) v[k] = Vs[(size_t)j * D + k];
+    if (hull) {  // v is still x_j here
+      const float dist = fmaxf(0.f, fmaxf(v[0] - m_hi, m_lo - v[0]));
+      bhull = fmaxf(bhull, Bs[j] - 0.5f * mp.Qi[0] * dist * dist);
+    }
     const float bj = column_beta<D>(mp, v, mu, Bs[j], bstar);
     beta[j] = bj;
 #pragma unroll
@@ -261,13 +299,20 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
     amax = fmaxf(amax, ai);
   }
   amax = warp_max(amax);
+  bhull = warp_max(bhull);
   __syncthreads();
-  if (lane == 0) red_s[warp] = amax;
+  if (lane == 0) {
+    red_s[warp] = amax;
+    red2_s[warp] = bhull;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float t = red_s[0];
-    for (int w = 1; w < NW; ++w) t = fmaxf(t, red_s[w]);
-    a.ws.logbar[s] = (double)mp.log_f_max + (double)t + (double)bstar;
+    float t = red_s[0], bh = red2_s[0];
+    for (int w = 1; w < NW; ++w) {
+      t = fmaxf(t, red_s[w]);
+      bh = fmaxf(bh, red2_s[w]);
+    }
+    a.ws.logbar[s] = (double)mp.log_f_max + (double)t + (double)(hull ? bh : bstar);
   }
   if (corrupt) record_status(a.ws.status, DSMC_ERR_INVALID_ARG);
   if (bad) record_status(a.ws.status, DSMC_ERR_NONFINITE);
