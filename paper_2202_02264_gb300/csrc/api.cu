@@ -159,7 +159,9 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p, int
   p.L = 0;
   while ((1 << p.L) < p.K) ++p.L;
   p.dense = cfg->resampler != DSMC_RS;
-  p.compute = cfg->compute;
+  // the cross-term precision only matters to the dense N x N pass; the lazy sampler
+  // evaluates its proposed pairs in FP32 and needs no tensor-core operands
+  p.compute = p.dense ? cfg->compute : DSMC_FP32;
   p.Nr = (p.N + 127) / 128 * 128;
   {
     const int kp = p.compute == DSMC_BF16 ? 16 : 8;
@@ -432,7 +434,7 @@ MergeArgs merge_args(const Plan& p, const dsmc_config_t* cfg, const float* y, in
   a.conditional = conditional;
   a.root = (level == p.L - 1);
   a.resampler = cfg->resampler;
-  a.compute = cfg->compute;
+  a.compute = p.compute;
   a.Nr = p.Nr;
   a.mma_planes = p.planes;
   a.seed = cfg->seed;

@@ -438,6 +438,58 @@ __device__ __forceinline__ int pick_mem(const float* x, int n, uint32_t w, int r
   return min(idx, n - 1);
 }
 
+// The tile stage over 32 < nT <= 64 tiles of a row in memory (16-byte aligned, nTp >= nT
+// floats, entries past nT ignored): the largest tile is the reference; both halves' image
+// sums, then the chosen half once more (the same index as one pass over all tiles).
+__device__ __forceinline__ int pick_tile64(const float* Ti, int nT, uint32_t w) {
+  const float4* T4 = reinterpret_cast<const float4*>(Ti);
+  auto at = [&](const float4& v, int k, int c) {  // element c of the float4 at tile 4k
+    const float x = c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+    return 4 * k + c < nT ? x : 0.f;
+  };
+  float tmax = 0.f;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    if (4 * k < nT) {
+      const float4 v = T4[k];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tmax = fmaxf(tmax, at(v, k, c));
+    }
+  }
+  const int be = ref_exponent(tmax);
+  unsigned long long Q1 = 0, Q2 = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    if (4 * k < nT) {
+      const float4 v = T4[k];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint32_t q = q24(at(v, k, c), be);
+        if (k < 8) Q1 += q; else Q2 += q;
+      }
+    }
+  }
+  const unsigned long long Q = Q1 + Q2;
+  if (Q == 0ull) return 0;
+  const unsigned long long T = __umul64hi((unsigned long long)w << 32, Q);
+  const bool second = T >= Q1;
+  const int k0 = second ? 8 : 0;
+  unsigned long long c = second ? Q1 : 0ull;
+  int cnt = second ? 32 : 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (4 * (k0 + k) < nT) {
+      const float4 v = T4[k0 + k];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        c += q24(at(v, k0 + k, e), be);
+        cnt += (4 * (k0 + k) + e < nT && c <= T) ? 1 : 0;
+      }
+    }
+  }
+  return min(cnt, nT - 1);
+}
+
 // Slot n's pair (i, j) of combination gid, one thread:
 //   row:    binary search of T = U64 * S >> 64 in the exact prefix sums;
 //   tile:   pick over the row's tile weights (reference: the largest), word w2;
@@ -469,6 +521,8 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
     kt = pick_tile<16>(Ti, nT, w.z);
   } else if (nT <= 32) {
     kt = pick_tile<32>(Ti, nT, w.z);
+  } else if (nT <= 64) {
+    kt = pick_tile64(Ti, nT, w.z);
   } else {
     float tmax = 0.f;
     for (int k = 0; k < nT; ++k) tmax = fmaxf(tmax, Ti[k]);
@@ -502,6 +556,45 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
       e[q] = (q < ncol) ? ex2(pair_exponent<D>(u, al, v, beta[bidx<PAD>(jj)])) : 0.f;
     }
     j = jb + pick32(e, ncol, w.w, tbe);
+  } else if (ncol <= 64) {
+    // two halves of 32 columns: both image sums, then the chosen half once more.  This is
+    // the index of one pass over all columns: every prefix sum of the other half lies on
+    // the far side of T (the first half's are <= Q1 <= T, the second's >= Q1 > T).
+    const int n2 = ncol - 32;
+    unsigned long long Q1 = 0, Q2 = 0;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      float v[D];
+      load_row<D>(V + vidx<D, PAD>(jb + q), v);
+      Q1 += q24(ex2(pair_exponent<D>(u, al, v, beta[bidx<PAD>(jb + q)])), tbe);
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int jj = jb + 32 + min(q, n2 - 1);
+      float v[D];
+      load_row<D>(V + vidx<D, PAD>(jj), v);
+      const float x = ex2(pair_exponent<D>(u, al, v, beta[bidx<PAD>(jj)]));
+      Q2 += (q < n2) ? q24(x, tbe) : 0u;
+    }
+    const unsigned long long Qc = Q1 + Q2;
+    j = jb;
+    if (Qc != 0ull) {
+      const unsigned long long Tc = __umul64hi((unsigned long long)w.w << 32, Qc);
+      const bool second = Tc >= Q1;
+      const int h0 = second ? jb + 32 : jb, hn = second ? n2 : 32;
+      unsigned long long cc = second ? Q1 : 0ull;
+      int cnt = second ? 32 : 0;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int jj = h0 + min(q, hn - 1);
+        float v[D];
+        load_row<D>(V + vidx<D, PAD>(jj), v);
+        const float x = ex2(pair_exponent<D>(u, al, v, beta[bidx<PAD>(jj)]));
+        cc += (q < hn) ? q24(x, tbe) : 0u;
+        cnt += (q < hn && cc <= Tc) ? 1 : 0;
+      }
+      j = jb + min(cnt, ncol - 1);
+    }
   } else {
     unsigned long long Qc = 0;
     for (int jj = jb; jj < jb + ncol; ++jj)
