@@ -232,7 +232,8 @@ def run_ours(args):
         args.compute = "fp32"   # the lazy sampler evaluates its proposed pairs in FP32
     compute = {"fp32": dsmc.FP32, "tf32": dsmc.TF32, "bf16": dsmc.BF16}[args.compute]
     sm = dsmc.Smoother(wl.model, K, N, seed=1000 + 7919 * rank, resampler=resampler, compute=compute,
-                       rs_max_attempts=spec.get("rs_max_attempts", 0))
+                       rs_max_attempts=spec.get("rs_max_attempts", 0),
+                       fused_max_merges=args.fused_max_merges or 0)
     y = torch.as_tensor(wl.y, dtype=torch.float32, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 126 MB L2
     stream = torch.cuda.current_stream()
@@ -749,6 +750,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: default launch schedule")
     ap.add_argument("--schedule", default=None,
                     help="batched workload: fixed 'fused_max_merges,max_merges_per_launch' instead of the autotuner")
+    ap.add_argument("--fused-max-merges", type=int, default=None,
+                    help="single-sequence workloads: levels with at most this many combinations run "
+                         "fused (-1: never; default: the library's)")
     ap.add_argument("--no-compare", action="store_true",
                     help="batched workload: skip the plain-FP32 comparison and accuracy legs (profiling runs)")
     ap.add_argument("--n-seq", type=int, default=None, help="batched workload: fewer sequences (profiling)")

@@ -85,9 +85,15 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
       }
     }
     float* xo = X + ((size_t)t * N + n) * d;
+    if ((D % 4) == 0 && d == D) {  // 16-byte vector stores (rows of D floats)
 #pragma unroll
-    for (int k = 0; k < D; ++k)
-      if (k < d) xo[k] = x[k];
+      for (int k4 = 0; k4 < D / 4; ++k4)
+        reinterpret_cast<float4*>(xo)[k4] = make_float4(x[4 * k4], x[4 * k4 + 1], x[4 * k4 + 2], x[4 * k4 + 3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+        if (k < d) xo[k] = x[k];
+    }
     float lq = 0.f;
 #pragma unroll
     for (int k = 0; k < D; ++k)
