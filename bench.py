@@ -516,6 +516,9 @@ def _plain_and_accuracy(model, Ks, N, seeds, ys, bw, mixed_means, units, stream)
     """The plain form (FP32, each sequence smoothed alone with dsmc_smooth, one call after
     another) timed on the device, and the smoothing-mean RMSE of both forms against
     Kalman/RTS on the first 32 sequences."""
+    import torch
+
+    from paper_2202_02264_gb300 import dsmc
     Kmax = max(Ks)
     single = dsmc.Smoother(model, Kmax, N, seed=seeds[0], compute=dsmc.FP32)
     plain_means = []

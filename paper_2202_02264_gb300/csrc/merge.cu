@@ -599,13 +599,14 @@ __global__ void __launch_bounds__(kSlotThreads) slots_kernel(MergeArgs a) {
 // the row totals, the row CDF and the increment are computed as in rowcdf_kernel, then
 // every slot is drawn (one thread per slot) against the shared-memory copies.
 // ---------------------------------------------------------------------------------------
-constexpr int kCdfSlotThreads = 512;
+constexpr int kCdfSlotThreads = 256;
 
-// Shared memory: padded v [vpad_floats], u [N][D], padded beta, l [N], prefix sums [N].
-// Shared-memory layout of the row CDF + draws kernel.  The tile sums T are staged too (row
+// Shared-memory layout of the row CDF + draws kernel: padded v [vpad_floats], u [N][D],
+// padded beta, l [N], prefix sums [N].  The tile sums T are staged too (row
 // stride nTs = nTp, plus 4 when nTp / 4 is even, so that the rows of 8 consecutive threads
-// fall in distinct 16-byte bank groups) when the whole fits kCdfStageMax (two CTAs per SM).
-constexpr size_t kCdfStageMax = 100 * 1024;
+// fall in distinct 16-byte bank groups) when the whole fits kCdfStageMax (four CTAs of 256
+// threads per SM: more combinations in flight beat staging T at larger N).
+constexpr size_t kCdfStageMax = 56 * 1024;
 struct CdfSlotsSmem {
   size_t v, u, b, l, c, t, total;
   int nTs;  // staged row stride of T, 0 when T stays in global memory
@@ -639,7 +640,7 @@ __host__ __device__ __forceinline__ CdfSlotsSmem cdf_slots_smem(int N, int nTp) 
 }
 
 template <int D>
-__global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 2 : 1) cdf_slots_kernel(MergeArgs a) {
+__global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_kernel(MergeArgs a) {
   constexpr int NT = kCdfSlotThreads;
   constexpr int NW = NT / 32;
   const int s = blockIdx.x;
