@@ -124,7 +124,7 @@ __host__ __device__ constexpr bool prologue_staged(int N, int d) {
 
 template <int D>
 __host__ __device__ constexpr int prologue_min_blocks() {
-  return D <= 4 ? 4 : 0;   // 0: no minimum (larger D would spill)
+  return D <= 4 ? 6 : 0;   // 0: no minimum (larger D would spill)
 }
 
 template <int D>
