@@ -167,9 +167,13 @@ def run_reference(args):
         return
     from paper_2202_02264_gb300 import workloads as W
     spec = WORKLOADS[args.workload]
+    config = None
     if spec.get("kind") == "batch":   # the oracle on the batch's first sequence
-        bw = W.batch_workload(spec["n_seq"], spec["N"])
+        bw = W.batch_workload(args.n_seq or spec["n_seq"], spec["N"])
         wl = W.Workload(args.workload, bw.model, int(bw.Ks[0]), bw.N, bw.ys[0], None)
+        Ks = [int(k) for k in bw.Ks]
+        config = {"workload": args.workload, "n_seq": len(Ks), "sum_K": sum(Ks), "K_range": [min(Ks), max(Ks)],
+                  "N": bw.N, "dx": bw.model.d, "resampler": "dense"}
     elif spec.get("kind") == "serving":   # the oracle on the stream's first request
         from paper_2202_02264_gb300 import serving as S
         r0 = S.request_stream(1, spec["rate"])[0]
@@ -201,8 +205,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "K": wl.K, "N": wl.N, "dx": wl.model.d,
-                       "sample_K": Kp},
+            "config": dict(config or {"workload": args.workload, "K": wl.K, "N": wl.N, "dx": wl.model.d},
+                           sample_K=Kp),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"each step: a whole smoothing of the first {Kp} of {wl.K} "
                                        f"steps, N={wl.N}, FP64"},
