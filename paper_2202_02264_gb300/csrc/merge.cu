@@ -608,7 +608,7 @@ constexpr int kCdfSlotThreads = 256;
 // threads per SM: more combinations in flight beat staging T at larger N).
 constexpr size_t kCdfStageMax = 56 * 1024;
 struct CdfSlotsSmem {
-  size_t v, u, b, l, c, t, total;
+  size_t v, u, b, l, c, ad, t, total;
   int nTs;  // staged row stride of T, 0 when T stays in global memory
 };
 
@@ -626,6 +626,7 @@ __host__ __device__ __forceinline__ CdfSlotsSmem cdf_slots_smem(int N, int nTp) 
   f.b = o; o = r16(o + (size_t)bpad_floats(N) * 4);
   f.l = o; o = r16(o + (size_t)N * 4);
   f.c = o; o = r16(o + (size_t)N * 8);
+  f.ad = o; o = r16(o + (size_t)N * 8);   // alpha_i and delta_i (row offsets of the draws)
   f.t = o;
   const int nTs = staged_tile_stride(nTp);
   const size_t with_t = r16(o + (size_t)N * nTs * 4);
@@ -656,6 +657,8 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
   float* sB = reinterpret_cast<float*>(smraw + L.b);
   float* sL = reinterpret_cast<float*>(smraw + L.l);
   unsigned long long* sC = reinterpret_cast<unsigned long long*>(smraw + L.c);
+  float* sAl = reinterpret_cast<float*>(smraw + L.ad);
+  float* sDl = sAl + N;
   int* under = reinterpret_cast<int*>(sC);
   __shared__ unsigned long long warp_tot[NW];
   __shared__ float redf[NW];
@@ -690,7 +693,10 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
       sU[q] = U[q];
     }
   }
-  for (int q = threadIdx.x; q < N; q += NT) sB[bidx<true>(q)] = beta[q];
+  for (int q = threadIdx.x; q < N; q += NT) {
+    sB[bidx<true>(q)] = beta[q];
+    sAl[q] = alpha[q];
+  }
   // row totals (and the staged copy of the tile sums)
   for (int i = threadIdx.x; i < N; i += NT) {
     if (sT) {
@@ -705,13 +711,14 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
     }
     sL[i] = t;
     delta[i] = 0.f;
+    sDl[i] = 0.f;
     if (t < 0x1p-64f) under[atomicAdd(&n_under, 1)] = i;
   }
   __syncthreads();
   for (int q = warp; q < n_under; q += NW) {
     const int i = under[q];
     float si, dl;
-    recompute_row<D, true>(sU + (size_t)i * D, alpha[i], sV, sB, N, a.B, nT, Tt + (size_t)i * nTp, &si, &dl);
+    recompute_row<D, true>(sU + (size_t)i * D, sAl[i], sV, sB, N, a.B, nT, Tt + (size_t)i * nTp, &si, &dl);
     __syncwarp();
     if (sT) {  // the rewritten row into the staged copy
       for (int k = lane; k < nT; k += 32) sT[(size_t)i * L.nTs + k] = Tt[(size_t)i * nTp + k];
@@ -721,6 +728,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
       si = row_total(Tt + (size_t)i * nTp, nT, nTp);
       sL[i] = isnan(si) ? 0.f : si;
       delta[i] = dl;
+      sDl[i] = dl;
     }
   }
   __syncthreads();
@@ -729,7 +737,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
   for (int i = threadIdx.x; i < N; i += NT) {
     const float t = sL[i];
     rowsum[i] = t;
-    const float v = row_log2_weight(shift[i], delta[i], t);
+    const float v = row_log2_weight(shift[i], sDl[i], t);
     sL[i] = v;
     mloc = fmaxf(mloc, v);
   }
@@ -767,8 +775,8 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
   in.cum = sC;
   in.T = sT ? sT : Tt;
   in.U = sU;
-  in.alpha = alpha;
-  in.delta = delta;
+  in.alpha = sAl;
+  in.delta = sDl;
   in.V = sV;
   in.beta = sB;
   in.N = N;
