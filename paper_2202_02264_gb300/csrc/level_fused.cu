@@ -15,8 +15,10 @@
 //   - the row log-weights l_i are exchanged through distributed shared memory (one cluster
 //     barrier), after which every CTA builds the same row CDF;
 //   - CTA r draws slots [r S, (r+1) S) of the combination, S = ceil(slots / C).
-// The arithmetic is the split path's, function for function (merge_parts.cuh), with the
-// same reduction orders for 512-thread blocks, so both paths give the same bits.
+// The arithmetic is the split path's, function for function (merge_parts.cuh), and every
+// reduction is either exact (maxima, the u64 prefix sums) or in an order that does not
+// depend on the block size (the column mean, the per-row tile sums), so both paths give
+// the same bits.
 #include <cooperative_groups.h>
 
 #include "kernels.cuh"

@@ -594,15 +594,17 @@ __global__ void __launch_bounds__(kSlotThreads) slots_kernel(MergeArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Row CDF and pair draws of one combination in one CTA (when its operands fit shared
-// memory): the column terms v_j, beta_j and the row terms u_i are staged in shared memory,
-// the row totals, the row CDF and the increment are computed as in rowcdf_kernel, then
-// every slot is drawn (one thread per slot) against the shared-memory copies.
+// Row CDF and pair draws of one combination in one 256-thread CTA (when its operands fit
+// shared memory; four CTAs per SM for d <= 8): the column terms v_j, beta_j, the row terms
+// u_i, alpha_i and the row shifts delta_i are staged in shared memory, the row totals, the
+// row CDF and the increment are computed as in rowcdf_kernel, then every slot is drawn
+// (one thread per slot, N / 256 slots each) against the shared-memory copies.
 // ---------------------------------------------------------------------------------------
 constexpr int kCdfSlotThreads = 256;
 
 // Shared-memory layout of the row CDF + draws kernel: padded v [vpad_floats], u [N][D],
-// padded beta, l [N], prefix sums [N].  The tile sums T are staged too (row
+// padded beta, l [N], prefix sums [N], alpha and delta [2][N].  The tile sums T are staged
+// too (row
 // stride nTs = nTp, plus 4 when nTp / 4 is even, so that the rows of 8 consecutive threads
 // fall in distinct 16-byte bank groups) when the whole fits kCdfStageMax (four CTAs of 256
 // threads per SM: more combinations in flight beat staging T at larger N).
