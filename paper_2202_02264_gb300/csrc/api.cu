@@ -124,7 +124,7 @@ struct Plan {
   int R, rows_per_cta;
   bool dense;
   int level_off[33];
-  size_t o_status, o_U, o_alpha, o_V, o_beta, o_shift, o_logbar, o_inc, o_T, o_rw, o_rowsum, o_cum,
+  size_t o_status, o_U, o_alpha, o_V, o_beta, o_shift, o_logbar, o_inc, o_T, o_rw, o_rowsum, o_rowpart, o_cum,
       o_delta, o_first, o_last, o_star, o_Ub, o_Vb, total;
 };
 
@@ -208,6 +208,7 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p, int
   p.o_last = take(no_maps ? 0 : 2 * (size_t)p.K * p.N * sizeof(int32_t));
   p.o_star = take(2 * sizeof(int32_t));
   const bool tc = p.compute != DSMC_FP32;
+  p.o_rowpart = take(tc ? 2 * MN * sizeof(float) : 0);
   p.o_Ub = take(tc ? (size_t)p.Mc * p.planes * p.Nr * 32 : 0);
   p.o_Vb = take(tc ? (size_t)p.Mc * p.planes * p.Nr * 32 : 0);
   p.total = o;
@@ -227,6 +228,7 @@ WsPtrs ws_ptrs(const Plan& p, void* ws) {
   w.T = reinterpret_cast<float*>(b + p.o_T);
   w.rw = reinterpret_cast<float*>(b + p.o_rw);
   w.rowsum = reinterpret_cast<float*>(b + p.o_rowsum);
+  w.rowpart = reinterpret_cast<float*>(b + p.o_rowpart);
   w.cum = reinterpret_cast<unsigned long long*>(b + p.o_cum);
   w.delta = reinterpret_cast<float*>(b + p.o_delta);
   w.first = reinterpret_cast<int32_t*>(b + p.o_first);

@@ -21,6 +21,8 @@ struct WsPtrs {
   float* T;          // [Mc][N][nTp] tile weights, relative to the row shift
   float* rw;         // [Mc][N]      row weights of the row stage
   float* rowsum;     // [Mc][N]      row totals (sums of the tile weights)
+  float* rowpart;    // [Mc][2][N]   tensor-core path, one column chunk: each epilogue half's
+                     //              running sum of its tile weights (the row total is their sum)
   unsigned long long* cum;  // [Mc][N] exact 2^40 fixed-point prefix sums of the row weights
   float* delta;      // [Mc][N]      extra base-2 shift of rows recomputed after underflow
   int32_t* first;    // [2][K][N]    first-time particle index of each block (double-buffered)

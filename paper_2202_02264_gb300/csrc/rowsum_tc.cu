@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
       const int s = cur.s;
       const int row = cur.rt * kTcRows + 32 * g + lane;
       float* Trow = a.ws.T + ((size_t)s * N + (row < N ? row : 0)) * a.nTp;
+      float racc = 0.f;  // this half's tile weights of the row, blocks in order
       bool stop = false;
       for (int b = 0; b < cur.nblk; ++b, ++q) {
         const int buf = q & 1;
@@ -352,6 +353,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
           t0 = exp_sum32<true>(acc0, cur.j1 - col0);
           t1 = exp_sum32<true>(acc1, cur.j1 - col0 - 32);
         }
+        racc = __fadd_rn(racc, __fadd_rn(t0, t1));
         if (row < N) {
           if (B == 32) {
             if (col0 < cur.j1) Trow[col0 / 32] = t0;
@@ -362,6 +364,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
         }
       }
       if (stop) break;
+      // one column chunk: the item covers the whole row, so its two halves' sums are the
+      // row total's two parts (the row-CDF kernel adds them instead of re-reading T)
+      if (a.CH == 1 && row < N) a.ws.rowpart[((size_t)s * 2 + h) * N + row] = racc;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
