@@ -97,8 +97,15 @@ typedef struct {
                                  DSMC_TF32 (dx <= 16) or DSMC_BF16 (any dx) on the tensor
                                  cores: the whole base-2 exponent alpha_i + beta_j + u_i.v_j
                                  is one MMA, alpha and beta entering as two-term splits in
-                                 the MMA type; FP32 accumulate, exp and sums; dense N <= 4096 */
-  int resampler;              /* DSMC_MULTINOMIAL (dense, Algorithm 1) or DSMC_RS (Alg. 8) */
+                                 the MMA type; FP32 accumulate, exp and sums; dense N <= 4096.
+                                 Ignored by DSMC_RS, which evaluates its proposed pairs in FP32 */
+  int resampler;              /* DSMC_MULTINOMIAL (dense, Algorithm 1) or DSMC_RS (Alg. 8:
+                                 uniform pair proposals accepted with probability
+                                 omega_ij / omega-bar, omega-bar = f_max e^{max_i a_i} max_j
+                                 e^{b'_j}; for dx = 1 the factor of column j is tightened to
+                                 e^{b'_j - dist_j^2 / 2Q}, dist_j the distance from x_j to the
+                                 hull of the transition means A x_i + c of the time-(c-1)
+                                 particles) */
   uint64_t seed;              /* Philox key */
   uint32_t counter_base;      /* < 2^28; e.g. the particle-Gibbs sweep index */
   uint32_t rs_max_attempts;   /* cap per slot for DSMC_RS (0 means 2^20) */
