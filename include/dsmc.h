@@ -112,7 +112,8 @@ typedef struct {
   int max_merges_per_launch;  /* 0 = default; bounds the workspace */
   int fused_max_merges;       /* dense sampler: levels with at most this many combinations run
                                  as one fused launch (a thread-block cluster per combination,
-                                 FP32 cross term); 0 = default (32), < 0 = never */
+                                 FP32 cross term); 0 = default (32; none with a
+                                 tensor-core precision and dx > 8), < 0 = never */
 } dsmc_config_t;
 
 /* Caller-owned DEVICE state of one smoothing (sizes from dsmc_state_sizes()).

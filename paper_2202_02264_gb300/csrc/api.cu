@@ -498,6 +498,9 @@ int fused_min_cluster(const Plan& p) {
 
 int fused_policy(const Plan& p, const dsmc_config_t* cfg, int M) {
   if (!p.dense) return 0;
+  // default: fused levels evaluate the cross term in FP32 on the CUDA cores, (d + 2) FMAs a
+  // pair; with a tensor-core precision and d > 8 the split path's MMA is the cheaper one
+  if (cfg->fused_max_merges == 0 && p.compute != DSMC_FP32 && p.D > 8) return 0;
   const int cap = cfg->fused_max_merges == 0 ? kDefaultFusedMaxMerges : cfg->fused_max_merges;
   if (cap < 0 || M > cap) return 0;
   return fused_min_cluster(p);
