@@ -43,11 +43,6 @@ constexpr int kRsThreads = 128;
 // (16 BF16 or 8 TF32 values); plane p of a combination is a [Nr][32 B] array in the
 // canonical no-swizzle K-major layout (8-row x 16-byte core matrices: row group g at
 // g*256 B, 16-byte chunk c at c*128 B).  Entries beyond D + 4 are zero.
-__host__ __device__ __forceinline__ int mma_planes(int D, int compute) {
-  const int kp = compute == DSMC_BF16 ? 16 : 8;
-  return (D + 4 + kp - 1) / kp;
-}
-
 template <int D, int KIND>
 __device__ __forceinline__ void store_mma_row_t(unsigned char* base, int Nr, int r, const float* x,
                                                 const float* ext) {
