@@ -347,9 +347,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
         }
         racc = __fadd_rn(racc, __fadd_rn(t0, t1));
         if (row < N) {
-          if (B == 32) {
-            if (col0 < cur.j1) Trow[col0 / 32] = t0;
-            if (col0 + 32 < cur.j1) Trow[col0 / 32 + 1] = t1;
+          if (B == 32) {  // tiles col0 / 32 (even: chunks start at multiples of 128) and + 1
+            if (col0 + 32 < cur.j1)
+              *reinterpret_cast<float2*>(Trow + col0 / 32) = make_float2(t0, t1);
+            else if (col0 < cur.j1)
+              Trow[col0 / 32] = t0;
           } else if (col0 < cur.j1) {
             Trow[col0 / 64] = __fadd_rn(t0, t1);
           }
