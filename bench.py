@@ -51,7 +51,7 @@ COMBINED_EXP_FACTOR = 1.28
 
 # ncu DRAM bytes per combination of the dominant kernel in the batched step, from one
 # full-size launch (a 1-pass capture; see profiles/).
-TRAFFIC_PER_COMBINATION = {("batched_lgssm_d4", "bf16"): {"bytes": 66595, "kernel": "rowsum_tc_kernel<BF16, 1 K plane>"}}
+TRAFFIC_PER_COMBINATION = {("batched_lgssm_d4", "bf16"): {"bytes": 66620, "kernel": "rowsum_tc_kernel<BF16, 1 K plane>"}}
 
 # ncu DRAM bytes per launch of the single-sequence workloads' dominant kernel (none current:
 # the kernels changed since the last capture).
