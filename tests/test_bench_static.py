@@ -1,6 +1,6 @@
-"""bench.py is run by the driver on the GPU machine only: a static check here catches a name
-that a refactor left undefined in one of its functions (a NameError there would only show
-on the GPU)."""
+"""bench.py runs only where a GPU is: a static check here catches a name that a refactor
+left undefined in one of its functions (a NameError there would otherwise show only on a
+GPU machine)."""
 import ast
 import builtins
 import os
