@@ -74,6 +74,10 @@ def _lib_handle():
                                                ip, ip]
             lib.orc_kp_rs_pairs.argtypes = [C.c_int, fp, C.c_uint32, C.c_uint32, C.c_uint32,
                                             C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip, up]
+            lib.orc_mh_pairs.argtypes = [C.c_int, dp, C.c_uint32, C.c_uint32, C.c_uint32,
+                                         C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip]
+            lib.orc_kp_mh_pairs.argtypes = [C.c_int, fp, C.c_uint32, C.c_uint32, C.c_uint32,
+                                            C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip]
             _lib = lib
     return _lib
 
@@ -248,6 +252,33 @@ def rs_pairs(logW, logbar, seed, gid, n0, n1, max_attempts=1 << 20, counter_base
     st = _check(lib.orc_rs_pairs(N, _p(W), logbar, lo, hi, counter_base, gid, n0, n1, max_attempts,
                                  _p(li, C.c_int32), _p(ri, C.c_int32), _p(att, C.c_uint64)), "rs_pairs")
     return li, ri, int(att[0]), st
+
+
+def mh_pairs(logW, seed, gid, n0, n1, B, counter_base=0):
+    """Algorithm 7 draws for slots [n0, n1): B Metropolis-Hastings steps from (n, n) on a
+    given log-weight matrix."""
+    lib = _lib_handle()
+    W = np.ascontiguousarray(logW, np.float64)
+    N = W.shape[0]
+    li = np.zeros(n1 - n0, np.int32)
+    ri = np.zeros(n1 - n0, np.int32)
+    lo, hi = _seed_words(seed)
+    _check(lib.orc_mh_pairs(N, _p(W), lo, hi, counter_base, gid, n0, n1, B,
+                            _p(li, C.c_int32), _p(ri, C.c_int32)), "mh_pairs")
+    return li, ri
+
+
+def kp_mh_pairs(ratio, seed, gid, n0, n1, B, counter_base=0):
+    """Device-precision Algorithm 7 on the device's own FP32 ratios [N][N]."""
+    lib = _lib_handle()
+    q = np.ascontiguousarray(ratio, np.float32)
+    N = q.shape[0]
+    li = np.zeros(n1 - n0, np.int32)
+    ri = np.zeros(n1 - n0, np.int32)
+    lo, hi = _seed_words(seed)
+    _check(lib.orc_kp_mh_pairs(N, _p(q, C.c_float), lo, hi, counter_base, gid, n0, n1, B,
+                               _p(li, C.c_int32), _p(ri, C.c_int32)), "kp_mh_pairs")
+    return li, ri
 
 
 def kp_dense_pairs(r, t, e, B, seed, gid, n0, n1, counter_base=0):

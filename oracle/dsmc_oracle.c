@@ -43,6 +43,7 @@
 #define ORC_PURPOSE_INIT 1u
 #define ORC_PURPOSE_DENSE 2u
 #define ORC_PURPOSE_RS 3u
+#define ORC_PURPOSE_MH 4u
 
 #define ORC_OK 0
 #define ORC_ERR_INVALID 1
@@ -462,6 +463,65 @@ int orc_rs_pairs(int N, const double* logW, double logbar, uint32_t seed_lo, uin
   mat_ctx m = {logW, N};
   return rs_draws(N, mat_logw, &m, logbar, seed_lo, seed_hi, base, gid, n0, n1, max_attempts, li,
                   ri, attempts);
+}
+
+/* Algorithm 7 (Metropolis-Hastings lazy resampling), FP64: slot n starts at (n mod N,
+ * n mod N); at step b it draws (slot n, combination gid, purpose MH, counter base, b):
+ * I* = floor(w0 N / 2^32), J* = floor(w1 N / 2^32), u = u23(w2), and moves to (I*, J*)
+ * when u < omega(I*, J*) / omega(I, J), here exp(logW* - logW) (a current weight of zero
+ * accepts any proposal of positive weight).  The target includes both leaf weights (the
+ * log-weights of Eq. normalized-weights).  After B steps the pair is the slot's draw. */
+int orc_mh_pairs(int N, const double* logW, uint32_t seed_lo, uint32_t seed_hi, uint32_t base,
+                 uint32_t gid, int n0, int n1, uint32_t B, int32_t* li, int32_t* ri) {
+  for (int n = n0; n < n1; ++n) {
+    int I = n % N, J = n % N;
+    double cur = logW[(size_t)I * N + J];
+    for (uint32_t b = 0; b < B; ++b) {
+      uint32_t w[4];
+      draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_MH, base, b, w);
+      const int Is = (int)(((uint64_t)w[0] * (uint64_t)N) >> 32);
+      const int Js = (int)(((uint64_t)w[1] * (uint64_t)N) >> 32);
+      const double prop = logW[(size_t)Is * N + Js];
+      const double u = u23(w[2]);
+      const int accept = (cur == -INFINITY) ? (prop > -INFINITY) : (u < exp(prop - cur));
+      if (accept) {
+        I = Is;
+        J = Js;
+        cur = prop;
+      }
+    }
+    li[n - n0] = I;
+    ri[n - n0] = J;
+  }
+  return ORC_OK;
+}
+
+/* The same chain on the device's own FP32 weight ratios r = omega / omega-bar [N][N]: the
+ * move is taken iff u r(I, J) < r(I*, J*) in FP32 (one rounding of the product), the form
+ * the device evaluates. */
+int orc_kp_mh_pairs(int N, const float* ratio, uint32_t seed_lo, uint32_t seed_hi, uint32_t base,
+                    uint32_t gid, int n0, int n1, uint32_t B, int32_t* li, int32_t* ri) {
+  for (int n = n0; n < n1; ++n) {
+    int I = n % N, J = n % N;
+    float cur = ratio[(size_t)I * N + J];
+    for (uint32_t b = 0; b < B; ++b) {
+      uint32_t w[4];
+      draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_MH, base, b, w);
+      const int Is = (int)(((uint64_t)w[0] * (uint64_t)N) >> 32);
+      const int Js = (int)(((uint64_t)w[1] * (uint64_t)N) >> 32);
+      const float prop = ratio[(size_t)Is * N + Js];
+      const float u = (float)u23(w[2]);
+      const float lhs = u * cur;
+      if (lhs < prop) {
+        I = Is;
+        J = Js;
+        cur = prop;
+      }
+    }
+    li[n - n0] = I;
+    ri[n - n0] = J;
+  }
+  return ORC_OK;
 }
 
 typedef struct {
