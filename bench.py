@@ -69,6 +69,8 @@ WORKLOADS = {
     # genuinely dominant pair (two low-tail particles with a near-zero observation) still
     # leaves some combinations accepting ~1e-6 of their uniform proposals, hence the cap
     "sv_rs": dict(K=4096, N=16384, resampler="rs", rs_max_attempts=1 << 26, steps=3),
+    # Algorithm 7 at N = 16384: B = 64 Metropolis-Hastings steps per slot (biased)
+    "sv_mh": dict(K=4096, N=16384, resampler="mh", steps=10),
     "lgssm_d4": dict(K=512, N=512, resampler="dense"),
 }
 
@@ -179,7 +181,7 @@ def run_reference(args):
         r0 = S.request_stream(1, spec["rate"])[0]
         wl = W.Workload(args.workload, r0.model, r0.K, r0.N, r0.y, None)
     else:
-        wl = W.workload(args.workload.replace("_rs", ""), K=spec["K"], N=spec["N"])
+        wl = W.workload(args.workload.replace("_rs", "").replace("_mh", ""), K=spec["K"], N=spec["N"])
     from oracle import core
     y = wl.y.astype(np.float32).astype(np.float64)
     # calibrate K' so that each step is a bounded slice of the workload (~2-4 s)
@@ -228,12 +230,12 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     spec = WORKLOADS[args.workload]
-    base_name = args.workload.replace("_rs", "")
+    base_name = args.workload.replace("_rs", "").replace("_mh", "")
     wl = W.workload(base_name, K=spec["K"], N=spec["N"])
     K, N = wl.K, wl.N
-    resampler = dsmc.RS if spec["resampler"] == "rs" else dsmc.MULTINOMIAL
-    if resampler == dsmc.RS:
-        args.compute = "fp32"   # the lazy sampler evaluates its proposed pairs in FP32
+    resampler = {"rs": dsmc.RS, "mh": dsmc.MH}.get(spec["resampler"], dsmc.MULTINOMIAL)
+    if resampler != dsmc.MULTINOMIAL:
+        args.compute = "fp32"   # the lazy samplers evaluate their proposed pairs in FP32
     compute = {"fp32": dsmc.FP32, "tf32": dsmc.TF32, "bf16": dsmc.BF16}[args.compute]
     sm = dsmc.Smoother(wl.model, K, N, seed=1000 + 7919 * rank, resampler=resampler, compute=compute,
                        rs_max_attempts=spec.get("rs_max_attempts", 0),
@@ -318,9 +320,9 @@ def run_ours(args):
     ex2_peak = MUFU_EX2_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9       # G exp / s
     achieved = rs_pairs / (rs_ms / 1e3) / 1e9 if rs_ms > 0 else None   # G exp / s
     d = wl.model.d
-    lazy = resampler == dsmc.RS   # no N x N pass: prologue + Algorithm 8's per-slot attempts
+    lazy = resampler != dsmc.MULTINOMIAL   # no N x N pass: prologue + per-slot proposals
     roofline = {"bound": "alu",
-                "kernel": ("sample_rs_kernel (Algorithm 8: proposed pairs only; no N x N pass to time)"
+                "kernel": ("lazy sampler (Algorithm 8 or 7: proposed pairs only; no N x N pass to time)"
                            if lazy else
                            "rowsum_kernel (fused exp / tile sums)" if args.compute == "fp32"
                            else "rowsum_tc_kernel (tcgen05 cross term, fused exp / tile sums)"),

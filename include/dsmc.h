@@ -58,7 +58,7 @@ enum { DSMC_MODEL_LGSSM = 0, DSMC_MODEL_SV = 1 };
 enum { DSMC_PROP_OBS = 0, DSMC_PROP_GAUSS = 1 };
 enum { DSMC_NU_EQ_Q = 0, DSMC_NU_PROP_H = 1 };
 enum { DSMC_FP32 = 0, DSMC_TF32 = 1, DSMC_BF16 = 2 };
-enum { DSMC_MULTINOMIAL = 0, DSMC_RS = 1 };
+enum { DSMC_MULTINOMIAL = 0, DSMC_RS = 1, DSMC_MH = 2 };
 
 /* The state-space model of Eq. (ssm) (Section 1).  All arrays are HOST, row-major, FP64,
  * read during the call only.
@@ -98,17 +98,22 @@ typedef struct {
                                  cores: the whole base-2 exponent alpha_i + beta_j + u_i.v_j
                                  is one MMA, alpha and beta entering as two-term splits in
                                  the MMA type; FP32 accumulate, exp and sums; dense N <= 4096.
-                                 Ignored by DSMC_RS, which evaluates its proposed pairs in FP32 */
+                                 Ignored by the lazy samplers (DSMC_RS, DSMC_MH), which
+                                 evaluate their proposed pairs in FP32 */
   int resampler;              /* DSMC_MULTINOMIAL (dense, Algorithm 1) or DSMC_RS (Alg. 8:
                                  uniform pair proposals accepted with probability
                                  omega_ij / omega-bar, omega-bar = f_max e^{max_i a_i} max_j
                                  e^{b'_j}; for dx = 1 the factor of column j is tightened to
                                  e^{b'_j - dist_j^2 / 2Q}, dist_j the distance from x_j to the
                                  hull of the transition means A x_i + c of the time-(c-1)
-                                 particles) */
+                                 particles); or DSMC_MH (Algorithm 7: per slot, B Metropolis-
+                                 Hastings steps from (n mod N, n mod N) with uniform pair
+                                 proposals, accepted iff u r(I,J) < r(I*,J*) in FP32, r the
+                                 pair's ratio omega / omega-bar; biased for finite B) */
   uint64_t seed;              /* Philox key */
   uint32_t counter_base;      /* < 2^28; e.g. the particle-Gibbs sweep index */
-  uint32_t rs_max_attempts;   /* cap per slot for DSMC_RS (0 means 2^20) */
+  uint32_t rs_max_attempts;   /* DSMC_RS: cap of attempts per slot (0 means 2^20);
+                                 DSMC_MH: the steps B of each slot's chain (0 means 64) */
   int max_merges_per_launch;  /* 0 = default; bounds the workspace */
   int fused_max_merges;       /* dense sampler: levels with at most this many combinations run
                                  as one fused launch (a thread-block cluster per combination,
@@ -172,7 +177,7 @@ dsmc_status_t dsmc_resolve(const dsmc_config_t* cfg, const dsmc_model_t* model,
                            void* stream);
 
 /* The whole smoother: init, every level, resolve.  logL_out: DEVICE FP64 scalar, the log
- * normalising-constant estimate of Eq. (rec-loglik) (NaN with DSMC_RS, which never forms
+ * normalising-constant estimate of Eq. (rec-loglik) (NaN with DSMC_RS or DSMC_MH, which never form
  * the N x N sums). */
 dsmc_status_t dsmc_smooth(const dsmc_config_t* cfg, const dsmc_model_t* model,
                           const dsmc_proposal_t* prop, const float* y, dsmc_state_t* state,

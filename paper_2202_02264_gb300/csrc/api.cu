@@ -100,6 +100,7 @@ dsmc_status_t cuda_fail(cudaError_t e, const char* what) {
 constexpr int kMaxDim = 32;
 constexpr int kMaxDenseN = 16384;
 constexpr int kDefaultMergeCap = 1024;
+constexpr uint32_t kDefaultMhSteps = 64;   // Algorithm 7's B when rs_max_attempts is 0
 constexpr int kRowsumTargetCtas = 152 * 8;  // 152 SMs, several CTAs each
 
 int pad_dim(int d) {
@@ -158,7 +159,7 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p, int
   p.D = pad_dim(model->dx);
   p.L = 0;
   while ((1 << p.L) < p.K) ++p.L;
-  p.dense = cfg->resampler != DSMC_RS;
+  p.dense = cfg->resampler == DSMC_MULTINOMIAL;
   // the cross-term precision only matters to the dense N x N pass; the lazy sampler
   // evaluates its proposed pairs in FP32 and needs no tensor-core operands
   p.compute = p.dense ? cfg->compute : DSMC_FP32;
@@ -354,7 +355,7 @@ dsmc_status_t check_config(const dsmc_config_t* cfg, const dsmc_model_t* model) 
   if (cfg->K < 1) return fail(DSMC_ERR_INVALID_ARG, "K must be >= 1");
   if (cfg->N < 1) return fail(DSMC_ERR_INVALID_ARG, "N must be >= 1");
   if (cfg->K > (1 << 24) || cfg->N > (1 << 24)) return fail(DSMC_ERR_UNSUPPORTED, "K or N too large");
-  if (cfg->resampler != DSMC_MULTINOMIAL && cfg->resampler != DSMC_RS)
+  if (cfg->resampler != DSMC_MULTINOMIAL && cfg->resampler != DSMC_RS && cfg->resampler != DSMC_MH)
     return fail(DSMC_ERR_INVALID_ARG, "unknown resampler");
   if (cfg->resampler == DSMC_MULTINOMIAL && cfg->N > kMaxDenseN)
     return fail(DSMC_ERR_UNSUPPORTED, "dense resampling supports N <= 16384; use DSMC_RS");
@@ -441,7 +442,9 @@ MergeArgs merge_args(const Plan& p, const dsmc_config_t* cfg, const float* y, in
   a.mma_planes = p.planes;
   a.seed = cfg->seed;
   a.base = cfg->counter_base;
-  a.rs_max = cfg->rs_max_attempts ? cfg->rs_max_attempts : (1u << 20);
+  // DSMC_RS: attempts per slot before DSMC_ERR_RS_LIMIT; DSMC_MH: the chain's steps B
+  a.rs_max = cfg->rs_max_attempts ? cfg->rs_max_attempts
+                                  : (cfg->resampler == DSMC_MH ? kDefaultMhSteps : (1u << 20));
   a.logN = (float)std::log((double)p.N);
   a.prop_mean = nullptr;
   a.prop_std = nullptr;
@@ -587,7 +590,7 @@ dsmc_status_t launch_combs(const Plan& p, const dsmc_config_t* cfg, const ParamB
       prof_count(3);
     } else {
       DSMC_CUDA(bd_begin(s, DSMC_KIND_DRAWS), "profile event");
-      DSMC_CUDA(launch_sample_rs(p.D, a, s), "rejection sampler kernel");
+      DSMC_CUDA(launch_sample_rs(p.D, a, s), "lazy sampler kernel");
       DSMC_CUDA(launch_epilogue(a, s), "epilogue kernel");
       DSMC_CUDA(bd_end(s), "profile event");
       prof_count(3);

@@ -14,6 +14,7 @@ namespace dsmc {
 constexpr uint32_t kPurposeInit = 1u;
 constexpr uint32_t kPurposeDense = 2u;
 constexpr uint32_t kPurposeRS = 3u;
+constexpr uint32_t kPurposeMH = 4u;
 
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.69314718055994531f;

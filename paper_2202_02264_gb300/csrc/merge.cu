@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
   // the distance from x_j to the hull, so log omega-bar = log f_max + max_i a_i +
   // max_j (b'_j - dist_j^2 Q^-1 / 2) is a valid bound of the combination's pair weights
   // (Algorithm 8 needs any bound; a particle far outside the hull otherwise sets it).
-  const bool hull = (D == 1) && a.resampler == DSMC_RS;
+  const bool hull = (D == 1) && a.resampler != DSMC_MULTINOMIAL;
   float m_lo = 0.f, m_hi = 0.f, bhull = -INFINITY;
   if (hull) {
     float lo = INFINITY, hi = -INFINITY;
@@ -856,6 +856,56 @@ __global__ void __launch_bounds__(kRsThreads) sample_rs_kernel(MergeArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Metropolis-Hastings lazy sampler (Algorithm 7): slot n starts at (n mod N, n mod N) and
+// takes B = rs_max steps; step b proposes (I*, J*) uniformly (Philox word pair) and moves
+// iff u r(I, J) < r(I*, J*) in FP32, r = omega / omega-bar the pair's ratio (the bound
+// cancels; a current ratio of 0 accepts any proposal of positive ratio).  Only the current
+// and the proposed pairs are evaluated.  One thread per slot; biased for finite B.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kRsThreads) sample_mh_kernel(MergeArgs a) {
+  const int s = blockIdx.y;
+  const Comb cb = comb_of(a, s);
+  const int gid = cb.gid;
+  const int N = a.N;
+  const int n_lo = cb.conditional ? 1 : 0;
+  const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
+  const int n = n_lo + blockIdx.x * kRsThreads + threadIdx.x;
+  const double logbar = a.ws.logbar[s];
+  int32_t* pl = cb.pairs + (size_t)gid * 2 * N;
+  int32_t* pr = pl + N;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ws.inc[s] = (double)NAN;  // the lazy sampler never forms the N x N sum
+    if (cb.conditional) {
+      pl[0] = 0;
+      pr[0] = 0;
+    }
+  }
+  if (n >= n_hi) return;
+  int I = n % N, J = n % N;
+  float cur = rs_ratio<D>(a, s, I, J, logbar);
+  for (uint32_t b = 0; b < a.rs_max; ++b) {
+    const uint4 w = draw(cb.seed, (uint32_t)n, (uint32_t)gid, kPurposeMH, cb.base, b);
+    const int Is = (int)__umulhi(w.x, (uint32_t)N);
+    const int Js = (int)__umulhi(w.y, (uint32_t)N);
+    const float prop = rs_ratio<D>(a, s, Is, Js, logbar);
+    if (__fmul_rn(u23(w.z), cur) < prop) {
+      I = Is;
+      J = Js;
+      cur = prop;
+    }
+  }
+  if (isnan(cur)) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+  if (n < N) {
+    pl[n] = I;
+    pr[n] = J;
+  } else {
+    cb.star[0] = I;
+    cb.star[1] = J;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Epilogue: the new block's first/last index maps (the composition of the Remark in
 // Section 3.1) into the other map buffer, and log L_{a:b} = log L_{a:c-1} + log L_{c:b} +
 // increment (Eq. rec-loglik, weighted form).
@@ -976,7 +1026,10 @@ cudaError_t sample_dense_t(const MergeArgs& a, cudaStream_t st) {
 template <int D>
 cudaError_t sample_rs_t(const MergeArgs& a, cudaStream_t st) {
   dim3 grid((launch_slots(a) + kRsThreads - 1) / kRsThreads, a.mc);
-  sample_rs_kernel<D><<<grid, kRsThreads, 0, st>>>(a);
+  if (a.resampler == DSMC_MH)
+    sample_mh_kernel<D><<<grid, kRsThreads, 0, st>>>(a);
+  else
+    sample_rs_kernel<D><<<grid, kRsThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

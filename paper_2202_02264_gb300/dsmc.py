@@ -29,7 +29,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "workspace too sm
           8: "rejection-sampling attempt cap", 9: "timeout"}
 
 FP32, TF32, BF16 = 0, 1, 2
-MULTINOMIAL, RS = 0, 1
+MULTINOMIAL, RS, MH = 0, 1, 2
 
 
 class DsmcError(RuntimeError):

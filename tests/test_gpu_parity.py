@@ -185,6 +185,43 @@ def test_rejection_indices_bit_exact(name, K, N, level):
     assert sm.status() == 0
 
 
+@pytest.mark.parametrize("name,K,N,level", [("sv", 8, 500, 0), ("sv", 16, 333, 2), ("lgssm_1d", 5, 64, 2),
+                                            ("lgssm_d4", 6, 96, 1)])
+def test_metropolis_hastings_indices_bit_exact(name, K, N, level):
+    """Algorithm 7 on the device against the oracle's device-precision chain fed the same
+    FP32 ratios: B = 64 steps from (n, n), u r(I, J) < r(I*, J*)."""
+    wl, m, sm = _level_setup(name, K, N, level, resampler=dsmc.MH)
+    M = core.merges_at_level(K, level)
+    dbg = dsmc.dsmc_debug_merge_weights(sm.cfg, sm.hm, level, M - 1, sm.ws, want=("ratio",))
+    q = dbg["ratio"].cpu().numpy()
+    li, ri = core.kp_mh_pairs(q, sm.cfg.seed, dbg["gid"], 0, N, 64)
+    pairs = sm.pairs.cpu().numpy()
+    np.testing.assert_array_equal(pairs[dbg["gid"], 0], li)
+    np.testing.assert_array_equal(pairs[dbg["gid"], 1], ri)
+    assert sm.status() == 0
+
+
+def test_metropolis_hastings_conditional_keeps_slot_zero_and_smooths():
+    """Conditional Algorithm 7 keeps slot 0 = (0, 0) at every level; a whole MH smoothing
+    with many steps lands near the Kalman/RTS means (its bias shrinks with B)."""
+    wl, m, sm = _level_setup("lgssm_1d", 16, 200, 3, resampler=dsmc.MH, conditional=True)
+    pairs = sm.pairs.cpu().numpy()
+    assert (pairs[:, :, 0] == 0).all()
+    assert sm.status() == 0
+    wl = W.workload("lgssm_1d")
+    ms, _, _ = kalman.rts_for(wl.model, wl.y)
+    y = dev(wl.y)
+    errs = {}
+    for res, B in ((dsmc.MULTINOMIAL, 0), (dsmc.MH, 256)):
+        g = []
+        for r in range(16):
+            smr = dsmc.Smoother(wl.model, wl.K, 256, seed=3000 + r, resampler=res, rs_max_attempts=B)
+            g.append(smr.smooth(y).cpu().numpy().copy())
+            assert smr.status() == 0
+        errs[res] = np.sqrt(((np.mean(g, 0) - ms) ** 2).mean())
+    assert errs[dsmc.MH] < 2.0 * errs[dsmc.MULTINOMIAL] + 0.02, errs
+
+
 def test_level0_increment_matches_oracle():
     """log L after level 0 = log L_{c-1} + log L_c + log sum_ij exp(logW_ij) (Eq. Lab)."""
     wl, m, sm = _level_setup("lgssm_d8", 16, 256, 0)
