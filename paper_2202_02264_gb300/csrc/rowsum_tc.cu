@@ -10,10 +10,13 @@
 //     TMA bulk copies (cp.async.bulk, operands pre-laid out by the prologue in the canonical
 //     no-swizzle K-major layout, one 32-byte K plane = 16 BF16 or 8 TF32 values per copy), and
 //     issues P tcgen05.mma (M = 128, N = 128, one per K plane) per block into one of two
-//     128-column TMEM accumulators;
+//     128-column TMEM accumulators; every MMA commits to its accumulator's barrier and to
+//     its column slot's, every row tile's last MMA to the tile's, and the control warp
+//     refills a slot or a tile as soon as the MMAs that read it have completed;
 //   - eight epilogue warps (two per TMEM lane quarter, splitting the block's columns) read the
 //     accumulator with tcgen05.ld, take 2^x on MUFU and keep the per-tile sums, while the
-//     tensor core already computes the next block.
+//     tensor core already computes the next block; when one chunk covers the whole row they
+//     also keep their half's running row total, which the row-CDF kernel adds up.
 // Every wait is bounded; on a timeout the CTA records DSMC_ERR_TIMEOUT, waits (bounded) for
 // its own outstanding MMA, frees its TMEM and returns.
 #include <cuda_bf16.h>
