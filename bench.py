@@ -82,6 +82,18 @@ def _dist():
     return ws, rank, lrank
 
 
+def job_time(t_local: float, device) -> float:
+    """The whole job's timed region: the slowest rank's time (a MAX all-reduce over the
+    process group), or the local time when the job runs as a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_local
+    tt = torch.tensor([t_local], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -276,10 +288,7 @@ def run_ours(args):
     clk = clocks.stop()
     per_step = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(per_step) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = job_time(t_total, dev)
     st = sm.status()
     if st != 0:
         raise RuntimeError(f"device status {st} after timed steps")
@@ -440,10 +449,7 @@ def run_batched(args):
     clk = clocks.stop()
     per_step = [a.elapsed_time(c) for a, c in ev]
     t_total = sum(per_step) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = job_time(t_total, dev)
     if b.status() != 0:
         raise RuntimeError(f"device status {b.status()} after timed steps")
     value = world * args.steps * units / t_total
