@@ -328,6 +328,12 @@ dsmc_status_t dsmc_profile_breakdown_read(double* ms /* [DSMC_KINDS] */, int64_t
 
 /* ---- Inspection entry points used by the parity tests (same arithmetic as the path). */
 
+/* Test switch for the bounded waits: while enabled, the tensor-core tile-sum launches
+ * issue no MMA, so their waits on the accumulators run out after their iteration limit
+ * (about a second); the kernel then records DSMC_ERR_TIMEOUT, frees its tensor memory and
+ * returns, and the context stays usable.  Off by default; host state of this process. */
+dsmc_status_t dsmc_debug_stall_tensor_cores(int enable);
+
 /* Philox4x32-10 of n counters: ctr DEVICE [n][4] uint32, out DEVICE [n][4] uint32. */
 dsmc_status_t dsmc_debug_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
                                 void* stream);

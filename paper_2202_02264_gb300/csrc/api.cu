@@ -67,6 +67,9 @@ struct Breakdown {
 };
 thread_local Breakdown g_bd;
 
+// Test switch of dsmc_debug_stall_tensor_cores: tile-sum launches issue no MMA.
+bool g_stall_tc = false;
+
 cudaError_t bd_begin(cudaStream_t s, int kind) {
   if (!g_bd.on) return cudaSuccess;
   if (g_bd.used == g_bd.a.size()) {
@@ -438,6 +441,7 @@ MergeArgs merge_args(const Plan& p, const dsmc_config_t* cfg, const float* y, in
   a.root = (level == p.L - 1);
   a.resampler = cfg->resampler;
   a.compute = p.compute;
+  a.stall = g_stall_tc ? 1 : 0;
   a.Nr = p.Nr;
   a.mma_planes = p.planes;
   a.seed = cfg->seed;
@@ -1359,6 +1363,11 @@ dsmc_status_t dsmc_profile_breakdown_read(double* ms, int64_t* launches) {
     ms[k] += t;
     launches[k] += 1;
   }
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_debug_stall_tensor_cores(int enable) {
+  g_stall_tc = enable != 0;
   return DSMC_OK;
 }
 

@@ -97,6 +97,8 @@ struct MergeArgs {
   int compute;       // DSMC_FP32, DSMC_TF32 or DSMC_BF16
   int Nr;            // N rounded up to 128 (tensor-core operand rows)
   int mma_planes;    // 32-byte K planes of the tensor-core operands
+  int stall;         // test switch: the tensor-core control warp issues no MMA, so every
+                     // wait on an accumulator runs out (dsmc_debug_stall_tensor_cores)
   uint64_t seed;
   uint32_t base;
   uint32_t rs_max;

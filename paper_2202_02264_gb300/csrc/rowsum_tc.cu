@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
           if (q >= 2) ok = mbar_wait(smem_u32(&bar_epi[buf]), (uint32_t)((q >> 1) - 1) & 1);
           if (ok) ok = mbar_wait(smem_u32(&bar_v[slot]), (uint32_t)(q / kVSlots) & 1);
           if (!ok) break;
+          if (a.stall) continue;  // test switch: nothing is issued, no accumulator completes
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sv = smem_u32(sV + (size_t)slot * kSlotBytes);
 #pragma unroll

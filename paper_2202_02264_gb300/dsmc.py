@@ -79,6 +79,7 @@ EXPORTS = ["dsmc_status_string", "dsmc_last_error", "dsmc_state_sizes", "dsmc_wo
            "dsmc_conditional_smooth", "dsmc_smooth_noalloc", "dsmc_stream_status",
            "dsmc_profile_enable",
            "dsmc_profile_read", "dsmc_debug_philox", "dsmc_debug_merge_weights",
+           "dsmc_debug_stall_tensor_cores",
            "dsmc_batch_workspace_size", "dsmc_batch_prepare", "dsmc_batch_run", "dsmc_smooth_batch",
            "dsmc_seq_maps_bytes", "dsmc_serve_workspace_size", "dsmc_serve_tick",
            "dsmc_profile_breakdown_enable", "dsmc_profile_breakdown_read"]
@@ -124,6 +125,7 @@ def load(build_if_needed: bool = False) -> C.CDLL:
         lib.dsmc_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                           C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         lib.dsmc_debug_philox.argtypes = [vp, C.c_int64, C.c_uint64, vp, vp]
+        lib.dsmc_debug_stall_tensor_cores.argtypes = [C.c_int]
         lib.dsmc_debug_merge_weights.argtypes = [cfgp, modp, C.c_int, C.c_int, vp, vp, vp, vp, vp,
                                                  vp, C.POINTER(C.c_int), vp, sz, vp]
         lib.dsmc_seq_maps_bytes.restype = C.c_size_t
@@ -278,6 +280,10 @@ def dsmc_profile_read():
     _check(load().dsmc_profile_read(C.byref(ms), C.byref(n), C.byref(pairs), C.byref(alln)),
            "dsmc_profile_read")
     return ms.value, n.value, pairs.value, alln.value
+
+
+def dsmc_debug_stall_tensor_cores(enable: bool):
+    _check(load().dsmc_debug_stall_tensor_cores(int(bool(enable))), "dsmc_debug_stall_tensor_cores")
 
 
 def dsmc_debug_philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:

@@ -630,3 +630,26 @@ def test_particle_gibbs_chain_on_rts():
     se = bm.std(0, ddof=1) / np.sqrt(nb)
     z = np.abs(bm.mean(0) - ms[:, 0]) / se
     assert z.max() < 4.5, z.max()
+
+
+def test_tensor_core_wait_runs_out_and_reports_timeout():
+    """Failure detection on the device: with the test switch on, the tensor-core launch
+    issues no MMA, so the epilogue's wait on its accumulator reaches its iteration limit;
+    the kernel records DSMC_ERR_TIMEOUT, frees its tensor memory and returns, and the next
+    smoothing on the same context runs clean."""
+    wl = W.workload("lgssm_d4", K=8, N=256)
+    y = dev(wl.y)
+    sm = dsmc.Smoother(wl.model, 8, 256, seed=3, compute=dsmc.BF16, fused_max_merges=-1)
+    sm.init(y)
+    dsmc.dsmc_debug_stall_tensor_cores(True)
+    try:
+        sm.merge_level(y, 0)
+        torch.cuda.synchronize()
+    finally:
+        dsmc.dsmc_debug_stall_tensor_cores(False)
+    assert sm.status() == 9          # DSMC_ERR_TIMEOUT
+    sm2 = dsmc.Smoother(wl.model, 8, 256, seed=3, compute=dsmc.BF16, fused_max_merges=-1)
+    sm2.smooth(y)
+    torch.cuda.synchronize()
+    assert sm2.status() == 0
+    assert torch.isfinite(sm2.mean).all()
