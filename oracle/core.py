@@ -173,7 +173,7 @@ def smooth(model, y, K, N, seed, counter_base=0, resampler="dense", rs_max_attem
     keep = _Keep(model, K, y)
     lo, hi = _seed_words(seed)
     cond = x_ref is not None
-    cf = Config(K, N, lo, hi, counter_base, 0 if resampler == "dense" else 1, rs_max_attempts,
+    cf = Config(K, N, lo, hi, counter_base, {"dense": 0, "rs": 1, "mh": 2}[resampler], rs_max_attempts,
                 1 if cond else 0)
     d = model.d
     mean = np.zeros((K, d))

@@ -125,7 +125,8 @@ typedef struct {
 typedef struct {
   int K, N;
   uint32_t seed_lo, seed_hi, counter_base;
-  int resampler; /* 0: multinomial inverse CDF on the full N x N matrix; 1: rejection */
+  int resampler; /* 0: multinomial inverse CDF on the full N x N matrix; 1: rejection
+                    (Algorithm 8); 2: Metropolis-Hastings (Algorithm 7) */
   uint32_t rs_max_attempts;
   int conditional;
 } orc_config;
@@ -465,23 +466,25 @@ int orc_rs_pairs(int N, const double* logW, double logbar, uint32_t seed_lo, uin
                   ri, attempts);
 }
 
-/* Algorithm 7 (Metropolis-Hastings lazy resampling), FP64: slot n starts at (n mod N,
- * n mod N); at step b it draws (slot n, combination gid, purpose MH, counter base, b):
- * I* = floor(w0 N / 2^32), J* = floor(w1 N / 2^32), u = u23(w2), and moves to (I*, J*)
- * when u < omega(I*, J*) / omega(I, J), here exp(logW* - logW) (a current weight of zero
- * accepts any proposal of positive weight).  The target includes both leaf weights (the
- * log-weights of Eq. normalized-weights).  After B steps the pair is the slot's draw. */
-int orc_mh_pairs(int N, const double* logW, uint32_t seed_lo, uint32_t seed_hi, uint32_t base,
-                 uint32_t gid, int n0, int n1, uint32_t B, int32_t* li, int32_t* ri) {
+/* Algorithm 7 (Metropolis-Hastings lazy resampling), FP64, on a pair log-weight
+ * evaluator: slot n starts at (n mod N, n mod N); at step b it draws (slot n, combination
+ * gid, purpose MH, counter base, b): I* = floor(w0 N / 2^32), J* = floor(w1 N / 2^32),
+ * u = u23(w2), and moves to (I*, J*) when u < omega(I*, J*) / omega(I, J), here
+ * exp(logW* - logW) (a current weight of zero accepts any proposal of positive weight).
+ * The target includes both leaf weights (the log-weights of Eq. normalized-weights).  After
+ * B steps the pair is the slot's draw. */
+static void mh_draws(int N, pair_logw_fn fn, const void* ctx, uint32_t seed_lo, uint32_t seed_hi,
+                     uint32_t base, uint32_t gid, int n0, int n1, uint32_t B, int32_t* li,
+                     int32_t* ri) {
   for (int n = n0; n < n1; ++n) {
     int I = n % N, J = n % N;
-    double cur = logW[(size_t)I * N + J];
+    double cur = fn(ctx, I, J);
     for (uint32_t b = 0; b < B; ++b) {
       uint32_t w[4];
       draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_MH, base, b, w);
       const int Is = (int)(((uint64_t)w[0] * (uint64_t)N) >> 32);
       const int Js = (int)(((uint64_t)w[1] * (uint64_t)N) >> 32);
-      const double prop = logW[(size_t)Is * N + Js];
+      const double prop = fn(ctx, Is, Js);
       const double u = u23(w[2]);
       const int accept = (cur == -INFINITY) ? (prop > -INFINITY) : (u < exp(prop - cur));
       if (accept) {
@@ -493,6 +496,13 @@ int orc_mh_pairs(int N, const double* logW, uint32_t seed_lo, uint32_t seed_hi, 
     li[n - n0] = I;
     ri[n - n0] = J;
   }
+}
+
+/* Algorithm 7 on a given log-weight matrix [N][N]. */
+int orc_mh_pairs(int N, const double* logW, uint32_t seed_lo, uint32_t seed_hi, uint32_t base,
+                 uint32_t gid, int n0, int n1, uint32_t B, int32_t* li, int32_t* ri) {
+  mat_ctx m = {logW, N};
+  mh_draws(N, mat_logw, &m, seed_lo, seed_hi, base, gid, n0, n1, B, li, ri);
   return ORC_OK;
 }
 
@@ -578,8 +588,10 @@ static int combine(const model_ctx* mc, const orc_config* cf, blocks* B, int a, 
     free(W);
     free(C);
   } else {
-    /* Algorithm 8 with the finite-set bound log wbar = log f_max + max_i a_i + max_j b'_j,
-     * b'_j = logw_R[j] + log h_c - log nu_c (the N x N weights are never formed). */
+    /* the lazy samplers: only the proposed pairs' weights are evaluated.  Algorithm 8 with
+     * the finite-set bound log wbar = log f_max + max_i a_i + max_j b'_j, or Algorithm 7
+     * (B = rs_max_attempts Metropolis-Hastings steps; 0 means 64);
+     * b'_j = logw_R[j] + log h_c - log nu_c. */
     double amax = -INFINITY, bmax = -INFINITY;
     double* bcol = (double*)malloc(sizeof(double) * N);
     if (!bcol) { free(li); free(ri); return ORC_ERR_OOM; }
@@ -591,8 +603,12 @@ static int combine(const model_ctx* mc, const orc_config* cf, blocks* B, int a, 
     }
     double logbar = log_f_max(mc) + amax + bmax;
     rs_ctx rc = {mc, B->Z + (size_t)(c - 1) * N * d, B->Z + (size_t)c * N * d, wl, bcol, d};
-    status = rs_draws(N, rs_model_logw, &rc, logbar, cf->seed_lo, cf->seed_hi, cf->counter_base,
-                      (uint32_t)gid, n0, nslots, cf->rs_max_attempts, li + n0, ri + n0, attempts);
+    if (cf->resampler == 2)
+      mh_draws(N, rs_model_logw, &rc, cf->seed_lo, cf->seed_hi, cf->counter_base, (uint32_t)gid, n0,
+               nslots, cf->rs_max_attempts ? cf->rs_max_attempts : 64u, li + n0, ri + n0);
+    else
+      status = rs_draws(N, rs_model_logw, &rc, logbar, cf->seed_lo, cf->seed_hi, cf->counter_base,
+                        (uint32_t)gid, n0, nslots, cf->rs_max_attempts, li + n0, ri + n0, attempts);
     free(bcol);
     /* the increment still needs the full weighted sum (Eq. Lab) */
     double M = -INFINITY;

@@ -55,6 +55,18 @@ def test_dsmc_rejection_matches_rts():
     _check_against(_seed_means(wl.model, wl.y, wl.K, wl.N, 48, resampler="rs"), ms)
 
 
+def test_dsmc_metropolis_hastings_near_rts():
+    """Algorithm 7 is biased for finite B; with B = 256 steps per slot its seed-averaged means
+    sit within a small multiple of the dense sampler's distance from the RTS means."""
+    wl = W.workload("lgssm_1d", K=17, N=64)
+    ms, _, _ = kalman.rts_for(wl.model, wl.y)
+    mh = _seed_means(wl.model, wl.y, wl.K, wl.N, 24, resampler="mh", rs_max_attempts=256)
+    de = _seed_means(wl.model, wl.y, wl.K, wl.N, 24)
+    e_mh = np.sqrt(((mh.mean(0) - ms) ** 2).mean())
+    e_de = np.sqrt(((de.mean(0) - ms) ** 2).mean())
+    assert e_mh < 2.0 * e_de + 0.02, (e_mh, e_de)
+
+
 def test_dsmc_sv_matches_grid():
     K, N = 24, 256
     m = W.sv(K)
