@@ -155,7 +155,7 @@ def oracle_sample(wl, target_s=12.0, seed=1000):
     same sequence at the same N (whole smoothings), K' grown until ~target_s of work."""
     from oracle import core
     m, y, N = wl.model, wl.y.astype(np.float32).astype(np.float64), wl.N
-    Kp = 8
+    Kp = 2
     done_units, done_s, runs = 0, 0.0, []
     while True:
         Kp = min(Kp, wl.K)
@@ -196,21 +196,25 @@ def run_reference(args):
         wl = W.workload(args.workload.replace("_rs", "").replace("_mh", ""), K=spec["K"], N=spec["N"])
     from oracle import core
     y = wl.y.astype(np.float32).astype(np.float64)
+    # the workload's own sampler (Algorithm 1, 8 or 7) and its attempt cap / step count
+    lazy = ({"resampler": spec["resampler"], "rs_max_attempts": spec.get("rs_max_attempts", 0) or
+             (64 if spec["resampler"] == "mh" else 1 << 20)}
+            if spec.get("resampler") in ("rs", "mh") else {})
     # calibrate K' so that each step is a bounded slice of the workload (~2-4 s)
-    Kp = 8
+    Kp = 2
     while True:
         t0 = time.perf_counter()
-        core.smooth(wl.model, y[:Kp], Kp, wl.N, 999)
+        core.smooth(wl.model, y[:Kp], Kp, wl.N, 999, **lazy)
         dt = time.perf_counter() - t0
         if dt > 1.0 or Kp >= wl.K:
             break
         Kp = min(Kp * 2, wl.K)
     for w in range(args.warmup):
-        core.smooth(wl.model, y[:Kp], Kp, wl.N, 900 + w)
+        core.smooth(wl.model, y[:Kp], Kp, wl.N, 900 + w, **lazy)
     times = []
     for s in range(args.steps):
         t0 = time.perf_counter()
-        core.smooth(wl.model, y[:Kp], Kp, wl.N, 1000 + s)
+        core.smooth(wl.model, y[:Kp], Kp, wl.N, 1000 + s, **lazy)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = args.steps * Kp * wl.N / tot
