@@ -165,7 +165,8 @@ def init(model, y, K, N, seed, counter_base=0, x_ref=None):
 def smooth(model, y, K, N, seed, counter_base=0, resampler="dense", rs_max_attempts=1 << 20,
            x_ref=None, want_traj=False, want_pairs=False):
     """Full dSMC smoother: Algorithm 2, then Algorithm 6 over Combine (Algorithm 1) or
-    ConditionalCombine (Algorithm 5), with multinomial or rejection (Algorithm 8) draws.
+    ConditionalCombine (Algorithm 5), with multinomial, rejection (Algorithm 8) or
+    Metropolis-Hastings (Algorithm 7, B = rs_max_attempts steps) draws.
 
     Returns a dict with mean [K][d], m2 [K][d], logL, and optionally traj [K][N][d],
     pairs [K-1][2][N], X_leaf [K][N][d], x_star [K][d], rs_attempts, status."""

@@ -67,6 +67,19 @@ def test_dsmc_metropolis_hastings_near_rts():
     assert e_mh < 2.0 * e_de + 0.02, (e_mh, e_de)
 
 
+@pytest.mark.parametrize("resampler", ["dense", "rs", "mh"])
+def test_output_values_are_leaf_particles(resampler):
+    """Every output trajectory takes, at each time t, one of the N particles drawn at t (the
+    stitching of Algorithm 1 only selects), for every sampler; K = 11 has pass-through blocks."""
+    wl = W.workload("lgssm_1d", K=11, N=32)
+    out = core.smooth(wl.model, wl.y, wl.K, wl.N, 9, resampler=resampler, want_traj=True,
+                      rs_max_attempts=(64 if resampler == "mh" else 1 << 20))
+    traj, X = out["traj"], out["X_leaf"]
+    for t in range(wl.K):
+        leaf = {float(v) for v in X[t, :, 0]}
+        assert all(float(v) in leaf for v in traj[t, :, 0]), t
+
+
 def test_dsmc_sv_matches_grid():
     K, N = 24, 256
     m = W.sv(K)
