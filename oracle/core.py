@@ -74,6 +74,8 @@ def _lib_handle():
                                                ip, ip]
             lib.orc_kp_rs_pairs.argtypes = [C.c_int, fp, C.c_uint32, C.c_uint32, C.c_uint32,
                                             C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip, up]
+            lib.orc_rs_bounds.argtypes = [C.POINTER(Model), C.c_int, dp, C.c_int, C.c_int, C.c_int,
+                                          dp, dp, dp, dp, dp]
             lib.orc_mh_pairs.argtypes = [C.c_int, dp, C.c_uint32, C.c_uint32, C.c_uint32,
                                          C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip]
             lib.orc_kp_mh_pairs.argtypes = [C.c_int, fp, C.c_uint32, C.c_uint32, C.c_uint32,
@@ -215,6 +217,20 @@ def logw_matrix(model, y, K, c, xl, xr, wl, wr):
     _check(lib.orc_logw_matrix(C.byref(keep.struct), K, _p(keep.y), c, Nl, Nr, _p(xl), _p(xr),
                                _p(wl), _p(wr), _p(out)), "logw_matrix")
     return out
+
+
+def rs_bounds(model, y, K, c, xl, xr, wl, wr):
+    """(finite-set bound, hull bound) of Algorithm 8 for one combination, FP64."""
+    lib = _lib_handle()
+    keep = _Keep(model, K, y)
+    xl = np.ascontiguousarray(xl, np.float64)
+    xr = np.ascontiguousarray(xr, np.float64)
+    wl = np.ascontiguousarray(wl, np.float64)
+    wr = np.ascontiguousarray(wr, np.float64)
+    out = np.zeros(2)
+    _check(lib.orc_rs_bounds(C.byref(keep.struct), K, _p(keep.y), c, wl.shape[0], wr.shape[0], _p(xl),
+                             _p(xr), _p(wl), _p(wr), _p(out)), "rs_bounds")
+    return float(out[0]), float(out[1])
 
 
 def model_logdens(model, y, K, t, xprev, x):

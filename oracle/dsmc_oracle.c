@@ -783,6 +783,46 @@ int orc_logw_matrix(const orc_model* m, int K, const double* y, int c, int Nl, i
   return ORC_OK;
 }
 
+/* The bounds of Algorithm 8 for one combination (reading of the paper): out[0] is the
+ * finite-set bound log f_max + max_i a_i + max_j b'_j with b'_j = wr_j + log h_c(xr_j) -
+ * log nu_c(xr_j); for one-dimensional states out[1] is the hull bound log f_max + max_i a_i
+ * + max_j (b'_j - dist_j^2 / 2Q), dist_j the distance from xr_j to [min_i m_i, max_i m_i],
+ * m_i the transition mean of xl_i (out[1] = out[0] when d > 1). */
+int orc_rs_bounds(const orc_model* m, int K, const double* y, int c, int Nl, int Nr,
+                  const double* xl, const double* xr, const double* wl, const double* wr,
+                  double out[2]) {
+  model_ctx mc;
+  int st = ctx_init(&mc, m, K, y);
+  if (st) return st;
+  const int d = m->d;
+  double amax = -INFINITY, bmax = -INFINITY, hmax = -INFINITY;
+  for (int i = 0; i < Nl; ++i) amax = wl[i] > amax ? wl[i] : amax;
+  double lo = INFINITY, hi = -INFINITY, Q = 0.0;
+  if (d == 1) {
+    const double A = m->kind == 0 ? m->A[0] : m->phi;
+    const double cf = m->kind == 0 ? 0.0 : m->mu * (1.0 - m->phi);
+    Q = m->kind == 0 ? m->Q[0] : m->sigma * m->sigma;
+    for (int i = 0; i < Nl; ++i) {
+      const double mi = A * xl[i] + cf;
+      lo = mi < lo ? mi : lo;
+      hi = mi > hi ? mi : hi;
+    }
+  }
+  for (int j = 0; j < Nr; ++j) {
+    const double* x = xr + (size_t)j * d;
+    const double b = wr[j] + log_h(&mc, c, x) - log_nu(&mc, c, x);
+    bmax = b > bmax ? b : bmax;
+    if (d == 1) {
+      double dist = x[0] > hi ? x[0] - hi : (x[0] < lo ? lo - x[0] : 0.0);
+      const double h = b - dist * dist / (2.0 * Q);
+      hmax = h > hmax ? h : hmax;
+    }
+  }
+  out[0] = log_f_max(&mc) + amax + bmax;
+  out[1] = d == 1 ? log_f_max(&mc) + amax + hmax : out[0];
+  return ORC_OK;
+}
+
 /* log f_max, log h, log nu for tests of the model densities. */
 int orc_model_logdens(const orc_model* m, int K, const double* y, int t, const double* xprev,
                       const double* x, double out[5]) {
