@@ -70,6 +70,21 @@ def test_sizes_and_argument_checks(lib):
     assert e.value.code == 2
 
 
+def test_lazy_samplers_plan_no_dense_buffers(lib):
+    """DSMC_RS and DSMC_MH lift the dense N limit and plan neither tile sums nor
+    tensor-core operands, whatever the precision field says; an unknown sampler is refused."""
+    dsmc, W, hm = _structs()
+    dense = dsmc.dsmc_workspace_size(dsmc.make_config(64, 1024, 1, compute=dsmc.BF16), hm)
+    for res in (dsmc.RS, dsmc.MH):
+        lazy_bf16 = dsmc.dsmc_workspace_size(dsmc.make_config(64, 1024, 1, resampler=res, compute=dsmc.BF16), hm)
+        lazy_fp32 = dsmc.dsmc_workspace_size(dsmc.make_config(64, 1024, 1, resampler=res), hm)
+        assert lazy_bf16 == lazy_fp32 < dense
+        assert dsmc.dsmc_workspace_size(dsmc.make_config(8, 20000, 1, resampler=res), hm) > 0
+    with pytest.raises(dsmc.DsmcError) as e:
+        dsmc.dsmc_workspace_size(dsmc.make_config(8, 64, 1, resampler=3), hm)
+    assert e.value.code == 1
+
+
 def test_invalid_model_rejected(lib):
     dsmc, W, _ = _structs()
     m = W.sv(8)
