@@ -31,6 +31,23 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def build_variant(replacements, out_dir: str) -> str:
+    """Compile a copy of the oracle source with textual replacements [(old, new), ...]
+    (each old text must occur) into out_dir; returns the library path."""
+    src = open(_SRC).read()
+    for old, new in replacements:
+        if old not in src:
+            raise ValueError(f"replacement target not found: {old!r}")
+        src = src.replace(old, new)
+    c_path = os.path.join(out_dir, "oracle_variant.c")
+    so_path = os.path.join(out_dir, "liboracle_variant.so")
+    with open(c_path, "w") as f:
+        f.write(src)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+                           "-o", so_path, c_path, "-lm"])
+    return so_path
+
+
 class Model(C.Structure):
     _fields_ = [("kind", C.c_int), ("d", C.c_int),
                 ("A", C.POINTER(C.c_double)), ("Q", C.POINTER(C.c_double)),
@@ -52,36 +69,74 @@ def _lib_handle():
     global _lib
     with _lock:
         if _lib is None:
-            lib = C.CDLL(build())
-            dp, ip, up = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint32)
-            u64p, fp = C.POINTER(C.c_uint64), C.POINTER(C.c_float)
-            lib.orc_philox4x32_10.argtypes = [up, up, up]
-            lib.orc_philox_many.argtypes = [C.c_int64, up, up, up]
-            lib.orc_init.argtypes = [C.POINTER(Model), C.POINTER(Config), dp, dp, dp, dp, dp]
-            lib.orc_smooth.argtypes = [C.POINTER(Model), C.POINTER(Config), dp, dp, dp, ip, dp, dp,
-                                       dp, dp, dp, u64p]
-            lib.orc_logw_matrix.argtypes = [C.POINTER(Model), C.c_int, dp, C.c_int, C.c_int, C.c_int,
-                                            dp, dp, dp, dp, dp]
-            lib.orc_model_logdens.argtypes = [C.POINTER(Model), C.c_int, dp, C.c_int, dp, dp, dp]
-            lib.orc_num_levels.argtypes = [C.c_int]
-            lib.orc_merges_at_level.argtypes = [C.c_int, C.c_int]
-            lib.orc_dense_pairs.argtypes = [C.c_int, dp, C.c_uint32, C.c_uint32, C.c_uint32,
-                                            C.c_uint32, C.c_int, C.c_int, ip, ip]
-            lib.orc_rs_pairs.argtypes = [C.c_int, dp, C.c_double, C.c_uint32, C.c_uint32, C.c_uint32,
-                                         C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip, u64p]
-            lib.orc_kp_dense_pairs.argtypes = [C.c_int, C.c_int, fp, fp, fp, C.c_uint32,
-                                               C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, C.c_int,
-                                               ip, ip]
-            lib.orc_kp_rs_pairs.argtypes = [C.c_int, fp, C.c_uint32, C.c_uint32, C.c_uint32,
-                                            C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip, up]
-            lib.orc_rs_bounds.argtypes = [C.POINTER(Model), C.c_int, dp, C.c_int, C.c_int, C.c_int,
-                                          dp, dp, dp, dp, dp]
-            lib.orc_mh_pairs.argtypes = [C.c_int, dp, C.c_uint32, C.c_uint32, C.c_uint32,
-                                         C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip]
-            lib.orc_kp_mh_pairs.argtypes = [C.c_int, fp, C.c_uint32, C.c_uint32, C.c_uint32,
-                                            C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip]
-            _lib = lib
+            _lib = _setup(C.CDLL(build()))
     return _lib
+
+
+def load_variant(path: str):
+    """A separately compiled copy of the oracle (tests plant mistakes in such copies to show
+    that a pin rejects them); use it through ``variant``."""
+    return _setup(C.CDLL(path))
+
+
+class variant:
+    """Context manager: the module's functions call the given oracle library inside it."""
+
+    def __init__(self, lib):
+        self.lib = lib
+
+    def __enter__(self):
+        global _lib
+        _lib_handle()
+        self.saved = _lib
+        _lib = self.lib
+        return self.lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def _setup(lib):
+    """Argument types of the oracle's exported functions."""
+    dp, ip, up = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint32)
+    u64p, fp = C.POINTER(C.c_uint64), C.POINTER(C.c_float)
+    lib.orc_philox4x32_10.argtypes = [up, up, up]
+    lib.orc_philox_many.argtypes = [C.c_int64, up, up, up]
+    lib.orc_init.argtypes = [C.POINTER(Model), C.POINTER(Config), dp, dp, dp, dp, dp]
+    lib.orc_smooth.argtypes = [C.POINTER(Model), C.POINTER(Config), dp, dp, dp, ip, dp, dp,
+                               dp, dp, dp, u64p]
+    lib.orc_logw_matrix.argtypes = [C.POINTER(Model), C.c_int, dp, C.c_int, C.c_int, C.c_int,
+                                    dp, dp, dp, dp, dp]
+    lib.orc_model_logdens.argtypes = [C.POINTER(Model), C.c_int, dp, C.c_int, dp, dp, dp]
+    lib.orc_num_levels.argtypes = [C.c_int]
+    lib.orc_merges_at_level.argtypes = [C.c_int, C.c_int]
+    lib.orc_dense_pairs.argtypes = [C.c_int, dp, C.c_uint32, C.c_uint32, C.c_uint32,
+                                    C.c_uint32, C.c_int, C.c_int, ip, ip]
+    lib.orc_rs_pairs.argtypes = [C.c_int, dp, C.c_double, C.c_uint32, C.c_uint32, C.c_uint32,
+                                 C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip, u64p]
+    lib.orc_kp_dense_pairs.argtypes = [C.c_int, C.c_int, fp, fp, fp, C.c_uint32,
+                                       C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, C.c_int,
+                                       ip, ip]
+    lib.orc_kp_rs_pairs.argtypes = [C.c_int, fp, C.c_uint32, C.c_uint32, C.c_uint32,
+                                    C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip, up]
+    lib.orc_rs_bounds.argtypes = [C.POINTER(Model), C.c_int, dp, C.c_int, C.c_int, C.c_int,
+                                  dp, dp, dp, dp, dp]
+    lib.orc_mh_pairs.argtypes = [C.c_int, dp, C.c_uint32, C.c_uint32, C.c_uint32,
+                                 C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip]
+    lib.orc_kp_mh_pairs.argtypes = [C.c_int, fp, C.c_uint32, C.c_uint32, C.c_uint32,
+                                    C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip]
+    lib.orc_sys_pairs.argtypes = [C.c_int, dp, C.c_uint32, C.c_uint32, C.c_uint32,
+                                  C.c_uint32, C.c_int, C.c_int, ip, ip]
+    lib.orc_kp_sys_pairs.argtypes = [C.c_int, C.c_int, fp, fp, fp, C.c_uint32,
+                                     C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, C.c_int,
+                                     ip, ip]
+    lib.orc_rsf_pairs.argtypes = [C.c_int, dp, dp, dp, C.c_uint32, C.c_uint32, C.c_uint32,
+                                  C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip, u64p]
+    lib.orc_kp_rsf_pairs.argtypes = [C.c_int, fp, fp, fp, C.c_uint32, C.c_uint32, C.c_uint32,
+                                     C.c_uint32, C.c_int, C.c_int, C.c_uint32, ip, ip, up]
+    return lib
 
 
 def _p(a, ctype=C.c_double):
@@ -164,11 +219,15 @@ def init(model, y, K, N, seed, counter_base=0, x_ref=None):
     return X, lw, lL
 
 
+RESAMPLERS = {"dense": 0, "rs": 1, "mh": 2, "systematic": 3, "rsf": 4}
+
+
 def smooth(model, y, K, N, seed, counter_base=0, resampler="dense", rs_max_attempts=1 << 20,
            x_ref=None, want_traj=False, want_pairs=False):
     """Full dSMC smoother: Algorithm 2, then Algorithm 6 over Combine (Algorithm 1) or
-    ConditionalCombine (Algorithm 5), with multinomial, rejection (Algorithm 8) or
-    Metropolis-Hastings (Algorithm 7, B = rs_max_attempts steps) draws.
+    ConditionalCombine (Algorithm 5), with multinomial, systematic, rejection (Algorithm 8,
+    uniform or factorised pair proposals) or Metropolis-Hastings (Algorithm 7,
+    B = rs_max_attempts steps) draws.
 
     Returns a dict with mean [K][d], m2 [K][d], logL, and optionally traj [K][N][d],
     pairs [K-1][2][N], X_leaf [K][N][d], x_star [K][d], rs_attempts, status."""
@@ -176,8 +235,7 @@ def smooth(model, y, K, N, seed, counter_base=0, resampler="dense", rs_max_attem
     keep = _Keep(model, K, y)
     lo, hi = _seed_words(seed)
     cond = x_ref is not None
-    cf = Config(K, N, lo, hi, counter_base, {"dense": 0, "rs": 1, "mh": 2}[resampler], rs_max_attempts,
-                1 if cond else 0)
+    cf = Config(K, N, lo, hi, counter_base, RESAMPLERS[resampler], rs_max_attempts, 1 if cond else 0)
     d = model.d
     mean = np.zeros((K, d))
     m2 = np.zeros((K, d))
@@ -328,4 +386,68 @@ def kp_rs_pairs(ratio, seed, gid, n0, n1, max_attempts=1 << 20, counter_base=0):
     st = _check(lib.orc_kp_rs_pairs(N, _p(q, C.c_float), lo, hi, counter_base, gid, n0, n1,
                                     max_attempts, _p(li, C.c_int32), _p(ri, C.c_int32),
                                     _p(att, C.c_uint32)), "kp_rs_pairs")
+    return li, ri, att, st
+
+
+def sys_pairs(logW, seed, gid, n0, n1, counter_base=0):
+    """Systematic draws (positions (k + U) / N of the flattened CDF) for slots [n0, n1)."""
+    lib = _lib_handle()
+    W = np.ascontiguousarray(logW, np.float64)
+    N = W.shape[0]
+    li = np.zeros(n1 - n0, np.int32)
+    ri = np.zeros(n1 - n0, np.int32)
+    lo, hi = _seed_words(seed)
+    _check(lib.orc_sys_pairs(N, _p(W), lo, hi, counter_base, gid, n0, n1, _p(li, C.c_int32),
+                             _p(ri, C.c_int32)), "sys_pairs")
+    return li, ri
+
+
+def kp_sys_pairs(r, t, e, B, seed, gid, n0, n1, counter_base=0):
+    """Device-precision systematic three-stage sampler on the device's own FP32 weights."""
+    lib = _lib_handle()
+    r = np.ascontiguousarray(r, np.float32)
+    t = np.ascontiguousarray(t, np.float32)
+    e = np.ascontiguousarray(e, np.float32)
+    N = r.shape[0]
+    li = np.zeros(n1 - n0, np.int32)
+    ri = np.zeros(n1 - n0, np.int32)
+    lo, hi = _seed_words(seed)
+    _check(lib.orc_kp_sys_pairs(N, B, _p(r, C.c_float), _p(t, C.c_float), _p(e, C.c_float), lo, hi,
+                                counter_base, gid, n0, n1, _p(li, C.c_int32), _p(ri, C.c_int32)),
+           "kp_sys_pairs")
+    return li, ri
+
+
+def rsf_pairs(la, lc, lacc, seed, gid, n0, n1, max_attempts=1 << 20, counter_base=0):
+    """Rejection draws with factorised proposals (rows by exp(la), columns by exp(lc),
+    acceptance exp(lacc) <= 1) for slots [n0, n1), FP64."""
+    lib = _lib_handle()
+    la = np.ascontiguousarray(la, np.float64)
+    lc = np.ascontiguousarray(lc, np.float64)
+    A = np.ascontiguousarray(lacc, np.float64)
+    N = la.shape[0]
+    li = np.zeros(n1 - n0, np.int32)
+    ri = np.zeros(n1 - n0, np.int32)
+    att = np.zeros(1, np.uint64)
+    lo, hi = _seed_words(seed)
+    st = _check(lib.orc_rsf_pairs(N, _p(la), _p(lc), _p(A), lo, hi, counter_base, gid, n0, n1, max_attempts,
+                                  _p(li, C.c_int32), _p(ri, C.c_int32), _p(att, C.c_uint64)), "rsf_pairs")
+    return li, ri, int(att[0]), st
+
+
+def kp_rsf_pairs(ra, rc, acc, seed, gid, n0, n1, max_attempts=1 << 20, counter_base=0):
+    """Device-precision factorised-proposal rejection sampler on the device's own FP32 row
+    and column proposal weights and acceptance ratios."""
+    lib = _lib_handle()
+    ra = np.ascontiguousarray(ra, np.float32)
+    rc = np.ascontiguousarray(rc, np.float32)
+    A = np.ascontiguousarray(acc, np.float32)
+    N = ra.shape[0]
+    li = np.zeros(n1 - n0, np.int32)
+    ri = np.zeros(n1 - n0, np.int32)
+    att = np.zeros(n1 - n0, np.uint32)
+    lo, hi = _seed_words(seed)
+    st = _check(lib.orc_kp_rsf_pairs(N, _p(ra, C.c_float), _p(rc, C.c_float), _p(A, C.c_float), lo, hi,
+                                     counter_base, gid, n0, n1, max_attempts, _p(li, C.c_int32),
+                                     _p(ri, C.c_int32), _p(att, C.c_uint32)), "kp_rsf_pairs")
     return li, ri, att, st

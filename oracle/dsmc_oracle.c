@@ -44,6 +44,9 @@
 #define ORC_PURPOSE_DENSE 2u
 #define ORC_PURPOSE_RS 3u
 #define ORC_PURPOSE_MH 4u
+#define ORC_PURPOSE_SYS 5u
+#define ORC_PURPOSE_RSF 6u
+#define ORC_PURPOSE_RSU 7u
 
 #define ORC_OK 0
 #define ORC_ERR_INVALID 1
@@ -126,7 +129,9 @@ typedef struct {
   int K, N;
   uint32_t seed_lo, seed_hi, counter_base;
   int resampler; /* 0: multinomial inverse CDF on the full N x N matrix; 1: rejection
-                    (Algorithm 8); 2: Metropolis-Hastings (Algorithm 7) */
+                    (Algorithm 8); 2: Metropolis-Hastings (Algorithm 7); 3: systematic
+                    inverse CDF on the full matrix (multinomial when conditional);
+                    4: rejection with factorised pair proposals */
   uint32_t rs_max_attempts;
   int conditional;
 } orc_config;
@@ -390,6 +395,23 @@ static void dense_draws(int N, const double* E, const double* C, uint32_t seed_l
   }
 }
 
+/* Systematic pair draws for slots [n0, n1) (Algorithm 1 names systematic resampling beside
+ * multinomial): one uniform U per combination, u53 of the counter (0, gid, SYS | base<<4, 0),
+ * and slot k takes the positions (k + U) / N of the row-major flattened matrix's CDF. */
+static void systematic_draws(int N, const double* E, const double* C, uint32_t seed_lo,
+                             uint32_t seed_hi, uint32_t base, uint32_t gid, int n0, int n1,
+                             int32_t* li, int32_t* ri) {
+  int64_t NN = (int64_t)N * N;
+  uint32_t w[4];
+  draw(seed_lo, seed_hi, 0u, gid, ORC_PURPOSE_SYS, base, 0u, w);
+  const double U = u53(w[0], w[1]);
+  for (int n = n0; n < n1; ++n) {
+    int64_t f = inverse_cdf(C, E, NN, ((double)n + U) / (double)N);
+    li[n - n0] = (int32_t)(f / N);
+    ri[n - n0] = (int32_t)(f % N);
+  }
+}
+
 /* Rejection draws (Algorithm 8) for slots [n0, n1) given the log-weights logW[i][j] and a
  * bound logbar >= max logW: per attempt (I, J, u) = (w0 N >> 32, w1 N >> 32, u23(w2)) from
  * the counter (n, gid, RS | base<<4, attempt); accept when u < exp(logW_IJ - logbar).
@@ -418,6 +440,46 @@ static int rs_draws(int N, pair_logw_fn fn, const void* ctx, double logbar, uint
   return status;
 }
 
+/* Rejection draws with factorised pair proposals (the future-work item of the paper's
+ * discussion: propose pairs by their a-priori weights).  The target log-weight of a pair is
+ * la[i] + lc[j] + lacc(i, j) with lacc <= 0; the proposal draws I with probability
+ * proportional to exp(la[i]) and J proportional to exp(lc[j]), independently, by inverse CDF
+ * on u53 uniforms of the counter (n, gid, RSF | base<<4, attempt) (words 0-1 for I, 2-3 for
+ * J), and accepts when u < exp(lacc(I, J)), u = u23 of word 0 of the counter
+ * (n, gid, RSU | base<<4, attempt).  Accepted pairs follow the target exactly; the expected
+ * number of attempts is sum_i e^la_i sum_j e^lc_j / sum_ij e^(la_i + lc_j + lacc_ij). */
+static int rsf_draws(int N, const double* la, const double* lc, pair_logw_fn lacc, const void* ctx,
+                     uint32_t seed_lo, uint32_t seed_hi, uint32_t base, uint32_t gid, int n0, int n1,
+                     uint32_t max_attempts, int32_t* li, int32_t* ri, uint64_t* attempts) {
+  double *EA = (double*)malloc(sizeof(double) * N), *CA = (double*)malloc(sizeof(double) * N);
+  double *EC = (double*)malloc(sizeof(double) * N), *CC = (double*)malloc(sizeof(double) * N);
+  if (!EA || !CA || !EC || !CC) { free(EA); free(CA); free(EC); free(CC); return ORC_ERR_OOM; }
+  double ma = -INFINITY, mc = -INFINITY, sa = 0.0, sc = 0.0;
+  for (int i = 0; i < N; ++i) ma = la[i] > ma ? la[i] : ma;
+  for (int j = 0; j < N; ++j) mc = lc[j] > mc ? lc[j] : mc;
+  for (int i = 0; i < N; ++i) { EA[i] = exp(la[i] - ma); sa += EA[i]; CA[i] = sa; }
+  for (int j = 0; j < N; ++j) { EC[j] = exp(lc[j] - mc); sc += EC[j]; CC[j] = sc; }
+  int status = ORC_OK;
+  for (int n = n0; n < n1; ++n) {
+    uint32_t att;
+    int I = 0, J = 0, ok = 0;
+    for (att = 0; att < max_attempts; ++att) {
+      uint32_t w[4], v[4];
+      draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_RSF, base, att, w);
+      draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_RSU, base, att, v);
+      I = (int)inverse_cdf(CA, EA, N, u53(w[0], w[1]));
+      J = (int)inverse_cdf(CC, EC, N, u53(w[2], w[3]));
+      if (u23(v[0]) < exp(lacc(ctx, I, J))) { ok = 1; ++att; break; }
+    }
+    if (!ok) status = ORC_ERR_RS_LIMIT;
+    if (attempts) *attempts += att;
+    li[n - n0] = I;
+    ri[n - n0] = J;
+  }
+  free(EA); free(CA); free(EC); free(CC);
+  return status;
+}
+
 typedef struct {
   const model_ctx* mc;
   const double *Zl, *Zr, *wl, *bcol;
@@ -437,6 +499,49 @@ typedef struct {
 static double mat_logw(const void* p, int i, int j) {
   const mat_ctx* m = (const mat_ctx*)p;
   return m->W[(size_t)i * m->N + j];
+}
+
+/* The factorised sampler's log acceptance for the model: log p_c(xr_J | xl_I) - log f_max,
+ * plus dist_J^2 / 2Q for one-dimensional states (the column factor took the hull term out). */
+typedef struct {
+  const model_ctx* mc;
+  const double *Zl, *Zr, *dist;
+  double lfmax, halfQi;
+  int d;
+} rsf_ctx;
+
+static double rsf_model_lacc(const void* p, int i, int j) {
+  const rsf_ctx* r = (const rsf_ctx*)p;
+  double v = log_f(r->mc, r->Zl + (size_t)i * r->d, r->Zr + (size_t)j * r->d) - r->lfmax;
+  if (r->dist) v += r->halfQi * r->dist[j] * r->dist[j];
+  return v;
+}
+
+/* Exported for the sampler tests: factorised-proposal rejection draws for slots [n0, n1)
+ * from row and column log-weights la, lc [N] and log acceptances lacc [N][N] (<= 0). */
+int orc_rsf_pairs(int N, const double* la, const double* lc, const double* lacc, uint32_t seed_lo,
+                  uint32_t seed_hi, uint32_t base, uint32_t gid, int n0, int n1, uint32_t max_attempts,
+                  int32_t* li, int32_t* ri, uint64_t* attempts) {
+  mat_ctx m = {lacc, N};
+  return rsf_draws(N, la, lc, mat_logw, &m, seed_lo, seed_hi, base, gid, n0, n1, max_attempts, li, ri,
+                   attempts);
+}
+
+/* Exported for the sampler tests: systematic draws from a given FP64 log-weight matrix. */
+int orc_sys_pairs(int N, const double* logW, uint32_t seed_lo, uint32_t seed_hi, uint32_t base,
+                  uint32_t gid, int n0, int n1, int32_t* li, int32_t* ri) {
+  int64_t NN = (int64_t)N * N;
+  double* E = (double*)malloc(sizeof(double) * NN);
+  double* C = (double*)malloc(sizeof(double) * NN);
+  if (!E || !C) { free(E); free(C); return ORC_ERR_OOM; }
+  double M = -INFINITY;
+  for (int64_t f = 0; f < NN; ++f) M = logW[f] > M ? logW[f] : M;
+  double S = 0.0;
+  for (int64_t f = 0; f < NN; ++f) { E[f] = exp(logW[f] - M); S += E[f]; C[f] = S; }
+  systematic_draws(N, E, C, seed_lo, seed_hi, base, gid, n0, n1, li, ri);
+  free(E);
+  free(C);
+  return ORC_OK;
 }
 
 /* Exported for the sampler tests: dense multinomial draws from a given FP64 log-weight
@@ -557,7 +662,7 @@ static int combine(const model_ctx* mc, const orc_config* cf, blocks* B, int a, 
   double inc;
   if (!li || !ri) { free(li); free(ri); return ORC_ERR_OOM; }
 
-  if (cf->resampler == 0) {
+  if (cf->resampler == 0 || cf->resampler == 3) {
     int64_t NN = (int64_t)N * N;
     double* W = (double*)malloc(sizeof(double) * NN);
     double* C = (double*)malloc(sizeof(double) * NN);
@@ -583,8 +688,12 @@ static int combine(const model_ctx* mc, const orc_config* cf, blocks* B, int a, 
       C[f] = S;
     }
     inc = M + log(S);
-    dense_draws(N, W, C, cf->seed_lo, cf->seed_hi, cf->counter_base, (uint32_t)gid, n0, nslots,
-                li + n0, ri + n0);
+    if (cf->resampler == 3 && !cf->conditional)  /* conditional combinations stay multinomial */
+      systematic_draws(N, W, C, cf->seed_lo, cf->seed_hi, cf->counter_base, (uint32_t)gid, n0, nslots,
+                       li + n0, ri + n0);
+    else
+      dense_draws(N, W, C, cf->seed_lo, cf->seed_hi, cf->counter_base, (uint32_t)gid, n0, nslots,
+                  li + n0, ri + n0);
     free(W);
     free(C);
   } else {
@@ -603,7 +712,38 @@ static int combine(const model_ctx* mc, const orc_config* cf, blocks* B, int a, 
     }
     double logbar = log_f_max(mc) + amax + bmax;
     rs_ctx rc = {mc, B->Z + (size_t)(c - 1) * N * d, B->Z + (size_t)c * N * d, wl, bcol, d};
-    if (cf->resampler == 2)
+    if (cf->resampler == 4) {
+      /* factorised proposals: rows by the left weights, columns by b'_j (for d = 1 less
+       * dist_j^2 / 2Q, dist_j the distance from xr_j to the hull of the transition means of
+       * the left block's end states), acceptance f / f_max (times e^{dist_j^2 / 2Q}) */
+      double* lc = (double*)malloc(sizeof(double) * N);
+      double* dist = d == 1 ? (double*)malloc(sizeof(double) * N) : NULL;
+      if (!lc || (d == 1 && !dist)) { free(lc); free(dist); free(bcol); free(li); free(ri); return ORC_ERR_OOM; }
+      double halfQi = 0.0;
+      if (d == 1) {
+        const orc_model* m = mc->m;
+        const double A = m->kind == 0 ? m->A[0] : m->phi;
+        const double cc = m->kind == 0 ? 0.0 : m->mu * (1.0 - m->phi);
+        const double Q = m->kind == 0 ? m->Q[0] : m->sigma * m->sigma;
+        halfQi = 0.5 / Q;
+        double lo = INFINITY, hi = -INFINITY;
+        for (int i = 0; i < N; ++i) {
+          const double mi = A * B->Z[(size_t)(c - 1) * N + i] + cc;
+          lo = mi < lo ? mi : lo;
+          hi = mi > hi ? mi : hi;
+        }
+        for (int j = 0; j < N; ++j) {
+          const double x = B->Z[(size_t)c * N + j];
+          dist[j] = x > hi ? x - hi : (x < lo ? lo - x : 0.0);
+        }
+      }
+      for (int j = 0; j < N; ++j) lc[j] = bcol[j] - (d == 1 ? halfQi * dist[j] * dist[j] : 0.0);
+      rsf_ctx fc = {mc, B->Z + (size_t)(c - 1) * N * d, B->Z + (size_t)c * N * d, dist, log_f_max(mc), halfQi, d};
+      status = rsf_draws(N, wl, lc, rsf_model_lacc, &fc, cf->seed_lo, cf->seed_hi, cf->counter_base,
+                         (uint32_t)gid, n0, nslots, cf->rs_max_attempts, li + n0, ri + n0, attempts);
+      free(lc);
+      free(dist);
+    } else if (cf->resampler == 2)
       mh_draws(N, rs_model_logw, &rc, cf->seed_lo, cf->seed_hi, cf->counter_base, (uint32_t)gid, n0,
                nslots, cf->rs_max_attempts ? cf->rs_max_attempts : 64u, li + n0, ri + n0);
     else
@@ -973,9 +1113,121 @@ int orc_kp_rs_pairs(int N, const float* ratio, uint32_t seed_lo, uint32_t seed_h
       if (u < ratio[(size_t)I * N + J]) { ok = 1; ++a; break; }
     }
     if (!ok) status = ORC_ERR_RS_LIMIT;
-    li[n - n0] = I;
-    ri[n - n0] = J;
+    li[n - n0] = ok ? I : -1;  /* a slot that hit the cap keeps no index */
+    ri[n - n0] = ok ? J : -1;
     attempts[n - n0] = a;
   }
+  return status;
+}
+
+/* Systematic variant of the three-stage sampler (same inputs and images as
+ * orc_kp_dense_pairs).  One 64-bit uniform U per combination (words 0-1 of the counter
+ * (0, gid, SYS | base<<4, 0)) gives V = floor(U S / 2^64); slot k takes the row target
+ * T_k = floor((k S + V) / N) = k q + floor((k r + V) / N), S = q N + r (exact integers);
+ * the remainder of T_k inside its row, as a fraction of the row's fixed-point weight, is the
+ * uniform word of the tile stage, w2 = trunc((T_k - cum_{i-1}) / Rq_i 2^32) (FP64 quotient,
+ * correctly rounded), and the remainder of the tile target inside its tile, as a fraction
+ * of the tile's image, the word of the column stage.  Each slot's position in the flattened
+ * fixed-point CDF moves by S / N from slot to slot. */
+static int fixed_pick_rem(const uint64_t* q, int n, uint32_t w, uint32_t* wnext) {
+  uint64_t Q = 0;
+  for (int k = 0; k < n; ++k) Q += q[k];
+  if (Q == 0) { *wnext = w; return 0; }
+  uint64_t T = mulhi64((uint64_t)w << 32, Q);
+  uint64_t c = 0, before = 0;
+  int idx = 0;
+  for (int k = 0; k < n; ++k) {
+    c += q[k];
+    if (c <= T) { idx = k + 1; before = c; }
+  }
+  if (idx > n - 1) idx = n - 1;
+  *wnext = q[idx] ? (uint32_t)(((double)(T - before) / (double)q[idx]) * 4294967296.0) : 0u;
+  return idx;
+}
+
+int orc_kp_sys_pairs(int N, int B, const float* r, const float* t, const float* e,
+                     uint32_t seed_lo, uint32_t seed_hi, uint32_t base,
+                     uint32_t gid, int n0, int n1, int32_t* li, int32_t* ri) {
+  int nT = (N + B - 1) / B;
+  uint64_t* cum = (uint64_t*)malloc(sizeof(uint64_t) * N);
+  uint64_t* q = (uint64_t*)malloc(sizeof(uint64_t) * (nT > B ? nT : B));
+  if (!cum || !q) { free(cum); free(q); return ORC_ERR_OOM; }
+  uint64_t S = 0;
+  for (int i = 0; i < N; ++i) {
+    S += row_quant(r[i]);
+    cum[i] = S;
+  }
+  if (S == 0) { free(cum); free(q); return ORC_ERR_DEGENERATE; }
+  uint32_t w0[4];
+  draw(seed_lo, seed_hi, 0u, gid, ORC_PURPOSE_SYS, base, 0u, w0);
+  const uint64_t V = mulhi64(((uint64_t)w0[0] << 32) | (uint64_t)w0[1], S);
+  const uint64_t qq = S / (uint64_t)N, rr = S % (uint64_t)N;
+  for (int n = n0; n < n1; ++n) {
+    const uint64_t k = (uint64_t)n;
+    const uint64_t T = k * qq + (k * rr + V) / (uint64_t)N;
+    int i = 0;
+    while (i < N - 1 && cum[i] <= T) ++i;
+    const uint64_t prev = i ? cum[i - 1] : 0;
+    const uint32_t w2 = (uint32_t)(((double)(T - prev) / (double)(cum[i] - prev)) * 4294967296.0);
+    const float* ti = t + (size_t)i * nT;
+    float tmax = 0.0f;
+    for (int kk = 0; kk < nT; ++kk) tmax = ti[kk] > tmax ? ti[kk] : tmax;
+    int rbe = ref_exponent(tmax);
+    for (int kk = 0; kk < nT; ++kk) q[kk] = q24(ti[kk], rbe);
+    uint32_t w3;
+    int kt = fixed_pick_rem(q, nT, w2, &w3);
+    int j0 = kt * B;
+    int width = (j0 + B <= N) ? B : N - j0;
+    int tbe = ref_exponent(ti[kt]);
+    for (int j = 0; j < width; ++j) q[j] = q24(e[(size_t)i * N + j0 + j], tbe);
+    li[n - n0] = i;
+    ri[n - n0] = j0 + fixed_pick(q, width, w3);
+  }
+  free(cum);
+  free(q);
+  return ORC_OK;
+}
+
+/* Factorised-proposal rejection sampler in the device's precision: ra [N] and rc [N] are the
+ * device's FP32 row and column proposal weights (relative to their maxima, in [0, 1]), acc
+ * [N][N] its FP32 acceptance ratios.  Proposal images Rq = trunc(ra 2^40), Cq = trunc(rc
+ * 2^40) with exact prefix sums; per attempt I = #{cumA <= floor(U1 SA / 2^64)} with U1 =
+ * words 0-1 of the counter (n, gid, RSF | base<<4, attempt), J likewise from words 2-3 and
+ * SC, and the pair is accepted when u < acc[I][J] in FP32, u = u23 of word 0 of the counter
+ * (n, gid, RSU | base<<4, attempt).  A slot that reaches max_attempts keeps the index -1. */
+int orc_kp_rsf_pairs(int N, const float* ra, const float* rc, const float* acc, uint32_t seed_lo,
+                     uint32_t seed_hi, uint32_t base, uint32_t gid, int n0, int n1,
+                     uint32_t max_attempts, int32_t* li, int32_t* ri, uint32_t* attempts) {
+  uint64_t* cA = (uint64_t*)malloc(sizeof(uint64_t) * N);
+  uint64_t* cC = (uint64_t*)malloc(sizeof(uint64_t) * N);
+  if (!cA || !cC) { free(cA); free(cC); return ORC_ERR_OOM; }
+  uint64_t SA = 0, SC = 0;
+  for (int i = 0; i < N; ++i) { SA += row_quant(ra[i]); cA[i] = SA; }
+  for (int j = 0; j < N; ++j) { SC += row_quant(rc[j]); cC[j] = SC; }
+  if (SA == 0 || SC == 0) { free(cA); free(cC); return ORC_ERR_DEGENERATE; }
+  int status = ORC_OK;
+  for (int n = n0; n < n1; ++n) {
+    uint32_t a;
+    int I = 0, J = 0, ok = 0;
+    for (a = 0; a < max_attempts; ++a) {
+      uint32_t w[4], v[4];
+      draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_RSF, base, a, w);
+      draw(seed_lo, seed_hi, (uint32_t)n, gid, ORC_PURPOSE_RSU, base, a, v);
+      const uint64_t TA = mulhi64(((uint64_t)w[0] << 32) | (uint64_t)w[1], SA);
+      const uint64_t TC = mulhi64(((uint64_t)w[2] << 32) | (uint64_t)w[3], SC);
+      I = 0;
+      while (I < N - 1 && cA[I] <= TA) ++I;
+      J = 0;
+      while (J < N - 1 && cC[J] <= TC) ++J;
+      const float u = (float)u23(v[0]);
+      if (u < acc[(size_t)I * N + J]) { ok = 1; ++a; break; }
+    }
+    if (!ok) status = ORC_ERR_RS_LIMIT;
+    li[n - n0] = ok ? I : -1;
+    ri[n - n0] = ok ? J : -1;
+    attempts[n - n0] = a;
+  }
+  free(cA);
+  free(cC);
   return status;
 }

@@ -55,6 +55,22 @@ def test_dsmc_rejection_matches_rts():
     _check_against(_seed_means(wl.model, wl.y, wl.K, wl.N, 48, resampler="rs"), ms)
 
 
+@pytest.mark.parametrize("resampler", ["systematic", "rsf"])
+def test_dsmc_systematic_and_factorised_match_rts(resampler):
+    """Systematic positions and rejection with factorised proposals target the same smoother."""
+    wl = W.workload("lgssm_1d", K=17, N=64)
+    ms, _, _ = kalman.rts_for(wl.model, wl.y)
+    _check_against(_seed_means(wl.model, wl.y, wl.K, wl.N, 48, resampler=resampler), ms)
+
+
+def test_dsmc_factorised_sv_matches_grid():
+    K, N = 24, 256
+    m = W.sv(K)
+    _, y = W.simulate(m, K, 2264 + 3)
+    gm, _, _ = grid.sv_grid_smoother(m.mu, m.phi, m.sigma, y[:, 0])
+    _check_against(_seed_means(m, y, K, N, 32, resampler="rsf"), gm[:, None])
+
+
 def test_dsmc_metropolis_hastings_near_rts():
     """Algorithm 7 is biased for finite B; with B = 256 steps per slot its seed-averaged means
     sit within a small multiple of the dense sampler's distance from the RTS means."""
@@ -67,7 +83,7 @@ def test_dsmc_metropolis_hastings_near_rts():
     assert e_mh < 2.0 * e_de + 0.02, (e_mh, e_de)
 
 
-@pytest.mark.parametrize("resampler", ["dense", "rs", "mh"])
+@pytest.mark.parametrize("resampler", ["dense", "rs", "mh", "systematic", "rsf"])
 def test_output_values_are_leaf_particles(resampler):
     """Every output trajectory takes, at each time t, one of the N particles drawn at t (the
     stitching of Algorithm 1 only selects), for every sampler; K = 11 has pass-through blocks."""
