@@ -51,14 +51,16 @@ typedef enum {
   DSMC_ERR_NONFINITE = 6,    /* device: a log-weight was NaN */
   DSMC_ERR_DEGENERATE = 7,   /* device: every weight of a combination was zero */
   DSMC_ERR_RS_LIMIT = 8,     /* device: a rejection-sampling slot hit rs_max_attempts */
-  DSMC_ERR_TIMEOUT = 9       /* device: a bounded wait gave up */
+  DSMC_ERR_TIMEOUT = 9,      /* device: a bounded wait gave up */
+  DSMC_ERR_BOUND = 10        /* device: a lazy sampler met a pair above its bound by more
+                                than FP32 rounding (ratio > 1 + 2^-10): a broken bound */
 } dsmc_status_t;
 
 enum { DSMC_MODEL_LGSSM = 0, DSMC_MODEL_SV = 1 };
 enum { DSMC_PROP_OBS = 0, DSMC_PROP_GAUSS = 1 };
 enum { DSMC_NU_EQ_Q = 0, DSMC_NU_PROP_H = 1 };
 enum { DSMC_FP32 = 0, DSMC_TF32 = 1, DSMC_BF16 = 2 };
-enum { DSMC_MULTINOMIAL = 0, DSMC_RS = 1, DSMC_MH = 2 };
+enum { DSMC_MULTINOMIAL = 0, DSMC_RS = 1, DSMC_MH = 2, DSMC_SYSTEMATIC = 3, DSMC_RS_FACTORED = 4 };
 
 /* The state-space model of Eq. (ssm) (Section 1).  All arrays are HOST, row-major, FP64,
  * read during the call only.
@@ -98,27 +100,57 @@ typedef struct {
                                  cores: the whole base-2 exponent alpha_i + beta_j + u_i.v_j
                                  is one MMA, alpha and beta entering as two-term splits in
                                  the MMA type; FP32 accumulate, exp and sums; dense N <= 4096.
-                                 Ignored by the lazy samplers (DSMC_RS, DSMC_MH), which
-                                 evaluate their proposed pairs in FP32 */
-  int resampler;              /* DSMC_MULTINOMIAL (dense, Algorithm 1) or DSMC_RS (Alg. 8:
-                                 uniform pair proposals accepted with probability
-                                 omega_ij / omega-bar, omega-bar = f_max e^{max_i a_i} max_j
-                                 e^{b'_j}; for dx = 1 the factor of column j is tightened to
-                                 e^{b'_j - dist_j^2 / 2Q}, dist_j the distance from x_j to the
-                                 hull of the transition means A x_i + c of the time-(c-1)
-                                 particles); or DSMC_MH (Algorithm 7: per slot, B Metropolis-
-                                 Hastings steps from (n mod N, n mod N) with uniform pair
-                                 proposals, accepted iff u r(I,J) < r(I*,J*) in FP32, r the
-                                 pair's ratio omega / omega-bar; biased for finite B) */
+                                 Ignored by the lazy samplers (DSMC_RS, DSMC_RS_FACTORED,
+                                 DSMC_MH), which evaluate their proposed pairs in FP32 */
+  int resampler;              /* how a combination draws its N pairs:
+                                 DSMC_MULTINOMIAL (Algorithm 1): N independent draws from the
+                                 normalised N x N weights, by the exact three-stage
+                                 fixed-point inverse CDF (row, tile, column);
+                                 DSMC_SYSTEMATIC (Algorithm 1's systematic option): the same
+                                 stages at the positions (k + U) / N of the flattened CDF, one
+                                 uniform U per combination (conditional combinations stay
+                                 multinomial, Algorithm 5);
+                                 DSMC_RS (Algorithm 8): uniform pair proposals accepted with
+                                 probability omega_ij / omega-bar, omega-bar = f_max
+                                 e^{max_i a_i} max_j e^{b'_j} (for dx = 1 the factor of column
+                                 j is tightened to e^{b'_j - dist_j^2 / 2Q}, dist_j the distance
+                                 from x_j to the hull of the transition means A x_i + c of the
+                                 time-(c-1) particles);
+                                 DSMC_RS_FACTORED (rejection with factorised proposals, the
+                                 future-work item of the paper's discussion): row i proposed
+                                 with probability proportional to e^{a_i}, column j to
+                                 e^{b'_j} (times e^{-dist_j^2 / 2Q} for dx = 1), accepted
+                                 with probability f(x_j | x_i) / f_max (times
+                                 e^{dist_j^2 / 2Q}): the same target, with the expected
+                                 attempts divided by the spread of the leaf and observation
+                                 weights;
+                                 DSMC_MH (Algorithm 7): per slot, B Metropolis-Hastings steps
+                                 from (n mod N, n mod N) with uniform pair proposals, accepted
+                                 iff u r(I,J) < r(I*,J*) in FP32, r the pair's ratio
+                                 omega / omega-bar; biased for finite B.
+                                 The two rejection samplers retire accepted slots and refill
+                                 their lanes (warp-compacted retry); a slot that reaches
+                                 rs_max_attempts keeps the pair (-1, -1) and records
+                                 DSMC_ERR_RS_LIMIT; a ratio above 1 + 2^-10 records
+                                 DSMC_ERR_BOUND */
   uint64_t seed;              /* Philox key */
   uint32_t counter_base;      /* < 2^28; e.g. the particle-Gibbs sweep index */
-  uint32_t rs_max_attempts;   /* DSMC_RS: cap of attempts per slot (0 means 2^20);
+  uint32_t rs_max_attempts;   /* DSMC_RS, DSMC_RS_FACTORED: cap of attempts per slot (0 means
+                                 2^26, which the uniform proposals of the stochastic-
+                                 volatility workload at N = 16384 need for their worst
+                                 combinations; the factorised proposals need far fewer);
                                  DSMC_MH: the steps B of each slot's chain (0 means 64) */
   int max_merges_per_launch;  /* 0 = default; bounds the workspace */
   int fused_max_merges;       /* dense sampler: levels with at most this many combinations run
                                  as one fused launch (a thread-block cluster per combination,
                                  FP32 cross term); 0 = default (32; none with a
                                  tensor-core precision and dx > 8), < 0 = never */
+  int tc_fused;               /* dense sampler with a tensor-core precision, N <= 512, dx <= 4:
+                                 0 = default, every other level chunk runs as one persistent
+                                 warp-specialised kernel (operand rows, tcgen05 cross term,
+                                 exponentials, row CDF and draws of each combination on one
+                                 SM, nothing but pairs, maps and log L written); < 0 = the
+                                 split kernels (terms, tile sums, draws).  Same results. */
 } dsmc_config_t;
 
 /* Caller-owned DEVICE state of one smoothing (sizes from dsmc_state_sizes()).
@@ -208,7 +240,10 @@ dsmc_status_t dsmc_conditional_smooth(const dsmc_config_t* cfg, const dsmc_model
  *     nothing.  The call allocates nothing: no cudaMalloc, cudaFree or allocating library
  *     routine.
  *   - The first call on a device looks up the array's device address (once per device,
- *     with that device current); make that first call before any stream capture.
+ *     with that device current); make that first call before any stream capture.  The
+ *     address is kept for the life of the process: it does not survive a reset of the
+ *     device (cudaDeviceReset, or a release of its primary context), which unloads the
+ *     array; do not call this entry point on a device after resetting it.
  *   - Every call shares the one array and leaves its contents behind; the smoother clears
  *     what must start at zero (its status word) at the start of each call.  Calls whose
  *     work overlaps on the GPU (other streams, other host threads) race on the array:
@@ -321,10 +356,20 @@ enum {
   DSMC_KIND_FUSED = 4,      /* fused single-launch levels */
   DSMC_KIND_RESOLVE = 5,    /* top-down composition of the pairs */
   DSMC_KIND_GATHER = 6,     /* gather of the trajectories and moments */
+  DSMC_KIND_FUSED_TC = 7,   /* fused tensor-core levels (terms, exponentials and draws) */
   DSMC_KINDS = 8
 };
 dsmc_status_t dsmc_profile_breakdown_enable(int enable);
 dsmc_status_t dsmc_profile_breakdown_read(double* ms /* [DSMC_KINDS] */, int64_t* launches /* [DSMC_KINDS] */);
+
+/* Arithmetic unit rates of the current device, for the roofline of the exponential kernels
+ * (which are bound by these units, not by HBM): results per second of MUFU ex2.approx,
+ * FP32 FFMA, packed FFMA2 (one per instruction lane) and FADD, each the best of three timed
+ * launches (CUDA events on `stream`, after one warm-up launch) of eight independent
+ * dependency chains per thread, four 256-thread CTAs per SM.  The paper has no counterpart:
+ * this is a measurement aid.  sink: DEVICE, one float the kernels may write (they do not for
+ * their fixed inputs).  ops_per_s: HOST [4].  Synchronises `stream`. */
+dsmc_status_t dsmc_profile_unit_rates(float* sink, double ops_per_s[4], void* stream);
 
 /* ---- Inspection entry points used by the parity tests (same arithmetic as the path). */
 
@@ -333,6 +378,13 @@ dsmc_status_t dsmc_profile_breakdown_read(double* ms /* [DSMC_KINDS] */, int64_t
  * (about a second); the kernel then records DSMC_ERR_TIMEOUT, frees its tensor memory and
  * returns, and the context stays usable.  Off by default; host state of this process. */
 dsmc_status_t dsmc_debug_stall_tensor_cores(int enable);
+
+/* Test switch for the inspection entry points: while enabled, the fused tensor-core levels
+ * (tc_fused) also store the intermediate weights they otherwise keep in shared memory (row
+ * and column terms, tile sums, row weights, prefix sums) in the workspace, where
+ * dsmc_debug_merge_weights and dsmc_debug_row_shift read them.  It adds stores only; every
+ * result is the same.  Off by default; host state of this process. */
+dsmc_status_t dsmc_debug_keep_weights(int enable);
 
 /* Philox4x32-10 of n counters: ctr DEVICE [n][4] uint32, out DEVICE [n][4] uint32. */
 dsmc_status_t dsmc_debug_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
@@ -352,6 +404,36 @@ dsmc_status_t dsmc_debug_merge_weights(const dsmc_config_t* cfg, const dsmc_mode
                                        int level, int m, float* logW, float* r, float* rowsum,
                                        float* tiles, float* e, float* ratio, int info[4],
                                        void* ws, size_t ws_bytes, void* stream);
+
+/* After dsmc_merge_level(level) with a dense resampler, the per-row scale of the tile and
+ * element weights of combination `m` (in the last launch chunk of the level): every weight
+ * w of row i stands for exp(shift_i + delta_i ln 2) w, so log of a tile's sum of pair
+ * weights (Eq. normalized-weights, unnormalised) is shift_i + delta_i ln 2 + ln t_ik.
+ *   shift DEVICE [N] FP64 or NULL; delta DEVICE [N] FP32 or NULL (the extra base-2 shift of
+ *   a row recomputed after underflow, else 0). */
+dsmc_status_t dsmc_debug_row_shift(const dsmc_config_t* cfg, const dsmc_model_t* model, int level, int m,
+                                   double* shift, float* delta, void* ws, size_t ws_bytes, void* stream);
+
+/* After dsmc_merge_level(level) with resampler DSMC_RS_FACTORED, the factorised proposals
+ * and acceptance ratios of combination `m` of that level (it must belong to the last launch
+ * chunk of the level), as the device evaluated them:
+ *   pa   DEVICE [N] FP32 or NULL: row proposal weights e^{a_i - max_i a_i} in [0, 1];
+ *   pc   DEVICE [N] FP32 or NULL: column proposal weights e^{c_j - max_j c_j} in [0, 1],
+ *        c_j = b'_j (less dist_j^2 / 2Q for dx = 1);
+ *   acc  DEVICE [N][N] FP32 or NULL: acceptance ratios f(x_j | x_i) / f_max (times
+ *        e^{dist_j^2 / 2Q} for dx = 1);
+ *   info HOST int[4] or NULL: {N, 0, combination id, left block leaf}.
+ * The proposal draws take trunc(pa 2^40) and trunc(pc 2^40) as exact fixed-point weights. */
+dsmc_status_t dsmc_debug_lazy_weights(const dsmc_config_t* cfg, const dsmc_model_t* model, int level, int m,
+                                      float* pa, float* pc, float* acc, int info[4], void* ws, size_t ws_bytes,
+                                      void* stream);
+
+/* Attempts the rejection samplers (DSMC_RS, DSMC_RS_FACTORED) made in this workspace since
+ * the last dsmc_init_particles (or batched / served call): the acceptance rate of a
+ * smoothing is the number of drawn slots over this count.  attempts: HOST.  Synchronises
+ * `stream`. */
+dsmc_status_t dsmc_lazy_attempts(const dsmc_config_t* cfg, const dsmc_model_t* model, void* ws, size_t ws_bytes,
+                                 void* stream, uint64_t* attempts);
 
 #ifdef __cplusplus
 }

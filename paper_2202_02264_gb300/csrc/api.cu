@@ -69,6 +69,8 @@ thread_local Breakdown g_bd;
 
 // Test switch of dsmc_debug_stall_tensor_cores: tile-sum launches issue no MMA.
 bool g_stall_tc = false;
+// Test switch of dsmc_debug_keep_weights: fused levels store their intermediate weights.
+bool g_keep_weights = false;
 
 cudaError_t bd_begin(cudaStream_t s, int kind) {
   if (!g_bd.on) return cudaSuccess;
@@ -104,7 +106,25 @@ constexpr int kMaxDim = 32;
 constexpr int kMaxDenseN = 16384;
 constexpr int kDefaultMergeCap = 1024;
 constexpr uint32_t kDefaultMhSteps = 64;   // Algorithm 7's B when rs_max_attempts is 0
-constexpr int kRowsumTargetCtas = 152 * 8;  // 152 SMs, several CTAs each
+constexpr uint32_t kDefaultRsCap = 1u << 26;  // rejection samplers' attempt cap when it is 0
+constexpr int kRowsumCtasPerSm = 8;  // FP32 tile-sum kernel: several CTAs per SM
+
+// The current device's SM count (queried once per device; sizes grids and chunks).
+cudaError_t device_sms(int* n) {
+  static std::mutex mu;
+  static int cache[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  if (dev < 0 || dev >= 64) return cudaDeviceGetAttribute(n, cudaDevAttrMultiProcessorCount, dev);
+  if (cache[dev] == 0) {
+    e = cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  *n = cache[dev];
+  return cudaSuccess;
+}
 
 int pad_dim(int d) {
   int D = 1;
@@ -129,15 +149,16 @@ struct Plan {
   bool dense;
   int level_off[33];
   size_t o_status, o_U, o_alpha, o_V, o_beta, o_shift, o_logbar, o_inc, o_T, o_rw, o_rowsum, o_rowpart, o_cum,
-      o_delta, o_first, o_last, o_star, o_Ub, o_Vb, total;
+      o_delta, o_first, o_last, o_star, o_Ub, o_Vb, o_attempts, o_alpha0, o_kappa, o_pa, o_pc, o_cumA, o_cumC,
+      total;
 };
 
-void chunking(const Plan& p, int mc, int& CH, int& CW) {
+void chunking(const Plan& p, int mc, int sms, int& CH, int& CW) {
   if (p.compute != DSMC_FP32) {
     // tensor-core path: 128-row CTAs, two per SM, chunks of whole 128-column blocks
     const int RT = (p.N + 127) / 128;
     const int nblk = (p.N + 127) / 128;
-    int want = (152 * 2 * 2 + mc * RT - 1) / (mc * RT);
+    int want = (sms * 2 * 2 + mc * RT - 1) / (mc * RT);
     want = std::max(1, std::min(want, nblk));
     const int bpc = (nblk + want - 1) / want;
     CW = bpc * 128;
@@ -145,7 +166,7 @@ void chunking(const Plan& p, int mc, int& CH, int& CW) {
     return;
   }
   const int RT = (p.N + p.rows_per_cta - 1) / p.rows_per_cta;
-  int want = (kRowsumTargetCtas + mc * RT - 1) / (mc * RT);
+  int want = (sms * kRowsumCtasPerSm + mc * RT - 1) / (mc * RT);
   want = std::max(1, std::min(want, p.nT));
   const int tpc = (p.nT + want - 1) / want;
   CW = tpc * p.B;
@@ -162,7 +183,8 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p, int
   p.D = pad_dim(model->dx);
   p.L = 0;
   while ((1 << p.L) < p.K) ++p.L;
-  p.dense = cfg->resampler == DSMC_MULTINOMIAL;
+  p.dense = cfg->resampler == DSMC_MULTINOMIAL || cfg->resampler == DSMC_SYSTEMATIC;
+  const bool factored = cfg->resampler == DSMC_RS_FACTORED;
   // the cross-term precision only matters to the dense N x N pass; the lazy sampler
   // evaluates its proposed pairs in FP32 and needs no tensor-core operands
   p.compute = p.dense ? cfg->compute : DSMC_FP32;
@@ -196,6 +218,7 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p, int
     return at;
   };
   p.o_status = take(sizeof(int));
+  p.o_attempts = take(sizeof(unsigned long long));
   p.o_U = take(MN * p.D * sizeof(float));
   p.o_alpha = take(MN * sizeof(float));
   p.o_V = take(MN * p.D * sizeof(float));
@@ -215,6 +238,12 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p, int
   p.o_rowpart = take(tc ? 2 * MN * sizeof(float) : 0);
   p.o_Ub = take(tc ? (size_t)p.Mc * p.planes * p.Nr * 32 : 0);
   p.o_Vb = take(tc ? (size_t)p.Mc * p.planes * p.Nr * 32 : 0);
+  p.o_alpha0 = take(factored ? MN * sizeof(float) : 0);
+  p.o_kappa = take(factored ? MN * sizeof(float) : 0);
+  p.o_pa = take(factored ? MN * sizeof(float) : 0);
+  p.o_pc = take(factored ? MN * sizeof(float) : 0);
+  p.o_cumA = take(factored ? MN * sizeof(unsigned long long) : 0);
+  p.o_cumC = take(factored ? MN * sizeof(unsigned long long) : 0);
   p.total = o;
 }
 
@@ -240,6 +269,13 @@ WsPtrs ws_ptrs(const Plan& p, void* ws) {
   w.star = reinterpret_cast<int32_t*>(b + p.o_star);
   w.Ub = reinterpret_cast<unsigned char*>(b + p.o_Ub);
   w.Vb = reinterpret_cast<unsigned char*>(b + p.o_Vb);
+  w.attempts_total = reinterpret_cast<unsigned long long*>(b + p.o_attempts);
+  w.alpha0 = reinterpret_cast<float*>(b + p.o_alpha0);
+  w.kappa = reinterpret_cast<float*>(b + p.o_kappa);
+  w.pa = reinterpret_cast<float*>(b + p.o_pa);
+  w.pc = reinterpret_cast<float*>(b + p.o_pc);
+  w.cumA = reinterpret_cast<unsigned long long*>(b + p.o_cumA);
+  w.cumC = reinterpret_cast<unsigned long long*>(b + p.o_cumC);
   return w;
 }
 
@@ -358,15 +394,17 @@ dsmc_status_t check_config(const dsmc_config_t* cfg, const dsmc_model_t* model) 
   if (cfg->K < 1) return fail(DSMC_ERR_INVALID_ARG, "K must be >= 1");
   if (cfg->N < 1) return fail(DSMC_ERR_INVALID_ARG, "N must be >= 1");
   if (cfg->K > (1 << 24) || cfg->N > (1 << 24)) return fail(DSMC_ERR_UNSUPPORTED, "K or N too large");
-  if (cfg->resampler != DSMC_MULTINOMIAL && cfg->resampler != DSMC_RS && cfg->resampler != DSMC_MH)
+  if (cfg->resampler != DSMC_MULTINOMIAL && cfg->resampler != DSMC_RS && cfg->resampler != DSMC_MH &&
+      cfg->resampler != DSMC_SYSTEMATIC && cfg->resampler != DSMC_RS_FACTORED)
     return fail(DSMC_ERR_INVALID_ARG, "unknown resampler");
-  if (cfg->resampler == DSMC_MULTINOMIAL && cfg->N > kMaxDenseN)
-    return fail(DSMC_ERR_UNSUPPORTED, "dense resampling supports N <= 16384; use DSMC_RS");
+  const bool dense = cfg->resampler == DSMC_MULTINOMIAL || cfg->resampler == DSMC_SYSTEMATIC;
+  if (dense && cfg->N > kMaxDenseN)
+    return fail(DSMC_ERR_UNSUPPORTED, "dense resampling supports N <= 16384; use DSMC_RS or DSMC_RS_FACTORED");
   if (cfg->compute != DSMC_FP32 && cfg->compute != DSMC_TF32 && cfg->compute != DSMC_BF16)
     return fail(DSMC_ERR_INVALID_ARG, "unknown compute precision");
   if (cfg->compute == DSMC_TF32 && model->dx > 16)
     return fail(DSMC_ERR_UNSUPPORTED, "the TF32 tensor-core cross term supports dx <= 16");
-  if (cfg->compute != DSMC_FP32 && cfg->resampler == DSMC_MULTINOMIAL && cfg->N > 4096)
+  if (cfg->compute != DSMC_FP32 && dense && cfg->N > 4096)
     return fail(DSMC_ERR_UNSUPPORTED, "the tensor-core cross term supports N <= 4096");
   if (cfg->counter_base >= (1u << 28)) return fail(DSMC_ERR_INVALID_ARG, "counter_base must be < 2^28");
   if (model->dx < 1 || model->dx > kMaxDim) return fail(DSMC_ERR_UNSUPPORTED, "dx must be in 1..32");
@@ -442,13 +480,14 @@ MergeArgs merge_args(const Plan& p, const dsmc_config_t* cfg, const float* y, in
   a.resampler = cfg->resampler;
   a.compute = p.compute;
   a.stall = g_stall_tc ? 1 : 0;
+  a.inspect = g_keep_weights ? 1 : 0;
   a.Nr = p.Nr;
   a.mma_planes = p.planes;
   a.seed = cfg->seed;
   a.base = cfg->counter_base;
   // DSMC_RS: attempts per slot before DSMC_ERR_RS_LIMIT; DSMC_MH: the chain's steps B
   a.rs_max = cfg->rs_max_attempts ? cfg->rs_max_attempts
-                                  : (cfg->resampler == DSMC_MH ? kDefaultMhSteps : (1u << 20));
+                                  : (cfg->resampler == DSMC_MH ? kDefaultMhSteps : kDefaultRsCap);
   a.logN = (float)std::log((double)p.N);
   a.prop_mean = nullptr;
   a.prop_std = nullptr;
@@ -467,6 +506,7 @@ dsmc_status_t do_init(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& m
                       const float* y, const float* x_ref, dsmc_state_t* st, const WsPtrs& w,
                       cudaStream_t s) {
   DSMC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), s), "reset status");
+  DSMC_CUDA(cudaMemsetAsync(w.attempts_total, 0, sizeof(unsigned long long), s), "reset attempts");
   DSMC_CUDA(cudaMemsetAsync(w.star, 0, 2 * sizeof(int32_t), s), "reset star");
   InitArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -543,9 +583,9 @@ bool fused_eligible(const Plan& p, const dsmc_config_t* cfg, int M) { return fus
 
 // Cluster size for a fused launch of M combinations: C doubles while the launch still
 // fills at most one wave of the SMs and every CTA keeps at least 32 rows.
-int fused_cluster(const Plan& p, int M) {
+int fused_cluster(const Plan& p, int M, int sms) {
   int C = 1;
-  while (C < 16 && (size_t)M * C * 2 <= 152 && p.N / (2 * C) >= 32) C *= 2;
+  while (C < 16 && (size_t)M * C * 2 <= (size_t)sms && p.N / (2 * C) >= 32) C *= 2;
   return std::max(C, fused_min_cluster(p));
 }
 
@@ -555,7 +595,9 @@ int fused_cluster(const Plan& p, int M) {
 dsmc_status_t launch_combs(const Plan& p, const dsmc_config_t* cfg, const ParamBuf& mp, const float* y,
                            int level, int conditional, dsmc_state_t* st, const WsPtrs& w, cudaStream_t s,
                            int M, const CombItem* items, const SeqDesc* seqs, bool fused) {
-  const int Cf = fused ? fused_cluster(p, M) : 0;
+  int sms = 0;
+  DSMC_CUDA(device_sms(&sms), "SM count");
+  const int Cf = fused ? fused_cluster(p, M, sms) : 0;
   for (int m0 = 0; m0 < M; m0 += p.Mc) {
     MergeArgs a = merge_args(p, cfg, y, level, conditional, st, w);
     a.prop_mean = mp.prop_mean;
@@ -565,7 +607,8 @@ dsmc_status_t launch_combs(const Plan& p, const dsmc_config_t* cfg, const ParamB
     a.m0 = m0;
     a.mc = std::min(p.Mc, M - m0);
     a.gid0 = items ? 0 : p.level_off[level] + m0;
-    chunking(p, a.mc, a.CH, a.CW);
+    a.sms = sms;
+    chunking(p, a.mc, sms, a.CH, a.CW);
     if (Cf > 0) {
       const int C = fused_schedulable(p, a, Cf);
       if (C > 0) {
@@ -575,6 +618,15 @@ dsmc_status_t launch_combs(const Plan& p, const dsmc_config_t* cfg, const ParamB
         prof_count(1);
         continue;
       }
+    }
+    if (p.dense && cfg->tc_fused >= 0 && fused_tc_supported(p.D, p.N, p.compute, p.planes)) {
+      DSMC_CUDA(prof_begin(s), "profile event");
+      DSMC_CUDA(bd_begin(s, DSMC_KIND_FUSED_TC), "profile event");
+      DSMC_CUDA(launch_merge_tc_fused(p.D, a, mp.bytes, s), "fused tensor-core level kernel");
+      DSMC_CUDA(bd_end(s), "profile event");
+      DSMC_CUDA(prof_end(s, (double)a.mc * p.N * p.N), "profile event");
+      prof_count(1);
+      continue;
     }
     DSMC_CUDA(bd_begin(s, DSMC_KIND_PROLOGUE), "profile event");
     DSMC_CUDA(launch_prologue(p.D, a, mp.bytes, s), "prologue kernel");
@@ -594,6 +646,10 @@ dsmc_status_t launch_combs(const Plan& p, const dsmc_config_t* cfg, const ParamB
       prof_count(3);
     } else {
       DSMC_CUDA(bd_begin(s, DSMC_KIND_DRAWS), "profile event");
+      if (cfg->resampler == DSMC_RS_FACTORED) {
+        DSMC_CUDA(launch_rsf_cdf(a, s), "proposal CDF kernel");
+        prof_count(1);
+      }
       DSMC_CUDA(launch_sample_rs(p.D, a, s), "lazy sampler kernel");
       DSMC_CUDA(launch_epilogue(a, s), "epilogue kernel");
       DSMC_CUDA(bd_end(s), "profile event");
@@ -954,6 +1010,7 @@ dsmc_status_t batch_launch(const dsmc_config_t* cfg, const dsmc_model_t* model, 
   const Plan& p = bl.p;
   char* b = static_cast<char*>(ws);
   DSMC_CUDA(cudaMemsetAsync(br.w.status, 0, sizeof(int), s), "reset status");
+  DSMC_CUDA(cudaMemsetAsync(br.w.attempts_total, 0, sizeof(unsigned long long), s), "reset attempts");
   DSMC_CUDA(cudaMemsetAsync(b + bl.o_star, 0, (size_t)bl.n_seq * 2 * sizeof(int32_t), s), "reset stars");
   for (int i = 0; i < bl.n_seq; ++i)
     if (seqs[i].maps)
@@ -1123,6 +1180,7 @@ dsmc_status_t serve_tick(const dsmc_config_t* cfg, const dsmc_model_t* model, co
                               s), "item upload");
   DSMC_CUDA(cudaStreamSynchronize(s), "upload synchronize");
   DSMC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), s), "reset status");
+  DSMC_CUDA(cudaMemsetAsync(w.attempts_total, 0, sizeof(unsigned long long), s), "reset attempts");
   // stage -1: Algorithm 2
   for (int i = 0; i < n_seq; ++i) {
     if (stage[i] != -1) continue;
@@ -1198,6 +1256,7 @@ const char* dsmc_status_string(dsmc_status_t s) {
     case DSMC_ERR_DEGENERATE: return "all weights of a combination are zero";
     case DSMC_ERR_RS_LIMIT: return "rejection sampling reached its attempt cap";
     case DSMC_ERR_TIMEOUT: return "bounded wait timed out";
+    case DSMC_ERR_BOUND: return "a lazy sampler's pair exceeded its bound";
   }
   return "unknown status";
 }
@@ -1371,6 +1430,11 @@ dsmc_status_t dsmc_debug_stall_tensor_cores(int enable) {
   return DSMC_OK;
 }
 
+dsmc_status_t dsmc_debug_keep_weights(int enable) {
+  g_keep_weights = enable != 0;
+  return DSMC_OK;
+}
+
 dsmc_status_t dsmc_debug_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
                                 void* stream) {
   if (n < 0 || (n > 0 && (!ctr || !out))) return fail(DSMC_ERR_INVALID_ARG, "philox buffers");
@@ -1405,6 +1469,70 @@ dsmc_status_t dsmc_debug_merge_weights(const dsmc_config_t* cfg, const dsmc_mode
   }
   DSMC_CUDA(launch_debug_weights(p.D, a, m - last_chunk, logW, r, rowsum, tiles, e, ratio,
                                  static_cast<cudaStream_t>(stream)), "inspection kernel");
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_debug_lazy_weights(const dsmc_config_t* cfg, const dsmc_model_t* model, int level, int m,
+                                      float* pa, float* pc, float* acc, int info[4], void* ws, size_t ws_bytes,
+                                      void* stream) {
+  Prepared pr;
+  DSMC_TRY(prepare(cfg, model, nullptr, ws, ws_bytes, pr));
+  const Plan& p = pr.p;
+  if (cfg->resampler != DSMC_RS_FACTORED)
+    return fail(DSMC_ERR_INVALID_ARG, "factorised proposals exist only with DSMC_RS_FACTORED");
+  if (level < 0 || level >= p.L) return fail(DSMC_ERR_INVALID_ARG, "level out of range");
+  const int M = merges_at_level(p.K, level);
+  if (m < 0 || m >= M) return fail(DSMC_ERR_INVALID_ARG, "combination out of range");
+  const int last_chunk = ((M - 1) / p.Mc) * p.Mc;
+  if (m < last_chunk) return fail(DSMC_ERR_INVALID_ARG, "combination not in the last launch chunk");
+  dsmc_state_t dummy = {nullptr, nullptr, nullptr, nullptr};
+  MergeArgs a = merge_args(p, cfg, nullptr, level, 0, &dummy, pr.w);
+  a.m0 = last_chunk;
+  a.mc = std::min(p.Mc, M - last_chunk);
+  a.gid0 = p.level_off[level] + last_chunk;
+  if (info) {
+    info[0] = p.N;
+    info[1] = 0;
+    info[2] = p.level_off[level] + m;
+    info[3] = level == 0 ? 1 : 0;
+  }
+  DSMC_CUDA(launch_debug_lazy(p.D, a, m - last_chunk, pa, pc, acc, static_cast<cudaStream_t>(stream)),
+            "inspection kernel");
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_debug_row_shift(const dsmc_config_t* cfg, const dsmc_model_t* model, int level, int m,
+                                   double* shift, float* delta, void* ws, size_t ws_bytes, void* stream) {
+  Prepared pr;
+  DSMC_TRY(prepare(cfg, model, nullptr, ws, ws_bytes, pr));
+  const Plan& p = pr.p;
+  if (!p.dense) return fail(DSMC_ERR_INVALID_ARG, "row shifts exist only with a dense resampler");
+  if (level < 0 || level >= p.L) return fail(DSMC_ERR_INVALID_ARG, "level out of range");
+  const int M = merges_at_level(p.K, level);
+  if (m < 0 || m >= M) return fail(DSMC_ERR_INVALID_ARG, "combination out of range");
+  const int last_chunk = ((M - 1) / p.Mc) * p.Mc;
+  if (m < last_chunk) return fail(DSMC_ERR_INVALID_ARG, "combination not in the last launch chunk");
+  const size_t off = (size_t)(m - last_chunk) * p.N;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (shift)
+    DSMC_CUDA(cudaMemcpyAsync(shift, pr.w.shift + off, sizeof(double) * p.N, cudaMemcpyDeviceToDevice, s),
+              "shift copy");
+  if (delta)
+    DSMC_CUDA(cudaMemcpyAsync(delta, pr.w.delta + off, sizeof(float) * p.N, cudaMemcpyDeviceToDevice, s),
+              "delta copy");
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_lazy_attempts(const dsmc_config_t* cfg, const dsmc_model_t* model, void* ws, size_t ws_bytes,
+                                 void* stream, uint64_t* attempts) {
+  if (!attempts) return fail(DSMC_ERR_INVALID_ARG, "null output");
+  Prepared pr;
+  DSMC_TRY(prepare(cfg, model, nullptr, ws, ws_bytes, pr));
+  unsigned long long h = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DSMC_CUDA(cudaMemcpyAsync(&h, pr.w.attempts_total, sizeof(h), cudaMemcpyDeviceToHost, s), "attempts copy");
+  DSMC_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+  *attempts = h;
   return DSMC_OK;
 }
 

@@ -15,6 +15,9 @@ constexpr uint32_t kPurposeInit = 1u;
 constexpr uint32_t kPurposeDense = 2u;
 constexpr uint32_t kPurposeRS = 3u;
 constexpr uint32_t kPurposeMH = 4u;
+constexpr uint32_t kPurposeSys = 5u;   // systematic offset, one per combination (slot 0)
+constexpr uint32_t kPurposeRSF = 6u;   // factorised proposals: the pair's two 64-bit uniforms
+constexpr uint32_t kPurposeRSU = 7u;   // factorised proposals: the acceptance uniform
 
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.69314718055994531f;

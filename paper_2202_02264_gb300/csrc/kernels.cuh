@@ -35,6 +35,16 @@ struct WsPtrs {
   // group g at g*256 B, chunk c at c*128 B), rows padded to a multiple of 128.
   unsigned char* Ub; // [Mc][planes][Nr][32 B]
   unsigned char* Vb; // [Mc][planes][Nr][32 B]
+  // rejection sampling with factorised proposals (DSMC_RS_FACTORED)
+  float* alpha0;     // [Mc][N]      alpha_i before the row shift: -log2(e) 1/2 w_i' Q^-1 w_i
+  float* kappa;      // [Mc][N]      log2(e) (dist_j^2 Q^-1 / 2 - 1/2 v_j' Q^-1 v_j): with alpha0_i
+                     //              and u_i . v_j, the base-2 log acceptance of pair (i, j)
+  float* pa;         // [Mc][N]      row proposal: log a_i from the prologue, then e^(a_i - max a)
+  float* pc;         // [Mc][N]      column proposal: b'_j - dist_j^2 Q^-1 / 2, then relative weight
+  unsigned long long* cumA;  // [Mc][N] exact 2^40 fixed-point prefix sums of the row proposal
+  unsigned long long* cumC;  // [Mc][N] the same of the column proposal
+  unsigned long long* attempts_total;  // attempts of the rejection samplers since the last
+                                      // init (inspection: acceptance rate)
 };
 
 // One sequence of a batched launch (device memory; built by the host per batch).
@@ -97,6 +107,9 @@ struct MergeArgs {
   int compute;       // DSMC_FP32, DSMC_TF32 or DSMC_BF16
   int Nr;            // N rounded up to 128 (tensor-core operand rows)
   int mma_planes;    // 32-byte K planes of the tensor-core operands
+  int sms;           // SMs of the device (persistent grids)
+  int inspect;       // fused kernels also store their intermediate weights in the workspace
+                     // (dsmc_debug_keep_weights), for the inspection entry points
   int stall;         // test switch: the tensor-core control warp issues no MMA, so every
                      // wait on an accumulator runs out (dsmc_debug_stall_tensor_cores)
   uint64_t seed;
@@ -231,7 +244,12 @@ cudaError_t launch_rowsum(int D, const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_rowsum_tc(const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_sample_dense(int D, const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_sample_rs(int D, const MergeArgs& a, cudaStream_t s);
+cudaError_t launch_rsf_cdf(const MergeArgs& a, cudaStream_t s);
+cudaError_t launch_debug_lazy(int D, const MergeArgs& a, int s_local, float* pa, float* pc, float* acc,
+                              cudaStream_t s);
 cudaError_t launch_epilogue(const MergeArgs& a, cudaStream_t s);
+bool fused_tc_supported(int D, int N, int compute, int planes);
+cudaError_t launch_merge_tc_fused(int D, const MergeArgs& a, const void* mp, cudaStream_t s);
 cudaError_t launch_gather(int D, const GatherArgs& a, cudaStream_t s);
 cudaError_t launch_resolve_level(const MergeArgs& a, cudaStream_t s);
 cudaError_t launch_debug_weights(int D, const MergeArgs& a, int s_local, float* logW, float* r,

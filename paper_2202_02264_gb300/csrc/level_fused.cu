@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
     last_out[0] = right_leaf ? 0 : last_R[0];
   }
   DrawIn in;
+  in.sys = (a.resampler == DSMC_SYSTEMATIC && !cb.conditional) ? 1 : 0;
   in.cum = sC;
   in.T = Tt;
   in.U = U;

@@ -24,74 +24,17 @@
 
 #include "kernels.cuh"
 #include "merge_parts.cuh"
+#include "tc_ops.cuh"
 
 namespace dsmc {
 
 namespace {
 
 using namespace parts;
+using namespace tc;
 
 constexpr int kEpiThreads = 256;
 constexpr int kRsThreads = 128;
-
-// Tensor-core operand rows.  The K dimension holds the D state coordinates followed by
-// four extra columns that carry the per-row and per-column exponent terms exactly as
-// two-term (hi + lo) splits in the MMA type:
-//   row i    (U): [u_i, alpha_hi, alpha_lo, 1, 1]
-//   column j (V): [v_j, 1, 1, beta_hi, beta_lo]
-// so that the MMA accumulates alpha_i + beta_j + u_i . v_j.  K is cut into 32-byte planes
-// (16 BF16 or 8 TF32 values); plane p of a combination is a [Nr][32 B] array in the
-// canonical no-swizzle K-major layout (8-row x 16-byte core matrices: row group g at
-// g*256 B, 16-byte chunk c at c*128 B).  Entries beyond D + 4 are zero.
-template <int D, int KIND>
-__device__ __forceinline__ void store_mma_row_t(unsigned char* base, int Nr, int r, const float* x,
-                                                const float* ext) {
-  constexpr int kp = KIND == DSMC_BF16 ? 16 : 8;      // values per 32-byte plane
-  constexpr int kc = KIND == DSMC_BF16 ? 8 : 4;       // values per 16-byte chunk
-  constexpr int np = (D + 4 + kp - 1) / kp;
-  unsigned char* row = base + (size_t)(r / 8) * 256 + (size_t)(r % 8) * 16;
-#pragma unroll
-  for (int ch = 0; ch < 2 * np; ++ch) {  // one 16-byte store per chunk
-    uint32_t w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (KIND == DSMC_BF16) {
-        const int k0 = ch * kc + 2 * q;
-        const float v0 = k0 < D ? x[k0] : (k0 < D + 4 ? ext[k0 - D] : 0.f);
-        const float v1 = k0 + 1 < D ? x[k0 + 1] : (k0 + 1 < D + 4 ? ext[k0 + 1 - D] : 0.f);
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-        w[q] = *reinterpret_cast<const uint32_t*>(&h);
-      } else {
-        const int k = ch * kc + q;
-        const float v = k < D ? x[k] : (k < D + 4 ? ext[k - D] : 0.f);
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[q]) : "f"(v));
-      }
-    }
-    *reinterpret_cast<uint4*>(row + (size_t)(ch / 2) * Nr * 32 + (ch % 2) * 128) =
-        make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
-
-template <int D>
-__device__ __forceinline__ void store_mma_row(unsigned char* base, int Nr, int r, const float* x,
-                                              const float* ext, int compute) {
-  if (compute == DSMC_BF16) store_mma_row_t<D, DSMC_BF16>(base, Nr, r, x, ext);
-  else store_mma_row_t<D, DSMC_TF32>(base, Nr, r, x, ext);
-}
-
-// hi + lo split of x in the MMA type (the two values the tensor core reads).
-__device__ __forceinline__ void split_mma(float x, int compute, float* hi, float* lo) {
-  if (compute == DSMC_BF16) {
-    *hi = __bfloat162float(__float2bfloat16_rn(x));
-    *lo = __bfloat162float(__float2bfloat16_rn(x - *hi));
-  } else {
-    uint32_t t;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
-    *hi = __uint_as_float(t);
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x - *hi));
-    *lo = __uint_as_float(t);
-  }
-}
 
 // ---------------------------------------------------------------------------------------
 // Prologue: endpoint states through the block index maps, column / row terms, bound.
@@ -197,7 +140,7 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
   // the distance from x_j to the hull, so log omega-bar = log f_max + max_i a_i +
   // max_j (b'_j - dist_j^2 Q^-1 / 2) is a valid bound of the combination's pair weights
   // (Algorithm 8 needs any bound; a particle far outside the hull otherwise sets it).
-  const bool hull = (D == 1) && a.resampler != DSMC_MULTINOMIAL;
+  const bool hull = (D == 1) && a.resampler != DSMC_MULTINOMIAL && a.resampler != DSMC_SYSTEMATIC;
   float m_lo = 0.f, m_hi = 0.f, bhull = -INFINITY;
   if (hull) {
     float lo = INFINITY, hi = -INFINITY;
@@ -236,15 +179,23 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
   });
 
   // pass 2a: columns  v_j = xR_j - mu,  beta_j = log2(e) (b'_j - B* - 1/2 v' Q^-1 v)
+  const bool factored = a.resampler == DSMC_RS_FACTORED;
   for (int j = threadIdx.x; j < N; j += kProThreads) {
     float v[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) v[k] = Vs[(size_t)j * D + k];
+    const float bp = Bs[j];
+    float dist2h = 0.f;  // dist_j^2 Q^-1 / 2
     if (hull) {  // v is still x_j here
       const float dist = fmaxf(0.f, fmaxf(v[0] - m_hi, m_lo - v[0]));
-      bhull = fmaxf(bhull, Bs[j] - 0.5f * mp.Qi[0] * dist * dist);
+      dist2h = 0.5f * mp.Qi[0] * dist * dist;
+      bhull = fmaxf(bhull, bp - dist2h);
     }
-    const float bj = column_beta<D>(mp, v, mu, Bs[j], bstar);
+    const float bj = column_beta<D>(mp, v, mu, bp, bstar);
+    if (factored) {  // column proposal weight (log) and acceptance term
+      a.ws.pc[(size_t)s * N + j] = bp - dist2h;
+      a.ws.kappa[(size_t)s * N + j] = kLog2e * (dist2h - 0.5f * quad_form<D>(mp.Qi, v));
+    }
     beta[j] = bj;
 #pragma unroll
     for (int k = 0; k < D; ++k) V[(size_t)j * D + k] = v[k];
@@ -280,6 +231,10 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
     const float dl = row_shift<D, false>(ul, al0, Vs, Bs, N);
     const float al = __fsub_rn(al0, dl);
     bad |= isnan(ai);
+    if (factored) {  // row proposal weight (log) and the unshifted row term
+      a.ws.pa[(size_t)s * N + i] = ai;
+      a.ws.alpha0[(size_t)s * N + i] = al0;
+    }
 #pragma unroll
     for (int k = 0; k < D; ++k) U[(size_t)i * D + k] = ul[k];
     if (a.compute != DSMC_FP32) {
@@ -515,51 +470,6 @@ __global__ void __launch_bounds__(kCdfThreads) rowcdf_kernel(MergeArgs a) {
 // ---------------------------------------------------------------------------------------
 constexpr int kSlotThreads = 128;
 
-struct SlotOut {
-  int32_t *pl, *pr, *first_out, *last_out;
-  const int32_t *first_L, *last_R;
-  bool left_leaf, right_leaf;
-  int N;
-  int32_t* star;
-  __device__ __forceinline__ void put(int n, int i, int j) const {
-    if (n < N) {
-      pl[n] = i;
-      pr[n] = j;
-      first_out[n] = left_leaf ? i : first_L[i];
-      last_out[n] = right_leaf ? j : last_R[j];
-    } else {
-      star[0] = i;
-      star[1] = j;
-    }
-  }
-};
-
-// The output maps of combination cb (and slot 0 of a conditional combination).
-__device__ __forceinline__ SlotOut slot_out(const MergeArgs& a, const Comb& cb, bool write_slot0) {
-  const int at = cb.at, c = cb.c, b = cb.b, K = cb.K;
-  const int N = a.N;
-  const int sR = b - c + 1;
-  const int bufL = cb.level & 1, bufR = ceil_log2(sR) & 1, bufO = (cb.level + 1) & 1;
-  SlotOut o;
-  o.pl = cb.pairs + (size_t)cb.gid * 2 * N;
-  o.pr = o.pl + N;
-  o.first_out = cb.first + ((size_t)bufO * K + at) * N;
-  o.last_out = cb.last + ((size_t)bufO * K + at) * N;
-  o.first_L = cb.first + ((size_t)bufL * K + at) * N;
-  o.last_R = cb.last + ((size_t)bufR * K + c) * N;
-  o.left_leaf = (cb.level == 0);
-  o.right_leaf = (sR == 1);
-  o.N = N;
-  o.star = cb.star;
-  if (cb.conditional && write_slot0) {
-    o.pl[0] = 0;
-    o.pr[0] = 0;
-    o.first_out[0] = o.left_leaf ? 0 : o.first_L[0];
-    o.last_out[0] = o.right_leaf ? 0 : o.last_R[0];
-  }
-  return o;
-}
-
 template <int D>
 __global__ void __launch_bounds__(kSlotThreads) slots_kernel(MergeArgs a) {
   const int s = blockIdx.x;
@@ -572,6 +482,7 @@ __global__ void __launch_bounds__(kSlotThreads) slots_kernel(MergeArgs a) {
   const int n = n_lo + blockIdx.y * kSlotThreads + threadIdx.x;
   if (n >= n_hi) return;
   DrawIn in;
+  in.sys = (a.resampler == DSMC_SYSTEMATIC && !cb.conditional) ? 1 : 0;
   in.cum = a.ws.cum + (size_t)s * N;
   in.T = a.ws.T + (size_t)s * N * a.nTp;
   in.U = a.ws.U + (size_t)s * N * D;
@@ -773,6 +684,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
   // pair draws
   const SlotOut o = slot_out(a, cb, threadIdx.x == 0);
   DrawIn in;
+  in.sys = (a.resampler == DSMC_SYSTEMATIC && !cb.conditional) ? 1 : 0;
   in.cum = sC;
   in.T = sT ? sT : Tt;
   in.U = sU;
@@ -794,10 +706,22 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
 }
 
 // ---------------------------------------------------------------------------------------
-// Lazy rejection sampler (Algorithm 8): per slot, attempts (I, J, u) until u < ratio(I, J),
-// ratio = exp(logW_IJ - log omega-bar); (I, J, u) are redrawn at every attempt.  Only the
-// proposed pairs are evaluated.  One thread per slot; capped at rs_max attempts.
+// Lazy rejection samplers.  Only the proposed pairs are evaluated; (I, J, u) are redrawn
+// at every attempt; each slot stops at its first acceptance or after rs_max attempts.
+//   Algorithm 8 (DSMC_RS): I, J uniform (words x, y of the counter (n, gid, RS, attempt)),
+//     accept iff u23(z) < exp(logW_IJ - log omega-bar).
+//   Factorised proposals (DSMC_RS_FACTORED): I with probability Rq_I / SA and J with
+//     probability Cq_J / SC (64-bit uniforms from words x:y and z:w of the counter
+//     (n, gid, RSF, attempt), binary search of the exact prefix sums), accept iff
+//     u23(x of (n, gid, RSU, attempt)) < f(x_J | x_I) / f_max (times e^{dist_J^2 / 2Q}).
+// Each warp owns a contiguous range of kRsSlotsPerWarp slots; a lane that finishes its slot
+// takes the range's next one (warp-compacted retry), so a slot with a low acceptance rate
+// holds one lane, not its warp.  A slot that reaches the cap keeps (-1, -1) and records
+// DSMC_ERR_RS_LIMIT; a ratio above 1 + 2^-10 records DSMC_ERR_BOUND.
 // ---------------------------------------------------------------------------------------
+constexpr int kRsSlotsPerWarp = 64;
+constexpr float kBoundSlack = 1.0009765625f;  // 1 + 2^-10: FP32 rounding of a valid bound stays below
+
 template <int D>
 __device__ __forceinline__ float rs_ratio(const MergeArgs& a, int s, int I, int J, double logbar) {
   const int N = a.N;
@@ -814,7 +738,32 @@ __device__ __forceinline__ float rs_ratio(const MergeArgs& a, int s, int I, int 
   return ex2(__fadd_rn(e, off));
 }
 
+// The factorised sampler's acceptance ratio of pair (I, J): 2^(alpha0_I + kappa_J + u_I . v_J).
 template <int D>
+__device__ __forceinline__ float rsf_ratio(const MergeArgs& a, int s, int I, int J) {
+  const int N = a.N;
+  const float* U = a.ws.U + ((size_t)s * N + I) * D;
+  const float* V = a.ws.V + ((size_t)s * N + J) * D;
+  float u[D], v[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    u[k] = U[k];
+    v[k] = V[k];
+  }
+  return ex2(pair_exponent<D>(u, a.ws.alpha0[(size_t)s * N + I], v, a.ws.kappa[(size_t)s * N + J]));
+}
+
+// First index with cum[idx] > T (cum[N-1] > T), through the read-only cache.
+__device__ __forceinline__ int search_cum(const unsigned long long* cum, int N, unsigned long long T) {
+  int lo = 0, hi = N - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(cum + mid) > T) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+template <int D, bool FACT>
 __global__ void __launch_bounds__(kRsThreads) sample_rs_kernel(MergeArgs a) {
   const int s = blockIdx.y;
   const Comb cb = comb_of(a, s);
@@ -822,8 +771,6 @@ __global__ void __launch_bounds__(kRsThreads) sample_rs_kernel(MergeArgs a) {
   const int N = a.N;
   const int n_lo = cb.conditional ? 1 : 0;
   const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
-  const int n = n_lo + blockIdx.x * kRsThreads + threadIdx.x;
-  const double logbar = a.ws.logbar[s];
   int32_t* pl = cb.pairs + (size_t)gid * 2 * N;
   int32_t* pr = pl + N;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -833,26 +780,130 @@ __global__ void __launch_bounds__(kRsThreads) sample_rs_kernel(MergeArgs a) {
       pr[0] = 0;
     }
   }
-  if (n >= n_hi) return;
-  int I = 0, J = 0;
-  bool ok = false;
-  for (uint32_t att = 0; att < a.rs_max; ++att) {
-    const uint4 w = draw(cb.seed, (uint32_t)n, (uint32_t)gid, kPurposeRS, cb.base, att);
-    I = (int)__umulhi(w.x, (uint32_t)N);
-    J = (int)__umulhi(w.y, (uint32_t)N);
-    if (u23(w.z) < rs_ratio<D>(a, s, I, J, logbar)) {
-      ok = true;
-      break;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w0 = n_lo + (blockIdx.x * (kRsThreads / 32) + warp) * kRsSlotsPerWarp;
+  const int w1 = min(w0 + kRsSlotsPerWarp, n_hi);
+  if (w0 >= n_hi) return;  // warp-uniform
+  const double logbar = FACT ? 0.0 : a.ws.logbar[s];
+  const unsigned long long* cumA = a.ws.cumA + (size_t)s * N;
+  const unsigned long long* cumC = a.ws.cumC + (size_t)s * N;
+  const unsigned long long SA = FACT ? cumA[N - 1] : 0ull, SC = FACT ? cumC[N - 1] : 0ull;
+  const bool degenerate = FACT && (SA == 0ull || SC == 0ull);
+  auto put = [&](int n, int I, int J) {
+    if (n < N) {
+      pl[n] = I;
+      pr[n] = J;
+    } else {
+      cb.star[0] = I;
+      cb.star[1] = J;
     }
+  };
+  int slot = w0 + lane < w1 ? w0 + lane : -1;
+  int next = w0 + 32;
+  uint32_t att = 0;
+  unsigned long long total = 0;
+  bool capped = false, over = false;
+  while (__any_sync(0xffffffffu, slot >= 0)) {
+    bool fin = false;
+    if (slot >= 0) {
+      int I = -1, J = -1;
+      bool acc = false;
+      if (!degenerate) {
+        float u, r;
+        if (FACT) {
+          const uint4 w = draw(cb.seed, (uint32_t)slot, (uint32_t)gid, kPurposeRSF, cb.base, att);
+          const uint4 v = draw(cb.seed, (uint32_t)slot, (uint32_t)gid, kPurposeRSU, cb.base, att);
+          I = search_cum(cumA, N, __umul64hi(((unsigned long long)w.x << 32) | w.y, SA));
+          J = search_cum(cumC, N, __umul64hi(((unsigned long long)w.z << 32) | w.w, SC));
+          u = u23(v.x);
+          r = rsf_ratio<D>(a, s, I, J);
+        } else {
+          const uint4 w = draw(cb.seed, (uint32_t)slot, (uint32_t)gid, kPurposeRS, cb.base, att);
+          I = (int)__umulhi(w.x, (uint32_t)N);
+          J = (int)__umulhi(w.y, (uint32_t)N);
+          u = u23(w.z);
+          r = rs_ratio<D>(a, s, I, J, logbar);
+        }
+        over |= r > kBoundSlack;
+        acc = u < r;
+        ++att;
+        ++total;
+      }
+      if (acc || att >= a.rs_max || degenerate) {
+        fin = true;
+        capped |= !acc;
+        put(slot, acc ? I : -1, acc ? J : -1);
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, fin);
+    if (fin) {
+      const int k = next + __popc(m & ((1u << lane) - 1u));
+      slot = k < w1 ? k : -1;
+      att = 0;
+    }
+    next += __popc(m);
   }
-  if (!ok) record_status(a.ws.status, DSMC_ERR_RS_LIMIT);
-  if (n < N) {
-    pl[n] = I;
-    pr[n] = J;
-  } else {
-    cb.star[0] = I;
-    cb.star[1] = J;
+  total = warp_sum(total);
+  if (lane == 0) atomicAdd(a.ws.attempts_total, total);
+  if (degenerate) {
+    if (lane == 0) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
+  } else if (capped) {
+    record_status(a.ws.status, DSMC_ERR_RS_LIMIT);
   }
+  if (over) record_status(a.ws.status, DSMC_ERR_BOUND);
+}
+
+// The factorised proposals of one combination (one CTA): the row and column log-weights
+// the prologue left in pa / pc become weights relative to their maxima, 2^((l - max) log2 e)
+// in FP32 clamped to [0, 1], and their exact 2^40 fixed-point prefix sums (chunks of
+// kCumChunk, exact u64 scans with a running carry).
+constexpr int kRsfCdfThreads = 512;
+constexpr int kCumChunk = 2048;
+
+__device__ void relative_weights_and_cum(float* w, unsigned long long* cum, int N, unsigned long long* chunk,
+                                         unsigned long long* warp_tot, float* redf, bool& bad) {
+  constexpr int NW = kRsfCdfThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float m = -INFINITY;
+  for (int i = threadIdx.x; i < N; i += kRsfCdfThreads) {
+    const float x = w[i];
+    bad |= isnan(x);
+    m = fmaxf(m, x);
+  }
+  m = warp_max(m);
+  if (lane == 0) redf[warp] = m;
+  __syncthreads();
+  float M = redf[0];
+  for (int k = 1; k < NW; ++k) M = fmaxf(M, redf[k]);
+  __syncthreads();  // redf is reused by the next call
+  unsigned long long carry = 0;
+  for (int c0 = 0; c0 < N; c0 += kCumChunk) {
+    const int n = min(kCumChunk, N - c0);
+    for (int k = threadIdx.x; k < n; k += kRsfCdfThreads) {
+      float r = M > -INFINITY ? ex2(__fmul_rn(__fsub_rn(w[c0 + k], M), kLog2e)) : 0.f;
+      if (!(r > 0.f)) r = 0.f;
+      if (r > 1.f) r = 1.f;
+      w[c0 + k] = r;
+      chunk[k] = (unsigned long long)__float2ull_rz(r * 0x1p40f);
+    }
+    __syncthreads();
+    block_scan_u64(chunk, n, warp_tot);
+    for (int k = threadIdx.x; k < n; k += kRsfCdfThreads) cum[c0 + k] = carry + chunk[k];
+    carry += chunk[n - 1];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kRsfCdfThreads) rsf_cdf_kernel(MergeArgs a) {
+  const int s = blockIdx.x;
+  const int N = a.N;
+  __shared__ unsigned long long chunk[kCumChunk];
+  __shared__ unsigned long long warp_tot[kRsfCdfThreads / 32];
+  __shared__ float redf[kRsfCdfThreads / 32];
+  bool bad = false;
+  relative_weights_and_cum(a.ws.pa + (size_t)s * N, a.ws.cumA + (size_t)s * N, N, chunk, warp_tot, redf, bad);
+  relative_weights_and_cum(a.ws.pc + (size_t)s * N, a.ws.cumC + (size_t)s * N, N, chunk, warp_tot, redf, bad);
+  if (bad) record_status(a.ws.status, DSMC_ERR_NONFINITE);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -964,6 +1015,18 @@ __global__ void debug_weights_kernel(MergeArgs a, int s, float* logW, float* r, 
       tiles[(size_t)i * a.nT + k] = a.ws.T[((size_t)s * N + i) * a.nTp + k];
 }
 
+template <int D>
+__global__ void debug_lazy_kernel(MergeArgs a, int s, float* pa, float* pc, float* acc) {
+  const int i = blockIdx.x;
+  const int N = a.N;
+  if (threadIdx.x == 0) {
+    if (pa) pa[i] = a.ws.pa[(size_t)s * N + i];
+    if (pc) pc[i] = a.ws.pc[(size_t)s * N + i];
+  }
+  if (acc)
+    for (int j = threadIdx.x; j < N; j += blockDim.x) acc[(size_t)i * N + j] = rsf_ratio<D>(a, s, i, j);
+}
+
 // ------------------------------------------------------------------- launch wrappers
 // Slots per combination to cover: N, one fewer when conditional (slot 0 is fixed), one more
 // at a conditional root (the next reference).  Batched launches cover N + 1 (every
@@ -1025,11 +1088,23 @@ cudaError_t sample_dense_t(const MergeArgs& a, cudaStream_t st) {
 
 template <int D>
 cudaError_t sample_rs_t(const MergeArgs& a, cudaStream_t st) {
-  dim3 grid((launch_slots(a) + kRsThreads - 1) / kRsThreads, a.mc);
-  if (a.resampler == DSMC_MH)
+  if (a.resampler == DSMC_MH) {
+    dim3 grid((launch_slots(a) + kRsThreads - 1) / kRsThreads, a.mc);
     sample_mh_kernel<D><<<grid, kRsThreads, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  constexpr int kSlotsPerCta = kRsSlotsPerWarp * (kRsThreads / 32);
+  dim3 grid((launch_slots(a) + kSlotsPerCta - 1) / kSlotsPerCta, a.mc);
+  if (a.resampler == DSMC_RS_FACTORED)
+    sample_rs_kernel<D, true><<<grid, kRsThreads, 0, st>>>(a);
   else
-    sample_rs_kernel<D><<<grid, kRsThreads, 0, st>>>(a);
+    sample_rs_kernel<D, false><<<grid, kRsThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t debug_lazy_t(const MergeArgs& a, int s, float* pa, float* pc, float* acc, cudaStream_t st) {
+  debug_lazy_kernel<D><<<a.N, 128, 0, st>>>(a, s, pa, pc, acc);
   return cudaGetLastError();
 }
 
@@ -1067,6 +1142,16 @@ cudaError_t launch_sample_dense(int D, const MergeArgs& a, cudaStream_t s) {
 
 cudaError_t launch_sample_rs(int D, const MergeArgs& a, cudaStream_t s) {
   DSMC_DISPATCH(D, sample_rs_t<DD>(a, s))
+}
+
+cudaError_t launch_rsf_cdf(const MergeArgs& a, cudaStream_t s) {
+  rsf_cdf_kernel<<<a.mc, kRsfCdfThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_lazy(int D, const MergeArgs& a, int s_local, float* pa, float* pc, float* acc,
+                              cudaStream_t s) {
+  DSMC_DISPATCH(D, debug_lazy_t<DD>(a, s_local, pa, pc, acc, s))
 }
 
 cudaError_t launch_epilogue(const MergeArgs& a, cudaStream_t s) {

@@ -363,6 +363,7 @@ __device__ __forceinline__ void load_row(const float* p, float* r) {
 //   column: the chosen tile's columns recomputed (pair_exponent + ex2), images relative to
 //           the tile weight t_ik, w3.
 struct DrawIn {
+  int sys;                        // systematic positions (k + U) / N instead of iid uniforms
   const unsigned long long* cum;  // [N] exact prefix sums of the row weights
   const float* T;                 // [N][nTp] tile weights
   const float* U;                 // [N][D]
@@ -378,8 +379,17 @@ struct DrawIn {
 // their tile weight), T = floor(w Q / 2^32) (w a 32-bit uniform word), the number of prefix
 // sums <= T, clamped to n - 1; 0 when Q = 0.  Entries past n add nothing to Q and never
 // count (their prefix sum is Q > T), so every W >= n gives the same index.
+// The systematic sampler's next uniform word: the target's position inside the chosen
+// interval [bef, aft) as a fraction of its length, trunc((T - bef) / (aft - bef) 2^32), with a
+// correctly rounded FP64 quotient (the oracle's checker computes the same bits).
+__device__ __forceinline__ uint32_t remainder_word(unsigned long long T, unsigned long long bef,
+                                                   unsigned long long aft) {
+  return __double2uint_rz(__ddiv_rn((double)(T - bef), (double)(aft - bef)) * 4294967296.0);
+}
+
+// When wrem is not null it receives remainder_word of the target inside the chosen entry.
 template <int W>
-__device__ __forceinline__ int pick_w(const float* x, int n, uint32_t w, int ref_be) {
+__device__ __forceinline__ int pick_w(const float* x, int n, uint32_t w, int ref_be, uint32_t* wrem = nullptr) {
   uint32_t q[W];
   uint32_t Q = 0;
 #pragma unroll
@@ -387,15 +397,23 @@ __device__ __forceinline__ int pick_w(const float* x, int n, uint32_t w, int ref
     q[k] = (k < n) ? q24(x[k], ref_be) : 0u;
     Q += q[k];
   }
-  if (Q == 0u) return 0;
+  if (Q == 0u) {
+    if (wrem) *wrem = w;
+    return 0;
+  }
   const uint32_t T = __umulhi(w, Q);
-  uint32_t c = 0;
+  uint32_t c = 0, bef = 0, aft = 0xFFFFFFFFu;
   int idx = 0;
 #pragma unroll
   for (int k = 0; k < W; ++k) {
     c += q[k];
     idx += (c <= T) ? 1 : 0;
+    if (wrem) {
+      bef = (c <= T) ? c : bef;
+      aft = (c > T) ? min(aft, c) : aft;
+    }
   }
+  if (wrem) *wrem = remainder_word(T, bef, aft);
   return min(idx, n - 1);
 }
 __device__ __forceinline__ int pick32(const float* x, int n, uint32_t w, int ref_be) {
@@ -405,7 +423,7 @@ __device__ __forceinline__ int pick32(const float* x, int n, uint32_t w, int ref
 // The tile stage over nT <= W tiles of a row held in registers: the largest tile is the
 // reference.
 template <int W>
-__device__ __forceinline__ int pick_tile(const float* Ti, int nT, uint32_t w) {
+__device__ __forceinline__ int pick_tile(const float* Ti, int nT, uint32_t w, uint32_t* wrem = nullptr) {
   float t[W];
   const float4* Ti4 = reinterpret_cast<const float4*>(Ti);
 #pragma unroll
@@ -420,28 +438,34 @@ __device__ __forceinline__ int pick_tile(const float* Ti, int nT, uint32_t w) {
 #pragma unroll
   for (int k = 0; k < W; ++k)
     if (k < nT) tmax = fmaxf(tmax, t[k]);
-  return pick_w<W>(t, nT, w, ref_exponent(tmax));
+  return pick_w<W>(t, nT, w, ref_exponent(tmax), wrem);
 }
 
 // The same pick over n weights in memory (any n; 64-bit sums).
-__device__ __forceinline__ int pick_mem(const float* x, int n, uint32_t w, int ref_be) {
+__device__ __forceinline__ int pick_mem(const float* x, int n, uint32_t w, int ref_be, uint32_t* wrem = nullptr) {
   unsigned long long Q = 0;
   for (int k = 0; k < n; ++k) Q += q24(x[k], ref_be);
-  if (Q == 0ull) return 0;
+  if (Q == 0ull) {
+    if (wrem) *wrem = w;
+    return 0;
+  }
   const unsigned long long T = __umul64hi((unsigned long long)w << 32, Q);
-  unsigned long long c = 0;
+  unsigned long long c = 0, bef = 0, aft = ~0ull;
   int idx = 0;
   for (int k = 0; k < n; ++k) {
     c += q24(x[k], ref_be);
     idx += (c <= T) ? 1 : 0;
+    bef = (c <= T) ? c : bef;
+    aft = (c > T) ? min(aft, c) : aft;
   }
+  if (wrem) *wrem = remainder_word(T, bef, aft);
   return min(idx, n - 1);
 }
 
 // The tile stage over 32 < nT <= 64 tiles of a row in memory (16-byte aligned, nTp >= nT
 // floats, entries past nT ignored): the largest tile is the reference; both halves' image
 // sums, then the chosen half once more (the same index as one pass over all tiles).
-__device__ __forceinline__ int pick_tile64(const float* Ti, int nT, uint32_t w) {
+__device__ __forceinline__ int pick_tile64(const float* Ti, int nT, uint32_t w, uint32_t* wrem = nullptr) {
   const float4* T4 = reinterpret_cast<const float4*>(Ti);
   auto at = [&](const float4& v, int k, int c) {  // element c of the float4 at tile 4k
     const float x = c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
@@ -470,11 +494,15 @@ __device__ __forceinline__ int pick_tile64(const float* Ti, int nT, uint32_t w) 
     }
   }
   const unsigned long long Q = Q1 + Q2;
-  if (Q == 0ull) return 0;
+  if (Q == 0ull) {
+    if (wrem) *wrem = w;
+    return 0;
+  }
   const unsigned long long T = __umul64hi((unsigned long long)w << 32, Q);
   const bool second = T >= Q1;
   const int k0 = second ? 8 : 0;
   unsigned long long c = second ? Q1 : 0ull;
+  unsigned long long bef = c, aft = ~0ull;
   int cnt = second ? 32 : 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -483,10 +511,16 @@ __device__ __forceinline__ int pick_tile64(const float* Ti, int nT, uint32_t w) 
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         c += q24(at(v, k0 + k, e), be);
-        cnt += (4 * (k0 + k) + e < nT && c <= T) ? 1 : 0;
+        const bool in = 4 * (k0 + k) + e < nT;
+        cnt += (in && c <= T) ? 1 : 0;
+        if (wrem && in) {
+          bef = (c <= T) ? c : bef;
+          aft = (c > T) ? min(aft, c) : aft;
+        }
       }
     }
   }
+  if (wrem) *wrem = remainder_word(T, bef, aft);
   return min(cnt, nT - 1);
 }
 
@@ -495,6 +529,11 @@ __device__ __forceinline__ int pick_tile64(const float* Ti, int nT, uint32_t w) 
 //   tile:   pick over the row's tile weights (reference: the largest), word w2;
 //   column: the chosen tile's columns recomputed (pair_exponent + ex2), pick with the
 //           tile weight t_ik as reference, word w3.
+// Systematic mode (in.sys): one 64-bit uniform U of the combination (counter (0, gid, SYS))
+// gives V = floor(U S / 2^64), slot k's row target is T_k = floor((k S + V) / N) =
+// k q + floor((k r + V) / N) with S = q N + r, and w2 / w3 are the remainder words of the
+// row and tile targets inside their chosen entries, so that every slot sits at its own
+// position of the flattened fixed-point CDF, S / N apart.
 // The tiles are held in registers when nT <= 32, the columns when the tile has <= 32.
 template <int D, bool PAD>
 __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint32_t base, int gid, int n,
@@ -506,27 +545,44 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
     j = n % N;
     return;
   }
-  const uint4 w = draw(seed, (uint32_t)n, (uint32_t)gid, kPurposeDense, base, 0u);
-  const unsigned long long Uw = ((unsigned long long)w.x << 32) | (unsigned long long)w.y;
-  const unsigned long long Tg = __umul64hi(Uw, S);
+  unsigned long long Tg;
+  uint32_t w2, w3;
+  if (in.sys) {
+    const uint4 w0 = draw(seed, 0u, (uint32_t)gid, kPurposeSys, base, 0u);
+    const unsigned long long V = __umul64hi(((unsigned long long)w0.x << 32) | (unsigned long long)w0.y, S);
+    const unsigned long long q = S / (unsigned long long)N, r = S % (unsigned long long)N;
+    Tg = (unsigned long long)n * q + ((unsigned long long)n * r + V) / (unsigned long long)N;
+    w2 = w3 = 0u;
+  } else {
+    const uint4 w = draw(seed, (uint32_t)n, (uint32_t)gid, kPurposeDense, base, 0u);
+    Tg = __umul64hi(((unsigned long long)w.x << 32) | (unsigned long long)w.y, S);
+    w2 = w.z;
+    w3 = w.w;
+  }
   int lo = 0, hi = N - 1;  // first i with cum[i] > Tg (cum[N-1] = S > Tg)
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
     if (in.cum[mid] > Tg) hi = mid; else lo = mid + 1;
   }
   i = lo;
+  uint32_t* wr = nullptr;
+  if (in.sys) {
+    const unsigned long long prev = i > 0 ? in.cum[i - 1] : 0ull;
+    w2 = remainder_word(Tg, prev, in.cum[i]);
+    wr = &w3;
+  }
   const float* Ti = in.T + (size_t)i * nTp;
   int kt;
   if (nT <= 16) {
-    kt = pick_tile<16>(Ti, nT, w.z);
+    kt = pick_tile<16>(Ti, nT, w2, wr);
   } else if (nT <= 32) {
-    kt = pick_tile<32>(Ti, nT, w.z);
+    kt = pick_tile<32>(Ti, nT, w2, wr);
   } else if (nT <= 64) {
-    kt = pick_tile64(Ti, nT, w.z);
+    kt = pick_tile64(Ti, nT, w2, wr);
   } else {
     float tmax = 0.f;
     for (int k = 0; k < nT; ++k) tmax = fmaxf(tmax, Ti[k]);
-    kt = pick_mem(Ti, nT, w.z, ref_exponent(tmax));
+    kt = pick_mem(Ti, nT, w2, ref_exponent(tmax), wr);
   }
   const int tbe = ref_exponent(Ti[kt]);
   const int jb = kt * B, ncol = min(jb + B, N) - jb;
@@ -545,7 +601,7 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
       load_row<D>(Vt + q * D, v);
       e[q] = ex2(pair_exponent<D>(u, al, v, bt[q]));
     }
-    j = jb + pick32(e, 32, w.w, tbe);
+    j = jb + pick32(e, 32, w3, tbe);
   } else if (ncol <= 32) {
     float e[32];
 #pragma unroll
@@ -555,7 +611,7 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
       load_row<D>(V + vidx<D, PAD>(jj), v);
       e[q] = (q < ncol) ? ex2(pair_exponent<D>(u, al, v, beta[bidx<PAD>(jj)])) : 0.f;
     }
-    j = jb + pick32(e, ncol, w.w, tbe);
+    j = jb + pick32(e, ncol, w3, tbe);
   } else if (ncol <= 64) {
     // two halves of 32 columns: both image sums, then the chosen half once more.  This is
     // the index of one pass over all columns: every prefix sum of the other half lies on
@@ -579,7 +635,7 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
     const unsigned long long Qc = Q1 + Q2;
     j = jb;
     if (Qc != 0ull) {
-      const unsigned long long Tc = __umul64hi((unsigned long long)w.w << 32, Qc);
+      const unsigned long long Tc = __umul64hi((unsigned long long)w3 << 32, Qc);
       const bool second = Tc >= Q1;
       const int h0 = second ? jb + 32 : jb, hn = second ? n2 : 32;
       unsigned long long cc = second ? Q1 : 0ull;
@@ -601,7 +657,7 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
       Qc += q24(ex2(pair_exponent<D>(u, al, V + vidx<D, PAD>(jj), beta[bidx<PAD>(jj)])), tbe);
     j = jb;
     if (Qc != 0ull) {
-      const unsigned long long Tc = __umul64hi((unsigned long long)w.w << 32, Qc);
+      const unsigned long long Tc = __umul64hi((unsigned long long)w3 << 32, Qc);
       unsigned long long cc = 0;
       int cnt = 0;
       for (int jj = jb; jj < jb + ncol; ++jj) {
@@ -611,6 +667,55 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
       j = jb + min(cnt, ncol - 1);
     }
   }
+}
+
+// ---------------------------------------------------------------- outputs of a combination
+// The pair of slot n, and the new block's first / last index maps (the composition of the
+// Remark in Section 3.1) into the other map buffer; slot N (a conditional root's extra draw)
+// goes to the next reference's root pair.
+struct SlotOut {
+  int32_t *pl, *pr, *first_out, *last_out;
+  const int32_t *first_L, *last_R;
+  bool left_leaf, right_leaf;
+  int N;
+  int32_t* star;
+  __device__ __forceinline__ void put(int n, int i, int j) const {
+    if (n < N) {
+      pl[n] = i;
+      pr[n] = j;
+      first_out[n] = left_leaf ? i : first_L[i];
+      last_out[n] = right_leaf ? j : last_R[j];
+    } else {
+      star[0] = i;
+      star[1] = j;
+    }
+  }
+};
+
+// The output maps of combination cb (and slot 0 of a conditional combination).
+__device__ __forceinline__ SlotOut slot_out(const MergeArgs& a, const Comb& cb, bool write_slot0) {
+  const int at = cb.at, c = cb.c, b = cb.b, K = cb.K;
+  const int N = a.N;
+  const int sR = b - c + 1;
+  const int bufL = cb.level & 1, bufR = ceil_log2(sR) & 1, bufO = (cb.level + 1) & 1;
+  SlotOut o;
+  o.pl = cb.pairs + (size_t)cb.gid * 2 * N;
+  o.pr = o.pl + N;
+  o.first_out = cb.first + ((size_t)bufO * K + at) * N;
+  o.last_out = cb.last + ((size_t)bufO * K + at) * N;
+  o.first_L = cb.first + ((size_t)bufL * K + at) * N;
+  o.last_R = cb.last + ((size_t)bufR * K + c) * N;
+  o.left_leaf = (cb.level == 0);
+  o.right_leaf = (sR == 1);
+  o.N = N;
+  o.star = cb.star;
+  if (cb.conditional && write_slot0) {
+    o.pl[0] = 0;
+    o.pr[0] = 0;
+    o.first_out[0] = o.left_leaf ? 0 : o.first_L[0];
+    o.last_out[0] = o.right_leaf ? 0 : o.last_R[0];
+  }
+  return o;
 }
 
 }  // namespace parts

@@ -18,14 +18,18 @@
 //     tensor core already computes the next block; when one chunk covers the whole row they
 //     also keep their half's running row total, which the row-CDF kernel adds up.
 // Every wait is bounded; on a timeout the CTA records DSMC_ERR_TIMEOUT, waits (bounded) for
-// its own outstanding MMA, frees its TMEM and returns.
+// its own outstanding MMA and for every bulk copy it issued but did not consume, frees its
+// TMEM and returns.
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
+#include "tc_ops.cuh"
 
 namespace dsmc {
 
 namespace {
+
+using namespace tc;
 
 constexpr int kTcRows = 128;                   // MMA M: one TMEM lane per row
 constexpr int kTcCols = 128;                   // MMA N: columns per block
@@ -33,105 +37,6 @@ constexpr int kEpiWarps = 8;
 constexpr int kTcThreads = (kEpiWarps + 1) * 32;
 constexpr int kTileBytes = 128 * 32;           // 128 rows (or columns) x 32 bytes of K
 constexpr uint32_t kTmemCols = 2 * kTcCols;    // two accumulators
-constexpr uint32_t kWaitLimit = 1u << 20;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (uint32_t it = 0; it < kWaitLimit && !done; ++it) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-  }
-  return done != 0;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// No-swizzle K-major operand: 16-byte K chunks 128 bytes apart (leading), 8-row groups 256
-// bytes apart (stride), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
-         ((uint64_t)(256u >> 4) << 32) | ((uint64_t)1 << 46);
-}
-
-// kind::f16 with BF16 operands, or kind::tf32; FP32 accumulator; both K-major; M x N.
-template <int KIND>
-__device__ __forceinline__ uint32_t instr_desc() {
-  const uint32_t fmt = KIND == DSMC_BF16 ? 1u : 2u;
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTcCols >> 3) << 17) |
-         ((uint32_t)(kTcRows >> 4) << 24);
-}
-
-template <int KIND>
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t accum) {
-  const uint32_t idesc = instr_desc<KIND>();
-  if (KIND == DSMC_BF16) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(da), "l"(db), "r"(idesc), "r"(accum));
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(da), "l"(db), "r"(idesc), "r"(accum));
-  }
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-// Issue a 32x32b.x32 TMEM load (one row per lane, 32 consecutive columns); the registers
-// are valid after tmem_wait().
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,"
-      "%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_wait() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// Sum over 32 columns of 2^acc with packed FP32 adds (pairs of columns); columns at or
-// beyond `valid` contribute nothing.  The order of the additions is fixed.
-template <bool MASK>
-__device__ __forceinline__ float exp_sum32(const uint32_t* acc, int valid) {
-  float2 s2 = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int q2 = 0; q2 < 16; ++q2) {
-    float2 e = make_float2(ex2(__uint_as_float(acc[2 * q2])), ex2(__uint_as_float(acc[2 * q2 + 1])));
-    if (MASK) {
-      e.x = 2 * q2 < valid ? e.x : 0.f;
-      e.y = 2 * q2 + 1 < valid ? e.y : 0.f;
-    }
-    s2 = __fadd2_rn(s2, e);
-  }
-  return __fadd_rn(s2.x, s2.y);
-}
-
 // Work item = (combination s, 128-row tile rt, column chunk ch); the grid is persistent
 // (two CTAs per SM) and each CTA walks items blockIdx.x, blockIdx.x + gridDim.x, ...
 struct Item {
@@ -205,8 +110,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
     if (lane == 0) {
       bool ok = true;
       int issued = 0;
-      // load cursor over the CTA's block sequence
+      // load cursor over the CTA's block sequence; a_armed / a_seen count the row tiles
+      // loaded and waited for, q_seen the column blocks waited for (lq counts those loaded)
       int l_it = blockIdx.x, l_b = 0, lq = 0;
+      int a_armed = 0, a_seen = 0, q_seen = 0;
       Item li = item_of(a, l_it);
       const size_t plane = (size_t)a.Nr * 32;  // bytes of one K plane of one combination
       auto load_next = [&]() {  // the P planes of the next column block, one barrier
@@ -234,6 +141,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
       };
       auto load_a = [&](int it, int slot) {
         if (it >= n_items) return;
+        ++a_armed;
         const Item t = item_of(a, it);
         const unsigned char* src = a.ws.Ub + (size_t)t.s * P * plane + (size_t)t.rt * kTileBytes;
         const uint32_t bar = smem_u32(&bar_a[slot]);
@@ -261,6 +169,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
       for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++k) {
         const Item cur = item_of(a, it);
         ok = mbar_wait(smem_u32(&bar_a[k & 1]), (uint32_t)(k >> 1) & 1);
+        if (ok) ++a_seen;
         const uint32_t sa = smem_u32(sA + (size_t)(k & 1) * kSlotBytes);
         for (int b = 0; b < cur.nblk && ok; ++b, ++q) {
           const int buf = q & 1;
@@ -268,6 +177,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
           if (q >= 2) ok = mbar_wait(smem_u32(&bar_epi[buf]), (uint32_t)((q >> 1) - 1) & 1);
           if (ok) ok = mbar_wait(smem_u32(&bar_v[slot]), (uint32_t)(q / kVSlots) & 1);
           if (!ok) break;
+          q_seen = q + 1;
           if (a.stall) continue;  // test switch: nothing is issued, no accumulator completes
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sv = smem_u32(sV + (size_t)slot * kSlotBytes);
@@ -302,6 +212,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
         mbar_wait(smem_u32(&bar_vfree[qq % kVSlots]), (uint32_t)(qq / kVSlots) & 1);
       }
       if (last_item >= 0) mbar_wait(smem_u32(&bar_afree[last_item & 1]), (uint32_t)(last_item >> 1) & 1);
+      // bulk copies issued but never waited for (an aborted walk) must land before the
+      // shared memory is released: one bounded wait on each pending phase (a slot or row
+      // buffer has at most one pending phase, since it is refilled only after it was read)
+      for (int qq = q_seen; qq < lq; ++qq)
+        mbar_wait(smem_u32(&bar_v[qq % kVSlots]), (uint32_t)(qq / kVSlots) & 1);
+      for (int kk = a_seen; kk < a_armed; ++kk)
+        mbar_wait(smem_u32(&bar_a[kk & 1]), (uint32_t)(kk >> 1) & 1);
       if (!ok) {
         atomicExch(&abort_s, 1);
         record_status(a.ws.status, DSMC_ERR_TIMEOUT);
@@ -389,7 +306,8 @@ cudaError_t launch_t(const MergeArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int RT = (a.N + kTcRows - 1) / kTcRows;
   const int n_items = a.mc * RT * a.CH;
-  const int grid = n_items < 2 * 152 ? n_items : 2 * 152;
+  const int full = 2 * (a.sms > 0 ? a.sms : 1);  // two resident CTAs per SM
+  const int grid = n_items < full ? n_items : full;
   rowsum_tc_kernel<KIND, P><<<grid, kTcThreads, kDynSmem, st>>>(a, n_items);
   return cudaGetLastError();
 }

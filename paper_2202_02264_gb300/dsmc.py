@@ -26,10 +26,10 @@ from . import workloads as W
 OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "workspace too small",
           5: "CUDA error", 6: "non-finite log-weight", 7: "degenerate weights",
-          8: "rejection-sampling attempt cap", 9: "timeout"}
+          8: "rejection-sampling attempt cap", 9: "timeout", 10: "lazy-sampler bound exceeded"}
 
 FP32, TF32, BF16 = 0, 1, 2
-MULTINOMIAL, RS, MH = 0, 1, 2
+MULTINOMIAL, RS, MH, SYSTEMATIC, RS_FACTORED = 0, 1, 2, 3, 4
 
 
 class DsmcError(RuntimeError):
@@ -55,7 +55,7 @@ class Config(C.Structure):
     _fields_ = [("K", C.c_int), ("N", C.c_int), ("compute", C.c_int), ("resampler", C.c_int),
                 ("seed", C.c_uint64), ("counter_base", C.c_uint32),
                 ("rs_max_attempts", C.c_uint32), ("max_merges_per_launch", C.c_int),
-                ("fused_max_merges", C.c_int)]
+                ("fused_max_merges", C.c_int), ("tc_fused", C.c_int)]
 
 
 class State(C.Structure):
@@ -82,7 +82,8 @@ EXPORTS = ["dsmc_status_string", "dsmc_last_error", "dsmc_state_sizes", "dsmc_wo
            "dsmc_debug_stall_tensor_cores",
            "dsmc_batch_workspace_size", "dsmc_batch_prepare", "dsmc_batch_run", "dsmc_smooth_batch",
            "dsmc_seq_maps_bytes", "dsmc_serve_workspace_size", "dsmc_serve_tick",
-           "dsmc_profile_breakdown_enable", "dsmc_profile_breakdown_read"]
+           "dsmc_profile_breakdown_enable", "dsmc_profile_breakdown_read", "dsmc_profile_unit_rates",
+           "dsmc_debug_lazy_weights", "dsmc_lazy_attempts", "dsmc_debug_row_shift", "dsmc_debug_keep_weights"]
 
 
 def library_path() -> str:
@@ -126,6 +127,7 @@ def load(build_if_needed: bool = False) -> C.CDLL:
                                           C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         lib.dsmc_debug_philox.argtypes = [vp, C.c_int64, C.c_uint64, vp, vp]
         lib.dsmc_debug_stall_tensor_cores.argtypes = [C.c_int]
+        lib.dsmc_debug_keep_weights.argtypes = [C.c_int]
         lib.dsmc_debug_merge_weights.argtypes = [cfgp, modp, C.c_int, C.c_int, vp, vp, vp, vp, vp,
                                                  vp, C.POINTER(C.c_int), vp, sz, vp]
         lib.dsmc_seq_maps_bytes.restype = C.c_size_t
@@ -134,6 +136,11 @@ def load(build_if_needed: bool = False) -> C.CDLL:
         lib.dsmc_serve_tick.argtypes = [cfgp, modp, prop_p, C.c_int, C.POINTER(Seq), C.POINTER(C.c_int), vp, sz, vp]
         lib.dsmc_profile_breakdown_enable.argtypes = [C.c_int]
         lib.dsmc_profile_breakdown_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        lib.dsmc_profile_unit_rates.argtypes = [vp, C.POINTER(C.c_double), vp]
+        lib.dsmc_debug_lazy_weights.argtypes = [cfgp, modp, C.c_int, C.c_int, vp, vp, vp, C.POINTER(C.c_int),
+                                                vp, sz, vp]
+        lib.dsmc_lazy_attempts.argtypes = [cfgp, modp, vp, sz, vp, C.POINTER(C.c_uint64)]
+        lib.dsmc_debug_row_shift.argtypes = [cfgp, modp, C.c_int, C.c_int, vp, vp, vp, sz, vp]
         seqp = C.POINTER(Seq)
         lib.dsmc_batch_workspace_size.argtypes = [cfgp, modp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         for name in ("dsmc_batch_prepare", "dsmc_batch_run", "dsmc_smooth_batch"):
@@ -184,10 +191,10 @@ class HostModel:
 
 
 def make_config(K, N, seed, counter_base=0, resampler=MULTINOMIAL, compute=FP32,
-                rs_max_attempts=0, max_merges_per_launch=0, fused_max_merges=0) -> Config:
+                rs_max_attempts=0, max_merges_per_launch=0, fused_max_merges=0, tc_fused=0) -> Config:
     return Config(int(K), int(N), int(compute), int(resampler), int(seed) & (2**64 - 1),
                   int(counter_base), int(rs_max_attempts), int(max_merges_per_launch),
-                  int(fused_max_merges))
+                  int(fused_max_merges), int(tc_fused))
 
 
 def make_proposal(m: W.SSM, K: int, device="cuda"):
@@ -286,6 +293,10 @@ def dsmc_debug_stall_tensor_cores(enable: bool):
     _check(load().dsmc_debug_stall_tensor_cores(int(bool(enable))), "dsmc_debug_stall_tensor_cores")
 
 
+def dsmc_debug_keep_weights(enable: bool):
+    _check(load().dsmc_debug_keep_weights(int(bool(enable))), "dsmc_debug_keep_weights")
+
+
 def dsmc_debug_philox(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
     ctr = ctr.contiguous()
     out = torch.empty_like(ctr)
@@ -322,6 +333,40 @@ def dsmc_debug_merge_weights(cfg, model, level, m, ws,
     return out
 
 
+def dsmc_debug_lazy_weights(cfg, model, level, m, ws, stream=None):
+    """The factorised proposals (pa, pc [N]) and acceptance ratios (acc [N][N]) of one
+    combination after dsmc_merge_level with DSMC_RS_FACTORED."""
+    N = cfg.N
+    info = (C.c_int * 4)()
+    dev = ws.device
+    out = {"pa": torch.empty((N,), dtype=torch.float32, device=dev),
+           "pc": torch.empty((N,), dtype=torch.float32, device=dev),
+           "acc": torch.empty((N, N), dtype=torch.float32, device=dev)}
+    _check(load().dsmc_debug_lazy_weights(C.byref(cfg), C.byref(model.struct), int(level), int(m),
+                                          _ptr(out["pa"]), _ptr(out["pc"]), _ptr(out["acc"]), info, _ptr(ws),
+                                          ws.numel(), _stream(stream)), "dsmc_debug_lazy_weights")
+    out.update(gid=info[2], left_leaf=info[3])
+    return out
+
+
+def dsmc_debug_row_shift(cfg, model, level, m, ws, stream=None):
+    """(shift [N] FP64, delta [N] FP32): the per-row scale of the tile and element weights of
+    one combination after dsmc_merge_level with a dense resampler."""
+    N = cfg.N
+    sh = torch.empty((N,), dtype=torch.float64, device=ws.device)
+    dl = torch.empty((N,), dtype=torch.float32, device=ws.device)
+    _check(load().dsmc_debug_row_shift(C.byref(cfg), C.byref(model.struct), int(level), int(m), _ptr(sh), _ptr(dl),
+                                       _ptr(ws), ws.numel(), _stream(stream)), "dsmc_debug_row_shift")
+    return sh, dl
+
+
+def dsmc_lazy_attempts(cfg, model, ws, stream=None) -> int:
+    out = C.c_uint64(0)
+    _check(load().dsmc_lazy_attempts(C.byref(cfg), C.byref(model.struct), _ptr(ws), ws.numel(), _stream(stream),
+                                     C.byref(out)), "dsmc_lazy_attempts")
+    return int(out.value)
+
+
 def dsmc_batch_workspace_size(cfg: Config, model: HostModel, Ks) -> int:
     K = (C.c_int * len(Ks))(*[int(k) for k in Ks])
     out = C.c_size_t(0)
@@ -348,7 +393,7 @@ def dsmc_smooth_batch(cfg, model, prop, seqs, ws, stream=None):
     _batch_call("dsmc_smooth_batch", cfg, model, prop, seqs, ws, stream)
 
 
-KINDS = ["init", "prologue", "tile_sums", "draws", "fused_levels", "resolve", "gather", "other"]
+KINDS = ["init", "prologue", "tile_sums", "draws", "fused_levels", "resolve", "gather", "fused_tc_levels"]
 
 
 def dsmc_profile_breakdown_enable(enable: bool):
@@ -360,6 +405,17 @@ def dsmc_profile_breakdown_read() -> dict:
     n = (C.c_int64 * 8)()
     _check(load().dsmc_profile_breakdown_read(ms, n), "dsmc_profile_breakdown_read")
     return {KINDS[k]: {"ms": ms[k], "launches": int(n[k])} for k in range(8) if n[k] > 0}
+
+
+UNIT_NAMES = ["ex2", "ffma", "ffma2_lanes", "fadd"]
+
+
+def dsmc_profile_unit_rates(stream=None) -> dict:
+    """Results per second of the device's MUFU ex2, FFMA, FFMA2 (lanes) and FADD units."""
+    sink = torch.zeros((1,), dtype=torch.float32, device="cuda")
+    out = (C.c_double * 4)()
+    _check(load().dsmc_profile_unit_rates(_ptr(sink), out, _stream(stream)), "dsmc_profile_unit_rates")
+    return {UNIT_NAMES[k]: out[k] for k in range(4)}
 
 
 def dsmc_seq_maps_bytes(K: int, N: int) -> int:
@@ -388,14 +444,14 @@ class Smoother:
 
     def __init__(self, model: W.SSM, K: int, N: int, seed: int = 0, resampler: int = MULTINOMIAL,
                  compute: int = FP32, rs_max_attempts: int = 0, max_merges_per_launch: int = 0,
-                 device: str = "cuda", want_traj: bool = False, fused_max_merges: int = 0):
+                 device: str = "cuda", want_traj: bool = False, fused_max_merges: int = 0, tc_fused: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("dSMC needs a CUDA device; there is no CPU path")
         self.model = model
         self.hm = HostModel(model)
         self.K, self.N, self.d = int(K), int(N), model.d
         self.cfg = make_config(K, N, seed, 0, resampler, compute, rs_max_attempts, max_merges_per_launch,
-                               fused_max_merges)
+                               fused_max_merges, tc_fused)
         self.prop, self._prop_keep = make_proposal(model, K, device)
         sizes = dsmc_state_sizes(self.cfg, self.hm)
         self.X = torch.empty((self.K, self.N, self.d), dtype=torch.float32, device=device)
@@ -457,7 +513,7 @@ class BatchSmoother:
 
     def __init__(self, model: W.SSM, Ks, N: int, seeds=None, resampler: int = MULTINOMIAL,
                  compute: int = FP32, max_merges_per_launch: int = 0, fused_max_merges: int = 0,
-                 device: str = "cuda", want_m2: bool = False):
+                 device: str = "cuda", want_m2: bool = False, tc_fused: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("dSMC needs a CUDA device; there is no CPU path")
         self.model = model
@@ -468,7 +524,7 @@ class BatchSmoother:
         self.seeds = list(seeds) if seeds is not None else [1000 + i for i in range(n)]
         self.counter_base = [0] * n
         self.cfg = make_config(max(self.Ks), N, 0, 0, resampler, compute, 0, max_merges_per_launch,
-                               fused_max_merges)
+                               fused_max_merges, tc_fused)
         if model.prop_kind == W.PROP_GAUSS:
             self.prop = Proposal(W.PROP_GAUSS, 1.0, None, None, int(model.nu))
         else:

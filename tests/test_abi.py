@@ -71,17 +71,24 @@ def test_sizes_and_argument_checks(lib):
 
 
 def test_lazy_samplers_plan_no_dense_buffers(lib):
-    """DSMC_RS and DSMC_MH lift the dense N limit and plan neither tile sums nor
-    tensor-core operands, whatever the precision field says; an unknown sampler is refused."""
+    """The lazy samplers (DSMC_RS, DSMC_RS_FACTORED, DSMC_MH) lift the dense N limit and plan
+    neither tile sums nor tensor-core operands, whatever the precision field says; the
+    systematic sampler is dense (same limit and buffers as multinomial); an unknown sampler
+    is refused."""
     dsmc, W, hm = _structs()
     dense = dsmc.dsmc_workspace_size(dsmc.make_config(64, 1024, 1, compute=dsmc.BF16), hm)
-    for res in (dsmc.RS, dsmc.MH):
+    assert dsmc.dsmc_workspace_size(dsmc.make_config(64, 1024, 1, compute=dsmc.BF16,
+                                                     resampler=dsmc.SYSTEMATIC), hm) == dense
+    with pytest.raises(dsmc.DsmcError) as e:
+        dsmc.dsmc_workspace_size(dsmc.make_config(8, 20000, 1, resampler=dsmc.SYSTEMATIC), hm)
+    assert e.value.code == 2
+    for res in (dsmc.RS, dsmc.RS_FACTORED, dsmc.MH):
         lazy_bf16 = dsmc.dsmc_workspace_size(dsmc.make_config(64, 1024, 1, resampler=res, compute=dsmc.BF16), hm)
         lazy_fp32 = dsmc.dsmc_workspace_size(dsmc.make_config(64, 1024, 1, resampler=res), hm)
         assert lazy_bf16 == lazy_fp32 < dense
         assert dsmc.dsmc_workspace_size(dsmc.make_config(8, 20000, 1, resampler=res), hm) > 0
     with pytest.raises(dsmc.DsmcError) as e:
-        dsmc.dsmc_workspace_size(dsmc.make_config(8, 64, 1, resampler=3), hm)
+        dsmc.dsmc_workspace_size(dsmc.make_config(8, 64, 1, resampler=5), hm)
     assert e.value.code == 1
 
 
@@ -97,5 +104,5 @@ def test_invalid_model_rejected(lib):
 
 def test_status_strings(lib):
     lib.dsmc_status_string.restype = C.c_char_p
-    for code in [0, 1, 2, 3, 5, 6, 7, 8, 9]:
+    for code in [0, 1, 2, 3, 5, 6, 7, 8, 9, 10]:
         assert lib.dsmc_status_string(code)
