@@ -408,15 +408,17 @@ def run_batched(args):
     seeds = [1000 + 7919 * rank + i for i in range(len(Ks))]
     from paper_2202_02264_gb300 import autotune
     if args.schedule:
-        fm, mc = (int(v) for v in args.schedule.split(","))
-        tuned = {"fused_max_merges": fm, "max_merges_per_launch": mc, "timings": {}}
+        v = [int(x) for x in args.schedule.split(",")]
+        tuned = {"fused_max_merges": v[0], "max_merges_per_launch": v[1], "tc_fused": v[2] if len(v) > 2 else 0,
+                 "timings": {}}
     elif args.no_autotune:
-        tuned = {"fused_max_merges": 0, "max_merges_per_launch": 0, "timings": {}}
+        tuned = {"fused_max_merges": 0, "max_merges_per_launch": 0, "tc_fused": 0, "timings": {}}
     else:
         tuned = autotune.tune_batch(model, Ks, N, bw.ys, compute, use_cache=False)   # untimed
     b = dsmc.BatchSmoother(model, Ks, N, seeds=seeds, compute=compute,
                            fused_max_merges=tuned["fused_max_merges"],
-                           max_merges_per_launch=tuned["max_merges_per_launch"])
+                           max_merges_per_launch=tuned["max_merges_per_launch"],
+                           tc_fused=tuned["tc_fused"])
     ys = [torch.as_tensor(y, dtype=torch.float32, device=dev) for y in bw.ys]
     b.set_inputs(ys)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -509,6 +511,7 @@ def run_batched(args):
                        "parallelism": f"replicas x{world}",
                        "autotuned": {"fused_max_merges": tuned["fused_max_merges"],
                                      "max_merges_per_launch": tuned["max_merges_per_launch"],
+                                     "tc_fused": tuned["tc_fused"],
                                      "candidates_ms": tuned["timings"]}},
             "plain_fp32_per_request": ({"value": plain_value, "unit": UNIT,
                                         "ms_per_batch": 1e3 * t_plain,

@@ -146,11 +146,12 @@ typedef struct {
                                  FP32 cross term); 0 = default (32; none with a
                                  tensor-core precision and dx > 8), < 0 = never */
   int tc_fused;               /* dense sampler with a tensor-core precision, N <= 512, dx <= 4:
-                                 0 = default, every other level chunk runs as one persistent
-                                 warp-specialised kernel (operand rows, tcgen05 cross term,
-                                 exponentials, row CDF and draws of each combination on one
-                                 SM, nothing but pairs, maps and log L written); < 0 = the
-                                 split kernels (terms, tile sums, draws).  Same results. */
+                                 > 0 = every level chunk not run as a fused small level runs
+                                 as one persistent warp-specialised kernel (operand rows,
+                                 tcgen05 cross term, exponentials, row CDF and draws of each
+                                 combination on one SM; nothing but pairs, maps and log L
+                                 written); 0 (default) or < 0 = the split kernels (terms,
+                                 tile sums, draws).  Same results. */
 } dsmc_config_t;
 
 /* Caller-owned DEVICE state of one smoothing (sizes from dsmc_state_sizes()).

@@ -619,7 +619,7 @@ dsmc_status_t launch_combs(const Plan& p, const dsmc_config_t* cfg, const ParamB
         continue;
       }
     }
-    if (p.dense && cfg->tc_fused >= 0 && fused_tc_supported(p.D, p.N, p.compute, p.planes)) {
+    if (p.dense && cfg->tc_fused > 0 && fused_tc_supported(p.D, p.N, p.compute, p.planes)) {
       DSMC_CUDA(prof_begin(s), "profile event");
       DSMC_CUDA(bd_begin(s, DSMC_KIND_FUSED_TC), "profile event");
       DSMC_CUDA(launch_merge_tc_fused(p.D, a, mp.bytes, s), "fused tensor-core level kernel");

@@ -16,7 +16,7 @@
 //     tile, column block) into one of four 128-column TMEM accumulators;
 //   - 8 epilogue warps read each accumulator (tcgen05.ld), take 2^x on MUFU and keep the
 //     tile sums and each row's two half totals in shared memory;
-//   - 8 draw warps, for combination k - 1: the row totals, the row weights and their exact
+//   - 7 draw warps, for combination k - 1: the row totals, the row weights and their exact
 //     2^40 fixed-point prefix sums, the increment of Eq. (Lab), then every slot's pair in
 //     three exact inverse-CDF stages (row, tile, column recomputed in FP32) and the new
 //     block's index maps.
@@ -45,8 +45,8 @@ using namespace tc;
 constexpr int kFNmax = 512;                 // largest N of the fused level
 constexpr int kFEpiWarps = 8;               // warps 0..7 (TMEM lane quarter = warp % 4)
 constexpr int kFLoadWarps = 4;              // warps 8..11
-constexpr int kFDrawWarps = 8;              // warps 12..19
-constexpr int kFCtrlWarp = kFEpiWarps + kFLoadWarps + kFDrawWarps;  // warp 20
+constexpr int kFDrawWarps = 7;              // warps 12..18 (20 warps in all: 96 registers each)
+constexpr int kFCtrlWarp = kFEpiWarps + kFLoadWarps + kFDrawWarps;  // warp 19
 constexpr int kFThreads = (kFCtrlWarp + 1) * 32;
 constexpr int kFLoadThreads = kFLoadWarps * 32;
 constexpr int kFDrawThreads = kFDrawWarps * 32;
