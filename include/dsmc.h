@@ -257,6 +257,29 @@ dsmc_status_t dsmc_smooth_noalloc(const dsmc_config_t* cfg, const dsmc_model_t* 
                                   float* traj_out, double* mean_out, double* m2_out,
                                   double* logL_out, dsmc_status_t* device_status, void* stream);
 
+/* ---- Parallel-in-time Gaussian proposals (Section 4.1, Algorithm 4).  The model is
+ * linearised around Gaussian marginals q_t = N(m_t, P_t) and smoothed exactly by the
+ * temporally parallel Kalman filter and RTS smoother (prefix scans of an associative
+ * operator over the K steps, ceil(log2 K) levels each, FP64 on the device); the smoothed
+ * marginals become the next q_t.  For the linear-Gaussian model the linearisation is the
+ * model itself and one pass is exact (the Kalman/RTS marginals).  For the stochastic-
+ * volatility model, whose observation noise is not additive, each pass expands
+ * log h_t(y_t | x) to second order around m_t (a Gaussian pseudo-observation with variance
+ * 1 / lambda_t, lambda_t = y_t^2 e^{-m_t} / 2; none where lambda_t vanishes), starting from
+ * init_mean or the stationary mean; the iterations move to the posterior mode and its
+ * curvature.  The outputs are the means and the marginal standard deviations, ready for
+ * DSMC_PROP_GAUSS with nu = DSMC_NU_EQ_Q (q_t = nu_t, as the paper uses them).
+ *   y:          DEVICE [K][dx] FP32 observations
+ *   iterations: passes for the SV model (>= 1; the linear-Gaussian model takes one)
+ *   init_mean:  DEVICE [K][dx] FP32 linearisation point of the first pass, or NULL
+ *   mean_out, std_out: DEVICE [K][dx] FP32
+ *   ws:         DEVICE workspace of dsmc_gaussian_proposals_workspace_size bytes; its first
+ *               word is a status word (dsmc_stream_status) recording DSMC_ERR_NONFINITE. */
+dsmc_status_t dsmc_gaussian_proposals_workspace_size(const dsmc_model_t* model, int K, size_t* bytes);
+dsmc_status_t dsmc_gaussian_proposals(const dsmc_model_t* model, int K, const float* y, int iterations,
+                                      const float* init_mean, float* mean_out, float* std_out, void* ws,
+                                      size_t ws_bytes, void* stream);
+
 /* Synchronises `stream` and returns in *device_status the first error any kernel recorded
  * in this workspace since the last dsmc_init_particles (DSMC_OK if none). */
 dsmc_status_t dsmc_stream_status(void* ws, void* stream, dsmc_status_t* device_status);

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdsmc.so")
-SOURCES = ["init.cu", "merge.cu", "level_fused.cu", "rowsum_tc.cu", "gather.cu", "api.cu", "probe.cu", "merge_tc_fused.cu"]
+SOURCES = ["init.cu", "merge.cu", "level_fused.cu", "rowsum_tc.cu", "gather.cu", "api.cu", "probe.cu", "merge_tc_fused.cu", "pit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

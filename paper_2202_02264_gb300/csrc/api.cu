@@ -148,7 +148,7 @@ struct Plan {
   int R, rows_per_cta;
   bool dense;
   int level_off[33];
-  size_t o_status, o_U, o_alpha, o_V, o_beta, o_shift, o_logbar, o_inc, o_T, o_rw, o_rowsum, o_rowpart, o_cum,
+  size_t o_status, o_U, o_alpha, o_V, o_beta, o_shift, o_logbar, o_inc, o_T, o_rw, o_rowsum, o_cum,
       o_delta, o_first, o_last, o_star, o_Ub, o_Vb, o_attempts, o_alpha0, o_kappa, o_pa, o_pc, o_cumA, o_cumC,
       total;
 };
@@ -235,7 +235,6 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p, int
   p.o_last = take(no_maps ? 0 : 2 * (size_t)p.K * p.N * sizeof(int32_t));
   p.o_star = take(2 * sizeof(int32_t));
   const bool tc = p.compute != DSMC_FP32;
-  p.o_rowpart = take(tc ? 2 * MN * sizeof(float) : 0);
   p.o_Ub = take(tc ? (size_t)p.Mc * p.planes * p.Nr * 32 : 0);
   p.o_Vb = take(tc ? (size_t)p.Mc * p.planes * p.Nr * 32 : 0);
   p.o_alpha0 = take(factored ? MN * sizeof(float) : 0);
@@ -261,7 +260,6 @@ WsPtrs ws_ptrs(const Plan& p, void* ws) {
   w.T = reinterpret_cast<float*>(b + p.o_T);
   w.rw = reinterpret_cast<float*>(b + p.o_rw);
   w.rowsum = reinterpret_cast<float*>(b + p.o_rowsum);
-  w.rowpart = reinterpret_cast<float*>(b + p.o_rowpart);
   w.cum = reinterpret_cast<unsigned long long*>(b + p.o_cum);
   w.delta = reinterpret_cast<float*>(b + p.o_delta);
   w.first = reinterpret_cast<int32_t*>(b + p.o_first);
@@ -1364,6 +1362,74 @@ dsmc_status_t dsmc_smooth_noalloc(const dsmc_config_t* cfg, const dsmc_model_t* 
     DSMC_CUDA(cudaStreamSynchronize(s), "stream synchronize");
     *device_status = static_cast<dsmc_status_t>(h);
   }
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_gaussian_proposals_workspace_size(const dsmc_model_t* model, int K, size_t* bytes) {
+  if (!model || !bytes) return fail(DSMC_ERR_INVALID_ARG, "null argument");
+  dsmc_config_t c;
+  std::memset(&c, 0, sizeof(c));
+  c.K = K;
+  c.N = 1;
+  DSMC_TRY(check_config(&c, model));
+  *bytes = pit_workspace_bytes(K, model->dx);
+  return DSMC_OK;
+}
+
+dsmc_status_t dsmc_gaussian_proposals(const dsmc_model_t* model, int K, const float* y, int iterations,
+                                      const float* init_mean, float* mean_out, float* std_out, void* ws,
+                                      size_t ws_bytes, void* stream) {
+  if (!model || !y || !mean_out || !std_out) return fail(DSMC_ERR_INVALID_ARG, "null argument");
+  dsmc_config_t c;
+  std::memset(&c, 0, sizeof(c));
+  c.K = K;
+  c.N = 1;
+  DSMC_TRY(check_config(&c, model));
+  if (iterations < 1) return fail(DSMC_ERR_INVALID_ARG, "iterations must be >= 1");
+  if (!ws) return fail(DSMC_ERR_INVALID_ARG, "null workspace");
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return fail(DSMC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  const int d = model->dx;
+  if (ws_bytes < pit_workspace_bytes(K, d)) return fail(DSMC_ERR_WORKSPACE, "workspace too small");
+  // the model in FP64: F, Q, R, P0 [d][d], c, m0 [d]
+  std::vector<double> mdl(4 * (size_t)d * d + 2 * (size_t)d, 0.0);
+  double* F = mdl.data();
+  double* Q = F + d * d;
+  double* R = Q + d * d;
+  double* P0 = R + d * d;
+  double* cc = P0 + d * d;
+  double* m0 = cc + d;
+  PitArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.K = K;
+  pa.d = d;
+  pa.kind = model->kind;
+  pa.y = y;
+  if (model->kind == DSMC_MODEL_SV) {
+    const double s2 = model->sigma * model->sigma;
+    F[0] = model->phi;
+    Q[0] = s2;
+    R[0] = 0.0;  // pseudo-observations carry their own variances
+    P0[0] = s2 / (1.0 - model->phi * model->phi);
+    cc[0] = model->mu * (1.0 - model->phi);
+    m0[0] = model->mu;
+    pa.mu = model->mu;
+  } else {
+    double L[kMaxDim * kMaxDim];
+    if (!cholesky(d, model->Q, L) || !cholesky(d, model->R, L) || !cholesky(d, model->P0, L))
+      return fail(DSMC_ERR_INVALID_ARG, "Q, R and P0 must be positive definite");
+    for (int i = 0; i < d * d; ++i) {
+      F[i] = model->A[i];
+      Q[i] = model->Q[i];
+      R[i] = model->R[i];
+      P0[i] = model->P0[i];
+    }
+    for (int i = 0; i < d; ++i) m0[i] = model->m0[i];
+  }
+  int launches = 0;
+  DSMC_CUDA(launch_pit(pa, mdl.data(), iterations, init_mean, mean_out, std_out, ws,
+                       static_cast<cudaStream_t>(stream), &launches),
+            "linearised smoother kernels");
+  prof_count(launches);
   return DSMC_OK;
 }
 

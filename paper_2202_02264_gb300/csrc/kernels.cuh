@@ -21,8 +21,6 @@ struct WsPtrs {
   float* T;          // [Mc][N][nTp] tile weights, relative to the row shift
   float* rw;         // [Mc][N]      row weights of the row stage
   float* rowsum;     // [Mc][N]      row totals (sums of the tile weights)
-  float* rowpart;    // [Mc][2][N]   tensor-core path, one column chunk: each epilogue half's
-                     //              running sum of its tile weights (the row total is their sum)
   unsigned long long* cum;  // [Mc][N] exact 2^40 fixed-point prefix sums of the row weights
   float* delta;      // [Mc][N]      extra base-2 shift of rows recomputed after underflow
   int32_t* first;    // [2][K][N]    first-time particle index of each block (double-buffered)
@@ -236,6 +234,18 @@ struct GatherArgs {
   float* x_star;
   int* status;
 };
+
+// The linearised Gaussian smoother of Section 4.1 (Algorithm 4): the model in FP64 (device
+// pointers into its workspace, set by launch_pit), observations [K][d].
+struct PitArgs {
+  int K, d, kind;
+  const float* y;
+  const double *F, *Q, *R, *P0, *c, *m0;   // [d][d] x 4, [d] x 2
+  double mu;                                // SV: the stationary mean (first linearisation)
+};
+size_t pit_workspace_bytes(int K, int d);
+cudaError_t launch_pit(PitArgs pa, const double* model, int iterations, const float* init_mean, float* mean_out,
+                       float* std_out, void* ws, cudaStream_t st, int* n_launches);
 
 // Launchers (defined in the .cu files, dispatched on the padded dimension D).
 cudaError_t launch_init(int D, const InitArgs& a, const void* mp, cudaStream_t s);

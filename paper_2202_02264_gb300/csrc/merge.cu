@@ -605,7 +605,6 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
     sB[bidx<true>(q)] = beta[q];
     sAl[q] = alpha[q];
   }
-  const bool parts = a.compute != DSMC_FP32 && a.CH == 1;
   // row totals (and the staged copy of the tile sums)
   for (int i = threadIdx.x; i < N; i += NT) {
     if (sT) {
@@ -615,8 +614,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
     }
     // the row total: the tensor-core epilogue's two half sums when it covered the whole row
     // in one chunk, else the tile weights in ascending order
-    float t = parts ? __fadd_rn(a.ws.rowpart[((size_t)s * 2) * N + i], a.ws.rowpart[((size_t)s * 2 + 1) * N + i])
-                    : (sT ? row_total(sT + (size_t)i * L.nTs, nT, nTp) : row_total(Tt + (size_t)i * nTp, nT, nTp));
+    float t = sT ? row_total(sT + (size_t)i * L.nTs, nT, nTp) : row_total(Tt + (size_t)i * nTp, nT, nTp);
     if (isnan(t)) {
       nonfinite_s = 1;
       t = 0.f;

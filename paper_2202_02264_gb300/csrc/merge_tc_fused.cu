@@ -15,7 +15,7 @@
 //   - 1 control thread issues, for combination k, one tcgen05.mma (M = N = 128) per (row
 //     tile, column block) into one of four 128-column TMEM accumulators;
 //   - 8 epilogue warps read each accumulator (tcgen05.ld), take 2^x on MUFU and keep the
-//     tile sums and each row's two half totals in shared memory;
+//     tile sums in shared memory;
 //   - 7 draw warps, for combination k - 1: the row totals, the row weights and their exact
 //     2^40 fixed-point prefix sums, the increment of Eq. (Lab), then every slot's pair in
 //     three exact inverse-CDF stages (row, tile, column recomputed in FP32) and the new
@@ -60,22 +60,26 @@ constexpr int kFTiles = kFNmax / 32;        // tiles of 32 columns per row (tile
 
 __host__ __device__ constexpr size_t rnd(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Byte offsets inside one stage (one combination's data).
+// Byte offsets inside one stage (one combination's data, N <= 512):
+//   opU, opV  the MMA row and column operands, [512][32 B] each, canonical K-major layout
+//   fV, fB    v_j [N][D] and beta_j, padded after every 32 columns (FP32)
+//   fU        u_i [N][D];  fAl alpha_i;  fDl delta_i (FP32);  fSh shift_i (FP64)
+//   T         tile weights [N][16] (before the MMA: the loader's staged inputs)
+//   cum       exact prefix sums of the row weights (u64);  fL the row log weights
 template <int D>
 struct Stage {
-  static constexpr size_t opU = 0;                                          // [512][32 B] MMA rows
-  static constexpr size_t opV = opU + (size_t)kFNmax * 32;                 // [512][32 B] MMA columns
-  static constexpr size_t fV = opV + (size_t)kFNmax * 32;                  // v_j, padded
+  static constexpr size_t opU = 0;
+  static constexpr size_t opV = opU + (size_t)kFNmax * 32;
+  static constexpr size_t fV = opV + (size_t)kFNmax * 32;
   static constexpr size_t fB = fV + rnd((size_t)(kFNmax * D + (kFNmax / 32) * kVPad<D>) * 4, 16);
-  static constexpr size_t fU = fB + rnd((size_t)(kFNmax + kFNmax / 32) * 4, 16);  // beta_j, padded
-  static constexpr size_t fAl = fU + (size_t)kFNmax * D * 4;                // u_i [N][D]
-  static constexpr size_t fDl = fAl + (size_t)kFNmax * 4;                   // alpha_i
-  static constexpr size_t fSh = fDl + (size_t)kFNmax * 4;                   // delta_i
-  static constexpr size_t T = fSh + (size_t)kFNmax * 8;                     // shift_i (FP64)
-  static constexpr size_t rp = T + (size_t)kFNmax * kFTiles * 4;            // tile weights [N][16]
-  static constexpr size_t cum = rp + (size_t)2 * kFNmax * 4;                // half totals [2][512]
-  static constexpr size_t fL = cum + (size_t)kFNmax * 8;                    // prefix sums
-  static constexpr size_t bytes = rnd(fL + (size_t)kFNmax * 4, 1024);       // row log weights
+  static constexpr size_t fU = fB + rnd((size_t)(kFNmax + kFNmax / 32) * 4, 16);
+  static constexpr size_t fAl = fU + (size_t)kFNmax * D * 4;
+  static constexpr size_t fDl = fAl + (size_t)kFNmax * 4;
+  static constexpr size_t fSh = fDl + (size_t)kFNmax * 4;
+  static constexpr size_t T = fSh + (size_t)kFNmax * 8;
+  static constexpr size_t cum = T + (size_t)kFNmax * kFTiles * 4;
+  static constexpr size_t fL = cum + (size_t)kFNmax * 8;
+  static constexpr size_t bytes = rnd(fL + (size_t)kFNmax * 4, 1024);
 };
 
 template <int D>
@@ -202,10 +206,8 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
     for (int k = 0, s = blockIdx.x; s < a.mc && !stop; ++k, s += gridDim.x) {
       unsigned char* st = fsm + (size_t)(k & 1) * L::bytes;
       float* Tq = reinterpret_cast<float*>(st + L::T);
-      float* rp = reinterpret_cast<float*>(st + L::rp);
       for (int rt = 0; rt < RT && !stop; ++rt) {
         const int row = rt * kMmaM + 32 * g + lane;
-        float racc = 0.f;
         for (int cb = 0; cb < RT; ++cb, ++blk) {
           const int acc = blk & (kFAcc - 1);
           const bool ok = __all_sync(0xffffffffu, mbar_wait_or_abort(smem_u32(&acc_full[acc]),
@@ -233,7 +235,6 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
             t0 = exp_sum32<true>(acc0, N - col0);
             t1 = exp_sum32<true>(acc1, N - col0 - 32);
           }
-          racc = __fadd_rn(racc, __fadd_rn(t0, t1));
           if (row < N) {
             if (col0 + 32 < N)
               *reinterpret_cast<float2*>(Tq + (size_t)row * nTp + col0 / 32) = make_float2(t0, t1);
@@ -241,7 +242,6 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
               Tq[(size_t)row * nTp + col0 / 32] = t0;
           }
         }
-        if (!stop && row < N) rp[h * kFNmax + row] = racc;
       }
       if (stop) break;
       __syncwarp();
@@ -435,7 +435,6 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
       float* fDl = reinterpret_cast<float*>(st + L::fDl);
       const double* fSh = reinterpret_cast<const double*>(st + L::fSh);
       float* Tq = reinterpret_cast<float*>(st + L::T);
-      const float* rp = reinterpret_cast<const float*>(st + L::rp);
       unsigned long long* cum = reinterpret_cast<unsigned long long*>(st + L::cum);
       float* fL = reinterpret_cast<float*>(st + L::fL);
       int* under = reinterpret_cast<int*>(cum);  // rows that underflowed (before cum is built)
@@ -445,9 +444,9 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
         nonfinite_s = 0;
       }
       bar_sync(kBarDraw, kFDrawThreads);
-      // row totals: the two epilogue halves' running sums
+      // row totals: the tile weights in ascending order (the split path's definition)
       for (int i = dt; i < N; i += kFDrawThreads) {
-        float t = __fadd_rn(rp[i], rp[kFNmax + i]);
+        float t = row_total(Tq + (size_t)i * nTp, nT, nTp);
         if (isnan(t)) {
           nonfinite_s = 1;
           t = 0.f;

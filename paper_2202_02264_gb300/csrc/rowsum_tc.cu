@@ -15,8 +15,7 @@
 //     refills a slot or a tile as soon as the MMAs that read it have completed;
 //   - eight epilogue warps (two per TMEM lane quarter, splitting the block's columns) read the
 //     accumulator with tcgen05.ld, take 2^x on MUFU and keep the per-tile sums, while the
-//     tensor core already computes the next block; when one chunk covers the whole row they
-//     also keep their half's running row total, which the row-CDF kernel adds up.
+//     tensor core already computes the next block.
 // Every wait is bounded; on a timeout the CTA records DSMC_ERR_TIMEOUT, waits (bounded) for
 // its own outstanding MMA and for every bulk copy it issued but did not consume, frees its
 // TMEM and returns.
@@ -233,7 +232,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
       const int s = cur.s;
       const int row = cur.rt * kTcRows + 32 * g + lane;
       float* Trow = a.ws.T + ((size_t)s * N + (row < N ? row : 0)) * a.nTp;
-      float racc = 0.f;  // this half's tile weights of the row, blocks in order
       bool stop = false;
       for (int b = 0; b < cur.nblk; ++b, ++q) {
         const int buf = q & 1;
@@ -266,7 +264,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
           t0 = exp_sum32<true>(acc0, cur.j1 - col0);
           t1 = exp_sum32<true>(acc1, cur.j1 - col0 - 32);
         }
-        racc = __fadd_rn(racc, __fadd_rn(t0, t1));
         if (row < N) {
           if (B == 32) {  // tiles col0 / 32 (even: chunks start at multiples of 128) and + 1
             if (col0 + 32 < cur.j1)
@@ -279,9 +276,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) rowsum_tc_kernel(MergeArgs a, i
         }
       }
       if (stop) break;
-      // one column chunk: the item covers the whole row, so its two halves' sums are the
-      // row total's two parts (the row-CDF kernel adds them instead of re-reading T)
-      if (a.CH == 1 && row < N) a.ws.rowpart[((size_t)s * 2 + h) * N + row] = racc;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -83,7 +83,8 @@ EXPORTS = ["dsmc_status_string", "dsmc_last_error", "dsmc_state_sizes", "dsmc_wo
            "dsmc_batch_workspace_size", "dsmc_batch_prepare", "dsmc_batch_run", "dsmc_smooth_batch",
            "dsmc_seq_maps_bytes", "dsmc_serve_workspace_size", "dsmc_serve_tick",
            "dsmc_profile_breakdown_enable", "dsmc_profile_breakdown_read", "dsmc_profile_unit_rates",
-           "dsmc_debug_lazy_weights", "dsmc_lazy_attempts", "dsmc_debug_row_shift", "dsmc_debug_keep_weights"]
+           "dsmc_debug_lazy_weights", "dsmc_lazy_attempts", "dsmc_debug_row_shift", "dsmc_debug_keep_weights",
+           "dsmc_gaussian_proposals_workspace_size", "dsmc_gaussian_proposals"]
 
 
 def library_path() -> str:
@@ -128,6 +129,8 @@ def load(build_if_needed: bool = False) -> C.CDLL:
         lib.dsmc_debug_philox.argtypes = [vp, C.c_int64, C.c_uint64, vp, vp]
         lib.dsmc_debug_stall_tensor_cores.argtypes = [C.c_int]
         lib.dsmc_debug_keep_weights.argtypes = [C.c_int]
+        lib.dsmc_gaussian_proposals_workspace_size.argtypes = [modp, C.c_int, C.POINTER(C.c_size_t)]
+        lib.dsmc_gaussian_proposals.argtypes = [modp, C.c_int, vp, C.c_int, vp, vp, vp, vp, sz, vp]
         lib.dsmc_debug_merge_weights.argtypes = [cfgp, modp, C.c_int, C.c_int, vp, vp, vp, vp, vp,
                                                  vp, C.POINTER(C.c_int), vp, sz, vp]
         lib.dsmc_seq_maps_bytes.restype = C.c_size_t
@@ -269,6 +272,27 @@ def dsmc_smooth_noalloc(cfg, model, prop, y, state, traj, mean, m2, logL, stream
                                       C.byref(state), _ptr(traj), _ptr(mean), _ptr(m2), _ptr(logL),
                                       C.byref(st), _stream(stream)), "dsmc_smooth_noalloc")
     return int(st.value)
+
+
+def dsmc_gaussian_proposals_workspace_size(model: HostModel, K: int) -> int:
+    out = C.c_size_t(0)
+    _check(load().dsmc_gaussian_proposals_workspace_size(C.byref(model.struct), int(K), C.byref(out)),
+           "dsmc_gaussian_proposals_workspace_size")
+    return int(out.value)
+
+
+def dsmc_gaussian_proposals(model: HostModel, y, iterations=1, init_mean=None, ws=None, stream=None):
+    """Algorithm 4's Gaussian marginals (means, standard deviations [K][dx] FP32 device tensors)
+    of the linearised smoother, for DSMC_PROP_GAUSS proposals."""
+    K, d = y.shape
+    if ws is None:
+        ws = torch.empty((dsmc_gaussian_proposals_workspace_size(model, K),), dtype=torch.uint8, device=y.device)
+    mean = torch.empty((K, d), dtype=torch.float32, device=y.device)
+    std = torch.empty((K, d), dtype=torch.float32, device=y.device)
+    _check(load().dsmc_gaussian_proposals(C.byref(model.struct), int(K), _ptr(y), int(iterations), _ptr(init_mean),
+                                          _ptr(mean), _ptr(std), _ptr(ws), ws.numel(), _stream(stream)),
+           "dsmc_gaussian_proposals")
+    return mean, std, ws
 
 
 def dsmc_stream_status(ws, stream=None) -> int:
