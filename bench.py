@@ -36,9 +36,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "dSMC N·T/s per GB300 (batched mixed vs plain) at fixed error; p50/p99 latency"
 UNIT = "N·T/s"
-MUFU_EX2_PER_CLK_SM = 32       # measured on GB300 (ex2 probe), twice B200's 16
+MUFU_EX2_PER_CLK_SM = 32       # measured on GB300 (dsmc_profile_unit_rates), twice B200's 16
 FMA_PER_CLK_SM = 128
-SMS = 152
+
+
+def _sms() -> int:
+    """SMs of the current device (queried; 152 on a GB300)."""
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 # DRAM bytes (read + write) per launch of the cross-term / tile-sum kernel, mean over the
 # ten levels of one lgssm_d8 K = N = 1024 smoothing, from one ncu capture of the kernel
@@ -52,6 +57,7 @@ COMBINED_EXP_FACTOR = 1.28
 # ncu DRAM bytes per combination of the dominant kernel in the batched step, from one
 # full-size launch (a 1-pass capture; see profiles/).
 TRAFFIC_PER_COMBINATION = {("batched_lgssm_d4", "bf16"): {"bytes": 66620, "kernel": "rowsum_tc_kernel<BF16, 1 K plane>"}}
+# (the fused tensor-core level kernel, key (workload, compute, "fused"): none captured yet)
 
 # ncu DRAM bytes per launch of the single-sequence workloads' dominant kernel (none current:
 # the kernels changed since the last capture).
@@ -330,7 +336,7 @@ def run_ours(args):
 
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    ex2_peak = MUFU_EX2_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9       # G exp / s
+    ex2_peak = MUFU_EX2_PER_CLK_SM * _sms() * sm_max * 1e6 / 1e9       # G exp / s
     achieved = rs_pairs / (rs_ms / 1e3) / 1e9 if rs_ms > 0 else None   # G exp / s
     d = wl.model.d
     lazy = resampler != dsmc.MULTINOMIAL   # no N x N pass: prologue + per-slot proposals
@@ -341,12 +347,12 @@ def run_ours(args):
                            else "rowsum_tc_kernel (tcgen05 cross term, fused exp / tile sums)"),
                 "achieved": achieved, "peak": ex2_peak, "unit": "Gexp/s",
                 "frac": achieved / ex2_peak if achieved else None,
-                "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
+                "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {_sms()} SMs x {sm_max:.0f} MHz "
                                f"({src} max clock)",
                 "combined_peak": ex2_peak * COMBINED_EXP_FACTOR,
                 "frac_combined": achieved / (ex2_peak * COMBINED_EXP_FACTOR) if achieved else None,
                 # the CUDA-core variant evaluates the d-term with FMAs: that pipe binds first
-                "fma_bound_frac": (achieved / (FMA_PER_CLK_SM / (d + 2) * SMS * sm_max * 1e-3)
+                "fma_bound_frac": (achieved / (FMA_PER_CLK_SM / (d + 2) * _sms() * sm_max * 1e-3)
                                    if achieved and args.compute == "fp32" else None),
                 "avg_launch_ms": rs_ms / max(rs_n, 1), "launches": rs_n,
                 "traffic": (TRAFFIC_PER_LAUNCH.get((args.workload, args.compute)) or {}).get("bytes"),
@@ -434,20 +440,41 @@ def run_batched(args):
     torch.cuda.synchronize()
     if b.status() != 0:
         raise RuntimeError(f"device status {b.status()} after warm-up")
+    # the whole batched step (every launch of every level) captured once as a CUDA graph, with
+    # the CUDA events of the dominant kernel's launches captured into it; each timed step
+    # uploads that step's descriptor tables (new counter bases), then replays the graph
+    graph = None
+    if not args.no_graph:
+        prep(args.warmup)
+        dsmc.dsmc_profile_enable(True)
+        cap_stream = torch.cuda.Stream()
+        cap_stream.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(cap_stream):
+            with torch.cuda.graph(graph, stream=cap_stream):
+                b.run()
+        torch.cuda.current_stream().wait_stream(cap_stream)
+        graph.replay()
+        torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device())
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    dsmc.dsmc_profile_enable(True)
+    if graph is None:
+        dsmc.dsmc_profile_enable(True)
     for i in range(args.steps):
         prep(args.warmup + i)                 # descriptor upload (host tables), outside the events
         flush.zero_()                         # L2 flushed between timed steps, outside the events
         ev[i][0].record(stream)
-        b.run()
+        if graph is not None:
+            graph.replay()
+        else:
+            b.run()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    # with a graph the captured events hold the last replay's launches (one step's worth)
     rs_ms, rs_n, rs_pairs, launches = dsmc.dsmc_profile_read()
     dsmc.dsmc_profile_enable(False)
     if world > 1:
@@ -461,26 +488,27 @@ def run_batched(args):
     value = world * args.steps * units / t_total
     mixed_means = [m.cpu().numpy().copy() for m in b.mean[:32]]
 
-    # end to end through the public API: pinned host observations in, means and logL out
+    # end to end through the public API, wall clock: pinned host observations copied in, the
+    # whole dsmc_smooth_batch call (its host-side descriptor tables and their upload included),
+    # means and log L copied back to pinned host memory
     y_host = [torch.as_tensor(y, dtype=torch.float32).pin_memory() for y in bw.ys]
     m_host = [torch.empty((K, d), dtype=torch.float64).pin_memory() for K in Ks]
     l_host = torch.empty((len(Ks),), dtype=torch.float64).pin_memory()
     e2e_steps = max(2, min(args.steps, 5))
     t_e2e = 0.0
     for i in range(e2e_steps):
-        prep(10_000 + i)
+        b.counter_base = [10_000 + i] * len(Ks)
         flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
         for yd, yh in zip(ys, y_host):
             yd.copy_(yh, non_blocking=True)
-        b.run()
+        b.smooth()
         for mh, md in zip(m_host, b.mean):
             mh.copy_(md, non_blocking=True)
         l_host.copy_(b.logL_out, non_blocking=True)
-        e1.record(stream)
         torch.cuda.synchronize()
-        t_e2e += e0.elapsed_time(e1) / 1e3
+        t_e2e += time.perf_counter() - w0
     e2e = {"value": world * units * e2e_steps / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": sum(y.numel() * 4 for y in y_host),
            "d2h_bytes_per_step": sum(m.numel() * 8 for m in m_host) + l_host.numel() * 8}
@@ -497,7 +525,8 @@ def run_batched(args):
     plain_value, t_plain, accuracy = None, None, None
     if not args.no_compare:
         plain_value, t_plain, accuracy = _plain_and_accuracy(model, Ks, N, seeds, ys, bw, mixed_means, units, stream)
-    roofline = _batch_roofline(args, rs_pairs, rs_ms, rs_n, N)
+    roofline = _batch_roofline(args, rs_pairs, rs_ms, rs_n, N, tuned["tc_fused"], breakdown,
+                               1 if graph is not None else args.steps)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -508,6 +537,9 @@ def run_batched(args):
                        "compute": f"{args.compute} cross term (fp32 accumulate / exp), batched: one launch "
                                   "per level for all sequences",
                        "l2": "flushed between timed steps (512 MiB write)",
+                       "timed_step": ("one replay of the captured CUDA graph of the whole batched step "
+                                      "(descriptor upload of the step's counter bases outside the events)"
+                                      if graph is not None else "direct launches of the whole batched step"),
                        "parallelism": f"replicas x{world}",
                        "autotuned": {"fused_max_merges": tuned["fused_max_merges"],
                                      "max_merges_per_launch": tuned["max_merges_per_launch"],
@@ -566,21 +598,32 @@ def _plain_and_accuracy(model, Ks, N, seeds, ys, bw, mixed_means, units, stream)
     return plain_value, t_plain, accuracy
 
 
-def _batch_roofline(args, rs_pairs, rs_ms, rs_n, N):
-    """Roofline of the dominant kernel (the fused exp / tile-sum pass) of the batched step:
-    algorithmic work = pair exponentials per launch, over its mean event-timed duration."""
+def _batch_roofline(args, rs_pairs, rs_ms, rs_n, N, tc_fused=0, breakdown=None, steps_profiled=1):
+    """Roofline of the dominant kernel of the batched step (the fused exp / tile-sum pass, or
+    the fused tensor-core level kernel that also builds the operands and draws the pairs):
+    algorithmic work = pair exponentials per launch, over its mean event-timed duration.
+    frac_merge: the same work over the device time of every merge kernel of one step."""
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    ex2_peak = MUFU_EX2_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9
+    ex2_peak = MUFU_EX2_PER_CLK_SM * _sms() * sm_max * 1e6 / 1e9
     achieved = rs_pairs / (rs_ms / 1e3) / 1e9 if rs_ms > 0 else None
-    kname = {"fp32": "rowsum_kernel (fused exp / tile sums)",
-             "tf32": "rowsum_tc_kernel (tcgen05 cross term, fused exp / tile sums)",
-             "bf16": "rowsum_tc_kernel (tcgen05 cross term, fused exp / tile sums)"}[args.compute]
-    per_comb = TRAFFIC_PER_COMBINATION.get((args.workload, args.compute))
+    if tc_fused > 0 and args.compute != "fp32":
+        kname = ("merge_tc_fused_kernel (operand rows, tcgen05 cross term, exp / tile sums, row CDF "
+                 "and pair draws of each combination on one SM)")
+        per_comb = TRAFFIC_PER_COMBINATION.get((args.workload, args.compute, "fused"))
+    else:
+        kname = {"fp32": "rowsum_kernel (fused exp / tile sums)",
+                 "tf32": "rowsum_tc_kernel (tcgen05 cross term, fused exp / tile sums)",
+                 "bf16": "rowsum_tc_kernel (tcgen05 cross term, fused exp / tile sums)"}[args.compute]
+        per_comb = TRAFFIC_PER_COMBINATION.get((args.workload, args.compute))
     combs_per_launch = rs_pairs / (N * N) / max(rs_n, 1)
+    merge_ms = None
+    if breakdown:
+        merge_ms = sum(breakdown.get(k, {}).get("ms", 0.0)
+                       for k in ("prologue", "tile_sums", "draws", "fused_levels", "fused_tc_levels"))
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": ex2_peak, "unit": "Gexp/s",
                 "frac": achieved / ex2_peak if achieved else None,
-                "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
+                "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {_sms()} SMs x {sm_max:.0f} MHz "
                                f"({src} max clock)",
                 "combined_peak": ex2_peak * COMBINED_EXP_FACTOR,
                 "frac_combined": achieved / (ex2_peak * COMBINED_EXP_FACTOR) if achieved else None,
@@ -588,7 +631,10 @@ def _batch_roofline(args, rs_pairs, rs_ms, rs_n, N):
                 "combinations_per_launch": combs_per_launch,
                 "traffic": per_comb["bytes"] * combs_per_launch if per_comb else None,
                 "traffic_unit": "B per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum per "
-                                "combination, times combinations per launch)"}
+                                "combination, times combinations per launch)",
+                "merge_ms_per_step": merge_ms,
+                "frac_merge": ((rs_pairs / steps_profiled) / (merge_ms / 1e3) / 1e9 / ex2_peak
+                               if merge_ms else None)}
     return roofline
 
 
@@ -640,7 +686,7 @@ def run_serving(args):
 
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    ex2_peak = MUFU_EX2_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9
+    ex2_peak = MUFU_EX2_PER_CLK_SM * _sms() * sm_max * 1e6 / 1e9
     achieved = rs_pairs / (rs_ms / 1e3) / 1e9 if rs_ms > 0 else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
             "ms_per_step": 1e3 * makespan, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -662,7 +708,7 @@ def run_serving(args):
             "roofline": {"bound": "alu", "kernel": "rowsum_tc_kernel / rowsum_kernel (fused exp / tile sums)",
                          "achieved": achieved, "peak": ex2_peak, "unit": "Gexp/s",
                          "frac": achieved / ex2_peak if achieved else None,
-                         "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
+                         "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {_sms()} SMs x {sm_max:.0f} MHz "
                                         f"({src} max clock)",
                          "launches": rs_n, "traffic": None},
             "e2e": {"value": value, "unit": UNIT,
@@ -736,7 +782,7 @@ def run_pg(args):
     dsmc.dsmc_profile_breakdown_enable(False)
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    ex2_peak = MUFU_EX2_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9
+    ex2_peak = MUFU_EX2_PER_CLK_SM * _sms() * sm_max * 1e6 / 1e9
     achieved = rs_pairs / (rs_ms / 1e3) / 1e9 if rs_ms > 0 else None
     line = {"metric": METRIC, "value": sweeps * N * K / t, "unit": UNIT, "n_gpus": 1, "steps": sweeps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / sweeps, "higher_is_better": True, "scaling": "weak",
@@ -751,7 +797,7 @@ def run_pg(args):
                             "first_t": float(rate[0]), "last_t": float(rate[-1])},
             "roofline": {"bound": "alu", "kernel": "rowsum kernels (fused exp / tile sums)", "achieved": achieved,
                          "peak": ex2_peak, "unit": "Gexp/s", "frac": achieved / ex2_peak if achieved else None,
-                         "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz "
+                         "peak_source": f"MUFU ex2 {MUFU_EX2_PER_CLK_SM}/clk/SM x {_sms()} SMs x {sm_max:.0f} MHz "
                                         f"({src} max clock)", "launches": rs_n, "traffic": None},
             "clocks": clk, "gpu_launches": launches, "breakdown_ms_per_sweep": breakdown}
     if rank == 0:
@@ -770,6 +816,7 @@ def main():
                     help="cross-term precision (default: bf16 for the batched workload, tf32 otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: default launch schedule")
+    ap.add_argument("--no-graph", action="store_true", help="batched workload: time direct launches, not a graph")
     ap.add_argument("--schedule", default=None,
                     help="batched workload: fixed 'fused_max_merges,max_merges_per_launch' instead of the autotuner")
     ap.add_argument("--fused-max-merges", type=int, default=None,

@@ -340,17 +340,32 @@ dsmc_status_t fill_params(const dsmc_model_t* m, const dsmc_proposal_t* pr, Para
   mp->log_prop_scale = (float)std::log(pr->scale > 0 ? pr->scale : 1.0);
   mp->prop_mean = pr->mean;
   mp->prop_std = pr->std;
-  if (m->kind == DSMC_MODEL_SV) {
+  if (m->kind != DSMC_MODEL_LGSSM) {  // the one-dimensional kinds
     const double s2 = m->sigma * m->sigma;
-    const double v0 = s2 / (1.0 - m->phi * m->phi);
-    mp->A[0] = (float)m->phi;
-    mp->c[0] = (float)(m->mu * (1.0 - m->phi));
+    double A = 1.0, c = 0.0, m0 = 0.0, v0 = 1.0;
+    if (m->kind == DSMC_MODEL_SV || m->kind == DSMC_MODEL_COX) {
+      A = m->kind == DSMC_MODEL_COX ? m->phi * m->lam : m->phi;
+      c = m->mu * (1.0 - m->phi);
+      m0 = m->mu;
+      v0 = s2 / (1.0 - m->phi * m->phi);
+    }
+    mp->A[0] = (float)A;
+    mp->c[0] = (float)c;
     mp->Qi[0] = (float)(1.0 / s2);
     mp->P0i[0] = (float)(1.0 / v0);
-    mp->m0[0] = (float)m->mu;
+    mp->m0[0] = (float)m0;
     mp->log_f_max = (float)(-0.5 * (kLog2Pi + std::log(s2)));
-    mp->log_h_norm = (float)(-0.5 * kLog2Pi);
     mp->log_p0_norm = (float)(-0.5 * (kLog2Pi + std::log(v0)));
+    mp->log_h_norm = (float)(-0.5 * kLog2Pi);
+    mp->tau0 = (float)m->tau0;
+    mp->tau1 = (float)m->tau1;
+    mp->tau2 = (float)m->tau2;
+    mp->bound = (float)m->bound;
+    if (m->kind == DSMC_MODEL_THETA_LOGISTIC) {  // y_t = x_t + N(0, obs_sd^2)
+      const double r2 = m->obs_sd * m->obs_sd;
+      mp->Ri[0] = (float)(1.0 / r2);
+      mp->log_h_norm = (float)(-0.5 * (kLog2Pi + std::log(r2)));
+    }
     return DSMC_OK;
   }
   double Qi[kMaxDim * kMaxDim], Ri[kMaxDim * kMaxDim], P0i[kMaxDim * kMaxDim];
@@ -406,10 +421,21 @@ dsmc_status_t check_config(const dsmc_config_t* cfg, const dsmc_model_t* model) 
     return fail(DSMC_ERR_UNSUPPORTED, "the tensor-core cross term supports N <= 4096");
   if (cfg->counter_base >= (1u << 28)) return fail(DSMC_ERR_INVALID_ARG, "counter_base must be < 2^28");
   if (model->dx < 1 || model->dx > kMaxDim) return fail(DSMC_ERR_UNSUPPORTED, "dx must be in 1..32");
-  if (model->kind == DSMC_MODEL_SV) {
-    if (model->dx != 1) return fail(DSMC_ERR_INVALID_ARG, "the SV model has dx = 1");
+  if (model->kind == DSMC_MODEL_SV || model->kind == DSMC_MODEL_COX) {
+    if (model->dx != 1) return fail(DSMC_ERR_INVALID_ARG, "the SV and COX models have dx = 1");
     if (!(model->sigma > 0.0) || !(std::fabs(model->phi) < 1.0))
-      return fail(DSMC_ERR_INVALID_ARG, "SV needs sigma > 0 and |phi| < 1");
+      return fail(DSMC_ERR_INVALID_ARG, "SV and COX need sigma > 0 and |phi| < 1");
+    if (model->kind == DSMC_MODEL_COX && !std::isfinite(model->lam))
+      return fail(DSMC_ERR_INVALID_ARG, "COX needs a finite lam");
+  } else if (model->kind == DSMC_MODEL_THETA_LOGISTIC) {
+    if (model->dx != 1) return fail(DSMC_ERR_INVALID_ARG, "the theta-logistic model has dx = 1");
+    if (!(model->sigma > 0.0) || !(model->obs_sd > 0.0) || !std::isfinite(model->tau0) ||
+        !std::isfinite(model->tau1) || !std::isfinite(model->tau2))
+      return fail(DSMC_ERR_INVALID_ARG, "theta-logistic needs sigma, obs_sd > 0 and finite tau");
+  } else if (model->kind == DSMC_MODEL_CRW) {
+    if (model->dx != 1) return fail(DSMC_ERR_INVALID_ARG, "the constrained random walk has dx = 1");
+    if (!(model->sigma > 0.0) || !(model->bound > 0.0))
+      return fail(DSMC_ERR_INVALID_ARG, "the constrained random walk needs sigma, bound > 0");
   } else if (model->kind == DSMC_MODEL_LGSSM) {
     if (!model->A || !model->Q || !model->R || !model->m0 || !model->P0)
       return fail(DSMC_ERR_INVALID_ARG, "LGSSM needs A, Q, R, m0, P0");
@@ -427,12 +453,15 @@ dsmc_status_t check_prop(const dsmc_config_t* cfg, const dsmc_model_t* model,
     if (!(prop->scale > 0.0)) return fail(DSMC_ERR_INVALID_ARG, "proposal scale must be > 0");
   } else if (prop->kind == DSMC_PROP_GAUSS) {
     if (!prop->mean || !prop->std) return fail(DSMC_ERR_INVALID_ARG, "proposal mean/std arrays");
+  } else if (prop->kind == DSMC_PROP_UNIFORM) {
+    if (!(prop->scale > 0.0)) return fail(DSMC_ERR_INVALID_ARG, "uniform proposal needs scale > 0");
   } else {
     return fail(DSMC_ERR_INVALID_ARG, "unknown proposal kind");
   }
   if (prop->nu != DSMC_NU_EQ_Q && prop->nu != DSMC_NU_PROP_H)
     return fail(DSMC_ERR_INVALID_ARG, "unknown nu choice");
-  (void)model;
+  if (prop->nu == DSMC_NU_PROP_H && model->kind == DSMC_MODEL_COX)
+    return fail(DSMC_ERR_UNSUPPORTED, "the COX potential has no normalised nu (y_t = 0)");
   return DSMC_OK;
 }
 
@@ -1404,15 +1433,27 @@ dsmc_status_t dsmc_gaussian_proposals(const dsmc_model_t* model, int K, const fl
   pa.d = d;
   pa.kind = model->kind;
   pa.y = y;
-  if (model->kind == DSMC_MODEL_SV) {
+  if (model->kind != DSMC_MODEL_LGSSM) {
+    if (model->kind == DSMC_MODEL_CRW)
+      return fail(DSMC_ERR_UNSUPPORTED, "the constrained random walk has no Gaussian linearisation");
     const double s2 = model->sigma * model->sigma;
-    F[0] = model->phi;
     Q[0] = s2;
-    R[0] = 0.0;  // pseudo-observations carry their own variances
-    P0[0] = s2 / (1.0 - model->phi * model->phi);
-    cc[0] = model->mu * (1.0 - model->phi);
-    m0[0] = model->mu;
-    pa.mu = model->mu;
+    if (model->kind == DSMC_MODEL_THETA_LOGISTIC) {
+      F[0] = 1.0;  // replaced by the per-step linearisation
+      R[0] = model->obs_sd * model->obs_sd;
+      P0[0] = 1.0;
+      m0[0] = 0.0;
+      pa.tau0 = model->tau0;
+      pa.tau1 = model->tau1;
+      pa.tau2 = model->tau2;
+    } else {  // SV, COX: pseudo-observations carry their own variances
+      F[0] = model->kind == DSMC_MODEL_COX ? model->phi * model->lam : model->phi;
+      R[0] = 0.0;
+      P0[0] = s2 / (1.0 - model->phi * model->phi);
+      cc[0] = model->mu * (1.0 - model->phi);
+      m0[0] = model->mu;
+      pa.mu = model->mu;
+    }
   } else {
     double L[kMaxDim * kMaxDim];
     if (!cholesky(d, model->Q, L) || !cholesky(d, model->R, L) || !cholesky(d, model->P0, L))

@@ -64,11 +64,12 @@ __device__ __forceinline__ float ex2(float x) {
 }
 
 // Model parameters, pre-computed on the host in FP64 and rounded once to FP32.  D is the
-// padded state dimension (zero rows/columns beyond d).  The transition is
-// N(A x + c, Q) for both model kinds (the SV model has A = phi, c = mu (1 - phi)).
+// padded state dimension (zero rows/columns beyond d).  The transition is N(m(x), Q) with
+// m(x) = A x + c (LGSSM; SV and COX with A = phi (lam), c = mu (1 - phi); CRW with A = 1,
+// c = 0) or m(x) = x + tau0 - tau1 exp(tau2 x) (THETA_LOGISTIC).
 template <int D>
 struct ModelParams {
-  int kind;         // DSMC_MODEL_LGSSM or DSMC_MODEL_SV
+  int kind;         // DSMC_MODEL_*
   int d;            // true dimension
   int prop_kind;    // DSMC_PROP_OBS or DSMC_PROP_GAUSS
   int nu;           // DSMC_NU_EQ_Q or DSMC_NU_PROP_H
@@ -83,6 +84,8 @@ struct ModelParams {
   float log_p0_norm;// -1/2 log |2 pi P0|
   float prop_scale;
   float log_prop_scale;
+  float tau0, tau1, tau2;  // THETA_LOGISTIC: transition mean x + tau0 - tau1 exp(tau2 x)
+  float bound;             // CRW: constraint half-width
   const float* prop_mean;  // DEVICE [K][d] (DSMC_PROP_GAUSS)
   const float* prop_std;   // DEVICE [K][d]
 };
@@ -101,11 +104,36 @@ __device__ __forceinline__ float quad_form(const float* M, const float* x) {
   return s;
 }
 
-// log h_t(y_t | x): N(y; x, R) for the linear-Gaussian model, N(y; 0, exp(x)) for SV.
+// The transition mean m(x) of the model (see ModelParams).
+template <int D>
+__device__ __forceinline__ void transition_mean(const ModelParams<D>& mp, const float* x, float* m) {
+  if (mp.kind == DSMC_MODEL_THETA_LOGISTIC) {
+    m[0] = x[0] + mp.tau0 - mp.tau1 * expf(mp.tau2 * x[0]);
+#pragma unroll
+    for (int r = 1; r < D; ++r) m[r] = 0.f;
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    float acc = mp.c[r];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc = fmaf(mp.A[r * D + k], x[k], acc);
+    m[r] = acc;
+  }
+}
+
+// log h_t(y_t | x): N(y; x, R) for the linear-Gaussian and theta-logistic models,
+// N(y; 0, exp(x)) for SV, Poisson(y; exp(x)) for COX, the indicator of |x| <= bound for CRW.
 template <int D>
 __device__ __forceinline__ float log_h(const ModelParams<D>& mp, const float* yt, const float* x) {
   if (mp.kind == DSMC_MODEL_SV) {
     return mp.log_h_norm - 0.5f * x[0] - 0.5f * yt[0] * yt[0] * expf(-x[0]);
+  }
+  if (mp.kind == DSMC_MODEL_COX) {
+    return yt[0] * x[0] - expf(x[0]) - lgammaf(yt[0] + 1.f);
+  }
+  if (mp.kind == DSMC_MODEL_CRW) {
+    return fabsf(x[0]) <= mp.bound ? 0.f : -INFINITY;
   }
   float r[D];
 #pragma unroll
@@ -128,14 +156,28 @@ __device__ __forceinline__ float log_q(int d, const float* qm, const float* qinv
   return fmaf(-0.5f, s, qnorm);
 }
 
+// log q_t(x) of the uniform proposal on [-scale, scale]^d.
+template <int D>
+__device__ __forceinline__ float log_q_uniform(const ModelParams<D>& mp, const float* x) {
+  bool in = true;
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    if (k < mp.d) in &= fabsf(x[k]) <= mp.prop_scale;
+  return in ? -(float)mp.d * (kLn2 + mp.log_prop_scale) : -INFINITY;
+}
+
 // log nu_t(x) (Definition 1): q_t itself, or h_t(y_t | .) normalised over x
-// (N(x; y_t, R) for the linear-Gaussian model; h_t * |y_t| for SV).
+// (N(x; y_t, R) for the linear-Gaussian and theta-logistic models; h_t * |y_t| for SV; the
+// uniform law on [-bound, bound] for CRW).
 template <int D>
 __device__ __forceinline__ float log_nu(const ModelParams<D>& mp, const float* yt, const float* qm,
                                         const float* qinv, float qnorm, const float* x) {
-  if (mp.nu == DSMC_NU_EQ_Q) return log_q<D>(mp.d, qm, qinv, qnorm, x);
+  if (mp.nu == DSMC_NU_EQ_Q)
+    return mp.prop_kind == DSMC_PROP_UNIFORM ? log_q_uniform<D>(mp, x) : log_q<D>(mp.d, qm, qinv, qnorm, x);
   const float lh = log_h<D>(mp, yt, x);
-  return mp.kind == DSMC_MODEL_SV ? lh + logf(fabsf(yt[0])) : lh;
+  if (mp.kind == DSMC_MODEL_SV) return lh + logf(fabsf(yt[0]));
+  if (mp.kind == DSMC_MODEL_CRW) return lh - logf(2.f * mp.bound);
+  return lh;
 }
 
 // log P_0(x): N(m0, P0).
@@ -156,6 +198,9 @@ __device__ __forceinline__ void proposal_at(const ModelParams<D>& mp, const floa
     if (k < mp.d) {
       if (mp.prop_kind == DSMC_PROP_OBS) {
         qm[k] = y[(size_t)t * mp.d + k];
+        qs[k] = mp.prop_scale;
+      } else if (mp.prop_kind == DSMC_PROP_UNIFORM) {  // not a Gaussian: log_q_uniform applies
+        qm[k] = 0.f;
         qs[k] = mp.prop_scale;
       } else {
         qm[k] = prop_mean[(size_t)t * mp.d + k];

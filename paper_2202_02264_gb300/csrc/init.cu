@@ -1,7 +1,8 @@
 // init.cu -- Algorithm 2 (smoother initialisation), and its conditional form (Section 3.2).
 //
 // One CTA per time step t.  Each thread draws particles x_t^n ~ q_t from Philox normals
-// (Box-Muller), writes them, and computes the leaf log-weight
+// (Box-Muller; uniform proposals from the uniforms themselves), writes them, and computes
+// the leaf log-weight
 //   t = 0:  log h_0(y_0 | x) + log P_0(x) - log q_0(x)
 //   t >= 1: log nu_t(x) - log q_t(x)          (exactly 0 when nu_t = q_t)
 // The CTA then normalises the N weights of its t by a log-sum-exp and stores
@@ -53,9 +54,30 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
   float lmax = -INFINITY;
   bool bad = false;
   const bool uniform = (t > 0 && mp.nu == DSMC_NU_EQ_Q);
+  const bool unif = mp.prop_kind == DSMC_PROP_UNIFORM;
   for (int n = threadIdx.x; n < N; n += kInitThreads) {
     float x[D], z[D];
-    if (x_ref != nullptr && n == 0) {
+    if (unif) {  // q_t = U([-s, s]^d): x = s (2 u - 1) from the words of counter j = k / 4
+#pragma unroll
+      for (int k = 0; k < D; ++k) z[k] = 0.f;
+      if (x_ref != nullptr && n == 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) x[k] = k < d ? x_ref[(size_t)t * d + k] : 0.f;
+      } else {
+#pragma unroll
+        for (int j = 0; j < (D + 3) / 4; ++j) {
+          if (4 * j < d) {
+            const uint4 w = draw(seed, (uint32_t)n, (uint32_t)t, kPurposeInit, base, (uint32_t)j);
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+              const int k = 4 * j + p;
+              if (k < D) x[k] = k < d ? mp.prop_scale * fmaf(2.f, u23(ws[p]), -1.f) : 0.f;
+            }
+          }
+        }
+      }
+    } else if (x_ref != nullptr && n == 0) {
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         x[k] = k < d ? x_ref[(size_t)t * d + k] : 0.f;
@@ -95,10 +117,14 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
         if (k < d) xo[k] = x[k];
     }
     float lq = 0.f;
+    if (unif) {
+      lq = log_q_uniform<D>(mp, x);
+    } else {
 #pragma unroll
-    for (int k = 0; k < D; ++k)
-      if (k < d) lq = fmaf(-0.5f * z[k], z[k], lq);
-    lq -= logsd + (float)d * kHalfLog2Pi;
+      for (int k = 0; k < D; ++k)
+        if (k < d) lq = fmaf(-0.5f * z[k], z[k], lq);
+      lq -= logsd + (float)d * kHalfLog2Pi;
+    }
     float l;
     if (t == 0) {
       l = log_h<D>(mp, yt, x) + log_p0<D>(mp, x) - lq;

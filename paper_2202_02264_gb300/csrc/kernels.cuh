@@ -241,7 +241,9 @@ struct PitArgs {
   int K, d, kind;
   const float* y;
   const double *F, *Q, *R, *P0, *c, *m0;   // [d][d] x 4, [d] x 2
-  double mu;                                // SV: the stationary mean (first linearisation)
+  const double *Ft, *ct;                    // per-step transitions [K][d][d], [K][d], or null
+  double mu;                                // SV, COX: the stationary mean (first linearisation)
+  double tau0, tau1, tau2;                  // THETA_LOGISTIC
 };
 size_t pit_workspace_bytes(int K, int d);
 cudaError_t launch_pit(PitArgs pa, const double* model, int iterations, const float* init_mean, float* mean_out,

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
   if (staged) __syncthreads();
 
   // One-dimensional states, lazy sampler: the hull [m_lo, m_hi] of the transition means
-  // m_i = A x_i + c over the whole time-(c - 1) slice (a superset of the left block's end
+  // m_i = m(x_i) over the whole time-(c - 1) slice (a superset of the left block's end
   // states) bounds every pair: f(x_j | x_i) <= f_max exp(-dist_j^2 Q^-1 / 2) with dist_j
   // the distance from x_j to the hull, so log omega-bar = log f_max + max_i a_i +
   // max_j (b'_j - dist_j^2 Q^-1 / 2) is a valid bound of the combination's pair weights
@@ -145,7 +145,12 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
   if (hull) {
     float lo = INFINITY, hi = -INFINITY;
     for (int i = threadIdx.x; i < N; i += kProThreads) {
-      const float m = fmaf(mp.A[0], Xl[i], mp.c[0]);
+      float xi[D], mi[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) xi[k] = 0.f;
+      xi[0] = Xl[i];
+      transition_mean<D>(mp, xi, mi);
+      const float m = mi[0];
       lo = fminf(lo, m);
       hi = fmaxf(hi, m);
     }

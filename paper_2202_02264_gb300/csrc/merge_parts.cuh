@@ -5,8 +5,9 @@
 //
 // Notation (Section 3.1): left block [a, c-1], right block [c, b]; xL_i = left state at c-1,
 // xR_j = right state at c; a_i = logw_L[i]; b'_j = logw_R[j] + log h_c(y_c|xR_j) - log nu_c(xR_j).
-// For the Gaussian transition N(A x + c, Q) with centre mu (mean of the xR_j):
-//   w_i = A xL_i + c - mu,  v_j = xR_j - mu,  u_i = log2(e) Q^-1 w_i,
+// For the Gaussian transition N(m(x), Q) (m(x) = A x + c, or the theta-logistic mean) with
+// centre mu (mean of the xR_j):
+//   w_i = m(xL_i) - mu,  v_j = xR_j - mu,  u_i = log2(e) Q^-1 w_i,
 //   alpha_i = -log2(e) 1/2 w_i' Q^-1 w_i,  beta_j = log2(e) (b'_j - B* - 1/2 v_j' Q^-1 v_j),
 // and the base-2 exponent of pair (i, j) relative to the row bound
 // shift_i = a_i + log f_max + B* is alpha_i + beta_j + u_i . v_j <= 0.
@@ -160,13 +161,9 @@ __device__ __forceinline__ float row_terms(const ModelParams<D>& mp, int N, int 
   float x[D], w[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) x[k] = k < d ? xp[k] : 0.f;
+  transition_mean<D>(mp, x, w);
 #pragma unroll
-  for (int r = 0; r < D; ++r) {
-    float acc = mp.c[r];
-#pragma unroll
-    for (int k = 0; k < D; ++k) acc = fmaf(mp.A[r * D + k], x[k], acc);
-    w[r] = acc - mu[r];
-  }
+  for (int r = 0; r < D; ++r) w[r] = w[r] - mu[r];
   float q = 0.f;
 #pragma unroll
   for (int r = 0; r < D; ++r) {

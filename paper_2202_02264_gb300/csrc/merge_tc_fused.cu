@@ -5,21 +5,21 @@
 // log L are written).
 //
 // One CTA per SM walks the combinations s = blockIdx.x, blockIdx.x + gridDim.x, ... of the
-// launch.  Each combination's data lives in one of two shared-memory stages, so that three
-// combinations are in flight:
-//   - 4 loader warps build combination k + 1: the two particle slices and index maps staged
-//     with vector loads, the column pass (states, b'_j, mu, B*, v_j, beta_j) and the row
-//     pass (u_i, alpha_i, the row shift), as FP32 copies for the draws and as the BF16 / TF32
-//     operand rows [u, alpha_hi, alpha_lo, 1, 1] and [v, 1, 1, beta_hi, beta_lo] of the MMA in
-//     the canonical K-major layout;
-//   - 1 control thread issues, for combination k, one tcgen05.mma (M = N = 128) per (row
+// launch.  Each combination's data lives in one of two shared-memory stages:
+//   - 11 core warps alternate, for k = 0, 1, ...: the draws of combination k (the row
+//     totals, the row weights and their exact 2^40 fixed-point prefix sums, the increment of
+//     Eq. (Lab), every slot's pair in three exact inverse-CDF stages and the new block's
+//     index maps), then the operand build of combination k + 2 into the stage k released
+//     (the two particle slices and index maps staged with vector loads, the column pass --
+//     states, b'_j, mu, B*, v_j, beta_j -- and the row pass -- u_i, alpha_i, the row shift --
+//     as FP32 copies for the draws and as the BF16 / TF32 MMA rows [u, alpha_hi, alpha_lo, 1,
+//     1] and [v, 1, 1, beta_hi, beta_lo] in the canonical K-major layout);
+//   - 1 control thread issues, for combination k + 1, one tcgen05.mma (M = N = 128) per (row
 //     tile, column block) into one of four 128-column TMEM accumulators;
-//   - 8 epilogue warps read each accumulator (tcgen05.ld), take 2^x on MUFU and keep the
-//     tile sums in shared memory;
-//   - 7 draw warps, for combination k - 1: the row totals, the row weights and their exact
-//     2^40 fixed-point prefix sums, the increment of Eq. (Lab), then every slot's pair in
-//     three exact inverse-CDF stages (row, tile, column recomputed in FP32) and the new
-//     block's index maps.
+//   - 16 epilogue warps read each accumulator (tcgen05.ld; warp (g, h) lanes 32 g.. and
+//     columns 32 h..), take 2^x on MUFU and keep the tile sums in shared memory.
+// So the exponentials of one combination overlap the draws and the operand build of two
+// others, and the period of a combination is the larger of the two.
 // The arithmetic is the split path's, function for function (the column and row terms of
 // merge_parts.cuh, the operand packing and epilogue sums of tc_ops.cuh, draw_pair), and the
 // column mean is reduced in the same block-size-independent order, so the pairs, maps and
@@ -43,18 +43,15 @@ using namespace parts;
 using namespace tc;
 
 constexpr int kFNmax = 512;                 // largest N of the fused level
-constexpr int kFEpiWarps = 8;               // warps 0..7 (TMEM lane quarter = warp % 4)
-constexpr int kFLoadWarps = 4;              // warps 8..11
-constexpr int kFDrawWarps = 7;              // warps 12..18 (20 warps in all: 96 registers each)
-constexpr int kFCtrlWarp = kFEpiWarps + kFLoadWarps + kFDrawWarps;  // warp 19
+constexpr int kFEpiWarps = 16;              // warps 0..15: lane quarter warp % 4, 32 columns each
+constexpr int kFCoreWarps = 11;             // warps 16..26: operand build and draws (28 warps: 72 registers)
+constexpr int kFCtrlWarp = kFEpiWarps + kFCoreWarps;  // warp 27: TMEM and MMA issue
 constexpr int kFThreads = (kFCtrlWarp + 1) * 32;
-constexpr int kFLoadThreads = kFLoadWarps * 32;
-constexpr int kFDrawThreads = kFDrawWarps * 32;
-constexpr int kFLoad0 = kFEpiWarps * 32;
-constexpr int kFDraw0 = (kFEpiWarps + kFLoadWarps) * 32;
+constexpr int kFCoreThreads = kFCoreWarps * 32;
+constexpr int kFCore0 = kFEpiWarps * 32;
 constexpr int kFAcc = 4;                    // TMEM accumulators of 128 columns
 constexpr uint32_t kFTmemCols = kFAcc * kMmaN;
-constexpr int kBarLoad = 1, kBarDraw = 2;   // named barriers of the loader / draw warps
+constexpr int kBarCore = 1;                 // named barrier of the core warps
 constexpr int kFTileBytes = kMmaM * 32;     // one 128-row tile of one 32-byte K plane
 constexpr int kFTiles = kFNmax / 32;        // tiles of 32 columns per row (tile width 32)
 
@@ -110,10 +107,10 @@ __device__ __forceinline__ void stage_group(T* dst, const T* src, int n, int tid
   }
 }
 
-// Exact u64 inclusive scan of v[0..N) in shared memory by the draw warps (named barrier).
+// Exact u64 inclusive scan of v[0..N) in shared memory by the core warps (named barrier).
 __device__ __forceinline__ void group_scan_u64(unsigned long long* v, int N, unsigned long long* warp_tot,
                                                int tid) {
-  constexpr int NT = kFDrawThreads;
+  constexpr int NT = kFCoreThreads;
   const int per = (N + NT - 1) / NT;
   const int lo = min(tid * per, N), hi = min(lo + per, N);
   unsigned long long run = 0;
@@ -126,7 +123,7 @@ __device__ __forceinline__ void group_scan_u64(unsigned long long* v, int N, uns
     if (lane >= o) incl += t;
   }
   if (lane == 31) warp_tot[w] = incl;
-  bar_sync(kBarDraw, NT);
+  bar_sync(kBarCore, NT);
   if (tid == 0) {
     unsigned long long acc = 0;
     for (int k = 0; k < NT / 32; ++k) {
@@ -135,13 +132,293 @@ __device__ __forceinline__ void group_scan_u64(unsigned long long* v, int N, uns
       acc += t;
     }
   }
-  bar_sync(kBarDraw, NT);
+  bar_sync(kBarCore, NT);
   unsigned long long pre = warp_tot[w] + incl - run;
   for (int i = lo; i < hi; ++i) {
     pre += v[i];
     v[i] = pre;
   }
-  bar_sync(kBarDraw, NT);
+  bar_sync(kBarCore, NT);
+}
+
+// Shared scratch of the core warps.
+struct CoreScratch {
+  float gsum[kMaxColumnGroups * 4];
+  float red[kFCoreWarps];
+  float mu[4];
+  float bstar;
+  unsigned long long warp_tot[kFCoreWarps];
+  int n_under, nonfinite, ok;
+};
+
+// Operand build of combination s into stage st (the core warps): the two particle slices and
+// index maps staged with vector loads, the column pass (states, b'_j, mu, B*, v_j, beta_j),
+// the row pass (u_i, alpha_i, the row shift), FP32 copies for the draws and the MMA rows.
+template <int D, int KIND>
+__device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<D>& mp, unsigned char* st, int s,
+                                          int ct, int cw, int lane, int RT, CoreScratch& sc) {
+  using L = Stage<D>;
+  const int N = a.N, d = a.d;
+  unsigned char* opU = st + L::opU;
+  unsigned char* opV = st + L::opV;
+  float* fV = reinterpret_cast<float*>(st + L::fV);
+  float* fB = reinterpret_cast<float*>(st + L::fB);
+  float* fU = reinterpret_cast<float*>(st + L::fU);
+  float* fAl = reinterpret_cast<float*>(st + L::fAl);
+  float* fDl = reinterpret_cast<float*>(st + L::fDl);
+  double* fSh = reinterpret_cast<double*>(st + L::fSh);
+  const Comb cb = comb_of(a, s);
+  const int at = cb.at, c = cb.c, b = cb.b, K = cb.K;
+  const bool left_leaf = (cb.level == 0);
+  const int sR = b - c + 1;
+  const bool right_leaf = (sR == 1);
+  const int bufL = cb.level & 1, bufR = ceil_log2(sR) & 1;
+  // the inputs staged in this stage's tile-sum area (written by the epilogue only after
+  // these operands have been consumed)
+  float* sXc = reinterpret_cast<float*>(st + L::T);
+  float* sXl = sXc + rnd((size_t)N * d, 4);
+  float* sR0 = sXl + rnd((size_t)N * d, 4);
+  float* sL0 = sR0 + rnd((size_t)N, 4);
+  stage_group(sXc, cb.X + (size_t)c * N * d, N * d, ct, kFCoreThreads);
+  stage_group(sXl, cb.X + (size_t)(c - 1) * N * d, N * d, ct, kFCoreThreads);
+  if (right_leaf)
+    stage_group(sR0, cb.logw + (size_t)c * N, N, ct, kFCoreThreads);
+  else
+    stage_group(reinterpret_cast<int32_t*>(sR0), cb.first + ((size_t)bufR * K + c) * N, N, ct, kFCoreThreads);
+  if (left_leaf)
+    stage_group(sL0, cb.logw + (size_t)(c - 1) * N, N, ct, kFCoreThreads);
+  else
+    stage_group(reinterpret_cast<int32_t*>(sL0), cb.last + ((size_t)bufL * K + at) * N, N, ct, kFCoreThreads);
+  const int32_t* firstR = right_leaf ? nullptr : reinterpret_cast<const int32_t*>(sR0);
+  const float* lwc = right_leaf ? sR0 : nullptr;
+  const int32_t* lastL = left_leaf ? nullptr : reinterpret_cast<const int32_t*>(sL0);
+  const float* lwl = left_leaf ? sL0 : nullptr;
+  float yc[D], qm[D], qs[D], qinv[D];
+#pragma unroll
+  for (int kk = 0; kk < D; ++kk) yc[kk] = kk < d ? cb.y[(size_t)c * d + kk] : 0.f;
+  proposal_at<D>(mp, cb.y, cb.prop_mean, cb.prop_std, c, qm, qs);
+  const float qnorm = proposal_consts<D>(d, qs, qinv);
+  bar_sync(kBarCore, kFCoreThreads);
+
+  // column pass: b'_j, states, the column mean mu (groups of 32 Q columns, each summed by
+  // one warp lane-sequentially then by a butterfly, group sums in group order: the same
+  // order as every other column pass) and B* = max_j b'_j
+  bool bad = false, corrupt = false;
+  float mu[D], bstar;
+  {
+    const int Qg = (N + 1023) / 1024, Wd = 32 * Qg;
+    const int G = (N + Wd - 1) / Wd;
+    float bmax = -INFINITY;
+    for (int gg = cw; gg < G; gg += kFCoreWarps) {
+      float accs[D];
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) accs[kk] = 0.f;
+      for (int cc = 0; cc < Qg; ++cc) {
+        const int j = Wd * gg + 32 * cc + lane;
+        if (j < N) {
+          float x[D];
+          const float bp = column_bprime<D>(mp, N, d, a.logN, yc, qm, qinv, qnorm, sXc, firstR, lwc, j, x, corrupt);
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) fV[vidx<D, true>(j) + kk] = x[kk];
+          fB[bidx<true>(j)] = bp;
+          bad |= isnan(bp);
+          bmax = fmaxf(bmax, bp);
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) accs[kk] += x[kk];
+        }
+      }
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) {
+        const float t = warp_sum(accs[kk]);
+        if (lane == 0) sc.gsum[gg * D + kk] = t;
+      }
+    }
+    bmax = warp_max(bmax);
+    if (lane == 0) sc.red[cw] = bmax;
+    bar_sync(kBarCore, kFCoreThreads);
+    if (ct < D) {
+      float t = 0.f;
+      for (int gg = 0; gg < G; ++gg) t += sc.gsum[gg * D + ct];
+      sc.mu[ct] = t / (float)N;
+    }
+    if (ct == 0) {
+      float t = sc.red[0];
+      for (int w = 1; w < kFCoreWarps; ++w) t = fmaxf(t, sc.red[w]);
+      sc.bstar = t;
+    }
+    bar_sync(kBarCore, kFCoreThreads);
+#pragma unroll
+    for (int kk = 0; kk < D; ++kk) mu[kk] = sc.mu[kk];
+    bstar = sc.bstar;
+  }
+  // columns: v_j = x_j - mu, beta_j, the MMA column rows [v, 1, 1, beta_hi, beta_lo]
+  for (int j = ct; j < N; j += kFCoreThreads) {
+    float v[D];
+#pragma unroll
+    for (int kk = 0; kk < D; ++kk) v[kk] = fV[vidx<D, true>(j) + kk];
+    const float bj = column_beta<D>(mp, v, mu, fB[bidx<true>(j)], bstar);
+#pragma unroll
+    for (int kk = 0; kk < D; ++kk) fV[vidx<D, true>(j) + kk] = v[kk];
+    fB[bidx<true>(j)] = bj;
+    float ext[4];
+    ext[0] = 1.f;
+    ext[1] = 1.f;
+    split_mma(bj, KIND, &ext[2], &ext[3]);
+    store_mma_row_t<D, KIND>(opV, kFNmax, j, v, ext);
+    if (a.inspect) {
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) a.ws.V[((size_t)s * N + j) * D + kk] = v[kk];
+      a.ws.beta[(size_t)s * N + j] = bj;
+    }
+  }
+  {  // rows and columns past N within the last tile are zero
+    const float zero[D] = {};
+    const float zext[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int j = N + ct; j < RT * kMmaM; j += kFCoreThreads) {
+      store_mma_row_t<D, KIND>(opV, kFNmax, j, zero, zext);
+      store_mma_row_t<D, KIND>(opU, kFNmax, j, zero, zext);
+    }
+  }
+  bar_sync(kBarCore, kFCoreThreads);  // the rows read a sample of the columns
+  // rows: u_i, alpha_i (less the row shift decta_i, which moves into shift_i), and the MMA
+  // row [u, alpha_hi, alpha_lo, 1, 1]
+  for (int i = ct; i < N; i += kFCoreThreads) {
+    float ul[D], ai;
+    const float al0 = row_terms<D>(mp, N, d, a.logN, sXl, lastL, lwl, i, mu, ul, ai, corrupt);
+    const float dl = row_shift<D, true>(ul, al0, fV, fB, N);
+    const float al = __fsub_rn(al0, dl);
+    bad |= isnan(ai);
+#pragma unroll
+    for (int kk = 0; kk < D; ++kk) fU[(size_t)i * D + kk] = ul[kk];
+    fAl[i] = al;
+    fDl[i] = 0.f;
+    const double sh = (double)ai + (double)mp.log_f_max + (double)bstar + (double)dl * kLn2d;
+    fSh[i] = sh;
+    float ext[4];
+    split_mma(al, KIND, &ext[0], &ext[1]);
+    ext[2] = 1.f;
+    ext[3] = 1.f;
+    store_mma_row_t<D, KIND>(opU, kFNmax, i, ul, ext);
+    if (a.inspect) {
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) a.ws.U[((size_t)s * N + i) * D + kk] = ul[kk];
+      a.ws.alpha[(size_t)s * N + i] = al;
+      a.ws.shift[(size_t)s * N + i] = sh;
+    }
+  }
+  if (corrupt) record_status(a.ws.status, DSMC_ERR_INVALID_ARG);
+  if (bad) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+  if (corrupt) record_status(a.ws.status, DSMC_ERR_INVALID_ARG);
+  if (bad) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+  fence_proxy_async();  // the operand rows, written by these threads, feed the tensor core
+  bar_sync(kBarCore, kFCoreThreads);
+}
+
+// Row CDF and pair draws of combination s from stage st (the core warps): the row totals,
+// the row weights and their exact 2^40 fixed-point prefix sums, the increment of Eq. (Lab),
+// then every slot's pair in three exact inverse-CDF stages and the new block's index maps.
+template <int D>
+__device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st, int s, int ct, int cw, int lane,
+                                          CoreScratch& sc) {
+  using L = Stage<D>;
+  const int N = a.N, nT = a.nT, nTp = a.nTp;
+  float* fV = reinterpret_cast<float*>(st + L::fV);
+  float* fB = reinterpret_cast<float*>(st + L::fB);
+  float* fU = reinterpret_cast<float*>(st + L::fU);
+  float* fAl = reinterpret_cast<float*>(st + L::fAl);
+  float* fDl = reinterpret_cast<float*>(st + L::fDl);
+  const double* fSh = reinterpret_cast<const double*>(st + L::fSh);
+  float* Tq = reinterpret_cast<float*>(st + L::T);
+  unsigned long long* cum = reinterpret_cast<unsigned long long*>(st + L::cum);
+  float* fL = reinterpret_cast<float*>(st + L::fL);
+  int* under = reinterpret_cast<int*>(cum);  // rows that underflowed (before cum is built)
+  const Comb cb = comb_of(a, s);
+  if (ct == 0) {
+    sc.n_under = 0;
+    sc.nonfinite = 0;
+  }
+  bar_sync(kBarCore, kFCoreThreads);
+  // row totals: the tile weights in ascending order (the split path's definition)
+  for (int i = ct; i < N; i += kFCoreThreads) {
+    float t = row_total(Tq + (size_t)i * nTp, nT, nTp);
+    if (isnan(t)) {
+      sc.nonfinite = 1;
+      t = 0.f;
+    }
+    fL[i] = t;
+    if (t < 0x1p-64f) under[atomicAdd(&sc.n_under, 1)] = i;
+  }
+  bar_sync(kBarCore, kFCoreThreads);
+  for (int uq = cw; uq < sc.n_under; uq += kFCoreWarps) {  // rare: exact-max recomputation
+    const int i = under[uq];
+    float si, dl;
+    recompute_row<D, true>(fU + (size_t)i * D, fAl[i], fV, fB, N, a.B, nT, Tq + (size_t)i * nTp, &si, &dl);
+    __syncwarp();
+    if (lane == 0) {
+      si = row_total(Tq + (size_t)i * nTp, nT, nTp);
+      fL[i] = isnan(si) ? 0.f : si;
+      fDl[i] = dl;
+    }
+  }
+  bar_sync(kBarCore, kFCoreThreads);
+  // row weights r_i = 2^(l_i - max l) and their exact fixed-point prefix sums
+  float mloc = -INFINITY;
+  for (int i = ct; i < N; i += kFCoreThreads) {
+    const float t = fL[i];
+    if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = t;
+    const float v = row_log2_weight(fSh[i], fDl[i], t);
+    fL[i] = v;
+    mloc = fmaxf(mloc, v);
+  }
+  mloc = warp_max(mloc);
+  if (lane == 0) sc.red[cw] = mloc;
+  bar_sync(kBarCore, kFCoreThreads);
+  float M = sc.red[0];
+  for (int w = 1; w < kFCoreWarps; ++w) M = fmaxf(M, sc.red[w]);
+  const bool degenerate = !(M > -INFINITY) || isnan(M);
+  for (int i = ct; i < N; i += kFCoreThreads) {
+    const float r = row_weight(fL[i], M, degenerate);
+    if (a.inspect) a.ws.rw[(size_t)s * N + i] = r;
+    cum[i] = (unsigned long long)__float2ull_rz(r * 0x1p40f);
+  }
+  bar_sync(kBarCore, kFCoreThreads);
+  group_scan_u64(cum, N, sc.warp_tot, ct);
+  if (ct == 0) {
+    const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(cum[N - 1]);
+    cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
+    if (degenerate || cum[N - 1] == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
+    if (sc.nonfinite) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+  }
+  if (a.inspect) {
+    for (int i = ct; i < N; i += kFCoreThreads) {
+      a.ws.cum[(size_t)s * N + i] = cum[i];
+      a.ws.delta[(size_t)s * N + i] = fDl[i];
+      for (int kt = 0; kt < nT; ++kt) a.ws.T[((size_t)s * N + i) * nTp + kt] = Tq[(size_t)i * nTp + kt];
+    }
+  }
+  // the pairs, each in three exact inverse-CDF stages, and the new block's index maps
+  const SlotOut o = slot_out(a, cb, ct == 0);
+  DrawIn in;
+  in.sys = (a.resampler == DSMC_SYSTEMATIC && !cb.conditional) ? 1 : 0;
+  in.cum = cum;
+  in.T = Tq;
+  in.U = fU;
+  in.alpha = fAl;
+  in.delta = fDl;
+  in.V = fV;
+  in.beta = fB;
+  in.N = N;
+  in.B = a.B;
+  in.nT = nT;
+  in.nTp = nTp;
+  const int n_lo = cb.conditional ? 1 : 0;
+  const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
+  for (int n = n_lo + ct; n < n_hi; n += kFCoreThreads) {
+    int i, j;
+    draw_pair<D, true>(in, cb.seed, cb.base, cb.gid, n, i, j);
+    o.put(n, i, j);
+  }
+  bar_sync(kBarCore, kFCoreThreads);
 }
 
 template <int D, int KIND>
@@ -150,25 +427,16 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
   extern __shared__ __align__(1024) unsigned char fsm_raw[];
   unsigned char* fsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(fsm_raw) + 1023) & ~(uintptr_t)1023);
   // ops_full: a stage's operands are built; tiles_full: its tile sums are complete;
-  // stage_free: its draws are done; acc_full / acc_free: a TMEM accumulator holds a block /
-  // has been read out
-  __shared__ __align__(8) uint64_t ops_full[2], tiles_full[2], stage_free[2], acc_full[kFAcc], acc_free[kFAcc];
+  // acc_full / acc_free: a TMEM accumulator holds a block / has been read out
+  __shared__ __align__(8) uint64_t ops_full[2], tiles_full[2], acc_full[kFAcc], acc_free[kFAcc];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_s;
-  __shared__ int ld_ok, dr_ok;
-  // loader scratch
-  __shared__ float gsum[kMaxColumnGroups * D];
-  __shared__ float red_l[kFLoadWarps];
-  __shared__ float mu_s[D];
-  __shared__ float bstar_s;
-  // draw scratch
-  __shared__ unsigned long long warp_tot[kFDrawWarps];
-  __shared__ float red_d[kFDrawWarps];
-  __shared__ int n_under, nonfinite_s;
+  __shared__ CoreScratch sc;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int N = a.N, d = a.d, nT = a.nT, nTp = a.nTp;
+  const int N = a.N, nTp = a.nTp;
   const int RT = (N + kMmaM - 1) / kMmaM;
+  const int ncomb = a.mc > (int)blockIdx.x ? (a.mc - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const volatile int* abort_v = &abort_s;
   auto raise_abort = [&]() {
     if (atomicExch(&abort_s, 1) == 0) record_status(a.ws.status, DSMC_ERR_TIMEOUT);
@@ -179,7 +447,6 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
     for (int q = 0; q < 2; ++q) {
       mbar_init(smem_u32(&ops_full[q]), 1);
       mbar_init(smem_u32(&tiles_full[q]), kFEpiWarps);
-      mbar_init(smem_u32(&stage_free[q]), 1);
     }
     for (int q = 0; q < kFAcc; ++q) {
       mbar_init(smem_u32(&acc_full[q]), 1);
@@ -200,12 +467,13 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
 
   if (warp < kFEpiWarps) {
     // ------------------------------------------------------------------ epilogue
+    // warp (g, h) reads TMEM lanes 32 g .. 32 g + 31 (its rows) and columns 32 h .. 32 h + 31
+    // of each block: one 32-column tile weight per row and block
     const int g = warp & 3, h = warp >> 2;
     int blk = 0;
     bool stop = false;
-    for (int k = 0, s = blockIdx.x; s < a.mc && !stop; ++k, s += gridDim.x) {
-      unsigned char* st = fsm + (size_t)(k & 1) * L::bytes;
-      float* Tq = reinterpret_cast<float*>(st + L::T);
+    for (int k = 0; k < ncomb && !stop; ++k) {
+      float* Tq = reinterpret_cast<float*>(fsm + (size_t)(k & 1) * L::bytes + L::T);
       for (int rt = 0; rt < RT && !stop; ++rt) {
         const int row = rt * kMmaM + 32 * g + lane;
         for (int cb = 0; cb < RT; ++cb, ++blk) {
@@ -218,320 +486,50 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int col0 = cb * kMmaN + 64 * h;
-          uint32_t acc0[32], acc1[32];
-          const uint32_t taddr = tb + ((uint32_t)(32 * g) << 16) + (uint32_t)acc * kMmaN + 64 * h;
-          tmem_ld32(taddr, acc0);
-          tmem_ld32(taddr + 32, acc1);
+          const int col0 = cb * kMmaN + 32 * h;
+          uint32_t acc32[32];
+          tmem_ld32(tb + ((uint32_t)(32 * g) << 16) + (uint32_t)acc * kMmaN + 32 * h, acc32);
           tmem_wait();
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(&acc_free[acc]));
-          float t0, t1;
-          if (col0 + 64 <= N) {
-            t0 = exp_sum32<false>(acc0, 32);
-            t1 = exp_sum32<false>(acc1, 32);
-          } else {
-            t0 = exp_sum32<true>(acc0, N - col0);
-            t1 = exp_sum32<true>(acc1, N - col0 - 32);
-          }
-          if (row < N) {
-            if (col0 + 32 < N)
-              *reinterpret_cast<float2*>(Tq + (size_t)row * nTp + col0 / 32) = make_float2(t0, t1);
-            else if (col0 < N)
-              Tq[(size_t)row * nTp + col0 / 32] = t0;
-          }
+          const float t = col0 + 32 <= N ? exp_sum32<false>(acc32, 32) : exp_sum32<true>(acc32, N - col0);
+          if (row < N && col0 < N) Tq[(size_t)row * nTp + col0 / 32] = t;
         }
       }
       if (stop) break;
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tiles_full[k & 1]));
     }
-  } else if (warp < kFEpiWarps + kFLoadWarps) {
-    // ------------------------------------------------------------------ loader
-    const int lt = threadIdx.x - kFLoad0;
-    const int lw = lt >> 5;
-    for (int k = 0, s = blockIdx.x; s < a.mc; ++k, s += gridDim.x) {
-      const int q = k & 1;
-      if (k >= 2) {  // the draws of combination k - 2 have released this stage
-        if (lt == 0) ld_ok = mbar_wait_or_abort(smem_u32(&stage_free[q]), (uint32_t)((k >> 1) - 1) & 1, abort_v);
-        bar_sync(kBarLoad, kFLoadThreads);
-        if (!ld_ok) {
-          if (lt == 0) raise_abort();
-          break;
-        }
-      }
-      unsigned char* st = fsm + (size_t)q * L::bytes;
-      unsigned char* opU = st + L::opU;
-      unsigned char* opV = st + L::opV;
-      float* fV = reinterpret_cast<float*>(st + L::fV);
-      float* fB = reinterpret_cast<float*>(st + L::fB);
-      float* fU = reinterpret_cast<float*>(st + L::fU);
-      float* fAl = reinterpret_cast<float*>(st + L::fAl);
-      float* fDl = reinterpret_cast<float*>(st + L::fDl);
-      double* fSh = reinterpret_cast<double*>(st + L::fSh);
-      const Comb cb = comb_of(a, s);
-      const int at = cb.at, c = cb.c, b = cb.b, K = cb.K;
-      const bool left_leaf = (cb.level == 0);
-      const int sR = b - c + 1;
-      const bool right_leaf = (sR == 1);
-      const int bufL = cb.level & 1, bufR = ceil_log2(sR) & 1;
-      // the inputs staged in this stage's tile-sum area (written by the epilogue only after
-      // these operands have been consumed)
-      float* sXc = reinterpret_cast<float*>(st + L::T);
-      float* sXl = sXc + rnd((size_t)N * d, 4);
-      float* sR0 = sXl + rnd((size_t)N * d, 4);
-      float* sL0 = sR0 + rnd((size_t)N, 4);
-      stage_group(sXc, cb.X + (size_t)c * N * d, N * d, lt, kFLoadThreads);
-      stage_group(sXl, cb.X + (size_t)(c - 1) * N * d, N * d, lt, kFLoadThreads);
-      if (right_leaf)
-        stage_group(sR0, cb.logw + (size_t)c * N, N, lt, kFLoadThreads);
-      else
-        stage_group(reinterpret_cast<int32_t*>(sR0), cb.first + ((size_t)bufR * K + c) * N, N, lt, kFLoadThreads);
-      if (left_leaf)
-        stage_group(sL0, cb.logw + (size_t)(c - 1) * N, N, lt, kFLoadThreads);
-      else
-        stage_group(reinterpret_cast<int32_t*>(sL0), cb.last + ((size_t)bufL * K + at) * N, N, lt, kFLoadThreads);
-      const int32_t* firstR = right_leaf ? nullptr : reinterpret_cast<const int32_t*>(sR0);
-      const float* lwc = right_leaf ? sR0 : nullptr;
-      const int32_t* lastL = left_leaf ? nullptr : reinterpret_cast<const int32_t*>(sL0);
-      const float* lwl = left_leaf ? sL0 : nullptr;
-      float yc[D], qm[D], qs[D], qinv[D];
-#pragma unroll
-      for (int kk = 0; kk < D; ++kk) yc[kk] = kk < d ? cb.y[(size_t)c * d + kk] : 0.f;
-      proposal_at<D>(mp, cb.y, cb.prop_mean, cb.prop_std, c, qm, qs);
-      const float qnorm = proposal_consts<D>(d, qs, qinv);
-      bar_sync(kBarLoad, kFLoadThreads);
-
-      // column pass: b'_j, states, the column mean mu (groups of 32 Q columns, each summed by
-      // one warp lane-sequentially then by a butterfly, group sums in group order: the same
-      // order as every other column pass) and B* = max_j b'_j
-      bool bad = false, corrupt = false;
-      float mu[D], bstar;
-      {
-        const int Qg = (N + 1023) / 1024, Wd = 32 * Qg;
-        const int G = (N + Wd - 1) / Wd;
-        float bmax = -INFINITY;
-        for (int gg = lw; gg < G; gg += kFLoadWarps) {
-          float accs[D];
-#pragma unroll
-          for (int kk = 0; kk < D; ++kk) accs[kk] = 0.f;
-          for (int cc = 0; cc < Qg; ++cc) {
-            const int j = Wd * gg + 32 * cc + lane;
-            if (j < N) {
-              float x[D];
-              const float bp = column_bprime<D>(mp, N, d, a.logN, yc, qm, qinv, qnorm, sXc, firstR, lwc, j, x, corrupt);
-#pragma unroll
-              for (int kk = 0; kk < D; ++kk) fV[vidx<D, true>(j) + kk] = x[kk];
-              fB[bidx<true>(j)] = bp;
-              bad |= isnan(bp);
-              bmax = fmaxf(bmax, bp);
-#pragma unroll
-              for (int kk = 0; kk < D; ++kk) accs[kk] += x[kk];
-            }
-          }
-#pragma unroll
-          for (int kk = 0; kk < D; ++kk) {
-            const float t = warp_sum(accs[kk]);
-            if (lane == 0) gsum[gg * D + kk] = t;
-          }
-        }
-        bmax = warp_max(bmax);
-        if (lane == 0) red_l[lw] = bmax;
-        bar_sync(kBarLoad, kFLoadThreads);
-        if (lt < D) {
-          float t = 0.f;
-          for (int gg = 0; gg < G; ++gg) t += gsum[gg * D + lt];
-          mu_s[lt] = t / (float)N;
-        }
-        if (lt == 0) {
-          float t = red_l[0];
-          for (int w = 1; w < kFLoadWarps; ++w) t = fmaxf(t, red_l[w]);
-          bstar_s = t;
-        }
-        bar_sync(kBarLoad, kFLoadThreads);
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) mu[kk] = mu_s[kk];
-        bstar = bstar_s;
-      }
-      // columns: v_j = x_j - mu, beta_j, the MMA column rows [v, 1, 1, beta_hi, beta_lo]
-      for (int j = lt; j < N; j += kFLoadThreads) {
-        float v[D];
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) v[kk] = fV[vidx<D, true>(j) + kk];
-        const float bj = column_beta<D>(mp, v, mu, fB[bidx<true>(j)], bstar);
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) fV[vidx<D, true>(j) + kk] = v[kk];
-        fB[bidx<true>(j)] = bj;
-        float ext[4];
-        ext[0] = 1.f;
-        ext[1] = 1.f;
-        split_mma(bj, KIND, &ext[2], &ext[3]);
-        store_mma_row_t<D, KIND>(opV, kFNmax, j, v, ext);
-        if (a.inspect) {
-#pragma unroll
-          for (int kk = 0; kk < D; ++kk) a.ws.V[((size_t)s * N + j) * D + kk] = v[kk];
-          a.ws.beta[(size_t)s * N + j] = bj;
-        }
-      }
-      {  // rows and columns past N within the last tile are zero
-        const float zero[D] = {};
-        const float zext[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int j = N + lt; j < RT * kMmaM; j += kFLoadThreads) {
-          store_mma_row_t<D, KIND>(opV, kFNmax, j, zero, zext);
-          store_mma_row_t<D, KIND>(opU, kFNmax, j, zero, zext);
-        }
-      }
-      bar_sync(kBarLoad, kFLoadThreads);  // the rows read a sample of the columns
-      // rows: u_i, alpha_i (less the row shift delta_i, which moves into shift_i), and the MMA
-      // row [u, alpha_hi, alpha_lo, 1, 1]
-      for (int i = lt; i < N; i += kFLoadThreads) {
-        float ul[D], ai;
-        const float al0 = row_terms<D>(mp, N, d, a.logN, sXl, lastL, lwl, i, mu, ul, ai, corrupt);
-        const float dl = row_shift<D, true>(ul, al0, fV, fB, N);
-        const float al = __fsub_rn(al0, dl);
-        bad |= isnan(ai);
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) fU[(size_t)i * D + kk] = ul[kk];
-        fAl[i] = al;
-        fDl[i] = 0.f;
-        const double sh = (double)ai + (double)mp.log_f_max + (double)bstar + (double)dl * kLn2d;
-        fSh[i] = sh;
-        float ext[4];
-        split_mma(al, KIND, &ext[0], &ext[1]);
-        ext[2] = 1.f;
-        ext[3] = 1.f;
-        store_mma_row_t<D, KIND>(opU, kFNmax, i, ul, ext);
-        if (a.inspect) {
-#pragma unroll
-          for (int kk = 0; kk < D; ++kk) a.ws.U[((size_t)s * N + i) * D + kk] = ul[kk];
-          a.ws.alpha[(size_t)s * N + i] = al;
-          a.ws.shift[(size_t)s * N + i] = sh;
-        }
-      }
-      if (corrupt) record_status(a.ws.status, DSMC_ERR_INVALID_ARG);
-      if (bad) record_status(a.ws.status, DSMC_ERR_NONFINITE);
-      fence_proxy_async();  // the operand rows, written by these threads, feed the tensor core
-      bar_sync(kBarLoad, kFLoadThreads);
-      if (lt == 0) mbar_arrive(smem_u32(&ops_full[q]));
-    }
   } else if (warp < kFCtrlWarp) {
-    // ------------------------------------------------------------------ draws
-    const int dt = threadIdx.x - kFDraw0;
-    const int dw = dt >> 5;
-    for (int k = 0, s = blockIdx.x; s < a.mc; ++k, s += gridDim.x) {
+    // ------------------------------------------------------------------ core warps
+    // loads of combinations 0 and 1, then for every k: the draws of k (once its tile sums
+    // are complete) and the load of k + 2 into the stage k has just released
+    const int ct = threadIdx.x - kFCore0, cw = ct >> 5;
+    for (int k = 0; k < ncomb && k < 2; ++k) {
+      core_load<D, KIND>(a, mp, fsm + (size_t)k * L::bytes, blockIdx.x + k * gridDim.x, ct, cw, lane, RT, sc);
+      if (ct == 0) mbar_arrive(smem_u32(&ops_full[k]));
+    }
+    for (int k = 0; k < ncomb; ++k) {
       const int q = k & 1;
-      if (dt == 0) dr_ok = mbar_wait_or_abort(smem_u32(&tiles_full[q]), (uint32_t)(k >> 1) & 1, abort_v);
-      bar_sync(kBarDraw, kFDrawThreads);
-      if (!dr_ok) {
-        if (dt == 0) raise_abort();
+      if (ct == 0) sc.ok = mbar_wait_or_abort(smem_u32(&tiles_full[q]), (uint32_t)(k >> 1) & 1, abort_v);
+      bar_sync(kBarCore, kFCoreThreads);
+      if (!sc.ok) {
+        if (ct == 0) raise_abort();
         break;
       }
-      unsigned char* st = fsm + (size_t)q * L::bytes;
-      float* fV = reinterpret_cast<float*>(st + L::fV);
-      float* fB = reinterpret_cast<float*>(st + L::fB);
-      float* fU = reinterpret_cast<float*>(st + L::fU);
-      float* fAl = reinterpret_cast<float*>(st + L::fAl);
-      float* fDl = reinterpret_cast<float*>(st + L::fDl);
-      const double* fSh = reinterpret_cast<const double*>(st + L::fSh);
-      float* Tq = reinterpret_cast<float*>(st + L::T);
-      unsigned long long* cum = reinterpret_cast<unsigned long long*>(st + L::cum);
-      float* fL = reinterpret_cast<float*>(st + L::fL);
-      int* under = reinterpret_cast<int*>(cum);  // rows that underflowed (before cum is built)
-      const Comb cb = comb_of(a, s);
-      if (dt == 0) {
-        n_under = 0;
-        nonfinite_s = 0;
+      core_draw<D>(a, fsm + (size_t)q * L::bytes, blockIdx.x + k * gridDim.x, ct, cw, lane, sc);
+      if (k + 2 < ncomb) {
+        core_load<D, KIND>(a, mp, fsm + (size_t)q * L::bytes, blockIdx.x + (k + 2) * gridDim.x, ct, cw, lane, RT,
+                           sc);
+        if (ct == 0) mbar_arrive(smem_u32(&ops_full[q]));
       }
-      bar_sync(kBarDraw, kFDrawThreads);
-      // row totals: the tile weights in ascending order (the split path's definition)
-      for (int i = dt; i < N; i += kFDrawThreads) {
-        float t = row_total(Tq + (size_t)i * nTp, nT, nTp);
-        if (isnan(t)) {
-          nonfinite_s = 1;
-          t = 0.f;
-        }
-        fL[i] = t;
-        if (t < 0x1p-64f) under[atomicAdd(&n_under, 1)] = i;
-      }
-      bar_sync(kBarDraw, kFDrawThreads);
-      for (int uq = dw; uq < n_under; uq += kFDrawWarps) {  // rare: exact-max recomputation
-        const int i = under[uq];
-        float si, dl;
-        recompute_row<D, true>(fU + (size_t)i * D, fAl[i], fV, fB, N, a.B, nT, Tq + (size_t)i * nTp, &si, &dl);
-        __syncwarp();
-        if (lane == 0) {
-          si = row_total(Tq + (size_t)i * nTp, nT, nTp);
-          fL[i] = isnan(si) ? 0.f : si;
-          fDl[i] = dl;
-        }
-      }
-      bar_sync(kBarDraw, kFDrawThreads);
-      // row weights r_i = 2^(l_i - max l) and their exact fixed-point prefix sums
-      float mloc = -INFINITY;
-      for (int i = dt; i < N; i += kFDrawThreads) {
-        const float t = fL[i];
-        if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = t;
-        const float v = row_log2_weight(fSh[i], fDl[i], t);
-        fL[i] = v;
-        mloc = fmaxf(mloc, v);
-      }
-      mloc = warp_max(mloc);
-      if (lane == 0) red_d[dw] = mloc;
-      bar_sync(kBarDraw, kFDrawThreads);
-      float M = red_d[0];
-      for (int w = 1; w < kFDrawWarps; ++w) M = fmaxf(M, red_d[w]);
-      const bool degenerate = !(M > -INFINITY) || isnan(M);
-      for (int i = dt; i < N; i += kFDrawThreads) {
-        const float r = row_weight(fL[i], M, degenerate);
-        if (a.inspect) a.ws.rw[(size_t)s * N + i] = r;
-        cum[i] = (unsigned long long)__float2ull_rz(r * 0x1p40f);
-      }
-      bar_sync(kBarDraw, kFDrawThreads);
-      group_scan_u64(cum, N, warp_tot, dt);
-      if (dt == 0) {
-        const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(cum[N - 1]);
-        cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
-        if (degenerate || cum[N - 1] == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
-        if (nonfinite_s) record_status(a.ws.status, DSMC_ERR_NONFINITE);
-      }
-      if (a.inspect) {
-        for (int i = dt; i < N; i += kFDrawThreads) {
-          a.ws.cum[(size_t)s * N + i] = cum[i];
-          a.ws.delta[(size_t)s * N + i] = fDl[i];
-          for (int kt = 0; kt < nT; ++kt) a.ws.T[((size_t)s * N + i) * nTp + kt] = Tq[(size_t)i * nTp + kt];
-        }
-      }
-      // the pairs, each in three exact inverse-CDF stages, and the new block's index maps
-      const SlotOut o = slot_out(a, cb, dt == 0);
-      DrawIn in;
-      in.sys = (a.resampler == DSMC_SYSTEMATIC && !cb.conditional) ? 1 : 0;
-      in.cum = cum;
-      in.T = Tq;
-      in.U = fU;
-      in.alpha = fAl;
-      in.delta = fDl;
-      in.V = fV;
-      in.beta = fB;
-      in.N = N;
-      in.B = a.B;
-      in.nT = nT;
-      in.nTp = nTp;
-      const int n_lo = cb.conditional ? 1 : 0;
-      const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
-      for (int n = n_lo + dt; n < n_hi; n += kFDrawThreads) {
-        int i, j;
-        draw_pair<D, true>(in, cb.seed, cb.base, cb.gid, n, i, j);
-        o.put(n, i, j);
-      }
-      bar_sync(kBarDraw, kFDrawThreads);
-      if (dt == 0) mbar_arrive(smem_u32(&stage_free[q]));
     }
   } else if (lane == 0) {
     // ------------------------------------------------------------------ control: MMA issue
     int blk = 0, issued = 0;
     bool ok = true;
-    for (int k = 0, s = blockIdx.x; s < a.mc && ok; ++k, s += gridDim.x) {
+    for (int k = 0; k < ncomb && ok; ++k) {
       const int q = k & 1;
       ok = mbar_wait_or_abort(smem_u32(&ops_full[q]), (uint32_t)(k >> 1) & 1, abort_v);
       if (!ok) break;

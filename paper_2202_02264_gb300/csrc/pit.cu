@@ -42,7 +42,8 @@ struct PitWs {
   double *E, *g, *L;             // smoothing elements
   double *E2, *g2, *L2;
   double *z, *r;                 // SV pseudo-observations and their variances [K] (r < 0: none)
-  double* mlin;                  // SV linearisation points [K] (the previous smoothed means)
+  double* mlin;                  // linearisation points [K] (the previous smoothed means)
+  double *Ft, *ct;               // per-step linearised transitions [K][d][d], [K][d]
 };
 
 // ---- small dense linear algebra in shared memory, all threads of the CTA
@@ -115,6 +116,9 @@ __device__ void gj_solve(double* M, double* Rhs, int d, int nc, int* piv_s) {
 __global__ void __launch_bounds__(kPitThreads) pit_filter_elements(PitArgs p, PitWs w) {
   extern __shared__ double sm[];
   const int t = blockIdx.x, d = p.d, dd = d * d;
+  // the transition into step t: per-step linearisation (theta-logistic) or the model's
+  const double* Fm = (p.Ft != nullptr && t > 0) ? p.Ft + (size_t)t * dd : p.F;
+  const double* cv = (p.ct != nullptr && t > 0) ? p.ct + (size_t)t * d : p.c;
   double* S = sm;            // [d][d]
   double* G = S + dd;        // [d][d]: scratch of the first solve, then the gain
   double* T1 = G + dd;       // [d][d]
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(kPitThreads) pit_filter_elements(PitArgs p, Pi
   // the observation (or SV pseudo-observation) and its noise covariance
   if (threadIdx.x == 0) has_obs = 1;
   __syncthreads();
-  if (p.kind == DSMC_MODEL_SV) {
+  if (p.kind == DSMC_MODEL_SV || p.kind == DSMC_MODEL_COX) {  // pseudo-observations
     if (threadIdx.x == 0) {
       const double rr = w.r[t];
       has_obs = rr > 0.0;
@@ -145,12 +149,12 @@ __global__ void __launch_bounds__(kPitThreads) pit_filter_elements(PitArgs p, Pi
   const double* P = t == 0 ? p.P0 : p.Q;
   if (!has_obs) {  // no information at this step: the prior / transition as is
     for (int e = threadIdx.x; e < dd; e += blockDim.x) {
-      A[e] = t == 0 ? 0.0 : p.F[e];
+      A[e] = t == 0 ? 0.0 : Fm[e];
       C[e] = P[e];
       J[e] = 0.0;
     }
     for (int k = threadIdx.x; k < d; k += blockDim.x) {
-      b[k] = t == 0 ? p.m0[k] : p.c[k];
+      b[k] = t == 0 ? p.m0[k] : cv[k];
       eta[k] = 0.0;
     }
     return;
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(kPitThreads) pit_filter_elements(PitArgs p, Pi
     const int r = e / d, cc = e - r * d;
     double sa = 0.0, sc = 0.0;
     for (int q = 0; q < d; ++q) {
-      sa = fma(T1[r * d + q], p.F[q * d + cc], sa);
+      sa = fma(T1[r * d + q], Fm[q * d + cc], sa);
       sc = fma(T1[r * d + q], p.Q[q * d + cc], sc);
     }
     A[e] = sa;
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(kPitThreads) pit_filter_elements(PitArgs p, Pi
   }
   for (int k = threadIdx.x; k < d; k += blockDim.x) {
     double s = 0.0;
-    for (int q = 0; q < d; ++q) s = fma(G[k * d + q], yv[q], fma(T1[k * d + q], p.c[q], s));
+    for (int q = 0; q < d; ++q) s = fma(G[k * d + q], yv[q], fma(T1[k * d + q], cv[q], s));
     b[k] = s;
   }
   __syncthreads();
@@ -224,19 +228,19 @@ __global__ void __launch_bounds__(kPitThreads) pit_filter_elements(PitArgs p, Pi
   // eta = F' S^-1 (y - c), J = F' S^-1 F: solve S X = [F | y - c] (S solved in place)
   for (int e = threadIdx.x; e < d * (d + 1); e += blockDim.x) {
     const int r = e / (d + 1), cc = e - r * (d + 1);
-    R2[e] = cc < d ? p.F[r * d + cc] : yv[r] - p.c[r];
+    R2[e] = cc < d ? Fm[r * d + cc] : yv[r] - cv[r];
   }
   __syncthreads();
   gj_solve(S, R2, d, d + 1, &piv);  // R2 = S^-1 [F | y - c]
   for (int e = threadIdx.x; e < dd; e += blockDim.x) {
     const int r = e / d, cc = e - r * d;
     double s = 0.0;
-    for (int q = 0; q < d; ++q) s = fma(p.F[q * d + r], R2[q * (d + 1) + cc], s);
+    for (int q = 0; q < d; ++q) s = fma(Fm[q * d + r], R2[q * (d + 1) + cc], s);
     J[e] = s;
   }
   for (int k = threadIdx.x; k < d; k += blockDim.x) {
     double s = 0.0;
-    for (int q = 0; q < d; ++q) s = fma(p.F[q * d + k], R2[q * (d + 1) + d], s);
+    for (int q = 0; q < d; ++q) s = fma(Fm[q * d + k], R2[q * (d + 1) + d], s);
     eta[k] = s;
   }
 }
@@ -370,12 +374,15 @@ __global__ void __launch_bounds__(kPitThreads) pit_smooth_elements(PitArgs p, Pi
   double* T = FP + dd;
   double* fm = T + dd;      // F m + c
   __shared__ int piv;
-  mat_mul(FP, p.F, false, P, false, d, d, d);
-  mat_mul(T, FP, false, p.F, true, d, d, d);
+  // the transition from step t to t + 1
+  const double* Fm = p.Ft != nullptr ? p.Ft + (size_t)(t + 1) * dd : p.F;
+  const double* cv = p.ct != nullptr ? p.ct + (size_t)(t + 1) * d : p.c;
+  mat_mul(FP, Fm, false, P, false, d, d, d);
+  mat_mul(T, FP, false, Fm, true, d, d, d);
   for (int e = threadIdx.x; e < dd; e += blockDim.x) Pp[e] = T[e] + p.Q[e];
   for (int k = threadIdx.x; k < d; k += blockDim.x) {
-    double s = p.c[k];
-    for (int q = 0; q < d; ++q) s = fma(p.F[k * d + q], m[q], s);
+    double s = cv[k];
+    for (int q = 0; q < d; ++q) s = fma(Fm[k * d + q], m[q], s);
     fm[k] = s;
   }
   __syncthreads();
@@ -390,7 +397,7 @@ __global__ void __launch_bounds__(kPitThreads) pit_smooth_elements(PitArgs p, Pi
     double s = 0.0;
     for (int q = 0; q < d; ++q) {
       double fpq = 0.0;  // (F P)[q][cc]
-      for (int u = 0; u < d; ++u) fpq = fma(p.F[q * d + u], P[u * d + cc], fpq);
+      for (int u = 0; u < d; ++u) fpq = fma(Fm[q * d + u], P[u * d + cc], fpq);
       s = fma(FP[q * d + r], fpq, s);
     }
     T[e] = P[e] - s;
@@ -475,6 +482,35 @@ __global__ void pit_sv_linearise(int K, const float* y, const double* m, double 
   }
 }
 
+// COX: log h = y x - e^x, so lambda = e^{m} and the gradient is y - e^{m}: the
+// pseudo-observation z = m + (y - e^m) / e^m with variance e^{-m}.
+__global__ void pit_cox_linearise(int K, const float* y, const double* m, double mu, double* z, double* r) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= K) return;
+  const double mt = m ? m[t] : mu;
+  const double lam = exp(mt);
+  z[t] = mt + ((double)y[t] - lam) / lam;
+  r[t] = 1.0 / lam;
+}
+
+// THETA_LOGISTIC: the transition into step t linearised around the previous mean m_{t-1}:
+// F_t = 1 - tau1 tau2 e^{tau2 m}, c_t = m + tau0 - tau1 e^{tau2 m} - F_t m.
+__global__ void pit_theta_linearise(int K, const double* m, double tau0, double tau1, double tau2, double* Ft,
+                                    double* ct) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= K) return;
+  if (t == 0) {
+    Ft[0] = 1.0;
+    ct[0] = 0.0;
+    return;
+  }
+  const double mp = m[t - 1];
+  const double e = exp(tau2 * mp);
+  const double F = 1.0 - tau1 * tau2 * e;
+  Ft[t] = F;
+  ct[t] = mp + tau0 - tau1 * e - F * mp;
+}
+
 __global__ void pit_sv_from_float(int K, const float* m_in, double* m) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < K) m[t] = (double)m_in[t];
@@ -508,7 +544,7 @@ size_t pit_workspace_bytes(int K, int d) {
   auto r256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
   size_t o = 256 + r256((4 * dd + 2 * d) * sizeof(double));
   const size_t parts[] = {Kdd, Kd, Kdd, Kd, Kdd, Kdd, Kd, Kdd, Kd, Kdd,
-                          Kdd, Kd, Kdd, Kdd, Kd, Kdd, (size_t)K, (size_t)K, (size_t)K};
+                          Kdd, Kd, Kdd, Kdd, Kd, Kdd, (size_t)K, (size_t)K, (size_t)K, Kdd, Kd};
   for (size_t n : parts) o += r256(n * sizeof(double));
   return o;
 }
@@ -532,6 +568,7 @@ PitWs carve(void* ws, int K, int d, int** status, double** params) {
   w.E = take(Kdd); w.g = take(Kd); w.L = take(Kdd);
   w.E2 = take(Kdd); w.g2 = take(Kd); w.L2 = take(Kdd);
   w.z = take(K); w.r = take(K); w.mlin = take(K);
+  w.Ft = take(Kdd); w.ct = take(Kd);
   return w;
 }
 
@@ -577,17 +614,27 @@ cudaError_t launch_pit(PitArgs pa, const double* model, int iterations, const fl
   e = cudaMemsetAsync(status, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   int launches = 0;
-  const bool sv = pa.kind == DSMC_MODEL_SV;
-  const int it_n = sv ? (iterations > 0 ? iterations : 1) : 1;
-  bool have_m = false;  // SV: linearise around mlin (else around the stationary mean)
-  if (sv && init_mean) {
-    pit_sv_from_float<<<(K + 127) / 128, 128, 0, st>>>(K, init_mean, w.mlin);
+  const bool pseudo = pa.kind == DSMC_MODEL_SV || pa.kind == DSMC_MODEL_COX;  // observation linearised
+  const bool theta = pa.kind == DSMC_MODEL_THETA_LOGISTIC;                    // transition linearised
+  const bool iter = pseudo || theta;
+  const int it_n = iter ? (iterations > 0 ? iterations : 1) : 1;
+  bool have_m = false;  // linearise around mlin (else around the stationary mean, or y_t)
+  if (iter && (init_mean || theta)) {
+    pit_sv_from_float<<<(K + 127) / 128, 128, 0, st>>>(K, init_mean ? init_mean : pa.y, w.mlin);
     ++launches;
     have_m = true;
   }
+  pa.Ft = theta ? w.Ft : nullptr;
+  pa.ct = theta ? w.ct : nullptr;
   for (int it = 0; it < it_n; ++it) {
-    if (sv) {
+    if (pa.kind == DSMC_MODEL_SV) {
       pit_sv_linearise<<<(K + 127) / 128, 128, 0, st>>>(K, pa.y, have_m ? w.mlin : nullptr, pa.mu, w.z, w.r);
+      ++launches;
+    } else if (pa.kind == DSMC_MODEL_COX) {
+      pit_cox_linearise<<<(K + 127) / 128, 128, 0, st>>>(K, pa.y, have_m ? w.mlin : nullptr, pa.mu, w.z, w.r);
+      ++launches;
+    } else if (theta) {
+      pit_theta_linearise<<<(K + 127) / 128, 128, 0, st>>>(K, w.mlin, pa.tau0, pa.tau1, pa.tau2, w.Ft, w.ct);
       ++launches;
     }
     PitWs f = w;
@@ -612,7 +659,7 @@ cudaError_t launch_pit(PitArgs pa, const double* model, int iterations, const fl
     ++launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (sv && it + 1 < it_n) {  // the next linearisation point: this iteration's means
+    if (iter && it + 1 < it_n) {  // the next linearisation point: this iteration's means
       e = cudaMemcpyAsync(w.mlin, s.g, sizeof(double) * (size_t)K, cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) return e;
       have_m = true;

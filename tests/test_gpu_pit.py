@@ -1,7 +1,9 @@
 """The parallel-in-time linearised Gaussian smoother (Section 4.1, Algorithm 4) on the device,
 through the C ABI, against the oracle's sequential FP64 smoother; and dSMC with its
-marginals as proposals q_t = nu_t (DSMC_PROP_GAUSS): the same smoother, with less Monte
-Carlo variance than the observation-centred or stationary proposals."""
+marginals as proposals q_t = nu_t (DSMC_PROP_GAUSS): the same smoother (RTS / the grid), and
+for the linear-Gaussian model less Monte Carlo variance than the observation-centred
+proposals.  (For the stochastic-volatility model the Laplace marginals are narrower than
+the skewed smoothing marginals, and the spread is not smaller; the means stay unbiased.)"""
 import dataclasses
 
 import numpy as np
@@ -111,6 +113,4 @@ def test_dsmc_with_sv_pit_proposals():
     mean, std, _ = dsmc.dsmc_gaussian_proposals(dsmc.HostModel(m), dev(y), iterations=20)
     gm, _, _ = grid.sv_grid_smoother(m.mu, m.phi, m.sigma, y[:, 0].astype(np.float64))
     pit = _seed_means(m, y, K, N, R, mean, std)
-    stat = _seed_means(m, y, K, N, R)
     _check(pit, gm[:, None])
-    assert pit.std(0, ddof=1).mean() < 0.8 * stat.std(0, ddof=1).mean()
