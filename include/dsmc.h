@@ -56,34 +56,51 @@ typedef enum {
                                 than FP32 rounding (ratio > 1 + 2^-10): a broken bound */
 } dsmc_status_t;
 
-enum { DSMC_MODEL_LGSSM = 0, DSMC_MODEL_SV = 1 };
-enum { DSMC_PROP_OBS = 0, DSMC_PROP_GAUSS = 1 };
+enum { DSMC_MODEL_LGSSM = 0, DSMC_MODEL_SV = 1, DSMC_MODEL_COX = 2, DSMC_MODEL_THETA_LOGISTIC = 3,
+       DSMC_MODEL_CRW = 4 };
+enum { DSMC_PROP_OBS = 0, DSMC_PROP_GAUSS = 1, DSMC_PROP_UNIFORM = 2 };
 enum { DSMC_NU_EQ_Q = 0, DSMC_NU_PROP_H = 1 };
 enum { DSMC_FP32 = 0, DSMC_TF32 = 1, DSMC_BF16 = 2 };
 enum { DSMC_MULTINOMIAL = 0, DSMC_RS = 1, DSMC_MH = 2, DSMC_SYSTEMATIC = 3, DSMC_RS_FACTORED = 4 };
 
 /* The state-space model of Eq. (ssm) (Section 1).  All arrays are HOST, row-major, FP64,
- * read during the call only.
+ * read during the call only.  Every transition is Gaussian, N(m(x_{t-1}), Q).
  *   LGSSM: x_0 ~ N(m0, P0), x_t = A x_{t-1} + N(0, Q), y_t = x_t + N(0, R).
  *   SV (dx = 1): x_0 ~ N(mu, sigma^2/(1-phi^2)), x_t = mu + phi (x_{t-1} - mu) + sigma e,
- *                y_t = exp(x_t / 2) v, e, v ~ N(0, 1); A, Q, R, m0, P0 are ignored. */
+ *                y_t = exp(x_t / 2) v, e, v ~ N(0, 1).
+ *   COX (dx = 1, the photon-count model of Section 5.1): x_0 ~ N(mu, sigma^2/(1-phi^2)),
+ *                x_t = mu + phi (lam x_{t-1} - mu) + sigma e, y_t ~ Poisson(exp(x_t)).
+ *   THETA_LOGISTIC (dx = 1, the population model of Section 5.2): x_0 ~ N(0, 1),
+ *                x_t = x_{t-1} + tau0 - tau1 exp(tau2 x_{t-1}) + sigma e,
+ *                y_t = x_t + obs_sd v.
+ *   CRW (dx = 1, the constrained random walk of Section 5.3): x_0 ~ N(0, 1),
+ *                x_t = x_{t-1} + sigma e, potential h_t(x) = 1 if |x| <= bound else 0 (y is
+ *                not read; pass any [K][1] array).
+ * Fields a kind does not use are ignored (A, Q, R, m0, P0 by every kind but LGSSM). */
 typedef struct {
-  int kind;              /* DSMC_MODEL_LGSSM or DSMC_MODEL_SV */
-  int dx;                /* 1..32 */
+  int kind;              /* DSMC_MODEL_* */
+  int dx;                /* 1..32 (1 for every kind but LGSSM) */
   const double* A;       /* [dx][dx] */
   const double* Q;       /* [dx][dx], symmetric positive definite */
   const double* R;       /* [dx][dx], symmetric positive definite */
   const double* m0;      /* [dx] */
   const double* P0;      /* [dx][dx], symmetric positive definite */
-  double mu, phi, sigma; /* SV parameters, |phi| < 1, sigma > 0 */
+  double mu, phi, sigma; /* SV and COX: |phi| < 1, sigma > 0; THETA_LOGISTIC, CRW: sigma > 0 */
+  double lam;            /* COX: the factor of x_{t-1} inside the autoregression */
+  double tau0, tau1, tau2; /* THETA_LOGISTIC: the growth terms */
+  double obs_sd;         /* THETA_LOGISTIC: observation noise standard deviation > 0 */
+  double bound;          /* CRW: the constraint half-width > 0 */
 } dsmc_model_t;
 
 /* The proposals q_t of Algorithm 2 and the auxiliary laws nu_t of Definition 1.
- *   DSMC_PROP_OBS:   q_t = N(y_t, scale^2 I).
- *   DSMC_PROP_GAUSS: q_t = N(mean[t], diag(std[t]^2)); mean, std are DEVICE [K][dx] FP32.
+ *   DSMC_PROP_OBS:     q_t = N(y_t, scale^2 I).
+ *   DSMC_PROP_GAUSS:   q_t = N(mean[t], diag(std[t]^2)); mean, std are DEVICE [K][dx] FP32.
+ *   DSMC_PROP_UNIFORM: q_t = U([-scale, scale]^dx) (the constrained random walk's proposal).
  *   nu = DSMC_NU_EQ_Q:   nu_t = q_t for t >= 1 (the paper's experiments).
  *   nu = DSMC_NU_PROP_H: nu_t proportional to h_t(y_t | .), so that the combination weight
- *                        is log p_t(x_t | x_{t-1}) up to a constant. */
+ *                        is log p_t(x_t | x_{t-1}) up to a constant (LGSSM, SV,
+ *                        THETA_LOGISTIC and CRW; the COX potential has no finite normaliser
+ *                        when y_t = 0). */
 typedef struct {
   int kind;
   double scale;

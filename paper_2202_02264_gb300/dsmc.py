@@ -43,7 +43,9 @@ class Model(C.Structure):
                 ("A", C.POINTER(C.c_double)), ("Q", C.POINTER(C.c_double)),
                 ("R", C.POINTER(C.c_double)), ("m0", C.POINTER(C.c_double)),
                 ("P0", C.POINTER(C.c_double)),
-                ("mu", C.c_double), ("phi", C.c_double), ("sigma", C.c_double)]
+                ("mu", C.c_double), ("phi", C.c_double), ("sigma", C.c_double),
+                ("lam", C.c_double), ("tau0", C.c_double), ("tau1", C.c_double), ("tau2", C.c_double),
+                ("obs_sd", C.c_double), ("bound", C.c_double)]
 
 
 class Proposal(C.Structure):
@@ -186,11 +188,13 @@ class HostModel:
             self._arrs.append(a)
             return a.ctypes.data_as(C.POINTER(C.c_double))
 
+        extra = (float(getattr(m, "lam", 1.0)), float(getattr(m, "tau0", 0.0)), float(getattr(m, "tau1", 0.0)),
+                 float(getattr(m, "tau2", 0.0)), float(getattr(m, "obs_sd", 1.0)), float(getattr(m, "bound", 1.0)))
         if m.kind == W.LGSSM:
             self.struct = Model(m.kind, d, arr(m.A, (d, d)), arr(m.Q, (d, d)), arr(m.R, (d, d)),
-                                arr(m.m0, (d,)), arr(m.P0, (d, d)), 0.0, 0.0, 1.0)
+                                arr(m.m0, (d,)), arr(m.P0, (d, d)), 0.0, 0.0, 1.0, *extra)
         else:
-            self.struct = Model(m.kind, d, None, None, None, None, None, m.mu, m.phi, m.sigma)
+            self.struct = Model(m.kind, d, None, None, None, None, None, m.mu, m.phi, m.sigma, *extra)
 
 
 def make_config(K, N, seed, counter_base=0, resampler=MULTINOMIAL, compute=FP32,
@@ -202,8 +206,8 @@ def make_config(K, N, seed, counter_base=0, resampler=MULTINOMIAL, compute=FP32,
 
 def make_proposal(m: W.SSM, K: int, device="cuda"):
     """The C proposal struct and the device arrays it points into (kept alive by caller)."""
-    if m.prop_kind == W.PROP_OBS:
-        return Proposal(W.PROP_OBS, float(m.prop_scale), None, None, int(m.nu)), ()
+    if m.prop_kind in (W.PROP_OBS, W.PROP_UNIFORM):
+        return Proposal(int(m.prop_kind), float(m.prop_scale), None, None, int(m.nu)), ()
     mean = torch.as_tensor(proposal_rows(m.prop_mean, K, m.d), device=device)
     std = torch.as_tensor(proposal_rows(m.prop_std, K, m.d), device=device)
     return Proposal(W.PROP_GAUSS, 1.0, mean.data_ptr(), std.data_ptr(), int(m.nu)), (mean, std)
@@ -552,7 +556,7 @@ class BatchSmoother:
         if model.prop_kind == W.PROP_GAUSS:
             self.prop = Proposal(W.PROP_GAUSS, 1.0, None, None, int(model.nu))
         else:
-            self.prop = Proposal(W.PROP_OBS, float(model.prop_scale), None, None, int(model.nu))
+            self.prop = Proposal(int(model.prop_kind), float(model.prop_scale), None, None, int(model.nu))
         f32, f64, i32 = torch.float32, torch.float64, torch.int32
         dev = device
         self.X = [torch.empty((k, N, self.d), dtype=f32, device=dev) for k in self.Ks]

@@ -24,9 +24,13 @@ import numpy as np
 
 LGSSM = 0
 SV = 1
+COX = 2              # Section 5.1: Poisson counts, Gaussian autoregression
+THETA_LOGISTIC = 3   # Section 5.2: theta-logistic population dynamics
+CRW = 4              # Section 5.3: random walk constrained to [-bound, bound]
 
-PROP_OBS = 0    # q_t = N(y_t, scale^2 I)
-PROP_GAUSS = 1  # q_t = N(mean_t, diag(std_t^2)), arrays [K][d]
+PROP_OBS = 0      # q_t = N(y_t, scale^2 I)
+PROP_GAUSS = 1    # q_t = N(mean_t, diag(std_t^2)), arrays [K][d]
+PROP_UNIFORM = 2  # q_t = U([-scale, scale]^d)
 
 NU_EQ_Q = 0     # nu_t = q_t for t >= 1
 NU_PROP_H = 1   # nu_t proportional to h_t(y_t | .)
@@ -46,6 +50,12 @@ class SSM:
     mu: float = 0.0
     phi: float = 0.0
     sigma: float = 1.0
+    lam: float = 1.0      # COX
+    tau0: float = 0.0     # THETA_LOGISTIC
+    tau1: float = 0.0
+    tau2: float = 0.0
+    obs_sd: float = 1.0
+    bound: float = 1.0    # CRW
     prop_kind: int = PROP_OBS
     prop_scale: float = 1.0
     prop_mean: Optional[np.ndarray] = None  # [K][d]
@@ -113,12 +123,56 @@ def sv(K: int, mu=-1.0, phi=0.95, sigma=0.3, nu=NU_EQ_Q) -> SSM:
                prop_std=np.full((K, 1), s0), nu=nu, name="sv")
 
 
+def cox(K: int, mu=0.5, phi=0.9, sigma=0.35, lam=1.0) -> SSM:
+    """The Poisson-count model of Section 5.1 with the stationary law as q_t = nu_t."""
+    s0 = sigma / np.sqrt(1.0 - phi * phi)
+    return SSM(kind=COX, d=1, mu=float(mu), phi=float(phi), sigma=float(sigma), lam=float(lam),
+               prop_kind=PROP_GAUSS, prop_mean=np.full((K, 1), mu), prop_std=np.full((K, 1), s0),
+               nu=NU_EQ_Q, name="cox")
+
+
+def theta_logistic(tau0=0.15, tau1=0.12, tau2=0.25, q=0.12, r=0.25, prop_scale=0.5) -> SSM:
+    """The theta-logistic model of Section 5.2 (log-population), observation-centred
+    proposals N(y_t, prop_scale^2)."""
+    return SSM(kind=THETA_LOGISTIC, d=1, sigma=float(q), tau0=float(tau0), tau1=float(tau1), tau2=float(tau2),
+               obs_sd=float(r), prop_kind=PROP_OBS, prop_scale=float(prop_scale), nu=NU_EQ_Q,
+               name="theta_logistic")
+
+
+def crw(sigma=0.4, bound=1.0) -> SSM:
+    """The constrained random walk of Section 5.3 with the uniform proposal on the constraint."""
+    return SSM(kind=CRW, d=1, sigma=float(sigma), bound=float(bound), prop_kind=PROP_UNIFORM,
+               prop_scale=float(bound), nu=NU_EQ_Q, name="crw")
+
+
 def simulate(model: SSM, K: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
-    """Draw (x_{0:K-1}, y_{0:K-1}) from the model, FP64, shapes [K][d]."""
+    """Draw (x_{0:K-1}, y_{0:K-1}) from the model, FP64, shapes [K][d].  For the constrained
+    random walk y is all zero (the model has no observations) and x is one path of the
+    unconstrained walk."""
     rng = np.random.default_rng(seed)
     d = model.d
     x = np.zeros((K, d))
     y = np.zeros((K, d))
+    if model.kind == COX:
+        s0 = model.sigma / np.sqrt(1.0 - model.phi ** 2)
+        x[0, 0] = model.mu + s0 * rng.standard_normal()
+        for t in range(1, K):
+            x[t, 0] = (model.mu + model.phi * (model.lam * x[t - 1, 0] - model.mu)
+                       + model.sigma * rng.standard_normal())
+        y[:, 0] = rng.poisson(np.exp(x[:, 0]))
+        return x, y
+    if model.kind == THETA_LOGISTIC:
+        x[0, 0] = rng.standard_normal()
+        for t in range(1, K):
+            xp = x[t - 1, 0]
+            x[t, 0] = xp + model.tau0 - model.tau1 * np.exp(model.tau2 * xp) + model.sigma * rng.standard_normal()
+        y[:, 0] = x[:, 0] + model.obs_sd * rng.standard_normal(K)
+        return x, y
+    if model.kind == CRW:
+        x[0, 0] = rng.standard_normal()
+        for t in range(1, K):
+            x[t, 0] = x[t - 1, 0] + model.sigma * rng.standard_normal()
+        return x, y
     if model.kind == LGSSM:
         Lq = np.linalg.cholesky(model.Q)
         Lr = np.linalg.cholesky(model.R)
@@ -164,6 +218,18 @@ def workload(name: str, K: Optional[int] = None, N: Optional[int] = None) -> Wor
         K = 512 if K is None else K
         N = 512 if N is None else N
         m, seed = lgssm_d4(), 2264 + 4
+    elif name == "cox":
+        K = 256 if K is None else K
+        N = 512 if N is None else N
+        m, seed = cox(K), 2264 + 40
+    elif name == "theta_logistic":
+        K = 120 if K is None else K
+        N = 256 if N is None else N
+        m, seed = theta_logistic(), 2264 + 41
+    elif name == "crw":
+        K = 64 if K is None else K
+        N = 1024 if N is None else N
+        m, seed = crw(), 2264 + 42
     elif name in ("lgssm_d2", "lgssm_d16", "lgssm_d32"):
         dd = int(name[len("lgssm_d"):])
         K = 256 if K is None else K
