@@ -56,7 +56,8 @@ class Model(C.Structure):
                 ("mu", C.c_double), ("phi", C.c_double), ("sigma", C.c_double),
                 ("prop_kind", C.c_int), ("prop_scale", C.c_double),
                 ("prop_mean", C.POINTER(C.c_double)), ("prop_std", C.POINTER(C.c_double)),
-                ("nu", C.c_int)]
+                ("nu", C.c_int), ("lam", C.c_double), ("tau0", C.c_double), ("tau1", C.c_double),
+                ("tau2", C.c_double), ("obs_sd", C.c_double), ("bound", C.c_double)]
 
 
 class Config(C.Structure):
@@ -164,7 +165,10 @@ class _Keep:
         self.y = np.ascontiguousarray(np.asarray(y, np.float64).reshape(K, d))
         self.struct = Model(model.kind, d, _p(self.A), _p(self.Q), _p(self.R), _p(self.m0),
                             _p(self.P0), model.mu, model.phi, model.sigma, model.prop_kind,
-                            model.prop_scale, _p(self.pm), _p(self.ps), model.nu)
+                            model.prop_scale, _p(self.pm), _p(self.ps), model.nu,
+                            float(getattr(model, "lam", 1.0)), float(getattr(model, "tau0", 0.0)),
+                            float(getattr(model, "tau1", 0.0)), float(getattr(model, "tau2", 0.0)),
+                            float(getattr(model, "obs_sd", 1.0)), float(getattr(model, "bound", 1.0)))
 
 
 def _seed_words(seed: int):

@@ -115,14 +115,22 @@ static double u53(uint32_t w0, uint32_t w1) {
 typedef struct {
   int kind; /* 0: linear-Gaussian x_t = A x_{t-1} + N(0,Q), y_t = x_t + N(0,R), x_0 ~ N(m0,P0)
                1: stochastic volatility x_t = mu + phi (x_{t-1} - mu) + sigma e,
-                  y_t = exp(x_t / 2) v, x_0 ~ N(mu, sigma^2 / (1 - phi^2)), d = 1 */
+                  y_t = exp(x_t / 2) v, x_0 ~ N(mu, sigma^2 / (1 - phi^2)), d = 1
+               2: Poisson counts (Section 5.1) x_t = mu + phi (lam x_{t-1} - mu) + sigma e,
+                  y_t ~ Poisson(exp(x_t)), x_0 ~ N(mu, sigma^2 / (1 - phi^2)), d = 1
+               3: theta-logistic (Section 5.2) x_t = x_{t-1} + tau0 - tau1 exp(tau2 x_{t-1})
+                  + sigma e, y_t = x_t + obs_sd v, x_0 ~ N(0, 1), d = 1
+               4: constrained random walk (Section 5.3) x_t = x_{t-1} + sigma e, potential
+                  1{|x_t| <= bound}, x_0 ~ N(0, 1), d = 1 */
   int d;
   const double *A, *Q, *R, *m0, *P0; /* row-major d x d / d */
   double mu, phi, sigma;
-  int prop_kind;     /* 0: q_t = N(y_t, s^2 I);  1: q_t = N(mean_t, diag(std_t^2)) */
+  int prop_kind;     /* 0: q_t = N(y_t, s^2 I);  1: q_t = N(mean_t, diag(std_t^2));
+                        2: q_t = U([-s, s]^d) */
   double prop_scale; /* s */
   const double *prop_mean, *prop_std; /* [K][d] when prop_kind == 1 */
   int nu;            /* 0: nu_t = q_t;  1: nu_t proportional to h_t(y_t | .) */
+  double lam, tau0, tau1, tau2, obs_sd, bound;
 } orc_model;
 
 typedef struct {
@@ -190,12 +198,26 @@ static int ctx_init(model_ctx* c, const orc_model* m, int K, const double* y) {
   if (m->kind == 0) {
     if (cholesky(m->d, m->Q, c->LQ) || cholesky(m->d, m->R, c->LR) || cholesky(m->d, m->P0, c->LP0))
       return ORC_ERR_INVALID;
-  } else if (m->kind == 1) {
+  } else if (m->kind == 1 || m->kind == 2) {
     if (m->d != 1 || !(m->sigma > 0.0) || !(fabs(m->phi) < 1.0)) return ORC_ERR_INVALID;
+  } else if (m->kind == 3) {
+    if (m->d != 1 || !(m->sigma > 0.0) || !(m->obs_sd > 0.0)) return ORC_ERR_INVALID;
+  } else if (m->kind == 4) {
+    if (m->d != 1 || !(m->sigma > 0.0) || !(m->bound > 0.0)) return ORC_ERR_INVALID;
   } else {
     return ORC_ERR_INVALID;
   }
   return ORC_OK;
+}
+
+/* The transition mean m(x) of a one-dimensional model kind (1..4). */
+static double trans_mean_1d(const orc_model* m, double x) {
+  switch (m->kind) {
+    case 1: return m->mu + m->phi * (x - m->mu);
+    case 2: return m->mu + m->phi * (m->lam * x - m->mu);
+    case 3: return x + m->tau0 - m->tau1 * exp(m->tau2 * x);
+    default: return x;
+  }
 }
 
 /* log p_t(x' | x): transition density P_t of Eq. (ssm). */
@@ -210,7 +232,7 @@ static double log_f(const model_ctx* c, const double* x, const double* xn) {
     }
     return gauss_logpdf_chol(m->d, xn, mean, c->LQ);
   }
-  return normal_logpdf(xn[0], m->mu + m->phi * (x[0] - m->mu), m->sigma);
+  return normal_logpdf(xn[0], trans_mean_1d(m, x[0]), m->sigma);
 }
 
 /* sup over (x, x') of log p_t(x' | x): the Gaussian density at its mode. */
@@ -229,6 +251,9 @@ static double log_h(const model_ctx* c, int t, const double* x) {
   const orc_model* m = c->m;
   const double* yt = c->y + (size_t)t * m->d;
   if (m->kind == 0) return gauss_logpdf_chol(m->d, yt, x, c->LR);
+  if (m->kind == 2) return yt[0] * x[0] - exp(x[0]) - lgamma(yt[0] + 1.0);  /* Poisson(exp(x)) */
+  if (m->kind == 3) return normal_logpdf(yt[0], x[0], m->obs_sd);
+  if (m->kind == 4) return fabs(x[0]) <= m->bound ? 0.0 : -INFINITY;
   /* y | x ~ N(0, exp(x)) */
   return -0.5 * LOG_2PI - 0.5 * x[0] - 0.5 * yt[0] * yt[0] * exp(-x[0]);
 }
@@ -237,6 +262,7 @@ static double log_h(const model_ctx* c, int t, const double* x) {
 static double log_p0(const model_ctx* c, const double* x) {
   const orc_model* m = c->m;
   if (m->kind == 0) return gauss_logpdf_chol(m->d, x, m->m0, c->LP0);
+  if (m->kind == 3 || m->kind == 4) return normal_logpdf(x[0], 0.0, 1.0);
   double s0 = m->sigma / sqrt(1.0 - m->phi * m->phi);
   return normal_logpdf(x[0], m->mu, s0);
 }
@@ -252,8 +278,13 @@ static void prop_params(const model_ctx* c, int t, int i, double* mean, double* 
   }
 }
 
-/* log q_t(x): independent diagonal-Gaussian proposal. */
+/* log q_t(x): independent diagonal-Gaussian proposal, or the uniform one on [-s, s]^d. */
 static double log_q(const model_ctx* c, int t, const double* x) {
+  if (c->m->prop_kind == 2) {
+    for (int i = 0; i < c->m->d; ++i)
+      if (fabs(x[i]) > c->m->prop_scale) return -INFINITY;
+    return -c->m->d * log(2.0 * c->m->prop_scale);
+  }
   double s = 0.0;
   for (int i = 0; i < c->m->d; ++i) {
     double mu, sd;
@@ -269,7 +300,8 @@ static double log_q(const model_ctx* c, int t, const double* x) {
 static double log_nu(const model_ctx* c, int t, const double* x) {
   const orc_model* m = c->m;
   if (m->nu == 0) return log_q(c, t, x);
-  if (m->kind == 0) return log_h(c, t, x);
+  if (m->kind == 0 || m->kind == 3) return log_h(c, t, x);
+  if (m->kind == 4) return log_h(c, t, x) - log(2.0 * m->bound);
   return log_h(c, t, x) + log(fabs(c->y[t]));
 }
 
@@ -316,6 +348,13 @@ int orc_init(const orc_model* m, const orc_config* cf, const double* y, const do
       double* x = X + ((size_t)t * N + n) * d;
       if (cf->conditional && n == 0) {
         for (int i = 0; i < d; ++i) x[i] = x_ref[(size_t)t * d + i];
+      } else if (m->prop_kind == 2) {  /* U([-s, s]^d): x = s (2 u - 1), u23 of the words */
+        for (int j = 0; 4 * j < d; ++j) {
+          uint32_t w[4];
+          draw(cf->seed_lo, cf->seed_hi, (uint32_t)n, (uint32_t)t, ORC_PURPOSE_INIT, cf->counter_base, (uint32_t)j,
+               w);
+          for (int p = 0; p < 4 && 4 * j + p < d; ++p) x[4 * j + p] = m->prop_scale * (2.0 * u23(w[p]) - 1.0);
+        }
       } else {
         double z[32];
         draw_particle(cf, d, t, n, z);
@@ -722,13 +761,12 @@ static int combine(const model_ctx* mc, const orc_config* cf, blocks* B, int a, 
       double halfQi = 0.0;
       if (d == 1) {
         const orc_model* m = mc->m;
-        const double A = m->kind == 0 ? m->A[0] : m->phi;
-        const double cc = m->kind == 0 ? 0.0 : m->mu * (1.0 - m->phi);
         const double Q = m->kind == 0 ? m->Q[0] : m->sigma * m->sigma;
         halfQi = 0.5 / Q;
         double lo = INFINITY, hi = -INFINITY;
         for (int i = 0; i < N; ++i) {
-          const double mi = A * B->Z[(size_t)(c - 1) * N + i] + cc;
+          const double xi = B->Z[(size_t)(c - 1) * N + i];
+          const double mi = m->kind == 0 ? m->A[0] * xi : trans_mean_1d(m, xi);
           lo = mi < lo ? mi : lo;
           hi = mi > hi ? mi : hi;
         }
@@ -939,11 +977,9 @@ int orc_rs_bounds(const orc_model* m, int K, const double* y, int c, int Nl, int
   for (int i = 0; i < Nl; ++i) amax = wl[i] > amax ? wl[i] : amax;
   double lo = INFINITY, hi = -INFINITY, Q = 0.0;
   if (d == 1) {
-    const double A = m->kind == 0 ? m->A[0] : m->phi;
-    const double cf = m->kind == 0 ? 0.0 : m->mu * (1.0 - m->phi);
     Q = m->kind == 0 ? m->Q[0] : m->sigma * m->sigma;
     for (int i = 0; i < Nl; ++i) {
-      const double mi = A * xl[i] + cf;
+      const double mi = m->kind == 0 ? m->A[0] * xl[i] : trans_mean_1d(m, xl[i]);
       lo = mi < lo ? mi : lo;
       hi = mi > hi ? mi : hi;
     }
