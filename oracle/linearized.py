@@ -9,6 +9,10 @@ through temporally parallel scans).
 
   * Linear-Gaussian model: the linearisation is the model itself, so one pass gives the
     Kalman/RTS marginals.
+  * Poisson counts (Section 5.1): log h_t = y_t x - e^x is expanded in the same way.
+  * Theta-logistic (Section 5.2): the observation is linear-Gaussian and the transition mean
+    m(x) = x + tau0 - tau1 e^{tau2 x} is linearised around the previous means (the iterated
+    extended Kalman smoother the paper uses), first around y_t.
   * Stochastic volatility (y_t = exp(x_t / 2) v_t): the observation noise is not additive;
     each pass expands log h_t(y_t | x) = -x/2 - y_t^2 e^{-x} / 2 + const to second order
     around m_t, which is the Gaussian pseudo-observation z_t = m_t + g_t / lambda_t with
@@ -24,14 +28,16 @@ from . import kalman
 
 
 def kalman_rts_affine(F, c, Q, m0, P0, z, R, obs):
-    """Kalman filter and RTS smoother of x_t = F x_{t-1} + c + N(0, Q), x_0 ~ N(m0, P0),
-    z_t = x_t + N(0, R_t) observed where obs[t].  Returns (means [K][d], covariances
-    [K][d][d])."""
+    """Kalman filter and RTS smoother of x_t = F_t x_{t-1} + c_t + N(0, Q), x_0 ~ N(m0, P0),
+    z_t = x_t + N(0, R_t) observed where obs[t]; F, c are one matrix / vector for every step
+    or per-step arrays [K][d][d] / [K][d].  Returns (means [K][d], covariances [K][d][d])."""
     z = np.asarray(z, np.float64)
     K, d = z.shape
-    F = np.atleast_2d(F).astype(np.float64)
+    F = np.asarray(F, np.float64)
+    c = np.asarray(c, np.float64)
+    Ft = F.reshape(K, d, d) if F.size == K * d * d and F.ndim == 3 else np.broadcast_to(F.reshape(d, d), (K, d, d))
+    ct = c.reshape(K, d) if c.size == K * d and c.ndim == 2 else np.broadcast_to(c.reshape(d), (K, d))
     Q = np.atleast_2d(Q).astype(np.float64)
-    c = np.asarray(c, np.float64).reshape(d)
     mf = np.zeros((K, d))
     Pf = np.zeros((K, d, d))
     mp = np.zeros((K, d))
@@ -40,8 +46,8 @@ def kalman_rts_affine(F, c, Q, m0, P0, z, R, obs):
     P = np.atleast_2d(P0).astype(np.float64)
     for t in range(K):
         if t > 0:
-            m = F @ m + c
-            P = F @ P @ F.T + Q
+            m = Ft[t] @ m + ct[t]
+            P = Ft[t] @ P @ Ft[t].T + Q
         mp[t], Pp[t] = m, P
         if obs[t]:
             S = P + np.atleast_2d(R[t])
@@ -52,7 +58,7 @@ def kalman_rts_affine(F, c, Q, m0, P0, z, R, obs):
         mf[t], Pf[t] = m, P
     ms, Ps = mf.copy(), Pf.copy()
     for t in range(K - 2, -1, -1):
-        J = Pf[t] @ F.T @ np.linalg.inv(Pp[t + 1])
+        J = Pf[t] @ Ft[t + 1].T @ np.linalg.inv(Pp[t + 1])
         ms[t] = mf[t] + J @ (ms[t + 1] - mp[t + 1])
         Ps[t] = Pf[t] + J @ (Ps[t + 1] - Pp[t + 1]) @ J.T
     return ms, Ps
@@ -68,6 +74,27 @@ def sv_pseudo_observations(y, m):
     return z, 1.0 / safe, obs
 
 
+def cox_pseudo_observations(y, m):
+    """The second-order expansion of log h_t = y_t x - e^x around m_t (Poisson counts):
+    lambda_t = e^{m_t}, gradient y_t - e^{m_t}; (z, variance, observed)."""
+    y = np.asarray(y, np.float64).reshape(-1)
+    lam = np.exp(np.asarray(m, np.float64).reshape(-1))
+    return m.reshape(-1) + (y - lam) / lam, 1.0 / lam, np.ones(y.shape[0], bool)
+
+
+def theta_transitions(model, m):
+    """The theta-logistic transition into step t linearised around m_{t-1}:
+    F_t = 1 - tau1 tau2 e^{tau2 m}, c_t = m + tau0 - tau1 e^{tau2 m} - F_t m."""
+    m = np.asarray(m, np.float64).reshape(-1)
+    K = m.shape[0]
+    F = np.ones((K, 1, 1))
+    c = np.zeros((K, 1))
+    e = np.exp(model.tau2 * m[:-1])
+    F[1:, 0, 0] = 1.0 - model.tau1 * model.tau2 * e
+    c[1:, 0] = m[:-1] + model.tau0 - model.tau1 * e - F[1:, 0, 0] * m[:-1]
+    return F, c
+
+
 def linearized_smoother(model, y, iterations=1, init_mean=None):
     """Algorithm 4's Gaussian marginals: (means [K][d], standard deviations [K][d])."""
     y = np.asarray(y, np.float64)
@@ -76,10 +103,19 @@ def linearized_smoother(model, y, iterations=1, init_mean=None):
         return ms, np.sqrt(np.einsum("tii->ti", Ps))
     K = y.shape[0]
     s2 = model.sigma ** 2
+    if model.kind == 3:  # theta-logistic: linearise the transition, first around y_t
+        m = y[:, 0].copy() if init_mean is None else np.asarray(init_mean, np.float64).reshape(K)
+        for _ in range(max(1, iterations)):
+            F, c = theta_transitions(model, m)
+            ms, Ps = kalman_rts_affine(F, c, [[s2]], [0.0], [[1.0]], y, np.full((K, 1, 1), model.obs_sd ** 2),
+                                       np.ones(K, bool))
+            m = ms[:, 0]
+        return ms, np.sqrt(Ps[:, :, 0])
+    A = model.phi * (model.lam if model.kind == 2 else 1.0)
     m = np.full(K, model.mu) if init_mean is None else np.asarray(init_mean, np.float64).reshape(K)
     for _ in range(max(1, iterations)):
-        z, r, obs = sv_pseudo_observations(y, m)
-        ms, Ps = kalman_rts_affine([[model.phi]], [model.mu * (1 - model.phi)], [[s2]], [model.mu],
+        z, r, obs = (cox_pseudo_observations if model.kind == 2 else sv_pseudo_observations)(y, m)
+        ms, Ps = kalman_rts_affine([[A]], [model.mu * (1 - model.phi)], [[s2]], [model.mu],
                                    [[s2 / (1 - model.phi ** 2)]], z[:, None], r[:, None, None], obs)
         m = ms[:, 0]
     return ms, np.sqrt(Ps[:, :, 0])

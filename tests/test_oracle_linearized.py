@@ -6,6 +6,8 @@
   * For the stochastic-volatility model the iteration's fixed point is the posterior mode:
     the gradient of the log joint density (written out by hand) vanishes there, and the
     smoothed variances are the diagonal of the inverse negative Hessian at the mode.
+  * The same fixed-point property for the Poisson-count model (second-order observation
+    expansion) and the theta-logistic model (iterated extended smoother).
 """
 import numpy as np
 
@@ -107,3 +109,44 @@ def test_sv_warm_start_is_a_continuation():
     b, sb = linearized.linearized_smoother(m, y, iterations=3, init_mean=b0[:, 0])
     np.testing.assert_allclose(a, b, atol=1e-12)
     np.testing.assert_allclose(sa, sb, atol=1e-12)
+
+
+def _theta_grad(model, y, x):
+    """Gradient of the theta-logistic log joint density, written out by hand."""
+    K = x.size
+    s2, r2 = model.sigma ** 2, model.obs_sd ** 2
+    g = np.zeros(K)
+    g[0] -= x[0]
+    e = np.exp(model.tau2 * x[:-1])
+    res = x[1:] - (x[:-1] + model.tau0 - model.tau1 * e)
+    g[1:] -= res / s2
+    g[:-1] += res * (1.0 - model.tau1 * model.tau2 * e) / s2
+    g += (y - x) / r2
+    return g
+
+
+def _cox_grad(model, y, x):
+    mu, phi, lam, s2 = model.mu, model.phi, model.lam, model.sigma ** 2
+    K = x.size
+    g = np.zeros(K)
+    g[0] -= (x[0] - mu) * (1 - phi * phi) / s2
+    res = x[1:] - (mu + phi * (lam * x[:-1] - mu))
+    g[1:] -= res / s2
+    g[:-1] += res * phi * lam / s2
+    g += y - np.exp(x)
+    return g
+
+
+def test_theta_logistic_iterated_extended_smoother_converges_to_the_mode():
+    m = W.theta_logistic()
+    K = 60
+    _, y = W.simulate(m, K, 41)
+    ms, _ = linearized.linearized_smoother(m, y, iterations=40)
+    assert np.abs(_theta_grad(m, y[:, 0], ms[:, 0])).max() < 1e-8
+
+
+def test_cox_iterated_smoother_converges_to_the_mode():
+    m = W.cox(80)
+    _, y = W.simulate(m, 80, 40)
+    ms, _ = linearized.linearized_smoother(m, y, iterations=40)
+    assert np.abs(_cox_grad(m, y[:, 0], ms[:, 0])).max() < 1e-8
