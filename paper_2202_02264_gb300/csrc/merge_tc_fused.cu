@@ -16,8 +16,8 @@
 //     1] and [v, 1, 1, beta_hi, beta_lo] in the canonical K-major layout);
 //   - 1 control thread issues, for combination k + 1, one tcgen05.mma (M = N = 128) per (row
 //     tile, column block) into one of four 128-column TMEM accumulators;
-//   - 16 epilogue warps read each accumulator (tcgen05.ld; warp (g, h) lanes 32 g.. and
-//     columns 32 h..), take 2^x on MUFU and keep the tile sums in shared memory.
+//   - 8 epilogue warps read each accumulator (tcgen05.ld; warp (g, h) lanes 32 g.. and
+//     columns 64 h..), take 2^x on MUFU and keep the tile sums in shared memory.
 // So the exponentials of one combination overlap the draws and the operand build of two
 // others, and the period of a combination is the larger of the two.
 // The arithmetic is the split path's, function for function (the column and row terms of
@@ -43,9 +43,9 @@ using namespace parts;
 using namespace tc;
 
 constexpr int kFNmax = 512;                 // largest N of the fused level
-constexpr int kFEpiWarps = 16;              // warps 0..15: lane quarter warp % 4, 32 columns each
-constexpr int kFCoreWarps = 11;             // warps 16..26: operand build and draws (28 warps: 72 registers)
-constexpr int kFCtrlWarp = kFEpiWarps + kFCoreWarps;  // warp 27: TMEM and MMA issue
+constexpr int kFEpiWarps = 8;               // warps 0..7: lane quarter warp % 4, 64 columns each
+constexpr int kFCoreWarps = 11;             // warps 8..18: operand build and draws
+constexpr int kFCtrlWarp = kFEpiWarps + kFCoreWarps;  // warp 19: TMEM and MMA issue (20 warps: 96 registers)
 constexpr int kFThreads = (kFCtrlWarp + 1) * 32;
 constexpr int kFCoreThreads = kFCoreWarps * 32;
 constexpr int kFCore0 = kFEpiWarps * 32;
@@ -467,8 +467,8 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
 
   if (warp < kFEpiWarps) {
     // ------------------------------------------------------------------ epilogue
-    // warp (g, h) reads TMEM lanes 32 g .. 32 g + 31 (its rows) and columns 32 h .. 32 h + 31
-    // of each block: one 32-column tile weight per row and block
+    // warp (g, h) reads TMEM lanes 32 g .. 32 g + 31 (its rows) and columns 64 h .. 64 h + 63
+    // of each block: two 32-column tile weights per row and block
     const int g = warp & 3, h = warp >> 2;
     int blk = 0;
     bool stop = false;
@@ -486,15 +486,29 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int col0 = cb * kMmaN + 32 * h;
-          uint32_t acc32[32];
-          tmem_ld32(tb + ((uint32_t)(32 * g) << 16) + (uint32_t)acc * kMmaN + 32 * h, acc32);
+          const int col0 = cb * kMmaN + 64 * h;
+          uint32_t acc0[32], acc1[32];
+          const uint32_t taddr = tb + ((uint32_t)(32 * g) << 16) + (uint32_t)acc * kMmaN + 64 * h;
+          tmem_ld32(taddr, acc0);
+          tmem_ld32(taddr + 32, acc1);
           tmem_wait();
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(&acc_free[acc]));
-          const float t = col0 + 32 <= N ? exp_sum32<false>(acc32, 32) : exp_sum32<true>(acc32, N - col0);
-          if (row < N && col0 < N) Tq[(size_t)row * nTp + col0 / 32] = t;
+          float t0, t1;
+          if (col0 + 64 <= N) {
+            t0 = exp_sum32<false>(acc0, 32);
+            t1 = exp_sum32<false>(acc1, 32);
+          } else {
+            t0 = exp_sum32<true>(acc0, N - col0);
+            t1 = exp_sum32<true>(acc1, N - col0 - 32);
+          }
+          if (row < N) {
+            if (col0 + 32 < N)
+              *reinterpret_cast<float2*>(Tq + (size_t)row * nTp + col0 / 32) = make_float2(t0, t1);
+            else if (col0 < N)
+              Tq[(size_t)row * nTp + col0 / 32] = t0;
+          }
         }
       }
       if (stop) break;
