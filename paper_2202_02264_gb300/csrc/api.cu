@@ -34,6 +34,17 @@ struct Profile {
 };
 thread_local Profile g_prof;
 
+// An event recorded on a capturing stream joins the graph as an event-record node only with
+// cudaEventRecordExternal; without it the record is internal to the capture and the event
+// cannot be read after a replay.
+cudaError_t record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t err = cudaStreamIsCapturing(s, &cs);
+  if (err != cudaSuccess) return err;
+  if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  return cudaEventRecord(e, s);
+}
+
 cudaError_t prof_begin(cudaStream_t s) {
   if (!g_prof.on) return cudaSuccess;
   if (g_prof.used == g_prof.start.size()) {
@@ -45,13 +56,13 @@ cudaError_t prof_begin(cudaStream_t s) {
     g_prof.start.push_back(a);
     g_prof.stop.push_back(b);
   }
-  return cudaEventRecord(g_prof.start[g_prof.used], s);
+  return record(g_prof.start[g_prof.used], s);
 }
 
 cudaError_t prof_end(cudaStream_t s, double pairs) {
   if (!g_prof.on) return cudaSuccess;
   g_prof.pairs += pairs;
-  return cudaEventRecord(g_prof.stop[g_prof.used++], s);
+  return record(g_prof.stop[g_prof.used++], s);
 }
 
 void prof_count(int n) {
@@ -85,12 +96,12 @@ cudaError_t bd_begin(cudaStream_t s, int kind) {
     g_bd.kind.push_back(0);
   }
   g_bd.kind[g_bd.used] = kind;
-  return cudaEventRecord(g_bd.a[g_bd.used], s);
+  return record(g_bd.a[g_bd.used], s);
 }
 
 cudaError_t bd_end(cudaStream_t s) {
   if (!g_bd.on) return cudaSuccess;
-  return cudaEventRecord(g_bd.b[g_bd.used++], s);
+  return record(g_bd.b[g_bd.used++], s);
 }
 
 dsmc_status_t fail(dsmc_status_t st, const std::string& msg) {

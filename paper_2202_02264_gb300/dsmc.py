@@ -498,6 +498,24 @@ class Smoother:
                      if want_traj else None)
         self.x_star = torch.empty((self.K, self.d), dtype=torch.float32, device=device)
 
+    def set_model(self, model: W.SSM, prop_mean: torch.Tensor = None, prop_std: torch.Tensor = None):
+        """Swap the model parameters (same kind and dimension: the buffers stay).  With device
+        FP32 [K][d] tensors prop_mean / prop_std the proposal is DSMC_PROP_GAUSS over them, kept
+        on the device (no host round trip), e.g. dsmc_gaussian_proposals' outputs."""
+        if model.kind != self.model.kind or model.d != self.d:
+            raise ValueError("set_model keeps the model kind and dimension")
+        self.model = model
+        self.hm = HostModel(model)
+        if prop_mean is None:
+            self.prop, self._prop_keep = make_proposal(model, self.K, self.X.device)
+        else:
+            if prop_mean.shape != (self.K, self.d) or prop_std.shape != (self.K, self.d) or \
+                    prop_mean.dtype != torch.float32 or prop_std.dtype != torch.float32:
+                raise ValueError("proposal arrays must be FP32 [K][d]")
+            pm, ps = prop_mean.contiguous(), prop_std.contiguous()
+            self.prop, self._prop_keep = Proposal(W.PROP_GAUSS, 1.0, pm.data_ptr(), ps.data_ptr(), int(model.nu)), \
+                (pm, ps)
+
     @property
     def levels(self) -> int:
         L = 0
