@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -79,6 +80,19 @@ WORKLOADS = {
     # genuinely dominant pair (two low-tail particles with a near-zero observation) still
     # leaves some combinations accepting ~1e-6 of their uniform proposals, hence the cap
     "sv_rs": dict(K=4096, N=16384, resampler="rs", rs_max_attempts=1 << 26, steps=3),
+    # rejection with factorised pair proposals (I ~ e^{a_i}, J ~ e^{b'_j} e^{-dist_j^2 / 2Q})
+    # at N = 16384 under the default attempt cap
+    "sv_rsf": dict(K=4096, N=16384, resampler="rsf", steps=3),
+    # systematic resampling on the dense sampler
+    "sv_sys": dict(K=4096, N=4096, resampler="sys"),
+    # the constrained random walk of the lazy-resampling experiment (sigma = 0.4, uniform
+    # proposals on [-1, 1]): rejection with uniform and with factorised pair proposals, and
+    # systematic resampling
+    "crw_rs": dict(K=1024, N=4096, resampler="rs", steps=10),
+    "crw_rsf": dict(K=1024, N=4096, resampler="rsf", steps=10),
+    "crw_sys": dict(K=1024, N=4096, resampler="sys", steps=20),
+    # the Poisson-count model of the Cox-process experiment (stationary Gaussian proposal)
+    "cox": dict(K=1024, N=1024, resampler="dense"),
     # Algorithm 7 at N = 16384: B = 64 Metropolis-Hastings steps per slot (biased)
     "sv_mh": dict(K=4096, N=16384, resampler="mh", steps=10),
     "lgssm_d4": dict(K=512, N=512, resampler="dense"),
@@ -203,13 +217,15 @@ def run_reference(args):
         r0 = S.request_stream(1, spec["rate"])[0]
         wl = W.Workload(args.workload, r0.model, r0.K, r0.N, r0.y, None)
     else:
-        wl = W.workload(args.workload.replace("_rs", "").replace("_mh", ""), K=spec["K"], N=spec["N"])
+        wl = W.workload(re.sub(r"_(rsf|rs|mh|sys)$", "", args.workload), K=spec["K"], N=spec["N"])
     from oracle import core
     y = wl.y.astype(np.float32).astype(np.float64)
-    # the workload's own sampler (Algorithm 1, 8 or 7) and its attempt cap / step count
-    lazy = ({"resampler": spec["resampler"], "rs_max_attempts": spec.get("rs_max_attempts", 0) or
-             (64 if spec["resampler"] == "mh" else 1 << 20)}
-            if spec.get("resampler") in ("rs", "mh") else {})
+    # the workload's own sampler (Algorithm 1 multinomial or systematic, 8 or 7) and its
+    # attempt cap / step count
+    res = spec.get("resampler", "dense")
+    lazy = ({"resampler": {"sys": "systematic"}.get(res, res),
+             "rs_max_attempts": spec.get("rs_max_attempts", 0) or (64 if res == "mh" else 1 << 26)}
+            if res in ("rs", "mh", "rsf", "sys") else {})
     # calibrate K' so that each step is a bounded slice of the workload (~2-4 s)
     Kp = 2
     while True:
@@ -256,11 +272,13 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     spec = WORKLOADS[args.workload]
-    base_name = args.workload.replace("_rs", "").replace("_mh", "")
+    base_name = re.sub(r"_(rsf|rs|mh|sys)$", "", args.workload)
     wl = W.workload(base_name, K=spec["K"], N=spec["N"])
     K, N = wl.K, wl.N
-    resampler = {"rs": dsmc.RS, "mh": dsmc.MH}.get(spec["resampler"], dsmc.MULTINOMIAL)
-    if resampler != dsmc.MULTINOMIAL:
+    resampler = {"rs": dsmc.RS, "mh": dsmc.MH, "rsf": dsmc.RS_FACTORED,
+                 "sys": dsmc.SYSTEMATIC}.get(spec["resampler"], dsmc.MULTINOMIAL)
+    lazy = resampler in (dsmc.RS, dsmc.MH, dsmc.RS_FACTORED)   # no N x N pass
+    if lazy:
         args.compute = "fp32"   # the lazy samplers evaluate their proposed pairs in FP32
     compute = {"fp32": dsmc.FP32, "tf32": dsmc.TF32, "bf16": dsmc.BF16}[args.compute]
     sm = dsmc.Smoother(wl.model, K, N, seed=1000 + 7919 * rank, resampler=resampler, compute=compute,
@@ -307,6 +325,12 @@ def run_ours(args):
     if st != 0:
         raise RuntimeError(f"device status {st} after timed steps")
     value = world * args.steps * N * K / t_total
+    acceptance = None
+    if resampler in (dsmc.RS, dsmc.RS_FACTORED):   # the last timed smoothing's attempts
+        att = dsmc.dsmc_lazy_attempts(sm.cfg, sm.hm, sm.ws)
+        acceptance = {"attempts_per_smoothing": att, "slots_per_smoothing": (K - 1) * N,
+                      "rate": (K - 1) * N / att if att else None,
+                      "cap": spec.get("rs_max_attempts") or "default (2^26)"}
 
     # end to end through the C ABI with host buffers: H2D of y, smoothing, D2H of results
     y_host = torch.as_tensor(wl.y, dtype=torch.float32).pin_memory()
@@ -343,7 +367,6 @@ def run_ours(args):
     ex2_peak = MUFU_EX2_PER_CLK_SM * _sms() * sm_max * 1e6 / 1e9       # G exp / s
     achieved = rs_pairs / (rs_ms / 1e3) / 1e9 if rs_ms > 0 else None   # G exp / s
     d = wl.model.d
-    lazy = resampler != dsmc.MULTINOMIAL   # no N x N pass: prologue + per-slot proposals
     roofline = {"bound": "alu",
                 "kernel": ("lazy sampler (Algorithm 8 or 7: proposed pairs only; no N x N pass to time)"
                            if lazy else
@@ -377,6 +400,8 @@ def run_ours(args):
             "gpu_launches": launches,
             "breakdown_ms_per_step": breakdown,
             "step_ms": {"median": float(np.median(per_step)), "p99": float(np.percentile(per_step, 99))}}
+    if acceptance:
+        line["acceptance"] = acceptance
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(wl)
     if rank == 0:
@@ -692,6 +717,23 @@ def run_serving(args):
     reqs70 = [S.Request(r.rid, r.lane, r.model, r.N, r.y, r.seed, r.arrival * scale) for r in reqs]
     _, res70, makespan70, lat70 = serve(reqs70)
 
+    # plain: the same requests one after another through dsmc_smooth in FP32 (no batching,
+    # no reduced precision), host observations in and host means out, wall clock
+    plain = None
+    if not args.no_compare:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in reqs:
+            sm = dsmc.Smoother(r.model, r.K, r.N, seed=r.seed, compute=dsmc.FP32)
+            yd = torch.as_tensor(r.y, dtype=torch.float32).to("cuda", non_blocking=True)
+            sm.smooth(yd)
+            _ = sm.mean.cpu(), sm.logL_out.cpu()
+            if sm.status() != 0:
+                raise RuntimeError(f"plain request {r.rid}: device status {sm.status()}")
+        t_plain = time.perf_counter() - t0
+        plain = {"value": units / t_plain, "unit": UNIT, "makespan_s": t_plain,
+                 "form": "each request alone through dsmc_smooth, FP32 cross term, sequential"}
+
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     ex2_peak = MUFU_EX2_PER_CLK_SM * _sms() * sm_max * 1e6 / 1e9
@@ -712,6 +754,8 @@ def run_serving(args):
                                       "p99": float(np.percentile(lat70, 99)), "makespan_s": makespan70,
                                       "throughput": units / makespan70}},
             "capacity_req_per_s": capacity,
+            "plain_fp32_sequential": plain,
+            "mixed_over_plain": value / plain["value"] if plain else None,
             "peak_active_requests": srv.sched.peak_active, "peak_request_bytes": srv.sched.peak_used,
             "roofline": {"bound": "alu", "kernel": "rowsum_tc_kernel / rowsum_kernel (fused exp / tile sums)",
                          "achieved": achieved, "peak": ex2_peak, "unit": "Gexp/s",

@@ -284,10 +284,19 @@ dsmc_status_t dsmc_smooth_noalloc(const dsmc_config_t* cfg, const dsmc_model_t* 
  * log h_t(y_t | x) to second order around m_t (a Gaussian pseudo-observation with variance
  * 1 / lambda_t, lambda_t = y_t^2 e^{-m_t} / 2; none where lambda_t vanishes), starting from
  * init_mean or the stationary mean; the iterations move to the posterior mode and its
- * curvature.  The outputs are the means and the marginal standard deviations, ready for
- * DSMC_PROP_GAUSS with nu = DSMC_NU_EQ_Q (q_t = nu_t, as the paper uses them).
+ * curvature.  The Poisson-count model (Section 5.1) is expanded the same way around m_t
+ * (lambda_t = e^{m_t}, pseudo-observation m_t + (y_t - lambda_t) / lambda_t).  The
+ * theta-logistic model (Section 5.2) has a linear-Gaussian observation; its transition mean
+ * x + tau0 - tau1 e^{tau2 x} is linearised around the previous pass's mean of step t - 1
+ * (F_t = 1 - tau1 tau2 e^{tau2 m}, the iterated extended Kalman smoother), the first pass
+ * around init_mean or else the observations.  The constrained random walk (Section 5.3) has
+ * no Gaussian expansion: DSMC_ERR_UNSUPPORTED.  The outputs are the means and the marginal
+ * standard deviations, ready for DSMC_PROP_GAUSS with nu = DSMC_NU_EQ_Q (q_t = nu_t, as the
+ * paper uses them).
  *   y:          DEVICE [K][dx] FP32 observations
- *   iterations: passes for the SV model (>= 1; the linear-Gaussian model takes one)
+ *   iterations: passes of the non-linear models (>= 1; the linear-Gaussian model takes one;
+ *               the paper runs 25 for a first approximation, then one per parameter update
+ *               started from the previous means)
  *   init_mean:  DEVICE [K][dx] FP32 linearisation point of the first pass, or NULL
  *   mean_out, std_out: DEVICE [K][dx] FP32
  *   ws:         DEVICE workspace of dsmc_gaussian_proposals_workspace_size bytes; its first

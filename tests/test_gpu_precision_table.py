@@ -1,0 +1,155 @@
+"""Error of each cross-term precision (FP32, TF32, BF16) on every workload configuration,
+against the FP64 oracle and the exact smoother (through the C ABI).
+
+For each configuration -- the 1-D linear-Gaussian model (K = 32, N = 64), d = 8 (K = N =
+1024), stochastic volatility (N = 4096), the batched d = 4 family (N = 512, full-length
+sequences) and the serving lanes (d = 2, 8, 32 and SV at their N) -- and each precision:
+
+  * tile error: the largest |log tile weight - oracle log-sum-exp over the tile| (nats) of
+    the device's tile sums at the bottom level and one upper level, on sampled rows,
+    against the bound of its precision (2.05 u S ln 2 for the MMA types, S the cross-term
+    scale, plus 0.01 ln 2 and 1e-4 relative for every precision);
+  * mean error: the RMSE of the smoothing means against Kalman/RTS (linear-Gaussian) or the
+    grid smoother (SV) over R seeds, its standard error, and the paired difference from the
+    FP32 form with its standard error (the same seeds).
+
+The table is printed and, when a gpurun_out directory exists at the repository root,
+written there as precision_table.md.  The assertions: every tile error within its bound and
+every reduced precision's mean RMSE within 4 paired standard errors of FP32's (equal error).
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import dev, levels
+from oracle import core, grid, kalman
+from paper_2202_02264_gb300 import dsmc, serving, workloads as W
+from test_gpu_tensor_core_oracle import check_tiles_against_oracle
+
+pytestmark = pytest.mark.gpu
+
+PREC = {"fp32": dsmc.FP32, "tf32": dsmc.TF32, "bf16": dsmc.BF16}
+ROWS = []
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2202_02264_gb300 import build
+    build.build()
+    dsmc.load()
+    yield
+    _write_table()
+
+
+def _write_table():
+    if not ROWS:
+        return
+    lines = ["| configuration | precision | tile log-error (nats) | bound | mean RMSE vs exact (± SE) | "
+             "RMSE - FP32 (± paired SE) |", "|---|---|---|---|---|---|"]
+    for r in ROWS:
+        lines.append(f"| {r['cfg']} | {r['prec']} | {r['tile_err']:.2e} | {r['tile_tol']:.2e} | "
+                     f"{r['rmse']:.4f} ± {r['rmse_se']:.4f} | {r['diff']:+.4f} ± {r['diff_se']:.4f} |")
+    text = "\n".join(lines)
+    print("\n" + text)
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, "precision_table.md"), "w") as f:
+            f.write(text + "\n")
+
+
+def _exact_means(m, y):
+    if m.kind == W.SV:
+        yy = y[:, 0].astype(np.float32).astype(np.float64)
+        gm, _, _ = grid.model_grid_smoother(m, yy, n_grid=1201)
+        return gm[:, None]
+    ms, _, _ = kalman.rts_for(m, y.astype(np.float32).astype(np.float64))
+    return ms
+
+
+def _tile_error(wl, K, N, compute, seed=5):
+    """Worst tile error over the bottom level and the middle level (one combination each)."""
+    sm = dsmc.Smoother(wl.model, K, N, seed=seed, compute=compute, fused_max_merges=-1)
+    y = dev(wl.y[:K])
+    sm.init(y)
+    L = levels(K)
+    probe = sorted({0, L // 2})
+    worst, tol = 0.0, np.inf
+    sub = W.Workload(wl.name, wl.model, K, N, wl.y[:K], None)
+    for level in range(max(probe) + 1):
+        sm.merge_level(y, level)
+        if level in probe:
+            torch.cuda.synchronize()
+            M = core.merges_at_level(K, level)
+            rows = None if N <= 512 else np.random.default_rng(level).choice(N, 256, replace=False)
+            err, t, _ = check_tiles_against_oracle(sub, sm, level, M - 1, compute, rows)
+            worst, tol = max(worst, err), min(tol, t)
+    assert sm.status() == 0
+    return worst, tol
+
+
+def _mean_rmse(m, ys, N, compute, R, Ks=None):
+    """Per-seed RMSE (over all sequences, t and k) of the means against the exact smoother."""
+    Ks = Ks or [y.shape[0] for y in ys]
+    exact = [_exact_means(m, y) for y in ys]
+    b = dsmc.BatchSmoother(m, Ks, N, seeds=[0] * len(Ks), compute=compute, fused_max_merges=-1,
+                           max_merges_per_launch=16384)
+    b.set_inputs([dev(y) for y in ys])
+    out = []
+    for r in range(R):
+        b.seeds = [1000 + 13 * r + k for k in range(len(Ks))]
+        b.smooth()
+        se = sum(float(((b.mean[k].cpu().numpy() - exact[k]) ** 2).sum()) for k in range(len(Ks)))
+        out.append(np.sqrt(se / sum(e.size for e in exact)))
+    assert b.status() == 0
+    return np.array(out)
+
+
+def _configs():
+    bw = W.batch_workload(256, 512)
+    longest = [int(i) for i in np.argsort(bw.Ks)[::-1][:2]]
+    lanes = serving.lane_models()
+    return [
+        ("1: LG d=1, K=32, N=64", lambda: (W.workload("lgssm_1d"), 32, 64, 32, 64)),
+        ("2: LG d=8, K=N=1024", lambda: (W.workload("lgssm_d8"), 1024, 1024, 64, 16)),
+        ("3: SV, K=512, N=4096", lambda: (W.workload("sv", K=512, N=4096), 512, 4096, 64, 16)),
+        ("4: batch LG d=4, 2 longest seqs, N=512",
+         lambda: (W.Workload("batch", bw.model, int(bw.Ks[longest[0]]), 512, bw.ys[longest[0]], None),
+                  int(bw.Ks[longest[0]]), 512, 64, 16, [bw.ys[s] for s in longest])),
+        ("5: serving LG d=2, N=256", lambda: (_lane(lanes["lg2"], 512, 256), 512, 256, 64, 16)),
+        ("5: serving LG d=8, N=1024", lambda: (_lane(lanes["lg8"], 512, 1024), 512, 1024, 64, 16)),
+        ("5: serving LG d=32, N=4096", lambda: (_lane(lanes["lg32"], 256, 4096), 256, 4096, 32, 8)),
+        ("5: serving SV, N=1024", lambda: (_lane(lanes["sv"], 512, 1024), 512, 1024, 64, 16)),
+    ]
+
+
+def _lane(m, K, N):
+    _, y = W.simulate(m, K, 50000 + K + N)
+    return W.Workload("lane", m, K, N, y, None)
+
+
+@pytest.mark.parametrize("idx", range(8))
+def test_precision_row(idx):
+    name, make = _configs()[idx]
+    spec = make()
+    wl, K, N, K_tile, R = spec[:5]
+    ys = spec[5] if len(spec) > 5 else [wl.y]
+    base = None
+    for prec, compute in PREC.items():
+        if compute == dsmc.TF32 and wl.model.d > 16:
+            continue   # TF32 cross term: dx <= 16
+        err, tol = _tile_error(wl, min(K_tile, K), N, compute)
+        rm = _mean_rmse(wl.model, ys, N, compute, R)
+        if base is None:
+            base = rm
+        diff = rm - base
+        row = {"cfg": name, "prec": prec, "tile_err": err, "tile_tol": tol, "rmse": rm.mean(),
+               "rmse_se": rm.std(ddof=1) / np.sqrt(R), "diff": diff.mean(),
+               "diff_se": diff.std(ddof=1) / np.sqrt(R) if prec != "fp32" else 0.0}
+        ROWS.append(row)
+        assert err < tol, (name, prec, err, tol)
+        if prec != "fp32":
+            assert abs(row["diff"]) <= 4 * row["diff_se"] + 1e-12, (name, prec, row)

@@ -75,7 +75,7 @@ def check_tiles_against_oracle(wl, sm, level, m_idx, compute, rows=None):
     big = t > 1e-6 * t.max(axis=1, keepdims=True)
     got = sh + np.log(np.where(big, t, 1.0))
     err = np.abs(got - ref_t)[big]
-    tol = LN2 * (2.05 * TC_UNIT[compute] * cross_scale(wl.model, xl, xr) + 0.01) + 1e-4 * max(1.0, np.abs(ref_t).max())
+    tol = LN2 * (2.05 * TC_UNIT.get(compute, 0.0) * cross_scale(wl.model, xl, xr) + 0.01) + 1e-4 * max(1.0, np.abs(ref_t).max())
     return float(err.max()), float(tol), dbg
 
 
