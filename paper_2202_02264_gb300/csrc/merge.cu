@@ -553,7 +553,8 @@ __host__ __device__ __forceinline__ CdfSlotsSmem cdf_slots_smem(int N, int nTp) 
   return f;
 }
 
-template <int D>
+// SMALL: nT <= 16 tiles of 32 columns (N <= 512), only the draw paths of that shape compiled.
+template <int D, bool SMALL>
 __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_kernel(MergeArgs a) {
   constexpr int NT = kCdfSlotThreads;
   constexpr int NW = NT / 32;
@@ -703,7 +704,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
   const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
   for (int n = n_lo + threadIdx.x; n < n_hi; n += NT) {
     int i, j;
-    draw_pair<D, true>(in, cb.seed, cb.base, gid, n, i, j);
+    draw_pair<D, true, SMALL>(in, cb.seed, cb.base, gid, n, i, j);
     o.put(n, i, j);
   }
 }
@@ -1069,10 +1070,16 @@ template <int D>
 cudaError_t sample_dense_t(const MergeArgs& a, cudaStream_t st) {
   const size_t smem_cs = cdf_slots_smem<D>(a.N, a.nTp).total;
   if (smem_cs <= 200 * 1024) {  // one CTA per combination: row CDF and draws
-    cudaError_t e = cudaFuncSetAttribute(cdf_slots_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_cs);
+    const bool small = a.nT <= 16 && a.B == 32;
+    cudaError_t e = small ? cudaFuncSetAttribute(cdf_slots_kernel<D, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cs)
+                          : cudaFuncSetAttribute(cdf_slots_kernel<D, false>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cs);
     if (e != cudaSuccess) return e;
-    cdf_slots_kernel<D><<<a.mc, kCdfSlotThreads, smem_cs, st>>>(a);
+    if (small)
+      cdf_slots_kernel<D, true><<<a.mc, kCdfSlotThreads, smem_cs, st>>>(a);
+    else
+      cdf_slots_kernel<D, false><<<a.mc, kCdfSlotThreads, smem_cs, st>>>(a);
     return cudaGetLastError();
   }
   const size_t smem = (size_t)a.N * (sizeof(unsigned long long) + sizeof(float));

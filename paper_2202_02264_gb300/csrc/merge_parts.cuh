@@ -532,7 +532,9 @@ __device__ __forceinline__ int pick_tile64(const float* Ti, int nT, uint32_t w, 
 // row and tile targets inside their chosen entries, so that every slot sits at its own
 // position of the flattened fixed-point CDF, S / N apart.
 // The tiles are held in registers when nT <= 32, the columns when the tile has <= 32.
-template <int D, bool PAD>
+// SMALL: the caller guarantees nT <= 16 and tiles of <= 32 columns (N <= 512 at B = 32),
+// and only those paths are compiled (the same decisions as the general form).
+template <int D, bool PAD, bool SMALL = false>
 __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint32_t base, int gid, int n,
                                           int& i, int& j) {
   const int N = in.N, B = in.B, nT = in.nT, nTp = in.nTp;
@@ -570,7 +572,7 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
   }
   const float* Ti = in.T + (size_t)i * nTp;
   int kt;
-  if (nT <= 16) {
+  if (SMALL || nT <= 16) {
     kt = pick_tile<16>(Ti, nT, w2, wr);
   } else if (nT <= 32) {
     kt = pick_tile<32>(Ti, nT, w2, wr);
@@ -599,7 +601,7 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
       e[q] = ex2(pair_exponent<D>(u, al, v, bt[q]));
     }
     j = jb + pick32(e, 32, w3, tbe);
-  } else if (ncol <= 32) {
+  } else if (SMALL || ncol <= 32) {
     float e[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) {

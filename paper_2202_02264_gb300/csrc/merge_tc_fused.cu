@@ -43,9 +43,15 @@ using namespace parts;
 using namespace tc;
 
 constexpr int kFNmax = 512;                 // largest N of the fused level
-constexpr int kFEpiWarps = 8;               // warps 0..7: lane quarter warp % 4, 64 columns each
-constexpr int kFCoreWarps = 11;             // warps 8..18: operand build and draws
-constexpr int kFCtrlWarp = kFEpiWarps + kFCoreWarps;  // warp 19: TMEM and MMA issue (20 warps: 96 registers)
+#ifndef DSMC_FUSED_EPI_WARPS
+#define DSMC_FUSED_EPI_WARPS 8
+#endif
+constexpr int kFEpiWarps = DSMC_FUSED_EPI_WARPS;  // lane quarter warp % 4, kFEpiCols columns each
+static_assert(kFEpiWarps == 4 || kFEpiWarps == 8, "4 or 8 epilogue warps");
+constexpr int kFEpiCols = 4 * 128 / kFEpiWarps;   // columns of a block per epilogue warp (64 or 128)
+// operand build and draws: the rest of 20 warps (at most 5 per scheduler: 96 registers)
+constexpr int kFCoreWarps = 19 - kFEpiWarps;
+constexpr int kFCtrlWarp = kFEpiWarps + kFCoreWarps;  // TMEM and MMA issue
 constexpr int kFThreads = (kFCtrlWarp + 1) * 32;
 constexpr int kFCoreThreads = kFCoreWarps * 32;
 constexpr int kFCore0 = kFEpiWarps * 32;
@@ -79,9 +85,19 @@ struct Stage {
   static constexpr size_t bytes = rnd(fL + (size_t)kFNmax * 4, 1024);
 };
 
+// The inputs of the next operand build (its two particle slices and the leaf weights or
+// index maps beside them), brought in by bulk copies while the previous combination draws.
+struct Inputs {
+  static constexpr size_t xc = 0;                          // X_c      [N][d] FP32
+  static constexpr size_t xl = xc + (size_t)kFNmax * 4 * 4;  // X_{c-1}  [N][d] FP32
+  static constexpr size_t r0 = xl + (size_t)kFNmax * 4 * 4;  // log w_c or first map [N]
+  static constexpr size_t l0 = r0 + (size_t)kFNmax * 4;      // log w_{c-1} or last map [N]
+  static constexpr size_t bytes = l0 + (size_t)kFNmax * 4;
+};
+
 template <int D>
 __host__ __device__ constexpr size_t fused_tc_smem() {
-  return 2 * Stage<D>::bytes + 1024;  // two stages, 1 KB of alignment slack
+  return 2 * Stage<D>::bytes + Inputs::bytes + 1024;  // two stages, the inputs, alignment slack
 }
 
 __device__ __forceinline__ void bar_sync(int id, int n) {
@@ -90,6 +106,17 @@ __device__ __forceinline__ void bar_sync(int id, int n) {
 
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Named barrier over n threads that also ANDs a predicate across them.
+__device__ __forceinline__ bool bar_and(int id, int n, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
 }
 
 // n 32-bit words from global to shared memory by a group of nt threads (vector loads when
@@ -107,56 +134,68 @@ __device__ __forceinline__ void stage_group(T* dst, const T* src, int n, int tid
   }
 }
 
-// Exact u64 inclusive scan of v[0..N) in shared memory by the core warps (named barrier).
-__device__ __forceinline__ void group_scan_u64(unsigned long long* v, int N, unsigned long long* warp_tot,
-                                               int tid) {
-  constexpr int NT = kFCoreThreads;
-  const int per = (N + NT - 1) / NT;
-  const int lo = min(tid * per, N), hi = min(lo + per, N);
-  unsigned long long run = 0;
-  for (int i = lo; i < hi; ++i) run += v[i];
-  const int lane = tid & 31, w = tid >> 5;
-  unsigned long long incl = run;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) warp_tot[w] = incl;
-  bar_sync(kBarCore, NT);
-  if (tid == 0) {
-    unsigned long long acc = 0;
-    for (int k = 0; k < NT / 32; ++k) {
-      const unsigned long long t = warp_tot[k];
-      warp_tot[k] = acc;
-      acc += t;
-    }
-  }
-  bar_sync(kBarCore, NT);
-  unsigned long long pre = warp_tot[w] + incl - run;
-  for (int i = lo; i < hi; ++i) {
-    pre += v[i];
-    v[i] = pre;
-  }
-  bar_sync(kBarCore, NT);
-}
-
 // Shared scratch of the core warps.
 struct CoreScratch {
   float gsum[kMaxColumnGroups * 4];
   float red[kFCoreWarps];
   float mu[4];
   float bstar;
-  unsigned long long warp_tot[kFCoreWarps];
   int n_under, nonfinite, ok;
+  int in_bulk;    // the next build's inputs come by bulk copy (1) or are staged by it (0)
+  int in_pend;    // bulk copies issued and not yet waited for
+  int in_phase;   // completed phases of the inputs barrier
 };
+
+// Global sources of combination s's build inputs.
+struct InputSrc {
+  const float *xc, *xl;
+  const void *r0, *l0;
+  uint32_t bx, bw;  // bytes of a slice, of a weight / map row
+};
+
+__device__ __forceinline__ InputSrc input_src(const MergeArgs& a, int s) {
+  const Comb cb = comb_of(a, s);
+  const int N = a.N, d = a.d, c = cb.c, sR = cb.b - cb.c + 1;
+  InputSrc r;
+  r.xc = cb.X + (size_t)c * N * d;
+  r.xl = cb.X + (size_t)(c - 1) * N * d;
+  r.r0 = sR == 1 ? static_cast<const void*>(cb.logw + (size_t)c * N)
+                 : static_cast<const void*>(cb.first + ((size_t)(ceil_log2(sR) & 1) * cb.K + c) * N);
+  r.l0 = cb.level == 0 ? static_cast<const void*>(cb.logw + (size_t)(c - 1) * N)
+                       : static_cast<const void*>(cb.last + ((size_t)(cb.level & 1) * cb.K + cb.at) * N);
+  r.bx = (uint32_t)(N * d * 4);
+  r.bw = (uint32_t)(N * 4);
+  return r;
+}
+
+// One thread: the bulk copies of combination s's inputs into `inb`, completing on `bar`,
+// when every source and size is 16-byte aligned (true when N is a multiple of 4 and d
+// divides evenly); otherwise nothing is issued and the build stages them itself.
+__device__ __forceinline__ bool issue_inputs(const MergeArgs& a, int s, unsigned char* inb, uint32_t bar) {
+  const InputSrc r = input_src(a, s);
+  const uintptr_t al = reinterpret_cast<uintptr_t>(r.xc) | reinterpret_cast<uintptr_t>(r.xl) |
+                       reinterpret_cast<uintptr_t>(r.r0) | reinterpret_cast<uintptr_t>(r.l0) | r.bx | r.bw;
+  if ((al & 15) != 0) return false;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2 * r.bx + 2 * r.bw)
+               : "memory");
+  const void* src[4] = {r.xc, r.xl, r.r0, r.l0};
+  const size_t off[4] = {Inputs::xc, Inputs::xl, Inputs::r0, Inputs::l0};
+  const uint32_t len[4] = {r.bx, r.bx, r.bw, r.bw};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(inb + off[q])),
+                 "l"(src[q]), "r"(len[q]), "r"(bar)
+                 : "memory");
+  return true;
+}
 
 // Operand build of combination s into stage st (the core warps): the two particle slices and
 // index maps staged with vector loads, the column pass (states, b'_j, mu, B*, v_j, beta_j),
 // the row pass (u_i, alpha_i, the row shift), FP32 copies for the draws and the MMA rows.
 template <int D, int KIND>
 __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<D>& mp, unsigned char* st, int s,
-                                          int ct, int cw, int lane, int RT, CoreScratch& sc) {
+                                          unsigned char* inb, int ct, int cw, int lane, int RT, CoreScratch& sc) {
   using L = Stage<D>;
   const int N = a.N, d = a.d;
   unsigned char* opU = st + L::opU;
@@ -173,22 +212,23 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
   const int sR = b - c + 1;
   const bool right_leaf = (sR == 1);
   const int bufL = cb.level & 1, bufR = ceil_log2(sR) & 1;
-  // the inputs staged in this stage's tile-sum area (written by the epilogue only after
-  // these operands have been consumed)
-  float* sXc = reinterpret_cast<float*>(st + L::T);
-  float* sXl = sXc + rnd((size_t)N * d, 4);
-  float* sR0 = sXl + rnd((size_t)N * d, 4);
-  float* sL0 = sR0 + rnd((size_t)N, 4);
-  stage_group(sXc, cb.X + (size_t)c * N * d, N * d, ct, kFCoreThreads);
-  stage_group(sXl, cb.X + (size_t)(c - 1) * N * d, N * d, ct, kFCoreThreads);
-  if (right_leaf)
-    stage_group(sR0, cb.logw + (size_t)c * N, N, ct, kFCoreThreads);
-  else
-    stage_group(reinterpret_cast<int32_t*>(sR0), cb.first + ((size_t)bufR * K + c) * N, N, ct, kFCoreThreads);
-  if (left_leaf)
-    stage_group(sL0, cb.logw + (size_t)(c - 1) * N, N, ct, kFCoreThreads);
-  else
-    stage_group(reinterpret_cast<int32_t*>(sL0), cb.last + ((size_t)bufL * K + at) * N, N, ct, kFCoreThreads);
+  // the inputs: bulk-copied beforehand, or staged here with vector loads
+  float* sXc = reinterpret_cast<float*>(inb + Inputs::xc);
+  float* sXl = reinterpret_cast<float*>(inb + Inputs::xl);
+  float* sR0 = reinterpret_cast<float*>(inb + Inputs::r0);
+  float* sL0 = reinterpret_cast<float*>(inb + Inputs::l0);
+  if (!sc.in_bulk) {
+    stage_group(sXc, cb.X + (size_t)c * N * d, N * d, ct, kFCoreThreads);
+    stage_group(sXl, cb.X + (size_t)(c - 1) * N * d, N * d, ct, kFCoreThreads);
+    if (right_leaf)
+      stage_group(sR0, cb.logw + (size_t)c * N, N, ct, kFCoreThreads);
+    else
+      stage_group(reinterpret_cast<int32_t*>(sR0), cb.first + ((size_t)bufR * K + c) * N, N, ct, kFCoreThreads);
+    if (left_leaf)
+      stage_group(sL0, cb.logw + (size_t)(c - 1) * N, N, ct, kFCoreThreads);
+    else
+      stage_group(reinterpret_cast<int32_t*>(sL0), cb.last + ((size_t)bufL * K + at) * N, N, ct, kFCoreThreads);
+  }
   const int32_t* firstR = right_leaf ? nullptr : reinterpret_cast<const int32_t*>(sR0);
   const float* lwc = right_leaf ? sR0 : nullptr;
   const int32_t* lastL = left_leaf ? nullptr : reinterpret_cast<const int32_t*>(sL0);
@@ -333,62 +373,98 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
   float* fL = reinterpret_cast<float*>(st + L::fL);
   int* under = reinterpret_cast<int*>(cum);  // rows that underflowed (before cum is built)
   const Comb cb = comb_of(a, s);
-  if (ct == 0) {
-    sc.n_under = 0;
-    sc.nonfinite = 0;
-  }
-  bar_sync(kBarCore, kFCoreThreads);
-  // row totals: the tile weights in ascending order (the split path's definition)
+  // (sc.n_under and sc.nonfinite are zero here: cleared before the first draw and at the end
+  // of every draw)
+  // row totals (the tile weights in ascending order, the split path's definition) and the
+  // rows' base-2 log weights; rows whose total underflows are recomputed below
+  float mloc = -INFINITY;
   for (int i = ct; i < N; i += kFCoreThreads) {
     float t = row_total(Tq + (size_t)i * nTp, nT, nTp);
     if (isnan(t)) {
       sc.nonfinite = 1;
       t = 0.f;
     }
-    fL[i] = t;
-    if (t < 0x1p-64f) under[atomicAdd(&sc.n_under, 1)] = i;
-  }
-  bar_sync(kBarCore, kFCoreThreads);
-  for (int uq = cw; uq < sc.n_under; uq += kFCoreWarps) {  // rare: exact-max recomputation
-    const int i = under[uq];
-    float si, dl;
-    recompute_row<D, true>(fU + (size_t)i * D, fAl[i], fV, fB, N, a.B, nT, Tq + (size_t)i * nTp, &si, &dl);
-    __syncwarp();
-    if (lane == 0) {
-      si = row_total(Tq + (size_t)i * nTp, nT, nTp);
-      fL[i] = isnan(si) ? 0.f : si;
-      fDl[i] = dl;
+    if (t < 0x1p-64f) {
+      under[atomicAdd(&sc.n_under, 1)] = i;
+    } else {
+      if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = t;
+      const float v = row_log2_weight(fSh[i], fDl[i], t);
+      fL[i] = v;
+      mloc = fmaxf(mloc, v);
     }
-  }
-  bar_sync(kBarCore, kFCoreThreads);
-  // row weights r_i = 2^(l_i - max l) and their exact fixed-point prefix sums
-  float mloc = -INFINITY;
-  for (int i = ct; i < N; i += kFCoreThreads) {
-    const float t = fL[i];
-    if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = t;
-    const float v = row_log2_weight(fSh[i], fDl[i], t);
-    fL[i] = v;
-    mloc = fmaxf(mloc, v);
   }
   mloc = warp_max(mloc);
   if (lane == 0) sc.red[cw] = mloc;
   bar_sync(kBarCore, kFCoreThreads);
+  if (sc.n_under > 0) {  // rare: exact-max recomputation, then the maximum again
+    for (int uq = cw; uq < sc.n_under; uq += kFCoreWarps) {
+      const int i = under[uq];
+      float si, dl;
+      recompute_row<D, true>(fU + (size_t)i * D, fAl[i], fV, fB, N, a.B, nT, Tq + (size_t)i * nTp, &si, &dl);
+      __syncwarp();
+      if (lane == 0) {
+        si = row_total(Tq + (size_t)i * nTp, nT, nTp);
+        si = isnan(si) ? 0.f : si;
+        if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = si;
+        fDl[i] = dl;
+        fL[i] = row_log2_weight(fSh[i], dl, si);
+      }
+    }
+    bar_sync(kBarCore, kFCoreThreads);
+    mloc = -INFINITY;
+    for (int i = ct; i < N; i += kFCoreThreads) mloc = fmaxf(mloc, fL[i]);
+    mloc = warp_max(mloc);
+    if (lane == 0) sc.red[cw] = mloc;
+    bar_sync(kBarCore, kFCoreThreads);
+  }
   float M = sc.red[0];
   for (int w = 1; w < kFCoreWarps; ++w) M = fmaxf(M, sc.red[w]);
   const bool degenerate = !(M > -INFINITY) || isnan(M);
+  // row weights r_i = 2^(l_i - M) as exact 2^40 fixed-point images
   for (int i = ct; i < N; i += kFCoreThreads) {
     const float r = row_weight(fL[i], M, degenerate);
     if (a.inspect) a.ws.rw[(size_t)s * N + i] = r;
     cum[i] = (unsigned long long)__float2ull_rz(r * 0x1p40f);
   }
   bar_sync(kBarCore, kFCoreThreads);
-  group_scan_u64(cum, N, sc.warp_tot, ct);
-  if (ct == 0) {
-    const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(cum[N - 1]);
-    cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
-    if (degenerate || cum[N - 1] == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
-    if (sc.nonfinite) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+  // their inclusive prefix sums by one warp (integer: exact in any order), then the
+  // increment of Eq. (Lab): the N <= 512 values as 16 rows of 32 (element 32 c + lane), one
+  // shuffle scan per row (independent, so they overlap) and the rows' totals carried in
+  // registers; every shared-memory access is one conflict-free row
+  if (cw == 0) {
+    constexpr int R = kFNmax / 32;
+    const int C = (N + 31) / 32;
+    unsigned long long v[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      const int i = 32 * c + lane;
+      v[c] = (c < C && i < N) ? cum[i] : 0ull;
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+      for (int c = 0; c < R; ++c) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, v[c], o);
+        if (lane >= o) v[c] += t;
+      }
+    }
+    unsigned long long carry = 0;
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      const unsigned long long row = __shfl_sync(0xffffffffu, v[c], 31);
+      const int i = 32 * c + lane;
+      if (c < C && i < N) cum[i] = carry + v[c];
+      carry += row;
+    }
+    const unsigned long long S = carry;
+    if (lane == 0) {
+      const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(S);
+      cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
+      if (degenerate || S == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
+      if (sc.nonfinite) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+    }
   }
+  bar_sync(kBarCore, kFCoreThreads);
   if (a.inspect) {
     for (int i = ct; i < N; i += kFCoreThreads) {
       a.ws.cum[(size_t)s * N + i] = cum[i];
@@ -415,8 +491,12 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
   const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
   for (int n = n_lo + ct; n < n_hi; n += kFCoreThreads) {
     int i, j;
-    draw_pair<D, true>(in, cb.seed, cb.base, cb.gid, n, i, j);
+    draw_pair<D, true, true>(in, cb.seed, cb.base, cb.gid, n, i, j);
     o.put(n, i, j);
+  }
+  if (ct == 0) {
+    sc.n_under = 0;
+    sc.nonfinite = 0;
   }
   bar_sync(kBarCore, kFCoreThreads);
 }
@@ -428,7 +508,7 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
   unsigned char* fsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(fsm_raw) + 1023) & ~(uintptr_t)1023);
   // ops_full: a stage's operands are built; tiles_full: its tile sums are complete;
   // acc_full / acc_free: a TMEM accumulator holds a block / has been read out
-  __shared__ __align__(8) uint64_t ops_full[2], tiles_full[2], acc_full[kFAcc], acc_free[kFAcc];
+  __shared__ __align__(8) uint64_t ops_full[2], tiles_full[2], acc_full[kFAcc], acc_free[kFAcc], in_full;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_s;
   __shared__ CoreScratch sc;
@@ -452,6 +532,7 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
       mbar_init(smem_u32(&acc_full[q]), 1);
       mbar_init(smem_u32(&acc_free[q]), kFEpiWarps);
     }
+    mbar_init(smem_u32(&in_full), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -467,8 +548,8 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
 
   if (warp < kFEpiWarps) {
     // ------------------------------------------------------------------ epilogue
-    // warp (g, h) reads TMEM lanes 32 g .. 32 g + 31 (its rows) and columns 64 h .. 64 h + 63
-    // of each block: two 32-column tile weights per row and block
+    // warp (g, h) reads TMEM lanes 32 g .. 32 g + 31 (its rows) and columns kFEpiCols h ..
+    // of each block, 64 at a time: two 32-column tile weights per row and 64 columns
     const int g = warp & 3, h = warp >> 2;
     int blk = 0;
     bool stop = false;
@@ -486,28 +567,34 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int col0 = cb * kMmaN + 64 * h;
-          uint32_t acc0[32], acc1[32];
-          const uint32_t taddr = tb + ((uint32_t)(32 * g) << 16) + (uint32_t)acc * kMmaN + 64 * h;
-          tmem_ld32(taddr, acc0);
-          tmem_ld32(taddr + 32, acc1);
-          tmem_wait();
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(&acc_free[acc]));
-          float t0, t1;
-          if (col0 + 64 <= N) {
-            t0 = exp_sum32<false>(acc0, 32);
-            t1 = exp_sum32<false>(acc1, 32);
-          } else {
-            t0 = exp_sum32<true>(acc0, N - col0);
-            t1 = exp_sum32<true>(acc1, N - col0 - 32);
-          }
-          if (row < N) {
-            if (col0 + 32 < N)
-              *reinterpret_cast<float2*>(Tq + (size_t)row * nTp + col0 / 32) = make_float2(t0, t1);
-            else if (col0 < N)
-              Tq[(size_t)row * nTp + col0 / 32] = t0;
+#pragma unroll
+          for (int part = 0; part < kFEpiCols / 64; ++part) {
+            const int col0 = cb * kMmaN + kFEpiCols * h + 64 * part;
+            uint32_t acc0[32], acc1[32];
+            const uint32_t taddr =
+                tb + ((uint32_t)(32 * g) << 16) + (uint32_t)acc * kMmaN + (uint32_t)(kFEpiCols * h + 64 * part);
+            tmem_ld32(taddr, acc0);
+            tmem_ld32(taddr + 32, acc1);
+            tmem_wait();
+            if (part == kFEpiCols / 64 - 1) {
+              asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+              __syncwarp();
+              if (lane == 0) mbar_arrive(smem_u32(&acc_free[acc]));
+            }
+            float t0, t1;
+            if (col0 + 64 <= N) {
+              t0 = exp_sum32<false>(acc0, 32);
+              t1 = exp_sum32<false>(acc1, 32);
+            } else {
+              t0 = exp_sum32<true>(acc0, N - col0);
+              t1 = exp_sum32<true>(acc1, N - col0 - 32);
+            }
+            if (row < N) {
+              if (col0 + 32 < N)
+                *reinterpret_cast<float2*>(Tq + (size_t)row * nTp + col0 / 32) = make_float2(t0, t1);
+              else if (col0 < N)
+                Tq[(size_t)row * nTp + col0 / 32] = t0;
+            }
           }
         }
       }
@@ -520,27 +607,65 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
     // loads of combinations 0 and 1, then for every k: the draws of k (once its tile sums
     // are complete) and the load of k + 2 into the stage k has just released
     const int ct = threadIdx.x - kFCore0, cw = ct >> 5;
-    for (int k = 0; k < ncomb && k < 2; ++k) {
-      core_load<D, KIND>(a, mp, fsm + (size_t)k * L::bytes, blockIdx.x + k * gridDim.x, ct, cw, lane, RT, sc);
+    unsigned char* inb = fsm + 2 * L::bytes;
+    const uint32_t in_bar = smem_u32(&in_full);
+    auto comb = [&](int k) { return (int)blockIdx.x + k * (int)gridDim.x; };
+    // one thread starts the inputs of combination k (the buffer is free: the previous build
+    // has read it, and its closing fence orders those reads before the bulk copies)
+    auto issue = [&](int k) {
+      if (ct == 0) sc.in_bulk = sc.in_pend = issue_inputs(a, comb(k), inb, in_bar) ? 1 : 0;
+    };
+    // every core thread waits for bulk-copied inputs; false on an abort or a timeout
+    auto inputs_ready = [&]() -> bool {
+      bar_sync(kBarCore, kFCoreThreads);  // sc.in_bulk is visible
+      bool ok = true;
+      if (sc.in_bulk) ok = mbar_wait_or_abort(in_bar, (uint32_t)sc.in_phase & 1, abort_v);
+      ok = bar_and(kBarCore, kFCoreThreads, ok);
+      if (ct == 0 && sc.in_bulk && ok) {
+        ++sc.in_phase;
+        sc.in_pend = 0;
+      }
+      return ok;
+    };
+    bool ok = true;
+    if (ct == 0) sc.in_phase = sc.in_pend = sc.in_bulk = sc.n_under = sc.nonfinite = 0;
+    if (ncomb > 0) issue(0);
+    for (int k = 0; k < ncomb && k < 2 && ok; ++k) {
+      ok = inputs_ready();
+      if (!ok) break;
+      core_load<D, KIND>(a, mp, fsm + (size_t)k * L::bytes, comb(k), inb, ct, cw, lane, RT, sc);
+      if (k + 1 < ncomb) issue(k + 1);
       if (ct == 0) mbar_arrive(smem_u32(&ops_full[k]));
     }
-    for (int k = 0; k < ncomb; ++k) {
+    for (int k = 0; k < ncomb && ok; ++k) {
       const int q = k & 1;
       if (ct == 0) sc.ok = mbar_wait_or_abort(smem_u32(&tiles_full[q]), (uint32_t)(k >> 1) & 1, abort_v);
       bar_sync(kBarCore, kFCoreThreads);
       if (!sc.ok) {
-        if (ct == 0) raise_abort();
+        ok = false;
         break;
       }
-      core_draw<D>(a, fsm + (size_t)q * L::bytes, blockIdx.x + k * gridDim.x, ct, cw, lane, sc);
+      core_draw<D>(a, fsm + (size_t)q * L::bytes, comb(k), ct, cw, lane, sc);
       if (k + 2 < ncomb) {
-        core_load<D, KIND>(a, mp, fsm + (size_t)q * L::bytes, blockIdx.x + (k + 2) * gridDim.x, ct, cw, lane, RT,
-                           sc);
+        ok = inputs_ready();
+        if (!ok) break;
+        core_load<D, KIND>(a, mp, fsm + (size_t)q * L::bytes, comb(k + 2), inb, ct, cw, lane, RT, sc);
+        if (k + 3 < ncomb) issue(k + 3);
         if (ct == 0) mbar_arrive(smem_u32(&ops_full[q]));
+      }
+    }
+    if (!ok) {
+      bar_sync(kBarCore, kFCoreThreads);
+      if (ct == 0) {
+        raise_abort();
+        // bulk copies still in flight land before the CTA leaves (bounded)
+        if (sc.in_pend) mbar_wait(in_bar, (uint32_t)sc.in_phase & 1);
       }
     }
   } else if (lane == 0) {
     // ------------------------------------------------------------------ control: MMA issue
+    // one MMA per (row tile, column block) of each combination once its operands are built,
+    // into the accumulator the epilogue has released (four accumulators in flight)
     int blk = 0, issued = 0;
     bool ok = true;
     for (int k = 0; k < ncomb && ok; ++k) {

@@ -6,11 +6,14 @@
 // Garcia-Fernandez, "Temporal parallelization of Bayesian smoothers", 2021): both passes are
 // prefix scans of an associative operator over per-step elements, so a pass over K steps has
 // ceil(log2 K) levels.  For the linear-Gaussian model the linearisation is the model itself
-// (one iteration is exact).  For the stochastic-volatility model, whose observation noise is
-// not additive, log h_t(y_t | x) is expanded to second order around the current mean m_t,
-// which is a Gaussian pseudo-observation z_t = m_t + g_t / lambda_t with variance
-// 1 / lambda_t (g_t, lambda_t the first and negated second derivatives; no observation where
-// lambda_t vanishes); iterating moves the marginals to the posterior mode and its curvature.
+// (one iteration is exact).  For the stochastic-volatility and Poisson-count models, whose
+// observations are not additive Gaussian, log h_t(y_t | x) is expanded to second order
+// around the current mean m_t, which is a Gaussian pseudo-observation z_t = m_t + g_t /
+// lambda_t with variance 1 / lambda_t (g_t, lambda_t the first and negated second
+// derivatives; no observation where lambda_t vanishes); iterating moves the marginals to the
+// posterior mode and its curvature.  For the theta-logistic model the observation is
+// linear-Gaussian and the transition mean is linearised around the previous pass's mean of
+// step t - 1 (per-step F_t, c_t: the iterated extended smoother).
 //
 // Every quantity is FP64 (the work is O(K d^3 log K), small next to the smoother itself).
 // Filtering element of step t (observation matrix I, transition x_t = F x_{t-1} + c + N(0, Q),
