@@ -373,6 +373,12 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
   float* fL = reinterpret_cast<float*>(st + L::fL);
   int* under = reinterpret_cast<int*>(cum);  // rows that underflowed (before cum is built)
   const Comb cb = comb_of(a, s);
+  // the output maps' sources, copied in the background into the operand area (free: every
+  // MMA of this stage has completed) while the row CDF is built
+  SlotOut o = slot_out(a, cb, ct == 0);
+  int32_t* sMF = reinterpret_cast<int32_t*>(st + L::opU);
+  int32_t* sML = sMF + kFNmax;
+  prefetch_maps(o, sMF, sML, ct, kFCoreThreads);
   // (sc.n_under and sc.nonfinite are zero here: cleared before the first draw and at the end
   // of every draw)
   // row totals (the tile weights in ascending order, the split path's definition) and the
@@ -473,7 +479,9 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
     }
   }
   // the pairs, each in three exact inverse-CDF stages, and the new block's index maps
-  const SlotOut o = slot_out(a, cb, ct == 0);
+  cp_async_wait_all();
+  bar_sync(kBarCore, kFCoreThreads);
+  map_in_smem(o, sMF, sML);
   DrawIn in;
   in.sys = (a.resampler == DSMC_SYSTEMATIC && !cb.conditional) ? 1 : 0;
   in.cum = cum;

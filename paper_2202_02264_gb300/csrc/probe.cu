@@ -1,5 +1,5 @@
 // probe.cu -- arithmetic unit rates of the device (MUFU ex2, FP32 FFMA, packed FFMA2,
-// FADD), measured with CUDA events on the caller's stream.  The fused exponential kernels
+// FADD, FP64 DFMA), measured with CUDA events on the caller's stream.  The fused exponential kernels
 // are bound by these units, not by HBM, so their roofline denominators come from here
 // (results per clock per SM) and the device's clock.
 #include <cuda_runtime.h>
@@ -14,16 +14,19 @@ __device__ __forceinline__ float ex2_unit(float x) {
   return y;
 }
 
-// Eight independent dependency chains per thread; MODE 0 ex2, 1 FFMA, 2 FFMA2, 3 FADD.
+// Eight independent dependency chains per thread; MODE 0 ex2, 1 FFMA, 2 FFMA2, 3 FADD,
+// 4 DFMA.
 // The sink store never happens for these inputs; it keeps the chains alive.
 template <int MODE>
 __global__ void unit_rate_kernel(float* sink, int iters) {
   float a[8];
   float2 b[8];
+  double c[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     a[k] = -1.0f - 0.001f * (float)(threadIdx.x + k);
     b[k] = make_float2(a[k], 0.5f * a[k]);
+    c[k] = (double)a[k];
   }
   const float2 m2 = make_float2(0.999f, 0.998f), c2 = make_float2(1e-3f, 2e-3f);
   for (int it = 0; it < iters; ++it) {
@@ -32,12 +35,13 @@ __global__ void unit_rate_kernel(float* sink, int iters) {
       if (MODE == 0) a[k] = ex2_unit(-a[k]);
       else if (MODE == 1) a[k] = fmaf(a[k], 0.999f, 1e-3f);
       else if (MODE == 2) b[k] = __ffma2_rn(b[k], m2, c2);
-      else a[k] = a[k] + 1e-3f;
+      else if (MODE == 3) a[k] = a[k] + 1e-3f;
+      else c[k] = fma(c[k], 0.999, 1e-3);
     }
   }
   float s = 0.f;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) s += a[k] + b[k].x + b[k].y;
+  for (int k = 0; k < 8; ++k) s += a[k] + b[k].x + b[k].y + (float)c[k];
   if (s == 123.456f) sink[0] = s;
 }
 
@@ -72,7 +76,7 @@ cudaError_t time_mode(float* sink, int sms, cudaStream_t st, double* ops_per_s) 
 
 }  // namespace
 
-extern "C" dsmc_status_t dsmc_profile_unit_rates(float* sink, double ops_per_s[4], void* stream) {
+extern "C" dsmc_status_t dsmc_profile_unit_rates(float* sink, double ops_per_s[5], void* stream) {
   if (!sink || !ops_per_s) return DSMC_ERR_INVALID_ARG;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return DSMC_ERR_CUDA;
@@ -82,5 +86,6 @@ extern "C" dsmc_status_t dsmc_profile_unit_rates(float* sink, double ops_per_s[4
   if (time_mode<1>(sink, sms, st, &ops_per_s[1]) != cudaSuccess) return DSMC_ERR_CUDA;
   if (time_mode<2>(sink, sms, st, &ops_per_s[2]) != cudaSuccess) return DSMC_ERR_CUDA;
   if (time_mode<3>(sink, sms, st, &ops_per_s[3]) != cudaSuccess) return DSMC_ERR_CUDA;
+  if (time_mode<4>(sink, sms, st, &ops_per_s[4]) != cudaSuccess) return DSMC_ERR_CUDA;
   return DSMC_OK;
 }

@@ -435,15 +435,15 @@ def dsmc_profile_breakdown_read() -> dict:
     return {KINDS[k]: {"ms": ms[k], "launches": int(n[k])} for k in range(8) if n[k] > 0}
 
 
-UNIT_NAMES = ["ex2", "ffma", "ffma2_lanes", "fadd"]
+UNIT_NAMES = ["ex2", "ffma", "ffma2_lanes", "fadd", "dfma"]
 
 
 def dsmc_profile_unit_rates(stream=None) -> dict:
-    """Results per second of the device's MUFU ex2, FFMA, FFMA2 (lanes) and FADD units."""
+    """Results per second of the device's MUFU ex2, FFMA, FFMA2 (lanes), FADD and DFMA units."""
     sink = torch.zeros((1,), dtype=torch.float32, device="cuda")
-    out = (C.c_double * 4)()
+    out = (C.c_double * len(UNIT_NAMES))()
     _check(load().dsmc_profile_unit_rates(_ptr(sink), out, _stream(stream)), "dsmc_profile_unit_rates")
-    return {UNIT_NAMES[k]: out[k] for k in range(4)}
+    return {UNIT_NAMES[k]: out[k] for k in range(len(UNIT_NAMES))}
 
 
 def dsmc_seq_maps_bytes(K: int, N: int) -> int:
