@@ -9,11 +9,13 @@
 //   - 11 core warps alternate, for k = 0, 1, ...: the draws of combination k (the row
 //     totals, the row weights and their exact 2^40 fixed-point prefix sums, the increment of
 //     Eq. (Lab), every slot's pair in three exact inverse-CDF stages and the new block's
-//     index maps), then the operand build of combination k + 2 into the stage k released
-//     (the two particle slices and index maps staged with vector loads, the column pass --
-//     states, b'_j, mu, B*, v_j, beta_j -- and the row pass -- u_i, alpha_i, the row shift --
-//     as FP32 copies for the draws and as the BF16 / TF32 MMA rows [u, alpha_hi, alpha_lo, 1,
-//     1] and [v, 1, 1, beta_hi, beta_lo] in the canonical K-major layout);
+//     index maps, whose source maps arrive by cp.async meanwhile), then the operand build of
+//     combination k + 2 into the stage k released (its inputs -- two particle slices and
+//     two leaf-weight or index-map rows -- brought into their own buffer by bulk copies
+//     issued one combination ahead; the column pass -- states, b'_j, mu, B*, v_j, beta_j --
+//     and the row pass -- u_i, alpha_i, the row shift -- as FP32 copies for the draws and as
+//     the BF16 / TF32 MMA rows [u, alpha_hi, alpha_lo, 1, 1] and [v, 1, 1, beta_hi, beta_lo]
+//     in the canonical K-major layout);
 //   - 1 control thread issues, for combination k + 1, one tcgen05.mma (M = N = 128) per (row
 //     tile, column block) into one of four 128-column TMEM accumulators;
 //   - 8 epilogue warps read each accumulator (tcgen05.ld; warp (g, h) lanes 32 g.. and
@@ -27,8 +29,8 @@
 //
 // Every wait is bounded and abort-aware: a role whose wait runs out records
 // DSMC_ERR_TIMEOUT and raises the CTA's abort flag; the other roles stop at their next wait,
-// the control thread waits (bounded) for its last committed MMA, and the CTA frees its
-// tensor memory and returns.
+// the core warps wait (bounded) for their bulk copies in flight, the control thread for its
+// last committed MMA, and the CTA frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -140,6 +142,7 @@ struct CoreScratch {
   float red[kFCoreWarps];
   float mu[4];
   float bstar;
+  unsigned long long S;  // exact total of the row weights' fixed-point images
   int n_under, nonfinite, ok;
   int in_bulk;    // the next build's inputs come by bulk copy (1) or are staged by it (0)
   int in_pend;    // bulk copies issued and not yet waited for
@@ -462,13 +465,7 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
       if (c < C && i < N) cum[i] = carry + v[c];
       carry += row;
     }
-    const unsigned long long S = carry;
-    if (lane == 0) {
-      const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(S);
-      cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
-      if (degenerate || S == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
-      if (sc.nonfinite) record_status(a.ws.status, DSMC_ERR_NONFINITE);
-    }
+    if (lane == 0) sc.S = carry;  // the total; the increment is taken after the draws
   }
   bar_sync(kBarCore, kFCoreThreads);
   if (a.inspect) {
@@ -502,11 +499,20 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
     draw_pair<D, true, true>(in, cb.seed, cb.base, cb.gid, n, i, j);
     o.put(n, i, j);
   }
+  // the increment of Eq. (Lab) and log L of the new block, by the last thread (one slot at
+  // most at N <= 512, so its global read-modify-write overlaps the others' second slots)
+  if (ct == kFCoreThreads - 1) {
+    const unsigned long long S = sc.S;
+    const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(S);
+    cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
+    if (degenerate || S == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
+    if (sc.nonfinite) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+  }
+  bar_sync(kBarCore, kFCoreThreads);
   if (ct == 0) {
     sc.n_under = 0;
     sc.nonfinite = 0;
   }
-  bar_sync(kBarCore, kFCoreThreads);
 }
 
 template <int D, int KIND>
