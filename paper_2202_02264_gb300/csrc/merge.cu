@@ -624,8 +624,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
       float4* dst = reinterpret_cast<float4*>(sT + (size_t)i * L.nTs);
       for (int k4 = 0; k4 < nTp / 4; ++k4) dst[k4] = src[k4];
     }
-    // the row total: the tensor-core epilogue's two half sums when it covered the whole row
-    // in one chunk, else the tile weights in ascending order
+    // the row total: the tile weights in ascending order (every path's definition)
     float t = sT ? row_total(sT + (size_t)i * L.nTs, nT, nTp) : row_total(Tt + (size_t)i * nTp, nT, nTp);
     if (isnan(t)) {
       nonfinite_s = 1;
