@@ -447,15 +447,15 @@ def run_batched(args):
     if args.schedule:
         v = [int(x) for x in args.schedule.split(",")]
         tuned = {"fused_max_merges": v[0], "max_merges_per_launch": v[1], "tc_fused": v[2] if len(v) > 2 else 0,
-                 "timings": {}}
+                 "tile_cols": v[3] if len(v) > 3 else 0, "timings": {}}
     elif args.no_autotune:
-        tuned = {"fused_max_merges": 0, "max_merges_per_launch": 0, "tc_fused": 0, "timings": {}}
+        tuned = {"fused_max_merges": 0, "max_merges_per_launch": 0, "tc_fused": 0, "tile_cols": 0, "timings": {}}
     else:
         tuned = autotune.tune_batch(model, Ks, N, bw.ys, compute, use_cache=False)   # untimed
     b = dsmc.BatchSmoother(model, Ks, N, seeds=seeds, compute=compute,
                            fused_max_merges=tuned["fused_max_merges"],
                            max_merges_per_launch=tuned["max_merges_per_launch"],
-                           tc_fused=tuned["tc_fused"])
+                           tc_fused=tuned["tc_fused"], tile_cols=tuned.get("tile_cols", 0))
     ys = [torch.as_tensor(y, dtype=torch.float32, device=dev) for y in bw.ys]
     b.set_inputs(ys)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -579,6 +579,7 @@ def run_batched(args):
                        "autotuned": {"fused_max_merges": tuned["fused_max_merges"],
                                      "max_merges_per_launch": tuned["max_merges_per_launch"],
                                      "tc_fused": tuned["tc_fused"],
+                                     "tile_cols": tuned.get("tile_cols", 0),
                                      "candidates_ms": tuned["timings"]}},
             "plain_fp32_per_request": ({"value": plain_value, "unit": UNIT,
                                         "ms_per_batch": 1e3 * t_plain,
@@ -931,7 +932,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: default launch schedule")
     ap.add_argument("--no-graph", action="store_true", help="batched workload: time direct launches, not a graph")
     ap.add_argument("--schedule", default=None,
-                    help="batched workload: fixed 'fused_max_merges,max_merges_per_launch' instead of the autotuner")
+                    help="batched workload: fixed 'fused_max_merges,max_merges_per_launch[,tc_fused[,tile_cols]]' "
+                         "instead of the autotuner")
     ap.add_argument("--fused-max-merges", type=int, default=None,
                     help="single-sequence workloads: levels with at most this many combinations run "
                          "fused (-1: never; default: the library's)")

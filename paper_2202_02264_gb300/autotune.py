@@ -9,13 +9,16 @@ Three knobs shape how a batch's levels are launched:
     launch count);
   * ``tc_fused`` (tensor-core precisions, N <= 512, d <= 4): the other levels run either as
     one persistent warp-specialised kernel per chunk (operand rows, tcgen05 cross term,
-    exponentials, row CDF and draws of a combination on one SM) or as the split kernels.
-None changes what is computed for a given choice of path: the chunk size and ``tc_fused``
-never change a result, and the fused small levels and the split path are bit-identical with
-the FP32 cross term (with a tensor-core cross term the fused small levels differ by that
-precision's rounding).
+    exponentials, row CDF and draws of a combination on one SM) or as the split kernels;
+  * ``tile_cols`` (the tile shape of the row tile sums: 32 or 64 columns per tile, at most 64
+    tiles per row; the fused tensor-core kernel takes 32): fewer, wider tiles halve the tile sums written
+    and read, and double the columns the draws recompute.
+The chunk size and ``tc_fused`` never change a result, and the fused small levels and the
+split path are bit-identical with the FP32 cross term (with a tensor-core cross term the
+fused small levels differ by that precision's rounding).  The tile width changes the
+sampler's random streams per stage (the same law, other draws), not the weights.
 
-``tune_batch`` times every candidate pair on the device for one batch shape (two timed
+``tune_batch`` times every candidate on the device for one batch shape (two timed
 runs each, after one warm-up) and returns the fastest; results are cached per shape in
 ``~/.cache/dsmc_gb300/autotune.json`` (the cache is optional: a read-only home only skips
 it)."""
@@ -33,6 +36,7 @@ from . import workloads as W
 FUSED_CANDIDATES = (-1, 8, 32, 128)
 CHUNK_CANDIDATES = (1024, 4096, 16384)
 TC_FUSED_CANDIDATES = (-1, 1)
+TILE_CANDIDATES = (32, 64)
 
 
 def tc_fused_eligible(model: W.SSM, N: int, compute: int) -> bool:
@@ -70,47 +74,65 @@ def _store_cache(cache: dict):
         pass
 
 
+def candidates(model: W.SSM, N: int, compute: int, fused=FUSED_CANDIDATES, chunks=CHUNK_CANDIDATES,
+               tc=TC_FUSED_CANDIDATES, tiles=TILE_CANDIDATES):
+    """The (fused_max_merges, max_merges_per_launch, tc_fused, tile_cols) schedules searched
+    for this shape: the fused tensor-core kernel where eligible (32-column tiles only), the
+    64-column tiles where they give at most 64 tiles per row."""
+    tcs = tuple(tc) if tc_fused_eligible(model, N, compute) else (-1,)
+    out = []
+    for tcf in tcs:
+        for tile in tiles:
+            if tile != 32 and (tcf > 0 or (N + tile - 1) // tile > 64):
+                continue
+            if tile == 32 and (N + 31) // 32 > 64:
+                continue
+            for fm in fused:
+                for mc in chunks:
+                    out.append((fm, mc, tcf, tile))
+    return out
+
+
 def tune_batch(model: W.SSM, Ks, N: int, ys, compute: int, use_cache: bool = True,
-               fused=FUSED_CANDIDATES, chunks=CHUNK_CANDIDATES, tc=TC_FUSED_CANDIDATES) -> dict:
-    """The fastest (fused_max_merges, max_merges_per_launch, tc_fused) for this batch shape,
-    with the timings of every candidate (ms per batched smoothing)."""
+               fused=FUSED_CANDIDATES, chunks=CHUNK_CANDIDATES, tc=TC_FUSED_CANDIDATES,
+               tiles=TILE_CANDIDATES) -> dict:
+    """The fastest (fused_max_merges, max_merges_per_launch, tc_fused, tile_cols) for this
+    batch shape, with the timings of every candidate (ms per batched smoothing)."""
     import torch
 
     from . import dsmc
     dev_name = torch.cuda.get_device_name()
-    key = shape_key(model, Ks, N, compute, dev_name) + "|tc"
-    tcs = tuple(tc) if tc_fused_eligible(model, N, compute) else (-1,)
+    key = shape_key(model, Ks, N, compute, dev_name) + "|tc|tile"
+    cands = candidates(model, N, compute, fused, chunks, tc, tiles)
     cache = _load_cache() if use_cache else {}
     if key in cache:
         return cache[key]
     timings = {}
     best = None
     yd = [torch.as_tensor(np.asarray(y, np.float32), device="cuda") for y in ys]
-    for tcf in tcs:
-        for fm in fused:
-            for mc in chunks:
-                b = dsmc.BatchSmoother(model, Ks, N, compute=compute, fused_max_merges=fm,
-                                       max_merges_per_launch=mc, tc_fused=tcf)
-                b.set_inputs(yd)
-                b.prepare()
-                b.run()
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(2):
-                    b.run()
-                e1.record()
-                torch.cuda.synchronize()
-                if b.status() != 0:
-                    raise RuntimeError(f"autotune candidate ({fm}, {mc}, {tcf}): device status {b.status()}")
-                ms = e0.elapsed_time(e1) / 2
-                timings[f"{fm},{mc},{tcf}"] = ms
-                if best is None or ms < best[3]:
-                    best = (fm, mc, tcf, ms)
-                del b
-                torch.cuda.empty_cache()
-    out = {"fused_max_merges": best[0], "max_merges_per_launch": best[1], "tc_fused": best[2], "ms": best[3],
-           "timings": timings}
+    for fm, mc, tcf, tile in cands:
+        b = dsmc.BatchSmoother(model, Ks, N, compute=compute, fused_max_merges=fm,
+                               max_merges_per_launch=mc, tc_fused=tcf, tile_cols=tile)
+        b.set_inputs(yd)
+        b.prepare()
+        b.run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(2):
+            b.run()
+        e1.record()
+        torch.cuda.synchronize()
+        if b.status() != 0:
+            raise RuntimeError(f"autotune candidate ({fm}, {mc}, {tcf}, {tile}): device status {b.status()}")
+        ms = e0.elapsed_time(e1) / 2
+        timings[f"{fm},{mc},{tcf},{tile}"] = ms
+        if best is None or ms < best[4]:
+            best = (fm, mc, tcf, tile, ms)
+        del b
+        torch.cuda.empty_cache()
+    out = {"fused_max_merges": best[0], "max_merges_per_launch": best[1], "tc_fused": best[2],
+           "tile_cols": best[3], "ms": best[4], "timings": timings}
     if use_cache:
         cache[key] = out
         _store_cache(cache)

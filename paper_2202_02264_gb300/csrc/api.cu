@@ -206,7 +206,7 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p, int
   }
   const int nT0 = std::min((p.N + 31) / 32, 64);
   const int per = (p.N + nT0 - 1) / nT0;
-  p.B = 32 * ((per + 31) / 32);
+  p.B = cfg->tile_cols > 0 ? cfg->tile_cols : 32 * ((per + 31) / 32);
   p.nT = (p.N + p.B - 1) / p.B;
   p.nTp = (p.nT + 3) / 4 * 4;
   const int M0 = std::max(1, M0_batch >= 0 ? M0_batch : merges_at_level(p.K, 0));
@@ -431,6 +431,11 @@ dsmc_status_t check_config(const dsmc_config_t* cfg, const dsmc_model_t* model) 
   if (cfg->compute != DSMC_FP32 && dense && cfg->N > 4096)
     return fail(DSMC_ERR_UNSUPPORTED, "the tensor-core cross term supports N <= 4096");
   if (cfg->counter_base >= (1u << 28)) return fail(DSMC_ERR_INVALID_ARG, "counter_base must be < 2^28");
+  if (cfg->tile_cols != 0) {
+    if (cfg->tile_cols != 32 && cfg->tile_cols != 64) return fail(DSMC_ERR_INVALID_ARG, "tile_cols must be 0, 32 or 64");
+    if ((cfg->N + cfg->tile_cols - 1) / cfg->tile_cols > 64)
+      return fail(DSMC_ERR_UNSUPPORTED, "tile_cols gives more than 64 tiles per row at this N");
+  }
   if (model->dx < 1 || model->dx > kMaxDim) return fail(DSMC_ERR_UNSUPPORTED, "dx must be in 1..32");
   if (model->kind == DSMC_MODEL_SV || model->kind == DSMC_MODEL_COX) {
     if (model->dx != 1) return fail(DSMC_ERR_INVALID_ARG, "the SV and COX models have dx = 1");
@@ -657,7 +662,7 @@ dsmc_status_t launch_combs(const Plan& p, const dsmc_config_t* cfg, const ParamB
         continue;
       }
     }
-    if (p.dense && cfg->tc_fused > 0 && fused_tc_supported(p.D, p.N, p.compute, p.planes)) {
+    if (p.dense && cfg->tc_fused > 0 && p.B == 32 && fused_tc_supported(p.D, p.N, p.compute, p.planes)) {
       DSMC_CUDA(prof_begin(s), "profile event");
       DSMC_CUDA(bd_begin(s, DSMC_KIND_FUSED_TC), "profile event");
       DSMC_CUDA(launch_merge_tc_fused(p.D, a, mp.bytes, s), "fused tensor-core level kernel");

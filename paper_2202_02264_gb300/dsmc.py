@@ -57,7 +57,7 @@ class Config(C.Structure):
     _fields_ = [("K", C.c_int), ("N", C.c_int), ("compute", C.c_int), ("resampler", C.c_int),
                 ("seed", C.c_uint64), ("counter_base", C.c_uint32),
                 ("rs_max_attempts", C.c_uint32), ("max_merges_per_launch", C.c_int),
-                ("fused_max_merges", C.c_int), ("tc_fused", C.c_int)]
+                ("fused_max_merges", C.c_int), ("tc_fused", C.c_int), ("tile_cols", C.c_int)]
 
 
 class State(C.Structure):
@@ -198,10 +198,11 @@ class HostModel:
 
 
 def make_config(K, N, seed, counter_base=0, resampler=MULTINOMIAL, compute=FP32,
-                rs_max_attempts=0, max_merges_per_launch=0, fused_max_merges=0, tc_fused=0) -> Config:
+                rs_max_attempts=0, max_merges_per_launch=0, fused_max_merges=0, tc_fused=0,
+                tile_cols=0) -> Config:
     return Config(int(K), int(N), int(compute), int(resampler), int(seed) & (2**64 - 1),
                   int(counter_base), int(rs_max_attempts), int(max_merges_per_launch),
-                  int(fused_max_merges), int(tc_fused))
+                  int(fused_max_merges), int(tc_fused), int(tile_cols))
 
 
 def make_proposal(m: W.SSM, K: int, device="cuda"):
@@ -472,14 +473,15 @@ class Smoother:
 
     def __init__(self, model: W.SSM, K: int, N: int, seed: int = 0, resampler: int = MULTINOMIAL,
                  compute: int = FP32, rs_max_attempts: int = 0, max_merges_per_launch: int = 0,
-                 device: str = "cuda", want_traj: bool = False, fused_max_merges: int = 0, tc_fused: int = 0):
+                 device: str = "cuda", want_traj: bool = False, fused_max_merges: int = 0, tc_fused: int = 0,
+                 tile_cols: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("dSMC needs a CUDA device; there is no CPU path")
         self.model = model
         self.hm = HostModel(model)
         self.K, self.N, self.d = int(K), int(N), model.d
         self.cfg = make_config(K, N, seed, 0, resampler, compute, rs_max_attempts, max_merges_per_launch,
-                               fused_max_merges, tc_fused)
+                               fused_max_merges, tc_fused, tile_cols)
         self.prop, self._prop_keep = make_proposal(model, K, device)
         sizes = dsmc_state_sizes(self.cfg, self.hm)
         self.X = torch.empty((self.K, self.N, self.d), dtype=torch.float32, device=device)
@@ -559,7 +561,7 @@ class BatchSmoother:
 
     def __init__(self, model: W.SSM, Ks, N: int, seeds=None, resampler: int = MULTINOMIAL,
                  compute: int = FP32, max_merges_per_launch: int = 0, fused_max_merges: int = 0,
-                 device: str = "cuda", want_m2: bool = False, tc_fused: int = 0):
+                 device: str = "cuda", want_m2: bool = False, tc_fused: int = 0, tile_cols: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("dSMC needs a CUDA device; there is no CPU path")
         self.model = model
@@ -570,7 +572,7 @@ class BatchSmoother:
         self.seeds = list(seeds) if seeds is not None else [1000 + i for i in range(n)]
         self.counter_base = [0] * n
         self.cfg = make_config(max(self.Ks), N, 0, 0, resampler, compute, 0, max_merges_per_launch,
-                               fused_max_merges, tc_fused)
+                               fused_max_merges, tc_fused, tile_cols)
         if model.prop_kind == W.PROP_GAUSS:
             self.prop = Proposal(W.PROP_GAUSS, 1.0, None, None, int(model.nu))
         else:

@@ -106,3 +106,16 @@ def test_status_strings(lib):
     lib.dsmc_status_string.restype = C.c_char_p
     for code in [0, 1, 2, 3, 5, 6, 7, 8, 9, 10]:
         assert lib.dsmc_status_string(code)
+
+
+def test_tile_cols_is_validated(lib):
+    dsmc, W, _ = _structs()
+    hm = dsmc.HostModel(W.lgssm_d4())
+    ok = dsmc.make_config(8, 512, 1, tile_cols=64)
+    assert dsmc.dsmc_workspace_size(ok, hm) > 0
+    for bad, code in (((8, 512, 48), 1), ((8, 8192, 64), 2), ((8, 4096, 32), 2)):
+        K, N, t = bad
+        c = dsmc.make_config(K, N, 1, tile_cols=t)
+        with pytest.raises(dsmc.DsmcError) as e:
+            dsmc.dsmc_workspace_size(c, hm)
+        assert e.value.code == code

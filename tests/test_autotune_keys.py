@@ -24,3 +24,16 @@ def test_cache_roundtrip(tmp_path, monkeypatch):
 def test_candidates_cover_never_fused_and_the_default():
     assert -1 in A.FUSED_CANDIDATES and 32 in A.FUSED_CANDIDATES
     assert 1024 in A.CHUNK_CANDIDATES
+
+
+def test_candidates_search_the_tile_width_and_keep_the_fused_kernel_at_32():
+    m = W.lgssm_d4()
+    c = A.candidates(m, 512, 2)
+    tiles = {t for *_, t in c}
+    assert tiles == {32, 64}
+    assert all(t == 32 for _, _, tcf, t in c if tcf > 0)        # the fused kernel takes 32
+    assert any(tcf > 0 for _, _, tcf, _ in c)                   # eligible: BF16, N <= 512, d <= 4
+    assert len(c) == len(set(c))
+    # FP32 cross term: no fused tensor-core candidates; N = 4096: only the wider tiles
+    assert all(tcf < 0 for _, _, tcf, _ in A.candidates(m, 512, 0))
+    assert {t for *_, t in A.candidates(m, 4096, 2)} == {64}
