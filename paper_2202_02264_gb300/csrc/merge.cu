@@ -521,7 +521,7 @@ constexpr int kCdfSlotThreads = 256;
 // threads per SM: more combinations in flight beat staging T at larger N).
 constexpr size_t kCdfStageMax = 56 * 1024;
 struct CdfSlotsSmem {
-  size_t v, u, b, l, c, ad, m, t, total;
+  size_t v, u, b, l, c, ad, t, total;
   int nTs;  // staged row stride of T, 0 when T stays in global memory
 };
 
@@ -540,7 +540,6 @@ __host__ __device__ __forceinline__ CdfSlotsSmem cdf_slots_smem(int N, int nTp) 
   f.l = o; o = r16(o + (size_t)N * 4);
   f.c = o; o = r16(o + (size_t)N * 8);
   f.ad = o; o = r16(o + (size_t)N * 8);   // alpha_i and delta_i (row offsets of the draws)
-  f.m = o; o = r16(o + (size_t)N * 8);    // the new block's source maps (two int32 rows)
   f.t = o;
   const int nTs = staged_tile_stride(nTp);
   const size_t with_t = r16(o + (size_t)N * nTs * 4);
@@ -574,12 +573,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
   unsigned long long* sC = reinterpret_cast<unsigned long long*>(smraw + L.c);
   float* sAl = reinterpret_cast<float*>(smraw + L.ad);
   float* sDl = sAl + N;
-  int32_t* sMF = reinterpret_cast<int32_t*>(smraw + L.m);
-  int32_t* sML = sMF + N;
   int* under = reinterpret_cast<int*>(sC);
-  // the output maps' sources, copied in the background while the row CDF is built
-  SlotOut o = slot_out(a, cb, threadIdx.x == 0);
-  prefetch_maps(o, sMF, sML, threadIdx.x, kCdfSlotThreads);
   __shared__ unsigned long long warp_tot[NW];
   __shared__ float redf[NW];
   __shared__ float M_s;
@@ -691,9 +685,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
     if (nonfinite_s) record_status(a.ws.status, DSMC_ERR_NONFINITE);
   }
   // pair draws
-  cp_async_wait_all();
-  __syncthreads();
-  map_in_smem(o, sMF, sML);
+  const SlotOut o = slot_out(a, cb, threadIdx.x == 0);
   DrawIn in;
   in.sys = (a.resampler == DSMC_SYSTEMATIC && !cb.conditional) ? 1 : 0;
   in.cum = sC;

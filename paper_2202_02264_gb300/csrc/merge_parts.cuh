@@ -717,30 +717,5 @@ __device__ __forceinline__ SlotOut slot_out(const MergeArgs& a, const Comb& cb, 
   return o;
 }
 
-// The new block's source maps -- the left block's first map and the right block's last map,
-// read once per slot by SlotOut::put -- copied into shared memory by asynchronous copies
-// (cp.async, 4 bytes each: any alignment) from the threads tid = 0, nt, ...; the caller waits
-// (cp_async_wait_all), synchronises, then points the SlotOut at sF / sLm (map_in_smem).
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
-__device__ __forceinline__ void prefetch_maps(const SlotOut& o, int32_t* sF, int32_t* sLm, int tid, int nt) {
-  if (!o.left_leaf)
-    for (int q = tid; q < o.N; q += nt) cp_async4(sF + q, o.first_L + q);
-  if (!o.right_leaf)
-    for (int q = tid; q < o.N; q += nt) cp_async4(sLm + q, o.last_R + q);
-}
-
-__device__ __forceinline__ void map_in_smem(SlotOut& o, const int32_t* sF, const int32_t* sLm) {
-  if (!o.left_leaf) o.first_L = sF;
-  if (!o.right_leaf) o.last_R = sLm;
-}
-
 }  // namespace parts
 }  // namespace dsmc

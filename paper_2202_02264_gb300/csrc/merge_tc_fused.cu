@@ -9,13 +9,12 @@
 //   - 11 core warps alternate, for k = 0, 1, ...: the draws of combination k (the row
 //     totals, the row weights and their exact 2^40 fixed-point prefix sums, the increment of
 //     Eq. (Lab), every slot's pair in three exact inverse-CDF stages and the new block's
-//     index maps, whose source maps arrive by cp.async meanwhile), then the operand build of
-//     combination k + 2 into the stage k released (its inputs -- two particle slices and
-//     two leaf-weight or index-map rows -- brought into their own buffer by bulk copies
-//     issued one combination ahead; the column pass -- states, b'_j, mu, B*, v_j, beta_j --
-//     and the row pass -- u_i, alpha_i, the row shift -- as FP32 copies for the draws and as
-//     the BF16 / TF32 MMA rows [u, alpha_hi, alpha_lo, 1, 1] and [v, 1, 1, beta_hi, beta_lo]
-//     in the canonical K-major layout);
+//     index maps), then the operand build of combination k + 2 into the stage k released
+//     (its inputs -- two particle slices and two leaf-weight or index-map rows -- brought
+//     into their own buffer by bulk copies issued one combination ahead; the column pass --
+//     states, b'_j, mu, B*, v_j, beta_j -- and the row pass -- u_i, alpha_i, the row shift --
+//     as FP32 copies for the draws and as the BF16 / TF32 MMA rows [u, alpha_hi, alpha_lo, 1,
+//     1] and [v, 1, 1, beta_hi, beta_lo] in the canonical K-major layout);
 //   - 1 control thread issues, for combination k + 1, one tcgen05.mma (M = N = 128) per (row
 //     tile, column block) into one of four 128-column TMEM accumulators;
 //   - 8 epilogue warps read each accumulator (tcgen05.ld; warp (g, h) lanes 32 g.. and
@@ -376,12 +375,6 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
   float* fL = reinterpret_cast<float*>(st + L::fL);
   int* under = reinterpret_cast<int*>(cum);  // rows that underflowed (before cum is built)
   const Comb cb = comb_of(a, s);
-  // the output maps' sources, copied in the background into the operand area (free: every
-  // MMA of this stage has completed) while the row CDF is built
-  SlotOut o = slot_out(a, cb, ct == 0);
-  int32_t* sMF = reinterpret_cast<int32_t*>(st + L::opU);
-  int32_t* sML = sMF + kFNmax;
-  prefetch_maps(o, sMF, sML, ct, kFCoreThreads);
   // (sc.n_under and sc.nonfinite are zero here: cleared before the first draw and at the end
   // of every draw)
   // row totals (the tile weights in ascending order, the split path's definition) and the
@@ -476,9 +469,7 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
     }
   }
   // the pairs, each in three exact inverse-CDF stages, and the new block's index maps
-  cp_async_wait_all();
-  bar_sync(kBarCore, kFCoreThreads);
-  map_in_smem(o, sMF, sML);
+  const SlotOut o = slot_out(a, cb, ct == 0);
   DrawIn in;
   in.sys = (a.resampler == DSMC_SYSTEMATIC && !cb.conditional) ? 1 : 0;
   in.cum = cum;
