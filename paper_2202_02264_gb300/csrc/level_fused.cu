@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
 
   __syncthreads();  // the column terms are in shared memory: the rows read a sample of them
   // ---------------------------------------------------------------- own rows
+  const double base_m = shift_base(-a.logN, mp.log_f_max, bstar);  // a merged left block's
   for (int i = lo + threadIdx.x; i < hi; i += NT) {
     float ul[D], ai;
     const float al0 = row_terms<D>(mp, N, d, a.logN, Xl, lastL, lwl, i, mu, ul, ai, corrupt);
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
     }
     alpha[i] = al;
     sAl[i - lo] = al;
-    const double sh = (double)ai + (double)mp.log_f_max + (double)bstar + (double)dl * kLn2d;
+    const double sh = row_shift_total(lwl != nullptr ? shift_base(ai, mp.log_f_max, bstar) : base_m, dl);
     shift[i] = sh;
     sSh[i - lo] = sh;
   }

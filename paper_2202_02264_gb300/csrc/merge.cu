@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
   //                alpha_i = -log2(e) 1/2 w_i' Q^-1 w_i - delta_i  (B* is folded into beta,
   //                delta_i, the row's sampled shift, into shift_i)
   float amax = -INFINITY;
+  const double base_m = shift_base(-a.logN, mp.log_f_max, bstar);  // a merged left block's
   for (int i = threadIdx.x; i < N; i += kProThreads) {
     float ul[D], ai;
     const float al0 = row_terms<D>(mp, N, d, a.logN, Xl, lastL, lwl, i, mu, ul, ai, corrupt);
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
       store_mma_row<D>(a.ws.Ub + (size_t)s * a.Nr * a.mma_planes * 32, a.Nr, i, ul, ext, a.compute);
     }
     alpha[i] = al;
-    shift[i] = (double)ai + (double)mp.log_f_max + (double)bstar + (double)dl * kLn2d;
+    shift[i] = row_shift_total(lwl != nullptr ? shift_base(ai, mp.log_f_max, bstar) : base_m, dl);
     amax = fmaxf(amax, ai);
   }
   amax = warp_max(amax);

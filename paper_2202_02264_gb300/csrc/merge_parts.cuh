@@ -229,10 +229,23 @@ __device__ __forceinline__ float row_total(const float* row, int nT, int nTp) {
   return t;
 }
 
-// The row's base-2 log weight l_i = shift_i log2(e) + delta_i + log2 s_i (-inf when s_i = 0).
+// The row's base-2 log weight l_i = shift_i log2(e) + delta_i + log2 s_i (-inf when s_i = 0),
+// summed in FP64 in that order (delta_i, almost always 0, is added only when it is not: the
+// same bits with fewer FP64 operations, which run at under 2 per clock per SM on GB300).
 __device__ __forceinline__ float row_log2_weight(double shift, float delta, float total) {
-  return total > 0.f ? (float)(shift * kLog2ed + (double)delta + (double)log2f(total)) : -INFINITY;
+  if (!(total > 0.f)) return -INFINITY;
+  double v = shift * kLog2ed;
+  if (delta != 0.f) v += (double)delta;
+  return (float)(v + (double)log2f(total));
 }
+
+// The row's natural-log shift a_i + log f_max + B* + dl_i ln 2 in FP64, in that order:
+// shift_base gives the first three terms; a merged left block has a_i = -log N on every row,
+// so its base is computed once per combination with the same bits.
+__device__ __forceinline__ double shift_base(float ai, float log_f_max, float bstar) {
+  return (double)ai + (double)log_f_max + (double)bstar;
+}
+__device__ __forceinline__ double row_shift_total(double base, float dl) { return base + (double)dl * kLn2d; }
 
 // The row weight r_i = 2^(l_i - M) in FP32, clamped to [0, 1].
 __device__ __forceinline__ float row_weight(float l, float M, bool degenerate) {

@@ -322,8 +322,9 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
     }
   }
   bar_sync(kBarCore, kFCoreThreads);  // the rows read a sample of the columns
-  // rows: u_i, alpha_i (less the row shift decta_i, which moves into shift_i), and the MMA
+  // rows: u_i, alpha_i (less the row shift delta_i, which moves into shift_i), and the MMA
   // row [u, alpha_hi, alpha_lo, 1, 1]
+  const double base_m = shift_base(-a.logN, mp.log_f_max, bstar);  // a merged left block's
   for (int i = ct; i < N; i += kFCoreThreads) {
     float ul[D], ai;
     const float al0 = row_terms<D>(mp, N, d, a.logN, sXl, lastL, lwl, i, mu, ul, ai, corrupt);
@@ -334,7 +335,7 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
     for (int kk = 0; kk < D; ++kk) fU[(size_t)i * D + kk] = ul[kk];
     fAl[i] = al;
     fDl[i] = 0.f;
-    const double sh = (double)ai + (double)mp.log_f_max + (double)bstar + (double)dl * kLn2d;
+    const double sh = row_shift_total(lwl != nullptr ? shift_base(ai, mp.log_f_max, bstar) : base_m, dl);
     fSh[i] = sh;
     float ext[4];
     split_mma(al, KIND, &ext[0], &ext[1]);
