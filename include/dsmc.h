@@ -169,13 +169,14 @@ typedef struct {
                                  combination on one SM; nothing but pairs, maps and log L
                                  written); 0 (default) or < 0 = the split kernels (terms,
                                  tile sums, draws).  Same results.  Needs tile_cols 32. */
-  int tile_cols;              /* dense sampler: columns per tile of the row tile sums (Section
-                                 on the sampler: the tile stage picks a tile, the column stage
-                                 recomputes its columns): 32 or 64, with at most 64 tiles per
-                                 row; 0 = default (32 up to N = 2048, then the smallest
-                                 multiple of 32 giving <= 64 tiles).  A different tile width
-                                 draws from the same law with different random streams per
-                                 stage, so the pairs differ; the weights do not. */
+  int tile_cols;              /* dense sampler: columns per tile of the row tile sums, the
+                                 tiles the sampler's tile stage picks from before its column
+                                 stage recomputes the chosen tile's columns: 32 or 64, with
+                                 at most 64 tiles per row; 0 = default (32 up to N = 2048,
+                                 then the smallest multiple of 32 giving <= 64 tiles).  Another
+                                 tile width draws from the same law with the same uniforms
+                                 split differently across the stages, so the pairs differ;
+                                 the weights do not. */
 } dsmc_config_t;
 
 /* Caller-owned DEVICE state of one smoothing (sizes from dsmc_state_sizes()).
