@@ -14,9 +14,10 @@ sequences) and the serving lanes (d = 2, 8, 32 and SV at their N) -- and each pr
     grid smoother (SV) over R seeds, its standard error, and the paired difference from the
     FP32 form with its standard error (the same seeds).
 
-The table is printed and, when a gpurun_out directory exists at the repository root,
-written there as precision_table.md.  The assertions: every tile error within its bound and
-every reduced precision's mean RMSE within 4 paired standard errors of FP32's (equal error).
+The table is printed (run with -s) and, when the environment variable DSMC_PRECISION_TABLE
+names a file, written there as Markdown.  The assertions: every tile error within its bound
+and every reduced precision's mean RMSE within 4 paired standard errors of FP32's (equal
+error).
 """
 import os
 
@@ -56,9 +57,9 @@ def _write_table():
                      f"{r['rmse']:.4f} ± {r['rmse_se']:.4f} | {r['diff']:+.4f} ± {r['diff_se']:.4f} |")
     text = "\n".join(lines)
     print("\n" + text)
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out):
-        with open(os.path.join(out, "precision_table.md"), "w") as f:
+    out = os.environ.get("DSMC_PRECISION_TABLE")
+    if out:
+        with open(out, "w") as f:
             f.write(text + "\n")
 
 
