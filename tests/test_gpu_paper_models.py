@@ -128,3 +128,27 @@ def test_gaussian_proposals_equal_oracle(name, iterations):
     mo, so = linearized.linearized_smoother(wl.model, y32.astype(np.float64), iterations=iterations)
     np.testing.assert_allclose(mean.cpu().numpy(), mo, rtol=0, atol=2e-6 * max(1.0, np.abs(mo).max()))
     np.testing.assert_allclose(std.cpu().numpy(), so, rtol=2e-6)
+
+
+def test_degenerate_weights_report_status_and_the_context_stays_usable():
+    """A constrained walk whose proposal puts (almost surely) every particle outside the
+    constraint: every pair weight is zero.  The oracle refuses it as degenerate; the device
+    reports a degenerate (or non-finite) status instead of faulting, draws its fallback pairs,
+    and the next smoothing on the same buffers is clean."""
+    import dataclasses
+    K, N = 4, 16
+    m = dataclasses.replace(W.crw(sigma=0.4, bound=1e-3), prop_scale=1.0)
+    y = np.zeros((K, 1))
+    with pytest.raises(RuntimeError, match="degenerate"):
+        core.smooth(m, y, K, N, 5)
+    sm = dsmc.Smoother(m, K, N, seed=5)
+    sm.smooth(dev(y))
+    torch.cuda.synchronize()
+    assert sm.status() in (6, 7)
+    pairs = sm.pairs.cpu().numpy()
+    assert ((pairs >= 0) & (pairs < N)).all()
+    ok = W.crw()
+    sm2 = dsmc.Smoother(ok, K, N, seed=6)
+    sm2.smooth(dev(y))
+    torch.cuda.synchronize()
+    assert sm2.status() == 0

@@ -76,3 +76,12 @@ def test_uniform_proposal_particles_inside_the_constraint():
     assert (np.abs(X) <= wl.model.bound).all()
     # t >= 1, nu_t = q_t: every leaf weight is 1 / N
     np.testing.assert_allclose(lw[1:], -np.log(500), atol=1e-12)
+
+
+def test_all_zero_weights_are_reported_as_degenerate():
+    """Every particle outside the constraint: the combination's weights are all zero, which
+    the oracle reports instead of dividing by a zero sum."""
+    import dataclasses
+    m = dataclasses.replace(W.crw(sigma=0.4, bound=1e-3), prop_scale=1.0)
+    with pytest.raises(RuntimeError, match="degenerate"):
+        core.smooth(m, np.zeros((4, 1)), 4, 16, 5)
