@@ -720,6 +720,18 @@ def run_serving(args):
     reqs70 = [S.Request(r.rid, r.lane, r.model, r.N, r.y, r.seed, r.arrival * scale) for r in reqs]
     _, res70, makespan70, lat70 = serve(reqs70)
 
+    # device time per launch kind over one more pass of the stream (untimed; events around
+    # every launch on the lanes' streams, summed over the lanes)
+    dsmc.dsmc_profile_breakdown_enable(True)
+    srv_b = S.Server(hbm_budget_bytes=150 * 10**9)
+    torch.cuda.synchronize()
+    tb0 = time.perf_counter()
+    srv_b.run(reqs, realtime=False)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - tb0
+    serve_breakdown = {"kinds": dsmc.dsmc_profile_breakdown_read(), "wall_s": tb, "ticks": srv_b.ticks}
+    dsmc.dsmc_profile_breakdown_enable(False)
+
     # plain: the same requests one after another through dsmc_smooth in FP32 (no batching,
     # no reduced precision), host observations in and host means out, wall clock
     plain = None
@@ -758,6 +770,7 @@ def run_serving(args):
                                       "throughput": units / makespan70}},
             "capacity_req_per_s": capacity,
             "plain_fp32_sequential": plain,
+            "breakdown_all_requests": serve_breakdown,
             "mixed_over_plain": value / plain["value"] if plain else None,
             "peak_active_requests": srv.sched.peak_active, "peak_request_bytes": srv.sched.peak_used,
             "roofline": {"bound": "alu", "kernel": "rowsum_tc_kernel / rowsum_kernel (fused exp / tile sums)",
