@@ -15,8 +15,10 @@ namespace {
 
 constexpr int kInitThreads = 256;
 
-template <int D>
-__global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelParams<D> mp) {
+// UNIF: the uniform proposal (a separate instance, so the Gaussian proposals' instance keeps
+// its registers and four CTAs per SM for D <= 4).
+template <int D, bool UNIF>
+__global__ void __launch_bounds__(kInitThreads, D <= 4 ? 4 : 1) init_kernel(InitArgs a, ModelParams<D> mp) {
   int t = blockIdx.x;
   const int N = a.N, d = a.d;
   // this block's sequence: the call's own, or one of a batch
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
   float lmax = -INFINITY;
   bool bad = false;
   const bool uniform = (t > 0 && mp.nu == DSMC_NU_EQ_Q);
-  const bool unif = mp.prop_kind == DSMC_PROP_UNIFORM;
+  constexpr bool unif = UNIF;
   for (int n = threadIdx.x; n < N; n += kInitThreads) {
     float x[D], z[D];
     if (unif) {  // q_t = U([-s, s]^d): x = s (2 u - 1) from the words of counter j = k / 4
@@ -180,7 +182,11 @@ __global__ void __launch_bounds__(kInitThreads) init_kernel(InitArgs a, ModelPar
 
 template <int D>
 cudaError_t launch_init_t(const InitArgs& a, const void* mp, cudaStream_t s) {
-  init_kernel<D><<<a.K, kInitThreads, 0, s>>>(a, *static_cast<const ModelParams<D>*>(mp));
+  const ModelParams<D>& p = *static_cast<const ModelParams<D>*>(mp);
+  if (p.prop_kind == DSMC_PROP_UNIFORM)
+    init_kernel<D, true><<<a.K, kInitThreads, 0, s>>>(a, p);
+  else
+    init_kernel<D, false><<<a.K, kInitThreads, 0, s>>>(a, p);
   return cudaGetLastError();
 }
 
