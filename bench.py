@@ -95,6 +95,10 @@ WORKLOADS = {
     "crw_sys": dict(K=1024, N=4096, resampler="sys", steps=20),
     # the Poisson-count model of the Cox-process experiment (stationary Gaussian proposal)
     "cox": dict(K=1024, N=1024, resampler="dense"),
+    # run time against the number of time steps on the same model (the paper's run-time
+    # figure: logarithmic in K while the levels fill the device, then linear)
+    "cox_scaling": dict(kind="scaling", Ks=(32, 64, 128, 256, 512, 1024, 2048, 4096, 16384),
+                        Ns=(256, 1024, 4096)),
     # Algorithm 7 at N = 16384: B = 64 Metropolis-Hastings steps per slot (biased)
     "sv_mh": dict(K=4096, N=16384, resampler="mh", steps=10),
     "lgssm_d4": dict(K=512, N=512, resampler="dense"),
@@ -218,6 +222,10 @@ def run_reference(args):
         from paper_2202_02264_gb300 import serving as S
         r0 = S.request_stream(1, spec["rate"])[0]
         wl = W.Workload(args.workload, r0.model, r0.K, r0.N, r0.y, None)
+    elif spec.get("kind") == "scaling":   # the oracle at the line's largest N and K
+        wl = W.workload("cox", K=spec["Ks"][-1], N=spec["Ns"][-1])
+    elif spec.get("kind") == "pg_theta":
+        wl = W.workload("theta_logistic", K=spec["K"], N=spec["N"])
     else:
         wl = W.workload(re.sub(r"_(rsf|rs|mh|sys)$", "", args.workload), K=spec["K"], N=spec["N"])
     from oracle import core
@@ -872,6 +880,62 @@ def run_pg(args):
         print(json.dumps(line))
 
 
+def run_scaling(args):
+    """Smoothing time against K on the Poisson-count model (Section 5.1): for each N and K, the
+    median CUDA-event time of whole smoothings (device-resident observations, L2 flushed
+    between runs).  The line's value is N*T/s at the largest N and K."""
+    import torch
+
+    from paper_2202_02264_gb300 import dsmc, workloads as W
+
+    torch.cuda.set_device(0)
+    spec = WORKLOADS[args.workload]
+    compute = {"fp32": dsmc.FP32, "tf32": dsmc.TF32, "bf16": dsmc.BF16}[args.compute]
+    reps = args.steps if args.steps else 9
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    table, launches = {}, 0
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for N in spec["Ns"]:
+        row = {}
+        for K in spec["Ks"]:
+            wl = W.workload("cox", K=K, N=N)
+            sm = dsmc.Smoother(wl.model, K, N, seed=3000, compute=compute)
+            y = torch.as_tensor(wl.y, dtype=torch.float32, device="cuda")
+            for w in range(args.warmup):
+                sm.set_seed(3000, counter_base=w)
+                sm.smooth(y)
+            ts = []
+            for r in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                sm.set_seed(3000, counter_base=100 + r)
+                e0.record(stream)
+                sm.smooth(y)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            if sm.status() != 0:
+                raise RuntimeError(f"device status {sm.status()} at N={N}, K={K}")
+            row[str(K)] = float(np.median(ts))
+            del sm
+        table[str(N)] = row
+    clk = clocks.stop()
+    Nl, Kl = spec["Ns"][-1], spec["Ks"][-1]
+    ms = table[str(Nl)][str(Kl)]
+    line = {"metric": METRIC, "value": Nl * Kl / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": reps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32+f32", "bf16": "bf16+f32"}[args.compute],
+            "data": "synthetic (simulated Poisson counts)",
+            "config": {"workload": args.workload, "model": "Poisson counts (Cox)", "resampler": "dense",
+                       "Ks": list(spec["Ks"]), "Ns": list(spec["Ns"]),
+                       "l2": "flushed between timed runs (512 MiB write)",
+                       "value_at": {"N": Nl, "K": Kl}},
+            "ms_per_smoothing": table, "clocks": clk}
+    print(json.dumps(line))
+
+
 def run_pg_theta(args):
     """Particle Gibbs with parameter updates on the theta-logistic model (Section 3.2,
     Section 5.2), K = 120: per sweep one pass of the linearised smoother from the previous
@@ -957,7 +1021,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     kind = WORKLOADS[args.workload].get("kind", "single")
-    if args.steps is None and kind not in ("pg", "pg_theta"):
+    if args.steps is None and kind not in ("pg", "pg_theta", "scaling"):
         args.steps = WORKLOADS[args.workload].get("steps", {"batch": 10, "serving": 1}.get(kind, 400))
     if args.compute is None:
         args.compute = {"batch": "bf16", "pg": "fp32", "pg_theta": "fp32"}.get(kind, "tf32")
@@ -974,6 +1038,8 @@ def main():
             run_pg(args)
         elif kind == "pg_theta":
             run_pg_theta(args)
+        elif kind == "scaling":
+            run_scaling(args)
         else:
             run_ours(args)
 
