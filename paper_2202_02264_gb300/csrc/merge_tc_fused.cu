@@ -59,6 +59,7 @@ constexpr int kFCore0 = kFEpiWarps * 32;
 constexpr int kFAcc = 4;                    // TMEM accumulators of 128 columns
 constexpr uint32_t kFTmemCols = kFAcc * kMmaN;
 constexpr int kBarCore = 1;                 // named barrier of the core warps
+constexpr int kBarEpi = 2;                  // named barrier of the epilogue warps
 constexpr int kFTileBytes = kMmaM * 32;     // one 128-row tile of one 32-byte K plane
 constexpr int kFTiles = kFNmax / 32;        // tiles of 32 columns per row (tile width 32)
 
@@ -141,8 +142,7 @@ struct CoreScratch {
   float red[kFCoreWarps];
   float mu[4];
   float bstar;
-  unsigned long long S;  // exact total of the row weights' fixed-point images
-  int n_under, nonfinite, ok;
+  int ok;
   int in_bulk;    // the next build's inputs come by bulk copy (1) or are staged by it (0)
   int in_pend;    // bulk copies issued and not yet waited for
   int in_phase;   // completed phases of the inputs barrier
@@ -357,13 +357,24 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
   bar_sync(kBarCore, kFCoreThreads);
 }
 
-// Row CDF and pair draws of combination s from stage st (the core warps): the row totals,
-// the row weights and their exact 2^40 fixed-point prefix sums, the increment of Eq. (Lab),
-// then every slot's pair in three exact inverse-CDF stages and the new block's index maps.
+// Shared scratch of the epilogue warps' row CDF.
+struct EpiScratch {
+  float red[kFEpiWarps];
+  unsigned long long rowtot[kFNmax / 32];
+  int n_under, nonfinite;
+};
+
+// Row CDF of combination s in stage st, by the epilogue warps once its tile sums are
+// complete (et = thread among them, ew = warp): the row totals (the tile weights in
+// ascending order, the split path's definition), the row log weights, a row whose total
+// underflows recomputed with its exact maximum, the row weights r_i = 2^(l_i - M) as exact
+// 2^40 fixed-point images and their inclusive prefix sums (16 rows of 32, one shuffle scan
+// per row, the rows' totals carried), then the increment of Eq. (Lab) and log L.
 template <int D>
-__device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st, int s, int ct, int cw, int lane,
-                                          CoreScratch& sc) {
+__device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* st, int s, int et, int ew, int lane,
+                                            EpiScratch& se) {
   using L = Stage<D>;
+  constexpr int NT = kFEpiWarps * 32;
   const int N = a.N, nT = a.nT, nTp = a.nTp;
   float* fV = reinterpret_cast<float*>(st + L::fV);
   float* fB = reinterpret_cast<float*>(st + L::fB);
@@ -375,20 +386,17 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
   unsigned long long* cum = reinterpret_cast<unsigned long long*>(st + L::cum);
   float* fL = reinterpret_cast<float*>(st + L::fL);
   int* under = reinterpret_cast<int*>(cum);  // rows that underflowed (before cum is built)
-  const Comb cb = comb_of(a, s);
-  // (sc.n_under and sc.nonfinite are zero here: cleared before the first draw and at the end
-  // of every draw)
-  // row totals (the tile weights in ascending order, the split path's definition) and the
-  // rows' base-2 log weights; rows whose total underflows are recomputed below
+  // (se.n_under and se.nonfinite are zero here: cleared before the first row CDF and at the
+  // end of every one)
   float mloc = -INFINITY;
-  for (int i = ct; i < N; i += kFCoreThreads) {
+  for (int i = et; i < N; i += NT) {
     float t = row_total(Tq + (size_t)i * nTp, nT, nTp);
     if (isnan(t)) {
-      sc.nonfinite = 1;
+      se.nonfinite = 1;
       t = 0.f;
     }
     if (t < 0x1p-64f) {
-      under[atomicAdd(&sc.n_under, 1)] = i;
+      under[atomicAdd(&se.n_under, 1)] = i;
     } else {
       if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = t;
       const float v = row_log2_weight(fSh[i], fDl[i], t);
@@ -397,10 +405,10 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
     }
   }
   mloc = warp_max(mloc);
-  if (lane == 0) sc.red[cw] = mloc;
-  bar_sync(kBarCore, kFCoreThreads);
-  if (sc.n_under > 0) {  // rare: exact-max recomputation, then the maximum again
-    for (int uq = cw; uq < sc.n_under; uq += kFCoreWarps) {
+  if (lane == 0) se.red[ew] = mloc;
+  bar_sync(kBarEpi, NT);
+  if (se.n_under > 0) {  // rare: exact-max recomputation, then the maximum again
+    for (int uq = ew; uq < se.n_under; uq += kFEpiWarps) {
       const int i = under[uq];
       float si, dl;
       recompute_row<D, true>(fU + (size_t)i * D, fAl[i], fV, fB, N, a.B, nT, Tq + (size_t)i * nTp, &si, &dl);
@@ -413,77 +421,87 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
         fL[i] = row_log2_weight(fSh[i], dl, si);
       }
     }
-    bar_sync(kBarCore, kFCoreThreads);
+    bar_sync(kBarEpi, NT);
     mloc = -INFINITY;
-    for (int i = ct; i < N; i += kFCoreThreads) mloc = fmaxf(mloc, fL[i]);
+    for (int i = et; i < N; i += NT) mloc = fmaxf(mloc, fL[i]);
     mloc = warp_max(mloc);
-    if (lane == 0) sc.red[cw] = mloc;
-    bar_sync(kBarCore, kFCoreThreads);
+    if (lane == 0) se.red[ew] = mloc;
+    bar_sync(kBarEpi, NT);
   }
-  float M = sc.red[0];
-  for (int w = 1; w < kFCoreWarps; ++w) M = fmaxf(M, sc.red[w]);
+  float M = se.red[0];
+  for (int w = 1; w < kFEpiWarps; ++w) M = fmaxf(M, se.red[w]);
   const bool degenerate = !(M > -INFINITY) || isnan(M);
-  // row weights r_i = 2^(l_i - M) as exact 2^40 fixed-point images
-  for (int i = ct; i < N; i += kFCoreThreads) {
+  for (int i = et; i < N; i += NT) {
     const float r = row_weight(fL[i], M, degenerate);
     if (a.inspect) a.ws.rw[(size_t)s * N + i] = r;
     cum[i] = (unsigned long long)__float2ull_rz(r * 0x1p40f);
   }
-  bar_sync(kBarCore, kFCoreThreads);
-  // their inclusive prefix sums by one warp (integer: exact in any order), then the
-  // increment of Eq. (Lab): the N <= 512 values as 16 rows of 32 (element 32 c + lane), one
-  // shuffle scan per row (independent, so they overlap) and the rows' totals carried in
-  // registers; every shared-memory access is one conflict-free row
-  if (cw == 0) {
-    constexpr int R = kFNmax / 32;
-    const int C = (N + 31) / 32;
-    unsigned long long v[R];
-#pragma unroll
-    for (int c = 0; c < R; ++c) {
-      const int i = 32 * c + lane;
-      v[c] = (c < C && i < N) ? cum[i] : 0ull;
-    }
+  bar_sync(kBarEpi, NT);
+  // prefix sums (integer: exact in any order): each warp scans its rows of 32, then every
+  // element takes the totals of the rows before its own
+  const int C = (N + 31) / 32;
+  for (int c = ew; c < C; c += kFEpiWarps) {
+    const int i = 32 * c + lane;
+    unsigned long long v = i < N ? cum[i] : 0ull;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-      for (int c = 0; c < R; ++c) {
-        const unsigned long long t = __shfl_up_sync(0xffffffffu, v[c], o);
-        if (lane >= o) v[c] += t;
-      }
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += t;
     }
-    unsigned long long carry = 0;
-#pragma unroll
-    for (int c = 0; c < R; ++c) {
-      const unsigned long long row = __shfl_sync(0xffffffffu, v[c], 31);
-      const int i = 32 * c + lane;
-      if (c < C && i < N) cum[i] = carry + v[c];
-      carry += row;
-    }
-    if (lane == 0) sc.S = carry;  // the total; the increment is taken after the draws
+    if (i < N) cum[i] = v;
+    if (lane == 31) se.rowtot[c] = v;
   }
-  bar_sync(kBarCore, kFCoreThreads);
+  bar_sync(kBarEpi, NT);
+  for (int c = ew; c < C; c += kFEpiWarps) {
+    unsigned long long carry = 0;
+    for (int q = 0; q < c; ++q) carry += se.rowtot[q];
+    const int i = 32 * c + lane;
+    if (i < N) cum[i] += carry;
+  }
+  if (et == 0) {
+    unsigned long long S = 0;
+    for (int q = 0; q < C; ++q) S += se.rowtot[q];
+    const Comb cb = comb_of(a, s);
+    const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(S);
+    cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
+    if (degenerate || S == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
+    if (se.nonfinite) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+  }
+  bar_sync(kBarEpi, NT);
   if (a.inspect) {
-    for (int i = ct; i < N; i += kFCoreThreads) {
+    for (int i = et; i < N; i += NT) {
       a.ws.cum[(size_t)s * N + i] = cum[i];
       a.ws.delta[(size_t)s * N + i] = fDl[i];
       for (int kt = 0; kt < nT; ++kt) a.ws.T[((size_t)s * N + i) * nTp + kt] = Tq[(size_t)i * nTp + kt];
     }
   }
-  // the pairs, each in three exact inverse-CDF stages, and the new block's index maps
+  if (et == 0) {
+    se.n_under = 0;
+    se.nonfinite = 0;
+  }
+}
+
+// The pairs of combination s from stage st (the core warps), each in three exact inverse-CDF
+// stages over the row CDF the epilogue warps built, and the new block's index maps.
+template <int D>
+__device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st, int s, int ct) {
+  using L = Stage<D>;
+  const int N = a.N;
+  const Comb cb = comb_of(a, s);
   const SlotOut o = slot_out(a, cb, ct == 0);
   DrawIn in;
   in.sys = (a.resampler == DSMC_SYSTEMATIC && !cb.conditional) ? 1 : 0;
-  in.cum = cum;
-  in.T = Tq;
-  in.U = fU;
-  in.alpha = fAl;
-  in.delta = fDl;
-  in.V = fV;
-  in.beta = fB;
+  in.cum = reinterpret_cast<unsigned long long*>(st + L::cum);
+  in.T = reinterpret_cast<float*>(st + L::T);
+  in.U = reinterpret_cast<float*>(st + L::fU);
+  in.alpha = reinterpret_cast<float*>(st + L::fAl);
+  in.delta = reinterpret_cast<float*>(st + L::fDl);
+  in.V = reinterpret_cast<float*>(st + L::fV);
+  in.beta = reinterpret_cast<float*>(st + L::fB);
   in.N = N;
   in.B = a.B;
-  in.nT = nT;
-  in.nTp = nTp;
+  in.nT = a.nT;
+  in.nTp = a.nTp;
   const int n_lo = cb.conditional ? 1 : 0;
   const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
   for (int n = n_lo + ct; n < n_hi; n += kFCoreThreads) {
@@ -491,20 +509,7 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
     draw_pair<D, true, true>(in, cb.seed, cb.base, cb.gid, n, i, j);
     o.put(n, i, j);
   }
-  // the increment of Eq. (Lab) and log L of the new block, by the last thread (one slot at
-  // most at N <= 512, so its global read-modify-write overlaps the others' second slots)
-  if (ct == kFCoreThreads - 1) {
-    const unsigned long long S = sc.S;
-    const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(S);
-    cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
-    if (degenerate || S == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
-    if (sc.nonfinite) record_status(a.ws.status, DSMC_ERR_NONFINITE);
-  }
   bar_sync(kBarCore, kFCoreThreads);
-  if (ct == 0) {
-    sc.n_under = 0;
-    sc.nonfinite = 0;
-  }
 }
 
 template <int D, int KIND>
@@ -518,6 +523,7 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
   __shared__ uint32_t tmem_base;
   __shared__ int abort_s;
   __shared__ CoreScratch sc;
+  __shared__ EpiScratch se;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = a.N, nTp = a.nTp;
@@ -530,6 +536,8 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
 
   if (threadIdx.x == 0) {
     abort_s = 0;
+    se.n_under = 0;
+    se.nonfinite = 0;
     for (int q = 0; q < 2; ++q) {
       mbar_init(smem_u32(&ops_full[q]), 1);
       mbar_init(smem_u32(&tiles_full[q]), kFEpiWarps);
@@ -604,7 +612,10 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
           }
         }
       }
-      if (stop) break;
+      // every epilogue warp reaches this barrier (a stopped one straight from its wait), so
+      // they agree whether to go on; then the row CDF of this combination
+      if (!bar_and(kBarEpi, kFEpiWarps * 32, !stop)) break;
+      epi_row_cdf<D>(a, fsm + (size_t)(k & 1) * L::bytes, blockIdx.x + k * gridDim.x, threadIdx.x, warp, lane, se);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tiles_full[k & 1]));
     }
@@ -634,7 +645,7 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
       return ok;
     };
     bool ok = true;
-    if (ct == 0) sc.in_phase = sc.in_pend = sc.in_bulk = sc.n_under = sc.nonfinite = 0;
+    if (ct == 0) sc.in_phase = sc.in_pend = sc.in_bulk = 0;
     if (ncomb > 0) issue(0);
     for (int k = 0; k < ncomb && k < 2 && ok; ++k) {
       ok = inputs_ready();
@@ -651,7 +662,7 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
         ok = false;
         break;
       }
-      core_draw<D>(a, fsm + (size_t)q * L::bytes, comb(k), ct, cw, lane, sc);
+      core_draw<D>(a, fsm + (size_t)q * L::bytes, comb(k), ct);
       if (k + 2 < ncomb) {
         ok = inputs_ready();
         if (!ok) break;
