@@ -110,6 +110,29 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// row_total (the ascending FP32 sum of a row's tile weights) of a 16-wide row: the four
+// float4 chunks are loaded starting at chunk rot, so that consecutive threads reading
+// consecutive 64-byte rows spread over the banks, and put back in order by selects before
+// the ascending sum -- the same bits as row_total.
+__device__ __forceinline__ float row_total16(const float* row, int nT, int rot) {
+  const float4* t4 = reinterpret_cast<const float4*>(row);
+  float4 q[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) q[j] = t4[(j + rot) & 3];
+  float t = 0.f;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int j = (m - rot) & 3;  // the load that holds chunk m
+    const float4 c = j == 0 ? q[0] : j == 1 ? q[1] : j == 2 ? q[2] : q[3];
+    const int k = 4 * m;
+    if (k < nT) t = __fadd_rn(t, c.x);
+    if (k + 1 < nT) t = __fadd_rn(t, c.y);
+    if (k + 2 < nT) t = __fadd_rn(t, c.z);
+    if (k + 3 < nT) t = __fadd_rn(t, c.w);
+  }
+  return t;
+}
+
 // Named barrier over n threads that also ANDs a predicate across them.
 __device__ __forceinline__ bool bar_and(int id, int n, bool v) {
   uint32_t r;
@@ -361,7 +384,9 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
 struct EpiScratch {
   float red[kFEpiWarps];
   unsigned long long rowtot[kFNmax / 32];
-  int n_under, nonfinite;
+  unsigned long long S;  // the row weights' exact fixed-point total
+  float M;               // their base-2 maximum
+  int n_under, nonfinite, degenerate;
 };
 
 // Row CDF of combination s in stage st, by the epilogue warps once its tile sums are
@@ -390,7 +415,7 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
   // end of every one)
   float mloc = -INFINITY;
   for (int i = et; i < N; i += NT) {
-    float t = row_total(Tq + (size_t)i * nTp, nT, nTp);
+    float t = nTp == 16 ? row_total16(Tq + (size_t)i * nTp, nT, i >> 1) : row_total(Tq + (size_t)i * nTp, nT, nTp);
     if (isnan(t)) {
       se.nonfinite = 1;
       t = 0.f;
@@ -461,11 +486,9 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
   if (et == 0) {
     unsigned long long S = 0;
     for (int q = 0; q < C; ++q) S += se.rowtot[q];
-    const Comb cb = comb_of(a, s);
-    const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(S);
-    cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
-    if (degenerate || S == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
-    if (se.nonfinite) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+    se.S = S;
+    se.M = M;
+    se.degenerate = degenerate ? 1 : 0;
   }
   bar_sync(kBarEpi, NT);
   if (a.inspect) {
@@ -475,10 +498,21 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
       for (int kt = 0; kt < nT; ++kt) a.ws.T[((size_t)s * N + i) * nTp + kt] = Tq[(size_t)i * nTp + kt];
     }
   }
-  if (et == 0) {
-    se.n_under = 0;
-    se.nonfinite = 0;
-  }
+}
+
+// The increment of Eq. (Lab) and log L of the new block (one thread, after the tile sums'
+// barrier has released the draws: its global read-modify-write is off their path); then the
+// row CDF's flags are cleared for the next combination.
+__device__ __forceinline__ void epi_increment(const MergeArgs& a, int s, EpiScratch& se) {
+  const Comb cb = comb_of(a, s);
+  const unsigned long long S = se.S;
+  const bool degenerate = se.degenerate != 0;
+  const double inc = degenerate ? (double)NAN : (double)se.M * kLn2d + log_fixed_total(S);
+  cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
+  if (degenerate || S == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
+  if (se.nonfinite) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+  se.n_under = 0;
+  se.nonfinite = 0;
 }
 
 // The pairs of combination s from stage st (the core warps), each in three exact inverse-CDF
@@ -618,6 +652,7 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
       epi_row_cdf<D>(a, fsm + (size_t)(k & 1) * L::bytes, blockIdx.x + k * gridDim.x, threadIdx.x, warp, lane, se);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tiles_full[k & 1]));
+      if (threadIdx.x == 0) epi_increment(a, blockIdx.x + k * gridDim.x, se);
     }
   } else if (warp < kFCtrlWarp) {
     // ------------------------------------------------------------------ core warps
