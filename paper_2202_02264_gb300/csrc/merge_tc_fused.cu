@@ -166,6 +166,8 @@ struct CoreScratch {
   float mu[4];
   float bstar;
   int ok;
+  Comb next_cb;   // the next build's combination, and its observation and proposal rows,
+  float next_yc[4], next_qm[4], next_qs[4];  // read one combination ahead
   int in_bulk;    // the next build's inputs come by bulk copy (1) or are staged by it (0)
   int in_pend;    // bulk copies issued and not yet waited for
   int in_phase;   // completed phases of the inputs barrier
@@ -178,8 +180,7 @@ struct InputSrc {
   uint32_t bx, bw;  // bytes of a slice, of a weight / map row
 };
 
-__device__ __forceinline__ InputSrc input_src(const MergeArgs& a, int s) {
-  const Comb cb = comb_of(a, s);
+__device__ __forceinline__ InputSrc input_src(const MergeArgs& a, const Comb& cb) {
   const int N = a.N, d = a.d, c = cb.c, sR = cb.b - cb.c + 1;
   InputSrc r;
   r.xc = cb.X + (size_t)c * N * d;
@@ -193,11 +194,11 @@ __device__ __forceinline__ InputSrc input_src(const MergeArgs& a, int s) {
   return r;
 }
 
-// One thread: the bulk copies of combination s's inputs into `inb`, completing on `bar`,
+// One thread: the bulk copies of combination cb's inputs into `inb`, completing on `bar`,
 // when every source and size is 16-byte aligned (true when N is a multiple of 4 and d
 // divides evenly); otherwise nothing is issued and the build stages them itself.
-__device__ __forceinline__ bool issue_inputs(const MergeArgs& a, int s, unsigned char* inb, uint32_t bar) {
-  const InputSrc r = input_src(a, s);
+__device__ __forceinline__ bool issue_inputs(const MergeArgs& a, const Comb& cb, unsigned char* inb, uint32_t bar) {
+  const InputSrc r = input_src(a, cb);
   const uintptr_t al = reinterpret_cast<uintptr_t>(r.xc) | reinterpret_cast<uintptr_t>(r.xl) |
                        reinterpret_cast<uintptr_t>(r.r0) | reinterpret_cast<uintptr_t>(r.l0) | r.bx | r.bw;
   if ((al & 15) != 0) return false;
@@ -220,7 +221,8 @@ __device__ __forceinline__ bool issue_inputs(const MergeArgs& a, int s, unsigned
 // the row pass (u_i, alpha_i, the row shift), FP32 copies for the draws and the MMA rows.
 template <int D, int KIND>
 __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<D>& mp, unsigned char* st, int s,
-                                          unsigned char* inb, int ct, int cw, int lane, int RT, CoreScratch& sc) {
+                                          unsigned char* inb, int ct, int cw, int lane, int RT, CoreScratch& sc,
+                                          Comb* cb_stage) {
   using L = Stage<D>;
   const int N = a.N, d = a.d;
   unsigned char* opU = st + L::opU;
@@ -231,7 +233,8 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
   float* fAl = reinterpret_cast<float*>(st + L::fAl);
   float* fDl = reinterpret_cast<float*>(st + L::fDl);
   double* fSh = reinterpret_cast<double*>(st + L::fSh);
-  const Comb cb = comb_of(a, s);
+  const Comb cb = sc.next_cb;  // read one combination ahead (issue_next)
+  if (ct == 0) *cb_stage = cb;  // for the draws of this stage
   const int at = cb.at, c = cb.c, b = cb.b, K = cb.K;
   const bool left_leaf = (cb.level == 0);
   const int sR = b - c + 1;
@@ -260,8 +263,11 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
   const float* lwl = left_leaf ? sL0 : nullptr;
   float yc[D], qm[D], qs[D], qinv[D];
 #pragma unroll
-  for (int kk = 0; kk < D; ++kk) yc[kk] = kk < d ? cb.y[(size_t)c * d + kk] : 0.f;
-  proposal_at<D>(mp, cb.y, cb.prop_mean, cb.prop_std, c, qm, qs);
+  for (int kk = 0; kk < D; ++kk) {
+    yc[kk] = sc.next_yc[kk];
+    qm[kk] = sc.next_qm[kk];
+    qs[kk] = sc.next_qs[kk];
+  }
   const float qnorm = proposal_consts<D>(d, qs, qinv);
   bar_sync(kBarCore, kFCoreThreads);
 
@@ -518,10 +524,9 @@ __device__ __forceinline__ void epi_increment(const MergeArgs& a, int s, EpiScra
 // The pairs of combination s from stage st (the core warps), each in three exact inverse-CDF
 // stages over the row CDF the epilogue warps built, and the new block's index maps.
 template <int D>
-__device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st, int s, int ct) {
+__device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st, const Comb& cb, int ct) {
   using L = Stage<D>;
   const int N = a.N;
-  const Comb cb = comb_of(a, s);
   const SlotOut o = slot_out(a, cb, ct == 0);
   DrawIn in;
   in.sys = (a.resampler == DSMC_SYSTEMATIC && !cb.conditional) ? 1 : 0;
@@ -558,6 +563,7 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
   __shared__ int abort_s;
   __shared__ CoreScratch sc;
   __shared__ EpiScratch se;
+  __shared__ Comb cbs[2];  // the combination of each stage (written by its build)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = a.N, nTp = a.nTp;
@@ -664,8 +670,22 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
     auto comb = [&](int k) { return (int)blockIdx.x + k * (int)gridDim.x; };
     // one thread starts the inputs of combination k (the buffer is free: the previous build
     // has read it, and its closing fence orders those reads before the bulk copies)
+    // and reads the combination's descriptor and its observation and proposal rows, for its
+    // build (each a dependent global round trip, here off the build's path)
     auto issue = [&](int k) {
-      if (ct == 0) sc.in_bulk = sc.in_pend = issue_inputs(a, comb(k), inb, in_bar) ? 1 : 0;
+      if (ct == 0) {
+        const Comb cb = comb_of(a, comb(k));
+        sc.next_cb = cb;
+        float qm[D], qs[D];
+        proposal_at<D>(mp, cb.y, cb.prop_mean, cb.prop_std, cb.c, qm, qs);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          sc.next_yc[kk] = kk < D && kk < a.d ? cb.y[(size_t)cb.c * a.d + kk] : 0.f;
+          sc.next_qm[kk] = kk < D ? qm[kk] : 0.f;
+          sc.next_qs[kk] = kk < D ? qs[kk] : 1.f;
+        }
+        sc.in_bulk = sc.in_pend = issue_inputs(a, cb, inb, in_bar) ? 1 : 0;
+      }
     };
     // every core thread waits for bulk-copied inputs; false on an abort or a timeout
     auto inputs_ready = [&]() -> bool {
@@ -685,7 +705,7 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
     for (int k = 0; k < ncomb && k < 2 && ok; ++k) {
       ok = inputs_ready();
       if (!ok) break;
-      core_load<D, KIND>(a, mp, fsm + (size_t)k * L::bytes, comb(k), inb, ct, cw, lane, RT, sc);
+      core_load<D, KIND>(a, mp, fsm + (size_t)k * L::bytes, comb(k), inb, ct, cw, lane, RT, sc, &cbs[k]);
       if (k + 1 < ncomb) issue(k + 1);
       if (ct == 0) mbar_arrive(smem_u32(&ops_full[k]));
     }
@@ -697,11 +717,11 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
         ok = false;
         break;
       }
-      core_draw<D>(a, fsm + (size_t)q * L::bytes, comb(k), ct);
+      core_draw<D>(a, fsm + (size_t)q * L::bytes, cbs[q], ct);
       if (k + 2 < ncomb) {
         ok = inputs_ready();
         if (!ok) break;
-        core_load<D, KIND>(a, mp, fsm + (size_t)q * L::bytes, comb(k + 2), inb, ct, cw, lane, RT, sc);
+        core_load<D, KIND>(a, mp, fsm + (size_t)q * L::bytes, comb(k + 2), inb, ct, cw, lane, RT, sc, &cbs[q]);
         if (k + 3 < ncomb) issue(k + 3);
         if (ct == 0) mbar_arrive(smem_u32(&ops_full[q]));
       }
