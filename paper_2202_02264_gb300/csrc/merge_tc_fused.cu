@@ -68,7 +68,7 @@ __host__ __device__ constexpr size_t rnd(size_t x, size_t a) { return (x + a - 1
 // Byte offsets inside one stage (one combination's data, N <= 512):
 //   opU, opV  the MMA row and column operands, [512][32 B] each, canonical K-major layout
 //   fV, fB    v_j [N][D] and beta_j, padded after every 32 columns (FP32)
-//   fU        u_i [N][D];  fAl alpha_i;  fDl delta_i (FP32);  fSh shift_i (FP64)
+//   fU        u_i [N][D];  fAl alpha_i;  fDl delta_i (FP32);  fSh shift_i log2(e) (FP64)
 //   T         tile weights [N][16] (before the MMA: the loader's staged inputs)
 //   cum       exact prefix sums of the row weights (u64);  fL the row log weights
 template <int D>
@@ -108,29 +108,6 @@ __device__ __forceinline__ void bar_sync(int id, int n) {
 
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// row_total (the ascending FP32 sum of a row's tile weights) of a 16-wide row: the four
-// float4 chunks are loaded starting at chunk rot, so that consecutive threads reading
-// consecutive 64-byte rows spread over the banks, and put back in order by selects before
-// the ascending sum -- the same bits as row_total.
-__device__ __forceinline__ float row_total16(const float* row, int nT, int rot) {
-  const float4* t4 = reinterpret_cast<const float4*>(row);
-  float4 q[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) q[j] = t4[(j + rot) & 3];
-  float t = 0.f;
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const int j = (m - rot) & 3;  // the load that holds chunk m
-    const float4 c = j == 0 ? q[0] : j == 1 ? q[1] : j == 2 ? q[2] : q[3];
-    const int k = 4 * m;
-    if (k < nT) t = __fadd_rn(t, c.x);
-    if (k + 1 < nT) t = __fadd_rn(t, c.y);
-    if (k + 2 < nT) t = __fadd_rn(t, c.z);
-    if (k + 3 < nT) t = __fadd_rn(t, c.w);
-  }
-  return t;
 }
 
 // Named barrier over n threads that also ANDs a predicate across them.
@@ -365,7 +342,7 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
     fAl[i] = al;
     fDl[i] = 0.f;
     const double sh = row_shift_total(lwl != nullptr ? shift_base(ai, mp.log_f_max, bstar) : base_m, dl);
-    fSh[i] = sh;
+    fSh[i] = sh * kLog2ed;  // base 2: the row CDF's FP64 product, taken here
     float ext[4];
     split_mma(al, KIND, &ext[0], &ext[1]);
     ext[2] = 1.f;
@@ -421,7 +398,7 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
   // end of every one)
   float mloc = -INFINITY;
   for (int i = et; i < N; i += NT) {
-    float t = nTp == 16 ? row_total16(Tq + (size_t)i * nTp, nT, i >> 1) : row_total(Tq + (size_t)i * nTp, nT, nTp);
+    float t = row_total(Tq + (size_t)i * nTp, nT, nTp);
     if (isnan(t)) {
       se.nonfinite = 1;
       t = 0.f;
@@ -430,7 +407,7 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
       under[atomicAdd(&se.n_under, 1)] = i;
     } else {
       if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = t;
-      const float v = row_log2_weight(fSh[i], fDl[i], t);
+      const float v = row_log2_weight2(fSh[i], fDl[i], t);
       fL[i] = v;
       mloc = fmaxf(mloc, v);
     }
@@ -449,7 +426,7 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
         si = isnan(si) ? 0.f : si;
         if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = si;
         fDl[i] = dl;
-        fL[i] = row_log2_weight(fSh[i], dl, si);
+        fL[i] = row_log2_weight2(fSh[i], dl, si);
       }
     }
     bar_sync(kBarEpi, NT);
