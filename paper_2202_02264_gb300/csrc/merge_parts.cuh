@@ -239,15 +239,6 @@ __device__ __forceinline__ float row_log2_weight(double shift, float delta, floa
   return (float)(v + (double)log2f(total));
 }
 
-// The same from the shift already scaled to base 2 (shift2 = shift_i log2(e), the same FP64
-// product): the same bits.
-__device__ __forceinline__ float row_log2_weight2(double shift2, float delta, float total) {
-  if (!(total > 0.f)) return -INFINITY;
-  double v = shift2;
-  if (delta != 0.f) v += (double)delta;
-  return (float)(v + (double)log2f(total));
-}
-
 // The row's natural-log shift a_i + log f_max + B* + dl_i ln 2 in FP64, in that order:
 // shift_base gives the first three terms; a merged left block has a_i = -log N on every row,
 // so its base is computed once per combination with the same bits.

@@ -68,7 +68,7 @@ __host__ __device__ constexpr size_t rnd(size_t x, size_t a) { return (x + a - 1
 // Byte offsets inside one stage (one combination's data, N <= 512):
 //   opU, opV  the MMA row and column operands, [512][32 B] each, canonical K-major layout
 //   fV, fB    v_j [N][D] and beta_j, padded after every 32 columns (FP32)
-//   fU        u_i [N][D];  fAl alpha_i;  fDl delta_i (FP32);  fSh shift_i log2(e) (FP64)
+//   fU        u_i [N][D];  fAl alpha_i;  fDl delta_i (FP32);  fSh shift_i (FP64)
 //   T         tile weights [N][16] (before the MMA: the loader's staged inputs)
 //   cum       exact prefix sums of the row weights (u64);  fL the row log weights
 template <int D>
@@ -342,7 +342,7 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
     fAl[i] = al;
     fDl[i] = 0.f;
     const double sh = row_shift_total(lwl != nullptr ? shift_base(ai, mp.log_f_max, bstar) : base_m, dl);
-    fSh[i] = sh * kLog2ed;  // base 2: the row CDF's FP64 product, taken here
+    fSh[i] = sh;
     float ext[4];
     split_mma(al, KIND, &ext[0], &ext[1]);
     ext[2] = 1.f;
@@ -407,7 +407,7 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
       under[atomicAdd(&se.n_under, 1)] = i;
     } else {
       if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = t;
-      const float v = row_log2_weight2(fSh[i], fDl[i], t);
+      const float v = row_log2_weight(fSh[i], fDl[i], t);
       fL[i] = v;
       mloc = fmaxf(mloc, v);
     }
@@ -426,7 +426,7 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
         si = isnan(si) ? 0.f : si;
         if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = si;
         fDl[i] = dl;
-        fL[i] = row_log2_weight2(fSh[i], dl, si);
+        fL[i] = row_log2_weight(fSh[i], dl, si);
       }
     }
     bar_sync(kBarEpi, NT);
