@@ -9,10 +9,11 @@ configuration at full size (through the C ABI).
     two-term splits of the row / column terms and FP32 accumulation (0.01), plus the FP32
     path's own 1e-5 relative.
   * The batched workload's shape: full-length sequences (K about 4000) of the d = 4
-    linear-Gaussian batch, N = 512, BF16 cross term, every level split (no fused level) with
-    up to 16384 combinations per launch: tile weights against the oracle and indices
-    bit-exact at the bottom, middle and top levels; smoothing means of the batched call
-    within Monte Carlo error of Kalman/RTS; the batched call equal to each sequence alone.
+    linear-Gaussian batch, N = 512, BF16 cross term, no fused small level, up to 16384
+    combinations per launch: tile weights against the oracle and indices bit-exact at the
+    bottom, middle and top levels; smoothing means of the batched call (split kernels and
+    the fused tensor-core level kernel) within Monte Carlo error of Kalman/RTS; the batched
+    call equal to each sequence alone.
 """
 import numpy as np
 import pytest
@@ -140,10 +141,11 @@ def test_headline_shape_levels_against_oracle():
         assert sm.status() == 0
 
 
-def test_headline_shape_batched_means_and_alone():
-    """The batched call (BF16, schedule (-1, 16384)) on the two longest sequences: seed-
-    averaged means within Monte Carlo error of Kalman/RTS, and the pairs of each sequence
-    equal to its own single-sequence smoothing."""
+@pytest.mark.parametrize("tc_fused", [-1, 1])
+def test_headline_shape_batched_means_and_alone(tc_fused):
+    """The batched call (BF16, schedule (-1, 16384), split kernels or the fused tensor-core
+    level kernel) on the two longest sequences: seed-averaged means within Monte Carlo error
+    of Kalman/RTS, and the pairs of each sequence equal to its own single-sequence smoothing."""
     bw, idx = _headline_sequences()
     N = bw.N
     Ks = [int(bw.Ks[s]) for s in idx]
@@ -151,7 +153,7 @@ def test_headline_shape_batched_means_and_alone():
     R = 16
     means = [[] for _ in idx]
     b = dsmc.BatchSmoother(bw.model, Ks, N, seeds=[0] * len(idx), compute=dsmc.BF16, fused_max_merges=-1,
-                           max_merges_per_launch=16384)
+                           max_merges_per_launch=16384, tc_fused=tc_fused)
     b.set_inputs(ys)
     for r in range(R):
         b.seeds = [1000 + 7 * r + k for k in range(len(idx))]
@@ -165,7 +167,7 @@ def test_headline_shape_batched_means_and_alone():
     # the last batch equals each sequence smoothed alone with the same seed
     for k, s in enumerate(idx):
         sm = dsmc.Smoother(bw.model, Ks[k], N, seed=b.seeds[k], compute=dsmc.BF16, fused_max_merges=-1,
-                           max_merges_per_launch=16384)
+                           max_merges_per_launch=16384, tc_fused=tc_fused)
         sm.smooth(ys[k])
         torch.cuda.synchronize()
         assert torch.equal(sm.pairs, b.pairs[k])
