@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(128) rowsum_kernel(MergeArgs a, int SC) {
 
 // ---------------------------------------------------------------------------------------
 // Row CDF of one combination (one CTA):
-//   row totals s_i = sum of the row's tile weights in ascending tile order (thread per row,
+//   row totals s_i = row_total of the row's tile weights (even / odd pair sums; thread per row,
 //   independent vector loads; no result depends on how the tile-sum kernel chunked the
 //   columns); a row whose total fell below 2^-64 of its bound is recomputed with its exact
 //   maximum as shift (rare; tiles rewritten, extra base-2 shift kept in delta);
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
       float4* dst = reinterpret_cast<float4*>(sT + (size_t)i * L.nTs);
       for (int k4 = 0; k4 < nTp / 4; ++k4) dst[k4] = src[k4];
     }
-    // the row total: the tile weights in ascending order (every path's definition)
+    // the row total: row_total's even / odd pair sums (every path's definition)
     float t = sT ? row_total(sT + (size_t)i * L.nTs, nT, nTp) : row_total(Tt + (size_t)i * nTp, nT, nTp);
     if (isnan(t)) {
       nonfinite_s = 1;

@@ -213,20 +213,21 @@ __device__ __forceinline__ float row_shift(const float* u, float al, const float
 }
 
 // ---------------------------------------------------------------- row totals and CDF
-// Sum of a row's tile weights in ascending tile order (vector loads; the row is 16-byte
-// aligned, nTp a multiple of 4).
+// The row total, every path's definition: the tile weights summed in pairs
+// q_p = t_{2p} + t_{2p+1} (t_{2p+1} = 0 past the last tile), the even pairs and the odd pairs
+// each accumulated in ascending p, then the two sums added (FP32, round to nearest).  A
+// tensor-core epilogue warp that holds the even (or odd) pairs of a row accumulates its
+// half as it goes; vector loads here (the row is 16-byte aligned, nTp a multiple of 4).
 __device__ __forceinline__ float row_total(const float* row, int nT, int nTp) {
   const float4* t4 = reinterpret_cast<const float4*>(row);
-  float t = 0.f;
+  float se = 0.f, so = 0.f;
   for (int k4 = 0; k4 < nTp / 4; ++k4) {
     const float4 v = t4[k4];
-    const int k = 4 * k4;
-    if (k < nT) t = __fadd_rn(t, v.x);
-    if (k + 1 < nT) t = __fadd_rn(t, v.y);
-    if (k + 2 < nT) t = __fadd_rn(t, v.z);
-    if (k + 3 < nT) t = __fadd_rn(t, v.w);
+    const int k = 4 * k4;  // pairs 2 k4 (even) and 2 k4 + 1 (odd)
+    if (k < nT) se = __fadd_rn(se, __fadd_rn(v.x, k + 1 < nT ? v.y : 0.f));
+    if (k + 2 < nT) so = __fadd_rn(so, __fadd_rn(v.z, k + 3 < nT ? v.w : 0.f));
   }
-  return t;
+  return __fadd_rn(se, so);
 }
 
 // The row's base-2 log weight l_i = shift_i log2(e) + delta_i + log2 s_i (-inf when s_i = 0),

@@ -373,8 +373,8 @@ struct EpiScratch {
 };
 
 // Row CDF of combination s in stage st, by the epilogue warps once its tile sums are
-// complete (et = thread among them, ew = warp): the row totals (the tile weights in
-// ascending order, the split path's definition), the row log weights, a row whose total
+// complete (et = thread among them, ew = warp): the row totals (row_total's definition, from
+// the two halves the epilogue accumulated), the row log weights, a row whose total
 // underflows recomputed with its exact maximum, the row weights r_i = 2^(l_i - M) as exact
 // 2^40 fixed-point images and their inclusive prefix sums (16 rows of 32, one shuffle scan
 // per row, the rows' totals carried), then the increment of Eq. (Lab) and log L.
@@ -397,8 +397,9 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
   // (se.n_under and se.nonfinite are zero here: cleared before the first row CDF and at the
   // end of every one)
   float mloc = -INFINITY;
+  const float* tot_o = reinterpret_cast<const float*>(cum) + kFNmax;
   for (int i = et; i < N; i += NT) {
-    float t = row_total(Tq + (size_t)i * nTp, nT, nTp);
+    float t = __fadd_rn(fL[i], tot_o[i]);  // row_total: the halves the epilogue accumulated
     if (isnan(t)) {
       se.nonfinite = 1;
       t = 0.f;
@@ -586,8 +587,14 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
     bool stop = false;
     for (int k = 0; k < ncomb && !stop; ++k) {
       float* Tq = reinterpret_cast<float*>(fsm + (size_t)(k & 1) * L::bytes + L::T);
+      // the row total's two halves (row_total's definition): the even and the odd tile pairs,
+      // each accumulated in ascending order as the blocks come (warp h holds pairs of
+      // parity h), kept in fL and in the upper half of cum until the row CDF
+      float* tot_e = reinterpret_cast<float*>(fsm + (size_t)(k & 1) * L::bytes + L::fL);
+      float* tot_o = reinterpret_cast<float*>(fsm + (size_t)(k & 1) * L::bytes + L::cum) + kFNmax;
       for (int rt = 0; rt < RT && !stop; ++rt) {
         const int row = rt * kMmaM + 32 * g + lane;
+        float h_even = 0.f, h_odd = 0.f;
         for (int cb = 0; cb < RT; ++cb, ++blk) {
           const int acc = blk & (kFAcc - 1);
           const bool ok = __all_sync(0xffffffffu, mbar_wait_or_abort(smem_u32(&acc_full[acc]),
@@ -626,7 +633,16 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
               else if (col0 < N)
                 Tq[(size_t)row * nTp + col0 / 32] = t0;
             }
+            const float q = __fadd_rn(t0, t1);  // 0 past the last tile
+            if ((col0 / 64) & 1)
+              h_odd = __fadd_rn(h_odd, q);
+            else
+              h_even = __fadd_rn(h_even, q);
           }
+        }
+        if (row < N) {
+          if (kFEpiWarps == 4 || h == 0) tot_e[row] = h_even;
+          if (kFEpiWarps == 4 || h == 1) tot_o[row] = h_odd;
         }
       }
       // every epilogue warp reaches this barrier (a stopped one straight from its wait), so
