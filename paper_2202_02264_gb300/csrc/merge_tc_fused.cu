@@ -142,7 +142,6 @@ struct CoreScratch {
   float red[kFCoreWarps];
   float mu[4];
   float bstar;
-  int ok;
   Comb next_cb;   // the next build's combination, and its observation and proposal rows,
   float next_yc[4], next_qm[4], next_qs[4];  // read one combination ahead
   int in_bulk;    // the next build's inputs come by bulk copy (1) or are staged by it (0)
@@ -526,7 +525,7 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
     draw_pair<D, true, true>(in, cb.seed, cb.base, cb.gid, n, i, j);
     o.put(n, i, j);
   }
-  bar_sync(kBarCore, kFCoreThreads);
+  // (no barrier here: the next build starts with one, before it writes this stage)
 }
 
 template <int D, int KIND>
@@ -681,8 +680,9 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
       }
     };
     // every core thread waits for bulk-copied inputs; false on an abort or a timeout
-    auto inputs_ready = [&]() -> bool {
-      bar_sync(kBarCore, kFCoreThreads);  // sc.in_bulk is visible
+    // (sync_first: a barrier first, where no other one has passed since issue wrote sc.in_bulk)
+    auto inputs_ready = [&](bool sync_first) -> bool {
+      if (sync_first) bar_sync(kBarCore, kFCoreThreads);
       bool ok = true;
       if (sc.in_bulk) ok = mbar_wait_or_abort(in_bar, (uint32_t)sc.in_phase & 1, abort_v);
       ok = bar_and(kBarCore, kFCoreThreads, ok);
@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
     if (ct == 0) sc.in_phase = sc.in_pend = sc.in_bulk = 0;
     if (ncomb > 0) issue(0);
     for (int k = 0; k < ncomb && k < 2 && ok; ++k) {
-      ok = inputs_ready();
+      ok = inputs_ready(true);
       if (!ok) break;
       core_load<D, KIND>(a, mp, fsm + (size_t)k * L::bytes, comb(k), inb, ct, cw, lane, RT, sc, &cbs[k]);
       if (k + 1 < ncomb) issue(k + 1);
@@ -704,15 +704,15 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
     }
     for (int k = 0; k < ncomb && ok; ++k) {
       const int q = k & 1;
-      if (ct == 0) sc.ok = mbar_wait_or_abort(smem_u32(&tiles_full[q]), (uint32_t)(k >> 1) & 1, abort_v);
-      bar_sync(kBarCore, kFCoreThreads);
-      if (!sc.ok) {
+      const bool tiles_ok =
+          ct != 0 || mbar_wait_or_abort(smem_u32(&tiles_full[q]), (uint32_t)(k >> 1) & 1, abort_v);
+      if (!bar_and(kBarCore, kFCoreThreads, tiles_ok)) {
         ok = false;
         break;
       }
       core_draw<D>(a, fsm + (size_t)q * L::bytes, cbs[q], ct);
       if (k + 2 < ncomb) {
-        ok = inputs_ready();
+        ok = inputs_ready(false);  // the draws' end and the build's start: its barrier
         if (!ok) break;
         core_load<D, KIND>(a, mp, fsm + (size_t)q * L::bytes, comb(k + 2), inb, ct, cw, lane, RT, sc, &cbs[q]);
         if (k + 3 < ncomb) issue(k + 3);
