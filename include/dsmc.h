@@ -422,8 +422,8 @@ dsmc_status_t dsmc_profile_breakdown_read(double* ms /* [DSMC_KINDS] */, int64_t
 
 /* Arithmetic unit rates of the current device, for the roofline of the exponential kernels
  * (which are bound by these units, not by HBM): results per second of MUFU ex2.approx,
- * FP32 FFMA, packed FFMA2 (one per instruction lane), FADD and FP64 DFMA (the row shifts and
- * per-combination increments are FP64), each the best of three timed
+ * FP32 FFMA, packed FFMA2 (one per instruction lane), FADD and FP64 DFMA (the lazy samplers'
+ * row shifts and the per-combination increments are FP64), each the best of three timed
  * launches (CUDA events on `stream`, after one warm-up launch) of eight independent
  * dependency chains per thread, four 256-thread CTAs per SM.  The paper has no counterpart:
  * this is a measurement aid.  sink: DEVICE, one float the kernels may write (they do not for

@@ -159,7 +159,7 @@ struct Plan {
   int R, rows_per_cta;
   bool dense;
   int level_off[33];
-  size_t o_status, o_U, o_alpha, o_V, o_beta, o_shift, o_logbar, o_inc, o_T, o_rw, o_rowsum, o_cum,
+  size_t o_status, o_U, o_alpha, o_V, o_beta, o_shift, o_g, o_cbase, o_logbar, o_inc, o_T, o_rw, o_rowsum, o_cum,
       o_delta, o_first, o_last, o_star, o_Ub, o_Vb, o_attempts, o_alpha0, o_kappa, o_pa, o_pc, o_cumA, o_cumC,
       total;
 };
@@ -235,6 +235,8 @@ void make_plan(const dsmc_config_t* cfg, const dsmc_model_t* model, Plan& p, int
   p.o_V = take(MN * p.D * sizeof(float));
   p.o_beta = take(MN * sizeof(float));
   p.o_shift = take(MN * sizeof(double));
+  p.o_g = take(p.dense ? MN * sizeof(float) : 0);
+  p.o_cbase = take(p.dense ? (size_t)p.Mc * sizeof(double) : 0);
   p.o_logbar = take((size_t)p.Mc * sizeof(double));
   p.o_inc = take((size_t)p.Mc * sizeof(double));
   p.o_T = take(p.dense ? MN * p.nTp * sizeof(float) : 0);
@@ -266,6 +268,8 @@ WsPtrs ws_ptrs(const Plan& p, void* ws) {
   w.V = reinterpret_cast<float*>(b + p.o_V);
   w.beta = reinterpret_cast<float*>(b + p.o_beta);
   w.shift = reinterpret_cast<double*>(b + p.o_shift);
+  w.g = reinterpret_cast<float*>(b + p.o_g);
+  w.cbase = reinterpret_cast<double*>(b + p.o_cbase);
   w.logbar = reinterpret_cast<double*>(b + p.o_logbar);
   w.inc = reinterpret_cast<double*>(b + p.o_inc);
   w.T = reinterpret_cast<float*>(b + p.o_T);

@@ -16,7 +16,10 @@ struct WsPtrs {
   float* alpha;      // [Mc][N]      row term of the base-2 exponent
   float* V;          // [Mc][N][D]   x_R - mu
   float* beta;       // [Mc][N]      column term of the base-2 exponent
-  double* shift;     // [Mc][N]      per-row shift (natural log): a_i + log f_max + B*
+  double* shift;     // [Mc][N]      per-row shift (natural log): a_i + log f_max + B* + dl_i ln 2
+  float* g;          // [Mc][N]      dense samplers: the same shift less the combination base,
+                     //              in base 2 (shift_i = cbase + g_i ln 2)
+  double* cbase;     // [Mc]         dense samplers: the combination base (natural log)
   double* logbar;    // [Mc]         log omega-bar, bound of the whole N x N matrix
   float* T;          // [Mc][N][nTp] tile weights, relative to the row shift
   float* rw;         // [Mc][N]      row weights of the row stage

@@ -52,7 +52,7 @@ __host__ __device__ __forceinline__ FusedSmem fused_smem(int N, int D, int rows_
   f.c = o;  o = round16(o + (size_t)N * sizeof(unsigned long long)); // prefix sums [N]
   f.u = o;  o = round16(o + (size_t)rows_per * D * sizeof(float));   // own u_i    [R][D]
   f.al = o; o = round16(o + (size_t)rows_per * sizeof(float));       // own alpha_i
-  f.sh = o; o = round16(o + (size_t)rows_per * sizeof(double));      // own shift_i
+  f.sh = o; o = round16(o + (size_t)rows_per * sizeof(float));       // own row offsets g_i
   f.total = o;
   return f;
 }
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   unsigned long long* sC = reinterpret_cast<unsigned long long*>(smraw + L.c);
   float* sU = reinterpret_cast<float*>(smraw + L.u);
   float* sAl = reinterpret_cast<float*>(smraw + L.al);
-  double* sSh = reinterpret_cast<double*>(smraw + L.sh);
+  float* sG = reinterpret_cast<float*>(smraw + L.sh);  // the own rows' offsets g_i (row_offset)
   int* under = reinterpret_cast<int*>(sC);  // own rows that underflowed (before the CDF)
 
   __shared__ float gsum[kMaxColumnGroups * D];
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
     sAl[i - lo] = al;
     const double sh = row_shift_total(lwl != nullptr ? shift_base(ai, mp.log_f_max, bstar) : base_m, dl);
     shift[i] = sh;
-    sSh[i - lo] = sh;
+    sG[i - lo] = row_offset(left_leaf, ai, dl);
   }
   // column / row errors are recorded before any row CDF of the cluster can report a
   // degenerate combination (the split path's order)
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   for (int i = lo + threadIdx.x; i < hi; i += NT) {
     const float t = sL[i];
     rowsum[i] = t;
-    sL[i] = row_log2_weight(sSh[i - lo], delta[i], t);
+    sL[i] = row_log2_weight(sG[i - lo], delta[i], t);
   }
 
   // ---------------------------------------------------------------- exchange l_i
@@ -301,7 +301,9 @@ __global__ void __launch_bounds__(fused_threads<D>(), 1) level_fused_kernel(Merg
   unsigned long long* gcum = a.ws.cum + (size_t)s * N;
   for (int i = lo + threadIdx.x; i < hi; i += NT) gcum[i] = sC[i];
   if (r == 0 && threadIdx.x == 0) {
-    const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(sC[N - 1]);
+    const double inc = degenerate ? (double)NAN
+                                  : lab_increment(comb_base(left_leaf, a.logN, mp.log_f_max, bstar), M,
+                                                  log_fixed_total(sC[N - 1]));
     a.ws.inc[s] = inc;
     cb.logL[at] = cb.logL[at] + cb.logL[c] + inc;
     if (degenerate || sC[N - 1] == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);

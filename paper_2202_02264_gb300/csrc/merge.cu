@@ -80,6 +80,8 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
   const int bufL = cb.level & 1;
   const int bufR = ceil_log2(sR) & 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // the dense samplers' row CDF takes the shift as a combination base and FP32 row offsets
+  const bool dense = a.resampler == DSMC_MULTINOMIAL || a.resampler == DSMC_SYSTEMATIC;
 
   float* V = a.ws.V + (size_t)s * N * D;
   float* beta = a.ws.beta + (size_t)s * N;
@@ -252,6 +254,7 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
     }
     alpha[i] = al;
     shift[i] = row_shift_total(lwl != nullptr ? shift_base(ai, mp.log_f_max, bstar) : base_m, dl);
+    if (dense) a.ws.g[(size_t)s * N + i] = row_offset(left_leaf, ai, dl);
     amax = fmaxf(amax, ai);
   }
   amax = warp_max(amax);
@@ -269,6 +272,7 @@ __global__ void __launch_bounds__(prologue_threads<D>(), prologue_min_blocks<D>(
       bh = fmaxf(bh, red2_s[w]);
     }
     a.ws.logbar[s] = (double)mp.log_f_max + (double)t + (double)(hull ? bh : bstar);
+    if (dense) a.ws.cbase[s] = comb_base(left_leaf, a.logN, mp.log_f_max, bstar);
   }
   if (corrupt) record_status(a.ws.status, DSMC_ERR_INVALID_ARG);
   if (bad) record_status(a.ws.status, DSMC_ERR_NONFINITE);
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(kCdfThreads) rowcdf_kernel(MergeArgs a) {
   }
   __syncthreads();
   const float* Tt = a.ws.T + (size_t)s * N * nTp;
-  const double* shift = a.ws.shift + (size_t)s * N;
+  const float* g = a.ws.g + (size_t)s * N;
   float* delta = a.ws.delta + (size_t)s * N;
   float* rowsum = a.ws.rowsum + (size_t)s * N;
   for (int i = threadIdx.x; i < N; i += kCdfThreads) {
@@ -431,7 +435,7 @@ __global__ void __launch_bounds__(kCdfThreads) rowcdf_kernel(MergeArgs a) {
   for (int i = threadIdx.x; i < N; i += kCdfThreads) {
     const float t = l2[i];
     rowsum[i] = t;
-    const float v = row_log2_weight(shift[i], delta[i], t);
+    const float v = row_log2_weight(g[i], delta[i], t);
     l2[i] = v;
     mloc = fmaxf(mloc, v);
   }
@@ -460,7 +464,7 @@ __global__ void __launch_bounds__(kCdfThreads) rowcdf_kernel(MergeArgs a) {
     const Comb cb = comb_of(a, s);
     // Eq. (Lab): log of sum_ij exp(logW_ij) = M ln 2 + ln(sum_i r_i), the row-weight total
     // taken from its exact fixed-point image
-    const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(cum[N - 1]);
+    const double inc = degenerate ? (double)NAN : lab_increment(a.ws.cbase[s], M, log_fixed_total(cum[N - 1]));
     a.ws.inc[s] = inc;
     cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
     if (degenerate || cum[N - 1] == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
@@ -589,7 +593,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
   const float* beta = a.ws.beta + (size_t)s * N;
   const float* alpha = a.ws.alpha + (size_t)s * N;
   float* Tt = a.ws.T + (size_t)s * N * nTp;
-  const double* shift = a.ws.shift + (size_t)s * N;
+  const float* g = a.ws.g + (size_t)s * N;
   float* delta = a.ws.delta + (size_t)s * N;
   float* rowsum = a.ws.rowsum + (size_t)s * N;
   // stage the operands (vector copies when D % 4 == 0: rows and pads are 16-byte aligned)
@@ -653,7 +657,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
   for (int i = threadIdx.x; i < N; i += NT) {
     const float t = sL[i];
     rowsum[i] = t;
-    const float v = row_log2_weight(shift[i], sDl[i], t);
+    const float v = row_log2_weight(g[i], sDl[i], t);
     sL[i] = v;
     mloc = fmaxf(mloc, v);
   }
@@ -679,7 +683,7 @@ __global__ void __launch_bounds__(kCdfSlotThreads, D <= 8 ? 4 : 1) cdf_slots_ker
   unsigned long long* gcum = a.ws.cum + (size_t)s * N;
   for (int i = threadIdx.x; i < N; i += NT) gcum[i] = sC[i];
   if (threadIdx.x == 0) {
-    const double inc = degenerate ? (double)NAN : (double)M * kLn2d + log_fixed_total(sC[N - 1]);
+    const double inc = degenerate ? (double)NAN : lab_increment(a.ws.cbase[s], M, log_fixed_total(sC[N - 1]));
     a.ws.inc[s] = inc;
     cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
     if (degenerate || sC[N - 1] == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);

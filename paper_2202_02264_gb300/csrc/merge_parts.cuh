@@ -230,23 +230,40 @@ __device__ __forceinline__ float row_total(const float* row, int nT, int nTp) {
   return __fadd_rn(se, so);
 }
 
-// The row's base-2 log weight l_i = shift_i log2(e) + delta_i + log2 s_i (-inf when s_i = 0),
-// summed in FP64 in that order (delta_i, almost always 0, is added only when it is not: the
-// same bits with fewer FP64 operations, which run at under 2 per clock per SM on GB300).
-__device__ __forceinline__ float row_log2_weight(double shift, float delta, float total) {
-  if (!(total > 0.f)) return -INFINITY;
-  double v = shift * kLog2ed;
-  if (delta != 0.f) v += (double)delta;
-  return (float)(v + (double)log2f(total));
-}
-
-// The row's natural-log shift a_i + log f_max + B* + dl_i ln 2 in FP64, in that order:
-// shift_base gives the first three terms; a merged left block has a_i = -log N on every row,
-// so its base is computed once per combination with the same bits.
+// The row's natural-log shift a_i + log f_max + B* + dl_i ln 2 in FP64, in that order (the
+// lazy samplers' acceptance terms and the inspection entry points): shift_base gives the first
+// three terms; a merged left block has a_i = -log N on every row, so its base is computed
+// once per combination with the same bits.
 __device__ __forceinline__ double shift_base(float ai, float log_f_max, float bstar) {
   return (double)ai + (double)log_f_max + (double)bstar;
 }
 __device__ __forceinline__ double row_shift_total(double base, float dl) { return base + (double)dl * kLn2d; }
+
+// The dense samplers split the same shift into a combination base C (natural log, FP64, once
+// per combination) and a per-row base-2 offset g_i (FP32), shift_i = C + g_i ln 2:
+//   C = log f_max + B*, less log N for a merged left block (whose a_i = -log N on every row);
+//   g_i = a_i log2(e) + dl_i for a leaf left block (lw = its log-weights), dl_i for a merged one.
+// Only differences between rows reach the row weights, and C enters only the increment of
+// Eq. (Lab), so no per-row arithmetic is FP64 (GB300 issues under 2 DFMA per clock per SM).
+__device__ __forceinline__ double comb_base(bool left_leaf, float logN, float log_f_max, float bstar) {
+  return shift_base(left_leaf ? 0.f : -logN, log_f_max, bstar);
+}
+__device__ __forceinline__ float row_offset(bool left_leaf, float ai, float dl) {
+  return left_leaf ? __fmaf_rn(ai, kLog2e, dl) : dl;
+}
+
+// The row's base-2 log weight relative to C: l_i = (g_i + delta_i) + log2 s_i in FP32
+// (-inf when s_i = 0); delta_i is the extra shift of a row recomputed after underflow (else 0).
+__device__ __forceinline__ float row_log2_weight(float g, float delta, float total) {
+  if (!(total > 0.f)) return -INFINITY;
+  return __fadd_rn(__fadd_rn(g, delta), log2f(total));
+}
+
+// The increment of Eq. (Lab): log sum_ij omega_ij = C + M ln 2 + ln(S 2^-40), with M the
+// largest row log weight and S the row weights' exact fixed-point total.
+__device__ __forceinline__ double lab_increment(double C, float M, double log_total) {
+  return (C + (double)M * kLn2d) + log_total;
+}
 
 // The row weight r_i = 2^(l_i - M) in FP32, clamped to [0, 1].
 __device__ __forceinline__ float row_weight(float l, float M, bool degenerate) {

@@ -68,7 +68,7 @@ __host__ __device__ constexpr size_t rnd(size_t x, size_t a) { return (x + a - 1
 // Byte offsets inside one stage (one combination's data, N <= 512):
 //   opU, opV  the MMA row and column operands, [512][32 B] each, canonical K-major layout
 //   fV, fB    v_j [N][D] and beta_j, padded after every 32 columns (FP32)
-//   fU        u_i [N][D];  fAl alpha_i;  fDl delta_i (FP32);  fSh shift_i (FP64)
+//   fU        u_i [N][D];  fAl alpha_i;  fDl delta_i;  fG the row offsets g_i (row_offset)
 //   T         tile weights [N][16] (before the MMA: the loader's staged inputs)
 //   cum       exact prefix sums of the row weights (u64);  fL the row log weights
 template <int D>
@@ -80,8 +80,8 @@ struct Stage {
   static constexpr size_t fU = fB + rnd((size_t)(kFNmax + kFNmax / 32) * 4, 16);
   static constexpr size_t fAl = fU + (size_t)kFNmax * D * 4;
   static constexpr size_t fDl = fAl + (size_t)kFNmax * 4;
-  static constexpr size_t fSh = fDl + (size_t)kFNmax * 4;
-  static constexpr size_t T = fSh + (size_t)kFNmax * 8;
+  static constexpr size_t fG = fDl + (size_t)kFNmax * 4;
+  static constexpr size_t T = fG + (size_t)kFNmax * 4;
   static constexpr size_t cum = T + (size_t)kFNmax * kFTiles * 4;
   static constexpr size_t fL = cum + (size_t)kFNmax * 8;
   static constexpr size_t bytes = rnd(fL + (size_t)kFNmax * 4, 1024);
@@ -198,7 +198,7 @@ __device__ __forceinline__ bool issue_inputs(const MergeArgs& a, const Comb& cb,
 template <int D, int KIND>
 __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<D>& mp, unsigned char* st, int s,
                                           unsigned char* inb, int ct, int cw, int lane, int RT, CoreScratch& sc,
-                                          Comb* cb_stage) {
+                                          Comb* cb_stage, double* cbase_stage) {
   using L = Stage<D>;
   const int N = a.N, d = a.d;
   unsigned char* opU = st + L::opU;
@@ -208,7 +208,7 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
   float* fU = reinterpret_cast<float*>(st + L::fU);
   float* fAl = reinterpret_cast<float*>(st + L::fAl);
   float* fDl = reinterpret_cast<float*>(st + L::fDl);
-  double* fSh = reinterpret_cast<double*>(st + L::fSh);
+  float* fG = reinterpret_cast<float*>(st + L::fG);
   const Comb cb = sc.next_cb;  // read one combination ahead (issue_next)
   if (ct == 0) *cb_stage = cb;  // for the draws of this stage
   const int at = cb.at, c = cb.c, b = cb.b, K = cb.K;
@@ -329,7 +329,7 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
   bar_sync(kBarCore, kFCoreThreads);  // the rows read a sample of the columns
   // rows: u_i, alpha_i (less the row shift delta_i, which moves into shift_i), and the MMA
   // row [u, alpha_hi, alpha_lo, 1, 1]
-  const double base_m = shift_base(-a.logN, mp.log_f_max, bstar);  // a merged left block's
+  if (ct == 0) *cbase_stage = comb_base(left_leaf, a.logN, mp.log_f_max, bstar);
   for (int i = ct; i < N; i += kFCoreThreads) {
     float ul[D], ai;
     const float al0 = row_terms<D>(mp, N, d, a.logN, sXl, lastL, lwl, i, mu, ul, ai, corrupt);
@@ -340,8 +340,7 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
     for (int kk = 0; kk < D; ++kk) fU[(size_t)i * D + kk] = ul[kk];
     fAl[i] = al;
     fDl[i] = 0.f;
-    const double sh = row_shift_total(lwl != nullptr ? shift_base(ai, mp.log_f_max, bstar) : base_m, dl);
-    fSh[i] = sh;
+    fG[i] = row_offset(left_leaf, ai, dl);
     float ext[4];
     split_mma(al, KIND, &ext[0], &ext[1]);
     ext[2] = 1.f;
@@ -351,7 +350,8 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
 #pragma unroll
       for (int kk = 0; kk < D; ++kk) a.ws.U[((size_t)s * N + i) * D + kk] = ul[kk];
       a.ws.alpha[(size_t)s * N + i] = al;
-      a.ws.shift[(size_t)s * N + i] = sh;
+      a.ws.shift[(size_t)s * N + i] =
+          row_shift_total(shift_base(lwl != nullptr ? ai : -a.logN, mp.log_f_max, bstar), dl);
     }
   }
   if (corrupt) record_status(a.ws.status, DSMC_ERR_INVALID_ARG);
@@ -388,7 +388,7 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
   float* fU = reinterpret_cast<float*>(st + L::fU);
   float* fAl = reinterpret_cast<float*>(st + L::fAl);
   float* fDl = reinterpret_cast<float*>(st + L::fDl);
-  const double* fSh = reinterpret_cast<const double*>(st + L::fSh);
+  const float* fG = reinterpret_cast<const float*>(st + L::fG);
   float* Tq = reinterpret_cast<float*>(st + L::T);
   unsigned long long* cum = reinterpret_cast<unsigned long long*>(st + L::cum);
   float* fL = reinterpret_cast<float*>(st + L::fL);
@@ -407,7 +407,7 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
       under[atomicAdd(&se.n_under, 1)] = i;
     } else {
       if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = t;
-      const float v = row_log2_weight(fSh[i], fDl[i], t);
+      const float v = row_log2_weight(fG[i], fDl[i], t);
       fL[i] = v;
       mloc = fmaxf(mloc, v);
     }
@@ -426,7 +426,7 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
         si = isnan(si) ? 0.f : si;
         if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = si;
         fDl[i] = dl;
-        fL[i] = row_log2_weight(fSh[i], dl, si);
+        fL[i] = row_log2_weight(fG[i], dl, si);
       }
     }
     bar_sync(kBarEpi, NT);
@@ -484,13 +484,14 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
 }
 
 // The increment of Eq. (Lab) and log L of the new block (one thread, after the tile sums'
-// barrier has released the draws: its global read-modify-write is off their path); then the
-// row CDF's flags are cleared for the next combination.
-__device__ __forceinline__ void epi_increment(const MergeArgs& a, int s, EpiScratch& se) {
+// barrier has released the draws: its global read-modify-write is off their path), from the
+// combination base cbase its build computed; then the row CDF's flags are cleared for the
+// next combination.
+__device__ __forceinline__ void epi_increment(const MergeArgs& a, int s, double cbase, EpiScratch& se) {
   const Comb cb = comb_of(a, s);
   const unsigned long long S = se.S;
   const bool degenerate = se.degenerate != 0;
-  const double inc = degenerate ? (double)NAN : (double)se.M * kLn2d + log_fixed_total(S);
+  const double inc = degenerate ? (double)NAN : lab_increment(cbase, se.M, log_fixed_total(S));
   cb.logL[cb.at] = cb.logL[cb.at] + cb.logL[cb.c] + inc;
   if (degenerate || S == 0ull) record_status(a.ws.status, DSMC_ERR_DEGENERATE);
   if (se.nonfinite) record_status(a.ws.status, DSMC_ERR_NONFINITE);
@@ -541,6 +542,7 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
   __shared__ CoreScratch sc;
   __shared__ EpiScratch se;
   __shared__ Comb cbs[2];  // the combination of each stage (written by its build)
+  __shared__ double cbase_s[2];  // and its combination base C (comb_base)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = a.N, nTp = a.nTp;
@@ -650,7 +652,7 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
       epi_row_cdf<D>(a, fsm + (size_t)(k & 1) * L::bytes, blockIdx.x + k * gridDim.x, threadIdx.x, warp, lane, se);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tiles_full[k & 1]));
-      if (threadIdx.x == 0) epi_increment(a, blockIdx.x + k * gridDim.x, se);
+      if (threadIdx.x == 0) epi_increment(a, blockIdx.x + k * gridDim.x, cbase_s[k & 1], se);
     }
   } else if (warp < kFCtrlWarp) {
     // ------------------------------------------------------------------ core warps
@@ -698,7 +700,8 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
     for (int k = 0; k < ncomb && k < 2 && ok; ++k) {
       ok = inputs_ready(true);
       if (!ok) break;
-      core_load<D, KIND>(a, mp, fsm + (size_t)k * L::bytes, comb(k), inb, ct, cw, lane, RT, sc, &cbs[k]);
+      core_load<D, KIND>(a, mp, fsm + (size_t)k * L::bytes, comb(k), inb, ct, cw, lane, RT, sc, &cbs[k],
+                         &cbase_s[k]);
       if (k + 1 < ncomb) issue(k + 1);
       if (ct == 0) mbar_arrive(smem_u32(&ops_full[k]));
     }
@@ -714,7 +717,8 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
       if (k + 2 < ncomb) {
         ok = inputs_ready(false);  // the draws' end and the build's start: its barrier
         if (!ok) break;
-        core_load<D, KIND>(a, mp, fsm + (size_t)q * L::bytes, comb(k + 2), inb, ct, cw, lane, RT, sc, &cbs[q]);
+        core_load<D, KIND>(a, mp, fsm + (size_t)q * L::bytes, comb(k + 2), inb, ct, cw, lane, RT, sc, &cbs[q],
+                           &cbase_s[q]);
         if (k + 3 < ncomb) issue(k + 3);
         if (ct == 0) mbar_arrive(smem_u32(&ops_full[q]));
       }
