@@ -230,6 +230,20 @@ __device__ __forceinline__ float row_total(const float* row, int nT, int nTp) {
   return __fadd_rn(se, so);
 }
 
+// row_total of a row of nT <= 16 tiles that is only 8-byte aligned: the same sums in the
+// same order.
+__device__ __forceinline__ float row_total_small(const float* row, int nT) {
+  float se = 0.f, so = 0.f;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {  // pair p = tiles 2p, 2p + 1; even p into se, odd p into so
+    if (2 * p < nT) {
+      const float q = __fadd_rn(row[2 * p], 2 * p + 1 < nT ? row[2 * p + 1] : 0.f);
+      if (p & 1) so = __fadd_rn(so, q); else se = __fadd_rn(se, q);
+    }
+  }
+  return __fadd_rn(se, so);
+}
+
 // The row's natural-log shift a_i + log f_max + B* + dl_i ln 2 in FP64, in that order (the
 // lazy samplers' acceptance terms and the inspection entry points): shift_base gives the first
 // three terms; a merged left block has a_i = -log N on every row, so its base is computed
@@ -449,18 +463,29 @@ __device__ __forceinline__ int pick32(const float* x, int n, uint32_t w, int ref
 }
 
 // The tile stage over nT <= W tiles of a row held in registers: the largest tile is the
-// reference.
-template <int W>
+// reference.  The row is read as float4 (16-byte aligned rows) or, with T2, as float2
+// (8-byte aligned rows); entries past nT are ignored.
+template <int W, bool T2 = false>
 __device__ __forceinline__ int pick_tile(const float* Ti, int nT, uint32_t w, uint32_t* wrem = nullptr) {
   float t[W];
-  const float4* Ti4 = reinterpret_cast<const float4*>(Ti);
+  if (T2) {
+    const float2* Ti2 = reinterpret_cast<const float2*>(Ti);
 #pragma unroll
-  for (int k4 = 0; k4 < W / 4; ++k4) {
-    const float4 v = (4 * k4 < nT) ? Ti4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
-    t[4 * k4] = v.x;
-    t[4 * k4 + 1] = v.y;
-    t[4 * k4 + 2] = v.z;
-    t[4 * k4 + 3] = v.w;
+    for (int k2 = 0; k2 < W / 2; ++k2) {
+      const float2 v = (2 * k2 < nT) ? Ti2[k2] : make_float2(0.f, 0.f);
+      t[2 * k2] = v.x;
+      t[2 * k2 + 1] = v.y;
+    }
+  } else {
+    const float4* Ti4 = reinterpret_cast<const float4*>(Ti);
+#pragma unroll
+    for (int k4 = 0; k4 < W / 4; ++k4) {
+      const float4 v = (4 * k4 < nT) ? Ti4[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      t[4 * k4] = v.x;
+      t[4 * k4 + 1] = v.y;
+      t[4 * k4 + 2] = v.z;
+      t[4 * k4 + 3] = v.w;
+    }
   }
   float tmax = 0.f;
 #pragma unroll
@@ -564,8 +589,9 @@ __device__ __forceinline__ int pick_tile64(const float* Ti, int nT, uint32_t w, 
 // position of the flattened fixed-point CDF, S / N apart.
 // The tiles are held in registers when nT <= 32, the columns when the tile has <= 32.
 // SMALL: the caller guarantees nT <= 16 and tiles of <= 32 columns (N <= 512 at B = 32),
-// and only those paths are compiled (the same decisions as the general form).
-template <int D, bool PAD, bool SMALL = false>
+// and only those paths are compiled (the same decisions as the general form).  T2: the tile
+// rows are only 8-byte aligned (SMALL only).
+template <int D, bool PAD, bool SMALL = false, bool T2 = false>
 __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint32_t base, int gid, int n,
                                           int& i, int& j) {
   const int N = in.N, B = in.B, nT = in.nT, nTp = in.nTp;
@@ -604,7 +630,7 @@ __device__ __forceinline__ void draw_pair(const DrawIn& in, uint64_t seed, uint3
   const float* Ti = in.T + (size_t)i * nTp;
   int kt;
   if (SMALL || nT <= 16) {
-    kt = pick_tile<16>(Ti, nT, w2, wr);
+    kt = pick_tile<16, T2>(Ti, nT, w2, wr);
   } else if (nT <= 32) {
     kt = pick_tile<32>(Ti, nT, w2, wr);
   } else if (nT <= 64) {

@@ -62,6 +62,9 @@ constexpr int kBarCore = 1;                 // named barrier of the core warps
 constexpr int kBarEpi = 2;                  // named barrier of the epilogue warps
 constexpr int kFTileBytes = kMmaM * 32;     // one 128-row tile of one 32-byte K plane
 constexpr int kFTiles = kFNmax / 32;        // tiles of 32 columns per row (tile width 32)
+// Row stride (floats) of the stage's tile sums: 18, not 16, so that the rows of a warp fall
+// on different banks (the epilogue stores 32 consecutive rows, the draws read random rows).
+constexpr int kFTs = kFTiles + 2;
 
 __host__ __device__ constexpr size_t rnd(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -69,7 +72,7 @@ __host__ __device__ constexpr size_t rnd(size_t x, size_t a) { return (x + a - 1
 //   opU, opV  the MMA row and column operands, [512][32 B] each, canonical K-major layout
 //   fV, fB    v_j [N][D] and beta_j, padded after every 32 columns (FP32)
 //   fU        u_i [N][D];  fAl alpha_i;  fDl delta_i;  fG the row offsets g_i (row_offset)
-//   T         tile weights [N][16] (before the MMA: the loader's staged inputs)
+//   T         tile weights [N][kFTs] (16 tiles and a 2-float pad per row)
 //   cum       exact prefix sums of the row weights (u64);  fL the row log weights
 template <int D>
 struct Stage {
@@ -82,7 +85,7 @@ struct Stage {
   static constexpr size_t fDl = fAl + (size_t)kFNmax * 4;
   static constexpr size_t fG = fDl + (size_t)kFNmax * 4;
   static constexpr size_t T = fG + (size_t)kFNmax * 4;
-  static constexpr size_t cum = T + (size_t)kFNmax * kFTiles * 4;
+  static constexpr size_t cum = T + (size_t)kFNmax * kFTs * 4;
   static constexpr size_t fL = cum + (size_t)kFNmax * 8;
   static constexpr size_t bytes = rnd(fL + (size_t)kFNmax * 4, 1024);
 };
@@ -382,7 +385,7 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
                                             EpiScratch& se) {
   using L = Stage<D>;
   constexpr int NT = kFEpiWarps * 32;
-  const int N = a.N, nT = a.nT, nTp = a.nTp;
+  const int N = a.N, nT = a.nT, nTp = a.nTp;  // nTp: the workspace's row stride (inspection)
   float* fV = reinterpret_cast<float*>(st + L::fV);
   float* fB = reinterpret_cast<float*>(st + L::fB);
   float* fU = reinterpret_cast<float*>(st + L::fU);
@@ -419,10 +422,10 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
     for (int uq = ew; uq < se.n_under; uq += kFEpiWarps) {
       const int i = under[uq];
       float si, dl;
-      recompute_row<D, true>(fU + (size_t)i * D, fAl[i], fV, fB, N, a.B, nT, Tq + (size_t)i * nTp, &si, &dl);
+      recompute_row<D, true>(fU + (size_t)i * D, fAl[i], fV, fB, N, a.B, nT, Tq + (size_t)i * kFTs, &si, &dl);
       __syncwarp();
       if (lane == 0) {
-        si = row_total(Tq + (size_t)i * nTp, nT, nTp);
+        si = row_total_small(Tq + (size_t)i * kFTs, nT);
         si = isnan(si) ? 0.f : si;
         if (a.inspect) a.ws.rowsum[(size_t)s * N + i] = si;
         fDl[i] = dl;
@@ -478,7 +481,7 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
     for (int i = et; i < N; i += NT) {
       a.ws.cum[(size_t)s * N + i] = cum[i];
       a.ws.delta[(size_t)s * N + i] = fDl[i];
-      for (int kt = 0; kt < nT; ++kt) a.ws.T[((size_t)s * N + i) * nTp + kt] = Tq[(size_t)i * nTp + kt];
+      for (int kt = 0; kt < nT; ++kt) a.ws.T[((size_t)s * N + i) * nTp + kt] = Tq[(size_t)i * kFTs + kt];
     }
   }
 }
@@ -518,12 +521,12 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
   in.N = N;
   in.B = a.B;
   in.nT = a.nT;
-  in.nTp = a.nTp;
+  in.nTp = kFTs;
   const int n_lo = cb.conditional ? 1 : 0;
   const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
   for (int n = n_lo + ct; n < n_hi; n += kFCoreThreads) {
     int i, j;
-    draw_pair<D, true, true>(in, cb.seed, cb.base, cb.gid, n, i, j);
+    draw_pair<D, true, true, true>(in, cb.seed, cb.base, cb.gid, n, i, j);
     o.put(n, i, j);
   }
   // (no barrier here: the next build starts with one, before it writes this stage)
@@ -545,7 +548,7 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
   __shared__ double cbase_s[2];  // and its combination base C (comb_base)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int N = a.N, nTp = a.nTp;
+  const int N = a.N;
   const int RT = (N + kMmaM - 1) / kMmaM;
   const int ncomb = a.mc > (int)blockIdx.x ? (a.mc - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const volatile int* abort_v = &abort_s;
@@ -630,9 +633,9 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
             }
             if (row < N) {
               if (col0 + 32 < N)
-                *reinterpret_cast<float2*>(Tq + (size_t)row * nTp + col0 / 32) = make_float2(t0, t1);
+                *reinterpret_cast<float2*>(Tq + (size_t)row * kFTs + col0 / 32) = make_float2(t0, t1);
               else if (col0 < N)
-                Tq[(size_t)row * nTp + col0 / 32] = t0;
+                Tq[(size_t)row * kFTs + col0 / 32] = t0;
             }
             const float q = __fadd_rn(t0, t1);  // 0 past the last tile
             if ((col0 / 64) & 1)
