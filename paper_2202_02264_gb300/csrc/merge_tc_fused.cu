@@ -145,8 +145,11 @@ struct CoreScratch {
   float red[kFCoreWarps];
   float mu[4];
   float bstar;
-  Comb next_cb;   // the next build's combination, and its observation and proposal rows,
-  float next_yc[4], next_qm[4], next_qs[4];  // read one combination ahead
+  // the descriptor of a build's combination and its observation and proposal rows, read one
+  // build ahead (double-buffered by the parity of the build: build m reads slot m & 1 while
+  // the next one's is written)
+  Comb nx_cb[2];
+  float nx_yc[2][4], nx_qm[2][4], nx_qs[2][4];
   int in_bulk;    // the next build's inputs come by bulk copy (1) or are staged by it (0)
   int in_pend;    // bulk copies issued and not yet waited for
   int in_phase;   // completed phases of the inputs barrier
@@ -195,13 +198,27 @@ __device__ __forceinline__ bool issue_inputs(const MergeArgs& a, const Comb& cb,
   return true;
 }
 
+// The observation row and proposal row of the descriptor in scratch slot q (one thread).
+template <int D>
+__device__ __forceinline__ void read_rows(const MergeArgs& a, const ModelParams<D>& mp, CoreScratch& sc, int q) {
+  const Comb& cb = sc.nx_cb[q];
+  float qm[D], qs[D];
+  proposal_at<D>(mp, cb.y, cb.prop_mean, cb.prop_std, cb.c, qm, qs);
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    sc.nx_yc[q][kk] = kk < D && kk < a.d ? cb.y[(size_t)cb.c * a.d + kk] : 0.f;
+    sc.nx_qm[q][kk] = kk < D ? qm[kk] : 0.f;
+    sc.nx_qs[q][kk] = kk < D ? qs[kk] : 1.f;
+  }
+}
+
 // Operand build of combination s into stage st (the core warps): the two particle slices and
 // index maps staged with vector loads, the column pass (states, b'_j, mu, B*, v_j, beta_j),
 // the row pass (u_i, alpha_i, the row shift), FP32 copies for the draws and the MMA rows.
 template <int D, int KIND>
 __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<D>& mp, unsigned char* st, int s,
                                           unsigned char* inb, int ct, int cw, int lane, int RT, CoreScratch& sc,
-                                          Comb* cb_stage, double* cbase_stage) {
+                                          Comb* cb_stage, double* cbase_stage, int par, int s_next) {
   using L = Stage<D>;
   const int N = a.N, d = a.d;
   unsigned char* opU = st + L::opU;
@@ -212,7 +229,7 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
   float* fAl = reinterpret_cast<float*>(st + L::fAl);
   float* fDl = reinterpret_cast<float*>(st + L::fDl);
   float* fG = reinterpret_cast<float*>(st + L::fG);
-  const Comb cb = sc.next_cb;  // read one combination ahead (issue_next)
+  const Comb cb = sc.nx_cb[par];  // read one build ahead
   if (ct == 0) *cb_stage = cb;  // for the draws of this stage
   const int at = cb.at, c = cb.c, b = cb.b, K = cb.K;
   const bool left_leaf = (cb.level == 0);
@@ -243,12 +260,17 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
   float yc[D], qm[D], qs[D], qinv[D];
 #pragma unroll
   for (int kk = 0; kk < D; ++kk) {
-    yc[kk] = sc.next_yc[kk];
-    qm[kk] = sc.next_qm[kk];
-    qs[kk] = sc.next_qs[kk];
+    yc[kk] = sc.nx_yc[par][kk];
+    qm[kk] = sc.nx_qm[par][kk];
+    qs[kk] = sc.nx_qs[par][kk];
   }
   const float qnorm = proposal_consts<D>(d, qs, qinv);
-  bar_sync(kBarCore, kFCoreThreads);
+  if (!sc.in_bulk) bar_sync(kBarCore, kFCoreThreads);  // the inputs it staged (bulk ones were waited for)
+  // The last core warp has one group of the column pass and one row of the row pass, the
+  // others up to two: in those idle second rounds one of its threads reads the next build's
+  // descriptor, then its observation and proposal rows (dependent global round trips, off
+  // the critical path), into the other scratch slot.
+  const bool prefetcher = s_next >= 0 && cw == kFCoreWarps - 1 && lane == 0;
 
   // column pass: b'_j, states, the column mean mu (groups of 32 Q columns, each summed by
   // one warp lane-sequentially then by a butterfly, group sums in group order: the same
@@ -283,12 +305,18 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
         if (lane == 0) sc.gsum[gg * D + kk] = t;
       }
     }
+    if (prefetcher) sc.nx_cb[par ^ 1] = comb_of(a, s_next);
     bmax = warp_max(bmax);
     if (lane == 0) sc.red[cw] = bmax;
     bar_sync(kBarCore, kFCoreThreads);
-    if (ct < D) {
+    if (ct < D) {  // G <= kFNmax / 32 groups: the loads first, then the sum in group order
+      float gs[kFNmax / 32];
+#pragma unroll
+      for (int gg = 0; gg < kFNmax / 32; ++gg) gs[gg] = gg < G ? sc.gsum[gg * D + ct] : 0.f;
       float t = 0.f;
-      for (int gg = 0; gg < G; ++gg) t += sc.gsum[gg * D + ct];
+#pragma unroll
+      for (int gg = 0; gg < kFNmax / 32; ++gg)
+        if (gg < G) t += gs[gg];
       sc.mu[ct] = t / (float)N;
     }
     if (ct == 0) {
@@ -357,8 +385,7 @@ __device__ __forceinline__ void core_load(const MergeArgs& a, const ModelParams<
           row_shift_total(shift_base(lwl != nullptr ? ai : -a.logN, mp.log_f_max, bstar), dl);
     }
   }
-  if (corrupt) record_status(a.ws.status, DSMC_ERR_INVALID_ARG);
-  if (bad) record_status(a.ws.status, DSMC_ERR_NONFINITE);
+  if (prefetcher) read_rows<D>(a, mp, sc, par ^ 1);
   if (corrupt) record_status(a.ws.status, DSMC_ERR_INVALID_ARG);
   if (bad) record_status(a.ws.status, DSMC_ERR_NONFINITE);
   fence_proxy_async();  // the operand rows, written by these threads, feed the tensor core
@@ -665,27 +692,15 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
     unsigned char* inb = fsm + 2 * L::bytes;
     const uint32_t in_bar = smem_u32(&in_full);
     auto comb = [&](int k) { return (int)blockIdx.x + k * (int)gridDim.x; };
-    // one thread starts the inputs of combination k (the buffer is free: the previous build
-    // has read it, and its closing fence orders those reads before the bulk copies)
-    // and reads the combination's descriptor and its observation and proposal rows, for its
-    // build (each a dependent global round trip, here off the build's path)
-    auto issue = [&](int k) {
-      if (ct == 0) {
-        const Comb cb = comb_of(a, comb(k));
-        sc.next_cb = cb;
-        float qm[D], qs[D];
-        proposal_at<D>(mp, cb.y, cb.prop_mean, cb.prop_std, cb.c, qm, qs);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          sc.next_yc[kk] = kk < D && kk < a.d ? cb.y[(size_t)cb.c * a.d + kk] : 0.f;
-          sc.next_qm[kk] = kk < D ? qm[kk] : 0.f;
-          sc.next_qs[kk] = kk < D ? qs[kk] : 1.f;
-        }
-        sc.in_bulk = sc.in_pend = issue_inputs(a, cb, inb, in_bar) ? 1 : 0;
-      }
+    // Build m (of combination m) reads its descriptor from scratch slot m & 1 and prefetches
+    // the next build's into the other slot.  After build m has read the inputs buffer (its
+    // closing fence orders those reads before the bulk copies), one thread starts the next
+    // build's inputs from that descriptor.
+    auto bulk_next = [&](int m) {
+      if (ct == 0) sc.in_bulk = sc.in_pend = issue_inputs(a, sc.nx_cb[(m + 1) & 1], inb, in_bar) ? 1 : 0;
     };
     // every core thread waits for bulk-copied inputs; false on an abort or a timeout
-    // (sync_first: a barrier first, where no other one has passed since issue wrote sc.in_bulk)
+    // (sync_first: a barrier first, where no other one has passed since sc.in_bulk was written)
     auto inputs_ready = [&](bool sync_first) -> bool {
       if (sync_first) bar_sync(kBarCore, kFCoreThreads);
       bool ok = true;
@@ -698,14 +713,20 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
       return ok;
     };
     bool ok = true;
-    if (ct == 0) sc.in_phase = sc.in_pend = sc.in_bulk = 0;
-    if (ncomb > 0) issue(0);
+    if (ct == 0) {
+      sc.in_phase = sc.in_pend = sc.in_bulk = 0;
+      if (ncomb > 0) {  // the first build's descriptor and inputs
+        sc.nx_cb[0] = comb_of(a, comb(0));
+        read_rows<D>(a, mp, sc, 0);
+        sc.in_bulk = sc.in_pend = issue_inputs(a, sc.nx_cb[0], inb, in_bar) ? 1 : 0;
+      }
+    }
     for (int k = 0; k < ncomb && k < 2 && ok; ++k) {
       ok = inputs_ready(true);
       if (!ok) break;
       core_load<D, KIND>(a, mp, fsm + (size_t)k * L::bytes, comb(k), inb, ct, cw, lane, RT, sc, &cbs[k],
-                         &cbase_s[k]);
-      if (k + 1 < ncomb) issue(k + 1);
+                         &cbase_s[k], k & 1, k + 1 < ncomb ? comb(k + 1) : -1);
+      if (k + 1 < ncomb) bulk_next(k);
       if (ct == 0) mbar_arrive(smem_u32(&ops_full[k]));
     }
     for (int k = 0; k < ncomb && ok; ++k) {
@@ -721,8 +742,8 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
         ok = inputs_ready(false);  // the draws' end and the build's start: its barrier
         if (!ok) break;
         core_load<D, KIND>(a, mp, fsm + (size_t)q * L::bytes, comb(k + 2), inb, ct, cw, lane, RT, sc, &cbs[q],
-                           &cbase_s[q]);
-        if (k + 3 < ncomb) issue(k + 3);
+                           &cbase_s[q], k & 1, k + 3 < ncomb ? comb(k + 3) : -1);
+        if (k + 3 < ncomb) bulk_next(k + 2);
         if (ct == 0) mbar_arrive(smem_u32(&ops_full[q]));
       }
     }
