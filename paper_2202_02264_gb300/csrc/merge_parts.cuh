@@ -432,27 +432,26 @@ __device__ __forceinline__ uint32_t remainder_word(unsigned long long T, unsigne
 // When wrem is not null it receives remainder_word of the target inside the chosen entry.
 template <int W>
 __device__ __forceinline__ int pick_w(const float* x, int n, uint32_t w, int ref_be, uint32_t* wrem = nullptr) {
-  uint32_t q[W];
+  uint32_t c[W];  // the prefix sums, formed as Q is summed
   uint32_t Q = 0;
 #pragma unroll
   for (int k = 0; k < W; ++k) {
-    q[k] = (k < n) ? q24(x[k], ref_be) : 0u;
-    Q += q[k];
+    Q += (k < n) ? q24(x[k], ref_be) : 0u;
+    c[k] = Q;
   }
   if (Q == 0u) {
     if (wrem) *wrem = w;
     return 0;
   }
   const uint32_t T = __umulhi(w, Q);
-  uint32_t c = 0, bef = 0, aft = 0xFFFFFFFFu;
+  uint32_t bef = 0, aft = 0xFFFFFFFFu;
   int idx = 0;
 #pragma unroll
   for (int k = 0; k < W; ++k) {
-    c += q[k];
-    idx += (c <= T) ? 1 : 0;
+    idx += (c[k] <= T) ? 1 : 0;
     if (wrem) {
-      bef = (c <= T) ? c : bef;
-      aft = (c > T) ? min(aft, c) : aft;
+      bef = (c[k] <= T) ? c[k] : bef;
+      aft = (c[k] > T) ? min(aft, c[k]) : aft;
     }
   }
   if (wrem) *wrem = remainder_word(T, bef, aft);
@@ -741,6 +740,23 @@ struct SlotOut {
       pr[n] = j;
       first_out[n] = left_leaf ? i : first_L[i];
       last_out[n] = right_leaf ? j : last_R[j];
+    } else {
+      star[0] = i;
+      star[1] = j;
+    }
+  }
+  // put in two halves: the composed map entries (global loads for merged blocks), and the
+  // stores, which a caller can place after other work while the loads are in flight
+  __device__ __forceinline__ void maps(int i, int j, int32_t& fi, int32_t& lj) const {
+    fi = left_leaf ? i : first_L[i];
+    lj = right_leaf ? j : last_R[j];
+  }
+  __device__ __forceinline__ void store(int n, int i, int j, int32_t fi, int32_t lj) const {
+    if (n < N) {
+      pl[n] = i;
+      pr[n] = j;
+      first_out[n] = fi;
+      last_out[n] = lj;
     } else {
       star[0] = i;
       star[1] = j;

@@ -551,11 +551,23 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
   in.nTp = kFTs;
   const int n_lo = cb.conditional ? 1 : 0;
   const int n_hi = N + ((cb.conditional && cb.root) ? 1 : 0);
+  // each slot's map loads are issued when it is drawn and its stores made after the next
+  // slot of the thread, so the loads of a merged block's maps overlap that draw
+  int pn = -1, pi = 0, pj = 0;
+  int32_t pf = 0, pq = 0;
   for (int n = n_lo + ct; n < n_hi; n += kFCoreThreads) {
     int i, j;
     draw_pair<D, true, true, true>(in, cb.seed, cb.base, cb.gid, n, i, j);
-    o.put(n, i, j);
+    int32_t fi, lj;
+    o.maps(i, j, fi, lj);
+    if (pn >= 0) o.store(pn, pi, pj, pf, pq);
+    pn = n;
+    pi = i;
+    pj = j;
+    pf = fi;
+    pq = lj;
   }
+  if (pn >= 0) o.store(pn, pi, pj, pf, pq);
   // (no barrier here: the next build starts with one, before it writes this stage)
 }
 
