@@ -6,7 +6,7 @@ Three knobs shape how a batch's levels are launched:
     larger levels go through the split kernels (column/row terms, the tensor-core or
     CUDA-core tile sums, the row CDF with the draws);
   * ``max_merges_per_launch``: the chunk of combinations per launch (workspace size versus
-    launch count);
+    launch count; larger chunks are searched for the fused tensor-core kernel);
   * ``tc_fused`` (tensor-core precisions, N <= 512, d <= 4): the other levels run either as
     one persistent warp-specialised kernel per chunk (operand rows, tcgen05 cross term,
     exponentials, row CDF and draws of a combination on one SM) or as the split kernels;
@@ -35,6 +35,10 @@ from . import workloads as W
 
 FUSED_CANDIDATES = (-1, 8, 32, 128)
 CHUNK_CANDIDATES = (1024, 4096, 16384)
+# the fused tensor-core kernel keeps a combination's intermediates in shared memory, so its
+# chunks can be larger (fewer launches, each with its pipeline fill and drain); the workspace
+# still sizes the split path's per-combination arrays by the chunk (13 GB at 131072, N = 512)
+TC_CHUNK_CANDIDATES = (16384, 65536, 131072)
 TC_FUSED_CANDIDATES = (-1, 1)
 TILE_CANDIDATES = (32, 64)
 
@@ -75,7 +79,7 @@ def _store_cache(cache: dict):
 
 
 def candidates(model: W.SSM, N: int, compute: int, fused=FUSED_CANDIDATES, chunks=CHUNK_CANDIDATES,
-               tc=TC_FUSED_CANDIDATES, tiles=TILE_CANDIDATES):
+               tc=TC_FUSED_CANDIDATES, tiles=TILE_CANDIDATES, tc_chunks=TC_CHUNK_CANDIDATES):
     """The (fused_max_merges, max_merges_per_launch, tc_fused, tile_cols) schedules searched
     for this shape: the fused tensor-core kernel where eligible (32-column tiles only), the
     64-column tiles where they give at most 64 tiles per row."""
@@ -88,22 +92,22 @@ def candidates(model: W.SSM, N: int, compute: int, fused=FUSED_CANDIDATES, chunk
             if tile == 32 and (N + 31) // 32 > 64:
                 continue
             for fm in fused:
-                for mc in chunks:
+                for mc in (tc_chunks if tcf > 0 else chunks):
                     out.append((fm, mc, tcf, tile))
     return out
 
 
 def tune_batch(model: W.SSM, Ks, N: int, ys, compute: int, use_cache: bool = True,
                fused=FUSED_CANDIDATES, chunks=CHUNK_CANDIDATES, tc=TC_FUSED_CANDIDATES,
-               tiles=TILE_CANDIDATES) -> dict:
+               tiles=TILE_CANDIDATES, tc_chunks=TC_CHUNK_CANDIDATES) -> dict:
     """The fastest (fused_max_merges, max_merges_per_launch, tc_fused, tile_cols) for this
     batch shape, with the timings of every candidate (ms per batched smoothing)."""
     import torch
 
     from . import dsmc
     dev_name = torch.cuda.get_device_name()
-    key = shape_key(model, Ks, N, compute, dev_name) + "|tc|tile"
-    cands = candidates(model, N, compute, fused, chunks, tc, tiles)
+    key = shape_key(model, Ks, N, compute, dev_name) + "|tc|tile|tcchunk"
+    cands = candidates(model, N, compute, fused, chunks, tc, tiles, tc_chunks)
     cache = _load_cache() if use_cache else {}
     if key in cache:
         return cache[key]

@@ -490,15 +490,21 @@ __device__ __forceinline__ void epi_row_cdf(const MergeArgs& a, unsigned char* s
     if (lane == 31) se.rowtot[c] = v;
   }
   bar_sync(kBarEpi, NT);
-  for (int c = ew; c < C; c += kFEpiWarps) {
-    unsigned long long carry = 0;
-    for (int q = 0; q < c; ++q) carry += se.rowtot[q];
-    const int i = 32 * c + lane;
-    if (i < N) cum[i] += carry;
+  // the rows' totals (C <= 32) scanned by every warp at once, lane q holding row q's
+  unsigned long long tl = lane < C ? se.rowtot[lane] : 0ull;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, tl, o);
+    if (lane >= o) tl += t;
   }
+  for (int c = ew; c < C; c += kFEpiWarps) {
+    const unsigned long long carry = __shfl_sync(0xffffffffu, tl, c > 0 ? c - 1 : 0);
+    const int i = 32 * c + lane;
+    if (i < N && c > 0) cum[i] += carry;
+  }
+  const unsigned long long S_all = __shfl_sync(0xffffffffu, tl, C - 1);
   if (et == 0) {
-    unsigned long long S = 0;
-    for (int q = 0; q < C; ++q) S += se.rowtot[q];
+    const unsigned long long S = S_all;
     se.S = S;
     se.M = M;
     se.degenerate = degenerate ? 1 : 0;

@@ -34,6 +34,9 @@ def test_candidates_search_the_tile_width_and_keep_the_fused_kernel_at_32():
     assert all(t == 32 for _, _, tcf, t in c if tcf > 0)        # the fused kernel takes 32
     assert any(tcf > 0 for _, _, tcf, _ in c)                   # eligible: BF16, N <= 512, d <= 4
     assert len(c) == len(set(c))
+    # the fused kernel is searched at its own (larger) chunks, the split path at the others
+    assert {mc for _, mc, tcf, _ in c if tcf > 0} == set(A.TC_CHUNK_CANDIDATES)
+    assert {mc for _, mc, tcf, _ in c if tcf < 0} == set(A.CHUNK_CANDIDATES)
     # FP32 cross term: no fused tensor-core candidates; N = 4096: only the wider tiles
     assert all(tcf < 0 for _, _, tcf, _ in A.candidates(m, 512, 0))
     assert {t for *_, t in A.candidates(m, 4096, 2)} == {64}
