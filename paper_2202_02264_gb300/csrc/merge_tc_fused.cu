@@ -541,7 +541,10 @@ template <int D>
 __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st, const Comb& cb, int ct) {
   using L = Stage<D>;
   const int N = a.N;
-  const SlotOut o = slot_out(a, cb, ct == 0);
+  // the output pointers are recomputed from the stage's descriptor at each store rather than
+  // held through the draws (fewer live registers: no spills); thread 0 also writes slot 0
+  // of a conditional combination
+  if (ct == 0) (void)slot_out(a, cb, true);
   DrawIn in;
   in.sys = (a.resampler == DSMC_SYSTEMATIC && !cb.conditional) ? 1 : 0;
   in.cum = reinterpret_cast<unsigned long long*>(st + L::cum);
@@ -565,6 +568,7 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
     int i, j;
     draw_pair<D, true, true, true>(in, cb.seed, cb.base, cb.gid, n, i, j);
     int32_t fi, lj;
+    const SlotOut o = slot_out(a, cb, false);
     o.maps(i, j, fi, lj);
     if (pn >= 0) o.store(pn, pi, pj, pf, pq);
     pn = n;
@@ -573,7 +577,7 @@ __device__ __forceinline__ void core_draw(const MergeArgs& a, unsigned char* st,
     pf = fi;
     pq = lj;
   }
-  if (pn >= 0) o.store(pn, pi, pj, pf, pq);
+  if (pn >= 0) slot_out(a, cb, false).store(pn, pi, pj, pf, pq);
   // (no barrier here: the next build starts with one, before it writes this stage)
 }
 
