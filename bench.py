@@ -59,7 +59,7 @@ COMBINED_EXP_FACTOR = 1.28
 # launch of 4096 combinations (working set above L2; profiles/kernels_batched_n64_N512.md),
 # scaled by the timed step's combinations per launch.
 TRAFFIC_PER_COMBINATION = {("batched_lgssm_d4", "bf16"): {"bytes": 52993, "kernel": "rowsum_tc_kernel<BF16, 1 K plane>"},
-                           ("batched_lgssm_d4", "bf16", "fused"): {"bytes": 23269,
+                           ("batched_lgssm_d4", "bf16", "fused"): {"bytes": 23150,
                                                                   "kernel": "merge_tc_fused_kernel<4, BF16>"}}
 
 # ncu DRAM bytes per launch of the single-sequence workloads' dominant kernel (none current:
