@@ -702,9 +702,12 @@ __global__ void __launch_bounds__(kFThreads, 1) merge_tc_fused_kernel(MergeArgs 
       // they agree whether to go on; then the row CDF of this combination
       if (!bar_and(kBarEpi, kFEpiWarps * 32, !stop)) break;
       epi_row_cdf<D>(a, fsm + (size_t)(k & 1) * L::bytes, blockIdx.x + k * gridDim.x, threadIdx.x, warp, lane, se);
+      // the combination base is read before the draws are released: the build that follows
+      // them rewrites it
+      const double cbase_k = threadIdx.x == 0 ? cbase_s[k & 1] : 0.0;
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tiles_full[k & 1]));
-      if (threadIdx.x == 0) epi_increment(a, blockIdx.x + k * gridDim.x, cbase_s[k & 1], se);
+      if (threadIdx.x == 0) epi_increment(a, blockIdx.x + k * gridDim.x, cbase_k, se);
     }
   } else if (warp < kFCtrlWarp) {
     // ------------------------------------------------------------------ core warps
