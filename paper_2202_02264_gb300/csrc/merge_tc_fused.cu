@@ -6,19 +6,22 @@
 //
 // One CTA per SM walks the combinations s = blockIdx.x, blockIdx.x + gridDim.x, ... of the
 // launch.  Each combination's data lives in one of two shared-memory stages:
-//   - 11 core warps alternate, for k = 0, 1, ...: the draws of combination k (the row
-//     totals, the row weights and their exact 2^40 fixed-point prefix sums, the increment of
-//     Eq. (Lab), every slot's pair in three exact inverse-CDF stages and the new block's
-//     index maps), then the operand build of combination k + 2 into the stage k released
-//     (its inputs -- two particle slices and two leaf-weight or index-map rows -- brought
-//     into their own buffer by bulk copies issued one combination ahead; the column pass --
-//     states, b'_j, mu, B*, v_j, beta_j -- and the row pass -- u_i, alpha_i, the row shift --
-//     as FP32 copies for the draws and as the BF16 / TF32 MMA rows [u, alpha_hi, alpha_lo, 1,
-//     1] and [v, 1, 1, beta_hi, beta_lo] in the canonical K-major layout);
+//   - 11 core warps alternate, for k = 0, 1, ...: the draws of combination k (every slot's
+//     pair in three exact inverse-CDF stages over the row CDF the epilogue built, and the
+//     new block's index maps), then the operand build of combination k + 2 into the stage k
+//     released (its inputs -- two particle slices and two leaf-weight or index-map rows --
+//     brought into their own buffer by bulk copies issued after the build before it; the
+//     column pass -- states, b'_j, mu, B*, v_j, beta_j -- and the row pass -- u_i, alpha_i,
+//     the row offsets -- as FP32 copies for the draws and as the BF16 / TF32 MMA rows [u,
+//     alpha_hi, alpha_lo, 1, 1] and [v, 1, 1, beta_hi, beta_lo] in the canonical K-major
+//     layout).  The next build's descriptor and observation / proposal rows are read during
+//     a build by the last core warp, in the second rounds it has no work in;
 //   - 1 control thread issues, for combination k + 1, one tcgen05.mma (M = N = 128) per (row
 //     tile, column block) into one of four 128-column TMEM accumulators;
 //   - 8 epilogue warps read each accumulator (tcgen05.ld; warp (g, h) lanes 32 g.. and
-//     columns 64 h..), take 2^x on MUFU and keep the tile sums in shared memory.
+//     columns 64 h..), take 2^x on MUFU and keep the tile sums in shared memory, then build
+//     the combination's row CDF (row totals, row log weights, their exact 2^40 fixed-point
+//     prefix sums) before releasing its draws, and add the increment of Eq. (Lab) to log L.
 // So the exponentials of one combination overlap the draws and the operand build of two
 // others, and the period of a combination is the larger of the two.
 // The arithmetic is the split path's, function for function (the column and row terms of
